@@ -1,0 +1,1433 @@
+/*
+ * ovl_oracle.c -- plain, slow FP64 CPU oracle for one timestep of the
+ * overlapping-partition rigid-body method of Kale & Kry, "Distributed
+ * Simulation of Large Multi-body Systems" (Algorithm 1, Sections 3-5).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, calls or
+ * executes this file: it is used by the tests, by the smoke check and by the
+ * benchmark's CPU-baseline leg.  It shares no code, header, table or constant
+ * generator with the CUDA library; both are fed from the seeded scene
+ * generators only.
+ *
+ * Every step is written in the paper's order and notation, single-threaded,
+ * with no blocking, fusion or reordering:
+ *
+ *   contacts  (Alg 1 line "getContacts", Section 5.4)      orc_contacts
+ *   graph G^t (Section 5.1, constraint graph)              orc_graph
+ *   LOADBALANCE (Alg 6) + BRIDGE (Alg 7)                   orc_load_balance
+ *   ASSIGNTOOVERLAPSET (Alg 2) + GROWOVERLAP (Alg 3)       orc_assign_overlap
+ *   P_i, O (Eq 9, Eq 10)                                   entries / pairs
+ *   per-worker PGS on the MLCP of Eq 1-7 + integration     solve_worker
+ *   D(o,i) (Eq 16, searched as in Alg 5)                   orc_geodesics
+ *   weights (Eq 15) and BLEND (Alg 4, Eq 11-14)            orc_weights/orc_blend
+ *
+ * Readings of passages that are silent, ambiguous or garbled (each one is
+ * listed in the design notes):
+ *  - PGS rows: contact = normal + two box-friction tangents bounded by
+ *    +-mu*lambda_n (current lambda_n); ball joint = three world-axis rows with
+ *    bounds +-inf.  Normal target -phi/h when phi > 0 (speculative), else
+ *    erp*max(-phi - slop, 0)/h; joint target -erp*(e.(pB - pA))/h; no
+ *    compliance (C = 0) -- Eq 2-4 written in the usual velocity-level form.
+ *  - Gauss-Seidel order: constraints are coloured greedily per worker in
+ *    descending priority mix64(kind<<62 ^ key) (SplitMix64 finaliser);
+ *    sweeps go colour by colour, constraints in canonical order, rows
+ *    normal, t1, t2 (joints x, y, z).  The paper does not colour (Bullet is
+ *    sequential); constraints of one colour share no dynamic body, so the
+ *    order inside a colour does not change any result.
+ *  - Contact test: a pair is in contact when its gap phi <= margin.  Because
+ *    that test decides an integer, it is evaluated in FP32 on FP32-rounded
+ *    positions with the operation order written below; so is the choice of
+ *    the tangent axis (the axis of the smallest |n_k| of the FP32 normal,
+ *    ties to the lower index).  Everything after the decision is FP64.
+ *  - Alg 6 input = every current contact between two dynamic bodies in
+ *    canonical (key) order; <W_x> = sum over workers in W_x of |P_w|, live;
+ *    the tie at line 5 activates B in W_A; line 14 uses W_A, W_B as read at
+ *    line 3; line 21 ties go to the lowest worker index; the removal branches
+ *    (lines 16-24) run only on steps whose index is a multiple of the removal
+ *    cadence.  Alg 7 reads the body under test ("B" in its line 2 is b).
+ *  - Alg 3 line 5 reads W_r \ W_b.  Alg 2 walks joints in index order over the
+ *    joint graph.
+ *  - Alg 5 / Eq 16: D(o,i) is the smallest BFS depth (1..beta) at which a body
+ *    active only in worker i is met; unmet workers get weight 0 and a body
+ *    with no worker met gets uniform weights.
+ *  - Alg 4: the sign test compares q_i with q_0, the copy of the lowest-index
+ *    worker; bodies outside O take their single copy unchanged.
+ *  - Newly activated bodies start from the blended state (every worker reads
+ *    the one blended state at the start of a step, Alg 1 lines 7-9).
+ *
+ * Build: gcc -O2 -ffp-contract=off -std=c11 -shared -fPIC (no fused
+ * multiply-add, so FP32 decisions round exactly as written).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_CAPACITY (-3)
+#define ORC_ERR_MEMBERSHIP (-6)
+
+#define ORC_MAX_COLOURS 256
+
+typedef struct {
+    double gravity[3];
+    double margin;       /* contact when gap <= margin */
+    double erp;          /* fraction of penetration / joint error removed per step */
+    double slop;         /* penetration allowed before push-out */
+    double warmstart;    /* factor on the previous step's impulses */
+    int lb_activate;     /* Alg 6 lines 4-15 enabled */
+    int lb_deact_every;  /* Alg 6 lines 16-24 on steps with index % k == 0; 0 = never */
+    double res_tol;      /* > 0: a worker stops sweeping once its RMS residual <= res_tol */
+    int res_check_every; /* sweeps between residual checks when res_tol > 0 */
+} orc_params;
+
+/* ------------------------------------------------------------------------ */
+/* small helpers                                                             */
+/* ------------------------------------------------------------------------ */
+
+static void *xcalloc(size_t n, size_t sz) {
+    void *p = calloc(n ? n : 1, sz ? sz : 1);
+    return p;
+}
+
+static int popc64(uint64_t x) {
+    int c = 0;
+    while (x) { x &= x - 1; ++c; }
+    return c;
+}
+
+static int lowest_bit(uint64_t x) {
+    for (int i = 0; i < 64; ++i) if (x >> i & 1u) return i;
+    return -1;
+}
+
+/* SplitMix64 output function (Steele, Lea & Flood 2014), used as the
+ * colouring priority. */
+uint64_t orc_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static void cross3(const double a[3], const double b[3], double out[3]) {
+    out[0] = a[1] * b[2] - a[2] * b[1];
+    out[1] = a[2] * b[0] - a[0] * b[2];
+    out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double a[3], const double b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/* rotation matrix of a unit quaternion q = (w, x, y, z) */
+static void quat_to_matrix(const double q[4], double R[9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+static void mat_vec(const double R[9], const double v[3], double out[3]) {
+    for (int i = 0; i < 3; ++i) out[i] = R[3 * i] * v[0] + R[3 * i + 1] * v[1] + R[3 * i + 2] * v[2];
+}
+
+/* Hamilton product a (x) b, quaternions as (w, x, y, z) */
+static void quat_mul(const double a[4], const double b[4], double out[4]) {
+    out[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    out[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    out[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    out[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+/* ------------------------------------------------------------------------ */
+/* c1: contacts                                                              */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int a, b;        /* a < b; b >= n_bodies is plane (b - n_bodies) */
+    double phi;      /* signed gap */
+    double n[3];     /* unit normal from a towards b */
+    double t1[3];    /* first tangent; t2 = n x t1 */
+} orc_contact;
+
+typedef struct { int64_t cx, cy, cz; int scene; int body; } cell_entry;
+
+static int cmp_cell(const void *pa, const void *pb) {
+    const cell_entry *a = pa, *b = pb;
+    if (a->scene != b->scene) return a->scene < b->scene ? -1 : 1;
+    if (a->cx != b->cx) return a->cx < b->cx ? -1 : 1;
+    if (a->cy != b->cy) return a->cy < b->cy ? -1 : 1;
+    if (a->cz != b->cz) return a->cz < b->cz ? -1 : 1;
+    return a->body < b->body ? -1 : (a->body > b->body);
+}
+
+static int cmp_contact_key(const void *pa, const void *pb) {
+    const orc_contact *a = pa, *b = pb;
+    if (a->a != b->a) return a->a < b->a ? -1 : 1;
+    return a->b < b->b ? -1 : (a->b > b->b);
+}
+
+/* FP32 contact decision for two spheres (integer outcome, evaluated in the
+ * kernel's precision): d = cb - ca, |d|^2 <= (ra + rb + margin)^2. */
+static int sphere_pair_touches_f32(const double *ca, const double *cb, double ra, double rb,
+                                   double margin) {
+    float ax = (float)ca[0], ay = (float)ca[1], az = (float)ca[2];
+    float bx = (float)cb[0], by = (float)cb[1], bz = (float)cb[2];
+    float dx = bx - ax, dy = by - ay, dz = bz - az;
+    float dxx = dx * dx, dyy = dy * dy, dzz = dz * dz;
+    float d2 = (dxx + dyy) + dzz;
+    float rs = ((float)ra + (float)rb) + (float)margin;
+    float rs2 = rs * rs;
+    return d2 <= rs2;
+}
+
+/* FP32 plane decision: ((nx*px + ny*py) + nz*pz) - d - r <= margin. */
+static int sphere_plane_touches_f32(const double *c, double r, const double *pl, double margin) {
+    float px = (float)c[0], py = (float)c[1], pz = (float)c[2];
+    float nx = (float)pl[0], ny = (float)pl[1], nz = (float)pl[2], d = (float)pl[3];
+    float s0 = nx * px, s1 = ny * py, s2 = nz * pz;
+    float dotp = (s0 + s1) + s2;
+    float phi = (dotp - d) - (float)r;
+    return phi <= (float)margin;
+}
+
+/* tangent axis: smallest |n_k| of the FP32 normal, ties to the lower index */
+static int tangent_axis_f32(float nx, float ny, float nz) {
+    float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
+    int k = 0;
+    float m = ax;
+    if (ay < m) { k = 1; m = ay; }
+    if (az < m) { k = 2; m = az; }
+    return k;
+}
+
+static void tangent_from_axis(const double n[3], int k, double t1[3]) {
+    double e[3] = {0, 0, 0};
+    e[k] = 1.0;
+    double ne = dot3(n, e);
+    double t[3] = {e[0] - ne * n[0], e[1] - ne * n[1], e[2] - ne * n[2]};
+    double L = sqrt(dot3(t, t));
+    t1[0] = t[0] / L; t1[1] = t[1] / L; t1[2] = t[2] / L;
+}
+
+static void fill_sphere_contact(orc_contact *c, int a, int b, const double *ca, const double *cb,
+                                double ra, double rb) {
+    c->a = a; c->b = b;
+    double d[3] = {cb[0] - ca[0], cb[1] - ca[1], cb[2] - ca[2]};
+    double L = sqrt(dot3(d, d));
+    c->phi = L - ra - rb;
+    /* FP32 normal for the axis decision, mirroring the contact test's rounding */
+    float fdx = (float)cb[0] - (float)ca[0];
+    float fdy = (float)cb[1] - (float)ca[1];
+    float fdz = (float)cb[2] - (float)ca[2];
+    float fxx = fdx * fdx, fyy = fdy * fdy, fzz = fdz * fdz;
+    float fL = sqrtf((fxx + fyy) + fzz);
+    int k;
+    if (L < 1e-12 || fL == 0.0f) {
+        c->n[0] = 0; c->n[1] = 0; c->n[2] = 1;
+        k = 0;
+    } else {
+        c->n[0] = d[0] / L; c->n[1] = d[1] / L; c->n[2] = d[2] / L;
+        k = tangent_axis_f32(fdx / fL, fdy / fL, fdz / fL);
+    }
+    tangent_from_axis(c->n, k, c->t1);
+}
+
+static void fill_plane_contact(orc_contact *c, int a, int b, const double *ca, double ra,
+                               const double *pl) {
+    c->a = a; c->b = b;
+    c->phi = dot3(pl, ca) - pl[3] - ra;
+    /* normal from the sphere (a) towards the plane (b): minus the plane normal */
+    c->n[0] = -pl[0]; c->n[1] = -pl[1]; c->n[2] = -pl[2];
+    int k = tangent_axis_f32(-(float)pl[0], -(float)pl[1], -(float)pl[2]);
+    tangent_from_axis(c->n, k, c->t1);
+}
+
+typedef struct {
+    int n;
+    const double *state;   /* n x 13 */
+    const double *radius;
+    const double *inv_mass;
+    int n_planes;
+    const double *planes;  /* np x 4 */
+    const int *plane_scene;
+    const int *scene_of_body;
+    const int *scene_flags;
+    double margin;
+} contact_input;
+
+/* All contacts of the current state in canonical order (ascending (a, b)).
+ * Sphere pairs are found through a uniform grid whose cells are at least as
+ * wide as the largest contact distance, so every touching pair lies in
+ * neighbouring cells; the grid only prunes, every candidate is tested.
+ * Pairs where both ends are static are skipped. Returns the count, or
+ * ORC_ERR_CAPACITY if more than cap contacts exist (out is then partial). */
+static int64_t contacts_impl(const contact_input *in, int use_grid, orc_contact **out_list) {
+    int n = in->n;
+    size_t cap = 1024, cnt = 0;
+    orc_contact *list = malloc(cap * sizeof(orc_contact));
+#define PUSH_CONTACT(expr)                                                         \
+    do {                                                                           \
+        if (cnt == cap) { cap *= 2; list = realloc(list, cap * sizeof(orc_contact)); } \
+        expr;                                                                      \
+        ++cnt;                                                                     \
+    } while (0)
+    double rmax = 0;
+    for (int i = 0; i < n; ++i) if (in->radius[i] > rmax) rmax = in->radius[i];
+    if (use_grid && n > 0) {
+        double cs = (2.0 * rmax + in->margin) * 1.01;
+        cell_entry *cells = malloc((size_t)n * sizeof(cell_entry));
+        for (int i = 0; i < n; ++i) {
+            const double *c = in->state + 13 * (size_t)i;
+            cells[i].cx = (int64_t)floor(c[0] / cs);
+            cells[i].cy = (int64_t)floor(c[1] / cs);
+            cells[i].cz = (int64_t)floor(c[2] / cs);
+            cells[i].scene = in->scene_of_body[i];
+            cells[i].body = i;
+        }
+        qsort(cells, n, sizeof(cell_entry), cmp_cell);
+        for (int i = 0; i < n; ++i) {
+            int a = i;
+            int s = in->scene_of_body[a];
+            if (!(in->scene_flags[s] & 1)) continue;
+            const double *ca = in->state + 13 * (size_t)a;
+            int64_t cx = (int64_t)floor(ca[0] / cs), cy = (int64_t)floor(ca[1] / cs),
+                    cz = (int64_t)floor(ca[2] / cs);
+            for (int dx = -1; dx <= 1; ++dx)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        cell_entry key = {cx + dx, cy + dy, cz + dz, s, -1};
+                        /* lower bound */
+                        int lo = 0, hi = n;
+                        while (lo < hi) {
+                            int mid = (lo + hi) / 2;
+                            if (cmp_cell(&cells[mid], &key) < 0) lo = mid + 1; else hi = mid;
+                        }
+                        for (int k = lo; k < n; ++k) {
+                            const cell_entry *e = &cells[k];
+                            if (e->scene != s || e->cx != key.cx || e->cy != key.cy || e->cz != key.cz) break;
+                            int b = e->body;
+                            if (b <= a) continue;
+                            if (in->inv_mass[a] == 0 && in->inv_mass[b] == 0) continue;
+                            const double *cb = in->state + 13 * (size_t)b;
+                            if (sphere_pair_touches_f32(ca, cb, in->radius[a], in->radius[b], in->margin))
+                                PUSH_CONTACT(fill_sphere_contact(&list[cnt], a, b, ca, cb, in->radius[a], in->radius[b]));
+                        }
+                    }
+        }
+        free(cells);
+    } else {
+        for (int a = 0; a < n; ++a) {
+            int s = in->scene_of_body[a];
+            if (!(in->scene_flags[s] & 1)) continue;
+            const double *ca = in->state + 13 * (size_t)a;
+            for (int b = a + 1; b < n; ++b) {
+                if (in->scene_of_body[b] != s) continue;
+                if (in->inv_mass[a] == 0 && in->inv_mass[b] == 0) continue;
+                const double *cb = in->state + 13 * (size_t)b;
+                if (sphere_pair_touches_f32(ca, cb, in->radius[a], in->radius[b], in->margin))
+                    PUSH_CONTACT(fill_sphere_contact(&list[cnt], a, b, ca, cb, in->radius[a], in->radius[b]));
+            }
+        }
+    }
+    for (int a = 0; a < n; ++a) {
+        if (in->inv_mass[a] == 0) continue;
+        const double *ca = in->state + 13 * (size_t)a;
+        for (int p = 0; p < in->n_planes; ++p) {
+            if (in->plane_scene[p] != in->scene_of_body[a]) continue;
+            const double *pl = in->planes + 4 * (size_t)p;
+            if (sphere_plane_touches_f32(ca, in->radius[a], pl, in->margin))
+                PUSH_CONTACT(fill_plane_contact(&list[cnt], a, n + p, ca, in->radius[a], pl));
+        }
+    }
+#undef PUSH_CONTACT
+    qsort(list, cnt, sizeof(orc_contact), cmp_contact_key);
+    *out_list = list;
+    return (int64_t)cnt;
+}
+
+/* Standalone entry point: contacts of a state; writes up to cap contacts.
+ * Returns the total number found (may exceed cap). */
+int64_t orc_contacts(int n, const double *state, const double *radius, const double *inv_mass,
+                     int n_planes, const double *planes, const int *plane_scene,
+                     const int *scene_of_body, const int *scene_flags, double margin, int use_grid,
+                     int64_t cap, int *out_ab, double *out_phi, double *out_n, double *out_t1) {
+    contact_input in = {n, state, radius, inv_mass, n_planes, planes, plane_scene, scene_of_body,
+                        scene_flags, margin};
+    orc_contact *list = NULL;
+    int64_t cnt = contacts_impl(&in, use_grid, &list);
+    for (int64_t i = 0; i < cnt && i < cap; ++i) {
+        out_ab[2 * i] = list[i].a; out_ab[2 * i + 1] = list[i].b;
+        out_phi[i] = list[i].phi;
+        for (int k = 0; k < 3; ++k) { out_n[3 * i + k] = list[i].n[k]; out_t1[3 * i + k] = list[i].t1[k]; }
+    }
+    free(list);
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* c2: constraint graph G^t (Section 5.1): vertices are bodies, an undirected  */
+/* edge joins two dynamic bodies linked by a contact or a joint; static       */
+/* bodies carry no edges; adjacency lists sorted ascending, duplicates merged. */
+/* ------------------------------------------------------------------------ */
+
+static int cmp_int(const void *a, const void *b) {
+    int x = *(const int *)a, y = *(const int *)b;
+    return x < y ? -1 : (x > y);
+}
+
+/* edges given as pairs (u[i], v[i]); entries with a negative end or a static
+ * end are ignored.  row_ptr has n+1 entries; returns the adjacency length. */
+static int64_t build_graph(int n, const double *inv_mass, int64_t ne, const int *eu, const int *ev,
+                           int **out_row_ptr, int **out_col) {
+    int *deg = xcalloc((size_t)n + 1, sizeof(int));
+    for (int64_t i = 0; i < ne; ++i) {
+        int u = eu[i], v = ev[i];
+        if (u < 0 || v < 0 || u >= n || v >= n || u == v) continue;
+        if (inv_mass[u] == 0 || inv_mass[v] == 0) continue;
+        deg[u]++; deg[v]++;
+    }
+    int *tmp_ptr = xcalloc((size_t)n + 1, sizeof(int));
+    for (int i = 0; i < n; ++i) tmp_ptr[i + 1] = tmp_ptr[i] + deg[i];
+    int *tmp = xcalloc((size_t)tmp_ptr[n] + 1, sizeof(int));
+    int *fill = xcalloc((size_t)n + 1, sizeof(int));
+    for (int64_t i = 0; i < ne; ++i) {
+        int u = eu[i], v = ev[i];
+        if (u < 0 || v < 0 || u >= n || v >= n || u == v) continue;
+        if (inv_mass[u] == 0 || inv_mass[v] == 0) continue;
+        tmp[tmp_ptr[u] + fill[u]++] = v;
+        tmp[tmp_ptr[v] + fill[v]++] = u;
+    }
+    int *row_ptr = xcalloc((size_t)n + 1, sizeof(int));
+    int *col = xcalloc((size_t)tmp_ptr[n] + 1, sizeof(int));
+    int64_t m = 0;
+    for (int i = 0; i < n; ++i) {
+        int *seg = tmp + tmp_ptr[i];
+        int len = tmp_ptr[i + 1] - tmp_ptr[i];
+        qsort(seg, len, sizeof(int), cmp_int);
+        row_ptr[i] = (int)m;
+        for (int k = 0; k < len; ++k)
+            if (k == 0 || seg[k] != seg[k - 1]) col[m++] = seg[k];
+    }
+    row_ptr[n] = (int)m;
+    free(deg); free(tmp_ptr); free(tmp); free(fill);
+    *out_row_ptr = row_ptr;
+    *out_col = col;
+    return m;
+}
+
+int64_t orc_graph(int n, const double *inv_mass, int64_t ne, const int *eu, const int *ev,
+                  int64_t cap, int *row_ptr_out, int *col_out) {
+    int *rp, *col;
+    int64_t m = build_graph(n, inv_mass, ne, eu, ev, &rp, &col);
+    memcpy(row_ptr_out, rp, ((size_t)n + 1) * sizeof(int));
+    for (int64_t i = 0; i < m && i < cap; ++i) col_out[i] = col[i];
+    free(rp); free(col);
+    return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* BFS helper: getBFSVertices(root, depth) = every vertex at graph distance   */
+/* 0..depth from root, root included (Alg 3 line 2, Alg 6 line 12).           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int n;
+    int *stamp;
+    int *dist;
+    int *queue;
+    int cur;
+} bfs_ws;
+
+static void bfs_ws_init(bfs_ws *w, int n) {
+    w->n = n;
+    w->stamp = xcalloc((size_t)n + 1, sizeof(int));
+    w->dist = xcalloc((size_t)n + 1, sizeof(int));
+    w->queue = xcalloc((size_t)n + 1, sizeof(int));
+    w->cur = 0;
+}
+
+static void bfs_ws_free(bfs_ws *w) { free(w->stamp); free(w->dist); free(w->queue); }
+
+/* fills w->queue[0..count) with the vertices in BFS order; returns count */
+static int bfs_vertices(bfs_ws *w, const int *row_ptr, const int *col, int root, int depth) {
+    w->cur++;
+    int head = 0, tail = 0;
+    w->queue[tail++] = root;
+    w->stamp[root] = w->cur;
+    w->dist[root] = 0;
+    while (head < tail) {
+        int u = w->queue[head++];
+        if (w->dist[u] >= depth) continue;
+        for (int k = row_ptr[u]; k < row_ptr[u + 1]; ++k) {
+            int v = col[k];
+            if (w->stamp[v] == w->cur) continue;
+            w->stamp[v] = w->cur;
+            w->dist[v] = w->dist[u] + 1;
+            w->queue[tail++] = v;
+        }
+    }
+    return tail;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Membership edits (Table 1: activate / deactivate), with live |P_w| counts  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t *mask;        /* per body, bit w = scene-local worker w */
+    const int *sob;        /* scene of body */
+    const int *part_base;  /* global index of worker 0 of each scene */
+    int64_t *count;        /* |P_w| per global worker */
+} membership;
+
+static void activate(membership *m, uint64_t W, int b) {
+    uint64_t add = W & ~m->mask[b];
+    int base = m->part_base[m->sob[b]];
+    for (int w = 0; w < 64; ++w) if (add >> w & 1u) m->count[base + w]++;
+    m->mask[b] |= add;
+}
+
+static void deactivate(membership *m, uint64_t W, int b) {
+    uint64_t rem = W & m->mask[b];
+    int base = m->part_base[m->sob[b]];
+    for (int w = 0; w < 64; ++w) if (rem >> w & 1u) m->count[base + w]--;
+    m->mask[b] &= ~rem;
+}
+
+/* <W_x>: total number of active bodies over the workers in W_x (Table 1) */
+static int64_t load_of(const membership *m, uint64_t W, int scene) {
+    int64_t s = 0;
+    int base = m->part_base[scene];
+    for (int w = 0; w < 64; ++w) if (W >> w & 1u) s += m->count[base + w];
+    return s;
+}
+
+/* Alg 7: b is a bridge body when the union of its neighbours' workers has
+ * more than one worker. */
+static int is_bridge(const membership *m, const int *row_ptr, const int *col, int b) {
+    uint64_t W = 0;
+    for (int k = row_ptr[b]; k < row_ptr[b + 1]; ++k) W |= m->mask[col[k]];
+    return popc64(W) > 1;
+}
+
+/* Alg 6 over the given contacts (pairs of dynamic bodies, canonical order). */
+static void load_balance_impl(membership *m, int n, const int *row_ptr, const int *col,
+                              int64_t nc, const int *ca, const int *cb, const int *scene_gamma,
+                              int do_activate, int do_deactivate) {
+    bfs_ws ws;
+    bfs_ws_init(&ws, n);
+    for (int64_t c = 0; c < nc; ++c) {
+        int A = ca[c], B = cb[c];
+        uint64_t WA = m->mask[A], WB = m->mask[B];          /* line 3 */
+        int scene = m->sob[A];
+        if ((WA & WB) == 0) {                                /* line 4 */
+            if (!do_activate) continue;
+            int root;
+            if (load_of(m, WA, scene) <= load_of(m, WB, scene)) {  /* line 5 */
+                activate(m, WA, B);                          /* line 6 */
+                root = B;
+            } else {
+                activate(m, WB, A);                          /* line 9 */
+                root = A;
+            }
+            int cnt = bfs_vertices(&ws, row_ptr, col, root, scene_gamma[scene]);  /* line 12 */
+            for (int k = 0; k < cnt; ++k) {                  /* lines 13-15 */
+                int v = ws.queue[k];
+                activate(m, (WA | WB) & ~m->mask[v], v);
+            }
+        } else if (!do_deactivate) {
+            continue;
+        } else if (popc64(WA) > 1 && popc64(WB) == 1 && !is_bridge(m, row_ptr, col, A)) {
+            deactivate(m, WA & ~WB, A);                      /* line 17 */
+        } else if (popc64(WB) > 1 && popc64(WA) == 1 && !is_bridge(m, row_ptr, col, B)) {
+            deactivate(m, WB & ~WA, B);                      /* line 19 */
+        } else if (WA == WB) {                               /* line 20 */
+            int base = m->part_base[scene];
+            int s = -1;
+            int64_t best = 0;
+            for (int w = 0; w < 64; ++w) {                   /* line 21, ties -> lowest */
+                if (!(WA >> w & 1u)) continue;
+                if (s < 0 || m->count[base + w] < best) { s = w; best = m->count[base + w]; }
+            }
+            uint64_t keep = (uint64_t)1 << s;
+            deactivate(m, WA & ~keep, A);                    /* line 22 */
+            deactivate(m, WB & ~keep, B);                    /* line 23 */
+        }
+    }
+    bfs_ws_free(&ws);
+}
+
+static int64_t *counts_from_masks(int n, const uint64_t *mask, const int *sob, const int *part_base,
+                                  int n_parts_total) {
+    int64_t *count = xcalloc((size_t)n_parts_total + 1, sizeof(int64_t));
+    for (int b = 0; b < n; ++b)
+        for (int w = 0; w < 64; ++w)
+            if (mask[b] >> w & 1u) count[part_base[sob[b]] + w]++;
+    return count;
+}
+
+/* Standalone Alg 6: masks updated in place. */
+void orc_load_balance(int n, uint64_t *mask, const int *scene_of_body, const int *part_base,
+                      int n_parts_total, const int *row_ptr, const int *col, int64_t nc,
+                      const int *ca, const int *cb, const int *scene_gamma, int do_activate,
+                      int do_deactivate) {
+    int64_t *count = counts_from_masks(n, mask, scene_of_body, part_base, n_parts_total);
+    membership m = {mask, scene_of_body, part_base, count};
+    load_balance_impl(&m, n, row_ptr, col, nc, ca, cb, scene_gamma, do_activate, do_deactivate);
+    free(count);
+}
+
+int orc_is_bridge(int n, const uint64_t *mask, const int *row_ptr, const int *col, int b) {
+    (void)n;
+    membership m = {(uint64_t *)mask, NULL, NULL, NULL};
+    return is_bridge(&m, row_ptr, col, b);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg 2 + Alg 3: overlap assignment for articulated bodies over joints.      */
+/* ------------------------------------------------------------------------ */
+
+static void grow_overlap(membership *m, bfs_ws *ws, const int *row_ptr, const int *col, int root,
+                         int gamma, uint64_t Wr) {
+    int cnt = bfs_vertices(ws, row_ptr, col, root, gamma);   /* Alg 3 line 2 */
+    for (int k = 0; k < cnt; ++k) {
+        int b = ws->queue[k];
+        if (popc64(m->mask[b]) >= 2) continue;                /* line 4: b in O */
+        activate(m, Wr & ~m->mask[b], b);                     /* line 5 */
+    }
+}
+
+/* masks updated in place; joints with a world end or a static end are skipped
+ * (they are not edges of G).  The BFS runs on the joint graph. */
+void orc_assign_overlap(int n, uint64_t *mask, const int *scene_of_body, const int *part_base,
+                        int n_parts_total, const double *inv_mass, int nj, const int *joint_ab,
+                        const int *scene_gamma) {
+    int *eu = xcalloc((size_t)nj + 1, sizeof(int)), *ev = xcalloc((size_t)nj + 1, sizeof(int));
+    for (int j = 0; j < nj; ++j) { eu[j] = joint_ab[2 * j]; ev[j] = joint_ab[2 * j + 1]; }
+    int *row_ptr, *col;
+    build_graph(n, inv_mass, nj, eu, ev, &row_ptr, &col);
+    int64_t *count = counts_from_masks(n, mask, scene_of_body, part_base, n_parts_total);
+    membership m = {mask, scene_of_body, part_base, count};
+    bfs_ws ws;
+    bfs_ws_init(&ws, n);
+    for (int j = 0; j < nj; ++j) {                              /* Alg 2 line 2 */
+        int A = eu[j], B = ev[j];
+        if (A < 0 || B < 0 || inv_mass[A] == 0 || inv_mass[B] == 0 || A == B) continue;
+        uint64_t WA = mask[A], WB = mask[B];
+        if (popc64(WA) == 1 && popc64(WB) == 1 && WA != WB) {   /* line 4 */
+            int gamma = scene_gamma[scene_of_body[A]];
+            activate(&m, mask[B], A);                           /* line 5 */
+            grow_overlap(&m, &ws, row_ptr, col, A, gamma, mask[A] | mask[B]);   /* line 6 */
+            activate(&m, mask[A], B);                           /* line 7 */
+            grow_overlap(&m, &ws, row_ptr, col, B, gamma, mask[A] | mask[B]);   /* line 8 */
+        }
+    }
+    bfs_ws_free(&ws);
+    free(count); free(row_ptr); free(col); free(eu); free(ev);
+}
+
+/* ------------------------------------------------------------------------ */
+/* c7: D(o,i) (Eq 16), searched breadth-first up to beta as in Alg 5.         */
+/* Entries are ordered by body, then worker; D has one byte per entry, 255   */
+/* where the worker is not met within beta (and for bodies outside O).        */
+/* ------------------------------------------------------------------------ */
+
+static void geodesics_impl(int n, const uint64_t *mask, const int *sob, const int *scene_beta,
+                           const int *row_ptr, const int *col, const int64_t *entry_ptr,
+                           uint8_t *D) {
+    bfs_ws ws;
+    bfs_ws_init(&ws, n);
+    for (int o = 0; o < n; ++o) {
+        uint64_t Wo = mask[o];
+        for (int64_t e = entry_ptr[o]; e < entry_ptr[o + 1]; ++e) D[e] = 255;
+        if (popc64(Wo) < 2) continue;
+        int beta = scene_beta[sob[o]];
+        /* breadth-first from o, depth 1..beta (Alg 5 lines 4-5); the first
+         * body met that is active only in worker i, with i in W_o (line 7),
+         * gives the minimum of Eq 16 for i */
+        ws.cur++;
+        int head = 0, tail = 0;
+        ws.queue[tail++] = o;
+        ws.stamp[o] = ws.cur;
+        ws.dist[o] = 0;
+        uint64_t found = 0;
+        while (head < tail && found != Wo) {
+            int u = ws.queue[head++];
+            if (ws.dist[u] >= beta) continue;
+            for (int k = row_ptr[u]; k < row_ptr[u + 1]; ++k) {
+                int v = col[k];
+                if (ws.stamp[v] == ws.cur) continue;
+                ws.stamp[v] = ws.cur;
+                ws.dist[v] = ws.dist[u] + 1;
+                ws.queue[tail++] = v;
+                uint64_t Wv = mask[v];
+                if (popc64(Wv) == 1 && (Wv & Wo) == Wv && !(found & Wv)) {
+                    found |= Wv;
+                    int w = lowest_bit(Wv);
+                    int rank = popc64(Wo & (((uint64_t)1 << w) - 1));
+                    D[entry_ptr[o] + rank] = (uint8_t)ws.dist[v];
+                }
+            }
+        }
+        /* stopping once every worker is met (Alg 5 line 12) changes nothing:
+         * later hits are at the same or a larger depth and are not recorded */
+    }
+    bfs_ws_free(&ws);
+}
+
+void orc_geodesics(int n, const uint64_t *mask, const int *scene_of_body, const int *scene_beta,
+                   const int *row_ptr, const int *col, uint8_t *D_out) {
+    int64_t *entry_ptr = xcalloc((size_t)n + 1, sizeof(int64_t));
+    for (int b = 0; b < n; ++b) entry_ptr[b + 1] = entry_ptr[b] + popc64(mask[b]);
+    geodesics_impl(n, mask, scene_of_body, scene_beta, row_ptr, col, entry_ptr, D_out);
+    free(entry_ptr);
+}
+
+/* c8: convex weights of Eq 15 from inverse distances; unmet workers weigh 0
+ * and a body that met none gets uniform weights. */
+void orc_weights(int k, const uint8_t *D, double *w) {
+    double s = 0;
+    for (int i = 0; i < k; ++i) {
+        w[i] = (D[i] != 255) ? 1.0 / (double)D[i] : 0.0;
+        s += w[i];
+    }
+    for (int i = 0; i < k; ++i) w[i] = (s > 0) ? w[i] / s : 1.0 / (double)k;
+}
+
+/* c9: Alg 4 over k copies (13 values each, workers in ascending order). */
+void orc_blend(int k, const double *copies, const double *w, double *out) {
+    double x[3] = {0, 0, 0}, v[3] = {0, 0, 0}, om[3] = {0, 0, 0}, q[4] = {0, 0, 0, 0};
+    const double *q0 = copies + 3;
+    for (int i = 0; i < k; ++i) {
+        const double *s = copies + 13 * (size_t)i;
+        for (int a = 0; a < 3; ++a) {
+            x[a] += w[i] * s[a];          /* Eq 11 */
+            v[a] += w[i] * s[7 + a];      /* Eq 12 */
+            om[a] += w[i] * s[10 + a];    /* Eq 13 */
+        }
+        double qi[4] = {s[3], s[4], s[5], s[6]};
+        double dq = qi[0] * q0[0] + qi[1] * q0[1] + qi[2] * q0[2] + qi[3] * q0[3];
+        if (i > 0 && dq < 0) for (int a = 0; a < 4; ++a) qi[a] = -qi[a];   /* lines 7-9 */
+        for (int a = 0; a < 4; ++a) q[a] += w[i] * qi[a];                  /* Eq 14 */
+    }
+    double L = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);  /* line 12 */
+    for (int a = 0; a < 3; ++a) { out[a] = x[a]; out[7 + a] = v[a]; out[10 + a] = om[a]; }
+    for (int a = 0; a < 4; ++a) out[3 + a] = q[a] / L;
+}
+
+/* ------------------------------------------------------------------------ */
+/* c5: greedy first-fit colouring in descending priority.                    */
+/* nodes: for each node its two dynamic body ids (-1 = none) and priority.   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { uint64_t prio; int idx; } prio_item;
+
+static int cmp_prio_desc(const void *pa, const void *pb) {
+    const prio_item *a = pa, *b = pb;
+    if (a->prio != b->prio) return a->prio > b->prio ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx);
+}
+
+/* body_slots: 2 per node, local body indices in [0, n_local) or -1.
+ * colour_out: one per node.  Returns the number of colours, or
+ * ORC_ERR_CAPACITY beyond ORC_MAX_COLOURS. */
+static int colour_nodes(int n_nodes, const int *body_slots, const uint64_t *prio, int n_local,
+                        int *colour_out) {
+    const int W = ORC_MAX_COLOURS / 64;
+    uint64_t *used = xcalloc((size_t)n_local * W + 1, sizeof(uint64_t));
+    prio_item *order = xcalloc((size_t)n_nodes + 1, sizeof(prio_item));
+    for (int i = 0; i < n_nodes; ++i) { order[i].prio = prio[i]; order[i].idx = i; }
+    qsort(order, n_nodes, sizeof(prio_item), cmp_prio_desc);
+    int ncol = 0, err = 0;
+    for (int r = 0; r < n_nodes; ++r) {
+        int u = order[r].idx;
+        int sa = body_slots[2 * u], sb = body_slots[2 * u + 1];
+        int c = -1;
+        for (int cc = 0; cc < ORC_MAX_COLOURS; ++cc) {
+            int wd = cc / 64, bit = cc % 64;
+            int taken = 0;
+            if (sa >= 0 && (used[(size_t)sa * W + wd] >> bit & 1u)) taken = 1;
+            if (sb >= 0 && (used[(size_t)sb * W + wd] >> bit & 1u)) taken = 1;
+            if (!taken) { c = cc; break; }
+        }
+        if (c < 0) { err = 1; c = 0; }
+        colour_out[u] = c;
+        if (sa >= 0) used[(size_t)sa * W + c / 64] |= (uint64_t)1 << (c % 64);
+        if (sb >= 0) used[(size_t)sb * W + c / 64] |= (uint64_t)1 << (c % 64);
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(used); free(order);
+    return err ? ORC_ERR_CAPACITY : ncol;
+}
+
+int orc_colour(int n_nodes, const int *body_slots, const uint64_t *prio, int n_local,
+               int *colour_out) {
+    return colour_nodes(n_nodes, body_slots, prio, n_local, colour_out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The simulation: state, membership, warm-start cache, last-step records.   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int part;           /* global worker */
+    uint64_t key;       /* kind<<62 | key */
+    double lam[3];
+} ws_item;
+
+static int cmp_ws(const void *pa, const void *pb) {
+    const ws_item *a = pa, *b = pb;
+    if (a->part != b->part) return a->part < b->part ? -1 : 1;
+    return a->key < b->key ? -1 : (a->key > b->key);
+}
+
+typedef struct {
+    orc_params P;
+    int n, np, nj, ns;
+    double *st;          /* n x 13 blended state */
+    double *rad, *im, *iI;
+    double *planes; int *plane_scene;
+    int *jab; double *janc;
+    int *sob; double *mu, *dt; int *sflags, *sgamma, *sbeta, *nsets, *part_base;
+    int n_parts;
+    uint64_t *mask;
+    ws_item *ws; int64_t ws_n;
+    int64_t step_index;
+    /* last step */
+    orc_contact *con; int64_t nc;
+    int *row_ptr, *col; int64_t nadj;
+    int64_t *entry_ptr; int64_t ne;
+    int *entry_part;
+    uint8_t *D;
+    double *weight;
+    double *copies;     /* ne x 13 */
+    /* pairs: (worker, constraint) in worker order, canonical inside */
+    int64_t npairs;
+    int *pair_part; int *pair_kind; int64_t *pair_cidx; uint64_t *pair_key; int *pair_colour;
+    double *pair_lam;   /* npairs x 3 */
+    int *part_iters; double *part_res_sq; int64_t *part_rows; int *part_colours;
+    double res_sq_total; double res_max; int64_t res_rows;
+    double joint_violation_max;
+} orc_sim;
+
+orc_sim *orc_create(const orc_params *P, int n, const double *state13, const double *radius,
+                    const double *inv_mass, int n_planes, const double *planes,
+                    const int *plane_scene, int n_joints, const int *joint_ab,
+                    const double *joint_anchors, int n_scenes, const int *scene_of_body,
+                    const double *scene_mu, const double *scene_dt, const int *scene_flags,
+                    const int *scene_gamma, const int *scene_beta, const int *n_sets) {
+    orc_sim *s = xcalloc(1, sizeof(orc_sim));
+    s->P = *P;
+    s->n = n; s->np = n_planes; s->nj = n_joints; s->ns = n_scenes;
+    s->st = xcalloc((size_t)n * 13 + 1, sizeof(double));
+    memcpy(s->st, state13, (size_t)n * 13 * sizeof(double));
+    s->rad = xcalloc((size_t)n + 1, sizeof(double));
+    s->im = xcalloc((size_t)n + 1, sizeof(double));
+    s->iI = xcalloc((size_t)n + 1, sizeof(double));
+    for (int i = 0; i < n; ++i) {
+        s->rad[i] = radius[i];
+        s->im[i] = inv_mass[i];
+        /* solid sphere: I = (2/5) m r^2, isotropic */
+        s->iI[i] = inv_mass[i] > 0 ? inv_mass[i] / (0.4 * radius[i] * radius[i]) : 0.0;
+    }
+    s->planes = xcalloc((size_t)n_planes * 4 + 1, sizeof(double));
+    memcpy(s->planes, planes, (size_t)n_planes * 4 * sizeof(double));
+    s->plane_scene = xcalloc((size_t)n_planes + 1, sizeof(int));
+    memcpy(s->plane_scene, plane_scene, (size_t)n_planes * sizeof(int));
+    s->jab = xcalloc((size_t)n_joints * 2 + 1, sizeof(int));
+    memcpy(s->jab, joint_ab, (size_t)n_joints * 2 * sizeof(int));
+    s->janc = xcalloc((size_t)n_joints * 6 + 1, sizeof(double));
+    memcpy(s->janc, joint_anchors, (size_t)n_joints * 6 * sizeof(double));
+    s->sob = xcalloc((size_t)n + 1, sizeof(int));
+    memcpy(s->sob, scene_of_body, (size_t)n * sizeof(int));
+    s->mu = xcalloc((size_t)n_scenes, sizeof(double));
+    s->dt = xcalloc((size_t)n_scenes, sizeof(double));
+    s->sflags = xcalloc((size_t)n_scenes, sizeof(int));
+    s->sgamma = xcalloc((size_t)n_scenes, sizeof(int));
+    s->sbeta = xcalloc((size_t)n_scenes, sizeof(int));
+    s->nsets = xcalloc((size_t)n_scenes, sizeof(int));
+    s->part_base = xcalloc((size_t)n_scenes + 1, sizeof(int));
+    for (int i = 0; i < n_scenes; ++i) {
+        s->mu[i] = scene_mu[i]; s->dt[i] = scene_dt[i]; s->sflags[i] = scene_flags[i];
+        s->sgamma[i] = scene_gamma[i]; s->sbeta[i] = scene_beta[i]; s->nsets[i] = n_sets[i];
+        s->part_base[i + 1] = s->part_base[i] + n_sets[i];
+    }
+    s->n_parts = s->part_base[n_scenes];
+    s->mask = xcalloc((size_t)n + 1, sizeof(uint64_t));
+    return s;
+}
+
+static void free_step_records(orc_sim *s) {
+    free(s->con); s->con = NULL;
+    free(s->row_ptr); free(s->col); s->row_ptr = s->col = NULL;
+    free(s->entry_ptr); free(s->entry_part); s->entry_ptr = NULL; s->entry_part = NULL;
+    free(s->D); free(s->weight); free(s->copies); s->D = NULL; s->weight = NULL; s->copies = NULL;
+    free(s->pair_part); free(s->pair_kind); free(s->pair_cidx); free(s->pair_key);
+    free(s->pair_colour); free(s->pair_lam);
+    s->pair_part = s->pair_kind = s->pair_colour = NULL; s->pair_cidx = NULL; s->pair_key = NULL;
+    s->pair_lam = NULL;
+    free(s->part_iters); free(s->part_res_sq); free(s->part_rows); free(s->part_colours);
+    s->part_iters = NULL; s->part_res_sq = NULL; s->part_rows = NULL; s->part_colours = NULL;
+}
+
+void orc_destroy(orc_sim *s) {
+    if (!s) return;
+    free_step_records(s);
+    free(s->st); free(s->rad); free(s->im); free(s->iI); free(s->planes); free(s->plane_scene);
+    free(s->jab); free(s->janc); free(s->sob); free(s->mu); free(s->dt); free(s->sflags);
+    free(s->sgamma); free(s->sbeta); free(s->nsets); free(s->part_base); free(s->mask); free(s->ws);
+    free(s);
+}
+
+/* initial partition: each body's single worker (scene-local index) */
+int orc_set_partition(orc_sim *s, const int *set_of_body) {
+    for (int b = 0; b < s->n; ++b) {
+        if (s->im[b] == 0) { s->mask[b] = 0; continue; }
+        int w = set_of_body[b];
+        if (w < 0 || w >= s->nsets[s->sob[b]] || w >= 64) return ORC_ERR_MEMBERSHIP;
+        s->mask[b] = (uint64_t)1 << w;
+    }
+    return ORC_OK;
+}
+
+int orc_set_masks(orc_sim *s, const uint64_t *mask) {
+    for (int b = 0; b < s->n; ++b) {
+        if (s->im[b] == 0) { s->mask[b] = 0; continue; }
+        int ns = s->nsets[s->sob[b]];
+        uint64_t allowed = ns >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << ns) - 1);
+        if (mask[b] == 0 || (mask[b] & ~allowed)) return ORC_ERR_MEMBERSHIP;
+        s->mask[b] = mask[b];
+    }
+    return ORC_OK;
+}
+
+void orc_get_masks(const orc_sim *s, uint64_t *out) { memcpy(out, s->mask, (size_t)s->n * sizeof(uint64_t)); }
+void orc_set_state(orc_sim *s, const double *st) { memcpy(s->st, st, (size_t)s->n * 13 * sizeof(double)); }
+void orc_get_state(const orc_sim *s, double *st) { memcpy(st, s->st, (size_t)s->n * 13 * sizeof(double)); }
+void orc_set_step_index(orc_sim *s, int64_t k) { s->step_index = k; }
+int64_t orc_get_step_index(const orc_sim *s) { return s->step_index; }
+
+int orc_assign(orc_sim *s) {
+    orc_assign_overlap(s->n, s->mask, s->sob, s->part_base, s->n_parts, s->im, s->nj, s->jab,
+                       s->sgamma);
+    return ORC_OK;
+}
+
+/* warm-start cache: n items (global worker, kind<<62|key, lambda[3]) */
+void orc_set_warmstart(orc_sim *s, int64_t n, const int *part, const uint64_t *key,
+                       const double *lam) {
+    free(s->ws);
+    s->ws = xcalloc((size_t)n + 1, sizeof(ws_item));
+    for (int64_t i = 0; i < n; ++i) {
+        s->ws[i].part = part[i]; s->ws[i].key = key[i];
+        for (int k = 0; k < 3; ++k) s->ws[i].lam[k] = lam[3 * i + k];
+    }
+    qsort(s->ws, n, sizeof(ws_item), cmp_ws);
+    s->ws_n = n;
+}
+
+int64_t orc_warmstart_size(const orc_sim *s) { return s->ws_n; }
+
+void orc_get_warmstart(const orc_sim *s, int *part, uint64_t *key, double *lam) {
+    for (int64_t i = 0; i < s->ws_n; ++i) {
+        part[i] = s->ws[i].part; key[i] = s->ws[i].key;
+        for (int k = 0; k < 3; ++k) lam[3 * i + k] = s->ws[i].lam[k];
+    }
+}
+
+static const double *ws_lookup(const orc_sim *s, int part, uint64_t key) {
+    ws_item probe;
+    probe.part = part; probe.key = key;
+    const ws_item *hit = bsearch(&probe, s->ws, s->ws_n, sizeof(ws_item), cmp_ws);
+    return hit ? hit->lam : NULL;
+}
+
+/* ------------------------------------------------------------------------ */
+/* c6: one worker's timestep -- PGS on the MLCP of Eq 1-7 over its active     */
+/* bodies and constraints, then integration (Section 3: velocities first,     */
+/* then positions with the new velocities).                                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int la, lb;          /* local body indices, -1 = static end */
+    double JA[6], JB[6]; /* (linear, angular) Jacobian blocks */
+    double k;            /* 1 / (J M^-1 J^T) */
+    double target;
+    int friction_of;     /* row index of the normal row for friction rows, else -1 */
+    double mu;
+    int bilateral;       /* joint rows: bounds +-inf */
+} pgs_row;
+
+static void row_bounds(const pgs_row *r, const double *lam, double *lo, double *hi) {
+    if (r->friction_of >= 0) {
+        double ln = lam[r->friction_of];
+        *lo = -r->mu * ln; *hi = r->mu * ln;
+    } else if (r->bilateral) {
+        *lo = -INFINITY; *hi = INFINITY;
+    } else {
+        *lo = 0.0; *hi = INFINITY;
+    }
+}
+
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+static double row_velocity(const pgs_row *r, const double *vel) {
+    double w = 0;
+    if (r->la >= 0) for (int a = 0; a < 6; ++a) w += r->JA[a] * vel[6 * r->la + a];
+    if (r->lb >= 0) for (int a = 0; a < 6; ++a) w += r->JB[a] * vel[6 * r->lb + a];
+    return w;
+}
+
+static void apply_impulse(const pgs_row *r, double *vel, const double *minv, double dl) {
+    if (r->la >= 0) for (int a = 0; a < 6; ++a) vel[6 * r->la + a] += minv[6 * r->la + a] * r->JA[a] * dl;
+    if (r->lb >= 0) for (int a = 0; a < 6; ++a) vel[6 * r->lb + a] += minv[6 * r->lb + a] * r->JB[a] * dl;
+}
+
+static double row_residual(const pgs_row *r, const double *vel, const double *lam, int i) {
+    double lo, hi;
+    row_bounds(r, lam, &lo, &hi);
+    double w = row_velocity(r, vel);
+    double proj = clampd(lam[i] + r->k * (r->target - w), lo, hi);
+    return (lam[i] - proj) / r->k;
+}
+
+/* one row of a rigid constraint along direction d between lever arms rA, rB
+ * (vectors from each body's centre to the constraint point) */
+static void make_row(pgs_row *row, int la, int lb, const double d[3], const double rA[3],
+                     const double rB[3], const double *minv) {
+    double ca[3], cb[3];
+    cross3(rA, d, ca);
+    cross3(rB, d, cb);
+    row->la = la; row->lb = lb;
+    for (int a = 0; a < 3; ++a) {
+        row->JA[a] = -d[a]; row->JA[3 + a] = -ca[a];
+        row->JB[a] = d[a];  row->JB[3 + a] = cb[a];
+    }
+    double s = 0;
+    if (la >= 0) for (int a = 0; a < 6; ++a) s += row->JA[a] * minv[6 * la + a] * row->JA[a];
+    if (lb >= 0) for (int a = 0; a < 6; ++a) s += row->JB[a] * minv[6 * lb + a] * row->JB[a];
+    row->k = 1.0 / s;
+    row->friction_of = -1; row->bilateral = 0; row->mu = 0; row->target = 0;
+}
+
+typedef struct {
+    int part;
+    int64_t first_pair, n_pairs;
+} worker_view;
+
+static int local_index(const int *bodies, int nb, int b) {
+    int lo = 0, hi = nb;
+    while (lo < hi) { int mid = (lo + hi) / 2; if (bodies[mid] < b) lo = mid + 1; else hi = mid; }
+    return (lo < nb && bodies[lo] == b) ? lo : -1;
+}
+
+static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int nb,
+                         const int64_t *body_entry, int64_t p0, int64_t p1, double h_override,
+                         int iters) {
+    const orc_params *P = &s->P;
+    double h = h_override > 0 ? h_override : s->dt[scene];
+    double mu = s->mu[scene];
+    double *vel = xcalloc((size_t)nb * 6 + 1, sizeof(double));
+    double *minv = xcalloc((size_t)nb * 6 + 1, sizeof(double));
+    for (int i = 0; i < nb; ++i) {
+        int b = bodies[i];
+        const double *x = s->st + 13 * (size_t)b;
+        for (int a = 0; a < 3; ++a) {
+            vel[6 * i + a] = x[7 + a] + h * P->gravity[a];   /* external force h*f */
+            vel[6 * i + 3 + a] = x[10 + a];
+            minv[6 * i + a] = s->im[b];
+            minv[6 * i + 3 + a] = s->iI[b];
+        }
+    }
+    int64_t np_ = p1 - p0;
+    pgs_row *rows = xcalloc((size_t)np_ * 3 + 1, sizeof(pgs_row));
+    double *lam = xcalloc((size_t)np_ * 3 + 1, sizeof(double));
+    int *slots = xcalloc((size_t)np_ * 2 + 1, sizeof(int));
+    uint64_t *prio = xcalloc((size_t)np_ + 1, sizeof(uint64_t));
+    /* rows, fixed for the step from the blended state (Alg 1 lines 7-9) */
+    for (int64_t q = 0; q < np_; ++q) {
+        int64_t pi = p0 + q;
+        pgs_row *r3 = rows + 3 * q;
+        if (s->pair_kind[pi] == 0) {
+            const orc_contact *c = &s->con[s->pair_cidx[pi]];
+            int a = c->a, b = c->b;
+            int la = (s->im[a] > 0) ? local_index(bodies, nb, a) : -1;
+            int lb = (b < s->n && s->im[b] > 0) ? local_index(bodies, nb, b) : -1;
+            double ra = s->rad[a];
+            double rA[3] = {ra * c->n[0], ra * c->n[1], ra * c->n[2]};
+            double rB[3] = {0, 0, 0};
+            if (b < s->n) { double rb = s->rad[b]; for (int k = 0; k < 3; ++k) rB[k] = -rb * c->n[k]; }
+            double t2[3];
+            cross3(c->n, c->t1, t2);
+            make_row(&r3[0], la, lb, c->n, rA, rB, minv);
+            make_row(&r3[1], la, lb, c->t1, rA, rB, minv);
+            make_row(&r3[2], la, lb, t2, rA, rB, minv);
+            r3[0].target = c->phi > 0 ? -c->phi / h : P->erp * fmax(-c->phi - P->slop, 0.0) / h;
+            r3[1].friction_of = (int)(3 * q); r3[1].mu = mu;
+            r3[2].friction_of = (int)(3 * q); r3[2].mu = mu;
+            slots[2 * q] = la; slots[2 * q + 1] = lb;
+        } else {
+            int j = (int)s->pair_cidx[pi];
+            int a = s->jab[2 * j], b = s->jab[2 * j + 1];
+            const double *anc = s->janc + 6 * (size_t)j;
+            double pA[3], pB[3], rA[3] = {0, 0, 0}, rB[3] = {0, 0, 0};
+            int la = -1, lb = -1;
+            if (a >= 0) {
+                const double *x = s->st + 13 * (size_t)a;
+                double R[9];
+                quat_to_matrix(x + 3, R);
+                mat_vec(R, anc, rA);
+                for (int k = 0; k < 3; ++k) pA[k] = x[k] + rA[k];
+                if (s->im[a] > 0) la = local_index(bodies, nb, a);
+            } else {
+                for (int k = 0; k < 3; ++k) pA[k] = anc[k];
+            }
+            if (b >= 0) {
+                const double *x = s->st + 13 * (size_t)b;
+                double R[9];
+                quat_to_matrix(x + 3, R);
+                mat_vec(R, anc + 3, rB);
+                for (int k = 0; k < 3; ++k) pB[k] = x[k] + rB[k];
+                if (s->im[b] > 0) lb = local_index(bodies, nb, b);
+            } else {
+                for (int k = 0; k < 3; ++k) pB[k] = anc[3 + k];
+            }
+            for (int ax = 0; ax < 3; ++ax) {
+                double e[3] = {0, 0, 0};
+                e[ax] = 1.0;
+                make_row(&r3[ax], la, lb, e, rA, rB, minv);
+                r3[ax].bilateral = 1;
+                r3[ax].target = -P->erp * (pB[ax] - pA[ax]) / h;
+            }
+            slots[2 * q] = la; slots[2 * q + 1] = lb;
+        }
+        /* priority mix64(kind<<62 ^ key); pair_key already holds kind<<62 ^ key */
+        prio[q] = orc_mix64(s->pair_key[pi]);
+    }
+    /* c5: greedy colouring in priority order */
+    int *colour = xcalloc((size_t)np_ + 1, sizeof(int));
+    int ncol = np_ > 0 ? colour_nodes((int)np_, slots, prio, nb, colour) : 0;
+    if (ncol < 0) ncol = ORC_MAX_COLOURS;
+    for (int64_t q = 0; q < np_; ++q) s->pair_colour[p0 + q] = colour[q];
+    s->part_colours[part] = ncol;
+    /* warm start: previous impulses of the same (worker, constraint) */
+    for (int64_t q = 0; q < np_; ++q) {
+        const double *prev = ws_lookup(s, part, s->pair_key[p0 + q]);
+        for (int k = 0; k < 3; ++k) {
+            double l0 = prev ? prev[k] * P->warmstart : 0.0;
+            lam[3 * q + k] = l0;
+            if (l0 != 0.0) apply_impulse(&rows[3 * q + k], vel, minv, l0);
+        }
+    }
+    /* constraints grouped by colour, canonical order inside a colour */
+    int64_t *by_colour = xcalloc((size_t)np_ + 1, sizeof(int64_t));
+    int64_t *col_start = xcalloc((size_t)ncol + 2, sizeof(int64_t));
+    for (int64_t q = 0; q < np_; ++q) col_start[colour[q] + 1]++;
+    for (int c = 0; c < ncol; ++c) col_start[c + 1] += col_start[c];
+    {
+        int64_t *fill = xcalloc((size_t)ncol + 1, sizeof(int64_t));
+        for (int64_t q = 0; q < np_; ++q) by_colour[col_start[colour[q]] + fill[colour[q]]++] = q;
+        free(fill);
+    }
+    /* sweeps: Gauss-Seidel with projection onto [lo, hi] (Eq 5-7) */
+    int it_done = 0;
+    for (int it = 0; it < iters; ++it) {
+        for (int c = 0; c < ncol; ++c) {
+            for (int64_t t = col_start[c]; t < col_start[c + 1]; ++t) {
+                int64_t q = by_colour[t];
+                for (int k = 0; k < 3; ++k) {
+                    int i = (int)(3 * q + k);
+                    const pgs_row *r = &rows[i];
+                    double lo, hi;
+                    row_bounds(r, lam, &lo, &hi);
+                    double w = row_velocity(r, vel);
+                    double lnew = clampd(lam[i] + r->k * (r->target - w), lo, hi);
+                    double dl = lnew - lam[i];
+                    lam[i] = lnew;
+                    apply_impulse(r, vel, minv, dl);
+                }
+            }
+        }
+        it_done = it + 1;
+        if (P->res_tol > 0 && P->res_check_every > 0 && it_done % P->res_check_every == 0 &&
+            np_ > 0) {
+            double sq = 0;
+            for (int64_t i = 0; i < 3 * np_; ++i) { double rr = row_residual(&rows[i], vel, lam, (int)i); sq += rr * rr; }
+            if (sqrt(sq / (double)(3 * np_)) <= P->res_tol) break;
+        }
+    }
+    /* c10: residual at the final iterate */
+    double sq = 0;
+    for (int64_t i = 0; i < 3 * np_; ++i) {
+        double rr = row_residual(&rows[i], vel, lam, (int)i);
+        sq += rr * rr;
+        if (fabs(rr) > s->res_max) s->res_max = fabs(rr);
+    }
+    s->part_res_sq[part] = sq;
+    s->part_rows[part] = 3 * np_;
+    s->part_iters[part] = it_done;
+    s->res_sq_total += sq;
+    s->res_rows += 3 * np_;
+    for (int64_t q = 0; q < np_; ++q)
+        for (int k = 0; k < 3; ++k) s->pair_lam[3 * (p0 + q) + k] = lam[3 * q + k];
+    /* integrate: x += h v, q <- normalise(q + h/2 (0, w) (x) q); write this
+     * worker's copy of every active body */
+    for (int i = 0; i < nb; ++i) {
+        int b = bodies[i];
+        const double *x = s->st + 13 * (size_t)b;
+        double *out = s->copies + 13 * (size_t)body_entry[i];
+        double om[4] = {0, vel[6 * i + 3], vel[6 * i + 4], vel[6 * i + 5]};
+        double dq[4];
+        quat_mul(om, x + 3, dq);
+        double qn[4];
+        for (int a = 0; a < 4; ++a) qn[a] = x[3 + a] + 0.5 * h * dq[a];
+        double L = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+        for (int a = 0; a < 3; ++a) out[a] = x[a] + h * vel[6 * i + a];
+        for (int a = 0; a < 4; ++a) out[3 + a] = qn[a] / L;
+        for (int a = 0; a < 3; ++a) { out[7 + a] = vel[6 * i + a]; out[10 + a] = vel[6 * i + 3 + a]; }
+    }
+    free(vel); free(minv); free(rows); free(lam); free(slots); free(prio); free(colour);
+    free(by_colour); free(col_start);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One timestep: Alg 1 lines 7-20.                                           */
+/* dt > 0 overrides every scene's dt.                                        */
+/* ------------------------------------------------------------------------ */
+
+int orc_step(orc_sim *s, double dt, int iters) {
+    free_step_records(s);
+    const int n = s->n;
+    s->res_sq_total = 0; s->res_max = 0; s->res_rows = 0;
+    /* line 10: contacts */
+    contact_input in = {n, s->st, s->rad, s->im, s->np, s->planes, s->plane_scene, s->sob,
+                        s->sflags, s->P.margin};
+    s->nc = contacts_impl(&in, 1, &s->con);
+    /* line 11: constraint graph G^t from contacts and joints */
+    int64_t nedge = s->nc + s->nj;
+    int *eu = xcalloc((size_t)nedge + 1, sizeof(int)), *ev = xcalloc((size_t)nedge + 1, sizeof(int));
+    for (int64_t i = 0; i < s->nc; ++i) { eu[i] = s->con[i].a; ev[i] = s->con[i].b < n ? s->con[i].b : -1; }
+    for (int j = 0; j < s->nj; ++j) { eu[s->nc + j] = s->jab[2 * j]; ev[s->nc + j] = s->jab[2 * j + 1]; }
+    s->nadj = build_graph(n, s->im, nedge, eu, ev, &s->row_ptr, &s->col);
+    free(eu); free(ev);
+    /* line 12: LOADBALANCE over contacts between two dynamic bodies */
+    {
+        int64_t m = 0;
+        int *ca = xcalloc((size_t)s->nc + 1, sizeof(int)), *cb = xcalloc((size_t)s->nc + 1, sizeof(int));
+        for (int64_t i = 0; i < s->nc; ++i) {
+            int a = s->con[i].a, b = s->con[i].b;
+            if (b >= n || s->im[a] == 0 || s->im[b] == 0) continue;
+            ca[m] = a; cb[m] = b; ++m;
+        }
+        int do_deact = s->P.lb_deact_every > 0 && (s->step_index % s->P.lb_deact_every) == 0;
+        int64_t *count = counts_from_masks(n, s->mask, s->sob, s->part_base, s->n_parts);
+        membership mem = {s->mask, s->sob, s->part_base, count};
+        if (s->P.lb_activate || do_deact)
+            load_balance_impl(&mem, n, s->row_ptr, s->col, m, ca, cb, s->sgamma, s->P.lb_activate, do_deact);
+        free(count); free(ca); free(cb);
+    }
+    for (int b = 0; b < n; ++b)
+        if (s->im[b] > 0 && s->mask[b] == 0) return ORC_ERR_MEMBERSHIP;
+    /* P_i and O (Eq 9-10): entries (body, worker), body-major */
+    s->entry_ptr = xcalloc((size_t)n + 1, sizeof(int64_t));
+    for (int b = 0; b < n; ++b) s->entry_ptr[b + 1] = s->entry_ptr[b] + popc64(s->mask[b]);
+    s->ne = s->entry_ptr[n];
+    s->entry_part = xcalloc((size_t)s->ne + 1, sizeof(int));
+    for (int b = 0; b < n; ++b) {
+        int64_t e = s->entry_ptr[b];
+        for (int w = 0; w < 64; ++w)
+            if (s->mask[b] >> w & 1u) s->entry_part[e++] = s->part_base[s->sob[b]] + w;
+    }
+    /* lines 13-15: weights from D(o,i) on G^t */
+    s->D = xcalloc((size_t)s->ne + 1, 1);
+    geodesics_impl(n, s->mask, s->sob, s->sbeta, s->row_ptr, s->col, s->entry_ptr, s->D);
+    s->weight = xcalloc((size_t)s->ne + 1, sizeof(double));
+    for (int b = 0; b < n; ++b) {
+        int64_t e0 = s->entry_ptr[b];
+        int k = (int)(s->entry_ptr[b + 1] - e0);
+        if (k == 1) s->weight[e0] = 1.0;
+        else if (k > 1) orc_weights(k, s->D + e0, s->weight + e0);
+    }
+    /* constraints of every worker: all dynamic ends active there; contacts
+     * (canonical order) then joints (index order) */
+    int64_t ncons = s->nc + s->nj;
+    uint64_t *cons_mask = xcalloc((size_t)ncons + 1, sizeof(uint64_t));
+    int *cons_scene = xcalloc((size_t)ncons + 1, sizeof(int));
+    for (int64_t i = 0; i < s->nc; ++i) {
+        int a = s->con[i].a, b = s->con[i].b;
+        uint64_t m = ~(uint64_t)0;
+        int any = 0;
+        if (s->im[a] > 0) { m &= s->mask[a]; any = 1; }
+        if (b < n && s->im[b] > 0) { m &= s->mask[b]; any = 1; }
+        cons_mask[i] = any ? m : 0;
+        cons_scene[i] = s->sob[a];
+    }
+    for (int j = 0; j < s->nj; ++j) {
+        int a = s->jab[2 * j], b = s->jab[2 * j + 1];
+        uint64_t m = ~(uint64_t)0;
+        int any = 0;
+        if (a >= 0 && s->im[a] > 0) { m &= s->mask[a]; any = 1; }
+        if (b >= 0 && s->im[b] > 0) { m &= s->mask[b]; any = 1; }
+        cons_mask[s->nc + j] = any ? m : 0;
+        cons_scene[s->nc + j] = a >= 0 ? s->sob[a] : (b >= 0 ? s->sob[b] : 0);
+    }
+    int64_t *pcount = xcalloc((size_t)s->n_parts + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < ncons; ++i)
+        for (int w = 0; w < 64; ++w)
+            if (cons_mask[i] >> w & 1u) pcount[s->part_base[cons_scene[i]] + w]++;
+    int64_t *pstart = xcalloc((size_t)s->n_parts + 2, sizeof(int64_t));
+    for (int p = 0; p < s->n_parts; ++p) pstart[p + 1] = pstart[p] + pcount[p];
+    s->npairs = pstart[s->n_parts];
+    s->pair_part = xcalloc((size_t)s->npairs + 1, sizeof(int));
+    s->pair_kind = xcalloc((size_t)s->npairs + 1, sizeof(int));
+    s->pair_cidx = xcalloc((size_t)s->npairs + 1, sizeof(int64_t));
+    s->pair_key = xcalloc((size_t)s->npairs + 1, sizeof(uint64_t));
+    s->pair_colour = xcalloc((size_t)s->npairs + 1, sizeof(int));
+    s->pair_lam = xcalloc((size_t)s->npairs * 3 + 1, sizeof(double));
+    {
+        int64_t *fill = xcalloc((size_t)s->n_parts + 1, sizeof(int64_t));
+        for (int64_t i = 0; i < ncons; ++i)
+            for (int w = 0; w < 64; ++w) {
+                if (!(cons_mask[i] >> w & 1u)) continue;
+                int p = s->part_base[cons_scene[i]] + w;
+                int64_t q = pstart[p] + fill[p]++;
+                s->pair_part[q] = p;
+                if (i < s->nc) {
+                    s->pair_kind[q] = 0;
+                    s->pair_cidx[q] = i;
+                    s->pair_key[q] = ((uint64_t)(uint32_t)s->con[i].a << 32) | (uint32_t)s->con[i].b;
+                } else {
+                    s->pair_kind[q] = 1;
+                    s->pair_cidx[q] = i - s->nc;
+                    s->pair_key[q] = ((uint64_t)1 << 62) | (uint64_t)(i - s->nc);
+                }
+            }
+        free(fill);
+    }
+    free(cons_mask); free(cons_scene);
+    /* line 16: every worker takes its timestep (sequentially here) */
+    s->copies = xcalloc((size_t)s->ne * 13 + 1, sizeof(double));
+    s->part_iters = xcalloc((size_t)s->n_parts + 1, sizeof(int));
+    s->part_res_sq = xcalloc((size_t)s->n_parts + 1, sizeof(double));
+    s->part_rows = xcalloc((size_t)s->n_parts + 1, sizeof(int64_t));
+    s->part_colours = xcalloc((size_t)s->n_parts + 1, sizeof(int));
+    {
+        /* bodies of each worker in ascending order, with their entry index */
+        int64_t *bstart = xcalloc((size_t)s->n_parts + 2, sizeof(int64_t));
+        for (int64_t e = 0; e < s->ne; ++e) bstart[s->entry_part[e] + 1]++;
+        for (int p = 0; p < s->n_parts; ++p) bstart[p + 1] += bstart[p];
+        int *pbody = xcalloc((size_t)s->ne + 1, sizeof(int));
+        int64_t *pentry = xcalloc((size_t)s->ne + 1, sizeof(int64_t));
+        int64_t *fill = xcalloc((size_t)s->n_parts + 1, sizeof(int64_t));
+        for (int b = 0; b < n; ++b)
+            for (int64_t e = s->entry_ptr[b]; e < s->entry_ptr[b + 1]; ++e) {
+                int p = s->entry_part[e];
+                int64_t k = bstart[p] + fill[p]++;
+                pbody[k] = b; pentry[k] = e;
+            }
+        int scene = 0;
+        for (int p = 0; p < s->n_parts; ++p) {
+            while (scene + 1 < s->ns && s->part_base[scene + 1] <= p) ++scene;
+            solve_worker(s, p, scene, pbody + bstart[p], (int)(bstart[p + 1] - bstart[p]),
+                         pentry + bstart[p], pstart[p], pstart[p + 1], dt, iters);
+        }
+        free(bstart); free(pbody); free(pentry); free(fill);
+    }
+    free(pcount); free(pstart);
+    /* lines 18-20: blend overlap bodies; others take their single copy */
+    for (int b = 0; b < n; ++b) {
+        int64_t e0 = s->entry_ptr[b];
+        int k = (int)(s->entry_ptr[b + 1] - e0);
+        if (k == 0) {
+            /* static body: unchanged */
+        } else if (k == 1) {
+            memcpy(s->st + 13 * (size_t)b, s->copies + 13 * (size_t)e0, 13 * sizeof(double));
+        } else {
+            orc_blend(k, s->copies + 13 * (size_t)e0, s->weight + e0, s->st + 13 * (size_t)b);
+        }
+    }
+    /* joint error after the step (position level) */
+    s->joint_violation_max = 0;
+    for (int j = 0; j < s->nj; ++j) {
+        int a = s->jab[2 * j], b = s->jab[2 * j + 1];
+        const double *anc = s->janc + 6 * (size_t)j;
+        double pA[3], pB[3], r[3], R[9];
+        if (a >= 0) { const double *x = s->st + 13 * (size_t)a; quat_to_matrix(x + 3, R); mat_vec(R, anc, r); for (int k = 0; k < 3; ++k) pA[k] = x[k] + r[k]; }
+        else for (int k = 0; k < 3; ++k) pA[k] = anc[k];
+        if (b >= 0) { const double *x = s->st + 13 * (size_t)b; quat_to_matrix(x + 3, R); mat_vec(R, anc + 3, r); for (int k = 0; k < 3; ++k) pB[k] = x[k] + r[k]; }
+        else for (int k = 0; k < 3; ++k) pB[k] = anc[3 + k];
+        double d[3] = {pB[0] - pA[0], pB[1] - pA[1], pB[2] - pA[2]};
+        double L = sqrt(dot3(d, d));
+        if (L > s->joint_violation_max) s->joint_violation_max = L;
+    }
+    /* keep impulses for the next step's warm start */
+    free(s->ws);
+    s->ws = xcalloc((size_t)s->npairs + 1, sizeof(ws_item));
+    for (int64_t q = 0; q < s->npairs; ++q) {
+        s->ws[q].part = s->pair_part[q];
+        s->ws[q].key = s->pair_key[q];
+        for (int k = 0; k < 3; ++k) s->ws[q].lam[k] = s->pair_lam[3 * q + k];
+    }
+    qsort(s->ws, s->npairs, sizeof(ws_item), cmp_ws);
+    s->ws_n = s->npairs;
+    s->step_index++;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Read-back of the last step's records                                      */
+/* ------------------------------------------------------------------------ */
+
+/* counts: [contacts, adjacency length, entries, pairs, n_parts] */
+void orc_get_counts(const orc_sim *s, int64_t *out) {
+    out[0] = s->nc; out[1] = s->nadj; out[2] = s->ne; out[3] = s->npairs; out[4] = s->n_parts;
+}
+
+void orc_get_contacts(const orc_sim *s, int *ab, double *phi, double *nrm, double *t1) {
+    for (int64_t i = 0; i < s->nc; ++i) {
+        ab[2 * i] = s->con[i].a; ab[2 * i + 1] = s->con[i].b;
+        phi[i] = s->con[i].phi;
+        for (int k = 0; k < 3; ++k) { nrm[3 * i + k] = s->con[i].n[k]; t1[3 * i + k] = s->con[i].t1[k]; }
+    }
+}
+
+void orc_get_graph(const orc_sim *s, int *row_ptr, int *col) {
+    memcpy(row_ptr, s->row_ptr, ((size_t)s->n + 1) * sizeof(int));
+    memcpy(col, s->col, (size_t)s->nadj * sizeof(int));
+}
+
+void orc_get_entries(const orc_sim *s, int64_t *entry_ptr, int *entry_part, uint8_t *D,
+                     double *weight, double *copies) {
+    memcpy(entry_ptr, s->entry_ptr, ((size_t)s->n + 1) * sizeof(int64_t));
+    memcpy(entry_part, s->entry_part, (size_t)s->ne * sizeof(int));
+    memcpy(D, s->D, (size_t)s->ne);
+    memcpy(weight, s->weight, (size_t)s->ne * sizeof(double));
+    memcpy(copies, s->copies, (size_t)s->ne * 13 * sizeof(double));
+}
+
+void orc_get_pairs(const orc_sim *s, int *part, int *kind, int64_t *cidx, uint64_t *key,
+                   int *colour, double *lam) {
+    memcpy(part, s->pair_part, (size_t)s->npairs * sizeof(int));
+    memcpy(kind, s->pair_kind, (size_t)s->npairs * sizeof(int));
+    memcpy(cidx, s->pair_cidx, (size_t)s->npairs * sizeof(int64_t));
+    memcpy(key, s->pair_key, (size_t)s->npairs * sizeof(uint64_t));
+    memcpy(colour, s->pair_colour, (size_t)s->npairs * sizeof(int));
+    memcpy(lam, s->pair_lam, (size_t)s->npairs * 3 * sizeof(double));
+}
+
+/* per worker: iterations run, residual sum of squares, rows, colours */
+void orc_get_part_stats(const orc_sim *s, int *iters, double *res_sq, int64_t *rows, int *colours) {
+    memcpy(iters, s->part_iters, (size_t)s->n_parts * sizeof(int));
+    memcpy(res_sq, s->part_res_sq, (size_t)s->n_parts * sizeof(double));
+    memcpy(rows, s->part_rows, (size_t)s->n_parts * sizeof(int64_t));
+    memcpy(colours, s->part_colours, (size_t)s->n_parts * sizeof(int));
+}
+
+/* [rms residual over all rows of all workers, max |residual|, max joint gap] */
+void orc_get_metrics(const orc_sim *s, double *out) {
+    out[0] = s->res_rows > 0 ? sqrt(s->res_sq_total / (double)s->res_rows) : 0.0;
+    out[1] = s->res_max;
+    out[2] = s->joint_violation_max;
+}
