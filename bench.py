@@ -1,0 +1,316 @@
+"""Throughput of the overlapping-partition rigid-body step on GB300.
+
+One "step" is Algorithm 1 lines 7-20 on the whole workload: contacts,
+constraint graph, load balance, membership, colouring, every worker's PGS
+solve + integration, geodesic weights and the blend.
+
+Default workload ``pile_large``: 262,144 spheres (64^3 lattice, r ~ U(0.4,0.6),
+density 1) dropped into a bowl of four 30-degree planes, 64 k-means workers,
+growth depth 2, weight depth 6, 30 PGS sweeps, dt = 1/60, load-balance removals
+every 10 steps.  The lattice needs ~130 steps of free fall before it touches
+the bowl, so the timed steps start after an untimed settle phase (150 steps by
+default) in the contact-rich regime.
+
+Printed (rank 0, one JSON line): body-steps/s over all ranks, the PGS row
+iterations/s, a roofline entry for the solver kernel, the FP64 oracle timed on
+the host as CPU baseline, an end-to-end figure through the C ABI with host
+buffers, SM clocks sampled during the timed region.
+
+--impl reference times the FP64 oracle instead (the CPU reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+CONTACT_ROW_BYTES = 80   # per constraint per sweep: 56 B record (2 slots, n, t1, k_n, k_t, r_a, r_b, target, mu) + 12 B lambda read + 12 B lambda write
+JOINT_ROW_BYTES = 80     # per joint per sweep: 56 B record (2 slots, r_A, r_B, k[3], target[3]) + 24 B lambda r/w
+ENTRY_BYTES = 120        # per (body, worker) per step: 60 B state + params read, 52 B copy write, 8 B index
+PAIR_ONCE_BYTES = 24     # per constraint per step: warm-start lambda read + final lambda write
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ovl", choices=["ovl", "reference"])
+    ap.add_argument("--workload", default="pile_large", choices=["pile_large", "chain", "pile_small"])
+    ap.add_argument("--settle", type=int, default=None, help="untimed steps before the warm-up")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def default_settle(workload):
+    return {"pile_large": 150, "chain": 0, "pile_small": 0}[workload]
+
+
+def make_scene(workload):
+    from paper_2403_17261_gb300 import scenes as S
+    return S.WORKLOADS[workload]()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 5 + k and r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU arm: the FP64 oracle, as it stands, on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+
+def oracle_sample_scene(workload):
+    from paper_2403_17261_gb300 import scenes as S
+    if workload == "pile_large":
+        return S.pile_large(side=16, n_sets=16), 150, "pile_large generator at 16^3 = 4096 bodies, 16 k-means workers, settled 150 steps by the oracle itself (untimed)"
+    if workload == "chain":
+        return S.chain(), 0, "the full 4096-sphere chain"
+    return S.pile_small(), 0, "the full 256-sphere pile"
+
+
+def oracle_run(workload, steps, warmup, max_seconds=None):
+    from oracle import oracle as O
+    sc, settle, desc = oracle_sample_scene(workload)
+    sim = O.OracleSim(sc)
+    if sc.assign_overlap:
+        sim.assign_overlap()
+    for _ in range(settle):
+        sim.step()
+    for _ in range(warmup):
+        sim.step()
+    t_total, body_steps, row_iters, done = 0.0, 0, 0, 0
+    for k in range(steps):
+        t0 = time.perf_counter()
+        sim.step()
+        t_total += time.perf_counter() - t0
+        body_steps += sc.n_bodies
+        row_iters += 3 * sim.counts()["pairs"] * sc.iters
+        done += 1
+        if max_seconds is not None and t_total > max_seconds:
+            break
+    return {"value": body_steps / t_total, "row_iters_per_s": row_iters / t_total, "steps": done,
+            "seconds": t_total, "sample": desc + f"; {done} timed steps after {warmup} warm-up",
+            "cores": 1}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    r = oracle_run(args.workload, args.steps, args.warmup, max_seconds=240.0)
+    line = {
+        "impl": "reference", "metric": "body-steps/s", "value": r["value"], "unit": "body-steps/s",
+        "n_gpus": args.gpus, "steps": r["steps"], "warmup": args.warmup,
+        "ms_per_step": 1e3 * r["seconds"] / max(r["steps"], 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": r["sample"]},
+        "cpu_baseline": {"value": r["value"], "unit": "body-steps/s", "cores": r["cores"], "kind": "oracle",
+                         "sample": r["sample"]},
+        "e2e": {"value": r["value"], "unit": "body-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "row_iters_per_s": r["row_iters_per_s"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def gpu_arm(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__ as g
+    from paper_2403_17261_gb300 import ovl
+
+    torch.cuda.set_device(local_rank)
+    g.build()
+    sc = make_scene(args.workload)
+    stream = torch.cuda.Stream()
+    params = dict(flags=ovl.OVL_FLAG_TIMING)
+    sim = ovl.Simulation(sc, params, stream=stream.cuda_stream)
+    settle = default_settle(args.workload) if args.settle is None else args.settle
+    for _ in range(settle):
+        sim.step()
+    for _ in range(args.warmup):
+        sim.step()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    solve_ms, rows_iters, bytes_solve, launches = [], 0, 0.0, []
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))          # L2 flush, outside the timed interval
+                starts[k].record(stream)
+            sim.step()
+            with torch.cuda.stream(stream):
+                ends[k].record(stream)
+            st = sim.stats()
+            solve_ms.append(st["phase_ms"]["solve"])
+            launches.append(st["n_launches"])
+            n_cons = st["n_pairs"]
+            rows_iters += st["n_rows"] * sc.iters
+            bytes_solve += (sc.iters * CONTACT_ROW_BYTES * n_cons + PAIR_ONCE_BYTES * n_cons
+                            + ENTRY_BYTES * st["n_entries"])
+        barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_local = sum(step_ms) / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    value = world * sc.n_bodies * args.steps / t_max
+    solve_s = sum(solve_ms) / 1e3
+    last = sim.stats()
+
+    # end to end through the C ABI with host buffers: pinned state in, state out
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.empty((sc.n_bodies, 13), dtype=torch.float32, pin_memory=True).numpy()
+        host_out = torch.empty((sc.n_bodies, 13), dtype=torch.float32, pin_memory=True).numpy()
+        sim.state(out=host_in)
+        e_s = torch.cuda.Event(enable_timing=True)
+        e_e = torch.cuda.Event(enable_timing=True)
+        n_e2e = max(3, args.steps // 2)
+        barrier()
+        e_s.record(stream)
+        for _ in range(n_e2e):
+            sim.set_state(host_in)
+            sim.step()
+            sim.state(out=host_out)
+            host_in, host_out = host_out, host_in
+        e_e.record(stream)
+        barrier()
+        te = e_s.elapsed_time(e_e) / 1e3
+        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        nbytes = sc.n_bodies * 13 * 4
+        e2e = {"value": world * sc.n_bodies * n_e2e / float(tt.item()), "unit": "body-steps/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": n_e2e}
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_solve / solve_s / 1e9
+    profile_traffic = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = oracle_run(args.workload, steps=80, warmup=1, max_seconds=15.0)
+        cpu = {"value": r["value"], "unit": "body-steps/s", "cores": r["cores"], "kind": "oracle",
+               "sample": r["sample"]}
+    line = {
+        "metric": "body-steps/s", "value": value, "unit": "body-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "bodies": sc.n_bodies, "workers": int(np.sum(sc.n_sets)),
+                   "pgs_iters": sc.iters, "dt": float(sc.scene_dt[0]), "settle_steps": settle,
+                   "l2": "flushed between timed steps (write of 2x L2)",
+                   "contacts_last_step": last["n_contacts"], "pairs_last_step": last["n_pairs"],
+                   "overlap_bodies_last_step": last["n_overlap"], "max_colours_last_step": last["max_colours"],
+                   "parallelism": f"replicas x{world}"},
+        "row_iters_per_s": rows_iters / solve_s,
+        "phase_ms_last_step": {k: round(v, 4) for k, v in last["phase_ms"].items()},
+        "roofline": {"bound": "hbm", "kernel": "k_solve", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": profile_traffic,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_solve / args.steps,
+                     "avg_launch_ms": 1e3 * solve_s / args.steps},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(sum(launches)),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    gpu_arm(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,1020 @@
+// ctx.cu -- the C ABI of libovl: context, scene upload, membership, and the
+// timestep of Algorithm 1 (lines 7-20) as a sequence of kernels on one
+// stream.  Counts that size the next buffers (contacts, graph edges,
+// entries, pairs) are read back between phases; the load balance runs on the
+// host between the graph and the membership phases.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <stdexcept>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace ovl;
+
+struct ovl_ctx {
+    ovl_params P{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int smem_optin = 0;
+    std::string err;
+
+    // scene (host copies)
+    bool has_scene = false;
+    HostScene hs;
+    int n = 0, np = 0, nj = 0, ns = 0, n_parts = 0, beta_max = 0;
+    std::vector<float> h_radius, h_im;
+    std::vector<int> h_body_base, h_plane_ptr, h_part_scene;
+    float cs = 1.f;
+    uint32_t tsize = 0;
+    long long vb_bits = 0;
+
+    // scene (device)
+    DBuf<float4> st, st_alt;
+    DBuf<float> radius, im, scene_mu, scene_dt;
+    DBuf<int> sob, scene_flags, n_sets, part_base, body_base, scene_beta, joint_scene, part_scene;
+    DBuf<float4> planes;
+    DBuf<int> plane_ptr, plane_list;
+    DBuf<int2> jab;
+    DBuf<float4> janc;
+    DBuf<long long> vb_base;
+    DBuf<uint64_t> mask;
+
+    // step buffers
+    DBuf<int> status;
+    DBuf<int4> cell;
+    DBuf<int> bucket_count, bucket_start, cursor, items, nb_list, nb_count, ccount, cstart;
+    DBuf<int2> c_ab;
+    DBuf<float4> c_n, c_t1;
+    DBuf<int> deg, tptr, cursor2, tcol, ucount, row_ptr, col;
+    DBuf<int> entry_count, entry_ptr, entry_body, entry_part, entry_slot, part_list, part_count,
+        part_bstart;
+    DBuf<uint32_t> sk, sv, sk2, sv2;
+    DBuf<int> cons_count, cons_start, pair_cons, pair_part, ps_cons, ps_part, part_pcount,
+        part_pstart, p_colour, part_ncol, col_off, pair_of_row;
+    DBuf<uint64_t> p_key;
+    DBuf<int2> p_slot;
+    DBuf<float4> p_lam0;
+    DBuf<unsigned long long> colour_scratch;
+    DBuf<float4> r0, r1, r2, rlam, lam_out;
+    DBuf<int4> r3;
+    DBuf<int> ws_pstart;
+    DBuf<uint64_t> ws_key;
+    DBuf<float4> ws_lam;
+    int64_t ws_n = 0;
+    DBuf<float4> copies, solve_scratch;
+    DBuf<int> part_iters;
+    DBuf<double> part_res_sq;
+    DBuf<uint32_t> visited, queue;
+    DBuf<int> qctl;
+    DBuf<uint8_t> D;
+    DBuf<float> weight;
+    DBuf<float> stage13;   // staging for host <-> device state transfers
+    DBuf<int> scan_tmp, sort_hist, sort_tmp;
+    HBuf<int> h_i32;
+    HBuf<int2> h_ab;
+    HBuf<int> h_rp, h_col;
+    HBuf<uint64_t> h_mask;
+
+    // last step
+    int64_t step_index = 0;
+    int nc = 0, nadj = 0, ne = 0, npairs = 0;
+    bool have_step = false;
+    cudaEvent_t ev[16] = {};
+    float phase_ms[12] = {};
+    long long last_launches = 0;
+};
+
+namespace {
+
+ovl_status fail(ovl_ctx *c, ovl_status code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+template <class F>
+ovl_status guarded(ovl_ctx *c, F &&f) {
+    if (!c) return OVL_ERR_ARG;
+    try {
+        return f();
+    } catch (const CudaError &e) {
+        return fail(c, OVL_ERR_CUDA, std::string(e.what) + ": " + cudaGetErrorString(e.err));
+    } catch (const std::bad_alloc &) {
+        return fail(c, OVL_ERR_CUDA, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(c, OVL_ERR_ARG, e.what());
+    }
+}
+
+int read_i32(ovl_ctx *c, const int *dptr) {
+    c->h_i32.ensure(1);
+    CK(cudaMemcpyAsync(c->h_i32.p, dptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return c->h_i32.p[0];
+}
+
+uint32_t next_pow2(uint64_t x) {
+    uint32_t p = 1;
+    while (p < x && p < (1u << 31)) p <<= 1;
+    return p;
+}
+
+int bits_for(int n) {
+    int b = 1;
+    while ((1 << b) < n && b < 31) ++b;
+    return b;
+}
+
+ovl_status check_device_status(ovl_ctx *c) {
+    int s = read_i32(c, c->status.p);
+    switch (s) {
+        case DEV_OK: return OVL_OK;
+        case DEV_ERR_CAPACITY:
+            return fail(c, OVL_ERR_CAPACITY, "a body has more than 32 sphere neighbours of larger index");
+        case DEV_ERR_NONFINITE: return fail(c, OVL_ERR_NONFINITE, "non-finite value in the blended state");
+        case DEV_ERR_MEMBERSHIP:
+            return fail(c, OVL_ERR_MEMBERSHIP, "dynamic body with no worker, or a worker index out of range");
+        case DEV_ERR_COLOURS: return fail(c, OVL_ERR_CAPACITY, "a worker needs more than 128 colours");
+        case DEV_ERR_TIMEOUT: return fail(c, OVL_ERR_TIMEOUT, "colouring did not finish within its round limit");
+        default: return fail(c, OVL_ERR_CUDA, "unknown device status");
+    }
+}
+
+void mark(ovl_ctx *c, int i) {
+    if (c->P.flags & OVL_FLAG_TIMING) CK(cudaEventRecord(c->ev[i], c->stream));
+}
+
+// ---- phases ----------------------------------------------------------------
+
+void phase_contacts(ovl_ctx *c) {
+    cudaStream_t s = c->stream;
+    const int n = c->n;
+    c->cell.ensure(n);
+    c->bucket_count.ensure((size_t)c->tsize + 1);
+    c->bucket_start.ensure((size_t)c->tsize + 1);
+    c->cursor.ensure(c->tsize);
+    c->items.ensure(n);
+    c->nb_list.ensure((size_t)n * OVL_MAX_NEIGH);
+    c->nb_count.ensure(n);
+    c->ccount.ensure((size_t)n + 1);
+    c->cstart.ensure((size_t)n + 1);
+    CK(cudaMemsetAsync(c->bucket_count.p, 0, sizeof(int) * ((size_t)c->tsize + 1), s));
+    CK(cudaMemsetAsync(c->cursor.p, 0, sizeof(int) * c->tsize, s));
+    ContactArgs a{};
+    a.st = c->st.p; a.im = c->im.p; a.n = n; a.sob = c->sob.p; a.scene_flags = c->scene_flags.p;
+    a.inv_cs = 1.0f / c->cs; a.tmask = c->tsize - 1;
+    a.cell = c->cell.p; a.bucket_count = c->bucket_count.p; a.bucket_start = c->bucket_start.p;
+    a.cursor = c->cursor.p; a.items = c->items.p; a.planes = c->planes.p;
+    a.plane_ptr = c->plane_ptr.p; a.plane_list = c->plane_list.p; a.margin = c->P.margin;
+    a.nb_list = c->nb_list.p; a.nb_count = c->nb_count.p; a.contact_count = c->ccount.p;
+    a.contact_start = c->cstart.p; a.status = c->status.p;
+    launch_cells(a, s);
+    scan_i32(c->bucket_count.p, c->bucket_start.p, (int)c->tsize, c->scan_tmp, s);
+    launch_bucket_fill(a, s);
+    launch_find_pairs(a, s);
+    scan_i32(c->ccount.p, c->cstart.p, n, c->scan_tmp, s);
+    c->nc = read_i32(c, c->cstart.p + n);
+    c->c_ab.ensure(c->nc + 1);
+    c->c_n.ensure(c->nc + 1);
+    c->c_t1.ensure(c->nc + 1);
+    a.c_ab = c->c_ab.p; a.c_n = c->c_n.p; a.c_t1 = c->c_t1.p;
+    launch_write_contacts(a, s);
+}
+
+void phase_graph(ovl_ctx *c) {
+    cudaStream_t s = c->stream;
+    const int n = c->n;
+    c->deg.ensure((size_t)n + 1);
+    c->tptr.ensure((size_t)n + 1);
+    c->cursor2.ensure((size_t)n + 1);
+    c->ucount.ensure((size_t)n + 1);
+    c->row_ptr.ensure((size_t)n + 1);
+    CK(cudaMemsetAsync(c->deg.p, 0, sizeof(int) * ((size_t)n + 1), s));
+    CK(cudaMemsetAsync(c->cursor2.p, 0, sizeof(int) * ((size_t)n + 1), s));
+    launch_edge_degree(c->c_ab.p, c->nc, c->jab.p, c->nj, c->im.p, n, c->deg.p, s);
+    scan_i32(c->deg.p, c->tptr.p, n, c->scan_tmp, s);
+    int e2 = read_i32(c, c->tptr.p + n);
+    c->tcol.ensure((size_t)e2 + 1);
+    launch_edge_fill(c->c_ab.p, c->nc, c->jab.p, c->nj, c->im.p, n, c->tptr.p, c->cursor2.p,
+                     c->tcol.p, s);
+    launch_adj_unique(c->tptr.p, n, c->tcol.p, c->ucount.p, s);
+    scan_i32(c->ucount.p, c->row_ptr.p, n, c->scan_tmp, s);
+    c->nadj = read_i32(c, c->row_ptr.p + n);
+    c->col.ensure((size_t)c->nadj + 1);
+    launch_adj_compact(c->tptr.p, c->tcol.p, n, c->row_ptr.p, c->col.p, s);
+}
+
+// Algorithm 6 on the host over the contacts between two dynamic bodies
+void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
+    if (!act && !deact) return;
+    cudaStream_t s = c->stream;
+    const int n = c->n;
+    c->h_ab.ensure(c->nc + 1);
+    c->h_rp.ensure((size_t)n + 1);
+    c->h_col.ensure((size_t)c->nadj + 1);
+    c->h_mask.ensure(n);
+    CK(cudaMemcpyAsync(c->h_ab.p, c->c_ab.p, sizeof(int2) * c->nc, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->h_rp.p, c->row_ptr.p, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->h_col.p, c->col.p, sizeof(int) * c->nadj, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->h_mask.p, c->mask.p, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int> ca, cb;
+    ca.reserve(c->nc);
+    cb.reserve(c->nc);
+    for (int i = 0; i < c->nc; ++i) {
+        int a = c->h_ab.p[i].x, b = c->h_ab.p[i].y;
+        if (b >= n || !(c->h_im[a] > 0.f) || !(c->h_im[b] > 0.f)) continue;
+        ca.push_back(a);
+        cb.push_back(b);
+    }
+    if (ca.empty()) return;
+    std::vector<uint64_t> m(c->h_mask.p, c->h_mask.p + n);
+    host_load_balance(c->hs, m, (int64_t)ca.size(), ca.data(), cb.data(), c->h_rp.p, c->h_col.p, act,
+                      deact);
+    std::copy(m.begin(), m.end(), c->h_mask.p);
+    CK(cudaMemcpyAsync(c->mask.p, c->h_mask.p, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+}
+
+MemberArgs member_args(ovl_ctx *c) {
+    MemberArgs a{};
+    a.n = c->n; a.nc = c->nc; a.nj = c->nj; a.n_parts = c->n_parts;
+    a.im = c->im.p; a.sob = c->sob.p; a.n_sets = c->n_sets.p; a.part_base = c->part_base.p;
+    a.joint_scene = c->joint_scene.p; a.mask = c->mask.p; a.c_ab = c->c_ab.p; a.jab = c->jab.p;
+    a.entry_count = c->entry_count.p; a.entry_ptr = c->entry_ptr.p; a.entry_body = c->entry_body.p;
+    a.entry_part = c->entry_part.p; a.entry_slot = c->entry_slot.p; a.part_list = c->part_list.p;
+    a.part_bstart = c->part_bstart.p; a.cons_count = c->cons_count.p; a.cons_start = c->cons_start.p;
+    a.pair_cons = c->pair_cons.p; a.pair_part = c->pair_part.p; a.ps_cons = c->ps_cons.p;
+    a.ps_part = c->ps_part.p; a.part_pstart = c->part_pstart.p; a.p_key = c->p_key.p;
+    a.p_slot = c->p_slot.p; a.p_lam0 = c->p_lam0.p; a.status = c->status.p;
+    return a;
+}
+
+// stable grouping of items by a small key (< n_parts): out = item indices
+void group_by(ovl_ctx *c, const int *key, int m, DBuf<int> &out) {
+    cudaStream_t s = c->stream;
+    c->sk.ensure(m + 1); c->sv.ensure(m + 1); c->sk2.ensure(m + 1); c->sv2.ensure(m + 1);
+    out.ensure(m + 1);
+    if (m == 0) return;
+    CK(cudaMemcpyAsync(c->sk.p, key, sizeof(int) * m, cudaMemcpyDeviceToDevice, s));
+    iota_u32(c->sv.p, m, s);
+    bool alt = false;
+    radix_sort_u32(c->sk.p, c->sv.p, c->sk2.p, c->sv2.p, m, bits_for(c->n_parts), c->sort_hist,
+                   c->sort_tmp, s, &alt);
+    CK(cudaMemcpyAsync(out.p, alt ? c->sv2.p : c->sv.p, sizeof(int) * m, cudaMemcpyDeviceToDevice, s));
+}
+
+void phase_membership(ovl_ctx *c, float dt_override) {
+    (void)dt_override;
+    cudaStream_t s = c->stream;
+    const int n = c->n, P = c->n_parts;
+    c->entry_count.ensure((size_t)n + 1);
+    c->entry_ptr.ensure((size_t)n + 1);
+    MemberArgs a = member_args(c);
+    launch_entry_count(a, s);
+    scan_i32(c->entry_count.p, c->entry_ptr.p, n, c->scan_tmp, s);
+    c->ne = read_i32(c, c->entry_ptr.p + n);
+    const int ne = c->ne;
+    c->entry_body.ensure(ne + 1); c->entry_part.ensure(ne + 1); c->entry_slot.ensure(ne + 1);
+    c->part_count.ensure((size_t)P + 1); c->part_bstart.ensure((size_t)P + 1);
+    a = member_args(c);
+    launch_entry_fill(a, s);
+    group_by(c, c->entry_part.p, ne, c->part_list);
+    CK(cudaMemsetAsync(c->part_count.p, 0, sizeof(int) * ((size_t)P + 1), s));
+    histogram_i32(c->entry_part.p, ne, c->part_count.p, s);
+    scan_i32(c->part_count.p, c->part_bstart.p, P, c->scan_tmp, s);
+    a = member_args(c);
+    launch_entry_slot(a, ne, s);
+    // (worker, constraint) pairs
+    const int K = c->nc + c->nj;
+    c->cons_count.ensure((size_t)K + 1); c->cons_start.ensure((size_t)K + 1);
+    a = member_args(c);
+    launch_cons_count(a, s);
+    scan_i32(c->cons_count.p, c->cons_start.p, K, c->scan_tmp, s);
+    c->npairs = read_i32(c, c->cons_start.p + K);
+    const int npr = c->npairs;
+    c->pair_cons.ensure(npr + 1); c->pair_part.ensure(npr + 1); c->ps_cons.ensure(npr + 1);
+    c->ps_part.ensure(npr + 1); c->part_pcount.ensure((size_t)P + 1); c->part_pstart.ensure((size_t)P + 1);
+    c->p_key.ensure(npr + 1); c->p_slot.ensure(npr + 1); c->p_lam0.ensure(npr + 1);
+    a = member_args(c);
+    launch_pair_fill(a, s);
+    DBuf<int> &order = c->pair_of_row;   // temporary use before colouring
+    order.ensure(npr + 1);
+    group_by(c, c->pair_part.p, npr, order);
+    launch_pair_gather(a, reinterpret_cast<const uint32_t *>(order.p), npr, s);
+    CK(cudaMemsetAsync(c->part_pcount.p, 0, sizeof(int) * ((size_t)P + 1), s));
+    histogram_i32(c->pair_part.p, npr, c->part_pcount.p, s);
+    scan_i32(c->part_pcount.p, c->part_pstart.p, P, c->scan_tmp, s);
+    WarmArgs w{};
+    w.ws_pstart = c->ws_pstart.p; w.ws_key = c->ws_key.p; w.ws_lam = c->ws_lam.p;
+    w.factor = c->P.warmstart;
+    launch_pair_setup(a, w, npr, s);
+}
+
+int colour_smem_slots(ovl_ctx *c) {
+    int avail = c->smem_optin - 20 * 1024;
+    return std::max(0, avail / 24);
+}
+
+int solve_smem_slots(ovl_ctx *c) {
+    int avail = c->smem_optin - 1024;
+    return std::max(0, avail / 32);
+}
+
+void phase_colour(ovl_ctx *c) {
+    const int P = c->n_parts, npr = c->npairs;
+    c->p_colour.ensure(npr + 1);
+    c->part_ncol.ensure((size_t)P + 1);
+    c->col_off.ensure((size_t)P * (2 * OVL_MAX_COLOURS + 1) + 1);
+    c->pair_of_row.ensure(npr + 1);
+    c->colour_scratch.ensure(3 * (size_t)c->ne + 1);
+    ColourArgs a{};
+    a.n_parts = P; a.part_bstart = c->part_bstart.p; a.part_pstart = c->part_pstart.p;
+    a.p_key = c->p_key.p; a.p_slot = c->p_slot.p; a.p_colour = c->p_colour.p;
+    a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p; a.pair_of_row = c->pair_of_row.p;
+    a.scratch = c->colour_scratch.p; a.smem_slots = colour_smem_slots(c); a.status = c->status.p;
+    launch_colour(a, c->stream);
+}
+
+void phase_rows(ovl_ctx *c, float dt_override) {
+    const int npr = c->npairs;
+    c->r0.ensure(npr + 1); c->r1.ensure(npr + 1); c->r2.ensure(npr + 1); c->r3.ensure(npr + 1);
+    c->rlam.ensure(npr + 1);
+    RowArgs a{};
+    a.n = c->n; a.nc = c->nc; a.np = npr; a.pair_of_row = c->pair_of_row.p; a.ps_cons = c->ps_cons.p;
+    a.ps_part = c->ps_part.p; a.p_slot = c->p_slot.p; a.p_lam0 = c->p_lam0.p; a.c_ab = c->c_ab.p;
+    a.c_n = c->c_n.p; a.c_t1 = c->c_t1.p; a.jab = c->jab.p; a.janc = c->janc.p;
+    a.joint_scene = c->joint_scene.p; a.st = c->st.p; a.sob = c->sob.p; a.part_scene = c->part_scene.p;
+    a.scene_dt = c->scene_dt.p; a.scene_mu = c->scene_mu.p; a.dt_override = dt_override;
+    a.erp = c->P.erp; a.slop = c->P.slop;
+    a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
+    launch_rows(a, c->stream);
+}
+
+int solve_threads(ovl_ctx *c) {
+    int t = c->P.pgs_threads;
+    if (t <= 0) t = 512;
+    t = std::max(32, std::min(1024, (t + 31) / 32 * 32));
+    return t;
+}
+
+void phase_solve(ovl_ctx *c, float dt_override, int iters) {
+    const int P = c->n_parts, npr = c->npairs;
+    c->lam_out.ensure(npr + 1);
+    c->copies.ensure(4 * (size_t)c->ne + 1);
+    c->solve_scratch.ensure(2 * (size_t)c->ne + 1);
+    c->part_iters.ensure((size_t)P + 1);
+    c->part_res_sq.ensure((size_t)P + 1);
+    CK(cudaMemsetAsync(c->part_res_sq.p, 0, sizeof(double) * ((size_t)P + 1), c->stream));
+    SolveArgs a{};
+    a.n_parts = P; a.part_bstart = c->part_bstart.p; a.part_list = c->part_list.p;
+    a.entry_body = c->entry_body.p; a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p;
+    a.part_scene = c->part_scene.p; a.scene_dt = c->scene_dt.p; a.dt_override = dt_override;
+    a.gravity = make_float3(c->P.gravity[0], c->P.gravity[1], c->P.gravity[2]);
+    a.st = c->st.p; a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
+    a.lam_out = c->lam_out.p; a.copies = c->copies.p; a.scratch = c->solve_scratch.p;
+    a.iters = iters; a.smem_slots = solve_smem_slots(c); a.flags = c->P.flags;
+    a.res_tol = c->P.res_tol; a.res_check_every = c->P.res_check_every;
+    a.part_iters = c->part_iters.p; a.part_res_sq = c->part_res_sq.p; a.status = c->status.p;
+    launch_solve(a, solve_threads(c), c->stream);
+}
+
+void phase_geodesics(ovl_ctx *c) {
+    cudaStream_t s = c->stream;
+    c->D.ensure(c->ne + 1);
+    c->visited.ensure((size_t)((c->vb_bits + 31) / 32) + 1);
+    c->queue.ensure((size_t)c->vb_bits + 1);
+    c->qctl.ensure((size_t)c->beta_max + 4);
+    CK(cudaMemsetAsync(c->visited.p, 0, sizeof(uint32_t) * ((size_t)((c->vb_bits + 31) / 32) + 1), s));
+    CK(cudaMemsetAsync(c->qctl.p, 0, sizeof(int) * ((size_t)c->beta_max + 4), s));
+    fill_u8(c->D.p, 255, c->ne, s);
+    GeoArgs a{};
+    a.n = c->n; a.mask = c->mask.p; a.sob = c->sob.p; a.scene_beta = c->scene_beta.p;
+    a.body_base = c->body_base.p; a.vb_base = c->vb_base.p; a.row_ptr = c->row_ptr.p; a.col = c->col.p;
+    a.entry_ptr = c->entry_ptr.p; a.visited = c->visited.p; a.queue = c->queue.p; a.qctl = c->qctl.p;
+    a.D = c->D.p;
+    launch_geo_sources(a, s);
+    for (int L = 1; L <= c->beta_max; ++L) launch_geo_level(a, L, s);
+}
+
+void phase_blend(ovl_ctx *c, float dt_override) {
+    c->weight.ensure(c->ne + 1);
+    c->st_alt.ensure(4 * (size_t)c->n);
+    BlendArgs a{};
+    a.n = c->n; a.entry_ptr = c->entry_ptr.p; a.D = c->D.p; a.copies = c->copies.p; a.st_in = c->st.p;
+    a.st_out = c->st_alt.p; a.weight = c->weight.p; a.status = c->status.p;
+    a.sob = c->sob.p; a.scene_dt = c->scene_dt.p; a.dt_override = dt_override;
+    launch_blend(a, c->stream);
+    std::swap(c->st, c->st_alt);
+    // the impulses of this step become the next step's warm-start cache
+    std::swap(c->ws_key, c->p_key);
+    std::swap(c->ws_lam, c->lam_out);
+    std::swap(c->ws_pstart, c->part_pstart);
+    c->ws_n = c->npairs;
+}
+
+ovl_status run_step(ovl_ctx *c, float dt, int iters) {
+    if (!c->has_scene) return fail(c, OVL_ERR_ARG, "no scene uploaded");
+    if (iters < 0) return fail(c, OVL_ERR_ARG, "iters must be >= 0");
+    cudaStream_t s = c->stream;
+    const long long launches0 = launch_count();
+    CK(cudaMemsetAsync(c->status.p, 0, sizeof(int), s));
+    bool deact = c->P.lb_deact_every > 0 && (c->step_index % c->P.lb_deact_every) == 0;
+    mark(c, 0);
+    phase_contacts(c);
+    mark(c, 1);
+    phase_graph(c);
+    mark(c, 2);
+    phase_load_balance(c, c->P.lb_activate != 0, deact);
+    mark(c, 3);
+    phase_membership(c, dt);
+    mark(c, 4);
+    phase_colour(c);
+    mark(c, 5);
+    phase_rows(c, dt);
+    mark(c, 6);
+    phase_solve(c, dt, iters);
+    mark(c, 7);
+    phase_geodesics(c);
+    mark(c, 8);
+    phase_blend(c, dt);
+    mark(c, 9);
+    ovl_status st = check_device_status(c);
+    c->last_launches = launch_count() - launches0;
+    c->have_step = true;
+    if (c->P.flags & OVL_FLAG_TIMING) {
+        CK(cudaEventSynchronize(c->ev[9]));
+        for (int i = 0; i < 9; ++i) CK(cudaEventElapsedTime(&c->phase_ms[i], c->ev[i], c->ev[i + 1]));
+        CK(cudaEventElapsedTime(&c->phase_ms[9], c->ev[0], c->ev[9]));
+    }
+    if (st != OVL_OK) return st;
+    c->step_index++;
+    return OVL_OK;
+}
+
+void validate_masks(const ovl_ctx *c, const uint64_t *m) {
+    for (int b = 0; b < c->n; ++b) {
+        int ns = c->hs.n_sets[c->hs.sob[b]];
+        uint64_t allowed = ns >= 64 ? ~0ull : ((1ull << ns) - 1ull);
+        bool dyn = c->h_im[b] > 0.f;
+        if ((dyn && m[b] == 0) || (!dyn && m[b] != 0) || (m[b] & ~allowed))
+            throw std::invalid_argument("membership: body " + std::to_string(b) +
+                                        " has an empty or out-of-range worker mask");
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+ovl_status ovl_default_params(ovl_params *p) {
+    if (!p) return OVL_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->gravity[0] = 0.f; p->gravity[1] = 0.f; p->gravity[2] = -9.81f;
+    p->margin = 0.05f; p->erp = 0.2f; p->slop = 0.001f; p->warmstart = 1.0f;
+    p->lb_activate = 1; p->lb_deact_every = 1;
+    p->res_tol = 0.f; p->res_check_every = 0; p->pgs_threads = 0; p->flags = 0;
+    return OVL_OK;
+}
+
+ovl_status ovl_create(ovl_ctx **out, const ovl_params *p, void *cuda_stream) {
+    if (!out) return OVL_ERR_ARG;
+    *out = nullptr;
+    ovl_ctx *c = new (std::nothrow) ovl_ctx();
+    if (!c) return OVL_ERR_ARG;
+    if (p) c->P = *p; else ovl_default_params(&c->P);
+    ovl_status st = guarded(c, [&]() -> ovl_status {
+        CK(cudaGetDevice(&c->device));
+        CK(cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+        if (cuda_stream) {
+            c->stream = (cudaStream_t)cuda_stream;
+        } else {
+            CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+            c->own_stream = true;
+        }
+        for (auto &e : c->ev) CK(cudaEventCreate(&e));
+        c->status.ensure(4);
+        CK(cudaMemsetAsync(c->status.p, 0, 4 * sizeof(int), c->stream));
+        return OVL_OK;
+    });
+    if (st != OVL_OK) {
+        delete c;
+        return st;
+    }
+    *out = c;
+    return OVL_OK;
+}
+
+const char *ovl_last_error(const ovl_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+const char *ovl_phase_name(int32_t phase) {
+    static const char *names[] = {"contacts", "graph", "load_balance", "membership", "colouring",
+                                  "rows",     "solve", "geodesics",    "blend",      "total"};
+    return (phase >= 0 && phase < 10) ? names[phase] : "";
+}
+
+}  // extern "C"
+
+namespace {
+
+void release_all(ovl_ctx *c) {
+    c->st.release(); c->st_alt.release(); c->radius.release(); c->im.release();
+    c->scene_mu.release(); c->scene_dt.release(); c->sob.release(); c->scene_flags.release();
+    c->n_sets.release(); c->part_base.release(); c->body_base.release(); c->scene_beta.release();
+    c->joint_scene.release(); c->part_scene.release(); c->planes.release(); c->plane_ptr.release();
+    c->plane_list.release(); c->jab.release(); c->janc.release(); c->vb_base.release();
+    c->mask.release(); c->cell.release(); c->bucket_count.release(); c->bucket_start.release();
+    c->cursor.release(); c->items.release(); c->nb_list.release(); c->nb_count.release();
+    c->ccount.release(); c->cstart.release(); c->c_ab.release(); c->c_n.release(); c->c_t1.release();
+    c->deg.release(); c->tptr.release(); c->cursor2.release(); c->tcol.release(); c->ucount.release();
+    c->row_ptr.release(); c->col.release(); c->entry_count.release(); c->entry_ptr.release();
+    c->entry_body.release(); c->entry_part.release(); c->entry_slot.release(); c->part_list.release();
+    c->part_count.release(); c->part_bstart.release(); c->sk.release(); c->sv.release();
+    c->sk2.release(); c->sv2.release(); c->cons_count.release(); c->cons_start.release();
+    c->pair_cons.release(); c->pair_part.release(); c->ps_cons.release(); c->ps_part.release();
+    c->part_pcount.release(); c->part_pstart.release(); c->p_colour.release(); c->part_ncol.release();
+    c->col_off.release(); c->pair_of_row.release(); c->p_key.release(); c->p_slot.release();
+    c->p_lam0.release(); c->colour_scratch.release(); c->r0.release(); c->r1.release();
+    c->r2.release(); c->rlam.release(); c->lam_out.release(); c->r3.release(); c->ws_pstart.release();
+    c->ws_key.release(); c->ws_lam.release(); c->copies.release(); c->solve_scratch.release();
+    c->part_iters.release(); c->part_res_sq.release(); c->visited.release(); c->queue.release();
+    c->qctl.release(); c->D.release(); c->weight.release(); c->stage13.release(); c->scan_tmp.release();
+    c->sort_hist.release(); c->sort_tmp.release();
+}
+
+template <class T>
+void upload(DBuf<T> &buf, const T *src, size_t n, cudaStream_t s) {
+    buf.ensure(n ? n : 1);
+    if (n) CK(cudaMemcpyAsync(buf.p, src, sizeof(T) * n, cudaMemcpyHostToDevice, s));
+}
+
+void reset_warmstart(ovl_ctx *c) {
+    c->ws_pstart.ensure((size_t)c->n_parts + 1);
+    CK(cudaMemsetAsync(c->ws_pstart.p, 0, sizeof(int) * ((size_t)c->n_parts + 1), c->stream));
+    c->ws_key.ensure(1);
+    c->ws_lam.ensure(1);
+    c->ws_n = 0;
+}
+
+void upload_masks(ovl_ctx *c, const std::vector<uint64_t> &m) {
+    upload(c->mask, m.data(), m.size(), c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+}
+
+std::vector<uint64_t> download_masks(ovl_ctx *c) {
+    std::vector<uint64_t> m(c->n);
+    if (c->n) CK(cudaMemcpyAsync(m.data(), c->mask.p, sizeof(uint64_t) * c->n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return m;
+}
+
+template <class T>
+void download(T *dst, const T *src, size_t n, cudaStream_t s) {
+    if (n) CK(cudaMemcpyAsync(dst, src, sizeof(T) * n, cudaMemcpyDeviceToHost, s));
+}
+
+}  // namespace
+
+extern "C" {
+
+ovl_status ovl_destroy(ovl_ctx *c) {
+    if (!c) return OVL_ERR_ARG;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    release_all(c);
+    c->h_i32.release(); c->h_ab.release(); c->h_rp.release(); c->h_col.release(); c->h_mask.release();
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return OVL_OK;
+}
+
+ovl_status ovl_scene_upload(ovl_ctx *c, const ovl_scene_desc *d) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!d || d->n_bodies <= 0 || !d->state || !d->radius || !d->inv_mass)
+            return fail(c, OVL_ERR_ARG, "scene: bodies, state, radius and inv_mass are required");
+        const int n = d->n_bodies, ns = d->n_scenes > 0 ? d->n_scenes : 1;
+        if (n >= (1 << 26)) return fail(c, OVL_ERR_ARG, "scene: at most 2^26 - 1 bodies");
+        if (d->n_planes < 0 || d->n_joints < 0) return fail(c, OVL_ERR_ARG, "scene: negative counts");
+        if (d->n_planes > 0 && !d->planes) return fail(c, OVL_ERR_ARG, "scene: planes missing");
+        if (d->n_joints > 0 && (!d->joint_bodies || !d->joint_anchors))
+            return fail(c, OVL_ERR_ARG, "scene: joints missing");
+        if (!d->scene_mu || !d->scene_dt || !d->scene_flags || !d->scene_gamma || !d->scene_beta || !d->n_sets)
+            return fail(c, OVL_ERR_ARG, "scene: per-scene arrays are required");
+        std::vector<int> sob(n, 0);
+        if (d->scene_of_body) std::copy(d->scene_of_body, d->scene_of_body + n, sob.begin());
+        for (int b = 0; b < n; ++b) {
+            if (sob[b] < 0 || sob[b] >= ns || (b > 0 && sob[b] < sob[b - 1]))
+                return fail(c, OVL_ERR_ARG, "scene: scene_of_body must be non-decreasing and < n_scenes");
+            if (!(d->radius[b] > 0.f) || !(d->inv_mass[b] >= 0.f))
+                return fail(c, OVL_ERR_ARG, "scene: radius must be > 0 and inv_mass >= 0");
+        }
+        for (int s = 0; s < ns; ++s) {
+            if (d->n_sets[s] < 1 || d->n_sets[s] > 64) return fail(c, OVL_ERR_ARG, "scene: n_sets must be 1..64");
+            if (d->scene_beta[s] < 0 || d->scene_beta[s] > 254 || d->scene_gamma[s] < 0)
+                return fail(c, OVL_ERR_ARG, "scene: beta must be 0..254 and gamma >= 0");
+            if (!(d->scene_dt[s] > 0.f)) return fail(c, OVL_ERR_ARG, "scene: dt must be > 0");
+        }
+        cudaStream_t s = c->stream;
+        CK(cudaStreamSynchronize(s));
+        release_all(c);
+        c->status.ensure(4);
+        c->n = n; c->ns = ns; c->np = d->n_planes; c->nj = d->n_joints;
+        c->h_radius.assign(d->radius, d->radius + n);
+        c->h_im.assign(d->inv_mass, d->inv_mass + n);
+        // scene ranges and worker numbering
+        c->h_body_base.assign(ns + 1, 0);
+        for (int b = 0; b < n; ++b) c->h_body_base[sob[b] + 1]++;
+        for (int i = 0; i < ns; ++i) c->h_body_base[i + 1] += c->h_body_base[i];
+        std::vector<int> part_base(ns + 1, 0);
+        for (int i = 0; i < ns; ++i) part_base[i + 1] = part_base[i] + d->n_sets[i];
+        c->n_parts = part_base[ns];
+        c->h_part_scene.assign(c->n_parts, 0);
+        for (int i = 0; i < ns; ++i)
+            for (int w = 0; w < d->n_sets[i]; ++w) c->h_part_scene[part_base[i] + w] = i;
+        std::vector<long long> vb(ns + 1, 0);
+        for (int i = 0; i < ns; ++i)
+            vb[i + 1] = vb[i] + (long long)d->n_sets[i] * (c->h_body_base[i + 1] - c->h_body_base[i]);
+        c->vb_bits = vb[ns];
+        c->beta_max = 0;
+        for (int i = 0; i < ns; ++i) c->beta_max = std::max(c->beta_max, d->scene_beta[i]);
+        // planes grouped by scene
+        std::vector<int> pscene(c->np, 0);
+        if (d->plane_scene) std::copy(d->plane_scene, d->plane_scene + c->np, pscene.begin());
+        c->h_plane_ptr.assign(ns + 1, 0);
+        for (int p = 0; p < c->np; ++p) {
+            if (pscene[p] < 0 || pscene[p] >= ns) return fail(c, OVL_ERR_ARG, "scene: bad plane_scene");
+            c->h_plane_ptr[pscene[p] + 1]++;
+        }
+        for (int i = 0; i < ns; ++i) c->h_plane_ptr[i + 1] += c->h_plane_ptr[i];
+        std::vector<int> plist(c->np), pfill(c->h_plane_ptr.begin(), c->h_plane_ptr.end() - 1);
+        for (int p = 0; p < c->np; ++p) plist[pfill[pscene[p]]++] = p;
+        std::vector<float4> planes(c->np);
+        for (int p = 0; p < c->np; ++p)
+            planes[p] = make_float4(d->planes[4 * p], d->planes[4 * p + 1], d->planes[4 * p + 2], d->planes[4 * p + 3]);
+        // joints
+        std::vector<int2> jab(c->nj);
+        std::vector<float4> janc(2 * (size_t)c->nj);
+        std::vector<int> jscene(c->nj, 0);
+        for (int j = 0; j < c->nj; ++j) {
+            int a = d->joint_bodies[2 * j], b = d->joint_bodies[2 * j + 1];
+            if (a < -1 || a >= n || b < -1 || b >= n || (a < 0 && b < 0))
+                return fail(c, OVL_ERR_ARG, "scene: joint bodies out of range");
+            if (a >= 0 && b >= 0 && sob[a] != sob[b]) return fail(c, OVL_ERR_ARG, "scene: joint across scenes");
+            jab[j] = make_int2(a, b);
+            const float *an = d->joint_anchors + 6 * (size_t)j;
+            janc[2 * j] = make_float4(an[0], an[1], an[2], 0.f);
+            janc[2 * j + 1] = make_float4(an[3], an[4], an[5], 0.f);
+            jscene[j] = a >= 0 ? sob[a] : sob[b];
+        }
+        // largest contact distance sets the grid cell
+        float rmax = 0.f;
+        for (int b = 0; b < n; ++b) rmax = std::max(rmax, d->radius[b]);
+        c->cs = (2.f * rmax + c->P.margin) * 1.01f;
+        c->tsize = next_pow2(2ull * (uint64_t)n);
+        // host scene for the sequential algorithms
+        c->hs.n = n; c->hs.ns = ns; c->hs.n_parts = c->n_parts;
+        c->hs.inv_mass = c->h_im; c->hs.sob = sob; c->hs.part_base = part_base;
+        c->hs.scene_gamma.assign(d->scene_gamma, d->scene_gamma + ns);
+        c->hs.n_sets.assign(d->n_sets, d->n_sets + ns);
+        c->hs.jab.assign(d->joint_bodies, d->joint_bodies + 2 * (size_t)c->nj);
+        // device copies
+        upload(c->radius, d->radius, n, s);
+        upload(c->im, d->inv_mass, n, s);
+        upload(c->sob, sob.data(), n, s);
+        upload(c->scene_mu, d->scene_mu, ns, s);
+        upload(c->scene_dt, d->scene_dt, ns, s);
+        upload(c->scene_flags, d->scene_flags, ns, s);
+        upload(c->scene_beta, d->scene_beta, ns, s);
+        upload(c->n_sets, d->n_sets, ns, s);
+        upload(c->part_base, part_base.data(), ns + 1, s);
+        upload(c->body_base, c->h_body_base.data(), ns + 1, s);
+        upload(c->part_scene, c->h_part_scene.data(), c->n_parts, s);
+        upload(c->vb_base, vb.data(), ns + 1, s);
+        upload(c->planes, planes.data(), c->np, s);
+        upload(c->plane_ptr, c->h_plane_ptr.data(), ns + 1, s);
+        upload(c->plane_list, plist.data(), c->np, s);
+        upload(c->jab, jab.data(), c->nj, s);
+        upload(c->janc, janc.data(), 2 * (size_t)c->nj, s);
+        upload(c->joint_scene, jscene.data(), c->nj, s);
+        // state
+        DBuf<float> tmp13;
+        upload(tmp13, d->state, 13 * (size_t)n, s);
+        c->st.ensure(4 * (size_t)n);
+        c->st_alt.ensure(4 * (size_t)n);
+        launch_pack_state(tmp13.p, c->radius.p, c->im.p, n, c->st.p, s);
+        CK(cudaStreamSynchronize(s));
+        tmp13.release();
+        c->mask.ensure(n);
+        CK(cudaMemsetAsync(c->mask.p, 0, sizeof(uint64_t) * n, s));
+        reset_warmstart(c);
+        CK(cudaMemsetAsync(c->status.p, 0, 4 * sizeof(int), s));
+        CK(cudaStreamSynchronize(s));
+        c->step_index = 0;
+        c->have_step = false;
+        c->has_scene = true;
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_set_partition(ovl_ctx *c, const int32_t *set_of_body) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->has_scene || !set_of_body) return fail(c, OVL_ERR_ARG, "no scene or null partition");
+        std::vector<uint64_t> m(c->n, 0);
+        for (int b = 0; b < c->n; ++b) {
+            if (!(c->h_im[b] > 0.f)) continue;
+            int w = set_of_body[b];
+            if (w < 0 || w >= c->hs.n_sets[c->hs.sob[b]])
+                return fail(c, OVL_ERR_MEMBERSHIP, "partition: worker index out of range for body " + std::to_string(b));
+            m[b] = 1ull << w;
+        }
+        upload_masks(c, m);
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_set_membership(ovl_ctx *c, const uint64_t *masks) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->has_scene || !masks) return fail(c, OVL_ERR_ARG, "no scene or null masks");
+        try {
+            validate_masks(c, masks);
+        } catch (const std::invalid_argument &e) {
+            return fail(c, OVL_ERR_MEMBERSHIP, e.what());
+        }
+        upload_masks(c, std::vector<uint64_t>(masks, masks + c->n));
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_read_membership(ovl_ctx *c, uint64_t *masks) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->has_scene || !masks) return fail(c, OVL_ERR_ARG, "no scene or null output");
+        std::vector<uint64_t> m = download_masks(c);
+        std::copy(m.begin(), m.end(), masks);
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_assign_overlap(ovl_ctx *c) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->has_scene) return fail(c, OVL_ERR_ARG, "no scene");
+        std::vector<uint64_t> m = download_masks(c);
+        try {
+            validate_masks(c, m.data());
+        } catch (const std::invalid_argument &e) {
+            return fail(c, OVL_ERR_MEMBERSHIP, e.what());
+        }
+        host_assign_overlap(c->hs, m);
+        upload_masks(c, m);
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_set_state(ovl_ctx *c, const float *state13, int32_t on_device) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->has_scene || !state13) return fail(c, OVL_ERR_ARG, "no scene or null state");
+        const float *src = state13;
+        if (!on_device) {
+            upload(c->stage13, state13, 13 * (size_t)c->n, c->stream);
+            src = c->stage13.p;
+        }
+        launch_pack_state(src, c->radius.p, c->im.p, c->n, c->st.p, c->stream);
+        if (!on_device) CK(cudaStreamSynchronize(c->stream));   // the host array may be reused
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_read_state(ovl_ctx *c, float *state13, int32_t on_device) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->has_scene || !state13) return fail(c, OVL_ERR_ARG, "no scene or null output");
+        if (on_device) {
+            launch_unpack_state(c->st.p, c->n, state13, c->stream);
+            return OVL_OK;
+        }
+        c->stage13.ensure(13 * (size_t)c->n);
+        launch_unpack_state(c->st.p, c->n, c->stage13.p, c->stream);
+        download(state13, c->stage13.p, 13 * (size_t)c->n, c->stream);
+        CK(cudaStreamSynchronize(c->stream));
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_set_step_index(ovl_ctx *c, int64_t k) {
+    if (!c) return OVL_ERR_ARG;
+    if (k < 0) return fail(c, OVL_ERR_ARG, "step index must be >= 0");
+    c->step_index = k;
+    return OVL_OK;
+}
+
+ovl_status ovl_set_warmstart(ovl_ctx *c, int64_t n, const int32_t *part, const uint64_t *key,
+                             const float *lambda3) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->has_scene || n < 0 || (n > 0 && (!part || !key || !lambda3)))
+            return fail(c, OVL_ERR_ARG, "warm start: bad arguments");
+        std::vector<int64_t> order(n);
+        std::iota(order.begin(), order.end(), 0);
+        for (int64_t i = 0; i < n; ++i)
+            if (part[i] < 0 || part[i] >= c->n_parts) return fail(c, OVL_ERR_ARG, "warm start: worker out of range");
+        std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+            return part[x] != part[y] ? part[x] < part[y] : key[x] < key[y];
+        });
+        std::vector<int> pstart(c->n_parts + 1, 0);
+        std::vector<uint64_t> k(n);
+        std::vector<float4> l(n);
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t o = order[i];
+            pstart[part[o] + 1]++;
+            k[i] = key[o];
+            l[i] = make_float4(lambda3[3 * o], lambda3[3 * o + 1], lambda3[3 * o + 2], 0.f);
+        }
+        for (int p = 0; p < c->n_parts; ++p) pstart[p + 1] += pstart[p];
+        upload(c->ws_pstart, pstart.data(), pstart.size(), c->stream);
+        upload(c->ws_key, k.data(), (size_t)n, c->stream);
+        upload(c->ws_lam, l.data(), (size_t)n, c->stream);
+        CK(cudaStreamSynchronize(c->stream));
+        c->ws_n = n;
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_read_warmstart(ovl_ctx *c, int64_t cap, int64_t *n, int32_t *part, uint64_t *key,
+                              float *lambda3) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->has_scene || !n) return fail(c, OVL_ERR_ARG, "no scene or null count");
+        *n = c->ws_n;
+        if (cap <= 0) return OVL_OK;
+        int64_t m = std::min(cap, c->ws_n);
+        std::vector<int> pstart(c->n_parts + 1);
+        std::vector<float4> l(m);
+        download(pstart.data(), c->ws_pstart.p, pstart.size(), c->stream);
+        if (key) download(key, c->ws_key.p, (size_t)m, c->stream);
+        download(l.data(), c->ws_lam.p, (size_t)m, c->stream);
+        CK(cudaStreamSynchronize(c->stream));
+        for (int p = 0; p < c->n_parts; ++p)
+            for (int64_t i = pstart[p]; i < pstart[p + 1] && i < m; ++i)
+                if (part) part[i] = p;
+        if (lambda3)
+            for (int64_t i = 0; i < m; ++i) {
+                lambda3[3 * i] = l[i].x; lambda3[3 * i + 1] = l[i].y; lambda3[3 * i + 2] = l[i].z;
+            }
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_step(ovl_ctx *c, float dt, int32_t iters) {
+    return guarded(c, [&]() -> ovl_status { return run_step(c, dt, iters); });
+}
+
+ovl_status ovl_load_balance(ovl_ctx *c, int32_t flags) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->has_scene) return fail(c, OVL_ERR_ARG, "no scene");
+        phase_contacts(c);
+        phase_graph(c);
+        phase_load_balance(c, (flags & 1) != 0, (flags & 2) != 0);
+        return check_device_status(c);
+    });
+}
+
+ovl_status ovl_sync(ovl_ctx *c) {
+    return guarded(c, [&]() -> ovl_status {
+        CK(cudaStreamSynchronize(c->stream));
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_read_stats(ovl_ctx *c, ovl_stats *out) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!out) return fail(c, OVL_ERR_ARG, "null output");
+        std::memset(out, 0, sizeof(*out));
+        out->n_workers = c->n_parts;
+        if (!c->have_step) return OVL_OK;
+        out->n_contacts = c->nc;
+        out->n_adjacency = c->nadj;
+        out->n_entries = c->ne;
+        out->n_pairs = c->npairs;
+        out->n_rows = 3ll * c->npairs;
+        std::vector<int> ep(c->n + 1), ncol(c->n_parts), its(c->n_parts);
+        std::vector<double> rs(c->n_parts);
+        download(ep.data(), c->entry_ptr.p, ep.size(), c->stream);
+        download(ncol.data(), c->part_ncol.p, ncol.size(), c->stream);
+        download(its.data(), c->part_iters.p, its.size(), c->stream);
+        download(rs.data(), c->part_res_sq.p, rs.size(), c->stream);
+        int dstat = 0;
+        download(&dstat, c->status.p, 1, c->stream);
+        CK(cudaStreamSynchronize(c->stream));
+        for (int b = 0; b < c->n; ++b) out->n_overlap += (ep[b + 1] - ep[b]) >= 2;
+        double sq = 0;
+        for (int p = 0; p < c->n_parts; ++p) {
+            out->max_colours = std::max(out->max_colours, ncol[p]);
+            out->max_iters = std::max(out->max_iters, its[p]);
+            sq += rs[p];
+        }
+        out->residual_rms = c->npairs > 0 ? std::sqrt(sq / (3.0 * c->npairs)) : 0.0;
+        out->device_status = dstat;
+        for (int i = 0; i < 10; ++i) out->phase_ms[i] = c->phase_ms[i];
+        out->n_launches = c->last_launches;
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_read_contacts(ovl_ctx *c, int32_t *ab, float *phi, float *normal, float *t1) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->have_step) return fail(c, OVL_ERR_ARG, "no step has run");
+        std::vector<int2> h_ab(c->nc);
+        std::vector<float4> h_n(c->nc), h_t(c->nc);
+        download(h_ab.data(), c->c_ab.p, c->nc, c->stream);
+        download(h_n.data(), c->c_n.p, c->nc, c->stream);
+        download(h_t.data(), c->c_t1.p, c->nc, c->stream);
+        CK(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < c->nc; ++i) {
+            if (ab) { ab[2 * i] = h_ab[i].x; ab[2 * i + 1] = h_ab[i].y; }
+            if (phi) phi[i] = h_n[i].w;
+            if (normal) { normal[3 * i] = h_n[i].x; normal[3 * i + 1] = h_n[i].y; normal[3 * i + 2] = h_n[i].z; }
+            if (t1) { t1[3 * i] = h_t[i].x; t1[3 * i + 1] = h_t[i].y; t1[3 * i + 2] = h_t[i].z; }
+        }
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_read_graph(ovl_ctx *c, int32_t *row_ptr, int32_t *col) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->have_step) return fail(c, OVL_ERR_ARG, "no step has run");
+        if (row_ptr) download(row_ptr, c->row_ptr.p, (size_t)c->n + 1, c->stream);
+        if (col) download(col, c->col.p, (size_t)c->nadj, c->stream);
+        CK(cudaStreamSynchronize(c->stream));
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_read_entries(ovl_ctx *c, int32_t *entry_ptr, int32_t *part, uint8_t *D, float *weight,
+                            float *copies13) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->have_step) return fail(c, OVL_ERR_ARG, "no step has run");
+        if (entry_ptr) download(entry_ptr, c->entry_ptr.p, (size_t)c->n + 1, c->stream);
+        if (part) download(part, c->entry_part.p, (size_t)c->ne, c->stream);
+        if (D) download(D, c->D.p, (size_t)c->ne, c->stream);
+        if (weight) download(weight, c->weight.p, (size_t)c->ne, c->stream);
+        std::vector<float4> cp;
+        if (copies13) {
+            cp.resize(4 * (size_t)c->ne);
+            download(cp.data(), c->copies.p, cp.size(), c->stream);
+        }
+        CK(cudaStreamSynchronize(c->stream));
+        if (copies13)
+            for (int e = 0; e < c->ne; ++e) {
+                float *o = copies13 + 13 * (size_t)e;
+                const float4 x = cp[4 * e], q = cp[4 * e + 1], v = cp[4 * e + 2], w = cp[4 * e + 3];
+                o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = q.x; o[4] = q.y; o[5] = q.z; o[6] = q.w;
+                o[7] = v.x; o[8] = v.y; o[9] = v.z; o[10] = w.x; o[11] = w.y; o[12] = w.z;
+            }
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_read_pairs(ovl_ctx *c, int32_t *part, uint64_t *key, int32_t *colour, float *lambda3) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->have_step) return fail(c, OVL_ERR_ARG, "no step has run");
+        // after the step the pair keys and impulses are the warm-start cache
+        if (part) download(part, c->ps_part.p, (size_t)c->npairs, c->stream);
+        if (key) download(key, c->ws_key.p, (size_t)c->npairs, c->stream);
+        if (colour) download(colour, c->p_colour.p, (size_t)c->npairs, c->stream);
+        std::vector<float4> l;
+        if (lambda3) {
+            l.resize(c->npairs);
+            download(l.data(), c->ws_lam.p, (size_t)c->npairs, c->stream);
+        }
+        CK(cudaStreamSynchronize(c->stream));
+        if (lambda3)
+            for (int i = 0; i < c->npairs; ++i) {
+                lambda3[3 * i] = l[i].x; lambda3[3 * i + 1] = l[i].y; lambda3[3 * i + 2] = l[i].z;
+            }
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_read_worker_stats(ovl_ctx *c, int32_t *iters, double *res_sq, int64_t *rows,
+                                 int32_t *colours) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->have_step) return fail(c, OVL_ERR_ARG, "no step has run");
+        std::vector<int> ps(c->n_parts + 1);
+        if (iters) download(iters, c->part_iters.p, (size_t)c->n_parts, c->stream);
+        if (res_sq) download(res_sq, c->part_res_sq.p, (size_t)c->n_parts, c->stream);
+        if (colours) download(colours, c->part_ncol.p, (size_t)c->n_parts, c->stream);
+        download(ps.data(), c->ws_pstart.p, ps.size(), c->stream);
+        CK(cudaStreamSynchronize(c->stream));
+        if (rows)
+            for (int p = 0; p < c->n_parts; ++p) rows[p] = 3ll * (ps[p + 1] - ps[p]);
+        return OVL_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,196 @@
+// host_alg.cpp -- the sequential, greedy membership algorithms of the method,
+// run on the host CPU: ASSIGNTOOVERLAPSET / GROWOVERLAP (Algorithms 2-3,
+// Section 5.1) at setup and LOADBALANCE / BRIDGE (Algorithms 6-7, Section 5.4)
+// once per step.  Their results depend on the order of the contacts and on
+// live worker loads, so they are run exactly in the paper's sequence.
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ovl {
+
+namespace {
+
+inline int popcount(uint64_t x) { return __builtin_popcountll(x); }
+
+// Live |P_w| per global worker plus the activate / deactivate primitives of
+// Table 1.
+class Membership {
+  public:
+    Membership(const HostScene &sc, std::vector<uint64_t> &mask) : sc_(sc), mask_(mask) {
+        load_.assign(sc.n_parts, 0);
+        for (int b = 0; b < sc.n; ++b) {
+            uint64_t m = mask[b];
+            int base = sc.part_base[sc.sob[b]];
+            while (m) {
+                int w = __builtin_ctzll(m);
+                m &= m - 1;
+                ++load_[base + w];
+            }
+        }
+    }
+    uint64_t W(int b) const { return mask_[b]; }
+    void activate(uint64_t workers, int b) {
+        uint64_t add = workers & ~mask_[b];
+        int base = sc_.part_base[sc_.sob[b]];
+        for (uint64_t m = add; m; m &= m - 1) ++load_[base + __builtin_ctzll(m)];
+        mask_[b] |= add;
+    }
+    void deactivate(uint64_t workers, int b) {
+        uint64_t rem = workers & mask_[b];
+        int base = sc_.part_base[sc_.sob[b]];
+        for (uint64_t m = rem; m; m &= m - 1) --load_[base + __builtin_ctzll(m)];
+        mask_[b] &= ~rem;
+    }
+    // <W>: active bodies summed over the workers of W (Table 1)
+    int64_t load(uint64_t workers, int scene) const {
+        int64_t s = 0;
+        int base = sc_.part_base[scene];
+        for (uint64_t m = workers; m; m &= m - 1) s += load_[base + __builtin_ctzll(m)];
+        return s;
+    }
+    // worker of W with the fewest active bodies, lowest index on ties
+    int least_loaded(uint64_t workers, int scene) const {
+        int base = sc_.part_base[scene];
+        int best = -1;
+        int64_t best_load = 0;
+        for (uint64_t m = workers; m; m &= m - 1) {
+            int w = __builtin_ctzll(m);
+            if (best < 0 || load_[base + w] < best_load) {
+                best = w;
+                best_load = load_[base + w];
+            }
+        }
+        return best;
+    }
+
+  private:
+    const HostScene &sc_;
+    std::vector<uint64_t> &mask_;
+    std::vector<int64_t> load_;
+};
+
+// vertices within `depth` hops of root (root first), over a CSR graph
+class Ball {
+  public:
+    explicit Ball(int n) : seen_(n, 0), depth_(n, 0) {}
+    const std::vector<int> &collect(const int *row_ptr, const int *col, int root, int depth) {
+        ++epoch_;
+        out_.clear();
+        out_.push_back(root);
+        seen_[root] = epoch_;
+        depth_[root] = 0;
+        for (size_t head = 0; head < out_.size(); ++head) {
+            int u = out_[head];
+            if (depth_[u] == depth) continue;
+            for (int k = row_ptr[u]; k < row_ptr[u + 1]; ++k) {
+                int v = col[k];
+                if (seen_[v] == epoch_) continue;
+                seen_[v] = epoch_;
+                depth_[v] = depth_[u] + 1;
+                out_.push_back(v);
+            }
+        }
+        return out_;
+    }
+
+  private:
+    std::vector<int> seen_, depth_, out_;
+    int epoch_ = 0;
+};
+
+}  // namespace
+
+// Algorithms 2 and 3 over the joints in index order.  The constraint graph
+// here is the articulated structure: joints between two dynamic bodies.
+void host_assign_overlap(const HostScene &sc, std::vector<uint64_t> &mask) {
+    const int n = sc.n;
+    const int nj = (int)sc.jab.size() / 2;
+    auto dyn = [&](int b) { return b >= 0 && b < n && sc.inv_mass[b] > 0.0f; };
+    std::vector<int> deg(n + 1, 0);
+    for (int j = 0; j < nj; ++j) {
+        int a = sc.jab[2 * j], b = sc.jab[2 * j + 1];
+        if (dyn(a) && dyn(b) && a != b) { ++deg[a]; ++deg[b]; }
+    }
+    std::vector<int> row_ptr(n + 1, 0);
+    for (int i = 0; i < n; ++i) row_ptr[i + 1] = row_ptr[i] + deg[i];
+    std::vector<int> col(row_ptr[n]);
+    std::vector<int> fill(row_ptr.begin(), row_ptr.end() - 1);
+    for (int j = 0; j < nj; ++j) {
+        int a = sc.jab[2 * j], b = sc.jab[2 * j + 1];
+        if (dyn(a) && dyn(b) && a != b) { col[fill[a]++] = b; col[fill[b]++] = a; }
+    }
+    // sorted, duplicate-free neighbour lists (the BFS result is a set anyway)
+    for (int i = 0; i < n; ++i) {
+        auto first = col.begin() + row_ptr[i], last = col.begin() + row_ptr[i + 1];
+        std::sort(first, last);
+    }
+    Membership mem(sc, mask);
+    Ball ball(n);
+    auto grow = [&](int root, int gamma, uint64_t Wr) {      // Algorithm 3
+        const std::vector<int> &N = ball.collect(row_ptr.data(), col.data(), root, gamma);
+        for (int b : N)
+            if (popcount(mem.W(b)) < 2) mem.activate(Wr & ~mem.W(b), b);
+    };
+    for (int j = 0; j < nj; ++j) {
+        int A = sc.jab[2 * j], B = sc.jab[2 * j + 1];
+        if (!dyn(A) || !dyn(B) || A == B) continue;
+        uint64_t WA = mem.W(A), WB = mem.W(B);
+        if (popcount(WA) != 1 || popcount(WB) != 1 || WA == WB) continue;   // line 4
+        int gamma = sc.scene_gamma[sc.sob[A]];
+        mem.activate(mem.W(B), A);                                          // line 5
+        grow(A, gamma, mem.W(A) | mem.W(B));                                // line 6
+        mem.activate(mem.W(A), B);                                          // line 7
+        grow(B, gamma, mem.W(A) | mem.W(B));                                // line 8
+    }
+}
+
+// Algorithm 6 over contacts between dynamic bodies, in canonical order.
+void host_load_balance(const HostScene &sc, std::vector<uint64_t> &mask, int64_t nc, const int *ca,
+                       const int *cb, const int *row_ptr, const int *col, bool do_activate,
+                       bool do_deactivate) {
+    if (nc == 0 || (!do_activate && !do_deactivate)) return;
+    Membership mem(sc, mask);
+    Ball ball(sc.n);
+    auto bridge = [&](int b) {                                  // Algorithm 7
+        uint64_t u = 0;
+        for (int k = row_ptr[b]; k < row_ptr[b + 1]; ++k) u |= mem.W(col[k]);
+        return popcount(u) > 1;
+    };
+    for (int64_t i = 0; i < nc; ++i) {
+        const int A = ca[i], B = cb[i];
+        const uint64_t WA = mem.W(A), WB = mem.W(B);
+        const int scene = sc.sob[A];
+        if ((WA & WB) == 0) {                                   // line 4
+            if (!do_activate) continue;
+            int root;
+            if (mem.load(WA, scene) <= mem.load(WB, scene)) {   // line 5
+                mem.activate(WA, B);
+                root = B;
+            } else {
+                mem.activate(WB, A);
+                root = A;
+            }
+            const std::vector<int> &N =
+                ball.collect(row_ptr, col, root, sc.scene_gamma[scene]);   // line 12
+            for (int v : N) mem.activate((WA | WB) & ~mem.W(v), v);         // line 14
+            continue;
+        }
+        if (!do_deactivate) continue;
+        const int pa = popcount(WA), pb = popcount(WB);
+        if (pa > 1 && pb == 1 && !bridge(A)) {
+            mem.deactivate(WA & ~WB, A);                        // line 17
+        } else if (pb > 1 && pa == 1 && !bridge(B)) {
+            mem.deactivate(WB & ~WA, B);                        // line 19
+        } else if (WA == WB) {
+            uint64_t keep = uint64_t(1) << mem.least_loaded(WA, scene);   // line 21
+            mem.deactivate(WA & ~keep, A);
+            mem.deactivate(WB & ~keep, B);
+        }
+    }
+}
+
+}  // namespace ovl

@@ -1,0 +1,320 @@
+// k_contacts.cu -- contacts of the blended state (Algorithm 1 line 10,
+// "getContacts", Section 5.4) and the constraint graph G^t (line 11,
+// Section 5.1).
+//
+// Broadphase: spatial hash grid, one thread per body (cell size >= the
+// largest contact distance, so touching spheres sit in neighbouring cells).
+// Narrowphase: sphere-sphere (a < b) and sphere-plane.  The contact test and
+// the choice of tangent axis decide integers, so they are evaluated in FP32
+// with explicit round-to-nearest operations in a fixed order (no fused
+// multiply-add):  d2 = (dx*dx + dy*dy) + dz*dz <= (ra + rb + margin)^2 and
+// ((nx*px + ny*py) + nz*pz - d) - r <= margin.
+//
+// Output order is canonical (ascending (a, b), planes numbered after the
+// bodies) without a global sort: a per-body count + scan gives each body a
+// slot range, and each body sorts its own (few) partners.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ovl {
+
+namespace {
+
+__device__ __forceinline__ uint32_t cell_hash(int ix, int iy, int iz, int scene, uint32_t mask) {
+    uint32_t h = ((uint32_t)ix * 73856093u) ^ ((uint32_t)iy * 19349663u) ^
+                 ((uint32_t)iz * 83492791u) ^ ((uint32_t)scene * 2654435761u);
+    return h & mask;
+}
+
+__global__ void k_cells(const float4 *__restrict__ st, int n, const int *__restrict__ sob,
+                        float inv_cs, uint32_t tmask, int4 *__restrict__ cell,
+                        int *__restrict__ bucket_count) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
+        float4 p = st[4 * b];
+        int ix = (int)floorf(p.x * inv_cs), iy = (int)floorf(p.y * inv_cs),
+            iz = (int)floorf(p.z * inv_cs);
+        uint32_t h = cell_hash(ix, iy, iz, sob[b], tmask);
+        cell[b] = make_int4(ix, iy, iz, (int)h);
+        atomicAdd(&bucket_count[h], 1);
+    }
+}
+
+__global__ void k_bucket_fill(const int4 *__restrict__ cell, int n, const int *__restrict__ bstart,
+                              int *__restrict__ cursor, int *__restrict__ items) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
+        int h = cell[b].w;
+        int slot = atomicAdd(&cursor[h], 1);
+        items[bstart[h] + slot] = b;
+    }
+}
+
+// FP32 sphere-pair test, explicit rounding order
+__device__ __forceinline__ bool pair_touches(float4 pa, float4 pb, float margin) {
+    float dx = __fsub_rn(pb.x, pa.x), dy = __fsub_rn(pb.y, pa.y), dz = __fsub_rn(pb.z, pa.z);
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    float rs = __fadd_rn(__fadd_rn(pa.w, pb.w), margin);
+    return d2 <= __fmul_rn(rs, rs);
+}
+
+__device__ __forceinline__ float plane_gap(float4 p, float4 pl) {
+    float dotp = __fadd_rn(__fadd_rn(__fmul_rn(pl.x, p.x), __fmul_rn(pl.y, p.y)), __fmul_rn(pl.z, p.z));
+    return __fsub_rn(__fsub_rn(dotp, pl.w), p.w);
+}
+
+// neighbours b > a of body a (sorted ascending) + its plane contacts
+__global__ void k_find_pairs(const float4 *__restrict__ st, const float *__restrict__ im, int n,
+                             const int *__restrict__ sob, const int *__restrict__ scene_flags,
+                             const int4 *__restrict__ cell, const int *__restrict__ bstart,
+                             const int *__restrict__ items, uint32_t tmask,
+                             const float4 *__restrict__ planes, const int *__restrict__ plane_ptr,
+                             const int *__restrict__ plane_list, float margin,
+                             int *__restrict__ nb_list, int *__restrict__ nb_count,
+                             int *__restrict__ contact_count, int *__restrict__ status) {
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        const int s = sob[a];
+        const float4 pa = st[4 * a];   // .w = radius
+        const bool dyn_a = im[a] > 0.0f;
+        int cnt = 0;
+        int local[OVL_MAX_NEIGH];
+        bool overflow = false;
+        if (scene_flags[s] & 1) {
+            const int4 ca = cell[a];
+            for (int dx = -1; dx <= 1; ++dx)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        const int cx = ca.x + dx, cy = ca.y + dy, cz = ca.z + dz;
+                        const uint32_t h = cell_hash(cx, cy, cz, s, tmask);
+                        for (int k = bstart[h]; k < bstart[h + 1]; ++k) {
+                            const int b = items[k];
+                            if (b <= a) continue;
+                            const int4 cb = cell[b];
+                            if (cb.x != cx || cb.y != cy || cb.z != cz || sob[b] != s) continue;
+                            if (!dyn_a && !(im[b] > 0.0f)) continue;
+                            if (!pair_touches(pa, st[4 * b], margin)) continue;
+                            if (cnt < OVL_MAX_NEIGH) {
+                                // insertion into the sorted local list
+                                int j = cnt;
+                                while (j > 0 && local[j - 1] > b) {
+                                    local[j] = local[j - 1];
+                                    --j;
+                                }
+                                local[j] = b;
+                                ++cnt;
+                            } else {
+                                overflow = true;
+                            }
+                        }
+                    }
+        }
+        if (overflow) atomicCAS(status, DEV_OK, DEV_ERR_CAPACITY);
+        for (int j = 0; j < cnt; ++j) nb_list[(size_t)a * OVL_MAX_NEIGH + j] = local[j];
+        nb_count[a] = cnt;
+        int np_ = 0;
+        if (dyn_a) {
+            for (int k = plane_ptr[s]; k < plane_ptr[s + 1]; ++k) {
+                const float4 pl = planes[plane_list[k]];
+                if (plane_gap(pa, pl) <= margin) ++np_;
+            }
+        }
+        contact_count[a] = cnt + np_;
+    }
+}
+
+// tangent axis: smallest |n_k| of the FP32 normal, ties to the lower index
+__device__ __forceinline__ int tangent_axis(float nx, float ny, float nz) {
+    float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
+    int k = 0;
+    float m = ax;
+    if (ay < m) { k = 1; m = ay; }
+    if (az < m) { k = 2; }
+    return k;
+}
+
+__device__ __forceinline__ float3 tangent_from(float3 n, int k) {
+    float nk = k == 0 ? n.x : (k == 1 ? n.y : n.z);
+    float3 t = make_float3(-nk * n.x, -nk * n.y, -nk * n.z);
+    if (k == 0) t.x += 1.0f; else if (k == 1) t.y += 1.0f; else t.z += 1.0f;
+    float inv = rsqrtf(t.x * t.x + t.y * t.y + t.z * t.z);
+    return make_float3(t.x * inv, t.y * inv, t.z * inv);
+}
+
+__global__ void k_write_contacts(const float4 *__restrict__ st, const float *__restrict__ im, int n,
+                                 const int *__restrict__ sob, const float4 *__restrict__ planes,
+                                 const int *__restrict__ plane_ptr, const int *__restrict__ plane_list,
+                                 float margin, const int *__restrict__ nb_list,
+                                 const int *__restrict__ nb_count, const int *__restrict__ cstart,
+                                 int2 *__restrict__ c_ab, float4 *__restrict__ c_n,
+                                 float4 *__restrict__ c_t1) {
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        const float4 pa = st[4 * a];
+        int o = cstart[a];
+        const int cnt = nb_count[a];
+        for (int j = 0; j < cnt; ++j) {
+            const int b = nb_list[(size_t)a * OVL_MAX_NEIGH + j];
+            const float4 pb = st[4 * b];
+            float dx = __fsub_rn(pb.x, pa.x), dy = __fsub_rn(pb.y, pa.y), dz = __fsub_rn(pb.z, pa.z);
+            float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            float L = __fsqrt_rn(d2);
+            float3 nn;
+            int k;
+            if (L == 0.0f) {
+                nn = make_float3(0.f, 0.f, 1.f);
+                k = 0;
+            } else {
+                nn = make_float3(__fdiv_rn(dx, L), __fdiv_rn(dy, L), __fdiv_rn(dz, L));
+                k = tangent_axis(nn.x, nn.y, nn.z);
+            }
+            float3 t = tangent_from(nn, k);
+            float phi = L - pa.w - pb.w;
+            c_ab[o] = make_int2(a, b);
+            c_n[o] = make_float4(nn.x, nn.y, nn.z, phi);
+            c_t1[o] = make_float4(t.x, t.y, t.z, 0.f);
+            ++o;
+        }
+        if (im[a] > 0.0f) {
+            const int s = sob[a];
+            for (int k2 = plane_ptr[s]; k2 < plane_ptr[s + 1]; ++k2) {
+                const int pidx = plane_list[k2];
+                const float4 pl = planes[pidx];
+                if (plane_gap(pa, pl) > margin) continue;   // the FP32 decision
+                // the gap itself from large coordinates: FP64, then rounded once
+                const float gap = (float)((double)pl.x * pa.x + (double)pl.y * pa.y +
+                                          (double)pl.z * pa.z - (double)pl.w - (double)pa.w);
+                // normal from the sphere towards the plane
+                float3 nn = make_float3(-pl.x, -pl.y, -pl.z);
+                int k = tangent_axis(nn.x, nn.y, nn.z);
+                float3 t = tangent_from(nn, k);
+                c_ab[o] = make_int2(a, n + pidx);
+                c_n[o] = make_float4(nn.x, nn.y, nn.z, gap);
+                c_t1[o] = make_float4(t.x, t.y, t.z, 0.f);
+                ++o;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// G^t: undirected edges between two dynamic bodies from contacts and joints
+// ---------------------------------------------------------------------------
+__global__ void k_edge_degree(const int2 *__restrict__ c_ab, int nc, const int2 *__restrict__ jab,
+                              int nj, const float *__restrict__ im, int n, int *__restrict__ deg) {
+    int total = nc + nj;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        int2 e = i < nc ? c_ab[i] : jab[i - nc];
+        if (e.x < 0 || e.y < 0 || e.x >= n || e.y >= n || e.x == e.y) continue;
+        if (!(im[e.x] > 0.0f) || !(im[e.y] > 0.0f)) continue;
+        atomicAdd(&deg[e.x], 1);
+        atomicAdd(&deg[e.y], 1);
+    }
+}
+
+__global__ void k_edge_fill(const int2 *__restrict__ c_ab, int nc, const int2 *__restrict__ jab,
+                            int nj, const float *__restrict__ im, int n,
+                            const int *__restrict__ tptr, int *__restrict__ cursor,
+                            int *__restrict__ tcol) {
+    int total = nc + nj;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        int2 e = i < nc ? c_ab[i] : jab[i - nc];
+        if (e.x < 0 || e.y < 0 || e.x >= n || e.y >= n || e.x == e.y) continue;
+        if (!(im[e.x] > 0.0f) || !(im[e.y] > 0.0f)) continue;
+        tcol[tptr[e.x] + atomicAdd(&cursor[e.x], 1)] = e.y;
+        tcol[tptr[e.y] + atomicAdd(&cursor[e.y], 1)] = e.x;
+    }
+}
+
+// sort each vertex's neighbours and drop duplicates in place
+__global__ void k_adj_unique(const int *__restrict__ tptr, int n, int *__restrict__ tcol,
+                             int *__restrict__ ucount) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int b = tptr[v], e = tptr[v + 1];
+        for (int i = b + 1; i < e; ++i) {
+            int x = tcol[i];
+            int j = i;
+            while (j > b && tcol[j - 1] > x) {
+                tcol[j] = tcol[j - 1];
+                --j;
+            }
+            tcol[j] = x;
+        }
+        int m = 0;
+        for (int i = b; i < e; ++i)
+            if (i == b || tcol[i] != tcol[i - 1]) tcol[b + m++] = tcol[i];
+        ucount[v] = m;
+    }
+}
+
+__global__ void k_adj_compact(const int *__restrict__ tptr, const int *__restrict__ tcol, int n,
+                              const int *__restrict__ row_ptr, int *__restrict__ col) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int m = row_ptr[v + 1] - row_ptr[v];
+        for (int k = 0; k < m; ++k) col[row_ptr[v] + k] = tcol[tptr[v] + k];
+    }
+}
+
+}  // namespace
+
+int grid1d(size_t n, int threads) {
+    size_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+void launch_cells(const ContactArgs &a, cudaStream_t s) {
+    k_cells<<<grid1d(a.n, 256), 256, 0, s>>>(a.st, a.n, a.sob, a.inv_cs, a.tmask, a.cell,
+                                             a.bucket_count);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_bucket_fill(const ContactArgs &a, cudaStream_t s) {
+    k_bucket_fill<<<grid1d(a.n, 256), 256, 0, s>>>(a.cell, a.n, a.bucket_start, a.cursor, a.items);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_find_pairs(const ContactArgs &a, cudaStream_t s) {
+    k_find_pairs<<<grid1d(a.n, 128), 128, 0, s>>>(
+        a.st, a.im, a.n, a.sob, a.scene_flags, a.cell, a.bucket_start, a.items, a.tmask, a.planes,
+        a.plane_ptr, a.plane_list, a.margin, a.nb_list, a.nb_count, a.contact_count, a.status);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_write_contacts(const ContactArgs &a, cudaStream_t s) {
+    k_write_contacts<<<grid1d(a.n, 128), 128, 0, s>>>(a.st, a.im, a.n, a.sob, a.planes, a.plane_ptr,
+                                                      a.plane_list, a.margin, a.nb_list,
+                                                      a.nb_count, a.contact_start, a.c_ab, a.c_n,
+                                                      a.c_t1);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_edge_degree(const int2 *c_ab, int nc, const int2 *jab, int nj, const float *im, int n,
+                        int *deg, cudaStream_t s) {
+    k_edge_degree<<<grid1d(nc + nj, 256), 256, 0, s>>>(c_ab, nc, jab, nj, im, n, deg);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_edge_fill(const int2 *c_ab, int nc, const int2 *jab, int nj, const float *im, int n,
+                      const int *tptr, int *cursor, int *tcol, cudaStream_t s) {
+    k_edge_fill<<<grid1d(nc + nj, 256), 256, 0, s>>>(c_ab, nc, jab, nj, im, n, tptr, cursor, tcol);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_adj_unique(const int *tptr, int n, int *tcol, int *ucount, cudaStream_t s) {
+    k_adj_unique<<<grid1d(n, 128), 128, 0, s>>>(tptr, n, tcol, ucount);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_adj_compact(const int *tptr, const int *tcol, int n, const int *row_ptr, int *col,
+                        cudaStream_t s) {
+    k_adj_compact<<<grid1d(n, 128), 128, 0, s>>>(tptr, tcol, n, row_ptr, col);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+}  // namespace ovl

@@ -1,0 +1,404 @@
+"""Thin ctypes binding of libovl (the C ABI declared in ``include/ovl.h``).
+
+Functions keep the C names (``ovl_create``, ``ovl_step``, ...) and only
+marshal arguments; every step of the method runs in the library's CUDA
+kernels (and its host-side membership code).  ``Simulation`` bundles a
+context with numpy/torch conveniences.
+
+There is no fallback: if the library is missing or cannot be loaded,
+``load_library`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libovl.so")
+
+OVL_OK = 0
+OVL_ERR_ARG = -1
+OVL_ERR_CUDA = -2
+OVL_ERR_CAPACITY = -3
+OVL_ERR_TIMEOUT = -4
+OVL_ERR_NONFINITE = -5
+OVL_ERR_MEMBERSHIP = -6
+OVL_FLAG_RESIDUAL = 1
+OVL_FLAG_TIMING = 2
+
+EXPORTED = [
+    "ovl_default_params", "ovl_create", "ovl_destroy", "ovl_last_error", "ovl_phase_name",
+    "ovl_scene_upload", "ovl_set_partition", "ovl_set_membership", "ovl_read_membership",
+    "ovl_assign_overlap", "ovl_set_state", "ovl_read_state", "ovl_set_step_index",
+    "ovl_set_warmstart", "ovl_read_warmstart", "ovl_step", "ovl_load_balance", "ovl_sync",
+    "ovl_read_stats", "ovl_read_contacts", "ovl_read_graph", "ovl_read_entries", "ovl_read_pairs",
+    "ovl_read_worker_stats",
+]
+
+
+class OvlError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libovl error {code}: {msg}")
+        self.code = code
+
+
+class ovl_params(C.Structure):
+    _fields_ = [("gravity", C.c_float * 3), ("margin", C.c_float), ("erp", C.c_float),
+                ("slop", C.c_float), ("warmstart", C.c_float), ("lb_activate", C.c_int32),
+                ("lb_deact_every", C.c_int32), ("res_tol", C.c_float),
+                ("res_check_every", C.c_int32), ("pgs_threads", C.c_int32), ("flags", C.c_int32)]
+
+
+_fp, _ip, _u64p, _u8p = C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint8)
+
+
+class ovl_scene_desc(C.Structure):
+    _fields_ = [("n_bodies", C.c_int32), ("state", _fp), ("radius", _fp), ("inv_mass", _fp),
+                ("n_planes", C.c_int32), ("planes", _fp), ("plane_scene", _ip),
+                ("n_joints", C.c_int32), ("joint_bodies", _ip), ("joint_anchors", _fp),
+                ("n_scenes", C.c_int32), ("scene_of_body", _ip), ("scene_mu", _fp),
+                ("scene_dt", _fp), ("scene_flags", _ip), ("scene_gamma", _ip), ("scene_beta", _ip),
+                ("n_sets", _ip)]
+
+
+class ovl_stats(C.Structure):
+    _fields_ = [("n_contacts", C.c_int64), ("n_adjacency", C.c_int64), ("n_entries", C.c_int64),
+                ("n_pairs", C.c_int64), ("n_rows", C.c_int64), ("n_overlap", C.c_int64),
+                ("n_workers", C.c_int32), ("max_colours", C.c_int32), ("max_iters", C.c_int32),
+                ("device_status", C.c_int32), ("residual_rms", C.c_double),
+                ("residual_max", C.c_double), ("phase_ms", C.c_float * 12),
+                ("n_launches", C.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Loads libovl.so (built by ``build.py``); raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OvlError(OVL_ERR_CUDA, f"{p} is missing: build it with paper_2403_17261_gb300.build.build()")
+    L = C.CDLL(p)
+    vp = C.c_void_p
+    sig = {
+        "ovl_default_params": [C.POINTER(ovl_params)],
+        "ovl_create": [C.POINTER(vp), C.POINTER(ovl_params), vp],
+        "ovl_destroy": [vp],
+        "ovl_scene_upload": [vp, C.POINTER(ovl_scene_desc)],
+        "ovl_set_partition": [vp, _ip],
+        "ovl_set_membership": [vp, _u64p],
+        "ovl_read_membership": [vp, _u64p],
+        "ovl_assign_overlap": [vp],
+        "ovl_set_state": [vp, vp, C.c_int32],
+        "ovl_read_state": [vp, vp, C.c_int32],
+        "ovl_set_step_index": [vp, C.c_int64],
+        "ovl_set_warmstart": [vp, C.c_int64, _ip, _u64p, _fp],
+        "ovl_read_warmstart": [vp, C.c_int64, C.POINTER(C.c_int64), _ip, _u64p, _fp],
+        "ovl_step": [vp, C.c_float, C.c_int32],
+        "ovl_load_balance": [vp, C.c_int32],
+        "ovl_sync": [vp],
+        "ovl_read_stats": [vp, C.POINTER(ovl_stats)],
+        "ovl_read_contacts": [vp, _ip, _fp, _fp, _fp],
+        "ovl_read_graph": [vp, _ip, _ip],
+        "ovl_read_entries": [vp, _ip, _ip, _u8p, _fp, _fp],
+        "ovl_read_pairs": [vp, _ip, _u64p, _ip, _fp],
+        "ovl_read_worker_stats": [vp, _ip, C.POINTER(C.c_double), C.POINTER(C.c_int64), _ip],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int32
+    L.ovl_last_error.argtypes = [vp]
+    L.ovl_last_error.restype = C.c_char_p
+    L.ovl_phase_name.argtypes = [C.c_int32]
+    L.ovl_phase_name.restype = C.c_char_p
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(ctx, rc: int):
+    if rc != OVL_OK:
+        msg = load_library().ovl_last_error(ctx).decode() if ctx else "no context"
+        raise OvlError(rc, msg)
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+# ---------------------------------------------------------------------------
+# functions with the C names
+# ---------------------------------------------------------------------------
+
+def ovl_default_params(**overrides) -> ovl_params:
+    p = ovl_params()
+    load_library().ovl_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if k == "gravity":
+            for i in range(3):
+                p.gravity[i] = v[i]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def ovl_create(params: ovl_params | None = None, stream: int | None = None):
+    h = C.c_void_p()
+    rc = load_library().ovl_create(C.byref(h), C.byref(params) if params is not None else None,
+                                   C.c_void_p(stream) if stream else None)
+    if rc != OVL_OK:
+        raise OvlError(rc, "ovl_create failed (is a CUDA device available?)")
+    return h
+
+
+def ovl_destroy(ctx):
+    load_library().ovl_destroy(ctx)
+
+
+class _SceneArrays:
+    """Keeps the contiguous host arrays alive for the duration of the upload."""
+
+    def __init__(self, scene):
+        f32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+        i32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+        self.state = f32(scene.state).reshape(-1, 13)
+        self.radius, self.inv_mass = f32(scene.radius), f32(scene.inv_mass)
+        self.planes = f32(scene.planes).reshape(-1, 4)
+        self.plane_scene = i32(scene.plane_scene)
+        self.joints = i32(scene.joints).reshape(-1, 2)
+        self.anchors = f32(scene.anchors).reshape(-1, 6)
+        self.sob = i32(scene.scene_of_body)
+        self.mu, self.dt = f32(scene.scene_mu), f32(scene.scene_dt)
+        self.flags, self.gamma = i32(scene.scene_flags), i32(scene.scene_gamma)
+        self.beta, self.n_sets = i32(scene.scene_beta), i32(scene.n_sets)
+        d = ovl_scene_desc()
+        d.n_bodies = self.state.shape[0]
+        d.state, d.radius, d.inv_mass = _ptr(self.state, _fp), _ptr(self.radius, _fp), _ptr(self.inv_mass, _fp)
+        d.n_planes = self.planes.shape[0]
+        d.planes, d.plane_scene = _ptr(self.planes, _fp), _ptr(self.plane_scene, _ip)
+        d.n_joints = self.joints.shape[0]
+        d.joint_bodies, d.joint_anchors = _ptr(self.joints, _ip), _ptr(self.anchors, _fp)
+        d.n_scenes = self.mu.shape[0]
+        d.scene_of_body = _ptr(self.sob, _ip)
+        d.scene_mu, d.scene_dt = _ptr(self.mu, _fp), _ptr(self.dt, _fp)
+        d.scene_flags, d.scene_gamma = _ptr(self.flags, _ip), _ptr(self.gamma, _ip)
+        d.scene_beta, d.n_sets = _ptr(self.beta, _ip), _ptr(self.n_sets, _ip)
+        self.desc = d
+
+
+def ovl_scene_upload(ctx, scene):
+    arr = _SceneArrays(scene)
+    _check(ctx, load_library().ovl_scene_upload(ctx, C.byref(arr.desc)))
+
+
+def ovl_set_partition(ctx, set_of_body):
+    s = np.ascontiguousarray(np.asarray(set_of_body, dtype=np.int32))
+    _check(ctx, load_library().ovl_set_partition(ctx, _ptr(s, _ip)))
+
+
+def ovl_set_membership(ctx, masks):
+    m = np.ascontiguousarray(np.asarray(masks, dtype=np.uint64))
+    _check(ctx, load_library().ovl_set_membership(ctx, _ptr(m, _u64p)))
+
+
+def ovl_read_membership(ctx, n):
+    m = np.zeros(n, np.uint64)
+    _check(ctx, load_library().ovl_read_membership(ctx, _ptr(m, _u64p)))
+    return m
+
+
+def ovl_assign_overlap(ctx):
+    _check(ctx, load_library().ovl_assign_overlap(ctx))
+
+
+def ovl_set_state(ctx, state, on_device: bool = False):
+    if on_device:
+        _check(ctx, load_library().ovl_set_state(ctx, C.c_void_p(int(state)), 1))
+    else:
+        s = np.ascontiguousarray(np.asarray(state, dtype=np.float32))
+        _check(ctx, load_library().ovl_set_state(ctx, s.ctypes.data_as(C.c_void_p), 0))
+
+
+def ovl_read_state(ctx, out, on_device: bool = False):
+    if on_device:
+        _check(ctx, load_library().ovl_read_state(ctx, C.c_void_p(int(out)), 1))
+    else:
+        assert out.dtype == np.float32 and out.flags["C_CONTIGUOUS"]
+        _check(ctx, load_library().ovl_read_state(ctx, out.ctypes.data_as(C.c_void_p), 0))
+    return out
+
+
+def ovl_set_step_index(ctx, k: int):
+    _check(ctx, load_library().ovl_set_step_index(ctx, int(k)))
+
+
+def ovl_set_warmstart(ctx, part, key, lam):
+    part = np.ascontiguousarray(np.asarray(part, dtype=np.int32))
+    key = np.ascontiguousarray(np.asarray(key, dtype=np.uint64))
+    lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float32)).reshape(-1, 3)
+    _check(ctx, load_library().ovl_set_warmstart(ctx, part.shape[0], _ptr(part, _ip), _ptr(key, _u64p),
+                                                 _ptr(lam, _fp)))
+
+
+def ovl_read_warmstart(ctx):
+    n = C.c_int64()
+    L = load_library()
+    _check(ctx, L.ovl_read_warmstart(ctx, 0, C.byref(n), None, None, None))
+    m = n.value
+    part, key, lam = np.zeros(max(m, 1), np.int32), np.zeros(max(m, 1), np.uint64), np.zeros((max(m, 1), 3), np.float32)
+    _check(ctx, L.ovl_read_warmstart(ctx, m, C.byref(n), _ptr(part, _ip), _ptr(key, _u64p), _ptr(lam, _fp)))
+    return part[:m], key[:m], lam[:m]
+
+
+def ovl_step(ctx, dt: float, iters: int):
+    _check(ctx, load_library().ovl_step(ctx, float(dt), int(iters)))
+
+
+def ovl_load_balance(ctx, flags: int = 3):
+    _check(ctx, load_library().ovl_load_balance(ctx, int(flags)))
+
+
+def ovl_sync(ctx):
+    _check(ctx, load_library().ovl_sync(ctx))
+
+
+def ovl_read_stats(ctx) -> dict:
+    s = ovl_stats()
+    _check(ctx, load_library().ovl_read_stats(ctx, C.byref(s)))
+    out = {k: getattr(s, k) for k, _ in ovl_stats._fields_ if k != "phase_ms"}
+    L = load_library()
+    out["phase_ms"] = {L.ovl_phase_name(i).decode(): s.phase_ms[i] for i in range(10)}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Simulation:
+    """One libovl context holding one (possibly batched) scene."""
+
+    def __init__(self, scene, params: ovl_params | dict | None = None, stream: int | None = None,
+                 partition: bool = True):
+        if isinstance(params, dict) or params is None:
+            kw = dict(lb_activate=scene.lb_activate, lb_deact_every=scene.lb_deact_every)
+            kw.update(params or {})
+            params = ovl_default_params(**kw)
+        self.params = params
+        self.scene = scene
+        self.n = scene.n_bodies
+        self.n_parts = int(np.sum(scene.n_sets))
+        self.ctx = ovl_create(params, stream)
+        ovl_scene_upload(self.ctx, scene)
+        if partition:
+            ovl_set_partition(self.ctx, scene.set_of_body)
+            if scene.assign_overlap:
+                ovl_assign_overlap(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ovl_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # membership / state -------------------------------------------------------
+    def set_partition(self, sets):
+        ovl_set_partition(self.ctx, sets)
+
+    def set_membership(self, masks):
+        ovl_set_membership(self.ctx, masks)
+
+    def membership(self):
+        return ovl_read_membership(self.ctx, self.n)
+
+    def assign_overlap(self):
+        ovl_assign_overlap(self.ctx)
+
+    def set_state(self, state):
+        if hasattr(state, "data_ptr"):
+            ovl_set_state(self.ctx, state.data_ptr(), on_device=True)
+        else:
+            ovl_set_state(self.ctx, state)
+
+    def state(self, out=None):
+        if out is not None and hasattr(out, "data_ptr"):
+            ovl_read_state(self.ctx, out.data_ptr(), on_device=True)
+            return out
+        o = np.zeros((self.n, 13), np.float32) if out is None else out
+        return ovl_read_state(self.ctx, o)
+
+    def set_step_index(self, k):
+        ovl_set_step_index(self.ctx, k)
+
+    def set_warmstart(self, part, key, lam):
+        ovl_set_warmstart(self.ctx, part, key, lam)
+
+    def warmstart(self):
+        return ovl_read_warmstart(self.ctx)
+
+    # stepping -----------------------------------------------------------------
+    def step(self, dt: float = 0.0, iters: int | None = None):
+        ovl_step(self.ctx, dt, self.scene.iters if iters is None else iters)
+
+    def load_balance(self, flags: int = 3):
+        ovl_load_balance(self.ctx, flags)
+
+    def sync(self):
+        ovl_sync(self.ctx)
+
+    # records of the last step -------------------------------------------------
+    def stats(self) -> dict:
+        return ovl_read_stats(self.ctx)
+
+    def contacts(self):
+        m = self.stats()["n_contacts"]
+        mm = max(m, 1)
+        ab, phi = np.zeros((mm, 2), np.int32), np.zeros(mm, np.float32)
+        nn, t1 = np.zeros((mm, 3), np.float32), np.zeros((mm, 3), np.float32)
+        _check(self.ctx, load_library().ovl_read_contacts(self.ctx, _ptr(ab, _ip), _ptr(phi, _fp),
+                                                          _ptr(nn, _fp), _ptr(t1, _fp)))
+        return ab[:m], phi[:m], nn[:m], t1[:m]
+
+    def graph(self):
+        m = self.stats()["n_adjacency"]
+        rp, col = np.zeros(self.n + 1, np.int32), np.zeros(max(m, 1), np.int32)
+        _check(self.ctx, load_library().ovl_read_graph(self.ctx, _ptr(rp, _ip), _ptr(col, _ip)))
+        return rp, col[:m]
+
+    def entries(self):
+        ne = self.stats()["n_entries"]
+        m = max(ne, 1)
+        ep, part = np.zeros(self.n + 1, np.int32), np.zeros(m, np.int32)
+        D, w, cp = np.zeros(m, np.uint8), np.zeros(m, np.float32), np.zeros((m, 13), np.float32)
+        _check(self.ctx, load_library().ovl_read_entries(self.ctx, _ptr(ep, _ip), _ptr(part, _ip),
+                                                         _ptr(D, _u8p), _ptr(w, _fp), _ptr(cp, _fp)))
+        return dict(entry_ptr=ep, part=part[:ne], D=D[:ne], weight=w[:ne], copies=cp[:ne])
+
+    def pairs(self):
+        npr = self.stats()["n_pairs"]
+        m = max(npr, 1)
+        part, key = np.zeros(m, np.int32), np.zeros(m, np.uint64)
+        colour, lam = np.zeros(m, np.int32), np.zeros((m, 3), np.float32)
+        _check(self.ctx, load_library().ovl_read_pairs(self.ctx, _ptr(part, _ip), _ptr(key, _u64p),
+                                                       _ptr(colour, _ip), _ptr(lam, _fp)))
+        return dict(part=part[:npr], key=key[:npr], colour=colour[:npr], lam=lam[:npr])
+
+    def worker_stats(self):
+        P = self.n_parts
+        it, rs = np.zeros(P, np.int32), np.zeros(P, np.float64)
+        rows, cols = np.zeros(P, np.int64), np.zeros(P, np.int32)
+        _check(self.ctx, load_library().ovl_read_worker_stats(
+            self.ctx, _ptr(it, _ip), rs.ctypes.data_as(C.POINTER(C.c_double)),
+            rows.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(cols, _ip)))
+        return dict(iters=it, res_sq=rs, rows=rows, colours=cols)

@@ -1,0 +1,128 @@
+"""Helpers for GPU-vs-oracle parity from identical inputs.
+
+``prepare`` runs the FP64 oracle for a few steps, rounds its state and
+warm-start impulses to FP32 once, and loads the same rounded values, the same
+membership masks and the same step index into both the oracle and a fresh
+libovl context -- no input ever comes from the CUDA path.  ``compare_step``
+then takes one step on both and checks every record element by element.
+
+Tolerances (FP32 kernel vs FP64 oracle from identical inputs):
+  integers (contacts, graph, masks, entries, D, pair order, colours): exact
+  velocities, angular velocities:   1e-4 m/s (rad/s) + 1e-5 x the step's largest speed
+                                    (the absolute part is the method's target; the relative
+                                    part, ~170 FP32 unit roundoffs, covers FP32 accumulation
+                                    over the sweeps of fast, deeply penetrating stress scenes)
+  positions:                        1e-5 m
+  quaternions:                      1e-5
+  contact gap, normal, tangent:     1e-5
+  weights:                          1e-6
+  impulses:                         the velocity bound x max(1, body mass) (Delta v = Delta lambda / m)
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import oracle as O
+from paper_2403_17261_gb300 import ovl
+
+TOL_V = 1e-4
+TOL_V_REL = 1e-5
+TOL_X = 1e-5
+TOL_Q = 1e-5
+TOL_GEOM = 1e-5
+TOL_W = 1e-6
+
+
+def prepare(scene, warm_steps: int = 0, params: dict | None = None, gpu_params: dict | None = None):
+    orc = O.OracleSim(scene, params)
+    if scene.assign_overlap:
+        orc.assign_overlap()
+    for _ in range(warm_steps):
+        orc.step()
+    st32 = orc.state().astype(np.float32)
+    part, key, lam = orc.warmstart()
+    lam32 = lam.astype(np.float32)
+    masks = orc.masks()
+    k = orc.step_index()
+    orc.set_state(st32.astype(np.float64))
+    orc.set_warmstart(part, key, lam32.astype(np.float64))
+    gp = dict(params or {})
+    gp.update(gpu_params or {})
+    gpu = ovl.Simulation(scene, gp, partition=False)
+    gpu.set_membership(masks)
+    gpu.set_state(st32)
+    gpu.set_warmstart(part, key, lam32)
+    gpu.set_step_index(k)
+    return orc, gpu
+
+
+def _maxabs(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max()) if a.size else 0.0
+
+
+def _qdist(qa, qb):
+    qa = np.asarray(qa, dtype=np.float64)
+    qb = np.asarray(qb, dtype=np.float64)
+    if not qa.size:
+        return 0.0
+    d1 = np.abs(qa - qb).max(axis=1)
+    d2 = np.abs(qa + qb).max(axis=1)
+    return float(np.minimum(d1, d2).max())
+
+
+def compare_step(orc, gpu, dt: float = 0.0, iters: int | None = None, check_lambda: bool = True):
+    """One step on both sides; asserts parity of every record; returns a report."""
+    orc.step(dt, iters)
+    gpu.step(dt, iters)
+    rep = {}
+    sc = orc.scene
+    # contacts (Algorithm 1 line 10)
+    ab_o, phi_o, n_o, t_o = orc.contacts()
+    ab_g, phi_g, n_g, t_g = gpu.contacts()
+    assert ab_o.shape == ab_g.shape, (ab_o.shape, ab_g.shape)
+    assert np.array_equal(ab_o, ab_g), "contact pairs differ"
+    rep["contacts"] = len(ab_o)
+    rep["phi"] = _maxabs(phi_o, phi_g)
+    rep["normal"] = _maxabs(n_o, n_g)
+    rep["t1"] = _maxabs(t_o, t_g)
+    assert rep["phi"] <= TOL_GEOM and rep["normal"] <= TOL_GEOM and rep["t1"] <= TOL_GEOM, rep
+    # constraint graph (line 11)
+    rp_o, col_o = orc.graph()
+    rp_g, col_g = gpu.graph()
+    assert np.array_equal(rp_o, rp_g) and np.array_equal(col_o, col_g), "graph differs"
+    # membership after the load balance (line 12)
+    assert np.array_equal(orc.masks(), gpu.membership()), "membership differs"
+    # entries, geodesics, weights, copies (lines 13-16)
+    eo, eg = orc.entries(), gpu.entries()
+    assert np.array_equal(eo["entry_ptr"], eg["entry_ptr"].astype(np.int64)), "entries differ"
+    assert np.array_equal(eo["part"], eg["part"]), "entry workers differ"
+    assert np.array_equal(eo["D"], eg["D"]), "geodesic distances differ"
+    rep["weight"] = _maxabs(eo["weight"], eg["weight"])
+    assert rep["weight"] <= TOL_W, rep
+    co, cg = eo["copies"], eg["copies"]
+    rep["copy_x"] = _maxabs(co[:, 0:3], cg[:, 0:3])
+    rep["copy_q"] = _qdist(co[:, 3:7], cg[:, 3:7])
+    rep["copy_v"] = _maxabs(co[:, 7:13], cg[:, 7:13])
+    # pairs: worker, key order and colours exact; impulses close
+    po, pg = orc.pairs(), gpu.pairs()
+    assert np.array_equal(po["part"], pg["part"]), "pair workers differ"
+    assert np.array_equal(po["key"], pg["key"]), "pair keys differ"
+    assert np.array_equal(po["colour"], pg["colour"]), "colours differ"
+    so, sg = orc.state(), gpu.state()
+    vmax = float(np.abs(so[:, 7:13]).max()) if so.size else 0.0
+    tol_v = TOL_V + TOL_V_REL * vmax
+    rep["tol_v"] = tol_v
+    mmax = float(np.max(1.0 / sc.inv_mass[sc.inv_mass > 0])) if np.any(sc.inv_mass > 0) else 1.0
+    rep["lambda"] = _maxabs(po["lam"], pg["lam"])
+    if check_lambda:
+        assert rep["lambda"] <= tol_v * max(1.0, mmax), rep
+    # blended state (lines 18-20)
+    rep["x"] = _maxabs(so[:, 0:3], sg[:, 0:3])
+    rep["q"] = _qdist(so[:, 3:7], sg[:, 3:7])
+    rep["v"] = _maxabs(so[:, 7:13], sg[:, 7:13])
+    assert rep["copy_x"] <= TOL_X and rep["x"] <= TOL_X, rep
+    assert rep["copy_q"] <= TOL_Q and rep["q"] <= TOL_Q, rep
+    assert rep["copy_v"] <= tol_v and rep["v"] <= tol_v, rep
+    return rep

@@ -1,0 +1,54 @@
+"""GPU parity: the CUDA path against the FP64 oracle, one step from identical
+inputs, every record compared (see tests/parity.py for the tolerances)."""
+import numpy as np
+import pytest
+
+from paper_2403_17261_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _parity():
+    import parity
+    return parity
+
+
+@pytest.mark.parametrize("warm", [0, 1, 5, 20])
+def test_pile_small(warm):
+    P = _parity()
+    orc, gpu = P.prepare(S.pile_small(), warm_steps=warm)
+    rep = P.compare_step(orc, gpu)
+    assert rep["contacts"] > 600
+
+
+@pytest.mark.parametrize("warm", [0, 3])
+def test_chain(warm):
+    P = _parity()
+    orc, gpu = P.prepare(S.chain(), warm_steps=warm)
+    rep = P.compare_step(orc, gpu)
+    assert rep["contacts"] > 2000
+
+
+@pytest.mark.parametrize("n,seed,sets", [(300, 11, 3), (1500, 12, 5), (4000, 13, 8)])
+def test_random_pile(n, seed, sets):
+    P = _parity()
+    sc = S.random_pile(n, seed, n_sets=sets, box=0.3 * n ** (1 / 3) + 1.0)
+    orc, gpu = P.prepare(sc, warm_steps=2)
+    P.compare_step(orc, gpu)
+
+
+def test_closed_forms_on_gpu():
+    from paper_2403_17261_gb300 import ovl
+    sc = S.resting_sphere()
+    g = ovl.Simulation(sc)
+    g.step()
+    lam = g.pairs()["lam"]
+    m, h = 1.0 / float(sc.inv_mass[0]), float(sc.scene_dt[0])
+    assert abs(lam[0, 0] - m * 9.81 * h) < 1e-6 * m * 9.81 * h
+    assert np.abs(g.state()[0, 7:13]).max() < 1e-6
