@@ -61,6 +61,9 @@ typedef struct ovl_params {
     int32_t res_check_every; /* sweeps between residual checks when res_tol > 0 */
     int32_t pgs_threads;     /* threads per worker CTA (0 = automatic) */
     int32_t flags;           /* OVL_FLAG_* */
+    int32_t pgs_cluster;     /* CTAs per worker, 1, 2 or 4 (0 = automatic from the SM count) */
+    int32_t smem_slot_limit; /* > 0: at most this many bodies per CTA in shared memory (larger
+                                workers use the global-memory path); 0 = as many as fit */
 } ovl_params;
 
 #define OVL_FLAG_RESIDUAL 1  /* compute the complementarity residual of every row after the sweeps */

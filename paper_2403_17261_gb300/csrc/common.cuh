@@ -99,7 +99,7 @@ void fill_i32(int *p, int v, size_t n, cudaStream_t s);
 void fill_u8(uint8_t *p, uint8_t v, size_t n, cudaStream_t s);
 void iota_u32(uint32_t *p, int n, cudaStream_t s);
 // counts[key[i]]++ for i < n
-void histogram_i32(const int *key, int n, int *counts, cudaStream_t s);
+void histogram_i32(const int *key, int n, int *counts, int nbins, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // host-side algorithms (host_alg.cpp): Algorithms 2, 3, 6, 7

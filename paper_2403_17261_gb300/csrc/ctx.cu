@@ -23,6 +23,10 @@ struct ovl_ctx {
     bool own_stream = false;
     int device = 0;
     int smem_optin = 0;
+    int num_sms = 0;
+    int smem_per_sm = 0;
+    int nb_max = 0;          // most bodies in one worker (last membership phase)
+    int last_cluster = 1;
     std::string err;
 
     // scene (host copies)
@@ -62,8 +66,10 @@ struct ovl_ctx {
     DBuf<int2> p_slot;
     DBuf<float4> p_lam0;
     DBuf<unsigned long long> colour_scratch;
-    DBuf<float4> r0, r1, r2, rlam, lam_out;
-    DBuf<int4> r3;
+    DBuf<int4> worklist, worklist2;
+    DBuf<unsigned long long> wprio, wprio2;
+    DBuf<float4> r0, r1, r2, r3, rlam, lam_out;
+    DBuf<int> rpair;
     DBuf<int> ws_pstart;
     DBuf<uint64_t> ws_key;
     DBuf<float4> ws_lam;
@@ -81,6 +87,10 @@ struct ovl_ctx {
     HBuf<int2> h_ab;
     HBuf<int> h_rp, h_col;
     HBuf<uint64_t> h_mask;
+    DBuf<int> lb_flag, lb_pos;
+    DBuf<int2> lb_pairs;
+    std::vector<int> lb_a, lb_b;
+    std::vector<uint64_t> lb_mask;
 
     // last step
     int64_t step_index = 0;
@@ -210,34 +220,40 @@ void phase_graph(ovl_ctx *c) {
     launch_adj_compact(c->tptr.p, c->tcol.p, n, c->row_ptr.p, c->col.p, s);
 }
 
-// Algorithm 6 on the host over the contacts between two dynamic bodies
+// Algorithm 6 on the host over the contacts between two dynamic bodies, in
+// canonical order.  The GPU first compacts the contacts that can act: all
+// dynamic pairs on removal steps, only worker-disjoint pairs otherwise.
 void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
-    if (!act && !deact) return;
+    if ((!act && !deact) || c->nc == 0) return;
     cudaStream_t s = c->stream;
     const int n = c->n;
-    c->h_ab.ensure(c->nc + 1);
+    c->lb_flag.ensure(c->nc + 1);
+    c->lb_pos.ensure(c->nc + 1);
+    c->lb_pairs.ensure(c->nc + 1);
+    launch_lb_flags(c->c_ab.p, c->nc, c->im.p, n, c->mask.p, deact ? 0 : 1, c->lb_flag.p, s);
+    scan_i32(c->lb_flag.p, c->lb_pos.p, c->nc, c->scan_tmp, s);
+    const int m = read_i32(c, c->lb_pos.p + c->nc);
+    if (m == 0) return;
+    launch_lb_compact(c->c_ab.p, c->nc, c->lb_flag.p, c->lb_pos.p, c->lb_pairs.p, s);
+    c->h_ab.ensure(m + 1);
     c->h_rp.ensure((size_t)n + 1);
     c->h_col.ensure((size_t)c->nadj + 1);
     c->h_mask.ensure(n);
-    CK(cudaMemcpyAsync(c->h_ab.p, c->c_ab.p, sizeof(int2) * c->nc, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->h_ab.p, c->lb_pairs.p, sizeof(int2) * m, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->h_rp.p, c->row_ptr.p, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->h_col.p, c->col.p, sizeof(int) * c->nadj, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->h_mask.p, c->mask.p, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    std::vector<int> ca, cb;
-    ca.reserve(c->nc);
-    cb.reserve(c->nc);
-    for (int i = 0; i < c->nc; ++i) {
-        int a = c->h_ab.p[i].x, b = c->h_ab.p[i].y;
-        if (b >= n || !(c->h_im[a] > 0.f) || !(c->h_im[b] > 0.f)) continue;
-        ca.push_back(a);
-        cb.push_back(b);
+    c->lb_a.resize(m);
+    c->lb_b.resize(m);
+    for (int i = 0; i < m; ++i) {
+        c->lb_a[i] = c->h_ab.p[i].x;
+        c->lb_b[i] = c->h_ab.p[i].y;
     }
-    if (ca.empty()) return;
-    std::vector<uint64_t> m(c->h_mask.p, c->h_mask.p + n);
-    host_load_balance(c->hs, m, (int64_t)ca.size(), ca.data(), cb.data(), c->h_rp.p, c->h_col.p, act,
-                      deact);
-    std::copy(m.begin(), m.end(), c->h_mask.p);
+    c->lb_mask.assign(c->h_mask.p, c->h_mask.p + n);
+    host_load_balance(c->hs, c->lb_mask, m, c->lb_a.data(), c->lb_b.data(), c->h_rp.p, c->h_col.p,
+                      act, deact);
+    std::copy(c->lb_mask.begin(), c->lb_mask.end(), c->h_mask.p);
     CK(cudaMemcpyAsync(c->mask.p, c->h_mask.p, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
 }
@@ -287,10 +303,17 @@ void phase_membership(ovl_ctx *c, float dt_override) {
     launch_entry_fill(a, s);
     group_by(c, c->entry_part.p, ne, c->part_list);
     CK(cudaMemsetAsync(c->part_count.p, 0, sizeof(int) * ((size_t)P + 1), s));
-    histogram_i32(c->entry_part.p, ne, c->part_count.p, s);
+    histogram_i32(c->entry_part.p, ne, c->part_count.p, P, s);
     scan_i32(c->part_count.p, c->part_bstart.p, P, c->scan_tmp, s);
     a = member_args(c);
     launch_entry_slot(a, ne, s);
+    {
+        std::vector<int> pb(P + 1);
+        CK(cudaMemcpyAsync(pb.data(), c->part_bstart.p, sizeof(int) * (P + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        c->nb_max = 0;
+        for (int p = 0; p < P; ++p) c->nb_max = std::max(c->nb_max, pb[p + 1] - pb[p]);
+    }
     // (worker, constraint) pairs
     const int K = c->nc + c->nj;
     c->cons_count.ensure((size_t)K + 1); c->cons_start.ensure((size_t)K + 1);
@@ -309,7 +332,7 @@ void phase_membership(ovl_ctx *c, float dt_override) {
     group_by(c, c->pair_part.p, npr, order);
     launch_pair_gather(a, reinterpret_cast<const uint32_t *>(order.p), npr, s);
     CK(cudaMemsetAsync(c->part_pcount.p, 0, sizeof(int) * ((size_t)P + 1), s));
-    histogram_i32(c->pair_part.p, npr, c->part_pcount.p, s);
+    histogram_i32(c->pair_part.p, npr, c->part_pcount.p, P, s);
     scan_i32(c->part_pcount.p, c->part_pstart.p, P, c->scan_tmp, s);
     WarmArgs w{};
     w.ws_pstart = c->ws_pstart.p; w.ws_key = c->ws_key.p; w.ws_lam = c->ws_lam.p;
@@ -319,12 +342,15 @@ void phase_membership(ovl_ctx *c, float dt_override) {
 
 int colour_smem_slots(ovl_ctx *c) {
     int avail = c->smem_optin - 20 * 1024;
-    return std::max(0, avail / 24);
+    int n = std::max(0, avail / 24);
+    return c->P.smem_slot_limit > 0 ? std::min(n, c->P.smem_slot_limit) : n;
 }
 
-int solve_smem_slots(ovl_ctx *c) {
-    int avail = c->smem_optin - 1024;
-    return std::max(0, avail / 32);
+// Shared-memory body slots per CTA (24 B each) for 1 or 2 resident CTAs per SM
+int solve_slot_capacity(ovl_ctx *c, int ctas_per_sm) {
+    int avail = ctas_per_sm == 1 ? c->smem_optin - 1024 : (c->smem_per_sm / 2) - 2048;
+    int n = std::max(0, avail / 24);
+    return c->P.smem_slot_limit > 0 ? std::min(n, c->P.smem_slot_limit) : n;
 }
 
 void phase_colour(ovl_ctx *c) {
@@ -334,18 +360,24 @@ void phase_colour(ovl_ctx *c) {
     c->col_off.ensure((size_t)P * (2 * OVL_MAX_COLOURS + 1) + 1);
     c->pair_of_row.ensure(npr + 1);
     c->colour_scratch.ensure(3 * (size_t)c->ne + 1);
+    c->worklist.ensure(npr + 1);
+    c->worklist2.ensure(npr + 1);
+    c->wprio.ensure(npr + 1);
+    c->wprio2.ensure(npr + 1);
     ColourArgs a{};
     a.n_parts = P; a.part_bstart = c->part_bstart.p; a.part_pstart = c->part_pstart.p;
     a.p_key = c->p_key.p; a.p_slot = c->p_slot.p; a.p_colour = c->p_colour.p;
     a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p; a.pair_of_row = c->pair_of_row.p;
     a.scratch = c->colour_scratch.p; a.smem_slots = colour_smem_slots(c); a.status = c->status.p;
+    a.worklist = c->worklist.p; a.worklist2 = c->worklist2.p;
+    a.wprio = c->wprio.p; a.wprio2 = c->wprio2.p;
     launch_colour(a, c->stream);
 }
 
 void phase_rows(ovl_ctx *c, float dt_override) {
     const int npr = c->npairs;
     c->r0.ensure(npr + 1); c->r1.ensure(npr + 1); c->r2.ensure(npr + 1); c->r3.ensure(npr + 1);
-    c->rlam.ensure(npr + 1);
+    c->rpair.ensure(npr + 1); c->rlam.ensure(npr + 1);
     RowArgs a{};
     a.n = c->n; a.nc = c->nc; a.np = npr; a.pair_of_row = c->pair_of_row.p; a.ps_cons = c->ps_cons.p;
     a.ps_part = c->ps_part.p; a.p_slot = c->p_slot.p; a.p_lam0 = c->p_lam0.p; a.c_ab = c->c_ab.p;
@@ -354,7 +386,36 @@ void phase_rows(ovl_ctx *c, float dt_override) {
     a.scene_dt = c->scene_dt.p; a.scene_mu = c->scene_mu.p; a.dt_override = dt_override;
     a.erp = c->P.erp; a.slop = c->P.slop;
     a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
+    a.rpair = c->rpair.p; a.status = c->status.p;
     launch_rows(a, c->stream);
+}
+
+// CTAs per worker (C) and shared-memory slots per CTA.  Preference: the
+// smallest C for which every CTA of the launch is resident at once with two
+// CTAs per SM (the largest worker's share fits half an SM's shared memory),
+// then with one CTA per SM, so no worker waits for a second wave; otherwise
+// the smallest C whose share fits one CTA.  A fixed pgs_cluster overrides C.
+void solve_config(ovl_ctx *c, int *cluster, int *slots) {
+    const int nbmax = c->nb_max;
+    const int cap2 = solve_slot_capacity(c, 2), cap1 = solve_slot_capacity(c, 1);
+    const int fixed = (c->P.pgs_cluster == 1 || c->P.pgs_cluster == 2 || c->P.pgs_cluster == 4 ||
+                       c->P.pgs_cluster == 8) ? c->P.pgs_cluster : 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int C = 1; C <= 8; C <<= 1) {
+            if (fixed && C != fixed) continue;
+            const int per = (nbmax + C - 1) / C;
+            const long long ctas = (long long)c->n_parts * C;
+            if (pass == 0 && per <= cap2 && ctas <= 2ll * c->num_sms) { *cluster = C; *slots = std::max(per, 1); return; }
+            if (pass == 1 && per <= cap1 && ctas <= c->num_sms) { *cluster = C; *slots = std::max(per, 1); return; }
+        }
+    for (int C = 1; C <= 8; C <<= 1) {
+        if (fixed && C != fixed) continue;
+        const int per = (nbmax + C - 1) / C;
+        if (per <= cap1) { *cluster = C; *slots = std::max(per, 1); return; }
+    }
+    // the largest workers go to the global-memory path
+    *cluster = fixed ? fixed : 4;
+    *slots = cap1;
 }
 
 int solve_threads(ovl_ctx *c) {
@@ -378,11 +439,15 @@ void phase_solve(ovl_ctx *c, float dt_override, int iters) {
     a.part_scene = c->part_scene.p; a.scene_dt = c->scene_dt.p; a.dt_override = dt_override;
     a.gravity = make_float3(c->P.gravity[0], c->P.gravity[1], c->P.gravity[2]);
     a.st = c->st.p; a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
+    a.rpair = c->rpair.p; a.scene_mu = c->scene_mu.p; a.n_entries = c->ne;
     a.lam_out = c->lam_out.p; a.copies = c->copies.p; a.scratch = c->solve_scratch.p;
-    a.iters = iters; a.smem_slots = solve_smem_slots(c); a.flags = c->P.flags;
+    int cluster = 1, slots = 0;
+    solve_config(c, &cluster, &slots);
+    c->last_cluster = cluster;
+    a.iters = iters; a.smem_slots = slots; a.flags = c->P.flags;
     a.res_tol = c->P.res_tol; a.res_check_every = c->P.res_check_every;
     a.part_iters = c->part_iters.p; a.part_res_sq = c->part_res_sq.p; a.status = c->status.p;
-    launch_solve(a, solve_threads(c), c->stream);
+    launch_solve(a, solve_threads(c), cluster, c->stream);
 }
 
 void phase_geodesics(ovl_ctx *c) {
@@ -495,6 +560,8 @@ ovl_status ovl_create(ovl_ctx **out, const ovl_params *p, void *cuda_stream) {
     ovl_status st = guarded(c, [&]() -> ovl_status {
         CK(cudaGetDevice(&c->device));
         CK(cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+        CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+        CK(cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device));
         if (cuda_stream) {
             c->stream = (cudaStream_t)cuda_stream;
         } else {
@@ -543,12 +610,13 @@ void release_all(ovl_ctx *c) {
     c->pair_cons.release(); c->pair_part.release(); c->ps_cons.release(); c->ps_part.release();
     c->part_pcount.release(); c->part_pstart.release(); c->p_colour.release(); c->part_ncol.release();
     c->col_off.release(); c->pair_of_row.release(); c->p_key.release(); c->p_slot.release();
-    c->p_lam0.release(); c->colour_scratch.release(); c->r0.release(); c->r1.release();
-    c->r2.release(); c->rlam.release(); c->lam_out.release(); c->r3.release(); c->ws_pstart.release();
+    c->p_lam0.release(); c->colour_scratch.release(); c->worklist.release(); c->worklist2.release(); c->wprio.release(); c->wprio2.release(); c->r0.release(); c->r1.release();
+    c->r2.release(); c->rlam.release(); c->lam_out.release(); c->r3.release(); c->rpair.release(); c->ws_pstart.release();
     c->ws_key.release(); c->ws_lam.release(); c->copies.release(); c->solve_scratch.release();
     c->part_iters.release(); c->part_res_sq.release(); c->visited.release(); c->queue.release();
     c->qctl.release(); c->D.release(); c->weight.release(); c->stage13.release(); c->scan_tmp.release();
     c->sort_hist.release(); c->sort_tmp.release();
+    c->lb_flag.release(); c->lb_pos.release(); c->lb_pairs.release();
 }
 
 template <class T>

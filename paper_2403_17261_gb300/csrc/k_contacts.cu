@@ -251,6 +251,26 @@ __global__ void k_adj_compact(const int *__restrict__ tptr, const int *__restric
     }
 }
 
+// Load-balance candidates: contacts between two dynamic bodies (all of
+// them when the removal branches run), or only those whose worker sets are
+// disjoint (activation-only steps: activations only add workers, so a pair
+// that shares a worker now can never reach Algorithm 6 line 4 later).
+__global__ void k_lb_flags(const int2 *__restrict__ c_ab, int nc, const float *__restrict__ im, int n,
+                           const uint64_t *__restrict__ mask, int disjoint_only, int *__restrict__ flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        int2 e = c_ab[i];
+        int f = e.y < n && im[e.x] > 0.0f && im[e.y] > 0.0f;
+        if (f && disjoint_only) f = (mask[e.x] & mask[e.y]) == 0ull;
+        flag[i] = f;
+    }
+}
+
+__global__ void k_lb_compact(const int2 *__restrict__ c_ab, int nc, const int *__restrict__ flag,
+                             const int *__restrict__ pos, int2 *__restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+        if (flag[i]) out[pos[i]] = c_ab[i];
+}
+
 }  // namespace
 
 int grid1d(size_t n, int threads) {
@@ -317,4 +337,21 @@ void launch_adj_compact(const int *tptr, const int *tcol, int n, const int *row_
     CK(cudaGetLastError());
 }
 
+}  // namespace ovl
+
+namespace ovl {
+void launch_lb_flags(const int2 *c_ab, int nc, const float *im, int n, const uint64_t *mask,
+                     int disjoint_only, int *flag, cudaStream_t s) {
+    if (!nc) return;
+    k_lb_flags<<<grid1d(nc, 256), 256, 0, s>>>(c_ab, nc, im, n, mask, disjoint_only, flag);
+    note_launch();
+    CK(cudaGetLastError());
+}
+void launch_lb_compact(const int2 *c_ab, int nc, const int *flag, const int *pos, int2 *out,
+                       cudaStream_t s) {
+    if (!nc) return;
+    k_lb_compact<<<grid1d(nc, 256), 256, 0, s>>>(c_ab, nc, flag, pos, out);
+    note_launch();
+    CK(cudaGetLastError());
+}
 }  // namespace ovl

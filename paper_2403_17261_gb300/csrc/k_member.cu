@@ -150,7 +150,7 @@ constexpr int NBUCKET = 2 * OVL_MAX_COLOURS;
 
 __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
     extern __shared__ unsigned long long dyn_smem[];
-    __shared__ int remaining, rounds_left, ncol_sh;
+    __shared__ int n_cur, n_next, rounds_left, ncol_sh;
     __shared__ int counts[NBUCKET + 1];
     __shared__ int running[NBUCKET];
     __shared__ int wcnt[COLOUR_WARPS][NBUCKET];
@@ -166,46 +166,66 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
     }
     used0 = slot_max + nb;
     used1 = used0 + nb;
-    for (int s = tid; s < nb; s += blockDim.x) { used0[s] = 0ull; used1[s] = 0ull; }
-    for (int k = tid; k < nq; k += blockDim.x) a.p_colour[q0 + k] = -1;
-    if (tid == 0) { remaining = nq; rounds_left = nq + 2; ncol_sh = 0; }
+    // worklists of uncoloured constraints, ping-pong: (index relative to q0,
+    // slot a, slot b) and the priority, read contiguously every round
+    int4 *wl_cur = a.worklist + q0, *wl_next = a.worklist2 + q0;
+    unsigned long long *pr_cur = a.wprio + q0, *pr_next = a.wprio2 + q0;
+    for (int s = tid; s < nb; s += blockDim.x) { used0[s] = 0ull; used1[s] = 0ull; slot_max[s] = 0ull; }
+    for (int k = tid; k < nq; k += blockDim.x) {
+        int2 sl = a.p_slot[q0 + k];
+        wl_cur[k] = make_int4(k, sl.x, sl.y, 0);
+        pr_cur[k] = mix64(a.p_key[q0 + k]);
+    }
+    if (tid == 0) { n_cur = nq; n_next = 0; rounds_left = nq + 2; ncol_sh = 0; }
     __syncthreads();
-    while (remaining > 0 && rounds_left > 0) {
-        for (int s = tid; s < nb; s += blockDim.x) slot_max[s] = 0ull;
-        __syncthreads();
-        for (int k = tid; k < nq; k += blockDim.x) {
-            if (a.p_colour[q0 + k] >= 0) continue;
-            unsigned long long pr = mix64(a.p_key[q0 + k]);
-            int2 sl = a.p_slot[q0 + k];
-            if (sl.x >= 0) atomicMax(&slot_max[sl.x], pr);
-            if (sl.y >= 0) atomicMax(&slot_max[sl.y], pr);
+    while (n_cur > 0 && rounds_left > 0) {
+        const int m = n_cur;
+        // highest priority among the uncoloured constraints at every slot
+        for (int i = tid; i < m; i += blockDim.x) {
+            const int4 w = wl_cur[i];
+            const unsigned long long pr = pr_cur[i];
+            if (w.y >= 0) atomicMax(&slot_max[w.y], pr);
+            if (w.z >= 0) atomicMax(&slot_max[w.z], pr);
         }
         __syncthreads();
-        for (int k = tid; k < nq; k += blockDim.x) {
-            if (a.p_colour[q0 + k] >= 0) continue;
-            unsigned long long pr = mix64(a.p_key[q0 + k]);
-            int2 sl = a.p_slot[q0 + k];
-            bool ready = (sl.x < 0 || slot_max[sl.x] == pr) && (sl.y < 0 || slot_max[sl.y] == pr);
-            if (!ready) continue;
+        for (int i = tid; i < m; i += blockDim.x) {
+            const int4 w = wl_cur[i];
+            const unsigned long long pr = pr_cur[i];
+            bool ready = (w.y < 0 || slot_max[w.y] == pr) && (w.z < 0 || slot_max[w.z] == pr);
+            if (!ready) {
+                int o = atomicAdd(&n_next, 1);
+                wl_next[o] = w;
+                pr_next[o] = pr;
+                continue;
+            }
             // only this constraint touches its slots in this round
             unsigned long long u0 = 0ull, u1 = 0ull;
-            if (sl.x >= 0) { u0 |= used0[sl.x]; u1 |= used1[sl.x]; }
-            if (sl.y >= 0) { u0 |= used0[sl.y]; u1 |= used1[sl.y]; }
+            if (w.y >= 0) { u0 |= used0[w.y]; u1 |= used1[w.y]; }
+            if (w.z >= 0) { u0 |= used0[w.z]; u1 |= used1[w.z]; }
             int c;
             if (~u0) c = __ffsll((long long)~u0) - 1;
             else if (~u1) c = 64 + __ffsll((long long)~u1) - 1;
             else { c = OVL_MAX_COLOURS - 1; atomicCAS(a.status, DEV_OK, DEV_ERR_COLOURS); }
-            a.p_colour[q0 + k] = c;
+            a.p_colour[q0 + w.x] = c;
             unsigned long long bit0 = c < 64 ? (1ull << c) : 0ull, bit1 = c >= 64 ? (1ull << (c - 64)) : 0ull;
-            if (sl.x >= 0) { used0[sl.x] |= bit0; used1[sl.x] |= bit1; }
-            if (sl.y >= 0) { used0[sl.y] |= bit0; used1[sl.y] |= bit1; }
-            atomicSub(&remaining, 1);
+            if (w.y >= 0) { used0[w.y] |= bit0; used1[w.y] |= bit1; }
+            if (w.z >= 0) { used0[w.z] |= bit0; used1[w.z] |= bit1; }
             atomicMax(&ncol_sh, c + 1);
         }
-        if (tid == 0) --rounds_left;
+        __syncthreads();
+        // clear the slot maxima that this round set
+        for (int i = tid; i < m; i += blockDim.x) {
+            const int4 w = wl_cur[i];
+            if (w.y >= 0) slot_max[w.y] = 0ull;
+            if (w.z >= 0) slot_max[w.z] = 0ull;
+        }
+        __syncthreads();
+        if (tid == 0) { n_cur = n_next; n_next = 0; --rounds_left; }
+        int4 *t = wl_cur; wl_cur = wl_next; wl_next = t;
+        unsigned long long *tp = pr_cur; pr_cur = pr_next; pr_next = tp;
         __syncthreads();
     }
-    if (tid == 0 && remaining > 0) atomicCAS(a.status, DEV_OK, DEV_ERR_TIMEOUT);
+    if (tid == 0 && n_cur > 0) atomicCAS(a.status, DEV_OK, DEV_ERR_TIMEOUT);
     // stable counting sort of the worker's constraints by (colour, kind):
     // contacts before joints inside a colour, canonical order kept
     for (int j = tid; j <= NBUCKET; j += blockDim.x) counts[j] = 0;
@@ -275,6 +295,14 @@ __device__ __forceinline__ float3 quat_rotate(float4 q, float3 v) {
                        v.z + q.x * t.z + (u.x * t.y - u.y * t.x));
 }
 
+// two 16-bit worker slots in one word (0xffff: static end)
+__device__ __forceinline__ int pack_slots(int2 sl, int *status) {
+    if (sl.x >= 0xffff || sl.y >= 0xffff) atomicCAS(status, DEV_OK, DEV_ERR_CAPACITY);
+    unsigned a = sl.x < 0 ? 0xffffu : (unsigned)sl.x & 0xffffu;
+    unsigned b = sl.y < 0 ? 0xffffu : (unsigned)sl.y & 0xffffu;
+    return (int)(a | (b << 16));
+}
+
 __global__ void k_rows(RowArgs a) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.np; r += gridDim.x * blockDim.x) {
         const int k = a.pair_of_row[r];
@@ -299,8 +327,8 @@ __global__ void k_rows(RowArgs a) {
             float target = phi > 0.f ? -phi / h : a.erp * fmaxf(-phi - a.slop, 0.f) / h;
             a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, kn);
             a.r1[r] = make_float4(t1.x, t1.y, t1.z, kt);
-            a.r2[r] = make_float4(ra, rb, target, a.scene_mu[scene]);
-            a.r3[r] = make_int4(sl.x, sl.y, k, 0);
+            a.r2[r] = make_float4(ra, rb, target, __int_as_float(pack_slots(sl, a.status)));
+            a.r3[r] = make_float4(ima, imb, iia, iib);
         } else {
             const int j = i - a.nc;
             const int2 ab = a.jab[j];
@@ -329,17 +357,13 @@ __global__ void k_rows(RowArgs a) {
             }
             float3 err = make_float3((xB.x - xA.x) + (rB.x - rA.x), (xB.y - xA.y) + (rB.y - rA.y),
                                      (xB.z - xA.z) + (rB.z - rA.z));
-            // K_kk = m_a^-1 + m_b^-1 + I_a^-1 |r_A x e_k|^2 + I_b^-1 |r_B x e_k|^2
-            float base = ima + imb;
-            float kx = 1.0f / (base + iia * (rA.y * rA.y + rA.z * rA.z) + iib * (rB.y * rB.y + rB.z * rB.z));
-            float ky = 1.0f / (base + iia * (rA.x * rA.x + rA.z * rA.z) + iib * (rB.x * rB.x + rB.z * rB.z));
-            float kz = 1.0f / (base + iia * (rA.x * rA.x + rA.y * rA.y) + iib * (rB.x * rB.x + rB.y * rB.y));
             float g = -a.erp / h;
             a.r0[r] = make_float4(rA.x, rA.y, rA.z, g * err.x);
             a.r1[r] = make_float4(rB.x, rB.y, rB.z, g * err.y);
-            a.r2[r] = make_float4(kx, ky, kz, g * err.z);
-            a.r3[r] = make_int4(sl.x, sl.y, k, 1);
+            a.r2[r] = make_float4(g * err.z, 0.f, 0.f, __int_as_float(pack_slots(sl, a.status)));
+            a.r3[r] = make_float4(ima, imb, iia, iib);
         }
+        a.rpair[r] = k;
         a.rlam[r] = a.p_lam0[k];
     }
 }

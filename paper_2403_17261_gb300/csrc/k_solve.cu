@@ -3,12 +3,17 @@
 // constraints, then integration (Section 3: velocities first, positions with
 // the new velocities), writing the worker's copy of each body.
 //
-// One CTA per worker.  The worker's body velocities live in shared memory
-// (32 B per body: (v, 1/m) and (w, 1/I)); workers too large for shared memory
-// keep them in a global scratch area instead.  Rows are streamed from HBM/L2
-// in colour order: constraints of one colour share no dynamic body, so a
-// colour is solved by all threads at once and a barrier separates colours --
-// the same result as sweeping the constraints one by one in colour order.
+// A worker is solved by a group of C CTAs (a thread-block cluster when C > 1).
+// Its body velocities (24 B per body: v and w) live in the shared memory of
+// the group -- slot s in CTA s % C at index s / C, reached through
+// distributed shared memory (mapa + ld/st.shared::cluster) -- or, for workers
+// too large for that, in a global scratch area solved by one CTA.  Rows are
+// streamed from HBM/L2 in colour order: constraints of one colour share no
+// dynamic body, so a colour is solved by all threads of the group at once and
+// a group barrier separates colours -- the same result as sweeping the
+// constraints one by one in colour order.  Inverse masses and inertias come
+// with every row record so the body state stays small enough for two groups'
+// CTAs to share an SM.
 //
 // Row model (sphere contact, normal n from a to b, lever arms r_a n and
 // -r_b n, tangents t1 and t2 = n x t1):
@@ -17,74 +22,131 @@
 //   w_t2 = t2.(v_b - v_a) + t1.(r_a w_a + r_b w_b)
 //   lambda' = clamp(lambda + k (target - w), lo, hi), impulses J^T (lambda' - lambda)
 // with lo/hi = [0, inf) for the normal and +-mu lambda_n for the tangents.
-// Ball joint: three rows along the world axes, w = (v_b + w_b x r_B - v_a - w_a x r_A)_k.
+// Ball joint: three rows along the world axes, w = (v_b + w_b x r_B - v_a - w_a x r_A)_k,
+// k = 1 / (1/m_a + 1/m_b + |r_A x e_k|^2 / I_a + |r_B x e_k|^2 / I_b).
+//
+// Row records (float4 each): contact r0 = (n, k_n), r1 = (t1, k_t),
+// r2 = (r_a, r_b, target, slots), r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b);
+// joint r0 = (r_A, target_x), r1 = (r_B, target_y), r2 = (target_z, 0, 0, slots),
+// r3 as for contacts.  slots = slot_a | slot_b << 16 (0xffff: static end).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ovl {
 
 namespace {
 
 constexpr int NB1 = 2 * OVL_MAX_COLOURS + 1;
+constexpr int SOLVE_THREADS = 512;
 
 __device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
     return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
-__device__ __forceinline__ void axpy(float4 &v, float s, float3 d) { v.x += s * d.x; v.y += s * d.y; v.z += s * d.z; }
+__device__ __forceinline__ void axpy(float3 &v, float s, float3 d) { v.x += s * d.x; v.y += s * d.y; v.z += s * d.z; }
 
 struct Body {
-    float4 v;  // (v, inverse mass)
-    float4 w;  // (omega, inverse inertia)
+    float3 v, w;
+    float im, ii;   // inverse mass and inertia (0 for a static end)
 };
 
-__device__ __forceinline__ Body load_body(const float4 *vel, const float4 *ang, int slot) {
-    Body b;
-    if (slot >= 0) {
-        b.v = vel[slot];
-        b.w = ang[slot];
-    } else {
-        b.v = make_float4(0.f, 0.f, 0.f, 0.f);
-        b.w = make_float4(0.f, 0.f, 0.f, 0.f);
+__device__ __forceinline__ int slot_a(int s) { int x = s & 0xffff; return x == 0xffff ? -1 : x; }
+__device__ __forceinline__ int slot_b(int s) { int x = (int)((unsigned)s >> 16); return x == 0xffff ? -1 : x; }
+
+// ---- body storage --------------------------------------------------------
+// Plain pointers: one CTA, shared or global memory.
+struct LocalSlots {
+    float4 *A;   // (vx, vy, vz, wx)
+    float2 *B;   // (wy, wz)
+    __device__ __forceinline__ void load(int s, Body &b) const {
+        float4 x = A[s];
+        float2 y = B[s];
+        b.v = make_float3(x.x, x.y, x.z);
+        b.w = make_float3(x.w, y.x, y.y);
     }
-    return b;
+    __device__ __forceinline__ void store(int s, const Body &b) const {
+        A[s] = make_float4(b.v.x, b.v.y, b.v.z, b.w.x);
+        B[s] = make_float2(b.w.y, b.w.z);
+    }
+};
+
+__device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
 }
 
-__device__ __forceinline__ void store_body(float4 *vel, float4 *ang, int slot, const Body &b) {
-    if (slot >= 0) {
-        vel[slot] = b.v;
-        ang[slot] = b.w;
+// Distributed over the C CTAs of a cluster: slot s in CTA s % C at index s / C.
+template <int C>
+struct ClusterSlots {
+    uint32_t A, B;   // shared-window offsets of this CTA's arrays (same in every CTA)
+    __device__ __forceinline__ void load(int s, Body &b) const {
+        const uint32_t r = (uint32_t)s % C, i = (uint32_t)s / C;
+        const uint32_t a = mapa(A + 16u * i, r), c = mapa(B + 8u * i, r);
+        float4 x;
+        float2 y;
+        asm volatile("ld.shared::cluster.v4.f32 {%0,%1,%2,%3}, [%4];"
+                     : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w) : "r"(a) : "memory");
+        asm volatile("ld.shared::cluster.v2.f32 {%0,%1}, [%2];" : "=f"(y.x), "=f"(y.y) : "r"(c) : "memory");
+        b.v = make_float3(x.x, x.y, x.z);
+        b.w = make_float3(x.w, y.x, y.y);
     }
+    __device__ __forceinline__ void store(int s, const Body &b) const {
+        const uint32_t r = (uint32_t)s % C, i = (uint32_t)s / C;
+        const uint32_t a = mapa(A + 16u * i, r), c = mapa(B + 8u * i, r);
+        asm volatile("st.shared::cluster.v4.f32 [%0], {%1,%2,%3,%4};"
+                     :: "r"(a), "f"(b.v.x), "f"(b.v.y), "f"(b.v.z), "f"(b.w.x) : "memory");
+        asm volatile("st.shared::cluster.v2.f32 [%0], {%1,%2};" :: "r"(c), "f"(b.w.y), "f"(b.w.z) : "memory");
+    }
+};
+
+template <class S>
+__device__ __forceinline__ void load_pair(const S &st, int slots, float4 m, Body &A, Body &B) {
+    const int sa = slot_a(slots), sb = slot_b(slots);
+    if (sa >= 0) st.load(sa, A); else { A.v = make_float3(0.f, 0.f, 0.f); A.w = A.v; }
+    if (sb >= 0) st.load(sb, B); else { B.v = make_float3(0.f, 0.f, 0.f); B.w = B.v; }
+    A.im = m.x; B.im = m.y; A.ii = m.z; B.ii = m.w;
 }
 
-// apply impulse vector lambda (n, t1, t2 components) of a contact
+template <class S>
+__device__ __forceinline__ void store_pair(const S &st, int slots, const Body &A, const Body &B) {
+    const int sa = slot_a(slots), sb = slot_b(slots);
+    if (sa >= 0) st.store(sa, A);
+    if (sb >= 0) st.store(sb, B);
+}
+
+// ---- rows ----------------------------------------------------------------
+// impulses (n, t1, t2) components (ln, l1, l2) of a contact
 __device__ __forceinline__ void contact_impulse(Body &A, Body &B, float3 n, float3 t1, float3 t2,
                                                 float ra, float rb, float ln, float l1, float l2) {
     float3 P = make_float3(n.x * ln + t1.x * l1 + t2.x * l2, n.y * ln + t1.y * l1 + t2.y * l2,
                            n.z * ln + t1.z * l1 + t2.z * l2);
-    axpy(A.v, -A.v.w, P);
-    axpy(B.v, B.v.w, P);
+    axpy(A.v, -A.im, P);
+    axpy(B.v, B.im, P);
     // angular: -(r_A x P) on a, (r_B x P) on b with r_A = r_a n, r_B = -r_b n
     float3 L = make_float3(t1.x * l2 - t2.x * l1, t1.y * l2 - t2.y * l1, t1.z * l2 - t2.z * l1);
-    axpy(A.w, A.w.w * ra, L);
-    axpy(B.w, B.w.w * rb, L);
+    axpy(A.w, A.ii * ra, L);
+    axpy(B.w, B.ii * rb, L);
 }
 
-__device__ __forceinline__ void contact_row(Body &A, Body &B, float4 r0, float4 r1, float4 r2,
+__device__ __forceinline__ void contact_row(Body &A, Body &B, float4 r0, float4 r1, float4 r2, float mu,
                                             float4 &lam) {
     const float3 n = f3(r0), t1 = f3(r1);
     const float kn = r0.w, kt = r1.w;
-    const float ra = r2.x, rb = r2.y, target = r2.z, mu = r2.w;
+    const float ra = r2.x, rb = r2.y, target = r2.z;
     const float3 t2 = cross3(n, t1);
     // normal row
     float3 dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
-    float wn = dot3(n, dv);
-    float ln = fmaxf(lam.x + kn * (target - wn), 0.f);
+    float ln = fmaxf(lam.x + kn * (target - dot3(n, dv)), 0.f);
     float d = ln - lam.x;
     lam.x = ln;
-    axpy(A.v, -A.v.w * d, n);
-    axpy(B.v, B.v.w * d, n);
+    axpy(A.v, -A.im * d, n);
+    axpy(B.v, B.im * d, n);
     const float lim = mu * ln;
     // first tangent
     dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
@@ -93,10 +155,10 @@ __device__ __forceinline__ void contact_row(Body &A, Body &B, float4 r0, float4 
     float l1 = fminf(fmaxf(lam.y - kt * wt, -lim), lim);
     d = l1 - lam.y;
     lam.y = l1;
-    axpy(A.v, -A.v.w * d, t1);
-    axpy(B.v, B.v.w * d, t1);
-    axpy(A.w, -A.w.w * ra * d, t2);
-    axpy(B.w, -B.w.w * rb * d, t2);
+    axpy(A.v, -A.im * d, t1);
+    axpy(B.v, B.im * d, t1);
+    axpy(A.w, -A.ii * ra * d, t2);
+    axpy(B.w, -B.ii * rb * d, t2);
     // second tangent
     dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
     u = make_float3(ra * A.w.x + rb * B.w.x, ra * A.w.y + rb * B.w.y, ra * A.w.z + rb * B.w.z);
@@ -104,14 +166,14 @@ __device__ __forceinline__ void contact_row(Body &A, Body &B, float4 r0, float4 
     float l2 = fminf(fmaxf(lam.z - kt * wt, -lim), lim);
     d = l2 - lam.z;
     lam.z = l2;
-    axpy(A.v, -A.v.w * d, t2);
-    axpy(B.v, B.v.w * d, t2);
-    axpy(A.w, A.w.w * ra * d, t1);
-    axpy(B.w, B.w.w * rb * d, t1);
+    axpy(A.v, -A.im * d, t2);
+    axpy(B.v, B.im * d, t2);
+    axpy(A.w, A.ii * ra * d, t1);
+    axpy(B.w, B.ii * rb * d, t1);
 }
 
 __device__ __forceinline__ float joint_w(const Body &A, const Body &B, float3 rA, float3 rB, int ax) {
-    float3 ca = cross3(f3(A.w), rA), cb = cross3(f3(B.w), rB);
+    float3 ca = cross3(A.w, rA), cb = cross3(B.w, rB);
     float3 rel = make_float3(B.v.x + cb.x - A.v.x - ca.x, B.v.y + cb.y - A.v.y - ca.y,
                              B.v.z + cb.z - A.v.z - ca.z);
     return ax == 0 ? rel.x : (ax == 1 ? rel.y : rel.z);
@@ -120,22 +182,26 @@ __device__ __forceinline__ float joint_w(const Body &A, const Body &B, float3 rA
 // impulse d along world axis ax at the pivot
 __device__ __forceinline__ void joint_impulse(Body &A, Body &B, float3 rA, float3 rB, int ax, float d) {
     float3 e = make_float3(ax == 0 ? d : 0.f, ax == 1 ? d : 0.f, ax == 2 ? d : 0.f);
-    axpy(A.v, -A.v.w, e);
-    axpy(B.v, B.v.w, e);
-    axpy(A.w, -A.w.w, cross3(rA, e));
-    axpy(B.w, B.w.w, cross3(rB, e));
+    axpy(A.v, -A.im, e);
+    axpy(B.v, B.im, e);
+    axpy(A.w, -A.ii, cross3(rA, e));
+    axpy(B.w, B.ii, cross3(rB, e));
 }
 
-__device__ __forceinline__ void joint_rows(Body &A, Body &B, float4 r0, float4 r1, float4 r2,
-                                           float4 &lam) {
+// k_kk = 1 / (1/m_a + 1/m_b + |r_A x e_k|^2 / I_a + |r_B x e_k|^2 / I_b)
+__device__ __forceinline__ float joint_k(const Body &A, const Body &B, float3 rA, float3 rB, int ax) {
+    float a2 = ax == 0 ? rA.y * rA.y + rA.z * rA.z : (ax == 1 ? rA.x * rA.x + rA.z * rA.z : rA.x * rA.x + rA.y * rA.y);
+    float b2 = ax == 0 ? rB.y * rB.y + rB.z * rB.z : (ax == 1 ? rB.x * rB.x + rB.z * rB.z : rB.x * rB.x + rB.y * rB.y);
+    return 1.0f / (A.im + B.im + A.ii * a2 + B.ii * b2);
+}
+
+__device__ __forceinline__ void joint_rows(Body &A, Body &B, float4 r0, float4 r1, float4 r2, float4 &lam) {
     const float3 rA = f3(r0), rB = f3(r1);
-    float k[3] = {r2.x, r2.y, r2.z};
-    float t[3] = {r0.w, r1.w, r2.w};
+    float t[3] = {r0.w, r1.w, r2.x};
     float l[3] = {lam.x, lam.y, lam.z};
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        float w = joint_w(A, B, rA, rB, ax);
-        float d = k[ax] * (t[ax] - w);
+        float d = joint_k(A, B, rA, rB, ax) * (t[ax] - joint_w(A, B, rA, rB, ax));
         l[ax] += d;
         joint_impulse(A, B, rA, rB, ax, d);
     }
@@ -144,13 +210,13 @@ __device__ __forceinline__ void joint_rows(Body &A, Body &B, float4 r0, float4 r
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 
-// residual (lambda - clamp(lambda + k (target - w), lo, hi)) / k of a
-// contact's three rows, squared and summed; *mx gets the largest magnitude
+// residual (lambda - clamp(lambda + k (target - w), lo, hi)) / k of a row
+// group, squared and summed
 __device__ __forceinline__ float contact_residual_sq(const Body &A, const Body &B, float4 r0, float4 r1,
-                                                     float4 r2, float4 lam, float *mx) {
+                                                     float4 r2, float mu, float4 lam) {
     const float3 n = f3(r0), t1 = f3(r1);
     const float kn = r0.w, kt = r1.w;
-    const float ra = r2.x, rb = r2.y, target = r2.z, mu = r2.w;
+    const float ra = r2.x, rb = r2.y, target = r2.z;
     const float3 t2 = cross3(n, t1);
     float3 dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
     float3 u = make_float3(ra * A.w.x + rb * B.w.x, ra * A.w.y + rb * B.w.y, ra * A.w.z + rb * B.w.z);
@@ -159,22 +225,19 @@ __device__ __forceinline__ float contact_residual_sq(const Body &A, const Body &
     float e0 = (lam.x - fmaxf(lam.x + kn * (target - wn), 0.f)) / kn;
     float e1 = (lam.y - clampf(lam.y - kt * w1, -lim, lim)) / kt;
     float e2 = (lam.z - clampf(lam.z - kt * w2, -lim, lim)) / kt;
-    *mx = fmaxf(*mx, fmaxf(fabsf(e0), fmaxf(fabsf(e1), fabsf(e2))));
     return e0 * e0 + e1 * e1 + e2 * e2;
 }
 
 __device__ __forceinline__ float joint_residual_sq(const Body &A, const Body &B, float4 r0, float4 r1,
-                                                   float4 r2, float4 lam, float *mx) {
+                                                   float4 r2) {
     const float3 rA = f3(r0), rB = f3(r1);
-    float t[3] = {r0.w, r1.w, r2.w};
+    float t[3] = {r0.w, r1.w, r2.x};
     float s = 0.f;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        float e = -(t[ax] - joint_w(A, B, rA, rB, ax));   // (lam - (lam + k (t - w))) / k
-        *mx = fmaxf(*mx, fabsf(e));
+        float e = joint_w(A, B, rA, rB, ax) - t[ax];   // (lam - (lam + k (t - w))) / k
         s += e * e;
     }
-    (void)lam;
     return s;
 }
 
@@ -188,127 +251,131 @@ __device__ float block_sum(float v, float *red) {
     return s;
 }
 
-template <bool SHARED>
-__device__ void solve_worker(const SolveArgs &a, float4 *vel, float4 *ang) {
+template <int C>
+__device__ __forceinline__ void group_sync() {
+    if (C == 1) __syncthreads();
+    else cg::this_cluster().sync();
+}
+
+// group-wide sum of one value per thread (every thread gets the total)
+template <int C>
+__device__ float group_sum(float v, float *red, float *slot) {
+    float t = block_sum(v, red);
+    if (C == 1) return t;
+    if (threadIdx.x == 0) *slot = t;
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    float tot = 0.f;
+    for (int r = 0; r < C; ++r) tot += *cl.map_shared_rank(slot, r);
+    cl.sync();
+    return tot;
+}
+
+template <class S>
+__device__ float rows_residual_sq(const SolveArgs &a, const S &st, const int *off, int ncol, float mu,
+                                  int g, int G) {
+    float sq = 0.f;
+    for (int c = 0; c < ncol; ++c) {
+        const int jb = off[2 * c + 1], ce = off[2 * c + 2];
+        for (int r = off[2 * c] + g; r < ce; r += G) {
+            float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r], m = a.r3[r], lam = a.rlam[r];
+            Body A, B;
+            int slots = __float_as_int(r2.w);
+            load_pair(st, slots, m, A, B);
+            sq += r < jb ? contact_residual_sq(A, B, r0, r1, r2, mu, lam) : joint_residual_sq(A, B, r0, r1, r2);
+        }
+    }
+    return sq;
+}
+
+// One worker solved by a group of C CTAs; threads are numbered g = rank T + tid
+// and in every colour thread g takes rows off + g, off + g + G, ... (G = C T).
+template <int C, class S>
+__device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank) {
     __shared__ float red[32];
-    __shared__ int stop_flag;
-    const int p = blockIdx.x;
+    __shared__ float part_sum;
     const int tid = threadIdx.x, T = blockDim.x;
+    const int g = rank * T + tid, G = C * T;
     const int b0 = a.part_bstart[p], nb = a.part_bstart[p + 1] - b0;
     const int scene = a.part_scene[p];
     const float h = a.dt_override > 0.f ? a.dt_override : a.scene_dt[scene];
-    // velocities after the external force (h f), from the blended state
-    for (int s = tid; s < nb; s += T) {
+    const float mu = a.scene_mu[scene];
+    // velocities after the external force (h f), from the blended state; each
+    // CTA loads the slots it holds
+    for (int s = rank + C * tid; s < nb; s += C * T) {
         int b = a.entry_body[a.part_list[b0 + s]];
         float4 v = a.st[4 * b + 2], w = a.st[4 * b + 3];
-        vel[s] = make_float4(v.x + h * a.gravity.x, v.y + h * a.gravity.y, v.z + h * a.gravity.z, v.w);
-        ang[s] = w;
+        Body x;
+        x.v = make_float3(v.x + h * a.gravity.x, v.y + h * a.gravity.y, v.z + h * a.gravity.z);
+        x.w = make_float3(w.x, w.y, w.z);
+        st.store(s, x);
     }
-    __syncthreads();
+    group_sync<C>();
     const int ncol = a.part_ncol[p];
     const int *off = a.col_off + (size_t)p * NB1;
     // warm start: apply the previous impulses, colour by colour
     for (int c = 0; c < ncol; ++c) {
-        const int cb = off[2 * c], jb = off[2 * c + 1], je = off[2 * c + 2];
-        for (int r = cb + tid; r < jb; r += T) {
+        const int jb = off[2 * c + 1], ce = off[2 * c + 2];
+        for (int r = off[2 * c] + g; r < ce; r += G) {
             float4 lam = a.rlam[r];
             if (lam.x == 0.f && lam.y == 0.f && lam.z == 0.f) continue;
-            float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r];
-            int4 r3 = a.r3[r];
-            Body A = load_body(vel, ang, r3.x), B = load_body(vel, ang, r3.y);
-            float3 n = f3(r0), t1 = f3(r1);
-            contact_impulse(A, B, n, t1, cross3(n, t1), r2.x, r2.y, lam.x, lam.y, lam.z);
-            store_body(vel, ang, r3.x, A);
-            store_body(vel, ang, r3.y, B);
+            float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r], m = a.r3[r];
+            int slots = __float_as_int(r2.w);
+            Body A, B;
+            load_pair(st, slots, m, A, B);
+            if (r < jb) {
+                float3 n = f3(r0), t1 = f3(r1);
+                contact_impulse(A, B, n, t1, cross3(n, t1), r2.x, r2.y, lam.x, lam.y, lam.z);
+            } else {
+                joint_impulse(A, B, f3(r0), f3(r1), 0, lam.x);
+                joint_impulse(A, B, f3(r0), f3(r1), 1, lam.y);
+                joint_impulse(A, B, f3(r0), f3(r1), 2, lam.z);
+            }
+            store_pair(st, slots, A, B);
         }
-        for (int r = jb + tid; r < je; r += T) {
-            float4 lam = a.rlam[r];
-            float4 r0 = a.r0[r], r1 = a.r1[r];
-            int4 r3 = a.r3[r];
-            Body A = load_body(vel, ang, r3.x), B = load_body(vel, ang, r3.y);
-            joint_impulse(A, B, f3(r0), f3(r1), 0, lam.x);
-            joint_impulse(A, B, f3(r0), f3(r1), 1, lam.y);
-            joint_impulse(A, B, f3(r0), f3(r1), 2, lam.z);
-            store_body(vel, ang, r3.x, A);
-            store_body(vel, ang, r3.y, B);
-        }
-        __syncthreads();
+        group_sync<C>();
     }
     // Gauss-Seidel sweeps
     int it_done = 0;
-    if (tid == 0) stop_flag = 0;
     for (int it = 0; it < a.iters; ++it) {
         for (int c = 0; c < ncol; ++c) {
-            const int cb = off[2 * c], jb = off[2 * c + 1], je = off[2 * c + 2];
-            for (int r = cb + tid; r < jb; r += T) {
-                float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r];
-                int4 r3 = a.r3[r];
-                float4 lam = a.rlam[r];
-                Body A = load_body(vel, ang, r3.x), B = load_body(vel, ang, r3.y);
-                contact_row(A, B, r0, r1, r2, lam);
-                store_body(vel, ang, r3.x, A);
-                store_body(vel, ang, r3.y, B);
+            const int jb = off[2 * c + 1], ce = off[2 * c + 2];
+            for (int r = off[2 * c] + g; r < ce; r += G) {
+                float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r], m = a.r3[r], lam = a.rlam[r];
+                int slots = __float_as_int(r2.w);
+                Body A, B;
+                load_pair(st, slots, m, A, B);
+                if (r < jb) contact_row(A, B, r0, r1, r2, mu, lam);
+                else joint_rows(A, B, r0, r1, r2, lam);
+                store_pair(st, slots, A, B);
                 a.rlam[r] = lam;
             }
-            for (int r = jb + tid; r < je; r += T) {
-                float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r];
-                int4 r3 = a.r3[r];
-                float4 lam = a.rlam[r];
-                Body A = load_body(vel, ang, r3.x), B = load_body(vel, ang, r3.y);
-                joint_rows(A, B, r0, r1, r2, lam);
-                store_body(vel, ang, r3.x, A);
-                store_body(vel, ang, r3.y, B);
-                a.rlam[r] = lam;
-            }
-            __syncthreads();
+            group_sync<C>();
         }
         it_done = it + 1;
-        if (a.res_tol > 0.f && a.res_check_every > 0 && it_done % a.res_check_every == 0) {
-            float sq = 0.f, mx = 0.f;
-            const int rb_ = off[0], re_ = off[2 * ncol];
-            for (int r = rb_ + tid; r < re_; r += T) {
-                float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r];
-                int4 r3 = a.r3[r];
-                float4 lam = a.rlam[r];
-                Body A = load_body(vel, ang, r3.x), B = load_body(vel, ang, r3.y);
-                sq += r3.w == 0 ? contact_residual_sq(A, B, r0, r1, r2, lam, &mx)
-                                : joint_residual_sq(A, B, r0, r1, r2, lam, &mx);
-            }
-            float tot = block_sum(sq, red);
-            int nrows = 3 * (re_ - rb_);
-            if (tid == 0) stop_flag = (nrows == 0 || sqrtf(tot / nrows) <= a.res_tol) ? 1 : 0;
-            __syncthreads();
-            if (stop_flag) break;
+        if (a.res_tol > 0.f && a.res_check_every > 0 && it_done % a.res_check_every == 0 && it_done < a.iters) {
+            float tot = group_sum<C>(rows_residual_sq(a, st, off, ncol, mu, g, G), red, &part_sum);
+            int nrows = 3 * (off[2 * ncol] - off[0]);
+            if (nrows == 0 || sqrtf(tot / nrows) <= a.res_tol) break;   // the same total in every CTA
         }
     }
     // residual of every row at the final iterate
     if (a.flags & OVL_FLAG_RESIDUAL) {
-        float sq = 0.f, mx = 0.f;
-        const int rb_ = off[0], re_ = off[2 * ncol];
-        for (int r = rb_ + tid; r < re_; r += T) {
-            float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r];
-            int4 r3 = a.r3[r];
-            float4 lam = a.rlam[r];
-            Body A = load_body(vel, ang, r3.x), B = load_body(vel, ang, r3.y);
-            sq += r3.w == 0 ? contact_residual_sq(A, B, r0, r1, r2, lam, &mx)
-                            : joint_residual_sq(A, B, r0, r1, r2, lam, &mx);
-        }
-        float tot = block_sum(sq, red);
-        if (tid == 0) a.part_res_sq[p] = (double)tot;
+        float tot = group_sum<C>(rows_residual_sq(a, st, off, ncol, mu, g, G), red, &part_sum);
+        if (rank == 0 && tid == 0) a.part_res_sq[p] = (double)tot;
     }
-    if (tid == 0) a.part_iters[p] = it_done;
+    if (rank == 0 && tid == 0) a.part_iters[p] = it_done;
     // impulses back in canonical pair order (next step's warm start)
-    {
-        const int rb_ = off[0], re_ = off[2 * ncol];
-        for (int r = rb_ + tid; r < re_; r += T) a.lam_out[a.r3[r].z] = a.rlam[r];
-    }
+    for (int r = off[0] + g; r < off[2 * ncol]; r += G) a.lam_out[a.rpair[r]] = a.rlam[r];
     // integrate: x += h v; q <- normalise(q + h/2 (0, w) (x) q); write this
-    // worker's copy of each body
-    for (int s = tid; s < nb; s += T) {
+    // worker's copy of each body the CTA holds
+    for (int s = rank + C * tid; s < nb; s += C * T) {
         int e = a.part_list[b0 + s];
         int b = a.entry_body[e];
-        float4 x = a.st[4 * b], q = a.st[4 * b + 1];
-        float4 v = vel[s], w = ang[s];
+        float4 x = a.st[4 * b], q = a.st[4 * b + 1], v0 = a.st[4 * b + 2], w0 = a.st[4 * b + 3];
+        Body y;
+        st.load(s, y);
+        float3 v = y.v, w = y.w;
         float4 xn = make_float4(x.x + h * v.x, x.y + h * v.y, x.z + h * v.z, x.w);
         // (0, w) (x) q = (-w.qv, qw w + w x qv)
         float dqw = -(w.x * q.y + w.y * q.z + w.z * q.w);
@@ -321,33 +388,76 @@ __device__ void solve_worker(const SolveArgs &a, float4 *vel, float4 *ang) {
         qn = make_float4(qn.x / L, qn.y / L, qn.z / L, qn.w / L);
         a.copies[4 * (size_t)e] = xn;
         a.copies[4 * (size_t)e + 1] = qn;
-        a.copies[4 * (size_t)e + 2] = v;
-        a.copies[4 * (size_t)e + 3] = w;
+        a.copies[4 * (size_t)e + 2] = make_float4(v.x, v.y, v.z, v0.w);
+        a.copies[4 * (size_t)e + 3] = make_float4(w.x, w.y, w.z, w0.w);
     }
+    // no CTA may leave while another can still reach its shared memory
+    if (C > 1) group_sync<C>();
 }
 
-__global__ void k_solve(SolveArgs a) {
+// C CTAs per worker; a worker's slots are spread over their shared memory when
+// they fit (ceil(nb / C) <= smem_slots), else CTA rank 0 solves it alone with
+// its body state in the global scratch area.
+template <int C>
+__global__ void __launch_bounds__(SOLVE_THREADS, 2) k_solve(SolveArgs a) {
     extern __shared__ float4 sm[];
-    const int p = blockIdx.x;
+    const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
+    const int p = blockIdx.x / C;
     const int b0 = a.part_bstart[p], nb = a.part_bstart[p + 1] - b0;
-    if (nb <= a.smem_slots) {
-        solve_worker<true>(a, sm, sm + nb);
-    } else {
-        float4 *base = a.scratch + 2 * (size_t)b0;
-        solve_worker<false>(a, base, base + nb);
+    const int per = (nb + C - 1) / C;
+    if (nb >= 0xffff) {
+        if (rank == 0 && threadIdx.x == 0) atomicCAS(a.status, DEV_OK, DEV_ERR_CAPACITY);
+        return;
+    }
+    if (per <= a.smem_slots) {
+        float4 *A = sm;
+        float2 *B = reinterpret_cast<float2 *>(sm + per);
+        if (C == 1) {
+            LocalSlots st{A, B};
+            solve_worker<C>(a, st, p, rank);
+        } else {
+            ClusterSlots<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B)};
+            solve_worker<C>(a, st, p, rank);
+        }
+    } else if (rank == 0) {
+        LocalSlots st{a.scratch + (size_t)b0, reinterpret_cast<float2 *>(a.scratch + (size_t)a.n_entries) + b0};
+        solve_worker<1>(a, st, p, 0);
     }
 }
 
 }  // namespace
 
-int solve_smem_bytes(int slots) { return slots * 2 * (int)sizeof(float4); }
+int solve_smem_bytes(int slots) { return slots * (int)(sizeof(float4) + sizeof(float2)); }
 
-void launch_solve(const SolveArgs &a, int threads, cudaStream_t s) {
-    if (!a.n_parts) return;
+template <int C>
+static void launch_solve_c(const SolveArgs &a, int threads, cudaStream_t s) {
     int smem = solve_smem_bytes(a.smem_slots);
-    CK(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_solve<<<a.n_parts, threads, smem, s>>>(a);
+    CK(cudaFuncSetAttribute(k_solve<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.n_parts * C);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k_solve<C>, a));
     note_launch();
+}
+
+void launch_solve(const SolveArgs &a, int threads, int cluster, cudaStream_t s) {
+    if (!a.n_parts) return;
+    if (threads > SOLVE_THREADS) threads = SOLVE_THREADS;
+    switch (cluster) {
+        case 8: launch_solve_c<8>(a, threads, s); break;
+        case 4: launch_solve_c<4>(a, threads, s); break;
+        case 2: launch_solve_c<2>(a, threads, s); break;
+        default: launch_solve_c<1>(a, threads, s); break;
+    }
     CK(cudaGetLastError());
 }
 

@@ -220,7 +220,18 @@ __global__ void k_fill_u8(uint8_t *p, uint8_t v, size_t n) {
 __global__ void k_iota(uint32_t *p, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = (uint32_t)i;
 }
-__global__ void k_hist(const int *key, int n, int *counts) {
+// bins privatised in shared memory (nbins <= 12288), one global add per bin and block
+__global__ void k_hist(const int *key, int n, int *counts, int nbins) {
+    extern __shared__ int h[];
+    for (int j = threadIdx.x; j < nbins; j += blockDim.x) h[j] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&h[key[i]], 1);
+    __syncthreads();
+    for (int j = threadIdx.x; j < nbins; j += blockDim.x)
+        if (h[j]) atomicAdd(&counts[j], h[j]);
+}
+__global__ void k_hist_global(const int *key, int n, int *counts) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         atomicAdd(&counts[key[i]], 1);
 }
@@ -250,9 +261,15 @@ void iota_u32(uint32_t *p, int n, cudaStream_t s) {
     note_launch();
     CK(cudaGetLastError());
 }
-void histogram_i32(const int *key, int n, int *counts, cudaStream_t s) {
+void histogram_i32(const int *key, int n, int *counts, int nbins, cudaStream_t s) {
     if (!n) return;
-    k_hist<<<grid_for((size_t)n, 256), 256, 0, s>>>(key, n, counts);
+    if (nbins <= 12288) {
+        int g = grid_for((size_t)n, 256);
+        if (g > 304) g = 304;
+        k_hist<<<g, 256, (size_t)nbins * sizeof(int), s>>>(key, n, counts, nbins);
+    } else {
+        k_hist_global<<<grid_for((size_t)n, 256), 256, 0, s>>>(key, n, counts);
+    }
     note_launch();
     CK(cudaGetLastError());
 }

@@ -43,6 +43,10 @@ void launch_edge_degree(const int2 *c_ab, int nc, const int2 *jab, int nj, const
 void launch_edge_fill(const int2 *c_ab, int nc, const int2 *jab, int nj, const float *im, int n,
                       const int *tptr, int *cursor, int *tcol, cudaStream_t s);
 void launch_adj_unique(const int *tptr, int n, int *tcol, int *ucount, cudaStream_t s);
+void launch_lb_flags(const int2 *c_ab, int nc, const float *im, int n, const uint64_t *mask,
+                     int disjoint_only, int *flag, cudaStream_t s);
+void launch_lb_compact(const int2 *c_ab, int nc, const int *flag, const int *pos, int2 *out,
+                       cudaStream_t s);
 void launch_adj_compact(const int *tptr, const int *tcol, int n, const int *row_ptr, int *col,
                         cudaStream_t s);
 
@@ -104,6 +108,8 @@ struct ColourArgs {
     int *col_off;              // [P][2*OVL_MAX_COLOURS+1] absolute row offsets per (colour, kind)
     int *pair_of_row;          // [np]
     unsigned long long *scratch;  // 3 per entry, for workers too large for shared memory
+    int4 *worklist, *worklist2;                 // [np] each: uncoloured constraints per round
+    unsigned long long *wprio, *wprio2;         // [np] each: their priorities
     int smem_slots;            // slots that fit in shared memory
     int *status;
 };
@@ -129,9 +135,10 @@ struct RowArgs {
     const float *scene_mu;
     float dt_override;
     float erp, slop;
-    float4 *r0, *r1, *r2;
-    int4 *r3;
+    float4 *r0, *r1, *r2, *r3;
+    int *rpair;                // [np] pair index of every row (canonical order)
     float4 *rlam;
+    int *status;
 };
 void launch_rows(const RowArgs &a, cudaStream_t s);
 
@@ -148,12 +155,14 @@ struct SolveArgs {
     float dt_override;
     float3 gravity;
     const float4 *st;
-    const float4 *r0, *r1, *r2;
-    const int4 *r3;
+    const float *scene_mu;
+    const float4 *r0, *r1, *r2, *r3;
+    const int *rpair;
     float4 *rlam;
+    int n_entries;
     float4 *lam_out;           // [np] canonical pair order
     float4 *copies;            // [ne][4]
-    float4 *scratch;           // [ne][2] velocities of workers too large for shared memory
+    float4 *scratch;           // [ne] float4 + [ne] float2: velocities of workers too large for shared memory
     int iters;
     int smem_slots;
     int flags;                 // OVL_FLAG_*
@@ -163,7 +172,7 @@ struct SolveArgs {
     double *part_res_sq;       // [P]
     int *status;
 };
-void launch_solve(const SolveArgs &a, int threads, cudaStream_t s);
+void launch_solve(const SolveArgs &a, int threads, int cluster, cudaStream_t s);
 int solve_smem_bytes(int slots);
 
 // ---- geodesics, weights, blend (k_blend.cu) --------------------------------

@@ -48,7 +48,8 @@ class ovl_params(C.Structure):
     _fields_ = [("gravity", C.c_float * 3), ("margin", C.c_float), ("erp", C.c_float),
                 ("slop", C.c_float), ("warmstart", C.c_float), ("lb_activate", C.c_int32),
                 ("lb_deact_every", C.c_int32), ("res_tol", C.c_float),
-                ("res_check_every", C.c_int32), ("pgs_threads", C.c_int32), ("flags", C.c_int32)]
+                ("res_check_every", C.c_int32), ("pgs_threads", C.c_int32), ("flags", C.c_int32),
+                ("pgs_cluster", C.c_int32), ("smem_slot_limit", C.c_int32)]
 
 
 _fp, _ip, _u64p, _u8p = C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint8)

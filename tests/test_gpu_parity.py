@@ -27,6 +27,17 @@ def test_pile_small(warm):
     assert rep["contacts"] > 600
 
 
+@pytest.mark.parametrize("cluster,limit", [(1, 0), (2, 0), (4, 0), (8, 0), (1, 16), (4, 16), (2, 40), (8, 20)])
+def test_solver_paths(cluster, limit):
+    """Every solver path: one CTA, clusters of 2 and 4 CTAs with the body state
+    spread over their shared memory, and the global-memory path for workers
+    above the shared-memory limit (also the colouring's scratch path)."""
+    P = _parity()
+    orc, gpu = P.prepare(S.pile_small(), warm_steps=3,
+                         gpu_params=dict(pgs_cluster=cluster, smem_slot_limit=limit))
+    P.compare_step(orc, gpu)
+
+
 @pytest.mark.parametrize("warm", [0, 3])
 def test_chain(warm):
     P = _parity()
