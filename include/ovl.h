@@ -68,6 +68,8 @@ typedef struct ovl_params {
 
 #define OVL_FLAG_RESIDUAL 1  /* compute the complementarity residual of every row after the sweeps */
 #define OVL_FLAG_TIMING 2    /* record per-phase times with CUDA events (ovl_read_stats) */
+#define OVL_FLAG_AUTOTUNE 4  /* time the solver's launch shapes on the first step of every problem-size
+                                bucket and keep the fastest (results are bit-identical across shapes) */
 
 /* A scene (or a batch of independent scenes whose bodies are contiguous). */
 typedef struct ovl_scene_desc {
@@ -107,6 +109,12 @@ typedef struct ovl_stats {
     double residual_max;       /* max |residual| */
     float phase_ms[12];        /* per-phase device times (OVL_FLAG_TIMING); see ovl_phase_name */
     int64_t n_launches;        /* CUDA kernels the library launched during the last step */
+    int32_t solve_cluster;     /* CTAs per worker of the last solve */
+    int32_t solve_threads;     /* threads per CTA of the last solve */
+    int32_t solve_rows_per_thread; /* rows a thread takes at once in a colour (colour block) */
+    int32_t colour_rounds_max; /* most colouring rounds any worker needed */
+    int64_t lb_candidates;     /* contacts handed to the host load balance in the last step */
+    double lb_host_ms;         /* host time of the load balance in the last step (copies included) */
 } ovl_stats;
 
 /* Fills *p with the defaults listed in ovl_params. */
@@ -188,6 +196,14 @@ ovl_status ovl_read_entries(ovl_ctx *ctx, int32_t *entry_ptr, int32_t *part, uin
                             float *weight, float *copies13);
 ovl_status ovl_read_pairs(ovl_ctx *ctx, int32_t *part, uint64_t *key, int32_t *colour,
                           float *lambda3);
+/* Autotuner cache (OVL_FLAG_AUTOTUNE) as JSON text, one entry per problem-size
+ * bucket: {"P64_nb16384_q65536": {"cluster": 2, "threads": 512, "rows_per_thread": 2, "ms": 3.9}}.
+ * export: writes at most cap bytes (NUL-terminated) and the full length to *len.
+ * import: merges entries produced by export.  No counterpart in the paper:
+ * this is the launch-shape tuner of the GPU solver. */
+ovl_status ovl_autotune_export(ovl_ctx *ctx, char *buf, size_t cap, size_t *len);
+ovl_status ovl_autotune_import(ovl_ctx *ctx, const char *json);
+
 /* Per worker: sweeps run, residual sum of squares, rows, colours. */
 ovl_status ovl_read_worker_stats(ovl_ctx *ctx, int32_t *iters, double *res_sq, int64_t *rows,
                                  int32_t *colours);

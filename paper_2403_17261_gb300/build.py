@@ -20,6 +20,10 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libovl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The solver is compiled without fused multiply-add contraction so that every
+# launch shape (CTAs per worker, threads, rows per thread) executes the same
+# IEEE operations and produces the same bits.
+PER_FILE_FLAGS = {"k_solve.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -54,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, "-c", src, "-o", obj] + common
+        cmd = [nvcc, "-c", src, "-o", obj] + common + PER_FILE_FLAGS.get(os.path.basename(src), [])
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")

@@ -20,7 +20,7 @@
 
 #include "../../include/ovl.h"
 
-#define OVL_MAX_COLOURS 128
+#define OVL_MAX_COLOURS 64
 #define OVL_MAX_NEIGH 32   // sphere neighbours with larger index gathered per body in one pass
 
 // device status codes (first error wins)

@@ -4,9 +4,12 @@
 // entries, pairs) are read back between phases; the load balance runs on the
 // host between the graph and the membership phases.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <exception>
+#include <map>
+#include <sstream>
 #include <stdexcept>
 #include <numeric>
 #include <string>
@@ -26,7 +29,9 @@ struct ovl_ctx {
     int num_sms = 0;
     int smem_per_sm = 0;
     int nb_max = 0;          // most bodies in one worker (last membership phase)
-    int last_cluster = 1;
+    int last_cluster = 1, last_threads = 512, last_unroll = 1;
+    struct TuneCfg { int cluster, threads, unroll; float ms; };
+    std::map<std::string, TuneCfg> tuned;   // autotuner results by problem-size bucket
     std::string err;
 
     // scene (host copies)
@@ -61,7 +66,7 @@ struct ovl_ctx {
         part_bstart;
     DBuf<uint32_t> sk, sv, sk2, sv2;
     DBuf<int> cons_count, cons_start, pair_cons, pair_part, ps_cons, ps_part, part_pcount,
-        part_pstart, p_colour, part_ncol, col_off, pair_of_row;
+        part_pstart, p_colour, part_ncol, part_rounds, col_off, pair_of_row;
     DBuf<uint64_t> p_key;
     DBuf<int2> p_slot;
     DBuf<float4> p_lam0;
@@ -99,6 +104,8 @@ struct ovl_ctx {
     cudaEvent_t ev[16] = {};
     float phase_ms[12] = {};
     long long last_launches = 0;
+    long long lb_candidates = 0;
+    double lb_host_ms = 0.0;
 };
 
 namespace {
@@ -224,6 +231,8 @@ void phase_graph(ovl_ctx *c) {
 // canonical order.  The GPU first compacts the contacts that can act: all
 // dynamic pairs on removal steps, only worker-disjoint pairs otherwise.
 void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
+    c->lb_candidates = 0;
+    c->lb_host_ms = 0.0;
     if ((!act && !deact) || c->nc == 0) return;
     cudaStream_t s = c->stream;
     const int n = c->n;
@@ -233,7 +242,9 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
     launch_lb_flags(c->c_ab.p, c->nc, c->im.p, n, c->mask.p, deact ? 0 : 1, c->lb_flag.p, s);
     scan_i32(c->lb_flag.p, c->lb_pos.p, c->nc, c->scan_tmp, s);
     const int m = read_i32(c, c->lb_pos.p + c->nc);
+    c->lb_candidates = m;
     if (m == 0) return;
+    const auto t0 = std::chrono::steady_clock::now();
     launch_lb_compact(c->c_ab.p, c->nc, c->lb_flag.p, c->lb_pos.p, c->lb_pairs.p, s);
     c->h_ab.ensure(m + 1);
     c->h_rp.ensure((size_t)n + 1);
@@ -256,6 +267,7 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
     std::copy(c->lb_mask.begin(), c->lb_mask.end(), c->h_mask.p);
     CK(cudaMemcpyAsync(c->mask.p, c->h_mask.p, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
+    c->lb_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
 MemberArgs member_args(ovl_ctx *c) {
@@ -340,10 +352,25 @@ void phase_membership(ovl_ctx *c, float dt_override) {
     launch_pair_setup(a, w, npr, s);
 }
 
-int colour_smem_slots(ovl_ctx *c) {
-    int avail = c->smem_optin - 20 * 1024;
-    int n = std::max(0, avail / 24);
+int colour_smem_capacity(ovl_ctx *c) {
+    int avail = c->smem_optin - 24 * 1024;   // the kernel's static shared memory is below 20 KB
+    int n = std::max(0, avail / 16);
     return c->P.smem_slot_limit > 0 ? std::min(n, c->P.smem_slot_limit) : n;
+}
+
+// CTAs per worker for the colouring: the smallest cluster whose share of the
+// largest worker's slots fits one CTA's shared memory (16 B per slot)
+void colour_config(ovl_ctx *c, int *cluster, int *slots) {
+    const int cap = colour_smem_capacity(c);
+    const int fixed = (c->P.pgs_cluster == 1 || c->P.pgs_cluster == 2 || c->P.pgs_cluster == 4 ||
+                       c->P.pgs_cluster == 8) ? c->P.pgs_cluster : 0;
+    for (int C = 1; C <= 8; C <<= 1) {
+        if (fixed && C != fixed) continue;
+        int per = std::max(1, (c->nb_max + C - 1) / C);
+        if (per <= cap) { *cluster = C; *slots = per; return; }
+    }
+    *cluster = fixed ? fixed : 1;
+    *slots = cap;
 }
 
 // Shared-memory body slots per CTA (24 B each) for 1 or 2 resident CTAs per SM
@@ -357,9 +384,10 @@ void phase_colour(ovl_ctx *c) {
     const int P = c->n_parts, npr = c->npairs;
     c->p_colour.ensure(npr + 1);
     c->part_ncol.ensure((size_t)P + 1);
+    c->part_rounds.ensure((size_t)P + 1);
     c->col_off.ensure((size_t)P * (2 * OVL_MAX_COLOURS + 1) + 1);
     c->pair_of_row.ensure(npr + 1);
-    c->colour_scratch.ensure(3 * (size_t)c->ne + 1);
+    c->colour_scratch.ensure(2 * (size_t)c->ne + 1);
     c->worklist.ensure(npr + 1);
     c->worklist2.ensure(npr + 1);
     c->wprio.ensure(npr + 1);
@@ -368,10 +396,13 @@ void phase_colour(ovl_ctx *c) {
     a.n_parts = P; a.part_bstart = c->part_bstart.p; a.part_pstart = c->part_pstart.p;
     a.p_key = c->p_key.p; a.p_slot = c->p_slot.p; a.p_colour = c->p_colour.p;
     a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p; a.pair_of_row = c->pair_of_row.p;
-    a.scratch = c->colour_scratch.p; a.smem_slots = colour_smem_slots(c); a.status = c->status.p;
+    a.part_rounds = c->part_rounds.p;
+    int cluster = 1, slots = 0;
+    colour_config(c, &cluster, &slots);
+    a.scratch = c->colour_scratch.p; a.smem_slots = slots; a.status = c->status.p;
     a.worklist = c->worklist.p; a.worklist2 = c->worklist2.p;
     a.wprio = c->wprio.p; a.wprio2 = c->wprio2.p;
-    launch_colour(a, c->stream);
+    launch_colour(a, cluster, c->stream);
 }
 
 void phase_rows(ovl_ctx *c, float dt_override) {
@@ -395,11 +426,18 @@ void phase_rows(ovl_ctx *c, float dt_override) {
 // CTAs per SM (the largest worker's share fits half an SM's shared memory),
 // then with one CTA per SM, so no worker waits for a second wave; otherwise
 // the smallest C whose share fits one CTA.  A fixed pgs_cluster overrides C.
-void solve_config(ovl_ctx *c, int *cluster, int *slots) {
+void solve_config(ovl_ctx *c, int *cluster, int *slots, int *unroll) {
+    *unroll = 1;
     const int nbmax = c->nb_max;
     const int cap2 = solve_slot_capacity(c, 2), cap1 = solve_slot_capacity(c, 1);
     const int fixed = (c->P.pgs_cluster == 1 || c->P.pgs_cluster == 2 || c->P.pgs_cluster == 4 ||
                        c->P.pgs_cluster == 8) ? c->P.pgs_cluster : 0;
+    // one resident CTA per SM with two rows per thread was the fastest shape
+    // measured on the large pile; fall back to the others in order
+    if (!fixed || fixed == 2) {
+        const int per = (nbmax + 1) / 2;
+        if (per <= cap1 && 2ll * c->n_parts <= c->num_sms) { *cluster = 2; *slots = std::max(per, 1); *unroll = 2; return; }
+    }
     for (int pass = 0; pass < 2; ++pass)
         for (int C = 1; C <= 8; C <<= 1) {
             if (fixed && C != fixed) continue;
@@ -425,6 +463,66 @@ int solve_threads(ovl_ctx *c) {
     return t;
 }
 
+SolveArgs solve_args(ovl_ctx *c, float dt_override, int iters) {
+    SolveArgs a{};
+    a.n_parts = c->n_parts; a.part_bstart = c->part_bstart.p; a.part_list = c->part_list.p;
+    a.entry_body = c->entry_body.p; a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p;
+    a.part_scene = c->part_scene.p; a.scene_dt = c->scene_dt.p; a.dt_override = dt_override;
+    a.gravity = make_float3(c->P.gravity[0], c->P.gravity[1], c->P.gravity[2]);
+    a.st = c->st.p; a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
+    a.rpair = c->rpair.p; a.scene_mu = c->scene_mu.p; a.n_entries = c->ne;
+    a.lam_out = c->lam_out.p; a.copies = c->copies.p; a.scratch = c->solve_scratch.p;
+    a.iters = iters; a.flags = c->P.flags;
+    a.res_tol = c->P.res_tol; a.res_check_every = c->P.res_check_every;
+    a.part_iters = c->part_iters.p; a.part_res_sq = c->part_res_sq.p; a.status = c->status.p;
+    return a;
+}
+
+// problem-size bucket of the autotuner: the number of workers and the largest
+// worker's body count rounded up to a power of four
+std::string tune_key(ovl_ctx *c) {
+    int b = 1;
+    while (b < c->nb_max) b <<= 2;
+    std::ostringstream k;
+    k << "P" << c->n_parts << "_nb" << b;
+    return k.str();
+}
+
+// shared-memory slots for a cluster size (the largest worker's share), or 0
+// if that share does not fit one CTA
+int solve_slots_for(ovl_ctx *c, int cluster) {
+    int per = std::max(1, (c->nb_max + cluster - 1) / cluster);
+    return per <= solve_slot_capacity(c, 1) ? per : 0;
+}
+
+// K13: time every feasible (CTAs per worker, threads per CTA, rows per thread
+// and colour step) on this step's rows and keep the fastest for the bucket.
+// Rows of one colour are independent, so every candidate computes the same
+// bits; re-running the row build restores the warm-start impulses.
+void autotune(ovl_ctx *c, float dt_override, int iters, const std::string &key) {
+    cudaStream_t s = c->stream;
+    ovl_ctx::TuneCfg best{0, 0, 0, 1e30f};
+    cudaEvent_t e0 = c->ev[10], e1 = c->ev[11];
+    for (int cl : {1, 2, 4, 8})
+        for (int th : {256, 512})
+            for (int un : {1, 2}) {
+                int slots = solve_slots_for(c, cl);
+                if (!slots) continue;
+                SolveArgs a = solve_args(c, dt_override, iters);
+                a.smem_slots = slots;
+                phase_rows(c, dt_override);
+                CK(cudaEventRecord(e0, s));
+                launch_solve(a, th, cl, un, s);
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best.ms) best = {cl, th, un, ms};
+            }
+    if (best.cluster) c->tuned[key] = best;
+    phase_rows(c, dt_override);   // fresh impulses for the real solve
+}
+
 void phase_solve(ovl_ctx *c, float dt_override, int iters) {
     const int P = c->n_parts, npr = c->npairs;
     c->lam_out.ensure(npr + 1);
@@ -433,21 +531,31 @@ void phase_solve(ovl_ctx *c, float dt_override, int iters) {
     c->part_iters.ensure((size_t)P + 1);
     c->part_res_sq.ensure((size_t)P + 1);
     CK(cudaMemsetAsync(c->part_res_sq.p, 0, sizeof(double) * ((size_t)P + 1), c->stream));
-    SolveArgs a{};
-    a.n_parts = P; a.part_bstart = c->part_bstart.p; a.part_list = c->part_list.p;
-    a.entry_body = c->entry_body.p; a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p;
-    a.part_scene = c->part_scene.p; a.scene_dt = c->scene_dt.p; a.dt_override = dt_override;
-    a.gravity = make_float3(c->P.gravity[0], c->P.gravity[1], c->P.gravity[2]);
-    a.st = c->st.p; a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
-    a.rpair = c->rpair.p; a.scene_mu = c->scene_mu.p; a.n_entries = c->ne;
-    a.lam_out = c->lam_out.p; a.copies = c->copies.p; a.scratch = c->solve_scratch.p;
-    int cluster = 1, slots = 0;
-    solve_config(c, &cluster, &slots);
+    int cluster = 1, slots = 0, threads = solve_threads(c), unroll = 1;
+    solve_config(c, &cluster, &slots, &unroll);
+    if (c->P.flags & OVL_FLAG_AUTOTUNE) {
+        std::string key = tune_key(c);
+        auto it = c->tuned.find(key);
+        if (it == c->tuned.end()) {
+            autotune(c, dt_override, iters, key);
+            it = c->tuned.find(key);
+        }
+        if (it != c->tuned.end()) {
+            int sl = solve_slots_for(c, it->second.cluster);
+            if (sl) {
+                cluster = it->second.cluster;
+                threads = it->second.threads;
+                unroll = it->second.unroll;
+                slots = sl;
+            }
+        }
+    }
     c->last_cluster = cluster;
-    a.iters = iters; a.smem_slots = slots; a.flags = c->P.flags;
-    a.res_tol = c->P.res_tol; a.res_check_every = c->P.res_check_every;
-    a.part_iters = c->part_iters.p; a.part_res_sq = c->part_res_sq.p; a.status = c->status.p;
-    launch_solve(a, solve_threads(c), cluster, c->stream);
+    c->last_threads = threads;
+    c->last_unroll = unroll;
+    SolveArgs a = solve_args(c, dt_override, iters);
+    a.smem_slots = slots;
+    launch_solve(a, threads, cluster, unroll, c->stream);
 }
 
 void phase_geodesics(ovl_ctx *c) {
@@ -608,7 +716,7 @@ void release_all(ovl_ctx *c) {
     c->part_count.release(); c->part_bstart.release(); c->sk.release(); c->sv.release();
     c->sk2.release(); c->sv2.release(); c->cons_count.release(); c->cons_start.release();
     c->pair_cons.release(); c->pair_part.release(); c->ps_cons.release(); c->ps_part.release();
-    c->part_pcount.release(); c->part_pstart.release(); c->p_colour.release(); c->part_ncol.release();
+    c->part_pcount.release(); c->part_pstart.release(); c->p_colour.release(); c->part_ncol.release(); c->part_rounds.release();
     c->col_off.release(); c->pair_of_row.release(); c->p_key.release(); c->p_slot.release();
     c->p_lam0.release(); c->colour_scratch.release(); c->worklist.release(); c->worklist2.release(); c->wprio.release(); c->wprio2.release(); c->r0.release(); c->r1.release();
     c->r2.release(); c->rlam.release(); c->lam_out.release(); c->r3.release(); c->rpair.release(); c->ws_pstart.release();
@@ -970,7 +1078,8 @@ ovl_status ovl_read_stats(ovl_ctx *c, ovl_stats *out) {
         out->n_entries = c->ne;
         out->n_pairs = c->npairs;
         out->n_rows = 3ll * c->npairs;
-        std::vector<int> ep(c->n + 1), ncol(c->n_parts), its(c->n_parts);
+        std::vector<int> ep(c->n + 1), ncol(c->n_parts), its(c->n_parts), rounds(c->n_parts);
+        download(rounds.data(), c->part_rounds.p, rounds.size(), c->stream);
         std::vector<double> rs(c->n_parts);
         download(ep.data(), c->entry_ptr.p, ep.size(), c->stream);
         download(ncol.data(), c->part_ncol.p, ncol.size(), c->stream);
@@ -984,12 +1093,18 @@ ovl_status ovl_read_stats(ovl_ctx *c, ovl_stats *out) {
         for (int p = 0; p < c->n_parts; ++p) {
             out->max_colours = std::max(out->max_colours, ncol[p]);
             out->max_iters = std::max(out->max_iters, its[p]);
+            out->colour_rounds_max = std::max(out->colour_rounds_max, rounds[p]);
             sq += rs[p];
         }
         out->residual_rms = c->npairs > 0 ? std::sqrt(sq / (3.0 * c->npairs)) : 0.0;
         out->device_status = dstat;
         for (int i = 0; i < 10; ++i) out->phase_ms[i] = c->phase_ms[i];
         out->n_launches = c->last_launches;
+        out->solve_cluster = c->last_cluster;
+        out->solve_threads = c->last_threads;
+        out->solve_rows_per_thread = c->last_unroll;
+        out->lb_candidates = c->lb_candidates;
+        out->lb_host_ms = c->lb_host_ms;
         return OVL_OK;
     });
 }
@@ -1081,6 +1196,67 @@ ovl_status ovl_read_worker_stats(ovl_ctx *c, int32_t *iters, double *res_sq, int
         CK(cudaStreamSynchronize(c->stream));
         if (rows)
             for (int p = 0; p < c->n_parts; ++p) rows[p] = 3ll * (ps[p + 1] - ps[p]);
+        return OVL_OK;
+    });
+}
+
+}  // extern "C"
+
+extern "C" {
+
+ovl_status ovl_autotune_export(ovl_ctx *c, char *buf, size_t cap, size_t *len) {
+    return guarded(c, [&]() -> ovl_status {
+        std::ostringstream o;
+        o << "{";
+        bool first = true;
+        for (const auto &kv : c->tuned) {
+            if (!first) o << ", ";
+            first = false;
+            o << "\"" << kv.first << "\": {\"cluster\": " << kv.second.cluster << ", \"threads\": "
+              << kv.second.threads << ", \"rows_per_thread\": " << kv.second.unroll << ", \"ms\": "
+              << kv.second.ms << "}";
+        }
+        o << "}";
+        std::string t = o.str();
+        if (len) *len = t.size();
+        if (buf && cap > 0) {
+            size_t m = std::min(cap - 1, t.size());
+            std::memcpy(buf, t.data(), m);
+            buf[m] = 0;
+        }
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_autotune_import(ovl_ctx *c, const char *json) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!json) return fail(c, OVL_ERR_ARG, "null json");
+        // flat format written by ovl_autotune_export
+        std::string t(json);
+        size_t pos = 0;
+        auto num = [&](const std::string &field, size_t from, size_t to) -> double {
+            size_t f = t.find("\"" + field + "\"", from);
+            if (f == std::string::npos || f > to) throw std::invalid_argument("autotune json: missing " + field);
+            f = t.find(':', f);
+            return std::strtod(t.c_str() + f + 1, nullptr);
+        };
+        while ((pos = t.find('"', pos)) != std::string::npos) {
+            size_t e = t.find('"', pos + 1);
+            if (e == std::string::npos) break;
+            std::string key = t.substr(pos + 1, e - pos - 1);
+            size_t ob = t.find('{', e), cb = t.find('}', e);
+            if (ob == std::string::npos || cb == std::string::npos) break;
+            ovl_ctx::TuneCfg cfg;
+            cfg.cluster = (int)num("cluster", ob, cb);
+            cfg.threads = (int)num("threads", ob, cb);
+            cfg.unroll = (int)num("rows_per_thread", ob, cb);
+            cfg.ms = (float)num("ms", ob, cb);
+            bool ok = (cfg.cluster == 1 || cfg.cluster == 2 || cfg.cluster == 4 || cfg.cluster == 8) &&
+                      (cfg.threads >= 32 && cfg.threads <= 512) && (cfg.unroll == 1 || cfg.unroll == 2);
+            if (!ok) return fail(c, OVL_ERR_ARG, "autotune json: bad entry " + key);
+            c->tuned[key] = cfg;
+            pos = cb + 1;
+        }
         return OVL_OK;
     });
 }

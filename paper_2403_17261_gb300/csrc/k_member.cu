@@ -3,8 +3,12 @@
 // (worker, constraint) pairs with their warm-start impulses, the per-worker
 // colouring that orders the Gauss-Seidel sweep, and the colour-ordered row
 // records the solver streams.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ovl {
 
@@ -148,50 +152,142 @@ constexpr int COLOUR_THREADS = 512;
 constexpr int COLOUR_WARPS = COLOUR_THREADS / 32;
 constexpr int NBUCKET = 2 * OVL_MAX_COLOURS;
 
-__global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
-    extern __shared__ unsigned long long dyn_smem[];
-    __shared__ int n_cur, n_next, rounds_left, ncol_sh;
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+// Per-slot colouring state of one worker: the maximum priority of the
+// uncoloured constraints posted this round (array 0) and the mask of colours
+// taken (array 1).
+// C > 1: spread over the cluster's shared memory, slot s in CTA s % C.  The
+// maximum is taken in two 32-bit stages (high words, then low words among the
+// constraints whose high word won), which is the 64-bit maximum: 64-bit atomic
+// max into another CTA's shared memory lost updates in a standalone test on
+// this GPU, 32-bit ones did not.
+template <int C>
+struct ColourSlots {
+    static constexpr bool two_stage = true;
+    uint32_t b0, b1;   // shared-window offsets of this CTA's arrays (hi/lo words, used mask)
+    __device__ __forceinline__ uint32_t at(int arr, int s) const {
+        uint32_t base = arr == 0 ? b0 : b1;
+        return mapa_u32(base + 8u * (uint32_t)(s / C), (uint32_t)(s % C));
+    }
+    // stage 1: high word (at offset +4 of the little-endian 64-bit slot)
+    __device__ __forceinline__ void amax_hi(int s, unsigned long long v) const {
+        asm volatile("red.shared::cluster.max.u32 [%0], %1;" ::"r"(at(0, s) + 4u), "r"((uint32_t)(v >> 32)) : "memory");
+    }
+    __device__ __forceinline__ void amax_lo(int s, unsigned long long v) const {
+        asm volatile("red.shared::cluster.max.u32 [%0], %1;" ::"r"(at(0, s)), "r"((uint32_t)v) : "memory");
+    }
+    __device__ __forceinline__ uint32_t ld_hi(int s) const {
+        uint32_t v;
+        asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(at(0, s) + 4u) : "memory");
+        return v;
+    }
+    __device__ __forceinline__ unsigned long long ld(int arr, int s) const {
+        unsigned long long v;
+        asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(at(arr, s)) : "memory");
+        return v;
+    }
+    __device__ __forceinline__ void st(int arr, int s, unsigned long long v) const {
+        asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(at(arr, s)), "l"(v) : "memory");
+    }
+};
+
+// One CTA: shared or global memory through plain pointers (volatile reads so
+// that values written by other threads' atomics are seen after a barrier);
+// one 64-bit atomic max per slot.
+struct ColourPtrs {
+    static constexpr bool two_stage = false;
+    unsigned long long *p0, *p1;
+    __device__ __forceinline__ unsigned long long *ptr(int arr, int s) const {
+        return (arr == 0 ? p0 : p1) + s;
+    }
+    __device__ __forceinline__ void amax_hi(int s, unsigned long long v) const { atomicMax(ptr(0, s), v); }
+    __device__ __forceinline__ void amax_lo(int, unsigned long long) const {}
+    __device__ __forceinline__ uint32_t ld_hi(int s) const {
+        return (uint32_t)(*reinterpret_cast<volatile unsigned long long *>(ptr(0, s)) >> 32);
+    }
+    __device__ __forceinline__ unsigned long long ld(int arr, int s) const {
+        return *reinterpret_cast<volatile unsigned long long *>(ptr(arr, s));
+    }
+    __device__ __forceinline__ void st(int arr, int s, unsigned long long v) const { *ptr(arr, s) = v; }
+};
+
+template <int C>
+__device__ __forceinline__ void csync() {
+    if (C == 1) __syncthreads();
+    else cg::this_cluster().sync();
+}
+
+// sum over the group's CTAs of one int per CTA held in shared variable *v
+template <int C>
+__device__ __forceinline__ int cluster_int_sum(int *v) {
+    if (C == 1) return *v;
+    cg::cluster_group cl = cg::this_cluster();
+    int t = 0;
+    for (int r = 0; r < C; ++r) t += *cl.map_shared_rank(v, r);
+    return t;
+}
+
+// Colours one worker with a group of C CTAs.  CTA `rank` owns the
+// constraints [i0, i1) of the worker (a contiguous share, so the final sort is
+// stable across CTAs) and the slots s with s % C == rank.
+template <int C, class SL>
+__device__ void colour_worker(const ColourArgs &a, const SL &S, int p, int rank, int per_slots) {
+    __shared__ int n_next, ncol_sh, pub_left, pub_ncol;
     __shared__ int counts[NBUCKET + 1];
+    __shared__ int base_b[NBUCKET + 1];
     __shared__ int running[NBUCKET];
     __shared__ int wcnt[COLOUR_WARPS][NBUCKET];
-    const int p = blockIdx.x;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, T = blockDim.x;
     const int b0 = a.part_bstart[p], nb = a.part_bstart[p + 1] - b0;
     const int q0 = a.part_pstart[p], nq = a.part_pstart[p + 1] - q0;
-    unsigned long long *slot_max, *used0, *used1;
-    if (nb <= a.smem_slots) {
-        slot_max = dyn_smem;
-    } else {
-        slot_max = a.scratch + 3 * (size_t)b0;
-    }
-    used0 = slot_max + nb;
-    used1 = used0 + nb;
-    // worklists of uncoloured constraints, ping-pong: (index relative to q0,
-    // slot a, slot b) and the priority, read contiguously every round
-    int4 *wl_cur = a.worklist + q0, *wl_next = a.worklist2 + q0;
-    unsigned long long *pr_cur = a.wprio + q0, *pr_next = a.wprio2 + q0;
-    for (int s = tid; s < nb; s += blockDim.x) { used0[s] = 0ull; used1[s] = 0ull; slot_max[s] = 0ull; }
-    for (int k = tid; k < nq; k += blockDim.x) {
+    const int chunk = (nq + C - 1) / C;
+    const int i0 = min(nq, rank * chunk), i1 = min(nq, i0 + chunk);
+    (void)per_slots;
+    // worklists of this CTA's uncoloured constraints: (index in worker,
+    // slot a, slot b) and the priority, ping-pong, read contiguously
+    int4 *wl_cur = a.worklist + q0 + i0, *wl_next = a.worklist2 + q0 + i0;
+    unsigned long long *pr_cur = a.wprio + q0 + i0, *pr_next = a.wprio2 + q0 + i0;
+    for (int s = rank + C * tid; s < nb; s += C * T) S.st(1, s, 0ull);
+    for (int k = i0 + tid; k < i1; k += T) {
         int2 sl = a.p_slot[q0 + k];
-        wl_cur[k] = make_int4(k, sl.x, sl.y, 0);
-        pr_cur[k] = mix64(a.p_key[q0 + k]);
+        wl_cur[k - i0] = make_int4(k, sl.x, sl.y, 0);
+        pr_cur[k - i0] = mix64(a.p_key[q0 + k]);
     }
-    if (tid == 0) { n_cur = nq; n_next = 0; rounds_left = nq + 2; ncol_sh = 0; }
-    __syncthreads();
-    while (n_cur > 0 && rounds_left > 0) {
-        const int m = n_cur;
-        // highest priority among the uncoloured constraints at every slot
-        for (int i = tid; i < m; i += blockDim.x) {
+    if (tid == 0) { n_next = 0; ncol_sh = 0; }
+    int m = i1 - i0;
+    int rounds = 0;
+    // Every round: each CTA zeroes the maxima of the slots it holds, all
+    // uncoloured constraints post their priority at their slots, and those
+    // holding the maximum at both slots take their colour.
+    while (rounds <= nq + 1) {
+        for (int s = rank + C * tid; s < nb; s += C * T) S.st(0, s, 0ull);
+        csync<C>();
+        for (int i = tid; i < m; i += T) {
             const int4 w = wl_cur[i];
             const unsigned long long pr = pr_cur[i];
-            if (w.y >= 0) atomicMax(&slot_max[w.y], pr);
-            if (w.z >= 0) atomicMax(&slot_max[w.z], pr);
+            if (w.y >= 0) S.amax_hi(w.y, pr);
+            if (w.z >= 0) S.amax_hi(w.z, pr);
         }
-        __syncthreads();
-        for (int i = tid; i < m; i += blockDim.x) {
+        csync<C>();
+        if (SL::two_stage) {
+            for (int i = tid; i < m; i += T) {
+                const int4 w = wl_cur[i];
+                const unsigned long long pr = pr_cur[i];
+                const uint32_t hi = (uint32_t)(pr >> 32);
+                if (w.y >= 0 && S.ld_hi(w.y) == hi) S.amax_lo(w.y, pr);
+                if (w.z >= 0 && S.ld_hi(w.z) == hi) S.amax_lo(w.z, pr);
+            }
+            csync<C>();
+        }
+        for (int i = tid; i < m; i += T) {
             const int4 w = wl_cur[i];
             const unsigned long long pr = pr_cur[i];
-            bool ready = (w.y < 0 || slot_max[w.y] == pr) && (w.z < 0 || slot_max[w.z] == pr);
+            bool ready = (w.y < 0 || S.ld(0, w.y) == pr) && (w.z < 0 || S.ld(0, w.z) == pr);
             if (!ready) {
                 int o = atomicAdd(&n_next, 1);
                 wl_next[o] = w;
@@ -199,62 +295,79 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
                 continue;
             }
             // only this constraint touches its slots in this round
-            unsigned long long u0 = 0ull, u1 = 0ull;
-            if (w.y >= 0) { u0 |= used0[w.y]; u1 |= used1[w.y]; }
-            if (w.z >= 0) { u0 |= used0[w.z]; u1 |= used1[w.z]; }
+            unsigned long long u = 0ull;
+            if (w.y >= 0) u |= S.ld(1, w.y);
+            if (w.z >= 0) u |= S.ld(1, w.z);
             int c;
-            if (~u0) c = __ffsll((long long)~u0) - 1;
-            else if (~u1) c = 64 + __ffsll((long long)~u1) - 1;
+            if (~u) c = __ffsll((long long)~u) - 1;
             else { c = OVL_MAX_COLOURS - 1; atomicCAS(a.status, DEV_OK, DEV_ERR_COLOURS); }
             a.p_colour[q0 + w.x] = c;
-            unsigned long long bit0 = c < 64 ? (1ull << c) : 0ull, bit1 = c >= 64 ? (1ull << (c - 64)) : 0ull;
-            if (w.y >= 0) { used0[w.y] |= bit0; used1[w.y] |= bit1; }
-            if (w.z >= 0) { used0[w.z] |= bit0; used1[w.z] |= bit1; }
+            const unsigned long long bit = 1ull << c;
+            if (w.y >= 0) S.st(1, w.y, S.ld(1, w.y) | bit);
+            if (w.z >= 0) S.st(1, w.z, S.ld(1, w.z) | bit);
             atomicMax(&ncol_sh, c + 1);
         }
         __syncthreads();
-        // clear the slot maxima that this round set
-        for (int i = tid; i < m; i += blockDim.x) {
-            const int4 w = wl_cur[i];
-            if (w.y >= 0) slot_max[w.y] = 0ull;
-            if (w.z >= 0) slot_max[w.z] = 0ull;
-        }
+        if (tid == 0) pub_left = n_next;
+        csync<C>();
+        const int left = cluster_int_sum<C>(&pub_left);
+        m = n_next;
+        ++rounds;
         __syncthreads();
-        if (tid == 0) { n_cur = n_next; n_next = 0; --rounds_left; }
-        int4 *t = wl_cur; wl_cur = wl_next; wl_next = t;
-        unsigned long long *tp = pr_cur; pr_cur = pr_next; pr_next = tp;
-        __syncthreads();
+        if (tid == 0) n_next = 0;
+        { int4 *t = wl_cur; wl_cur = wl_next; wl_next = t; }
+        { unsigned long long *t = pr_cur; pr_cur = pr_next; pr_next = t; }
+        if (left == 0) break;
+        csync<C>();   // the counts published above stay readable until every CTA has summed them
     }
-    if (tid == 0 && n_cur > 0) atomicCAS(a.status, DEV_OK, DEV_ERR_TIMEOUT);
+    if (rank == 0 && tid == 0 && rounds > nq + 1) atomicCAS(a.status, DEV_OK, DEV_ERR_TIMEOUT);
     // stable counting sort of the worker's constraints by (colour, kind):
-    // contacts before joints inside a colour, canonical order kept
-    for (int j = tid; j <= NBUCKET; j += blockDim.x) counts[j] = 0;
-    for (int j = tid; j < NBUCKET; j += blockDim.x) running[j] = 0;
-    for (int j = tid; j < COLOUR_WARPS * NBUCKET; j += blockDim.x) (&wcnt[0][0])[j] = 0;
+    // contacts before joints inside a colour, canonical order kept; CTA r's
+    // share goes after the shares of lower ranks in every bucket
+    for (int j = tid; j <= NBUCKET; j += T) counts[j] = 0;
+    for (int j = tid; j < NBUCKET; j += T) running[j] = 0;
+    for (int j = tid; j < COLOUR_WARPS * NBUCKET; j += T) (&wcnt[0][0])[j] = 0;
     __syncthreads();
-    for (int k = tid; k < nq; k += blockDim.x) {
+    for (int k = i0 + tid; k < i1; k += T) {
         int c = a.p_colour[q0 + k];
         int kind = (int)(a.p_key[q0 + k] >> 62) & 1;
         atomicAdd(&counts[2 * c + kind], 1);
     }
-    __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int j = 0; j <= NBUCKET; ++j) {
-            int v = j < NBUCKET ? counts[j] : 0;
-            counts[j] = acc;
-            acc += v;
+    if (tid == 0) pub_ncol = ncol_sh;
+    csync<C>();
+    // bucket base of this CTA: all earlier buckets of every CTA, plus this
+    // bucket in lower-ranked CTAs
+    for (int j = tid; j <= NBUCKET; j += T) {
+        int before = 0, lower = 0;
+        if (C == 1) {
+            for (int jj = 0; jj < j; ++jj) before += counts[jj];
+        } else {
+            cg::cluster_group cl = cg::this_cluster();
+            for (int r = 0; r < C; ++r) {
+                const int *cr = cl.map_shared_rank(counts, r);
+                for (int jj = 0; jj < j; ++jj) before += cr[jj];
+                if (r < rank && j < NBUCKET) lower += cr[j];
+            }
         }
-        a.part_ncol[p] = ncol_sh;
+        base_b[j] = before + lower;
+        if (rank == 0) a.col_off[(size_t)p * (NBUCKET + 1) + j] = q0 + before;
+    }
+    if (rank == 0 && tid == 0) {
+        int nc = 0;
+        if (C == 1) nc = ncol_sh;
+        else {
+            cg::cluster_group cl = cg::this_cluster();
+            for (int r = 0; r < C; ++r) nc = max(nc, *cl.map_shared_rank(&pub_ncol, r));
+        }
+        a.part_ncol[p] = nc;
+        a.part_rounds[p] = rounds;
     }
     __syncthreads();
-    int *off = a.col_off + (size_t)p * (NBUCKET + 1);
-    for (int j = tid; j <= NBUCKET; j += blockDim.x) off[j] = q0 + counts[j];
     const int lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    for (int base = 0; base < nq; base += blockDim.x) {
+    for (int base = i0; base < i1; base += T) {
         int k = base + tid;
-        bool valid = k < nq;
+        bool valid = k < i1;
         int bucket = NBUCKET;
         if (valid) bucket = 2 * a.p_colour[q0 + k] + ((int)(a.p_key[q0 + k] >> 62) & 1);
         unsigned peers = __match_any_sync(0xffffffffu, bucket);
@@ -264,16 +377,40 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
         if (valid) {
             int pre = 0;
             for (int w = 0; w < warp; ++w) pre += wcnt[w][bucket];
-            int row = q0 + counts[bucket] + running[bucket] + pre + lrank;
-            a.pair_of_row[row] = q0 + k;
+            a.pair_of_row[q0 + base_b[bucket] + running[bucket] + pre + lrank] = q0 + k;
         }
         __syncthreads();
-        for (int j = tid; j < NBUCKET; j += blockDim.x) {
+        for (int j = tid; j < NBUCKET; j += T) {
             int add = 0;
             for (int w = 0; w < COLOUR_WARPS; ++w) { add += wcnt[w][j]; wcnt[w][j] = 0; }
             running[j] += add;
         }
         __syncthreads();
+    }
+    // no CTA may leave while another can still reach its shared memory
+    csync<C>();
+}
+
+template <int C>
+__global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
+    extern __shared__ unsigned long long dyn_smem[];
+    const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
+    const int p = blockIdx.x / C;
+    const int nb = a.part_bstart[p + 1] - a.part_bstart[p];
+    const int per = (nb + C - 1) / C;
+    if (per <= a.smem_slots) {
+        unsigned long long *mx = dyn_smem, *u = dyn_smem + per;
+        if (C == 1) {
+            ColourPtrs S{mx, u};
+            colour_worker<1>(a, S, p, 0, per);
+        } else {
+            ColourSlots<C> S{(uint32_t)__cvta_generic_to_shared(mx), (uint32_t)__cvta_generic_to_shared(u)};
+            colour_worker<C>(a, S, p, rank, per);
+        }
+    } else if (rank == 0) {
+        unsigned long long *mx = a.scratch + 2 * (size_t)a.part_bstart[p];
+        ColourPtrs S{mx, mx + nb};
+        colour_worker<1>(a, S, p, 0, nb);
     }
 }
 
@@ -410,14 +547,37 @@ void launch_pair_setup(const MemberArgs &a, const WarmArgs &w, int np, cudaStrea
     note_launch();
     CK(cudaGetLastError());
 }
-void launch_colour(const ColourArgs &a, cudaStream_t s) {
-    if (!a.n_parts) return;
-    size_t smem = (size_t)a.smem_slots * 3 * sizeof(unsigned long long);
-    CK(cudaFuncSetAttribute(k_colour, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_colour<<<a.n_parts, COLOUR_THREADS, smem, s>>>(a);
+template <int C>
+static void launch_colour_c(const ColourArgs &a, cudaStream_t s) {
+    size_t smem = (size_t)a.smem_slots * 2 * sizeof(unsigned long long);
+    CK(cudaFuncSetAttribute(k_colour<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.n_parts * C);
+    cfg.blockDim = dim3(COLOUR_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k_colour<C>, a));
     note_launch();
+}
+
+void launch_colour(const ColourArgs &a, int cluster, cudaStream_t s) {
+    if (!a.n_parts) return;
+    switch (cluster) {
+        case 8: launch_colour_c<8>(a, s); break;
+        case 4: launch_colour_c<4>(a, s); break;
+        case 2: launch_colour_c<2>(a, s); break;
+        default: launch_colour_c<1>(a, s); break;
+    }
     CK(cudaGetLastError());
 }
+
 void launch_rows(const RowArgs &a, cudaStream_t s) {
     if (!a.np) return;
     k_rows<<<grid1d(a.np, 256), 256, 0, s>>>(a);

@@ -82,6 +82,8 @@ __device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
 }
 
 // Distributed over the C CTAs of a cluster: slot s in CTA s % C at index s / C.
+// The accesses are volatile asm, so they keep their order among themselves and
+// with the cluster barriers; ordinary loads of row records may move around them.
 template <int C>
 struct ClusterSlots {
     uint32_t A, B;   // shared-window offsets of this CTA's arrays (same in every CTA)
@@ -91,8 +93,8 @@ struct ClusterSlots {
         float4 x;
         float2 y;
         asm volatile("ld.shared::cluster.v4.f32 {%0,%1,%2,%3}, [%4];"
-                     : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w) : "r"(a) : "memory");
-        asm volatile("ld.shared::cluster.v2.f32 {%0,%1}, [%2];" : "=f"(y.x), "=f"(y.y) : "r"(c) : "memory");
+                     : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w) : "r"(a));
+        asm volatile("ld.shared::cluster.v2.f32 {%0,%1}, [%2];" : "=f"(y.x), "=f"(y.y) : "r"(c));
         b.v = make_float3(x.x, x.y, x.z);
         b.w = make_float3(x.w, y.x, y.y);
     }
@@ -100,8 +102,8 @@ struct ClusterSlots {
         const uint32_t r = (uint32_t)s % C, i = (uint32_t)s / C;
         const uint32_t a = mapa(A + 16u * i, r), c = mapa(B + 8u * i, r);
         asm volatile("st.shared::cluster.v4.f32 [%0], {%1,%2,%3,%4};"
-                     :: "r"(a), "f"(b.v.x), "f"(b.v.y), "f"(b.v.z), "f"(b.w.x) : "memory");
-        asm volatile("st.shared::cluster.v2.f32 [%0], {%1,%2};" :: "r"(c), "f"(b.w.y), "f"(b.w.z) : "memory");
+                     :: "r"(a), "f"(b.v.x), "f"(b.v.y), "f"(b.v.z), "f"(b.w.x));
+        asm volatile("st.shared::cluster.v2.f32 [%0], {%1,%2};" :: "r"(c), "f"(b.w.y), "f"(b.w.z));
     }
 };
 
@@ -289,8 +291,9 @@ __device__ float rows_residual_sq(const SolveArgs &a, const S &st, const int *of
 }
 
 // One worker solved by a group of C CTAs; threads are numbered g = rank T + tid
-// and in every colour thread g takes rows off + g, off + g + G, ... (G = C T).
-template <int C, class S>
+// and in every colour thread g takes rows off + g, off + g + G, ... (G = C T),
+// U of them at a time.
+template <int C, int U, class S>
 __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank) {
     __shared__ float red[32];
     __shared__ float part_sum;
@@ -340,7 +343,28 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank) {
     for (int it = 0; it < a.iters; ++it) {
         for (int c = 0; c < ncol; ++c) {
             const int jb = off[2 * c + 1], ce = off[2 * c + 2];
-            for (int r = off[2 * c] + g; r < ce; r += G) {
+            int r = off[2 * c] + g;
+            if (U == 2) {
+                // two rows of the colour at once (independent: no shared body)
+                for (; r + G < ce; r += 2 * G) {
+                    const int q = r + G;
+                    float4 x0 = a.r0[r], x1 = a.r1[r], x2 = a.r2[r], xm = a.r3[r], xl = a.rlam[r];
+                    float4 y0 = a.r0[q], y1 = a.r1[q], y2 = a.r2[q], ym = a.r3[q], yl = a.rlam[q];
+                    const int sx = __float_as_int(x2.w), sy = __float_as_int(y2.w);
+                    Body A, B, D, E;
+                    load_pair(st, sx, xm, A, B);
+                    load_pair(st, sy, ym, D, E);
+                    if (r < jb) contact_row(A, B, x0, x1, x2, mu, xl);
+                    else joint_rows(A, B, x0, x1, x2, xl);
+                    if (q < jb) contact_row(D, E, y0, y1, y2, mu, yl);
+                    else joint_rows(D, E, y0, y1, y2, yl);
+                    store_pair(st, sx, A, B);
+                    store_pair(st, sy, D, E);
+                    a.rlam[r] = xl;
+                    a.rlam[q] = yl;
+                }
+            }
+            for (; r < ce; r += G) {
                 float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r], m = a.r3[r], lam = a.rlam[r];
                 int slots = __float_as_int(r2.w);
                 Body A, B;
@@ -398,8 +422,8 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank) {
 // C CTAs per worker; a worker's slots are spread over their shared memory when
 // they fit (ceil(nb / C) <= smem_slots), else CTA rank 0 solves it alone with
 // its body state in the global scratch area.
-template <int C>
-__global__ void __launch_bounds__(SOLVE_THREADS, 2) k_solve(SolveArgs a) {
+template <int C, int U>
+__global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveArgs a) {
     extern __shared__ float4 sm[];
     const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
     const int p = blockIdx.x / C;
@@ -414,14 +438,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 2) k_solve(SolveArgs a) {
         float2 *B = reinterpret_cast<float2 *>(sm + per);
         if (C == 1) {
             LocalSlots st{A, B};
-            solve_worker<C>(a, st, p, rank);
+            solve_worker<C, U>(a, st, p, rank);
         } else {
             ClusterSlots<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B)};
-            solve_worker<C>(a, st, p, rank);
+            solve_worker<C, U>(a, st, p, rank);
         }
     } else if (rank == 0) {
         LocalSlots st{a.scratch + (size_t)b0, reinterpret_cast<float2 *>(a.scratch + (size_t)a.n_entries) + b0};
-        solve_worker<1>(a, st, p, 0);
+        solve_worker<1, U>(a, st, p, 0);
     }
 }
 
@@ -429,10 +453,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 2) k_solve(SolveArgs a) {
 
 int solve_smem_bytes(int slots) { return slots * (int)(sizeof(float4) + sizeof(float2)); }
 
-template <int C>
+template <int C, int U>
 static void launch_solve_c(const SolveArgs &a, int threads, cudaStream_t s) {
     int smem = solve_smem_bytes(a.smem_slots);
-    CK(cudaFuncSetAttribute(k_solve<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaFuncSetAttribute(k_solve<C, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.n_parts * C);
     cfg.blockDim = dim3(threads);
@@ -445,20 +469,33 @@ static void launch_solve_c(const SolveArgs &a, int threads, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, k_solve<C>, a));
+    CK(cudaLaunchKernelEx(&cfg, k_solve<C, U>, a));
     note_launch();
 }
 
-void launch_solve(const SolveArgs &a, int threads, int cluster, cudaStream_t s) {
+void launch_solve(const SolveArgs &a, int threads, int cluster, int unroll, cudaStream_t s) {
     if (!a.n_parts) return;
     if (threads > SOLVE_THREADS) threads = SOLVE_THREADS;
-    switch (cluster) {
-        case 8: launch_solve_c<8>(a, threads, s); break;
-        case 4: launch_solve_c<4>(a, threads, s); break;
-        case 2: launch_solve_c<2>(a, threads, s); break;
-        default: launch_solve_c<1>(a, threads, s); break;
+    if (unroll == 2) {
+        switch (cluster) {
+            case 8: launch_solve_c<8, 2>(a, threads, s); break;
+            case 4: launch_solve_c<4, 2>(a, threads, s); break;
+            case 2: launch_solve_c<2, 2>(a, threads, s); break;
+            default: launch_solve_c<1, 2>(a, threads, s); break;
+        }
+    } else {
+        switch (cluster) {
+            case 8: launch_solve_c<8, 1>(a, threads, s); break;
+            case 4: launch_solve_c<4, 1>(a, threads, s); break;
+            case 2: launch_solve_c<2, 1>(a, threads, s); break;
+            default: launch_solve_c<1, 1>(a, threads, s); break;
+        }
     }
     CK(cudaGetLastError());
 }
+
+// shared-memory bytes a CTA can use when `per_sm` CTAs share an SM, for the
+// unroll variant's register budget
+int solve_ctas_per_sm(int unroll) { return unroll == 2 ? 1 : 2; }
 
 }  // namespace ovl

@@ -105,15 +105,16 @@ struct ColourArgs {
     const int2 *p_slot;
     int *p_colour;             // [np]
     int *part_ncol;            // [P]
+    int *part_rounds;          // [P] colouring rounds taken
     int *col_off;              // [P][2*OVL_MAX_COLOURS+1] absolute row offsets per (colour, kind)
     int *pair_of_row;          // [np]
-    unsigned long long *scratch;  // 3 per entry, for workers too large for shared memory
+    unsigned long long *scratch;  // 2 per entry, for workers too large for shared memory
     int4 *worklist, *worklist2;                 // [np] each: uncoloured constraints per round
     unsigned long long *wprio, *wprio2;         // [np] each: their priorities
     int smem_slots;            // slots that fit in shared memory
     int *status;
 };
-void launch_colour(const ColourArgs &a, cudaStream_t s);
+void launch_colour(const ColourArgs &a, int cluster, cudaStream_t s);
 
 struct RowArgs {
     int n, nc, np;
@@ -172,7 +173,8 @@ struct SolveArgs {
     double *part_res_sq;       // [P]
     int *status;
 };
-void launch_solve(const SolveArgs &a, int threads, int cluster, cudaStream_t s);
+void launch_solve(const SolveArgs &a, int threads, int cluster, int unroll, cudaStream_t s);
+int solve_ctas_per_sm(int unroll);
 int solve_smem_bytes(int slots);
 
 // ---- geodesics, weights, blend (k_blend.cu) --------------------------------

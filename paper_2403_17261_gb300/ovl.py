@@ -27,6 +27,7 @@ OVL_ERR_NONFINITE = -5
 OVL_ERR_MEMBERSHIP = -6
 OVL_FLAG_RESIDUAL = 1
 OVL_FLAG_TIMING = 2
+OVL_FLAG_AUTOTUNE = 4
 
 EXPORTED = [
     "ovl_default_params", "ovl_create", "ovl_destroy", "ovl_last_error", "ovl_phase_name",
@@ -34,7 +35,7 @@ EXPORTED = [
     "ovl_assign_overlap", "ovl_set_state", "ovl_read_state", "ovl_set_step_index",
     "ovl_set_warmstart", "ovl_read_warmstart", "ovl_step", "ovl_load_balance", "ovl_sync",
     "ovl_read_stats", "ovl_read_contacts", "ovl_read_graph", "ovl_read_entries", "ovl_read_pairs",
-    "ovl_read_worker_stats",
+    "ovl_read_worker_stats", "ovl_autotune_export", "ovl_autotune_import",
 ]
 
 
@@ -70,7 +71,9 @@ class ovl_stats(C.Structure):
                 ("n_workers", C.c_int32), ("max_colours", C.c_int32), ("max_iters", C.c_int32),
                 ("device_status", C.c_int32), ("residual_rms", C.c_double),
                 ("residual_max", C.c_double), ("phase_ms", C.c_float * 12),
-                ("n_launches", C.c_int64)]
+                ("n_launches", C.c_int64), ("solve_cluster", C.c_int32), ("solve_threads", C.c_int32),
+                ("solve_rows_per_thread", C.c_int32), ("colour_rounds_max", C.c_int32),
+                ("lb_candidates", C.c_int64), ("lb_host_ms", C.c_double)]
 
 
 _lib = None
@@ -109,6 +112,8 @@ def load_library(path: str | None = None):
         "ovl_read_entries": [vp, _ip, _ip, _u8p, _fp, _fp],
         "ovl_read_pairs": [vp, _ip, _u64p, _ip, _fp],
         "ovl_read_worker_stats": [vp, _ip, C.POINTER(C.c_double), C.POINTER(C.c_int64), _ip],
+        "ovl_autotune_export": [vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
+        "ovl_autotune_import": [vp, C.c_char_p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -269,6 +274,19 @@ def ovl_sync(ctx):
     _check(ctx, load_library().ovl_sync(ctx))
 
 
+def ovl_autotune_export(ctx) -> str:
+    n = C.c_size_t()
+    L = load_library()
+    _check(ctx, L.ovl_autotune_export(ctx, None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value + 1)
+    _check(ctx, L.ovl_autotune_export(ctx, buf, n.value + 1, C.byref(n)))
+    return buf.value.decode()
+
+
+def ovl_autotune_import(ctx, text: str):
+    _check(ctx, load_library().ovl_autotune_import(ctx, text.encode()))
+
+
 def ovl_read_stats(ctx) -> dict:
     s = ovl_stats()
     _check(ctx, load_library().ovl_read_stats(ctx, C.byref(s)))
@@ -351,6 +369,12 @@ class Simulation:
     # stepping -----------------------------------------------------------------
     def step(self, dt: float = 0.0, iters: int | None = None):
         ovl_step(self.ctx, dt, self.scene.iters if iters is None else iters)
+
+    def autotune_export(self) -> str:
+        return ovl_autotune_export(self.ctx)
+
+    def autotune_import(self, text: str):
+        ovl_autotune_import(self.ctx, text)
 
     def load_balance(self, flags: int = 3):
         ovl_load_balance(self.ctx, flags)

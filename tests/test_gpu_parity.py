@@ -63,3 +63,31 @@ def test_closed_forms_on_gpu():
     m, h = 1.0 / float(sc.inv_mass[0]), float(sc.scene_dt[0])
     assert abs(lam[0, 0] - m * 9.81 * h) < 1e-6 * m * 9.81 * h
     assert np.abs(g.state()[0, 7:13]).max() < 1e-6
+
+
+def test_launch_shapes_bit_identical():
+    """Rows of one colour touch disjoint bodies, so every launch shape (CTAs
+    per worker, threads, rows per thread) and the autotuner's pick compute
+    the same bits."""
+    from paper_2403_17261_gb300 import ovl
+    sc = S.random_pile(3000, 21, n_sets=6, box=5.0)
+    ref = None
+    shapes = [dict(pgs_cluster=1, pgs_threads=512), dict(pgs_cluster=2, pgs_threads=256),
+              dict(pgs_cluster=4, pgs_threads=512), dict(pgs_cluster=8, pgs_threads=256),
+              dict(pgs_cluster=2, smem_slot_limit=64), dict(flags=ovl.OVL_FLAG_AUTOTUNE)]
+    for kw in shapes:
+        g = ovl.Simulation(sc, kw)
+        for _ in range(3):
+            g.step()
+        st = g.state()
+        if ref is None:
+            ref = st
+        else:
+            assert np.array_equal(ref, st), kw
+        if kw.get("flags"):
+            txt = g.autotune_export()
+            assert "cluster" in txt
+            g2 = ovl.Simulation(sc, kw)
+            g2.autotune_import(txt)
+            assert g2.autotune_export() == txt
+        g.close()
