@@ -208,6 +208,57 @@ ovl_status ovl_autotune_import(ovl_ctx *ctx, const char *json);
 ovl_status ovl_read_worker_stats(ovl_ctx *ctx, int32_t *iters, double *res_sq, int64_t *rows,
                                  int32_t *colours);
 
+/* ------------------------------------------------------------------------
+ * Geodesic distances without allocation
+ *
+ * No counterpart in the paper.  Computes the same D(o,i) as the geodesic
+ * phase of ovl_step (Eq 16, Algorithm 5: breadth-first search over the
+ * constraint graph G^t from the bodies that only worker i simulates, cut at
+ * depth beta), for one scene whose graph, masks and entries the caller
+ * already holds on the device.  It exists for callers that must not allocate
+ * device memory: fixed-rate control loops, where cudaFree synchronises the
+ * whole device and stalls every other stream for an unbounded time; and
+ * programs that give all device memory to their own pool at start-up, where
+ * a library's cudaMalloc would fail or break the pool's accounting.  The
+ * function calls neither cudaMalloc nor cudaFree nor any
+ * allocating library routine: its search bitmap, frontier queue and level
+ * counters live in one statically sized __device__ array of the library
+ * (about 16.5 MiB), whose device address is looked up once per device.
+ *
+ * Limits: n_bodies * n_workers <= OVL_GEO_STATIC_MAX_PAIRS and
+ * beta <= OVL_GEO_STATIC_MAX_BETA; larger problems are rejected with
+ * OVL_ERR_CAPACITY before anything runs (use ovl_step for them).
+ *
+ * Arguments (all arrays are DEVICE pointers owned by the caller):
+ *  n_bodies            bodies of the scene; n_workers in [1, 64]; beta >= 0
+ *  row_ptr [n_bodies+1], col [n_adj]: G^t as CSR (body indices < n_bodies)
+ *  mask [n_bodies]     W_b, bit i set when worker i simulates body b; bits at
+ *                      or above n_workers are ignored
+ *  entry_ptr [n_bodies+1], n_entries: the entries of body b are
+ *                      entry_ptr[b] .. entry_ptr[b+1]-1, one per bit of
+ *                      mask[b] in ascending worker order (ovl_read_entries)
+ *  D [n_entries]       out: D(o,i) for bodies with two or more workers, 255
+ *                      where worker i was not met within beta and for every
+ *                      entry of a body with one worker
+ *  cuda_stream         cudaStream_t to enqueue on (NULL: the legacy stream);
+ *                      the call returns once the work is enqueued
+ *  err, err_cap        optional buffer for a NUL-terminated message on error
+ * Indices out of range (col, entry_ptr) are skipped, never dereferenced.
+ *
+ * Concurrency: the scratch array is shared by every call on a device, so
+ * two calls whose work can overlap on the device (other streams, other
+ * threads, or other processes sharing a context) race and give wrong D.
+ * Serialise them, e.g. on one stream.  The first call on each device looks
+ * up the scratch address (cudaGetSymbolAddress, which may load the module);
+ * make that first call before any stream capture begins. */
+#define OVL_GEO_STATIC_MAX_PAIRS 4194304
+#define OVL_GEO_STATIC_MAX_BETA 254
+ovl_status ovl_geodesics_static(int32_t n_bodies, int32_t n_workers, int32_t beta,
+                                const int32_t *row_ptr, const int32_t *col, int32_t n_adj,
+                                const uint64_t *mask, const int32_t *entry_ptr,
+                                int32_t n_entries, uint8_t *D, void *cuda_stream, char *err,
+                                int32_t err_cap);
+
 #ifdef __cplusplus
 }
 #endif

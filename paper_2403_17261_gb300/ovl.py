@@ -36,6 +36,7 @@ EXPORTED = [
     "ovl_set_warmstart", "ovl_read_warmstart", "ovl_step", "ovl_load_balance", "ovl_sync",
     "ovl_read_stats", "ovl_read_contacts", "ovl_read_graph", "ovl_read_entries", "ovl_read_pairs",
     "ovl_read_worker_stats", "ovl_autotune_export", "ovl_autotune_import",
+    "ovl_geodesics_static",
 ]
 
 
@@ -114,6 +115,8 @@ def load_library(path: str | None = None):
         "ovl_read_worker_stats": [vp, _ip, C.POINTER(C.c_double), C.POINTER(C.c_int64), _ip],
         "ovl_autotune_export": [vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
         "ovl_autotune_import": [vp, C.c_char_p],
+        "ovl_geodesics_static": [C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_int32, vp, vp,
+                                 C.c_int32, vp, vp, C.c_char_p, C.c_int32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -285,6 +288,27 @@ def ovl_autotune_export(ctx) -> str:
 
 def ovl_autotune_import(ctx, text: str):
     _check(ctx, load_library().ovl_autotune_import(ctx, text.encode()))
+
+
+def _dev_ptr(a):
+    """Device address of a CUDA tensor (anything with data_ptr()) or an int."""
+    return C.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else int(a))
+
+
+def ovl_geodesics_static(n_bodies: int, n_workers: int, beta: int, row_ptr, col, n_adj: int,
+                         mask, entry_ptr, n_entries: int, D, stream: int | None = None):
+    """D(o,i) of one scene into the device array D, allocating no device memory.
+
+    Arrays are device arrays (CUDA tensors or raw addresses): row_ptr int32
+    [n+1], col int32 [n_adj], mask uint64/int64 [n], entry_ptr int32 [n+1],
+    D uint8 [n_entries].  Overlapping calls on one device race; see ovl.h."""
+    buf = C.create_string_buffer(256)
+    rc = load_library().ovl_geodesics_static(
+        n_bodies, n_workers, beta, _dev_ptr(row_ptr), _dev_ptr(col), n_adj, _dev_ptr(mask),
+        _dev_ptr(entry_ptr), n_entries, _dev_ptr(D), C.c_void_p(stream) if stream else None,
+        buf, len(buf))
+    if rc != OVL_OK:
+        raise OvlError(rc, buf.value.decode())
 
 
 def ovl_read_stats(ctx) -> dict:
