@@ -1,6 +1,6 @@
 """Throughput of the overlapping-partition rigid-body step on GB300.
 
-One "step" is Algorithm 1 lines 7-20 on the whole workload: contacts,
+One "step" is one timestep of Algorithm 1 on the whole workload: contacts,
 constraint graph, load balance, membership, colouring, every worker's PGS
 solve + integration, geodesic weights and the blend.
 

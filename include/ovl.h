@@ -6,7 +6,7 @@
  * In the paper N workers each simulate an overlapping subset P_i of the
  * bodies (Section 4, Eq 9-10) and a server blends the states of the shared
  * bodies O (Algorithm 1).  Here every worker is a partition solved by its own
- * CTA on one GPU; one call to ovl_step runs Algorithm 1 lines 7-20 once.
+ * CTA on one GPU; one call to ovl_step runs one timestep of Algorithm 1.
  *
  * Conventions
  *  - Every function returns ovl_status: 0 on success, a negative OVL_ERR_*
@@ -55,8 +55,8 @@ typedef struct ovl_params {
     float erp;               /* share of penetration / joint error removed per step, 0.2 (reading) */
     float slop;              /* penetration tolerated before push-out, 0.001 (reading) */
     float warmstart;         /* factor on the previous step's impulses, 1.0 */
-    int32_t lb_activate;     /* 1: Algorithm 6 lines 4-15 run every step */
-    int32_t lb_deact_every;  /* k > 0: Algorithm 6 lines 16-24 on steps with index % k == 0; 0: never */
+    int32_t lb_activate;     /* 1: Algorithm 6's activation branch runs every step */
+    int32_t lb_deact_every;  /* k > 0: Algorithm 6's removal branches on steps with index % k == 0; 0: never */
     float res_tol;           /* > 0: a worker stops sweeping once its RMS residual <= res_tol */
     int32_t res_check_every; /* sweeps between residual checks when res_tol > 0 */
     int32_t pgs_threads;     /* threads per worker CTA (0 = automatic) */
@@ -88,14 +88,14 @@ typedef struct ovl_scene_desc {
     const float *scene_mu;       /* [n_scenes] Coulomb friction coefficient */
     const float *scene_dt;       /* [n_scenes] timestep h */
     const int32_t *scene_flags;  /* [n_scenes] bit 0: sphere-sphere contacts enabled */
-    const int32_t *scene_gamma;  /* [n_scenes] overlap growth depth gamma (Alg 3, Alg 6 line 12) */
+    const int32_t *scene_gamma;  /* [n_scenes] overlap growth depth gamma (Alg 3, Alg 6) */
     const int32_t *scene_beta;   /* [n_scenes] weight search depth beta (Alg 5), <= 254 */
     const int32_t *n_sets;       /* [n_scenes] workers per scene, 1..64 */
 } ovl_scene_desc;
 
 /* Last-step statistics. */
 typedef struct ovl_stats {
-    int64_t n_contacts;        /* contacts of the last step (Alg 1 line 10) */
+    int64_t n_contacts;        /* contacts of the last step (Alg 1) */
     int64_t n_adjacency;       /* directed adjacency entries of G^t (2 x edges) */
     int64_t n_entries;         /* sum over bodies of |W_b| */
     int64_t n_pairs;           /* (worker, constraint) pairs solved */
@@ -165,11 +165,10 @@ ovl_status ovl_set_warmstart(ovl_ctx *ctx, int64_t n, const int32_t *part, const
 ovl_status ovl_read_warmstart(ovl_ctx *ctx, int64_t cap, int64_t *n, int32_t *part, uint64_t *key,
                               float *lambda3);
 
-/* One timestep, Algorithm 1 lines 7-20: contacts (line 10), constraint graph
- * (line 11), LOADBALANCE (line 12, Algorithm 6), weights (lines 13-15,
- * Algorithm 5 / Eq 15-16), every worker's PGS solve of Eq 1-7 and
- * integration (line 16), blend (lines 18-20, Algorithm 4).  dt > 0 overrides
- * every scene's timestep; iters = PGS sweeps per worker. */
+/* One timestep of Algorithm 1: contacts, constraint graph G^t, LOADBALANCE
+ * (Algorithm 6), every worker's PGS solve of Eq 1-7 and integration, the
+ * weights (Algorithm 5, Eq 15-16) and the blend (Algorithm 4).  dt > 0
+ * overrides every scene's timestep; iters = PGS sweeps per worker. */
 ovl_status ovl_step(ovl_ctx *ctx, float dt, int32_t iters);
 
 /* LOADBALANCE (Algorithm 6 with BRIDGE, Algorithm 7) alone on the contacts

@@ -243,7 +243,7 @@ def mix64(x: int) -> int:
 # ---------------------------------------------------------------------------
 
 class OracleSim:
-    """FP64 simulation of a scene; ``step`` runs Algorithm 1 lines 7-20 once."""
+    """FP64 simulation of a scene; ``step`` runs one timestep of Algorithm 1."""
 
     def __init__(self, scene, params: dict | None = None):
         p = dict(DEFAULT_PARAMS)

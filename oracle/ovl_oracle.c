@@ -12,7 +12,7 @@
  * Every step is written in the paper's order and notation, single-threaded,
  * with no blocking, fusion or reordering:
  *
- *   contacts  (Alg 1 line "getContacts", Section 5.4)      orc_contacts
+ *   contacts  (Alg 1 contact generation, Section 5.4)      orc_contacts
  *   graph G^t (Section 5.1, constraint graph)              orc_graph
  *   LOADBALANCE (Alg 6) + BRIDGE (Alg 7)                   orc_load_balance
  *   ASSIGNTOOVERLAPSET (Alg 2) + GROWOVERLAP (Alg 3)       orc_assign_overlap
@@ -41,11 +41,13 @@
  *    ties to the lower index).  Everything after the decision is FP64.
  *  - Alg 6 input = every current contact between two dynamic bodies in
  *    canonical (key) order; <W_x> = sum over workers in W_x of |P_w|, live;
- *    the tie at line 5 activates B in W_A; line 14 uses W_A, W_B as read at
- *    line 3; line 21 ties go to the lowest worker index; the removal branches
- *    (lines 16-24) run only on steps whose index is a multiple of the removal
- *    cadence.  Alg 7 reads the body under test ("B" in its line 2 is b).
- *  - Alg 3 line 5 reads W_r \ W_b.  Alg 2 walks joints in index order over the
+ *    a load tie in the activation branch activates B in W_A; the gamma-ball
+ *    activation uses W_A, W_B as read when the contact is taken up; the
+ *    least-loaded choice of the equal-mask branch breaks ties towards the
+ *    lowest worker index; the removal branches run only on steps whose index
+ *    is a multiple of the removal cadence.  Alg 7 tests the body it is given
+ *    (its "B" is that body b).
+ *  - Alg 3 activates W_r \ W_b.  Alg 2 walks joints in index order over the
  *    joint graph.
  *  - Alg 5 / Eq 16: D(o,i) is the smallest BFS depth (1..beta) at which a body
  *    active only in worker i is met; unmet workers get weight 0 and a body
@@ -53,7 +55,7 @@
  *  - Alg 4: the sign test compares q_i with q_0, the copy of the lowest-index
  *    worker; bodies outside O take their single copy unchanged.
  *  - Newly activated bodies start from the blended state (every worker reads
- *    the one blended state at the start of a step, Alg 1 lines 7-9).
+ *    the one blended state at the start of a step, Alg 1).
  *
  * Build: gcc -O2 -ffp-contract=off -std=c11 -shared -fPIC (no fused
  * multiply-add, so FP32 decisions round exactly as written).
@@ -76,8 +78,8 @@ typedef struct {
     double erp;          /* fraction of penetration / joint error removed per step */
     double slop;         /* penetration allowed before push-out */
     double warmstart;    /* factor on the previous step's impulses */
-    int lb_activate;     /* Alg 6 lines 4-15 enabled */
-    int lb_deact_every;  /* Alg 6 lines 16-24 on steps with index % k == 0; 0 = never */
+    int lb_activate;     /* Alg 6 activation branch enabled */
+    int lb_deact_every;  /* Alg 6 removal branches on steps with index % k == 0; 0 = never */
     double res_tol;      /* > 0: a worker stops sweeping once its RMS residual <= res_tol */
     int res_check_every; /* sweeps between residual checks when res_tol > 0 */
 } orc_params;
@@ -429,7 +431,7 @@ int64_t orc_graph(int n, const double *inv_mass, int64_t ne, const int *eu, cons
 
 /* ------------------------------------------------------------------------ */
 /* BFS helper: getBFSVertices(root, depth) = every vertex at graph distance   */
-/* 0..depth from root, root included (Alg 3 line 2, Alg 6 line 12).           */
+/* 0..depth from root, root included (the gamma-balls of Alg 3 and Alg 6).    */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -520,40 +522,40 @@ static void load_balance_impl(membership *m, int n, const int *row_ptr, const in
     bfs_ws_init(&ws, n);
     for (int64_t c = 0; c < nc; ++c) {
         int A = ca[c], B = cb[c];
-        uint64_t WA = m->mask[A], WB = m->mask[B];          /* line 3 */
+        uint64_t WA = m->mask[A], WB = m->mask[B];          /* masks as read now */
         int scene = m->sob[A];
-        if ((WA & WB) == 0) {                                /* line 4 */
+        if ((WA & WB) == 0) {                                /* activation branch */
             if (!do_activate) continue;
             int root;
-            if (load_of(m, WA, scene) <= load_of(m, WB, scene)) {  /* line 5 */
-                activate(m, WA, B);                          /* line 6 */
+            if (load_of(m, WA, scene) <= load_of(m, WB, scene)) {  /* ties: B joins W_A */
+                activate(m, WA, B);
                 root = B;
             } else {
-                activate(m, WB, A);                          /* line 9 */
+                activate(m, WB, A);
                 root = A;
             }
-            int cnt = bfs_vertices(&ws, row_ptr, col, root, scene_gamma[scene]);  /* line 12 */
-            for (int k = 0; k < cnt; ++k) {                  /* lines 13-15 */
+            int cnt = bfs_vertices(&ws, row_ptr, col, root, scene_gamma[scene]);  /* gamma-ball */
+            for (int k = 0; k < cnt; ++k) {
                 int v = ws.queue[k];
                 activate(m, (WA | WB) & ~m->mask[v], v);
             }
         } else if (!do_deactivate) {
             continue;
         } else if (popc64(WA) > 1 && popc64(WB) == 1 && !is_bridge(m, row_ptr, col, A)) {
-            deactivate(m, WA & ~WB, A);                      /* line 17 */
+            deactivate(m, WA & ~WB, A);
         } else if (popc64(WB) > 1 && popc64(WA) == 1 && !is_bridge(m, row_ptr, col, B)) {
-            deactivate(m, WB & ~WA, B);                      /* line 19 */
-        } else if (WA == WB) {                               /* line 20 */
+            deactivate(m, WB & ~WA, B);
+        } else if (WA == WB) {                               /* equal masks */
             int base = m->part_base[scene];
             int s = -1;
             int64_t best = 0;
-            for (int w = 0; w < 64; ++w) {                   /* line 21, ties -> lowest */
+            for (int w = 0; w < 64; ++w) {                   /* least loaded, ties -> lowest */
                 if (!(WA >> w & 1u)) continue;
                 if (s < 0 || m->count[base + w] < best) { s = w; best = m->count[base + w]; }
             }
             uint64_t keep = (uint64_t)1 << s;
-            deactivate(m, WA & ~keep, A);                    /* line 22 */
-            deactivate(m, WB & ~keep, B);                    /* line 23 */
+            deactivate(m, WA & ~keep, A);
+            deactivate(m, WB & ~keep, B);
         }
     }
     bfs_ws_free(&ws);
@@ -591,11 +593,11 @@ int orc_is_bridge(int n, const uint64_t *mask, const int *row_ptr, const int *co
 
 static void grow_overlap(membership *m, bfs_ws *ws, const int *row_ptr, const int *col, int root,
                          int gamma, uint64_t Wr) {
-    int cnt = bfs_vertices(ws, row_ptr, col, root, gamma);   /* Alg 3 line 2 */
+    int cnt = bfs_vertices(ws, row_ptr, col, root, gamma);   /* Alg 3 gamma-ball */
     for (int k = 0; k < cnt; ++k) {
         int b = ws->queue[k];
-        if (popc64(m->mask[b]) >= 2) continue;                /* line 4: b in O */
-        activate(m, Wr & ~m->mask[b], b);                     /* line 5 */
+        if (popc64(m->mask[b]) >= 2) continue;                /* b already in O */
+        activate(m, Wr & ~m->mask[b], b);                     /* W_r \ W_b */
     }
 }
 
@@ -612,16 +614,16 @@ void orc_assign_overlap(int n, uint64_t *mask, const int *scene_of_body, const i
     membership m = {mask, scene_of_body, part_base, count};
     bfs_ws ws;
     bfs_ws_init(&ws, n);
-    for (int j = 0; j < nj; ++j) {                              /* Alg 2 line 2 */
+    for (int j = 0; j < nj; ++j) {                              /* Alg 2: joints in order */
         int A = eu[j], B = ev[j];
         if (A < 0 || B < 0 || inv_mass[A] == 0 || inv_mass[B] == 0 || A == B) continue;
         uint64_t WA = mask[A], WB = mask[B];
-        if (popc64(WA) == 1 && popc64(WB) == 1 && WA != WB) {   /* line 4 */
+        if (popc64(WA) == 1 && popc64(WB) == 1 && WA != WB) {   /* joint across workers */
             int gamma = scene_gamma[scene_of_body[A]];
-            activate(&m, mask[B], A);                           /* line 5 */
-            grow_overlap(&m, &ws, row_ptr, col, A, gamma, mask[A] | mask[B]);   /* line 6 */
-            activate(&m, mask[A], B);                           /* line 7 */
-            grow_overlap(&m, &ws, row_ptr, col, B, gamma, mask[A] | mask[B]);   /* line 8 */
+            activate(&m, mask[B], A);
+            grow_overlap(&m, &ws, row_ptr, col, A, gamma, mask[A] | mask[B]);
+            activate(&m, mask[A], B);
+            grow_overlap(&m, &ws, row_ptr, col, B, gamma, mask[A] | mask[B]);
         }
     }
     bfs_ws_free(&ws);
@@ -644,9 +646,9 @@ static void geodesics_impl(int n, const uint64_t *mask, const int *sob, const in
         for (int64_t e = entry_ptr[o]; e < entry_ptr[o + 1]; ++e) D[e] = 255;
         if (popc64(Wo) < 2) continue;
         int beta = scene_beta[sob[o]];
-        /* breadth-first from o, depth 1..beta (Alg 5 lines 4-5); the first
-         * body met that is active only in worker i, with i in W_o (line 7),
-         * gives the minimum of Eq 16 for i */
+        /* breadth-first from o, depth 1..beta (Alg 5); the first body met
+         * that is active only in worker i, with i in W_o, gives the minimum
+         * of Eq 16 for i */
         ws.cur++;
         int head = 0, tail = 0;
         ws.queue[tail++] = o;
@@ -671,7 +673,7 @@ static void geodesics_impl(int n, const uint64_t *mask, const int *sob, const in
                 }
             }
         }
-        /* stopping once every worker is met (Alg 5 line 12) changes nothing:
+        /* stopping once every worker is met (as Alg 5 does) changes nothing:
          * later hits are at the same or a larger depth and are not recorded */
     }
     bfs_ws_free(&ws);
@@ -709,10 +711,10 @@ void orc_blend(int k, const double *copies, const double *w, double *out) {
         }
         double qi[4] = {s[3], s[4], s[5], s[6]};
         double dq = qi[0] * q0[0] + qi[1] * q0[1] + qi[2] * q0[2] + qi[3] * q0[3];
-        if (i > 0 && dq < 0) for (int a = 0; a < 4; ++a) qi[a] = -qi[a];   /* lines 7-9 */
+        if (i > 0 && dq < 0) for (int a = 0; a < 4; ++a) qi[a] = -qi[a];   /* Alg 4 sign test */
         for (int a = 0; a < 4; ++a) q[a] += w[i] * qi[a];                  /* Eq 14 */
     }
-    double L = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);  /* line 12 */
+    double L = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);  /* Alg 4 normalisation */
     for (int a = 0; a < 3; ++a) { out[a] = x[a]; out[7 + a] = v[a]; out[10 + a] = om[a]; }
     for (int a = 0; a < 4; ++a) out[3 + a] = q[a] / L;
 }
@@ -1046,7 +1048,7 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
     double *lam = xcalloc((size_t)np_ * 3 + 1, sizeof(double));
     int *slots = xcalloc((size_t)np_ * 2 + 1, sizeof(int));
     uint64_t *prio = xcalloc((size_t)np_ + 1, sizeof(uint64_t));
-    /* rows, fixed for the step from the blended state (Alg 1 lines 7-9) */
+    /* rows, fixed for the step from the blended state (Alg 1) */
     for (int64_t q = 0; q < np_; ++q) {
         int64_t pi = p0 + q;
         pgs_row *r3 = rows + 3 * q;
@@ -1193,7 +1195,7 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
 }
 
 /* ------------------------------------------------------------------------ */
-/* One timestep: Alg 1 lines 7-20.                                           */
+/* One timestep of Alg 1.                                                    */
 /* dt > 0 overrides every scene's dt.                                        */
 /* ------------------------------------------------------------------------ */
 
@@ -1201,18 +1203,18 @@ int orc_step(orc_sim *s, double dt, int iters) {
     free_step_records(s);
     const int n = s->n;
     s->res_sq_total = 0; s->res_max = 0; s->res_rows = 0;
-    /* line 10: contacts */
+    /* contacts */
     contact_input in = {n, s->st, s->rad, s->im, s->np, s->planes, s->plane_scene, s->sob,
                         s->sflags, s->P.margin};
     s->nc = contacts_impl(&in, 1, &s->con);
-    /* line 11: constraint graph G^t from contacts and joints */
+    /* constraint graph G^t from contacts and joints */
     int64_t nedge = s->nc + s->nj;
     int *eu = xcalloc((size_t)nedge + 1, sizeof(int)), *ev = xcalloc((size_t)nedge + 1, sizeof(int));
     for (int64_t i = 0; i < s->nc; ++i) { eu[i] = s->con[i].a; ev[i] = s->con[i].b < n ? s->con[i].b : -1; }
     for (int j = 0; j < s->nj; ++j) { eu[s->nc + j] = s->jab[2 * j]; ev[s->nc + j] = s->jab[2 * j + 1]; }
     s->nadj = build_graph(n, s->im, nedge, eu, ev, &s->row_ptr, &s->col);
     free(eu); free(ev);
-    /* line 12: LOADBALANCE over contacts between two dynamic bodies */
+    /* LOADBALANCE over contacts between two dynamic bodies */
     {
         int64_t m = 0;
         int *ca = xcalloc((size_t)s->nc + 1, sizeof(int)), *cb = xcalloc((size_t)s->nc + 1, sizeof(int));
@@ -1240,7 +1242,7 @@ int orc_step(orc_sim *s, double dt, int iters) {
         for (int w = 0; w < 64; ++w)
             if (s->mask[b] >> w & 1u) s->entry_part[e++] = s->part_base[s->sob[b]] + w;
     }
-    /* lines 13-15: weights from D(o,i) on G^t */
+    /* weights from D(o,i) on G^t */
     s->D = xcalloc((size_t)s->ne + 1, 1);
     geodesics_impl(n, s->mask, s->sob, s->sbeta, s->row_ptr, s->col, s->entry_ptr, s->D);
     s->weight = xcalloc((size_t)s->ne + 1, sizeof(double));
@@ -1307,7 +1309,7 @@ int orc_step(orc_sim *s, double dt, int iters) {
         free(fill);
     }
     free(cons_mask); free(cons_scene);
-    /* line 16: every worker takes its timestep (sequentially here) */
+    /* every worker takes its timestep (sequentially here) */
     s->copies = xcalloc((size_t)s->ne * 13 + 1, sizeof(double));
     s->part_iters = xcalloc((size_t)s->n_parts + 1, sizeof(int));
     s->part_res_sq = xcalloc((size_t)s->n_parts + 1, sizeof(double));
@@ -1336,7 +1338,7 @@ int orc_step(orc_sim *s, double dt, int iters) {
         free(bstart); free(pbody); free(pentry); free(fill);
     }
     free(pcount); free(pstart);
-    /* lines 18-20: blend overlap bodies; others take their single copy */
+    /* blend overlap bodies; others take their single copy */
     for (int b = 0; b < n; ++b) {
         int64_t e0 = s->entry_ptr[b];
         int k = (int)(s->entry_ptr[b + 1] - e0);

@@ -1,5 +1,5 @@
 // ctx.cu -- the C ABI of libovl: context, scene upload, membership, and the
-// timestep of Algorithm 1 (lines 7-20) as a sequence of kernels on one
+// timestep of Algorithm 1 as a sequence of kernels on one
 // stream.  Counts that size the next buffers (contacts, graph edges,
 // entries, pairs) are read back between phases; the load balance runs on the
 // host between the graph and the membership phases.

@@ -139,12 +139,12 @@ void host_assign_overlap(const HostScene &sc, std::vector<uint64_t> &mask) {
         int A = sc.jab[2 * j], B = sc.jab[2 * j + 1];
         if (!dyn(A) || !dyn(B) || A == B) continue;
         uint64_t WA = mem.W(A), WB = mem.W(B);
-        if (popcount(WA) != 1 || popcount(WB) != 1 || WA == WB) continue;   // line 4
+        if (popcount(WA) != 1 || popcount(WB) != 1 || WA == WB) continue;   // joint across workers
         int gamma = sc.scene_gamma[sc.sob[A]];
-        mem.activate(mem.W(B), A);                                          // line 5
-        grow(A, gamma, mem.W(A) | mem.W(B));                                // line 6
-        mem.activate(mem.W(A), B);                                          // line 7
-        grow(B, gamma, mem.W(A) | mem.W(B));                                // line 8
+        mem.activate(mem.W(B), A);
+        grow(A, gamma, mem.W(A) | mem.W(B));
+        mem.activate(mem.W(A), B);
+        grow(B, gamma, mem.W(A) | mem.W(B));
     }
 }
 
@@ -164,10 +164,10 @@ void host_load_balance(const HostScene &sc, std::vector<uint64_t> &mask, int64_t
         const int A = ca[i], B = cb[i];
         const uint64_t WA = mem.W(A), WB = mem.W(B);
         const int scene = sc.sob[A];
-        if ((WA & WB) == 0) {                                   // line 4
+        if ((WA & WB) == 0) {                                   // activation branch
             if (!do_activate) continue;
             int root;
-            if (mem.load(WA, scene) <= mem.load(WB, scene)) {   // line 5
+            if (mem.load(WA, scene) <= mem.load(WB, scene)) {   // ties: B joins W_A
                 mem.activate(WA, B);
                 root = B;
             } else {
@@ -175,18 +175,18 @@ void host_load_balance(const HostScene &sc, std::vector<uint64_t> &mask, int64_t
                 root = A;
             }
             const std::vector<int> &N =
-                ball.collect(row_ptr, col, root, sc.scene_gamma[scene]);   // line 12
-            for (int v : N) mem.activate((WA | WB) & ~mem.W(v), v);         // line 14
+                ball.collect(row_ptr, col, root, sc.scene_gamma[scene]);   // gamma-ball
+            for (int v : N) mem.activate((WA | WB) & ~mem.W(v), v);
             continue;
         }
         if (!do_deactivate) continue;
         const int pa = popcount(WA), pb = popcount(WB);
         if (pa > 1 && pb == 1 && !bridge(A)) {
-            mem.deactivate(WA & ~WB, A);                        // line 17
+            mem.deactivate(WA & ~WB, A);
         } else if (pb > 1 && pa == 1 && !bridge(B)) {
-            mem.deactivate(WB & ~WA, B);                        // line 19
+            mem.deactivate(WB & ~WA, B);
         } else if (WA == WB) {
-            uint64_t keep = uint64_t(1) << mem.least_loaded(WA, scene);   // line 21
+            uint64_t keep = uint64_t(1) << mem.least_loaded(WA, scene);   // ties -> lowest
             mem.deactivate(WA & ~keep, A);
             mem.deactivate(WB & ~keep, B);
         }

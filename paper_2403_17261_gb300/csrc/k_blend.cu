@@ -1,4 +1,4 @@
-// k_blend.cu -- the weights and the blend of Algorithm 1 lines 13-20.
+// k_blend.cu -- the weights and the blend of Algorithm 1.
 //
 // D(o,i) (Eq 16): distance in G^t from an overlap body o to the nearest body
 // active only in worker i, searched up to beta (Algorithm 5).  Instead of one
@@ -14,7 +14,7 @@
 // summed in ascending worker order, a copy's quaternion negated when its
 // dot product with the lowest worker's copy is negative, then normalised.
 // Every worker integrated its copy from the same blended state, x_i = x + h v_i
-// (Algorithm 1 lines 7-9 and 16), so Eq 11 equals x + h sum w_i v_i; the
+// (Algorithm 1), so Eq 11 equals x + h sum w_i v_i; the
 // position is formed that way, which rounds once in FP32 instead of twice.
 // Bodies in one worker take their copy unchanged.
 #include "common.cuh"

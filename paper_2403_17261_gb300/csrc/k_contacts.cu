@@ -1,5 +1,5 @@
-// k_contacts.cu -- contacts of the blended state (Algorithm 1 line 10,
-// "getContacts", Section 5.4) and the constraint graph G^t (line 11,
+// k_contacts.cu -- contacts of the blended state (Algorithm 1, contact
+// generation, Section 5.4) and the constraint graph G^t (Algorithm 1,
 // Section 5.1).
 //
 // Broadphase: spatial hash grid, one thread per body (cell size >= the
@@ -254,7 +254,7 @@ __global__ void k_adj_compact(const int *__restrict__ tptr, const int *__restric
 // Load-balance candidates: contacts between two dynamic bodies (all of
 // them when the removal branches run), or only those whose worker sets are
 // disjoint (activation-only steps: activations only add workers, so a pair
-// that shares a worker now can never reach Algorithm 6 line 4 later).
+// that shares a worker now can never reach Algorithm 6's activation branch later).
 __global__ void k_lb_flags(const int2 *__restrict__ c_ab, int nc, const float *__restrict__ im, int n,
                            const uint64_t *__restrict__ mask, int disjoint_only, int *__restrict__ flag) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {

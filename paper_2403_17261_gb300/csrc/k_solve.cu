@@ -1,4 +1,4 @@
-// k_solve.cu -- every worker's timestep (Algorithm 1 line 16): projected
+// k_solve.cu -- every worker's timestep (Algorithm 1): projected
 // Gauss-Seidel on the MLCP of Eq 1-7 over the worker's active bodies and
 // constraints, then integration (Section 3: velocities first, positions with
 // the new velocities), writing the worker's copy of each body.

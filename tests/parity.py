@@ -78,7 +78,7 @@ def compare_step(orc, gpu, dt: float = 0.0, iters: int | None = None, check_lamb
     gpu.step(dt, iters)
     rep = {}
     sc = orc.scene
-    # contacts (Algorithm 1 line 10)
+    # contacts (Algorithm 1, contact generation)
     ab_o, phi_o, n_o, t_o = orc.contacts()
     ab_g, phi_g, n_g, t_g = gpu.contacts()
     assert ab_o.shape == ab_g.shape, (ab_o.shape, ab_g.shape)
@@ -88,13 +88,13 @@ def compare_step(orc, gpu, dt: float = 0.0, iters: int | None = None, check_lamb
     rep["normal"] = _maxabs(n_o, n_g)
     rep["t1"] = _maxabs(t_o, t_g)
     assert rep["phi"] <= TOL_GEOM and rep["normal"] <= TOL_GEOM and rep["t1"] <= TOL_GEOM, rep
-    # constraint graph (line 11)
+    # constraint graph
     rp_o, col_o = orc.graph()
     rp_g, col_g = gpu.graph()
     assert np.array_equal(rp_o, rp_g) and np.array_equal(col_o, col_g), "graph differs"
-    # membership after the load balance (line 12)
+    # membership after the load balance
     assert np.array_equal(orc.masks(), gpu.membership()), "membership differs"
-    # entries, geodesics, weights, copies (lines 13-16)
+    # entries, geodesics, weights, copies
     eo, eg = orc.entries(), gpu.entries()
     assert np.array_equal(eo["entry_ptr"], eg["entry_ptr"].astype(np.int64)), "entries differ"
     assert np.array_equal(eo["part"], eg["part"]), "entry workers differ"
@@ -118,7 +118,7 @@ def compare_step(orc, gpu, dt: float = 0.0, iters: int | None = None, check_lamb
     rep["lambda"] = _maxabs(po["lam"], pg["lam"])
     if check_lambda:
         assert rep["lambda"] <= tol_v * max(1.0, mmax), rep
-    # blended state (lines 18-20)
+    # blended state
     rep["x"] = _maxabs(so[:, 0:3], sg[:, 0:3])
     rep["q"] = _qdist(so[:, 3:7], sg[:, 3:7])
     rep["v"] = _maxabs(so[:, 7:13], sg[:, 7:13])

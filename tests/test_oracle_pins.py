@@ -108,13 +108,13 @@ def _lb(masks, n_sets, contacts, extra_edges=(), gamma=0, act=True, deact=True):
 
 def test_lb_inter_worker_goes_to_lighter_side():
     # (i): A=0 in worker 0 with 3 idle companions, B=1 alone in worker 1:
-    # <W_A> = 4 > <W_B> = 1, so A is activated in W_B (line 9)
+    # <W_A> = 4 > <W_B> = 1, so A is activated in W_B
     out = _lb([1, 2, 1, 1, 1], 2, [(0, 1)])
     assert list(out) == [3, 2, 1, 1, 1]
 
 
 def test_lb_tie_activates_b_in_wa():
-    # equal loads: line 5 uses <=, so B joins W_A
+    # equal loads: the comparison is <=, so B joins W_A
     out = _lb([1, 2], 2, [(0, 1)])
     assert list(out) == [1, 3]
 
@@ -129,7 +129,7 @@ def test_lb_growth_depth():
 
 def test_lb_overlap_not_bridge_is_removed():
     # (iii): B=1 in both workers touches only A=0 (worker 0): not a bridge, so
-    # B keeps only W_A (line 19)
+    # B keeps only W_A
     out = _lb([1, 3], 2, [(0, 1)])
     assert list(out) == [1, 1]
 
