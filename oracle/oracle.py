@@ -81,6 +81,7 @@ def lib():
         L.orc_get_entries.argtypes = [C.c_void_p, i64p, ip, u8p, dp, dp]
         L.orc_get_pairs.argtypes = [C.c_void_p, ip, ip, i64p, u64p, ip, dp]
         L.orc_get_part_stats.argtypes = [C.c_void_p, ip, dp, i64p, ip]
+        L.orc_get_features.argtypes = [C.c_void_p, dp, dp, ip, u8p]
         L.orc_get_metrics.argtypes = [C.c_void_p, dp]
         L.orc_contacts.restype = C.c_int64
         L.orc_contacts.argtypes = [C.c_int, dp, dp, dp, C.c_int, dp, ip, ip, ip, C.c_double, C.c_int,
@@ -375,6 +376,19 @@ class OracleSim:
                             _ptr(key, u64p), _ptr(colour_, ip), _ptr(lam, dp))
         return dict(part=part[:m], kind=kind[:m], cidx=cidx[:m], key=key[:m], colour=colour_[:m],
                     lam=lam[:m])
+
+    N_FEATURES = 12
+    DEPTH_CAP = 8
+
+    def features(self):
+        """Learned-warm-start features of the last step: per pair [12], the
+        scale s, whether previous impulses existed; per body the depth to O."""
+        m = self.counts()["pairs"]
+        mm = max(m, 1)
+        f, sc, found = np.zeros((mm, 12)), np.zeros(mm), np.zeros(mm, np.int32)
+        depth = np.zeros(max(self.n, 1), np.uint8)
+        lib().orc_get_features(self._h, _ptr(f, dp), _ptr(sc, dp), _ptr(found, ip), _ptr(depth, u8p))
+        return dict(feat=f[:m], scale=sc[:m], found=found[:m].astype(bool), depth=depth[:self.n])
 
     def part_stats(self):
         n = self.n_parts

@@ -56,6 +56,19 @@
  *    worker; bodies outside O take their single copy unchanged.
  *  - Newly activated bodies start from the blended state (every worker reads
  *    the one blended state at the start of a step, Alg 1).
+ *  - Learned warm start (not in the paper): 12 features per (worker,
+ *    contact) pair, all taken from the blended state at the start of the
+ *    step (before gravity) and made dimensionless with g_ref = max(|g|, 1):
+ *      0-2  J v along n, t1, t2 (B minus A; static ends have v = 0) / (g_ref h)
+ *      3    penetration max(-phi, 0) / (g_ref h^2)
+ *      4-6  the previous-step impulses the plain warm start applies / s
+ *      7-8  inverse masses of A and B (0 for a static end or a plane)
+ *      9-10 degrees of A and B in G^t / 8 (0 for a static end)
+ *      11   min over the dynamic ends of the BFS distance in G^t to the
+ *           nearest body of O, capped at ORC_DEPTH_CAP, / ORC_DEPTH_CAP
+ *    with s = k_n g_ref h, k_n = 1 / (im_A + im_B) over the dynamic ends:
+ *    the impulse that cancels one step of gravity on the normal row.  Joint
+ *    pairs have all-zero features and s = 0.
  *
  * Build: gcc -O2 -ffp-contract=off -std=c11 -shared -fPIC (no fused
  * multiply-add, so FP32 decisions round exactly as written).
@@ -71,6 +84,8 @@
 #define ORC_ERR_MEMBERSHIP (-6)
 
 #define ORC_MAX_COLOURS 256
+#define ORC_DEPTH_CAP 8       /* depth feature: BFS levels searched from O */
+#define ORC_NFEAT 12
 
 typedef struct {
     double gravity[3];
@@ -809,6 +824,10 @@ typedef struct {
     int64_t npairs;
     int *pair_part; int *pair_kind; int64_t *pair_cidx; uint64_t *pair_key; int *pair_colour;
     double *pair_lam;   /* npairs x 3 */
+    double *pair_feat;  /* npairs x ORC_NFEAT learned-warm-start features */
+    double *pair_scale; /* npairs: s = k_n g_ref h (0 for joints) */
+    int *pair_found;    /* npairs: 1 if the previous step left impulses for it */
+    uint8_t *depth;     /* n: BFS distance in G^t to O, capped at ORC_DEPTH_CAP */
     int *part_iters; double *part_res_sq; int64_t *part_rows; int *part_colours;
     double res_sq_total; double res_max; int64_t res_rows;
     double joint_violation_max;
@@ -870,6 +889,8 @@ static void free_step_records(orc_sim *s) {
     free(s->pair_colour); free(s->pair_lam);
     s->pair_part = s->pair_kind = s->pair_colour = NULL; s->pair_cidx = NULL; s->pair_key = NULL;
     s->pair_lam = NULL;
+    free(s->pair_feat); free(s->pair_scale); free(s->pair_found); free(s->depth);
+    s->pair_feat = NULL; s->pair_scale = NULL; s->pair_found = NULL; s->depth = NULL;
     free(s->part_iters); free(s->part_res_sq); free(s->part_rows); free(s->part_colours);
     s->part_iters = NULL; s->part_res_sq = NULL; s->part_rows = NULL; s->part_colours = NULL;
 }
@@ -1195,6 +1216,83 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
 }
 
 /* ------------------------------------------------------------------------ */
+/* Learned warm start: features of every (worker, contact) pair, read from   */
+/* the blended state at the start of the step (definitions in the header).   */
+/* ------------------------------------------------------------------------ */
+
+static void compute_features(orc_sim *s, double dt_override) {
+    const int n = s->n;
+    /* depth: breadth-first from every body of O at once */
+    s->depth = xcalloc((size_t)n + 1, 1);
+    int *queue = xcalloc((size_t)n + 1, sizeof(int));
+    int head = 0, tail = 0;
+    for (int b = 0; b < n; ++b) {
+        if (s->im[b] > 0 && popc64(s->mask[b]) >= 2) { s->depth[b] = 0; queue[tail++] = b; }
+        else s->depth[b] = ORC_DEPTH_CAP;
+    }
+    while (head < tail) {
+        int u = queue[head++];
+        if (s->depth[u] + 1 >= ORC_DEPTH_CAP) continue;
+        for (int k = s->row_ptr[u]; k < s->row_ptr[u + 1]; ++k) {
+            int v = s->col[k];
+            if (s->depth[v] != ORC_DEPTH_CAP) continue;
+            s->depth[v] = (uint8_t)(s->depth[u] + 1);
+            queue[tail++] = v;
+        }
+    }
+    free(queue);
+    double g = sqrt(dot3(s->P.gravity, s->P.gravity));
+    double g_ref = g > 1.0 ? g : 1.0;
+    s->pair_feat = xcalloc((size_t)s->npairs * ORC_NFEAT + 1, sizeof(double));
+    s->pair_scale = xcalloc((size_t)s->npairs + 1, sizeof(double));
+    s->pair_found = xcalloc((size_t)s->npairs + 1, sizeof(int));
+    for (int64_t q = 0; q < s->npairs; ++q) {
+        const double *prev = ws_lookup(s, s->pair_part[q], s->pair_key[q]);
+        s->pair_found[q] = prev != NULL;
+        if (s->pair_kind[q] != 0) continue;
+        const orc_contact *c = &s->con[s->pair_cidx[q]];
+        int a = c->a, b = c->b;
+        int dyn_a = s->im[a] > 0, dyn_b = b < n && s->im[b] > 0;
+        int scene = s->sob[a];
+        double h = dt_override > 0 ? dt_override : s->dt[scene];
+        /* velocity of each end's contact point; rA = r_a n, rB = -r_b n */
+        double pa[3] = {0, 0, 0}, pb[3] = {0, 0, 0};
+        if (dyn_a) {
+            const double *x = s->st + 13 * (size_t)a;
+            double rA[3] = {s->rad[a] * c->n[0], s->rad[a] * c->n[1], s->rad[a] * c->n[2]}, wr[3];
+            cross3(x + 10, rA, wr);
+            for (int k = 0; k < 3; ++k) pa[k] = x[7 + k] + wr[k];
+        }
+        if (dyn_b) {
+            const double *x = s->st + 13 * (size_t)b;
+            double rB[3] = {-s->rad[b] * c->n[0], -s->rad[b] * c->n[1], -s->rad[b] * c->n[2]}, wr[3];
+            cross3(x + 10, rB, wr);
+            for (int k = 0; k < 3; ++k) pb[k] = x[7 + k] + wr[k];
+        }
+        double rel[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+        double t2[3];
+        cross3(c->n, c->t1, t2);
+        double ima = dyn_a ? s->im[a] : 0.0, imb = dyn_b ? s->im[b] : 0.0;
+        double scale = g_ref * h / (ima + imb);
+        double *f = s->pair_feat + (size_t)q * ORC_NFEAT;
+        f[0] = dot3(c->n, rel) / (g_ref * h);
+        f[1] = dot3(c->t1, rel) / (g_ref * h);
+        f[2] = dot3(t2, rel) / (g_ref * h);
+        f[3] = fmax(-c->phi, 0.0) / (g_ref * h * h);
+        for (int k = 0; k < 3; ++k) f[4 + k] = prev ? prev[k] * s->P.warmstart / scale : 0.0;
+        f[7] = ima;
+        f[8] = imb;
+        f[9] = dyn_a ? (s->row_ptr[a + 1] - s->row_ptr[a]) / 8.0 : 0.0;
+        f[10] = dyn_b ? (s->row_ptr[b + 1] - s->row_ptr[b]) / 8.0 : 0.0;
+        int d = ORC_DEPTH_CAP;
+        if (dyn_a && s->depth[a] < d) d = s->depth[a];
+        if (dyn_b && s->depth[b] < d) d = s->depth[b];
+        f[11] = (double)d / ORC_DEPTH_CAP;
+        s->pair_scale[q] = scale;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* One timestep of Alg 1.                                                    */
 /* dt > 0 overrides every scene's dt.                                        */
 /* ------------------------------------------------------------------------ */
@@ -1309,6 +1407,7 @@ int orc_step(orc_sim *s, double dt, int iters) {
         free(fill);
     }
     free(cons_mask); free(cons_scene);
+    compute_features(s, dt);
     /* every worker takes its timestep (sequentially here) */
     s->copies = xcalloc((size_t)s->ne * 13 + 1, sizeof(double));
     s->part_iters = xcalloc((size_t)s->n_parts + 1, sizeof(int));
@@ -1417,6 +1516,15 @@ void orc_get_pairs(const orc_sim *s, int *part, int *kind, int64_t *cidx, uint64
     memcpy(key, s->pair_key, (size_t)s->npairs * sizeof(uint64_t));
     memcpy(colour, s->pair_colour, (size_t)s->npairs * sizeof(int));
     memcpy(lam, s->pair_lam, (size_t)s->npairs * 3 * sizeof(double));
+}
+
+/* per pair: ORC_NFEAT features, scale s, previous-impulse flag; per body:
+ * depth to O (all of the last step) */
+void orc_get_features(const orc_sim *s, double *feat, double *scale, int *found, uint8_t *depth) {
+    memcpy(feat, s->pair_feat, (size_t)s->npairs * ORC_NFEAT * sizeof(double));
+    memcpy(scale, s->pair_scale, (size_t)s->npairs * sizeof(double));
+    memcpy(found, s->pair_found, (size_t)s->npairs * sizeof(int));
+    memcpy(depth, s->depth, (size_t)s->n);
 }
 
 /* per worker: iterations run, residual sum of squares, rows, colours */

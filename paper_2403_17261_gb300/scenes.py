@@ -443,6 +443,72 @@ def random_pile(n: int, seed: int, n_sets: int = 3, box: float = 3.0, radius_lo:
     return sc
 
 
+def spinning_sphere(omega_y: float = 3.0, height: float = 0.5, radius: float = 0.5,
+                    mass: float = 1.0, dt: float = 1.0 / 60.0) -> Scene:
+    """One sphere above the ground plane z=0 with its centre at ``height``
+    (height < radius: penetrating), spinning about y, no linear velocity."""
+    pos = np.array([[0.0, 0.0, height]])
+    sc = _single("spinning_sphere", pos, [radius], [1.0 / mass], [[0, 0, 1, 0]], mu=0.5, dt=dt,
+                 flags=1, gamma=0, beta=2, n_sets=1, set_of_body=[0], iters=20, steps=1)
+    st = sc.state.astype(np.float64)
+    st[0, 11] = omega_y
+    sc.state = st.astype(np.float32)
+    return sc
+
+
+def head_on(speed: float = 1.0, gap: float = 0.0, radius: float = 0.5, mass: float = 1.0,
+            dt: float = 1.0 / 60.0) -> Scene:
+    """Two free spheres on the x axis, ``gap`` apart, moving towards each other
+    at ``speed`` each; no planes."""
+    pos = np.array([[0.0, 0.0, 5.0], [2 * radius + gap, 0.0, 5.0]])
+    sc = _single("head_on", pos, [radius, radius], [1.0 / mass, 1.0 / mass], np.zeros((0, 4)),
+                 mu=0.5, dt=dt, flags=1, gamma=0, beta=2, n_sets=1, set_of_body=[0, 0], iters=20,
+                 steps=1)
+    st = sc.state.astype(np.float64)
+    st[0, 7], st[1, 7] = speed, -speed
+    sc.state = st.astype(np.float32)
+    return sc
+
+
+# ----------------------------------------------------------------------------
+# Learned warm start: seeded parameters and synthetic training rows
+# ----------------------------------------------------------------------------
+
+MLP_LAYERS = (12, 64, 64, 3)
+MLP_N_PARAMS = 12 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
+
+
+def mlp_init_params(seed: int = 5) -> np.ndarray:
+    """Initial parameters of the 12-64-64-3 network in the C ABI's layout
+    (W1 [12][64], b1, W2 [64][64], b2, W3 [64][3], b3): weights uniform in
+    +-sqrt(6 / fan_in) (He et al. 2015, uniform form), biases zero; FP32."""
+    rng = SplitMix64(seed)
+    parts = []
+    for fan_in, fan_out in zip(MLP_LAYERS[:-1], MLP_LAYERS[1:]):
+        lim = math.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(fan_in * fan_out, -lim, lim))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def synthetic_rows(n: int, seed: int = 6) -> tuple[np.ndarray, np.ndarray]:
+    """n rows of (12 features, 3 targets) in the ranges the step produces
+    (FP32): scaled velocities in +-3, penetration in [0, 2], previous impulses
+    around 1, inverse masses in [0, 4], degrees in [0, 1.5], depth in [0, 1];
+    targets near the previous impulses.  For gradient and training checks."""
+    rng = SplitMix64(seed)
+    f = np.zeros((n, 12))
+    f[:, 0:3] = rng.uniform(3 * n, -3.0, 3.0).reshape(n, 3)
+    f[:, 3] = rng.uniform(n, 0.0, 2.0)
+    f[:, 4] = rng.uniform(n, 0.0, 2.0)
+    f[:, 5:7] = rng.uniform(2 * n, -0.5, 0.5).reshape(n, 2)
+    f[:, 7:9] = rng.uniform(2 * n, 0.0, 4.0).reshape(n, 2)
+    f[:, 9:11] = rng.uniform(2 * n, 0.0, 1.5).reshape(n, 2)
+    f[:, 11] = rng.uniform(n, 0.0, 1.0)
+    t = f[:, 4:7] + rng.uniform(3 * n, -0.3, 0.3).reshape(n, 3)
+    return f.astype(np.float32), t.astype(np.float32)
+
+
 WORKLOADS = {
     "pile_small": pile_small,
     "chain": chain,
