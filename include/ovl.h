@@ -70,6 +70,17 @@ typedef struct ovl_params {
 #define OVL_FLAG_TIMING 2    /* record per-phase times with CUDA events (ovl_read_stats) */
 #define OVL_FLAG_AUTOTUNE 4  /* time the solver's launch shapes on the first step of every problem-size
                                 bucket and keep the fastest (results are bit-identical across shapes) */
+#define OVL_FLAG_FEATURES 8  /* compute the learned warm start's contact features every step, even
+                                with the plain warm start (ovl_read_features) */
+
+/* Warm-start modes (ovl_set_warmstart_mode).  PREVIOUS is the method's own
+ * warm start: each (worker, constraint) starts from the impulses it had in
+ * the previous step, times ovl_params.warmstart, or from zero.  The MLP
+ * modes replace that start for contacts by the network's proposal (below);
+ * joints always keep the previous impulses. */
+#define OVL_WS_PREVIOUS 0
+#define OVL_WS_MLP 1       /* every contact starts from the network's proposal */
+#define OVL_WS_MLP_NEW 2   /* only contacts without previous impulses do */
 
 /* A scene (or a batch of independent scenes whose bodies are contiguous). */
 typedef struct ovl_scene_desc {
@@ -107,7 +118,9 @@ typedef struct ovl_stats {
     int32_t device_status;     /* first device-side error code of the step, 0 if none */
     double residual_rms;       /* RMS complementarity residual over all rows (OVL_FLAG_RESIDUAL) */
     double residual_max;       /* max |residual| */
-    float phase_ms[12];        /* per-phase device times (OVL_FLAG_TIMING); see ovl_phase_name */
+    float phase_ms[12];        /* per-phase device times (OVL_FLAG_TIMING); see ovl_phase_name;
+                                  index 10 = learned warm start (features + network), which the
+                                  membership phase (index 3) includes */
     int64_t n_launches;        /* CUDA kernels the library launched during the last step */
     int32_t solve_cluster;     /* CTAs per worker of the last solve */
     int32_t solve_threads;     /* threads per CTA of the last solve */
@@ -206,6 +219,94 @@ ovl_status ovl_autotune_import(ovl_ctx *ctx, const char *json);
 /* Per worker: sweeps run, residual sum of squares, rows, colours. */
 ovl_status ovl_read_worker_stats(ovl_ctx *ctx, int32_t *iters, double *res_sq, int64_t *rows,
                                  int32_t *colours);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (not in the paper)
+ *
+ * A 12-64-64-3 ReLU network proposes each contact's three impulses
+ * (normal, t1, t2) from 12 features of the contact, all read from the
+ * blended state at the start of the step, before gravity.  With
+ * g_ref = max(|gravity|, 1) and s = g_ref h / (im_A + im_B) over the dynamic
+ * ends (the impulse that cancels one step of gravity on the normal row):
+ *   0-2  J v along n, t1, t2 (B minus A; static ends have v = 0) / (g_ref h)
+ *   3    penetration max(-phi, 0) / (g_ref h^2)
+ *   4-6  the previous-step impulses the plain warm start applies / s
+ *   7-8  inverse masses of A and B (0 for a static end or a plane)
+ *   9-10 degrees of A and B in G^t / 8 (0 for a static end)
+ *   11   min over the dynamic ends of the BFS distance in G^t to the nearest
+ *        body of O, capped at 8, / 8
+ * The network's three outputs y are impulses / s; features 4-6 feed them
+ * directly, so the layers learn a correction to the method's own warm start.
+ * The warm start is s y with the normal impulse made non-negative and each
+ * friction impulse clamped to +-mu times it.  Inference uses BF16 operands with FP32 accumulation on the
+ * tensor cores.  Training reads a log of (features, impulses / s) pairs that
+ * steps append, minimises the mean squared error with Adam, and runs in the
+ * library's own forward and backward kernels (BF16 operands, FP32 sums, FP32
+ * master parameters).
+ *
+ * Parameter vector (OVL_MLP_N_PARAMS floats): W1 [12][64] (input-major), b1
+ * [64], W2 [64][64], b2 [64], W3 [64][3], b3 [3]; y = x[4:7] + W3^T
+ * relu(W2^T relu(W1^T x + b1) + b2) + b3.
+ * ------------------------------------------------------------------------ */
+#define OVL_MLP_N_PARAMS 5187
+#define OVL_N_FEATURES 12
+
+/* OVL_WS_PREVIOUS, OVL_WS_MLP or OVL_WS_MLP_NEW for the following steps.
+ * The MLP modes need parameters (ovl_mlp_set_params). */
+ovl_status ovl_set_warmstart_mode(ovl_ctx *ctx, int32_t mode);
+
+/* Per (worker, constraint) pair of the last step, in ovl_read_pairs order
+ * (host outputs, n_pairs rows; any may be NULL): the features [12] (zero for
+ * joints), the scale s (0 for joints), 1 if previous impulses existed, and
+ * the warm-start impulses [3] the solve started from.  OVL_ERR_ARG if the
+ * last step computed no features (plain mode without OVL_FLAG_FEATURES or
+ * logging). */
+ovl_status ovl_read_features(ovl_ctx *ctx, float *feat12, float *scale, int32_t *found,
+                             float *lambda0_3);
+
+/* Sets / reads the network's parameters (host arrays of n =
+ * OVL_MLP_N_PARAMS floats).  Setting them also resets Adam's moments and
+ * step count. */
+ovl_status ovl_mlp_set_params(ovl_ctx *ctx, const float *theta, int32_t n);
+ovl_status ovl_mlp_get_params(ovl_ctx *ctx, float *theta, int32_t n);
+
+/* The network's raw outputs y [n][3] for host features [n][12] (the same
+ * kernel the step uses). */
+ovl_status ovl_mlp_forward(ovl_ctx *ctx, int64_t n, const float *feat12, float *y3);
+
+/* The training log: rows of (features [12], target impulses / s [3]) in
+ * device memory.  reserve: allocates room for capacity rows (0 frees) and
+ * empties it.  enable: while on, every step appends its contact pairs with
+ * the impulses its solve ended with (rows beyond the capacity are dropped).
+ * append / read: host rows in and out, e.g. for data made elsewhere. */
+ovl_status ovl_log_reserve(ovl_ctx *ctx, int64_t capacity);
+ovl_status ovl_log_enable(ovl_ctx *ctx, int32_t on);
+ovl_status ovl_log_size(ovl_ctx *ctx, int64_t *n);
+ovl_status ovl_log_append(ovl_ctx *ctx, int64_t n, const float *feat12, const float *target3);
+ovl_status ovl_log_read(ovl_ctx *ctx, int64_t first, int64_t n, float *feat12, float *target3);
+
+typedef struct ovl_train_desc {
+    int64_t first, count;  /* log rows [first, first + count) */
+    int32_t batch;         /* samples per Adam step, 1 .. 1048576 */
+    int32_t steps;         /* Adam steps */
+    int32_t sampling;      /* 0: consecutive batches cycling through the rows; 1: rows drawn
+                              uniformly with replacement (SplitMix64 of seed and sample index) */
+    float lr, beta1, beta2, eps;   /* Adam (defaults 1e-3, 0.9, 0.999, 1e-8) */
+    uint64_t seed;
+} ovl_train_desc;
+
+/* Runs desc->steps Adam steps on the mean squared error of the scaled
+ * impulses; loss_per_step (host, may be NULL) receives the loss of each
+ * step's batch before its update. */
+ovl_status ovl_mlp_train(ovl_ctx *ctx, const ovl_train_desc *desc, float *loss_per_step);
+
+/* Gradient [OVL_MLP_N_PARAMS] and loss of the mean squared error over the
+ * log rows [first, first + count) at the current parameters (no update);
+ * count <= 1048576. */
+ovl_status ovl_mlp_grad(ovl_ctx *ctx, int64_t first, int64_t count, float *grad, double *loss);
+
+/* Mean squared error over the log rows [first, first + count). */
+ovl_status ovl_mlp_loss(ovl_ctx *ctx, int64_t first, int64_t count, double *loss);
 
 /* ------------------------------------------------------------------------
  * Geodesic distances without allocation

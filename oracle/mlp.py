@@ -2,8 +2,10 @@
 
 The network maps the 12 contact features (their definitions are in the
 header of ``ovl_oracle.c``) to the three impulses of the contact divided by
-its scale s: y = W3^T relu(W2^T relu(W1^T x + b1) + b2) + b3, with layers
-12-64-64-3.  It is trained by mean squared error against impulses the solver
+its scale s: y = x[4:7] + W3^T relu(W2^T relu(W1^T x + b1) + b2) + b3, with
+layers 12-64-64-3.  Features 4-6 are the previous-step impulses / s, so the
+layers learn a correction to the method's own warm start (zero for a new
+contact's missing history).  It is trained by mean squared error against impulses the solver
 produced, with Adam (Kingma & Ba, Algorithm 1: bias-corrected first and
 second moments).  None of this is in the paper: it is the learned part added
 on top of the method's warm start.
@@ -52,7 +54,7 @@ def forward(theta, X):
     h1 = relu(z1)
     z2 = h1 @ p["W2"] + p["b2"]
     h2 = relu(z2)
-    y = h2 @ p["W3"] + p["b3"]
+    y = X[:, 4:7] + h2 @ p["W3"] + p["b3"]
     return y, dict(X=X, z1=z1, h1=h1, z2=z2, h2=h2)
 
 

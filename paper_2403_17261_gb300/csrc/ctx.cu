@@ -15,126 +15,12 @@
 #include <string>
 #include <vector>
 
-#include "common.cuh"
-#include "kernels.cuh"
+#include "ctx.cuh"
 
 using namespace ovl;
 
-struct ovl_ctx {
-    ovl_params P{};
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int device = 0;
-    int smem_optin = 0;
-    int num_sms = 0;
-    int smem_per_sm = 0;
-    int nb_max = 0;          // most bodies in one worker (last membership phase)
-    int last_cluster = 1, last_threads = 512, last_unroll = 1;
-    struct TuneCfg { int cluster, threads, unroll; float ms; };
-    std::map<std::string, TuneCfg> tuned;   // autotuner results by problem-size bucket
-    std::string err;
-
-    // scene (host copies)
-    bool has_scene = false;
-    HostScene hs;
-    int n = 0, np = 0, nj = 0, ns = 0, n_parts = 0, beta_max = 0;
-    std::vector<float> h_radius, h_im;
-    std::vector<int> h_body_base, h_plane_ptr, h_part_scene;
-    float cs = 1.f;
-    uint32_t tsize = 0;
-    long long vb_bits = 0;
-
-    // scene (device)
-    DBuf<float4> st, st_alt;
-    DBuf<float> radius, im, scene_mu, scene_dt;
-    DBuf<int> sob, scene_flags, n_sets, part_base, body_base, scene_beta, joint_scene, part_scene;
-    DBuf<float4> planes;
-    DBuf<int> plane_ptr, plane_list;
-    DBuf<int2> jab;
-    DBuf<float4> janc;
-    DBuf<long long> vb_base;
-    DBuf<uint64_t> mask;
-
-    // step buffers
-    DBuf<int> status;
-    DBuf<int4> cell;
-    DBuf<int> bucket_count, bucket_start, cursor, items, nb_list, nb_count, ccount, cstart;
-    DBuf<int2> c_ab;
-    DBuf<float4> c_n, c_t1;
-    DBuf<int> deg, tptr, cursor2, tcol, ucount, row_ptr, col;
-    DBuf<int> entry_count, entry_ptr, entry_body, entry_part, entry_slot, part_list, part_count,
-        part_bstart;
-    DBuf<uint32_t> sk, sv, sk2, sv2;
-    DBuf<int> cons_count, cons_start, pair_cons, pair_part, ps_cons, ps_part, part_pcount,
-        part_pstart, p_colour, part_ncol, part_rounds, col_off, pair_of_row;
-    DBuf<uint64_t> p_key;
-    DBuf<int2> p_slot;
-    DBuf<float4> p_lam0;
-    DBuf<unsigned long long> colour_scratch;
-    DBuf<int4> worklist, worklist2;
-    DBuf<unsigned long long> wprio, wprio2;
-    DBuf<float4> r0, r1, r2, r3, rlam, lam_out;
-    DBuf<int> rpair;
-    DBuf<int> ws_pstart;
-    DBuf<uint64_t> ws_key;
-    DBuf<float4> ws_lam;
-    int64_t ws_n = 0;
-    DBuf<float4> copies, solve_scratch;
-    DBuf<int> part_iters;
-    DBuf<double> part_res_sq;
-    DBuf<uint32_t> visited, queue;
-    DBuf<int> qctl;
-    DBuf<uint8_t> D;
-    DBuf<float> weight;
-    DBuf<float> stage13;   // staging for host <-> device state transfers
-    DBuf<int> scan_tmp, sort_hist, sort_tmp;
-    HBuf<int> h_i32;
-    HBuf<int2> h_ab;
-    HBuf<int> h_rp, h_col;
-    HBuf<uint64_t> h_mask;
-    DBuf<int> lb_flag, lb_pos;
-    DBuf<int2> lb_pairs;
-    std::vector<int> lb_a, lb_b;
-    std::vector<uint64_t> lb_mask;
-
-    // last step
-    int64_t step_index = 0;
-    int nc = 0, nadj = 0, ne = 0, npairs = 0;
-    bool have_step = false;
-    cudaEvent_t ev[16] = {};
-    float phase_ms[12] = {};
-    long long last_launches = 0;
-    long long lb_candidates = 0;
-    double lb_host_ms = 0.0;
-};
 
 namespace {
-
-ovl_status fail(ovl_ctx *c, ovl_status code, const std::string &msg) {
-    if (c) c->err = msg;
-    return code;
-}
-
-template <class F>
-ovl_status guarded(ovl_ctx *c, F &&f) {
-    if (!c) return OVL_ERR_ARG;
-    try {
-        return f();
-    } catch (const CudaError &e) {
-        return fail(c, OVL_ERR_CUDA, std::string(e.what) + ": " + cudaGetErrorString(e.err));
-    } catch (const std::bad_alloc &) {
-        return fail(c, OVL_ERR_CUDA, "host allocation failed");
-    } catch (const std::exception &e) {
-        return fail(c, OVL_ERR_ARG, e.what());
-    }
-}
-
-int read_i32(ovl_ctx *c, const int *dptr) {
-    c->h_i32.ensure(1);
-    CK(cudaMemcpyAsync(c->h_i32.p, dptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return c->h_i32.p[0];
-}
 
 uint32_t next_pow2(uint64_t x) {
     uint32_t p = 1;
@@ -607,12 +493,14 @@ ovl_status run_step(ovl_ctx *c, float dt, int iters) {
     phase_load_balance(c, c->P.lb_activate != 0, deact);
     mark(c, 3);
     phase_membership(c, dt);
+    phase_warmstart(c, dt);
     mark(c, 4);
     phase_colour(c);
     mark(c, 5);
     phase_rows(c, dt);
     mark(c, 6);
     phase_solve(c, dt, iters);
+    phase_log(c);
     mark(c, 7);
     phase_geodesics(c);
     mark(c, 8);
@@ -625,6 +513,8 @@ ovl_status run_step(ovl_ctx *c, float dt, int iters) {
         CK(cudaEventSynchronize(c->ev[9]));
         for (int i = 0; i < 9; ++i) CK(cudaEventElapsedTime(&c->phase_ms[i], c->ev[i], c->ev[i + 1]));
         CK(cudaEventElapsedTime(&c->phase_ms[9], c->ev[0], c->ev[9]));
+        c->phase_ms[10] = 0.f;
+        if (c->feat_valid) CK(cudaEventElapsedTime(&c->phase_ms[10], c->ev[12], c->ev[13]));
     }
     if (st != OVL_OK) return st;
     c->step_index++;
@@ -692,9 +582,10 @@ ovl_status ovl_create(ovl_ctx **out, const ovl_params *p, void *cuda_stream) {
 const char *ovl_last_error(const ovl_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 const char *ovl_phase_name(int32_t phase) {
-    static const char *names[] = {"contacts", "graph", "load_balance", "membership", "colouring",
-                                  "rows",     "solve", "geodesics",    "blend",      "total"};
-    return (phase >= 0 && phase < 10) ? names[phase] : "";
+    static const char *names[] = {"contacts", "graph",     "load_balance", "membership",
+                                  "colouring", "rows",     "solve",        "geodesics",
+                                  "blend",     "total",    "warmstart"};
+    return (phase >= 0 && phase < 11) ? names[phase] : "";
 }
 
 }  // extern "C"
@@ -727,11 +618,6 @@ void release_all(ovl_ctx *c) {
     c->lb_flag.release(); c->lb_pos.release(); c->lb_pairs.release();
 }
 
-template <class T>
-void upload(DBuf<T> &buf, const T *src, size_t n, cudaStream_t s) {
-    buf.ensure(n ? n : 1);
-    if (n) CK(cudaMemcpyAsync(buf.p, src, sizeof(T) * n, cudaMemcpyHostToDevice, s));
-}
 
 void reset_warmstart(ovl_ctx *c) {
     c->ws_pstart.ensure((size_t)c->n_parts + 1);
@@ -753,10 +639,6 @@ std::vector<uint64_t> download_masks(ovl_ctx *c) {
     return m;
 }
 
-template <class T>
-void download(T *dst, const T *src, size_t n, cudaStream_t s) {
-    if (n) CK(cudaMemcpyAsync(dst, src, sizeof(T) * n, cudaMemcpyDeviceToHost, s));
-}
 
 }  // namespace
 
@@ -766,6 +648,7 @@ ovl_status ovl_destroy(ovl_ctx *c) {
     if (!c) return OVL_ERR_ARG;
     if (c->stream) cudaStreamSynchronize(c->stream);
     release_all(c);
+    release_mlp(c);
     c->h_i32.release(); c->h_ab.release(); c->h_rp.release(); c->h_col.release(); c->h_mask.release();
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -1098,7 +981,7 @@ ovl_status ovl_read_stats(ovl_ctx *c, ovl_stats *out) {
         }
         out->residual_rms = c->npairs > 0 ? std::sqrt(sq / (3.0 * c->npairs)) : 0.0;
         out->device_status = dstat;
-        for (int i = 0; i < 10; ++i) out->phase_ms[i] = c->phase_ms[i];
+        for (int i = 0; i < 11; ++i) out->phase_ms[i] = c->phase_ms[i];
         out->n_launches = c->last_launches;
         out->solve_cluster = c->last_cluster;
         out->solve_threads = c->last_threads;

@@ -1,0 +1,165 @@
+// ctx.cuh -- the library context (ovl_ctx) and the host helpers the
+// translation units of the C ABI share.
+#pragma once
+
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace ovl;
+
+struct ovl_ctx {
+    ovl_params P{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int smem_optin = 0;
+    int num_sms = 0;
+    int smem_per_sm = 0;
+    int nb_max = 0;          // most bodies in one worker (last membership phase)
+    int last_cluster = 1, last_threads = 512, last_unroll = 1;
+    struct TuneCfg { int cluster, threads, unroll; float ms; };
+    std::map<std::string, TuneCfg> tuned;   // autotuner results by problem-size bucket
+    std::string err;
+
+    // scene (host copies)
+    bool has_scene = false;
+    HostScene hs;
+    int n = 0, np = 0, nj = 0, ns = 0, n_parts = 0, beta_max = 0;
+    std::vector<float> h_radius, h_im;
+    std::vector<int> h_body_base, h_plane_ptr, h_part_scene;
+    float cs = 1.f;
+    uint32_t tsize = 0;
+    long long vb_bits = 0;
+
+    // scene (device)
+    DBuf<float4> st, st_alt;
+    DBuf<float> radius, im, scene_mu, scene_dt;
+    DBuf<int> sob, scene_flags, n_sets, part_base, body_base, scene_beta, joint_scene, part_scene;
+    DBuf<float4> planes;
+    DBuf<int> plane_ptr, plane_list;
+    DBuf<int2> jab;
+    DBuf<float4> janc;
+    DBuf<long long> vb_base;
+    DBuf<uint64_t> mask;
+
+    // step buffers
+    DBuf<int> status;
+    DBuf<int4> cell;
+    DBuf<int> bucket_count, bucket_start, cursor, items, nb_list, nb_count, ccount, cstart;
+    DBuf<int2> c_ab;
+    DBuf<float4> c_n, c_t1;
+    DBuf<int> deg, tptr, cursor2, tcol, ucount, row_ptr, col;
+    DBuf<int> entry_count, entry_ptr, entry_body, entry_part, entry_slot, part_list, part_count,
+        part_bstart;
+    DBuf<uint32_t> sk, sv, sk2, sv2;
+    DBuf<int> cons_count, cons_start, pair_cons, pair_part, ps_cons, ps_part, part_pcount,
+        part_pstart, p_colour, part_ncol, part_rounds, col_off, pair_of_row;
+    DBuf<uint64_t> p_key;
+    DBuf<int2> p_slot;
+    DBuf<float4> p_lam0;
+    DBuf<unsigned long long> colour_scratch;
+    DBuf<int4> worklist, worklist2;
+    DBuf<unsigned long long> wprio, wprio2;
+    DBuf<float4> r0, r1, r2, r3, rlam, lam_out;
+    DBuf<int> rpair;
+    DBuf<int> ws_pstart;
+    DBuf<uint64_t> ws_key;
+    DBuf<float4> ws_lam;
+    int64_t ws_n = 0;
+    DBuf<float4> copies, solve_scratch;
+    DBuf<int> part_iters;
+    DBuf<double> part_res_sq;
+    DBuf<uint32_t> visited, queue;
+    DBuf<int> qctl;
+    DBuf<uint8_t> D;
+    DBuf<float> weight;
+    DBuf<float> stage13;   // staging for host <-> device state transfers
+    DBuf<int> scan_tmp, sort_hist, sort_tmp;
+    HBuf<int> h_i32;
+    HBuf<int2> h_ab;
+    HBuf<int> h_rp, h_col;
+    HBuf<uint64_t> h_mask;
+    DBuf<int> lb_flag, lb_pos;
+    DBuf<int2> lb_pairs;
+    std::vector<int> lb_a, lb_b;
+    std::vector<uint64_t> lb_mask;
+
+    // last step
+    int64_t step_index = 0;
+    int nc = 0, nadj = 0, ne = 0, npairs = 0;
+    bool have_step = false;
+    cudaEvent_t ev[16] = {};
+    float phase_ms[12] = {};
+    long long last_launches = 0;
+    long long lb_candidates = 0;
+    double lb_host_ms = 0.0;
+
+    // learned warm start
+    int ws_mode = OVL_WS_PREVIOUS;
+    bool feat_valid = false;          // the last step computed features
+    DBuf<float4> feat;                // [np][4]
+    DBuf<int> is_contact, contact_pos;
+    DBuf<uint8_t> depth;
+    bool mlp_ready = false;           // parameters were set
+    DBuf<float> mlp_theta, mlp_m, mlp_v, mlp_grad, mlp_loss;
+    DBuf<uint32_t> mlp_packed;
+    long long adam_t = 0;
+    DBuf<float> log_feat, log_targ;
+    long long log_cap = 0, log_n = 0;
+    bool log_on = false;
+    DBuf<float> train_act, train_sample_loss, train_partials, train_loss_hist, infer_y;
+    DBuf<float4> infer_feat;
+    DBuf<double> loss_acc;
+};
+
+namespace ovl {
+
+inline ovl_status fail(ovl_ctx *c, ovl_status code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+template <class F>
+ovl_status guarded(ovl_ctx *c, F &&f) {
+    if (!c) return OVL_ERR_ARG;
+    try {
+        return f();
+    } catch (const CudaError &e) {
+        return fail(c, OVL_ERR_CUDA, std::string(e.what) + ": " + cudaGetErrorString(e.err));
+    } catch (const std::bad_alloc &) {
+        return fail(c, OVL_ERR_CUDA, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(c, OVL_ERR_ARG, e.what());
+    }
+}
+
+inline int read_i32(ovl_ctx *c, const int *dptr) {
+    c->h_i32.ensure(1);
+    CK(cudaMemcpyAsync(c->h_i32.p, dptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return c->h_i32.p[0];
+}
+
+template <class T>
+void upload(DBuf<T> &buf, const T *src, size_t n, cudaStream_t s) {
+    buf.ensure(n ? n : 1);
+    if (n) CK(cudaMemcpyAsync(buf.p, src, sizeof(T) * n, cudaMemcpyHostToDevice, s));
+}
+
+template <class T>
+void download(T *dst, const T *src, size_t n, cudaStream_t s) {
+    if (n) CK(cudaMemcpyAsync(dst, src, sizeof(T) * n, cudaMemcpyDeviceToHost, s));
+}
+
+// learned warm start (mlp.cu): features and the network's proposal before
+// the rows are built; the log after the solve; buffers freed with the context
+void phase_warmstart(ovl_ctx *c, float dt_override);
+void phase_log(ovl_ctx *c);
+void release_mlp(ovl_ctx *c);
+
+}  // namespace ovl

@@ -1,0 +1,585 @@
+// k_mlp.cu -- the learned warm start (not part of the paper's method): per
+// contact features, a 12-64-64-3 ReLU network that proposes the contact's
+// three impulses, the log of (features, converged impulses) the solver
+// produces, and the network's training.
+//
+// Features of a (worker, contact) pair, from the blended state at the start
+// of the step (before gravity), with g_ref = max(|g|, 1) and
+// s = g_ref h / (im_A + im_B) over the dynamic ends:
+//   0-2  J v along n, t1, t2 (static ends have v = 0) / (g_ref h)
+//   3    penetration max(-phi, 0) / (g_ref h^2)
+//   4-6  the previous-step impulses the plain warm start applies / s
+//   7-8  inverse masses of the two ends (0 when static or a plane)
+//   9-10 their degrees in G^t / 8
+//   11   min over the dynamic ends of the BFS distance to O (capped at 8) / 8
+// The network's outputs are impulses / s, y = x[4:7] + W3^T relu(W2^T
+// relu(W1^T x + b1) + b2) + b3: the layers correct the previous-step impulses
+// (features 4-6, added in FP32).  A warm start takes s y, keeps the normal
+// impulse non-negative and clamps each friction impulse to mu times it.
+//
+// Inference runs on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32
+// accumulators): a warp takes 16 pairs, and the accumulator fragments of one
+// layer become the operand fragments of the next without leaving registers.
+// Training uses the same arithmetic on CUDA cores (operands rounded to BF16,
+// products exact in FP32, FP32 sums): one thread per sample for the forward
+// and backward passes, block-partial weight gradients summed in block order
+// (deterministic), and Adam on FP32 master parameters.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ovl {
+
+namespace {
+
+// parameter vector (C ABI layout)
+constexpr int OFF_W1 = 0, OFF_B1 = 768, OFF_W2 = 832, OFF_B2 = 4928, OFF_W3 = 4992, OFF_B3 = 5184;
+static_assert(OFF_B3 + 3 == MLP_N_PARAMS, "parameter layout");
+// packed inference weights (32-bit words): B fragments of W1 [8 n-tiles][32
+// lanes][2], W2 [4 k-tiles][8 n-tiles][32][2], W3 [4 k-tiles][32][2], then
+// FP32 biases b1 [64], b2 [64], b3 [8] (zero-padded)
+constexpr int PK_W1 = 0, PK_W2 = 512, PK_W3 = 2560, PK_B1 = 2816, PK_B2 = 2880, PK_B3 = 2944;
+static_assert(PK_B3 + 8 == MLP_PK_WORDS, "packed layout");
+// activation rows of the training pass
+constexpr int A_X = 0, A_H1 = 16, A_H2 = 80, A_DZ1 = 144, A_DZ2 = 208, A_DY = 272;
+static_assert(A_DY + 4 == MLP_ACT_STRIDE, "activation layout");
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x (low half) = lo
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint2 b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {   // SplitMix64 finaliser
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ---- depth to O ------------------------------------------------------------
+
+__global__ void k_depth_init(const uint64_t *mask, int n, uint8_t *depth) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x)
+        depth[b] = __popcll(mask[b]) >= 2 ? 0 : MLP_DEPTH_CAP;
+}
+
+// Vertices at level L-1 mark their unreached neighbours with L.  Only the
+// value L is written during a level, so concurrent writes agree.
+__global__ void k_depth_level(const int *row_ptr, const int *col, int n, uint8_t *depth, int L) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        if (depth[u] != L - 1) continue;
+        for (int k = row_ptr[u]; k < row_ptr[u + 1]; ++k) {
+            const int v = col[k];
+            if (depth[v] == MLP_DEPTH_CAP) depth[v] = (uint8_t)L;
+        }
+    }
+}
+
+// ---- features ----------------------------------------------------------------
+
+__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__global__ void k_features(FeatArgs a) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.np; k += gridDim.x * blockDim.x) {
+        const int i = a.ps_cons[k], p = a.ps_part[k];
+        const uint64_t key = a.p_key[k];
+        int lo = a.ws.ws_pstart[p], hi = a.ws.ws_pstart[p + 1];
+        const int end = hi;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (a.ws.ws_key[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        const bool found = lo < end && a.ws.ws_key[lo] == key;
+        float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0;
+        float4 meta = make_float4(found ? 1.f : 0.f, 0.f, 0.f, 0.f);
+        const bool contact = i < a.nc;
+        if (contact) {
+            const int2 ab = a.c_ab[i];
+            const float4 nphi = a.c_n[i];
+            const float3 n = f3(nphi), t1 = f3(a.c_t1[i]), t2 = cross(n, t1);
+            float3 pa = make_float3(0.f, 0.f, 0.f), pb = pa;
+            const float4 va = a.st[4 * ab.x + 2];
+            const float ima = va.w;   // 0 for a static body
+            if (ima > 0.f) {
+                const float ra = a.st[4 * ab.x].w;
+                const float3 w = f3(a.st[4 * ab.x + 3]);
+                const float3 wr = cross(w, make_float3(ra * n.x, ra * n.y, ra * n.z));
+                pa = make_float3(va.x + wr.x, va.y + wr.y, va.z + wr.z);
+            }
+            float imb = 0.f;
+            if (ab.y < a.n) {
+                const float4 vb = a.st[4 * ab.y + 2];
+                if (vb.w > 0.f) {
+                    imb = vb.w;
+                    const float rb = a.st[4 * ab.y].w;
+                    const float3 w = f3(a.st[4 * ab.y + 3]);
+                    const float3 wr = cross(w, make_float3(-rb * n.x, -rb * n.y, -rb * n.z));
+                    pb = make_float3(vb.x + wr.x, vb.y + wr.y, vb.z + wr.z);
+                }
+            }
+            const float3 rel = make_float3(pb.x - pa.x, pb.y - pa.y, pb.z - pa.z);
+            const int scene = a.part_scene[p];
+            const float h = a.dt_override > 0.f ? a.dt_override : a.scene_dt[scene];
+            const float gh = a.g_ref * h;
+            const float scale = gh / (ima + imb);
+            float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (found) {
+                const float4 v = a.ws.ws_lam[lo];
+                l = make_float4(v.x * a.ws.factor, v.y * a.ws.factor, v.z * a.ws.factor, 0.f);
+            }
+            const bool dyn_b = imb > 0.f;
+            int d = MLP_DEPTH_CAP;
+            if (ima > 0.f) d = min(d, (int)a.depth[ab.x]);
+            if (dyn_b) d = min(d, (int)a.depth[ab.y]);
+            const float dga = ima > 0.f ? (float)(a.row_ptr[ab.x + 1] - a.row_ptr[ab.x]) * 0.125f : 0.f;
+            const float dgb = dyn_b ? (float)(a.row_ptr[ab.y + 1] - a.row_ptr[ab.y]) * 0.125f : 0.f;
+            o0 = make_float4(dot(n, rel) / gh, dot(t1, rel) / gh, dot(t2, rel) / gh,
+                             fmaxf(-nphi.w, 0.f) / (gh * h));
+            o1 = make_float4(l.x / scale, l.y / scale, l.z / scale, ima);
+            o2 = make_float4(imb, dga, dgb, (float)d / (float)MLP_DEPTH_CAP);
+            meta = make_float4(found ? 1.f : 0.f, scale, a.scene_mu[scene], 1.f);
+        }
+        a.feat[4 * (size_t)k] = o0;
+        a.feat[4 * (size_t)k + 1] = o1;
+        a.feat[4 * (size_t)k + 2] = o2;
+        a.feat[4 * (size_t)k + 3] = meta;
+        a.is_contact[k] = contact ? 1 : 0;
+    }
+}
+
+// ---- inference ---------------------------------------------------------------
+
+__global__ void k_mlp_pack(const float *th, uint32_t *pk) {
+    for (int e = threadIdx.x; e < 8 * 32; e += blockDim.x) {
+        const int j = e >> 5, lane = e & 31, g = lane >> 2, t = lane & 3, col = 8 * j + g;
+        auto w = [&](int k) { return k < 12 ? th[OFF_W1 + k * 64 + col] : 0.f; };
+        pk[PK_W1 + 2 * e] = pack_bf16(w(2 * t), w(2 * t + 1));
+        pk[PK_W1 + 2 * e + 1] = pack_bf16(w(2 * t + 8), w(2 * t + 9));
+    }
+    for (int e = threadIdx.x; e < 4 * 8 * 32; e += blockDim.x) {
+        const int kk = e >> 8, j = (e >> 5) & 7, lane = e & 31, g = lane >> 2, t = lane & 3;
+        const int col = 8 * j + g, k0 = 16 * kk + 2 * t;
+        auto w = [&](int k) { return th[OFF_W2 + k * 64 + col]; };
+        pk[PK_W2 + 2 * e] = pack_bf16(w(k0), w(k0 + 1));
+        pk[PK_W2 + 2 * e + 1] = pack_bf16(w(k0 + 8), w(k0 + 9));
+    }
+    for (int e = threadIdx.x; e < 4 * 32; e += blockDim.x) {
+        const int kk = e >> 5, lane = e & 31, g = lane >> 2, t = lane & 3, k0 = 16 * kk + 2 * t;
+        auto w = [&](int k) { return g < 3 ? th[OFF_W3 + k * 3 + g] : 0.f; };
+        pk[PK_W3 + 2 * e] = pack_bf16(w(k0), w(k0 + 1));
+        pk[PK_W3 + 2 * e + 1] = pack_bf16(w(k0 + 8), w(k0 + 9));
+    }
+    float *bias = reinterpret_cast<float *>(pk);
+    for (int e = threadIdx.x; e < 64; e += blockDim.x) {
+        bias[PK_B1 + e] = th[OFF_B1 + e];
+        bias[PK_B2 + e] = th[OFF_B2 + e];
+    }
+    for (int e = threadIdx.x; e < 8; e += blockDim.x) bias[PK_B3 + e] = e < 3 ? th[OFF_B3 + e] : 0.f;
+}
+
+template <int MODE>
+__device__ __forceinline__ void infer_store(int r, int n, float y0, float y1, float y2,
+                                            const float4 *feat, float4 *lam0, float *y3) {
+    if (r >= n) return;
+    // skip connection: features 4-6 (previous impulses / s), in FP32
+    const float4 f1 = feat[4 * (size_t)r + 1];
+    y0 += f1.x; y1 += f1.y; y2 += f1.z;
+    if (MODE == 0) {
+        y3[3 * (size_t)r] = y0; y3[3 * (size_t)r + 1] = y1; y3[3 * (size_t)r + 2] = y2;
+        return;
+    }
+    const float4 meta = feat[4 * (size_t)r + 3];   // found, scale, mu, contact
+    if (meta.w == 0.f) return;                    // joints keep the previous impulses
+    if (MODE == 2 && meta.x != 0.f) return;       // contacts seen last step keep them too
+    const float ln = fmaxf(meta.y * y0, 0.f), lim = meta.z * ln;
+    lam0[r] = make_float4(ln, fminf(fmaxf(meta.y * y1, -lim), lim),
+                          fminf(fmaxf(meta.y * y2, -lim), lim), 0.f);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_mlp_infer(const uint32_t *pk, const float4 *feat, int n,
+                                                   float4 *lam0, float *y3) {
+    __shared__ __align__(16) uint32_t sp[MLP_PK_WORDS];
+    for (int i = threadIdx.x; i < MLP_PK_WORDS; i += blockDim.x) sp[i] = pk[i];
+    __syncthreads();
+    const uint2 *w1 = reinterpret_cast<const uint2 *>(sp + PK_W1);
+    const uint2 *w2 = reinterpret_cast<const uint2 *>(sp + PK_W2);
+    const uint2 *w3 = reinterpret_cast<const uint2 *>(sp + PK_W3);
+    const float *b1 = reinterpret_cast<const float *>(sp + PK_B1);
+    const float *b2 = reinterpret_cast<const float *>(sp + PK_B2);
+    const float *b3 = reinterpret_cast<const float *>(sp + PK_B3);
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const float *F = reinterpret_cast<const float *>(feat);
+    const int tiles = (n + 15) >> 4;
+    for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < tiles; tile += warps) {
+        const int r0 = 16 * tile + g, r1 = r0 + 8;
+        // layer-1 operands: features 0..11 of rows r0 and r1, columns 12..15 zero
+        float2 x00 = make_float2(0.f, 0.f), x01 = x00, x10 = x00, x11 = x00;
+        if (r0 < n) {
+            x00 = *reinterpret_cast<const float2 *>(F + 16 * (size_t)r0 + 2 * t);
+            if (t < 2) x01 = *reinterpret_cast<const float2 *>(F + 16 * (size_t)r0 + 2 * t + 8);
+        }
+        if (r1 < n) {
+            x10 = *reinterpret_cast<const float2 *>(F + 16 * (size_t)r1 + 2 * t);
+            if (t < 2) x11 = *reinterpret_cast<const float2 *>(F + 16 * (size_t)r1 + 2 * t + 8);
+        }
+        uint32_t a[4] = {pack_bf16(x00.x, x00.y), pack_bf16(x10.x, x10.y), pack_bf16(x01.x, x01.y),
+                         pack_bf16(x11.x, x11.y)};
+        float acc[8][4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float c0 = b1[8 * j + 2 * t], c1 = b1[8 * j + 2 * t + 1];
+            acc[j][0] = c0; acc[j][1] = c1; acc[j][2] = c0; acc[j][3] = c1;
+            mma_bf16(acc[j], a, w1[j * 32 + lane]);
+        }
+        uint32_t hf[4][4];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            hf[kk][0] = pack_bf16(fmaxf(acc[2 * kk][0], 0.f), fmaxf(acc[2 * kk][1], 0.f));
+            hf[kk][1] = pack_bf16(fmaxf(acc[2 * kk][2], 0.f), fmaxf(acc[2 * kk][3], 0.f));
+            hf[kk][2] = pack_bf16(fmaxf(acc[2 * kk + 1][0], 0.f), fmaxf(acc[2 * kk + 1][1], 0.f));
+            hf[kk][3] = pack_bf16(fmaxf(acc[2 * kk + 1][2], 0.f), fmaxf(acc[2 * kk + 1][3], 0.f));
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float c0 = b2[8 * j + 2 * t], c1 = b2[8 * j + 2 * t + 1];
+            acc[j][0] = c0; acc[j][1] = c1; acc[j][2] = c0; acc[j][3] = c1;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) mma_bf16(acc[j], hf[kk], w2[(kk * 8 + j) * 32 + lane]);
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            hf[kk][0] = pack_bf16(fmaxf(acc[2 * kk][0], 0.f), fmaxf(acc[2 * kk][1], 0.f));
+            hf[kk][1] = pack_bf16(fmaxf(acc[2 * kk][2], 0.f), fmaxf(acc[2 * kk][3], 0.f));
+            hf[kk][2] = pack_bf16(fmaxf(acc[2 * kk + 1][0], 0.f), fmaxf(acc[2 * kk + 1][1], 0.f));
+            hf[kk][3] = pack_bf16(fmaxf(acc[2 * kk + 1][2], 0.f), fmaxf(acc[2 * kk + 1][3], 0.f));
+        }
+        float o[4] = {b3[2 * t], b3[2 * t + 1], b3[2 * t], b3[2 * t + 1]};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) mma_bf16(o, hf[kk], w3[kk * 32 + lane]);
+        // outputs 0, 1 sit in lane 4g (t = 0), output 2 in lane 4g + 1
+        const float y2a = __shfl_down_sync(0xffffffffu, o[0], 1);
+        const float y2b = __shfl_down_sync(0xffffffffu, o[2], 1);
+        if (t == 0) {
+            infer_store<MODE>(r0, n, o[0], o[1], y2a, feat, lam0, y3);
+            infer_store<MODE>(r1, n, o[2], o[3], y2b, feat, lam0, y3);
+        }
+    }
+}
+
+// ---- log -----------------------------------------------------------------------
+
+__global__ void k_log_append(const float4 *feat, const float4 *lam, const int *pos, int np,
+                             float *log_feat, float *log_targ, long long base, long long cap) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+        const float4 meta = feat[4 * (size_t)k + 3];
+        if (meta.w == 0.f) continue;
+        const long long row = base + pos[k];
+        if (row >= cap) continue;
+        const float4 f0 = feat[4 * (size_t)k], f1 = feat[4 * (size_t)k + 1], f2 = feat[4 * (size_t)k + 2];
+        float *o = log_feat + 12 * row;
+        o[0] = f0.x; o[1] = f0.y; o[2] = f0.z; o[3] = f0.w;
+        o[4] = f1.x; o[5] = f1.y; o[6] = f1.z; o[7] = f1.w;
+        o[8] = f2.x; o[9] = f2.y; o[10] = f2.z; o[11] = f2.w;
+        const float4 l = lam[k];
+        float *tg = log_targ + 3 * row;
+        tg[0] = l.x / meta.y; tg[1] = l.y / meta.y; tg[2] = l.z / meta.y;
+    }
+}
+
+// ---- training --------------------------------------------------------------------
+
+constexpr int TRAIN_THREADS = 256;
+constexpr int WGRAD_THREADS = 256, WGRAD_CHUNK = 128, WGRAD_TILE = 32;
+constexpr int WGRAD_PER_THREAD = (MLP_N_PARAMS + 1 + WGRAD_THREADS - 1) / WGRAD_THREADS;
+
+__device__ __forceinline__ long long sample_row(const TrainArgs &a, int j) {
+    if (a.sampling == 0) return a.first + (long long)(((unsigned long long)a.step * a.batch + j) % (unsigned long long)a.count);
+    const uint64_t z = mix64(a.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(a.step * (long long)a.batch + j + 1));
+    return a.first + (long long)(z % (uint64_t)a.count);
+}
+
+// Forward, loss and the backward pass down to the pre-activation gradients,
+// one warp per sample at a time: lane l owns hidden units l and l + 32, and
+// the activations of the layer below are broadcast by shuffles.  The
+// operands every product uses (x, h1, h2, dy, dz2 and the weights) are
+// rounded to BF16; sums are FP32 in a fixed order.
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(TRAIN_THREADS) k_train_fwd(TrainArgs a) {
+    __shared__ float W[MLP_N_PARAMS];
+    __shared__ float W2T[64 * 64];   // W2 transposed: [out][in]
+    for (int i = threadIdx.x; i < MLP_N_PARAMS; i += blockDim.x) {
+        const bool bias = (i >= OFF_B1 && i < OFF_W2) || (i >= OFF_B2 && i < OFF_W3) || i >= OFF_B3;
+        W[i] = bias ? a.theta[i] : bf16r(a.theta[i]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) W2T[(i % 64) * 64 + i / 64] = W[OFF_W2 + i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned full = 0xffffffffu;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < a.batch; j += warps) {
+        const long long r = sample_row(a, j);
+        const float xraw = lane < 12 ? a.log_feat[12 * r + lane] : 0.f;
+        const float xv = bf16r(xraw);
+        float z1a = W[OFF_B1 + lane], z1b = W[OFF_B1 + lane + 32];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            const float x = __shfl_sync(full, xv, i);
+            z1a += x * W[OFF_W1 + i * 64 + lane];
+            z1b += x * W[OFF_W1 + i * 64 + lane + 32];
+        }
+        const float h1a = bf16r(fmaxf(z1a, 0.f)), h1b = bf16r(fmaxf(z1b, 0.f));
+        float z2a = W[OFF_B2 + lane], z2b = W[OFF_B2 + lane + 32];
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const float h = __shfl_sync(full, h1a, k);
+            z2a += h * W[OFF_W2 + k * 64 + lane];
+            z2b += h * W[OFF_W2 + k * 64 + lane + 32];
+        }
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const float h = __shfl_sync(full, h1b, k);
+            z2a += h * W[OFF_W2 + (k + 32) * 64 + lane];
+            z2b += h * W[OFF_W2 + (k + 32) * 64 + lane + 32];
+        }
+        const float h2a = bf16r(fmaxf(z2a, 0.f)), h2b = bf16r(fmaxf(z2b, 0.f));
+        float y[3], dy[3], loss = 0.f;
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+            y[o] = W[OFF_B3 + o] + warp_sum(h2a * W[OFF_W3 + lane * 3 + o] + h2b * W[OFF_W3 + (lane + 32) * 3 + o]) +
+                   __shfl_sync(full, xraw, 4 + o);   // skip connection, FP32
+            const float d = y[o] - a.log_targ[3 * r + o];
+            loss += d * d;
+            dy[o] = bf16r(2.f * d / (3.f * (float)a.batch));
+        }
+        if (lane == 0) a.sample_loss[j] = loss;
+        if (!a.backward) continue;
+        float *act = a.act + (size_t)j * MLP_ACT_STRIDE;
+        if (lane < 16) act[A_X + lane] = xv;
+        act[A_H1 + lane] = h1a; act[A_H1 + lane + 32] = h1b;
+        act[A_H2 + lane] = h2a; act[A_H2 + lane + 32] = h2b;
+        if (lane < 4) act[A_DY + lane] = lane == 0 ? dy[0] : (lane == 1 ? dy[1] : (lane == 2 ? dy[2] : 0.f));
+        // dz2 = (W3 dy) where h2 > 0
+        const float sa = W[OFF_W3 + lane * 3] * dy[0] + W[OFF_W3 + lane * 3 + 1] * dy[1] + W[OFF_W3 + lane * 3 + 2] * dy[2];
+        const float sb = W[OFF_W3 + (lane + 32) * 3] * dy[0] + W[OFF_W3 + (lane + 32) * 3 + 1] * dy[1] +
+                         W[OFF_W3 + (lane + 32) * 3 + 2] * dy[2];
+        const float dz2a = h2a > 0.f ? bf16r(sa) : 0.f, dz2b = h2b > 0.f ? bf16r(sb) : 0.f;
+        act[A_DZ2 + lane] = dz2a; act[A_DZ2 + lane + 32] = dz2b;
+        // dz1 = (W2 dz2) where h1 > 0
+        float ta = 0.f, tb = 0.f;
+#pragma unroll 8
+        for (int u = 0; u < 32; ++u) {
+            const float d = __shfl_sync(full, dz2a, u);
+            ta += W2T[u * 64 + lane] * d;
+            tb += W2T[u * 64 + lane + 32] * d;
+        }
+#pragma unroll 8
+        for (int u = 0; u < 32; ++u) {
+            const float d = __shfl_sync(full, dz2b, u);
+            ta += W2T[(u + 32) * 64 + lane] * d;
+            tb += W2T[(u + 32) * 64 + lane + 32] * d;
+        }
+        act[A_DZ1 + lane] = h1a > 0.f ? bf16r(ta) : 0.f;
+        act[A_DZ1 + lane + 32] = h1b > 0.f ? bf16r(tb) : 0.f;
+    }
+}
+
+// Block-partial gradients over WGRAD_CHUNK samples: every parameter is a sum
+// over samples of (operand A) x (operand B) taken from the activation rows;
+// biases have A = 1.  Slot MLP_N_PARAMS holds the block's loss sum.
+__device__ __forceinline__ void param_operands(int p, int &oa, int &ob) {
+    if (p < OFF_B1) { oa = A_X + p / 64; ob = A_DZ1 + p % 64; }
+    else if (p < OFF_W2) { oa = -1; ob = A_DZ1 + (p - OFF_B1); }
+    else if (p < OFF_B2) { const int q = p - OFF_W2; oa = A_H1 + q / 64; ob = A_DZ2 + q % 64; }
+    else if (p < OFF_W3) { oa = -1; ob = A_DZ2 + (p - OFF_B2); }
+    else if (p < OFF_B3) { const int q = p - OFF_W3; oa = A_H2 + q / 3; ob = A_DY + q % 3; }
+    else { oa = -1; ob = A_DY + (p - OFF_B3); }
+}
+
+__global__ void __launch_bounds__(WGRAD_THREADS) k_train_wgrad(TrainArgs a) {
+    __shared__ float tile[WGRAD_TILE * MLP_ACT_STRIDE];
+    __shared__ float lsum[WGRAD_THREADS];
+    const int s0 = blockIdx.x * WGRAD_CHUNK, s1 = min(s0 + WGRAD_CHUNK, a.batch);
+    int oa[WGRAD_PER_THREAD], ob[WGRAD_PER_THREAD];
+    float acc[WGRAD_PER_THREAD];
+#pragma unroll
+    for (int m = 0; m < WGRAD_PER_THREAD; ++m) {
+        const int p = threadIdx.x + m * WGRAD_THREADS;
+        acc[m] = 0.f;
+        if (p < MLP_N_PARAMS) param_operands(p, oa[m], ob[m]);
+        else { oa[m] = -2; ob[m] = 0; }
+    }
+    for (int base = s0; base < s1; base += WGRAD_TILE) {
+        const int cnt = min(WGRAD_TILE, s1 - base);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt * MLP_ACT_STRIDE; i += blockDim.x)
+            tile[i] = a.act[(size_t)base * MLP_ACT_STRIDE + i];
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < WGRAD_PER_THREAD; ++m) {
+            if (oa[m] == -2) continue;
+            float s = acc[m];
+            if (oa[m] < 0) {
+                for (int q = 0; q < cnt; ++q) s += tile[q * MLP_ACT_STRIDE + ob[m]];
+            } else {
+                for (int q = 0; q < cnt; ++q) s += tile[q * MLP_ACT_STRIDE + oa[m]] * tile[q * MLP_ACT_STRIDE + ob[m]];
+            }
+            acc[m] = s;
+        }
+    }
+    float *out = a.partials + (size_t)blockIdx.x * (MLP_N_PARAMS + 1);
+#pragma unroll
+    for (int m = 0; m < WGRAD_PER_THREAD; ++m) {
+        const int p = threadIdx.x + m * WGRAD_THREADS;
+        if (p < MLP_N_PARAMS) out[p] = acc[m];
+    }
+    // loss of this block's samples, summed in a fixed tree order
+    float l = 0.f;
+    for (int q = s0 + threadIdx.x; q < s1; q += blockDim.x) l += a.sample_loss[q];
+    lsum[threadIdx.x] = l;
+    __syncthreads();
+    for (int w = WGRAD_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) lsum[threadIdx.x] += lsum[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[MLP_N_PARAMS] = lsum[0];
+}
+
+__global__ void k_train_reduce(const float *partials, int blocks, int batch, float *grad_out,
+                               float *loss_out, int adam, float *theta, float *m, float *v,
+                               float lr, float beta1, float beta2, float eps, float c1, float c2) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > MLP_N_PARAMS) return;
+    float g = 0.f;
+    for (int b = 0; b < blocks; ++b) g += partials[(size_t)b * (MLP_N_PARAMS + 1) + p];
+    if (p == MLP_N_PARAMS) {
+        if (loss_out) loss_out[0] = g / (3.f * (float)batch);
+        return;
+    }
+    if (grad_out) grad_out[p] = g;
+    if (!adam) return;
+    const float mm = beta1 * m[p] + (1.f - beta1) * g;
+    const float vv = beta2 * v[p] + (1.f - beta2) * g * g;
+    m[p] = mm;
+    v[p] = vv;
+    theta[p] -= lr * (mm * c1) / (sqrtf(vv * c2) + eps);
+}
+
+__global__ void k_loss_sum(const float *sample_loss, int n, double *acc) {
+    __shared__ double part[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += sample_loss[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) acc[0] += part[0];
+}
+
+}  // namespace
+
+void launch_depth(const uint64_t *mask, const int *row_ptr, const int *col, int n, uint8_t *depth,
+                  cudaStream_t s) {
+    if (n <= 0) return;
+    const int grid = std::min((n + 255) / 256, 152 * 8);
+    k_depth_init<<<grid, 256, 0, s>>>(mask, n, depth);
+    note_launch();
+    for (int L = 1; L < MLP_DEPTH_CAP; ++L) {
+        k_depth_level<<<grid, 256, 0, s>>>(row_ptr, col, n, depth, L);
+        note_launch();
+    }
+    CK(cudaGetLastError());
+}
+
+void launch_features(const FeatArgs &a, cudaStream_t s) {
+    if (a.np <= 0) return;
+    k_features<<<std::min((a.np + 255) / 256, 152 * 16), 256, 0, s>>>(a);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_mlp_pack(const float *theta, uint32_t *packed, cudaStream_t s) {
+    k_mlp_pack<<<1, 256, 0, s>>>(theta, packed);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_mlp_infer(const uint32_t *packed, const float4 *feat, int n, int mode, float4 *lam0,
+                      float *y3, int grid_limit, cudaStream_t s) {
+    if (n <= 0) return;
+    const int tiles = (n + 15) / 16;
+    int grid = std::min((tiles + 7) / 8, grid_limit > 0 ? grid_limit : 152 * 4);
+    if (mode == 0) k_mlp_infer<0><<<grid, 256, 0, s>>>(packed, feat, n, lam0, y3);
+    else if (mode == 1) k_mlp_infer<1><<<grid, 256, 0, s>>>(packed, feat, n, lam0, y3);
+    else k_mlp_infer<2><<<grid, 256, 0, s>>>(packed, feat, n, lam0, y3);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_log_append(const float4 *feat, const float4 *lam, const int *pos, int np,
+                       float *log_feat, float *log_targ, long long base, long long cap,
+                       cudaStream_t s) {
+    if (np <= 0) return;
+    k_log_append<<<std::min((np + 255) / 256, 152 * 16), 256, 0, s>>>(feat, lam, pos, np, log_feat,
+                                                                        log_targ, base, cap);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_train_fwd(const TrainArgs &a, cudaStream_t s) {
+    const int warps_per_block = TRAIN_THREADS / 32;
+    const int grid = std::min((a.batch + warps_per_block - 1) / warps_per_block, 152 * 2);
+    k_train_fwd<<<grid, TRAIN_THREADS, 0, s>>>(a);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+int train_wgrad_blocks(int batch) { return (batch + WGRAD_CHUNK - 1) / WGRAD_CHUNK; }
+
+void launch_train_wgrad(const TrainArgs &a, cudaStream_t s) {
+    k_train_wgrad<<<train_wgrad_blocks(a.batch), WGRAD_THREADS, 0, s>>>(a);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_train_reduce(const float *partials, int blocks, int batch, float *grad_out,
+                         float *loss_out, int adam, float *theta, float *m, float *v, float lr,
+                         float beta1, float beta2, float eps, float c1, float c2, cudaStream_t s) {
+    k_train_reduce<<<(MLP_N_PARAMS + 1 + 255) / 256, 256, 0, s>>>(
+        partials, blocks, batch, grad_out, loss_out, adam, theta, m, v, lr, beta1, beta2, eps, c1, c2);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_loss_sum(const float *sample_loss, int n, double *acc, cudaStream_t s) {
+    k_loss_sum<<<1, 256, 0, s>>>(sample_loss, n, acc);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+}  // namespace ovl

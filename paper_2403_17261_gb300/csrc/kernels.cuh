@@ -216,4 +216,62 @@ void launch_pack_state(const float *in13, const float *radius, const float *im, 
                        cudaStream_t s);
 void launch_unpack_state(const float4 *st, int n, float *out13, cudaStream_t s);
 
+// ---- learned warm start (k_mlp.cu) ------------------------------------------
+// Per pair, 16 floats: the 12 features, then previous-impulses flag, scale s,
+// friction coefficient, contact flag (1 for contacts, 0 for joints).
+#define MLP_DEPTH_CAP 8
+#define MLP_N_PARAMS 5187
+#define MLP_PK_WORDS 2952      // packed BF16 fragments + FP32 biases
+#define MLP_ACT_STRIDE 276     // x 16, h1 64, h2 64, dz1 64, dz2 64, dy 4
+struct FeatArgs {
+    int np, nc, n;
+    const int *ps_cons, *ps_part, *part_scene;
+    const int2 *c_ab;
+    const float4 *c_n, *c_t1;
+    const float4 *st;
+    const int *row_ptr;
+    const uint8_t *depth;
+    const float *scene_dt, *scene_mu;
+    float dt_override;
+    float g_ref;
+    const uint64_t *p_key;
+    WarmArgs ws;
+    float4 *feat;              // [np][4]
+    int *is_contact;           // [np]
+};
+void launch_depth(const uint64_t *mask, const int *row_ptr, const int *col, int n, uint8_t *depth,
+                  cudaStream_t s);
+void launch_features(const FeatArgs &a, cudaStream_t s);
+void launch_mlp_pack(const float *theta, uint32_t *packed, cudaStream_t s);
+// mode 0: raw outputs to y3 [n][3]; 1: warm start of every contact into lam0;
+// 2: warm start of the contacts without previous impulses into lam0
+void launch_mlp_infer(const uint32_t *packed, const float4 *feat, int n, int mode, float4 *lam0,
+                      float *y3, int grid_limit, cudaStream_t s);
+void launch_log_append(const float4 *feat, const float4 *lam, const int *pos, int np,
+                       float *log_feat, float *log_targ, long long base, long long cap,
+                       cudaStream_t s);
+
+struct TrainArgs {
+    const float *log_feat, *log_targ;   // [rows][12], [rows][3]
+    long long first, count;             // rows sampled from [first, first + count)
+    int batch;
+    int sampling;                       // 0 contiguous, 1 uniform with replacement
+    unsigned long long seed;
+    long long step;                     // Adam step within the call (sampling)
+    int backward;                       // 0: loss only
+    const float *theta;                 // FP32 master parameters
+    float *act;                         // [batch][MLP_ACT_STRIDE]
+    float *sample_loss;                 // [batch]
+    float *partials;                    // [blocks][MLP_N_PARAMS + 1]
+};
+void launch_train_fwd(const TrainArgs &a, cudaStream_t s);
+int train_wgrad_blocks(int batch);
+void launch_train_wgrad(const TrainArgs &a, cudaStream_t s);
+// sums the partials in block order; grad_out (optional) gets the gradient and
+// loss_out[0] the mean loss; with adam != 0 also updates theta, m, v
+void launch_train_reduce(const float *partials, int blocks, int batch, float *grad_out,
+                         float *loss_out, int adam, float *theta, float *m, float *v, float lr,
+                         float beta1, float beta2, float eps, float c1, float c2, cudaStream_t s);
+void launch_loss_sum(const float *sample_loss, int n, double *acc, cudaStream_t s);
+
 }  // namespace ovl

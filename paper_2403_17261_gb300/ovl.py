@@ -28,6 +28,10 @@ OVL_ERR_MEMBERSHIP = -6
 OVL_FLAG_RESIDUAL = 1
 OVL_FLAG_TIMING = 2
 OVL_FLAG_AUTOTUNE = 4
+OVL_FLAG_FEATURES = 8
+OVL_WS_PREVIOUS, OVL_WS_MLP, OVL_WS_MLP_NEW = 0, 1, 2
+OVL_MLP_N_PARAMS = 5187
+OVL_N_FEATURES = 12
 
 EXPORTED = [
     "ovl_default_params", "ovl_create", "ovl_destroy", "ovl_last_error", "ovl_phase_name",
@@ -36,7 +40,9 @@ EXPORTED = [
     "ovl_set_warmstart", "ovl_read_warmstart", "ovl_step", "ovl_load_balance", "ovl_sync",
     "ovl_read_stats", "ovl_read_contacts", "ovl_read_graph", "ovl_read_entries", "ovl_read_pairs",
     "ovl_read_worker_stats", "ovl_autotune_export", "ovl_autotune_import",
-    "ovl_geodesics_static",
+    "ovl_geodesics_static", "ovl_set_warmstart_mode", "ovl_read_features", "ovl_mlp_set_params",
+    "ovl_mlp_get_params", "ovl_mlp_forward", "ovl_log_reserve", "ovl_log_enable", "ovl_log_size",
+    "ovl_log_append", "ovl_log_read", "ovl_mlp_train", "ovl_mlp_grad", "ovl_mlp_loss",
 ]
 
 
@@ -55,6 +61,13 @@ class ovl_params(C.Structure):
 
 
 _fp, _ip, _u64p, _u8p = C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint8)
+
+
+class ovl_train_desc(C.Structure):
+    _fields_ = [("first", C.c_int64), ("count", C.c_int64), ("batch", C.c_int32),
+                ("steps", C.c_int32), ("sampling", C.c_int32), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("seed", C.c_uint64)]
 
 
 class ovl_scene_desc(C.Structure):
@@ -115,6 +128,19 @@ def load_library(path: str | None = None):
         "ovl_read_worker_stats": [vp, _ip, C.POINTER(C.c_double), C.POINTER(C.c_int64), _ip],
         "ovl_autotune_export": [vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
         "ovl_autotune_import": [vp, C.c_char_p],
+        "ovl_set_warmstart_mode": [vp, C.c_int32],
+        "ovl_read_features": [vp, _fp, _fp, _ip, _fp],
+        "ovl_mlp_set_params": [vp, _fp, C.c_int32],
+        "ovl_mlp_get_params": [vp, _fp, C.c_int32],
+        "ovl_mlp_forward": [vp, C.c_int64, _fp, _fp],
+        "ovl_log_reserve": [vp, C.c_int64],
+        "ovl_log_enable": [vp, C.c_int32],
+        "ovl_log_size": [vp, C.POINTER(C.c_int64)],
+        "ovl_log_append": [vp, C.c_int64, _fp, _fp],
+        "ovl_log_read": [vp, C.c_int64, C.c_int64, _fp, _fp],
+        "ovl_mlp_train": [vp, C.POINTER(ovl_train_desc), _fp],
+        "ovl_mlp_grad": [vp, C.c_int64, C.c_int64, _fp, C.POINTER(C.c_double)],
+        "ovl_mlp_loss": [vp, C.c_int64, C.c_int64, C.POINTER(C.c_double)],
         "ovl_geodesics_static": [C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_int32, vp, vp,
                                  C.c_int32, vp, vp, C.c_char_p, C.c_int32],
     }
@@ -316,7 +342,7 @@ def ovl_read_stats(ctx) -> dict:
     _check(ctx, load_library().ovl_read_stats(ctx, C.byref(s)))
     out = {k: getattr(s, k) for k, _ in ovl_stats._fields_ if k != "phase_ms"}
     L = load_library()
-    out["phase_ms"] = {L.ovl_phase_name(i).decode(): s.phase_ms[i] for i in range(10)}
+    out["phase_ms"] = {L.ovl_phase_name(i).decode(): s.phase_ms[i] for i in range(11)}
     return out
 
 
@@ -451,3 +477,77 @@ class Simulation:
             self.ctx, _ptr(it, _ip), rs.ctypes.data_as(C.POINTER(C.c_double)),
             rows.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(cols, _ip)))
         return dict(iters=it, res_sq=rs, rows=rows, colours=cols)
+
+    # learned warm start ----------------------------------------------------------
+
+    def set_warmstart_mode(self, mode: int):
+        _check(self.ctx, load_library().ovl_set_warmstart_mode(self.ctx, int(mode)))
+
+    def features(self):
+        """Per pair of the last step: features [12], scale, previous-impulse
+        flag and the warm-start impulses the solve started from."""
+        npr = self.stats()["n_pairs"]
+        m = max(npr, 1)
+        f, sc = np.zeros((m, 12), np.float32), np.zeros(m, np.float32)
+        found, lam0 = np.zeros(m, np.int32), np.zeros((m, 3), np.float32)
+        _check(self.ctx, load_library().ovl_read_features(self.ctx, _ptr(f, _fp), _ptr(sc, _fp),
+                                                          _ptr(found, _ip), _ptr(lam0, _fp)))
+        return dict(feat=f[:npr], scale=sc[:npr], found=found[:npr].astype(bool), lam0=lam0[:npr])
+
+    def mlp_set_params(self, theta):
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+        _check(self.ctx, load_library().ovl_mlp_set_params(self.ctx, _ptr(th, _fp), th.size))
+
+    def mlp_params(self):
+        th = np.zeros(OVL_MLP_N_PARAMS, np.float32)
+        _check(self.ctx, load_library().ovl_mlp_get_params(self.ctx, _ptr(th, _fp), th.size))
+        return th
+
+    def mlp_forward(self, feat):
+        f = np.ascontiguousarray(np.asarray(feat, dtype=np.float32)).reshape(-1, 12)
+        y = np.zeros((max(len(f), 1), 3), np.float32)
+        _check(self.ctx, load_library().ovl_mlp_forward(self.ctx, len(f), _ptr(f, _fp), _ptr(y, _fp)))
+        return y[:len(f)]
+
+    def log_reserve(self, capacity: int):
+        _check(self.ctx, load_library().ovl_log_reserve(self.ctx, int(capacity)))
+
+    def log_enable(self, on: bool = True):
+        _check(self.ctx, load_library().ovl_log_enable(self.ctx, int(bool(on))))
+
+    def log_size(self) -> int:
+        n = C.c_int64()
+        _check(self.ctx, load_library().ovl_log_size(self.ctx, C.byref(n)))
+        return n.value
+
+    def log_append(self, feat, target):
+        f = np.ascontiguousarray(np.asarray(feat, dtype=np.float32)).reshape(-1, 12)
+        t = np.ascontiguousarray(np.asarray(target, dtype=np.float32)).reshape(-1, 3)
+        assert len(f) == len(t)
+        _check(self.ctx, load_library().ovl_log_append(self.ctx, len(f), _ptr(f, _fp), _ptr(t, _fp)))
+
+    def log_read(self, first: int = 0, n: int | None = None):
+        n = self.log_size() - first if n is None else n
+        f, t = np.zeros((max(n, 1), 12), np.float32), np.zeros((max(n, 1), 3), np.float32)
+        _check(self.ctx, load_library().ovl_log_read(self.ctx, first, n, _ptr(f, _fp), _ptr(t, _fp)))
+        return f[:n], t[:n]
+
+    def mlp_train(self, first: int, count: int, batch: int, steps: int, sampling: int = 1,
+                  lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                  seed: int = 0):
+        d = ovl_train_desc(first=first, count=count, batch=batch, steps=steps, sampling=sampling,
+                           lr=lr, beta1=beta1, beta2=beta2, eps=eps, seed=seed)
+        loss = np.zeros(max(steps, 1), np.float32)
+        _check(self.ctx, load_library().ovl_mlp_train(self.ctx, C.byref(d), _ptr(loss, _fp)))
+        return loss[:steps]
+
+    def mlp_grad(self, first: int, count: int):
+        g = np.zeros(OVL_MLP_N_PARAMS, np.float32)
+        loss = C.c_double()
+        _check(self.ctx, load_library().ovl_mlp_grad(self.ctx, first, count, _ptr(g, _fp), C.byref(loss)))
+        return loss.value, g
+
+    def mlp_loss(self, first: int, count: int) -> float:
+        loss = C.c_double()
+        _check(self.ctx, load_library().ovl_mlp_loss(self.ctx, first, count, C.byref(loss)))
+        return loss.value

@@ -258,14 +258,14 @@ def bowl_planes(angle_deg: float = 30.0) -> np.ndarray:
     return np.array([[s, 0, c, 0], [-s, 0, c, 0], [0, s, c, 0], [0, -s, c, 0]], dtype=np.float64)
 
 
-def pile_large(seed: int = 2, side: int = 64, n_sets: int = 64) -> Scene:
+def pile_large(seed: int = 2, side: int = 64, n_sets: int = 64, z0: float = 24.0) -> Scene:
     """side^3 spheres (default 262,144), spacing 1.25, x/y centred, bottom layer
-    at z=24, r~U(0.4,0.6), density 1; bowl of 4 planes at 30 degrees; mu=0.6,
+    at z=z0 (24), r~U(0.4,0.6), density 1; bowl of 4 planes at 30 degrees; mu=0.6,
     dt=1/60, 30 iterations, 300 steps; sets from k-means on the initial
     positions; growth depth 2, weight search depth 6; load-balance removals
     every 10 steps."""
     rng = SplitMix64(seed)
-    pos = _lattice_pile(side, side, side, 1.25, 24.0, 0.0, rng)
+    pos = _lattice_pile(side, side, side, 1.25, z0, 0.0, rng)
     n = pos.shape[0]
     r = rng.uniform(n, 0.4, 0.6).astype(np.float32).astype(np.float64)
     mass = (4.0 / 3.0) * math.pi * r ** 3
@@ -478,17 +478,31 @@ MLP_LAYERS = (12, 64, 64, 3)
 MLP_N_PARAMS = 12 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
 
 
-def mlp_init_params(seed: int = 5) -> np.ndarray:
+def bf16_grid(x) -> np.ndarray:
+    """FP32 values rounded to the nearest BF16 value (ties to even), still
+    stored as FP32: inputs that BF16 arithmetic represents exactly."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def mlp_init_params(seed: int = 5, bias_scale: float = 0.0, bf16_exact: bool = False,
+                    zero_output: bool = False) -> np.ndarray:
     """Initial parameters of the 12-64-64-3 network in the C ABI's layout
     (W1 [12][64], b1, W2 [64][64], b2, W3 [64][3], b3): weights uniform in
-    +-sqrt(6 / fan_in) (He et al. 2015, uniform form), biases zero; FP32."""
+    +-sqrt(6 / fan_in) (He et al. 2015, uniform form), biases uniform in
+    +-bias_scale (zero by default); FP32, optionally on the BF16 grid.
+    zero_output: W3 = 0 (the network then starts as the plain warm start)."""
     rng = SplitMix64(seed)
     parts = []
     for fan_in, fan_out in zip(MLP_LAYERS[:-1], MLP_LAYERS[1:]):
         lim = math.sqrt(6.0 / fan_in)
         parts.append(rng.uniform(fan_in * fan_out, -lim, lim))
-        parts.append(np.zeros(fan_out))
-    return np.concatenate(parts).astype(np.float32)
+        parts.append(rng.uniform(fan_out, -bias_scale, bias_scale) if bias_scale > 0 else np.zeros(fan_out))
+    if zero_output:
+        parts[-2] = np.zeros_like(parts[-2])
+    th = np.concatenate(parts).astype(np.float32)
+    return bf16_grid(th) if bf16_exact else th
 
 
 def synthetic_rows(n: int, seed: int = 6) -> tuple[np.ndarray, np.ndarray]:

@@ -25,7 +25,8 @@ def test_layout_matches_generator():
 
 def test_forward_hand_worked():
     # hidden units copy the inputs, output 0 sums their positive parts,
-    # output 1 is minus that sum, output 2 is its bias
+    # output 1 is minus that sum, output 2 is its bias; inputs 4-6 (the
+    # previous impulses) are added to the three outputs
     p = {k: np.zeros(s) for k, s in M.SHAPES}
     p["W1"][np.arange(12), np.arange(12)] = 1.0
     p["W2"][np.arange(12), np.arange(12)] = 1.0
@@ -34,7 +35,8 @@ def test_forward_hand_worked():
     p["b3"][:] = [0.5, 0.0, -2.0]
     x = np.array([[1.0, -2.0, 3.0, 0.0, 0.25, -0.5, 0.0, 0.0, 0.0, 0.0, 0.0, 0.5]])
     y, _ = M.forward(M.pack(p), x)
-    np.testing.assert_array_equal(y, [[5.25, -4.75, -2.0]])   # 1 + 3 + 0.25 + 0.5 (+0.5 bias)
+    # 1 + 3 + 0.25 + 0.5 (+0.5 bias) + 0.25; -4.75 - 0.5; -2 + 0
+    np.testing.assert_array_equal(y, [[5.5, -5.25, -2.0]])
 
 
 def test_gradient_matches_central_differences():
@@ -53,6 +55,13 @@ def test_gradient_matches_central_differences():
     # every parameter block is exercised
     for name, sl in zip(("W1", "W2", "W3"), (slice(0, 768), slice(832, 4928), slice(4992, 5184))):
         assert np.abs(g[sl]).max() > 0, name
+
+
+def test_zero_layers_give_the_previous_impulses():
+    th = np.zeros(M.N_PARAMS)
+    X, _ = S.synthetic_rows(50, seed=13)
+    y, _ = M.forward(th, X)
+    np.testing.assert_array_equal(y, X[:, 4:7].astype(np.float64))
 
 
 def test_zero_loss_at_exact_targets():
