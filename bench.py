@@ -52,7 +52,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ovl", choices=["ovl", "reference"])
-    ap.add_argument("--workload", default="pile_large", choices=["pile_large", "chain", "pile_small"])
+    ap.add_argument("--workload", default="pile_large",
+                    choices=["pile_large", "chain", "pile_small", "warmstart"],
+                    help="warmstart: the learned warm start on the large pile (log, train, "
+                         "sweeps to RMS residual 1e-4 against the previous-step warm start)")
+    ap.add_argument("--ws-log-steps", type=int, default=6)
+    ap.add_argument("--ws-eval-steps", type=int, default=50)
+    ap.add_argument("--ws-train-steps", type=int, default=20000)
     ap.add_argument("--settle", type=int, default=None, help="untimed steps before the warm-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -60,7 +66,7 @@ def parse():
 
 
 def default_settle(workload):
-    return {"pile_large": 150, "chain": 0, "pile_small": 0}[workload]
+    return {"pile_large": 150, "chain": 0, "pile_small": 0, "warmstart": 150}[workload]
 
 
 def make_scene(workload):
@@ -128,7 +134,7 @@ class ClockSampler:
 
 def oracle_sample_scene(workload):
     from paper_2403_17261_gb300 import scenes as S
-    if workload == "pile_large":
+    if workload in ("pile_large", "warmstart"):
         return S.pile_large(side=16, n_sets=16), 150, "pile_large generator at 16^3 = 4096 bodies, 16 k-means workers, settled 150 steps by the oracle itself (untimed)"
     if workload == "chain":
         return S.chain(), 0, "the full 4096-sphere chain"
@@ -298,6 +304,76 @@ def gpu_arm(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Learned warm start: sweeps and time to the residual tolerance
+# ---------------------------------------------------------------------------
+
+def warmstart_arm(args, rank, world, local_rank):
+    """Logs converged impulses (RMS 1e-5 or 1000 sweeps) from plain steps of
+    the large pile (seed 2) after it has settled into the bowl, trains the
+    network on the GPU, then on a fresh pile (seed 4) compares, step by step
+    from identical snapshots, the sweeps and device time the learned and the
+    previous-step warm starts need to bring every worker to RMS 1e-4."""
+    import torch
+    import __graft_entry__ as g
+    from paper_2403_17261_gb300 import learned, ovl
+    from paper_2403_17261_gb300 import scenes as S
+
+    torch.cuda.set_device(local_rank)
+    g.build()
+    settle = default_settle("warmstart") if args.settle is None else args.settle
+    t0 = time.time()
+    log_sim = ovl.Simulation(S.pile_large(seed=2), dict(res_tol=1e-5, res_check_every=5))
+    for _ in range(settle):
+        log_sim.step()
+    sizes = learned.collect(log_sim, steps=args.ws_log_steps, iters=1000, capacity=30_000_000)
+    t_log = time.time() - t0
+    split = sizes[-2]
+    t1 = time.time()
+    hist = learned.train(log_sim, split, steps=args.ws_train_steps)
+    t_train = time.time() - t1
+    held = learned.heldout(log_sim, split, sizes[-1] - split)
+    theta = log_sim.mlp_params()
+    log_sim.close()
+
+    ev = ovl.Simulation(S.pile_large(seed=4), dict(res_tol=1e-4, res_check_every=1,
+                                                   flags=ovl.OVL_FLAG_TIMING | ovl.OVL_FLAG_RESIDUAL))
+    ev.mlp_set_params(theta)
+    for _ in range(settle):
+        ev.step()
+    with ClockSampler(local_rank) as clk:
+        r = learned.compare(ev, steps=args.ws_eval_steps)
+    ev.close()
+    if rank != 0:
+        return
+    mlp, prev = r[ovl.OVL_WS_MLP], r[ovl.OVL_WS_PREVIOUS]
+
+    def summary(x):
+        return {"sweeps_sum_over_workers": float(x["sweeps"].mean()),
+                "sweeps_max_worker": float(x["max_sweeps"].mean()),
+                "solve_ms": float(x["solve_ms"].mean()), "warmstart_ms": float(x["warmstart_ms"].mean()),
+                "step_ms": float(x["step_ms"].mean()), "steps_all_workers_converged": int(x["converged"].sum()),
+                "residual_rms": float(x["residual_rms"].mean())}
+
+    line = {
+        "metric": "PGS sweeps to RMS residual <= 1e-4 (learned warm start)",
+        "value": float(mlp["sweeps"].mean()), "unit": "sweeps/step (sum over workers)",
+        "higher_is_better": False, "n_gpus": 1, "steps": args.ws_eval_steps, "warmup": settle,
+        "vs_baseline": None, "dtype": "f32 solve, bf16 network", "data": "synthetic",
+        "config": {"workload": "pile_large 262,144 spheres, 64 workers: logged on seed 2, evaluated on seed 4",
+                   "settle_steps": settle, "log_steps": args.ws_log_steps, "log_rows": sizes[-1],
+                   "train_rows": split, "train_steps": args.ws_train_steps, "batch": 4096, "lr": 1e-3,
+                   "eval_tolerance": 1e-4, "sweep_cap": 1000},
+        "learned": summary(mlp), "previous_step": summary(prev),
+        "sweeps_ratio_learned_over_previous": float(mlp["sweeps"].mean() / prev["sweeps"].mean()),
+        "solve_time_ratio_learned_over_previous": float((mlp["solve_ms"] + mlp["warmstart_ms"]).mean() / prev["solve_ms"].mean()),
+        "heldout_mse": held, "train_loss_last": float(np.mean(hist[-100:])),
+        "seconds": {"log": t_log, "train": t_train},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -305,6 +381,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.workload == "warmstart":
+        warmstart_arm(args, rank, world, local_rank)
         return
     if world > 1:
         import torch

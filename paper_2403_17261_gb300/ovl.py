@@ -361,6 +361,7 @@ class Simulation:
             params = ovl_default_params(**kw)
         self.params = params
         self.scene = scene
+        self._step_index = 0      # mirrors the context's step counter
         self.n = scene.n_bodies
         self.n_parts = int(np.sum(scene.n_sets))
         self.ctx = ovl_create(params, stream)
@@ -409,6 +410,11 @@ class Simulation:
 
     def set_step_index(self, k):
         ovl_set_step_index(self.ctx, k)
+        self._step_index = int(k)
+
+    def step_index_value(self) -> int:
+        """Index of the next step (load-balance cadence)."""
+        return self._step_index
 
     def set_warmstart(self, part, key, lam):
         ovl_set_warmstart(self.ctx, part, key, lam)
@@ -419,6 +425,7 @@ class Simulation:
     # stepping -----------------------------------------------------------------
     def step(self, dt: float = 0.0, iters: int | None = None):
         ovl_step(self.ctx, dt, self.scene.iters if iters is None else iters)
+        self._step_index += 1
 
     def autotune_export(self) -> str:
         return ovl_autotune_export(self.ctx)
