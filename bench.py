@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ovl", choices=["ovl", "reference"])
     ap.add_argument("--workload", default="pile_large",
-                    choices=["pile_large", "chain", "pile_small", "warmstart"],
+                    choices=["pile_large", "chain", "pile_small", "batched", "warmstart"],
                     help="warmstart: the learned warm start on the large pile (log, train, "
                          "sweeps to RMS residual 1e-4 against the previous-step warm start)")
     ap.add_argument("--ws-log-steps", type=int, default=6)
@@ -66,7 +66,7 @@ def parse():
 
 
 def default_settle(workload):
-    return {"pile_large": 150, "chain": 0, "pile_small": 0, "warmstart": 150}[workload]
+    return {"pile_large": 150, "chain": 0, "pile_small": 0, "batched": 0, "warmstart": 150}[workload]
 
 
 def make_scene(workload):
@@ -138,6 +138,8 @@ def oracle_sample_scene(workload):
         return S.pile_large(side=16, n_sets=16), 150, "pile_large generator at 16^3 = 4096 bodies, 16 k-means workers, settled 150 steps by the oracle itself (untimed)"
     if workload == "chain":
         return S.chain(), 0, "the full 4096-sphere chain"
+    if workload == "batched":
+        return S.batched(n_scenes=16), 0, "the first 16 of the 512 batched scenes (same generator and seed)"
     return S.pile_small(), 0, "the full 256-sphere pile"
 
 

@@ -108,13 +108,15 @@ struct HostScene {
     int n = 0, ns = 0, n_parts = 0;
     std::vector<float> inv_mass;
     std::vector<int> sob, part_base, scene_gamma, n_sets;
+    std::vector<int> body_base;  // [ns+1] first body of every scene
     std::vector<int> jab;  // 2 per joint
 };
 
 void host_assign_overlap(const HostScene &sc, std::vector<uint64_t> &mask);
-// contacts: pairs of dynamic bodies in canonical order; graph CSR of G^t
-void host_load_balance(const HostScene &sc, std::vector<uint64_t> &mask, int64_t nc, const int *ca,
-                       const int *cb, const int *row_ptr, const int *col, bool do_activate,
-                       bool do_deactivate);
+// contacts ab: pairs of dynamic bodies in canonical order; graph CSR of G^t;
+// mask [n] updated in place; scenes spread over up to `threads` threads
+void host_load_balance(const HostScene &sc, uint64_t *mask, int64_t nc, const int2 *ab,
+                       const int *row_ptr, const int *col, bool do_activate, bool do_deactivate,
+                       int threads);
 
 }  // namespace ovl

@@ -13,6 +13,7 @@
 #include <stdexcept>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ctx.cuh"
@@ -141,16 +142,8 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
     CK(cudaMemcpyAsync(c->h_col.p, c->col.p, sizeof(int) * c->nadj, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->h_mask.p, c->mask.p, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    c->lb_a.resize(m);
-    c->lb_b.resize(m);
-    for (int i = 0; i < m; ++i) {
-        c->lb_a[i] = c->h_ab.p[i].x;
-        c->lb_b[i] = c->h_ab.p[i].y;
-    }
-    c->lb_mask.assign(c->h_mask.p, c->h_mask.p + n);
-    host_load_balance(c->hs, c->lb_mask, m, c->lb_a.data(), c->lb_b.data(), c->h_rp.p, c->h_col.p,
-                      act, deact);
-    std::copy(c->lb_mask.begin(), c->lb_mask.end(), c->h_mask.p);
+    host_load_balance(c->hs, c->h_mask.p, m, c->h_ab.p, c->h_rp.p, c->h_col.p, act, deact,
+                      c->lb_threads);
     CK(cudaMemcpyAsync(c->mask.p, c->h_mask.p, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     c->lb_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -236,6 +229,14 @@ void phase_membership(ovl_ctx *c, float dt_override) {
     w.ws_pstart = c->ws_pstart.p; w.ws_key = c->ws_key.p; w.ws_lam = c->ws_lam.p;
     w.factor = c->P.warmstart;
     launch_pair_setup(a, w, npr, s);
+    // launch order of the per-worker kernels: most constraints first, so
+    // the longest workers start in the first wave
+    c->worker_order.ensure((size_t)P + 1);
+    c->wk.ensure((size_t)P + 1); c->wk2.ensure((size_t)P + 1); c->wv2.ensure((size_t)P + 1);
+    launch_worker_cost_keys(c->part_pstart.p, P, c->wk.p, c->worker_order.p, s);
+    bool alt = false;
+    radix_sort_u32(c->wk.p, c->worker_order.p, c->wk2.p, c->wv2.p, P, 24, c->sort_hist, c->sort_tmp, s, &alt);
+    if (alt) std::swap(c->worker_order, c->wv2);
 }
 
 int colour_smem_capacity(ovl_ctx *c) {
@@ -280,6 +281,7 @@ void phase_colour(ovl_ctx *c) {
     c->wprio2.ensure(npr + 1);
     ColourArgs a{};
     a.n_parts = P; a.part_bstart = c->part_bstart.p; a.part_pstart = c->part_pstart.p;
+    a.order = c->worker_order.p;
     a.p_key = c->p_key.p; a.p_slot = c->p_slot.p; a.p_colour = c->p_colour.p;
     a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p; a.pair_of_row = c->pair_of_row.p;
     a.part_rounds = c->part_rounds.p;
@@ -352,6 +354,7 @@ int solve_threads(ovl_ctx *c) {
 SolveArgs solve_args(ovl_ctx *c, float dt_override, int iters) {
     SolveArgs a{};
     a.n_parts = c->n_parts; a.part_bstart = c->part_bstart.p; a.part_list = c->part_list.p;
+    a.order = c->worker_order.p;
     a.entry_body = c->entry_body.p; a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p;
     a.part_scene = c->part_scene.p; a.scene_dt = c->scene_dt.p; a.dt_override = dt_override;
     a.gravity = make_float3(c->P.gravity[0], c->P.gravity[1], c->P.gravity[2]);
@@ -567,6 +570,7 @@ ovl_status ovl_create(ovl_ctx **out, const ovl_params *p, void *cuda_stream) {
             c->own_stream = true;
         }
         for (auto &e : c->ev) CK(cudaEventCreate(&e));
+        c->lb_threads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
         c->status.ensure(4);
         CK(cudaMemsetAsync(c->status.p, 0, 4 * sizeof(int), c->stream));
         return OVL_OK;
@@ -616,6 +620,7 @@ void release_all(ovl_ctx *c) {
     c->qctl.release(); c->D.release(); c->weight.release(); c->stage13.release(); c->scan_tmp.release();
     c->sort_hist.release(); c->sort_tmp.release();
     c->lb_flag.release(); c->lb_pos.release(); c->lb_pairs.release();
+    c->worker_order.release(); c->wk.release(); c->wk2.release(); c->wv2.release();
 }
 
 
@@ -745,6 +750,7 @@ ovl_status ovl_scene_upload(ovl_ctx *c, const ovl_scene_desc *d) {
         c->hs.inv_mass = c->h_im; c->hs.sob = sob; c->hs.part_base = part_base;
         c->hs.scene_gamma.assign(d->scene_gamma, d->scene_gamma + ns);
         c->hs.n_sets.assign(d->n_sets, d->n_sets + ns);
+        c->hs.body_base = c->h_body_base;
         c->hs.jab.assign(d->joint_bodies, d->joint_bodies + 2 * (size_t)c->nj);
         // device copies
         upload(c->radius, d->radius, n, s);

@@ -86,8 +86,8 @@ struct ovl_ctx {
     HBuf<uint64_t> h_mask;
     DBuf<int> lb_flag, lb_pos;
     DBuf<int2> lb_pairs;
-    std::vector<int> lb_a, lb_b;
-    std::vector<uint64_t> lb_mask;
+    DBuf<uint32_t> worker_order, wk, wk2, wv2;   // workers longest first (launch order)
+    int lb_threads = 1;            // host threads of the load balance (scenes run in parallel)
 
     // last step
     int64_t step_index = 0;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -17,18 +18,20 @@ namespace {
 inline int popcount(uint64_t x) { return __builtin_popcountll(x); }
 
 // Live |P_w| per global worker plus the activate / deactivate primitives of
-// Table 1.
+// Table 1.  Workers and bodies of different scenes are disjoint index ranges,
+// so one instance may be used by several threads that each touch only their
+// own scenes.
 class Membership {
   public:
-    Membership(const HostScene &sc, std::vector<uint64_t> &mask) : sc_(sc), mask_(mask) {
-        load_.assign(sc.n_parts, 0);
-        for (int b = 0; b < sc.n; ++b) {
-            uint64_t m = mask[b];
-            int base = sc.part_base[sc.sob[b]];
+    Membership(const HostScene &sc, uint64_t *mask) : sc_(sc), mask_(mask), load_(sc.n_parts, 0) {}
+    // |P_w| of the workers of scenes [s0, s1) from the masks
+    void count(int s0, int s1) {
+        for (int b = sc_.body_base[s0]; b < sc_.body_base[s1]; ++b) {
+            uint64_t m = mask_[b];
+            int base = sc_.part_base[sc_.sob[b]];
             while (m) {
-                int w = __builtin_ctzll(m);
+                ++load_[base + __builtin_ctzll(m)];
                 m &= m - 1;
-                ++load_[base + w];
             }
         }
     }
@@ -69,36 +72,39 @@ class Membership {
 
   private:
     const HostScene &sc_;
-    std::vector<uint64_t> &mask_;
+    uint64_t *mask_;
     std::vector<int64_t> load_;
 };
 
-// vertices within `depth` hops of root (root first), over a CSR graph
+// vertices within `depth` hops of root (root first), over a CSR graph whose
+// vertices lie in [lo, lo + n) (one scene: edges never leave it)
 class Ball {
   public:
-    explicit Ball(int n) : seen_(n, 0), depth_(n, 0) {}
+    explicit Ball(int n, int lo = 0) : seen_(n, 0), depth_(n, 0), lo_(lo) {}
     const std::vector<int> &collect(const int *row_ptr, const int *col, int root, int depth) {
         ++epoch_;
         out_.clear();
         out_.push_back(root);
-        seen_[root] = epoch_;
-        depth_[root] = 0;
+        seen_[root - lo_] = epoch_;
+        depth_[root - lo_] = 0;
         for (size_t head = 0; head < out_.size(); ++head) {
             int u = out_[head];
-            if (depth_[u] == depth) continue;
+            if (depth_[u - lo_] == depth) continue;
             for (int k = row_ptr[u]; k < row_ptr[u + 1]; ++k) {
                 int v = col[k];
-                if (seen_[v] == epoch_) continue;
-                seen_[v] = epoch_;
-                depth_[v] = depth_[u] + 1;
+                if (seen_[v - lo_] == epoch_) continue;
+                seen_[v - lo_] = epoch_;
+                depth_[v - lo_] = depth_[u - lo_] + 1;
                 out_.push_back(v);
             }
         }
         return out_;
     }
+    void rebase(int lo) { lo_ = lo; }
 
   private:
     std::vector<int> seen_, depth_, out_;
+    int lo_;
     int epoch_ = 0;
 };
 
@@ -128,7 +134,8 @@ void host_assign_overlap(const HostScene &sc, std::vector<uint64_t> &mask) {
         auto first = col.begin() + row_ptr[i], last = col.begin() + row_ptr[i + 1];
         std::sort(first, last);
     }
-    Membership mem(sc, mask);
+    Membership mem(sc, mask.data());
+    mem.count(0, sc.ns);
     Ball ball(n);
     auto grow = [&](int root, int gamma, uint64_t Wr) {      // Algorithm 3
         const std::vector<int> &N = ball.collect(row_ptr.data(), col.data(), root, gamma);
@@ -148,20 +155,25 @@ void host_assign_overlap(const HostScene &sc, std::vector<uint64_t> &mask) {
     }
 }
 
-// Algorithm 6 over contacts between dynamic bodies, in canonical order.
-void host_load_balance(const HostScene &sc, std::vector<uint64_t> &mask, int64_t nc, const int *ca,
-                       const int *cb, const int *row_ptr, const int *col, bool do_activate,
-                       bool do_deactivate) {
-    if (nc == 0 || (!do_activate && !do_deactivate)) return;
-    Membership mem(sc, mask);
-    Ball ball(sc.n);
+namespace {
+
+// Algorithm 6 over candidates [i0, i1), all of scenes [s0, s1)
+void load_balance_range(const HostScene &sc, Membership &mem, const int2 *ab, int64_t i0, int64_t i1,
+                        int s0, int s1, const int *row_ptr, const int *col, bool do_activate,
+                        bool do_deactivate) {
+    mem.count(s0, s1);
+    if (i0 == i1) return;
+    int widest = 0;
+    for (int s = s0; s < s1; ++s) widest = std::max(widest, sc.body_base[s + 1] - sc.body_base[s]);
+    Ball ball(widest, sc.body_base[s0]);
+    int ball_scene = -1;
     auto bridge = [&](int b) {                                  // Algorithm 7
         uint64_t u = 0;
         for (int k = row_ptr[b]; k < row_ptr[b + 1]; ++k) u |= mem.W(col[k]);
         return popcount(u) > 1;
     };
-    for (int64_t i = 0; i < nc; ++i) {
-        const int A = ca[i], B = cb[i];
+    for (int64_t i = i0; i < i1; ++i) {
+        const int A = ab[i].x, B = ab[i].y;
         const uint64_t WA = mem.W(A), WB = mem.W(B);
         const int scene = sc.sob[A];
         if ((WA & WB) == 0) {                                   // activation branch
@@ -174,6 +186,7 @@ void host_load_balance(const HostScene &sc, std::vector<uint64_t> &mask, int64_t
                 mem.activate(WB, A);
                 root = A;
             }
+            if (scene != ball_scene) { ball.rebase(sc.body_base[scene]); ball_scene = scene; }
             const std::vector<int> &N =
                 ball.collect(row_ptr, col, root, sc.scene_gamma[scene]);   // gamma-ball
             for (int v : N) mem.activate((WA | WB) & ~mem.W(v), v);
@@ -191,6 +204,46 @@ void host_load_balance(const HostScene &sc, std::vector<uint64_t> &mask, int64_t
             mem.deactivate(WB & ~keep, B);
         }
     }
+}
+
+}  // namespace
+
+// Algorithm 6 over contacts between dynamic bodies, in canonical order.
+// Contacts of one scene are contiguous in that order and touch only that
+// scene's masks and worker loads, so runs of whole scenes go to up to
+// `threads` host threads; the result is the sequential one.
+void host_load_balance(const HostScene &sc, uint64_t *mask, int64_t nc, const int2 *ab,
+                       const int *row_ptr, const int *col, bool do_activate, bool do_deactivate,
+                       int threads) {
+    if (nc == 0 || (!do_activate && !do_deactivate)) return;
+    Membership mem(sc, mask);
+    // candidate range of every scene
+    std::vector<int64_t> first(sc.ns + 1, nc);
+    for (int64_t i = nc - 1; i >= 0; --i) first[sc.sob[ab[i].x]] = i;
+    for (int s = sc.ns - 1; s >= 0; --s) first[s] = std::min(first[s], first[s + 1]);
+    // chunks of whole scenes with about equal candidates plus bodies
+    const int T = std::max(1, std::min(threads, sc.ns));
+    std::vector<int> cut{0};
+    const double per = (double)(nc + sc.n) / T;
+    double acc = 0.0;
+    for (int s = 0; s < sc.ns; ++s) {
+        acc += (double)(first[s + 1] - first[s]) + (sc.body_base[s + 1] - sc.body_base[s]);
+        if (acc >= per * (double)cut.size() && (int)cut.size() < T && s + 1 < sc.ns) cut.push_back(s + 1);
+    }
+    cut.push_back(sc.ns);
+    auto run = [&](size_t k) {
+        const int s0 = cut[k], s1 = cut[k + 1];
+        load_balance_range(sc, mem, ab, first[s0], first[s1], s0, s1, row_ptr, col, do_activate,
+                           do_deactivate);
+    };
+    if (cut.size() == 2) {
+        run(0);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (size_t k = 1; k + 1 < cut.size(); ++k) pool.emplace_back(run, k);
+    run(0);
+    for (auto &t : pool) t.join();
 }
 
 }  // namespace ovl

@@ -102,6 +102,14 @@ __device__ __forceinline__ int body_slot(const MemberArgs &a, int x, int w) {
     return a.entry_slot[e];
 }
 
+__global__ void k_worker_cost_keys(const int *part_pstart, int P, uint32_t *keys, uint32_t *vals) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const uint32_t cost = (uint32_t)min(part_pstart[p + 1] - part_pstart[p], (1 << 24) - 1);
+        keys[p] = ((1u << 24) - 1u) - cost;
+        vals[p] = (uint32_t)p;
+    }
+}
+
 __global__ void k_pair_setup(MemberArgs a, WarmArgs ws, int np) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
         int i = a.ps_cons[k], p = a.ps_part[k];
@@ -395,7 +403,7 @@ template <int C>
 __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
     extern __shared__ unsigned long long dyn_smem[];
     const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
-    const int p = blockIdx.x / C;
+    const int p = a.order ? (int)a.order[blockIdx.x / C] : (int)(blockIdx.x / C);
     const int nb = a.part_bstart[p + 1] - a.part_bstart[p];
     const int per = (nb + C - 1) / C;
     if (per <= a.smem_slots) {
@@ -544,6 +552,14 @@ void launch_pair_gather(const MemberArgs &a, const uint32_t *order, int np, cuda
 void launch_pair_setup(const MemberArgs &a, const WarmArgs &w, int np, cudaStream_t s) {
     if (!np) return;
     k_pair_setup<<<grid1d(np, 256), 256, 0, s>>>(a, w, np);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_worker_cost_keys(const int *part_pstart, int P, uint32_t *keys, uint32_t *vals,
+                             cudaStream_t s) {
+    if (P <= 0) return;
+    k_worker_cost_keys<<<grid1d(P, 256), 256, 0, s>>>(part_pstart, P, keys, vals);
     note_launch();
     CK(cudaGetLastError());
 }

@@ -426,7 +426,7 @@ template <int C, int U>
 __global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveArgs a) {
     extern __shared__ float4 sm[];
     const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
-    const int p = blockIdx.x / C;
+    const int p = a.order ? (int)a.order[blockIdx.x / C] : (int)(blockIdx.x / C);
     const int b0 = a.part_bstart[p], nb = a.part_bstart[p + 1] - b0;
     const int per = (nb + C - 1) / C;
     if (nb >= 0xffff) {

@@ -96,9 +96,14 @@ struct WarmArgs {
     float factor;
 };
 void launch_pair_setup(const MemberArgs &a, const WarmArgs &w, int np, cudaStream_t s);
+// keys[p] = 2^24 - 1 - min(pairs of worker p, 2^24 - 1), vals[p] = p: an
+// ascending stable sort of the keys lists the workers longest first
+void launch_worker_cost_keys(const int *part_pstart, int P, uint32_t *keys, uint32_t *vals,
+                             cudaStream_t s);
 
 struct ColourArgs {
     int n_parts;
+    const uint32_t *order;     // [P] worker of each CTA group, longest first (NULL: identity)
     const int *part_bstart;
     const int *part_pstart;
     const uint64_t *p_key;
@@ -146,6 +151,7 @@ void launch_rows(const RowArgs &a, cudaStream_t s);
 // ---- PGS solve + integration (k_solve.cu) ----------------------------------
 struct SolveArgs {
     int n_parts;
+    const uint32_t *order;     // [P] worker of each CTA group, longest first (NULL: identity)
     const int *part_bstart;
     const int *part_list;
     const int *entry_body;

@@ -54,6 +54,17 @@ def test_random_pile(n, seed, sets):
     P.compare_step(orc, gpu)
 
 
+@pytest.mark.parametrize("n_scenes,hi", [(12, 1024), (40, 300)])
+def test_batched_scenes(n_scenes, hi):
+    """Independent scenes of log-uniform sizes (piles and chains, 1-16 uneven
+    sets each) stepped as one batch: every scene's records match the oracle."""
+    P = _parity()
+    sc = S.batched(seed=3, n_scenes=n_scenes, lo=64, hi=hi)
+    orc, gpu = P.prepare(sc, warm_steps=2)
+    rep = P.compare_step(orc, gpu)
+    assert rep["contacts"] > 100
+
+
 def test_closed_forms_on_gpu():
     from paper_2403_17261_gb300 import ovl
     sc = S.resting_sphere()
