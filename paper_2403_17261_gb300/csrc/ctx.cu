@@ -367,6 +367,107 @@ SolveArgs solve_args(ovl_ctx *c, float dt_override, int iters) {
     return a;
 }
 
+// Per-worker CTA counts for the default launch: every worker starts at the
+// fewest CTAs (1, 2, 4 or 8) whose shares of its bodies fit one CTA's shared
+// memory; while all CTAs still fit one per SM, the worker with the most rows
+// per CTA doubles its CTAs.  Workers with the same count form one launch, and
+// the launches run side by side on the context's streams.  Every launch
+// shape gives the same bits (the solver is built without FMA contraction),
+// so the plan changes only the time.  Returns false when some worker does
+// not fit even 8 CTAs (the uniform launch then takes it to global memory).
+struct SolveClass { int C, first, count, slots; };
+
+// the doubling stops at this many CTAs per worker (more only where a
+// worker's bodies need them), and leaves this many SMs unclaimed: clusters
+// must fit inside one GPC, so a launch that claims every SM can leave a
+// cluster waiting for a second wave
+#ifndef OVL_SOLVE_MAX_DOUBLE
+#define OVL_SOLVE_MAX_DOUBLE 4
+#endif
+#ifndef OVL_SOLVE_SM_SLACK
+#define OVL_SOLVE_SM_SLACK 8
+#endif
+
+// CTA shapes of the per-class launches: threads, rows per thread, CTAs per SM
+struct SolveShape { int threads, unroll, per_sm; };
+constexpr SolveShape kSolveShapes[3] = {{512, 2, 1}, {512, 1, 2}, {256, 2, 2}};
+
+// the shape without tuning: one CTA per SM while the workers do not
+// outnumber the SMs, else two smaller CTAs per SM
+int default_solve_shape(const ovl_ctx *c) { return c->n_parts <= c->num_sms ? 0 : 2; }
+
+bool plan_solve_classes(ovl_ctx *c, const SolveShape &shape, std::vector<SolveClass> &classes) {
+    const int P = c->n_parts;
+    std::vector<int> pb(P + 1), pp(P + 1);
+    download(pb.data(), c->part_bstart.p, (size_t)P + 1, c->stream);
+    download(pp.data(), c->part_pstart.p, (size_t)P + 1, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+    const int cap1 = solve_slot_capacity(c, shape.per_sm);
+    std::vector<int> C(P);
+    long long total = 0;
+    for (int p = 0; p < P; ++p) {
+        const int nb = pb[p + 1] - pb[p];
+        int k = 1;
+        while (k <= 8 && (nb + k - 1) / k > cap1) k <<= 1;
+        if (k > 8) return false;
+        C[p] = k;
+        total += k;
+    }
+    // rows per CTA, the solve time of a worker up to a constant
+    auto load = [&](int p) { return (double)(pp[p + 1] - pp[p]) / C[p]; };
+    const long long budget = (long long)shape.per_sm * c->num_sms - OVL_SOLVE_SM_SLACK;
+    if (total <= budget) {
+        std::vector<int> heap(P);
+        std::iota(heap.begin(), heap.end(), 0);
+        auto less = [&](int x, int y) { return load(x) < load(y) || (load(x) == load(y) && x > y); };
+        std::make_heap(heap.begin(), heap.end(), less);
+        while (!heap.empty()) {
+            std::pop_heap(heap.begin(), heap.end(), less);
+            const int p = heap.back();
+            if (C[p] >= OVL_SOLVE_MAX_DOUBLE || total + C[p] > budget) break;
+            total += C[p];
+            C[p] <<= 1;
+            std::push_heap(heap.begin(), heap.end(), less);
+        }
+    }
+    // launch order: by CTA count, then most rows first
+    std::vector<int> order(P);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (C[x] != C[y]) return C[x] > C[y];
+        return pp[x + 1] - pp[x] > pp[y + 1] - pp[y];
+    });
+    classes.clear();
+    for (int i = 0; i < P; ++i) {
+        const int p = order[i], nb = pb[p + 1] - pb[p];
+        if (classes.empty() || classes.back().C != C[p]) classes.push_back({C[p], i, 0, 1});
+        SolveClass &k = classes.back();
+        k.count++;
+        k.slots = std::max(k.slots, (nb + C[p] - 1) / C[p]);
+    }
+    std::vector<uint32_t> o(order.begin(), order.end());
+    upload(c->class_order, o.data(), o.size(), c->stream);
+    return true;
+}
+
+void launch_solve_classes(ovl_ctx *c, const SolveArgs &a, const SolveShape &shape,
+                          const std::vector<SolveClass> &classes) {
+    CK(cudaEventRecord(c->fork, c->stream));
+    for (size_t k = 0; k < classes.size(); ++k) {
+        cudaStream_t sk = k == 0 ? c->stream : c->aux[k - 1];
+        if (k) CK(cudaStreamWaitEvent(sk, c->fork, 0));
+        SolveArgs b = a;
+        b.n_parts = classes[k].count;
+        b.order = c->class_order.p + classes[k].first;
+        b.smem_slots = classes[k].slots;
+        launch_solve(b, shape.threads, classes[k].C, shape.unroll, sk);
+    }
+    for (size_t k = 1; k < classes.size(); ++k) {
+        CK(cudaEventRecord(c->join[k - 1], c->aux[k - 1]));
+        CK(cudaStreamWaitEvent(c->stream, c->join[k - 1], 0));
+    }
+}
+
 // problem-size bucket of the autotuner: the number of workers and the largest
 // worker's body count rounded up to a power of four
 std::string tune_key(ovl_ctx *c) {
@@ -384,13 +485,14 @@ int solve_slots_for(ovl_ctx *c, int cluster) {
     return per <= solve_slot_capacity(c, 1) ? per : 0;
 }
 
-// K13: time every feasible (CTAs per worker, threads per CTA, rows per thread
-// and colour step) on this step's rows and keep the fastest for the bucket.
+// K13: time every feasible uniform launch (CTAs per worker, threads per CTA,
+// rows per thread and colour step) and every per-worker plan shape on this
+// step's rows and keep the fastest for the bucket.
 // Rows of one colour are independent, so every candidate computes the same
 // bits; re-running the row build restores the warm-start impulses.
 void autotune(ovl_ctx *c, float dt_override, int iters, const std::string &key) {
     cudaStream_t s = c->stream;
-    ovl_ctx::TuneCfg best{0, 0, 0, 1e30f};
+    ovl_ctx::TuneCfg best{0, 0, 0, 1e30f, 0};
     cudaEvent_t e0 = c->ev[10], e1 = c->ev[11];
     for (int cl : {1, 2, 4, 8})
         for (int th : {256, 512})
@@ -406,9 +508,22 @@ void autotune(ovl_ctx *c, float dt_override, int iters, const std::string &key) 
                 CK(cudaEventSynchronize(e1));
                 float ms = 0.f;
                 CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best.ms) best = {cl, th, un, ms};
+                if (ms < best.ms) best = {cl, th, un, ms, 0};
             }
-    if (best.cluster) c->tuned[key] = best;
+    for (int sh = 0; sh < 3; ++sh) {
+        std::vector<SolveClass> classes;
+        if (!plan_solve_classes(c, kSolveShapes[sh], classes)) continue;
+        SolveArgs a = solve_args(c, dt_override, iters);
+        phase_rows(c, dt_override);
+        CK(cudaEventRecord(e0, s));
+        launch_solve_classes(c, a, kSolveShapes[sh], classes);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best.ms) best = {0, kSolveShapes[sh].threads, kSolveShapes[sh].unroll, ms, sh + 1};
+    }
+    if (best.cluster || best.shape) c->tuned[key] = best;
     phase_rows(c, dt_override);   // fresh impulses for the real solve
 }
 
@@ -420,9 +535,10 @@ void phase_solve(ovl_ctx *c, float dt_override, int iters) {
     c->part_iters.ensure((size_t)P + 1);
     c->part_res_sq.ensure((size_t)P + 1);
     CK(cudaMemsetAsync(c->part_res_sq.p, 0, sizeof(double) * ((size_t)P + 1), c->stream));
+    const bool fixed = c->P.pgs_cluster > 0 || c->P.pgs_threads > 0 || c->P.smem_slot_limit > 0;
     int cluster = 1, slots = 0, threads = solve_threads(c), unroll = 1;
-    solve_config(c, &cluster, &slots, &unroll);
-    if (c->P.flags & OVL_FLAG_AUTOTUNE) {
+    int shape = fixed ? -1 : default_solve_shape(c);   // >= 0: per-worker plan with that shape
+    if (!fixed && (c->P.flags & OVL_FLAG_AUTOTUNE) && P > 0) {
         std::string key = tune_key(c);
         auto it = c->tuned.find(key);
         if (it == c->tuned.end()) {
@@ -430,8 +546,10 @@ void phase_solve(ovl_ctx *c, float dt_override, int iters) {
             it = c->tuned.find(key);
         }
         if (it != c->tuned.end()) {
-            int sl = solve_slots_for(c, it->second.cluster);
-            if (sl) {
+            if (it->second.shape > 0) {
+                shape = it->second.shape - 1;
+            } else if (int sl = solve_slots_for(c, it->second.cluster)) {
+                shape = -1;
                 cluster = it->second.cluster;
                 threads = it->second.threads;
                 unroll = it->second.unroll;
@@ -439,6 +557,15 @@ void phase_solve(ovl_ctx *c, float dt_override, int iters) {
             }
         }
     }
+    std::vector<SolveClass> classes;
+    if (shape >= 0 && P > 0 && plan_solve_classes(c, kSolveShapes[shape], classes)) {
+        launch_solve_classes(c, solve_args(c, dt_override, iters), kSolveShapes[shape], classes);
+        c->last_cluster = classes.front().C;
+        c->last_threads = kSolveShapes[shape].threads;
+        c->last_unroll = kSolveShapes[shape].unroll;
+        return;
+    }
+    if (slots == 0) solve_config(c, &cluster, &slots, &unroll);
     c->last_cluster = cluster;
     c->last_threads = threads;
     c->last_unroll = unroll;
@@ -570,6 +697,9 @@ ovl_status ovl_create(ovl_ctx **out, const ovl_params *p, void *cuda_stream) {
             c->own_stream = true;
         }
         for (auto &e : c->ev) CK(cudaEventCreate(&e));
+        for (auto &x : c->aux) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+        for (auto &e : c->join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         c->lb_threads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
         c->status.ensure(4);
         CK(cudaMemsetAsync(c->status.p, 0, 4 * sizeof(int), c->stream));
@@ -621,6 +751,7 @@ void release_all(ovl_ctx *c) {
     c->sort_hist.release(); c->sort_tmp.release();
     c->lb_flag.release(); c->lb_pos.release(); c->lb_pairs.release();
     c->worker_order.release(); c->wk.release(); c->wk2.release(); c->wv2.release();
+    c->class_order.release();
 }
 
 
@@ -656,6 +787,11 @@ ovl_status ovl_destroy(ovl_ctx *c) {
     release_mlp(c);
     c->h_i32.release(); c->h_ab.release(); c->h_rp.release(); c->h_col.release(); c->h_mask.release();
     for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    for (auto &x : c->aux)
+        if (x) { cudaStreamSynchronize(x); cudaStreamDestroy(x); }
+    if (c->fork) cudaEventDestroy(c->fork);
+    for (auto &e : c->join)
         if (e) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1102,8 +1238,8 @@ ovl_status ovl_autotune_export(ovl_ctx *c, char *buf, size_t cap, size_t *len) {
             if (!first) o << ", ";
             first = false;
             o << "\"" << kv.first << "\": {\"cluster\": " << kv.second.cluster << ", \"threads\": "
-              << kv.second.threads << ", \"rows_per_thread\": " << kv.second.unroll << ", \"ms\": "
-              << kv.second.ms << "}";
+              << kv.second.threads << ", \"rows_per_thread\": " << kv.second.unroll << ", \"per_worker\": "
+              << kv.second.shape << ", \"ms\": " << kv.second.ms << "}";
         }
         o << "}";
         std::string t = o.str();
@@ -1140,8 +1276,10 @@ ovl_status ovl_autotune_import(ovl_ctx *c, const char *json) {
             cfg.threads = (int)num("threads", ob, cb);
             cfg.unroll = (int)num("rows_per_thread", ob, cb);
             cfg.ms = (float)num("ms", ob, cb);
-            bool ok = (cfg.cluster == 1 || cfg.cluster == 2 || cfg.cluster == 4 || cfg.cluster == 8) &&
-                      (cfg.threads >= 32 && cfg.threads <= 512) && (cfg.unroll == 1 || cfg.unroll == 2);
+            cfg.shape = t.find("\"per_worker\"", ob) < cb ? (int)num("per_worker", ob, cb) : 0;
+            bool ok = cfg.shape > 0 ? cfg.shape <= 3
+                                    : (cfg.cluster == 1 || cfg.cluster == 2 || cfg.cluster == 4 || cfg.cluster == 8) &&
+                                          (cfg.threads >= 32 && cfg.threads <= 512) && (cfg.unroll == 1 || cfg.unroll == 2);
             if (!ok) return fail(c, OVL_ERR_ARG, "autotune json: bad entry " + key);
             c->tuned[key] = cfg;
             pos = cb + 1;

@@ -22,7 +22,8 @@ struct ovl_ctx {
     int smem_per_sm = 0;
     int nb_max = 0;          // most bodies in one worker (last membership phase)
     int last_cluster = 1, last_threads = 512, last_unroll = 1;
-    struct TuneCfg { int cluster, threads, unroll; float ms; };
+    // a tuned solve launch: uniform (cluster > 0) or per-worker plan (shape = 1 + its index)
+    struct TuneCfg { int cluster, threads, unroll; float ms; int shape; };
     std::map<std::string, TuneCfg> tuned;   // autotuner results by problem-size bucket
     std::string err;
 
@@ -87,6 +88,9 @@ struct ovl_ctx {
     DBuf<int> lb_flag, lb_pos;
     DBuf<int2> lb_pairs;
     DBuf<uint32_t> worker_order, wk, wk2, wv2;   // workers longest first (launch order)
+    DBuf<uint32_t> class_order;                  // solve: workers grouped by CTAs per worker
+    cudaStream_t aux[3] = {};                    // side streams of the per-class solve launches
+    cudaEvent_t fork = nullptr, join[3] = {};
     int lb_threads = 1;            // host threads of the load balance (scenes run in parallel)
 
     // last step
