@@ -141,9 +141,14 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
     CK(cudaMemcpyAsync(c->h_rp.p, c->row_ptr.p, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->h_col.p, c->col.p, sizeof(int) * c->nadj, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->h_mask.p, c->mask.p, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, s));
+    c->lb_loads.ensure((size_t)c->n_parts + 1);
+    c->h_loads.ensure((size_t)c->n_parts + 1);
+    launch_worker_loads(c->mask.p, c->sob.p, c->part_base.p, n, c->n_parts, c->lb_loads.p, s);
+    CK(cudaMemcpyAsync(c->h_loads.p, c->lb_loads.p, sizeof(int) * c->n_parts, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    host_load_balance(c->hs, c->h_mask.p, m, c->h_ab.p, c->h_rp.p, c->h_col.p, act, deact,
-                      c->lb_threads);
+    if ((int)c->lb_ws.size() != c->lb_threads) c->lb_ws.resize(c->lb_threads);
+    host_load_balance(c->hs, c->h_mask.p, c->h_loads.p, m, c->h_ab.p, c->h_rp.p, c->h_col.p, act,
+                      deact, c->lb_ws);
     CK(cudaMemcpyAsync(c->mask.p, c->h_mask.p, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     c->lb_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -751,7 +756,7 @@ void release_all(ovl_ctx *c) {
     c->sort_hist.release(); c->sort_tmp.release();
     c->lb_flag.release(); c->lb_pos.release(); c->lb_pairs.release();
     c->worker_order.release(); c->wk.release(); c->wk2.release(); c->wv2.release();
-    c->class_order.release();
+    c->class_order.release(); c->lb_loads.release();
 }
 
 
@@ -785,6 +790,7 @@ ovl_status ovl_destroy(ovl_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     release_all(c);
     release_mlp(c);
+    c->h_loads.release();
     c->h_i32.release(); c->h_ab.release(); c->h_rp.release(); c->h_col.release(); c->h_mask.release();
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);

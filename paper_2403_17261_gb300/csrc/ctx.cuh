@@ -92,6 +92,9 @@ struct ovl_ctx {
     cudaStream_t aux[3] = {};                    // side streams of the per-class solve launches
     cudaEvent_t fork = nullptr, join[3] = {};
     int lb_threads = 1;            // host threads of the load balance (scenes run in parallel)
+    std::vector<BallWorkspace> lb_ws;
+    DBuf<int> lb_loads;
+    HBuf<int> h_loads;
 
     // last step
     int64_t step_index = 0;

@@ -24,6 +24,8 @@ inline int popcount(uint64_t x) { return __builtin_popcountll(x); }
 class Membership {
   public:
     Membership(const HostScene &sc, uint64_t *mask) : sc_(sc), mask_(mask), load_(sc.n_parts, 0) {}
+    Membership(const HostScene &sc, uint64_t *mask, const int *loads)
+        : sc_(sc), mask_(mask), load_(loads, loads + sc.n_parts) {}
     // |P_w| of the workers of scenes [s0, s1) from the masks
     void count(int s0, int s1) {
         for (int b = sc_.body_base[s0]; b < sc_.body_base[s1]; ++b) {
@@ -77,35 +79,46 @@ class Membership {
 };
 
 // vertices within `depth` hops of root (root first), over a CSR graph whose
-// vertices lie in [lo, lo + n) (one scene: edges never leave it)
+// vertices lie in [lo, lo + n) (one scene: edges never leave it); the
+// stamps live in a workspace that outlasts the call
 class Ball {
   public:
-    explicit Ball(int n, int lo = 0) : seen_(n, 0), depth_(n, 0), lo_(lo) {}
+    Ball(BallWorkspace &w, int n, int lo = 0) : w_(w), lo_(lo) {
+        if ((int)w_.seen.size() < n) {
+            w_.seen.assign(n, 0);
+            w_.depth.assign(n, 0);
+            w_.epoch = 0;
+        }
+    }
     const std::vector<int> &collect(const int *row_ptr, const int *col, int root, int depth) {
-        ++epoch_;
-        out_.clear();
-        out_.push_back(root);
-        seen_[root - lo_] = epoch_;
-        depth_[root - lo_] = 0;
-        for (size_t head = 0; head < out_.size(); ++head) {
-            int u = out_[head];
-            if (depth_[u - lo_] == depth) continue;
+        if (++w_.epoch == 0x7fffffff) {
+            std::fill(w_.seen.begin(), w_.seen.end(), 0);
+            w_.epoch = 1;
+        }
+        const int ep = w_.epoch;
+        std::vector<int> &out = w_.out;
+        out.clear();
+        out.push_back(root);
+        w_.seen[root - lo_] = ep;
+        w_.depth[root - lo_] = 0;
+        for (size_t head = 0; head < out.size(); ++head) {
+            int u = out[head];
+            if (w_.depth[u - lo_] == depth) continue;
             for (int k = row_ptr[u]; k < row_ptr[u + 1]; ++k) {
                 int v = col[k];
-                if (seen_[v - lo_] == epoch_) continue;
-                seen_[v - lo_] = epoch_;
-                depth_[v - lo_] = depth_[u - lo_] + 1;
-                out_.push_back(v);
+                if (w_.seen[v - lo_] == ep) continue;
+                w_.seen[v - lo_] = ep;
+                w_.depth[v - lo_] = w_.depth[u - lo_] + 1;
+                out.push_back(v);
             }
         }
-        return out_;
+        return out;
     }
     void rebase(int lo) { lo_ = lo; }
 
   private:
-    std::vector<int> seen_, depth_, out_;
+    BallWorkspace &w_;
     int lo_;
-    int epoch_ = 0;
 };
 
 }  // namespace
@@ -136,7 +149,8 @@ void host_assign_overlap(const HostScene &sc, std::vector<uint64_t> &mask) {
     }
     Membership mem(sc, mask.data());
     mem.count(0, sc.ns);
-    Ball ball(n);
+    BallWorkspace bw;
+    Ball ball(bw, n);
     auto grow = [&](int root, int gamma, uint64_t Wr) {      // Algorithm 3
         const std::vector<int> &N = ball.collect(row_ptr.data(), col.data(), root, gamma);
         for (int b : N)
@@ -160,12 +174,11 @@ namespace {
 // Algorithm 6 over candidates [i0, i1), all of scenes [s0, s1)
 void load_balance_range(const HostScene &sc, Membership &mem, const int2 *ab, int64_t i0, int64_t i1,
                         int s0, int s1, const int *row_ptr, const int *col, bool do_activate,
-                        bool do_deactivate) {
-    mem.count(s0, s1);
+                        bool do_deactivate, BallWorkspace &bw) {
     if (i0 == i1) return;
     int widest = 0;
     for (int s = s0; s < s1; ++s) widest = std::max(widest, sc.body_base[s + 1] - sc.body_base[s]);
-    Ball ball(widest, sc.body_base[s0]);
+    Ball ball(bw, widest, sc.body_base[s0]);
     int ball_scene = -1;
     auto bridge = [&](int b) {                                  // Algorithm 7
         uint64_t u = 0;
@@ -212,11 +225,12 @@ void load_balance_range(const HostScene &sc, Membership &mem, const int2 *ab, in
 // Contacts of one scene are contiguous in that order and touch only that
 // scene's masks and worker loads, so runs of whole scenes go to up to
 // `threads` host threads; the result is the sequential one.
-void host_load_balance(const HostScene &sc, uint64_t *mask, int64_t nc, const int2 *ab,
-                       const int *row_ptr, const int *col, bool do_activate, bool do_deactivate,
-                       int threads) {
-    if (nc == 0 || (!do_activate && !do_deactivate)) return;
-    Membership mem(sc, mask);
+void host_load_balance(const HostScene &sc, uint64_t *mask, const int *loads, int64_t nc,
+                       const int2 *ab, const int *row_ptr, const int *col, bool do_activate,
+                       bool do_deactivate, std::vector<BallWorkspace> &ws) {
+    if (nc == 0 || (!do_activate && !do_deactivate) || ws.empty()) return;
+    const int threads = (int)ws.size();
+    Membership mem(sc, mask, loads);
     // candidate range of every scene
     std::vector<int64_t> first(sc.ns + 1, nc);
     for (int64_t i = nc - 1; i >= 0; --i) first[sc.sob[ab[i].x]] = i;
@@ -234,7 +248,7 @@ void host_load_balance(const HostScene &sc, uint64_t *mask, int64_t nc, const in
     auto run = [&](size_t k) {
         const int s0 = cut[k], s1 = cut[k + 1];
         load_balance_range(sc, mem, ab, first[s0], first[s1], s0, s1, row_ptr, col, do_activate,
-                           do_deactivate);
+                           do_deactivate, ws[k]);
     };
     if (cut.size() == 2) {
         run(0);

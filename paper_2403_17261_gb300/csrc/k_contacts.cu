@@ -340,6 +340,47 @@ void launch_adj_compact(const int *tptr, const int *tcol, int n, const int *row_
 }  // namespace ovl
 
 namespace ovl {
+namespace {
+
+// |P_w| of every worker: one count per set bit of every mask; a block-local
+// histogram when the workers fit shared memory
+__global__ void k_worker_loads(const uint64_t *mask, const int *sob, const int *part_base, int n,
+                               int P, int *loads) {
+    extern __shared__ int hist[];
+    const bool local = P <= 8192;
+    if (local) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+    }
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
+        uint64_t m = mask[b];
+        if (!m) continue;
+        const int base = part_base[sob[b]];
+        while (m) {
+            const int w = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            atomicAdd(local ? &hist[base + w] : &loads[base + w], 1);
+        }
+    }
+    if (local) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < P; i += blockDim.x)
+            if (hist[i]) atomicAdd(&loads[i], hist[i]);
+    }
+}
+
+}  // namespace
+
+void launch_worker_loads(const uint64_t *mask, const int *sob, const int *part_base, int n, int P,
+                         int *loads, cudaStream_t s) {
+    CK(cudaMemsetAsync(loads, 0, sizeof(int) * (size_t)P, s));
+    if (n <= 0) return;
+    const int smem = P <= 8192 ? P * (int)sizeof(int) : 0;
+    k_worker_loads<<<std::min(grid1d(n, 256), 152 * 2), 256, smem, s>>>(mask, sob, part_base, n, P, loads);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
 void launch_lb_flags(const int2 *c_ab, int nc, const float *im, int n, const uint64_t *mask,
                      int disjoint_only, int *flag, cudaStream_t s) {
     if (!nc) return;

@@ -43,6 +43,9 @@ void launch_edge_degree(const int2 *c_ab, int nc, const int2 *jab, int nj, const
 void launch_edge_fill(const int2 *c_ab, int nc, const int2 *jab, int nj, const float *im, int n,
                       const int *tptr, int *cursor, int *tcol, cudaStream_t s);
 void launch_adj_unique(const int *tptr, int n, int *tcol, int *ucount, cudaStream_t s);
+// loads [P] := |P_w| of every worker from the masks
+void launch_worker_loads(const uint64_t *mask, const int *sob, const int *part_base, int n, int P,
+                         int *loads, cudaStream_t s);
 void launch_lb_flags(const int2 *c_ab, int nc, const float *im, int n, const uint64_t *mask,
                      int disjoint_only, int *flag, cudaStream_t s);
 void launch_lb_compact(const int2 *c_ab, int nc, const int *flag, const int *pos, int2 *out,
