@@ -373,21 +373,21 @@ SolveArgs solve_args(ovl_ctx *c, float dt_override, int iters) {
 }
 
 // Per-worker CTA counts for the default launch: every worker starts at the
-// fewest CTAs (1, 2, 4 or 8) whose shares of its bodies fit one CTA's shared
-// memory; while all CTAs still fit one per SM, the worker with the most rows
-// per CTA doubles its CTAs.  Workers with the same count form one launch, and
+// fewest CTAs (1, 2, 3, 4, 6 or 8) whose shares of its bodies fit one CTA's
+// shared memory; while all CTAs still fit the SMs, the worker with the most
+// rows per CTA moves to the next count.  Workers with the same count form one launch, and
 // the launches run side by side on the context's streams.  Every launch
 // shape gives the same bits (the solver is built without FMA contraction),
 // so the plan changes only the time.  Returns false when some worker does
 // not fit even 8 CTAs (the uniform launch then takes it to global memory).
 struct SolveClass { int C, first, count, slots; };
 
-// the doubling stops at this many CTAs per worker (more only where a
+// the growth stops at this many CTAs per worker (more only where a
 // worker's bodies need them), and leaves this many SMs unclaimed: clusters
 // must fit inside one GPC, so a launch that claims every SM can leave a
 // cluster waiting for a second wave
-#ifndef OVL_SOLVE_MAX_DOUBLE
-#define OVL_SOLVE_MAX_DOUBLE 4
+#ifndef OVL_SOLVE_MAX_GROW
+#define OVL_SOLVE_MAX_GROW 4
 #endif
 #ifndef OVL_SOLVE_SM_SLACK
 #define OVL_SOLVE_SM_SLACK 8
@@ -408,13 +408,15 @@ bool plan_solve_classes(ovl_ctx *c, const SolveShape &shape, std::vector<SolveCl
     download(pp.data(), c->part_pstart.p, (size_t)P + 1, c->stream);
     CK(cudaStreamSynchronize(c->stream));
     const int cap1 = solve_slot_capacity(c, shape.per_sm);
+    static const int kSizes[] = {1, 2, 3, 4, 6, 8};
+    auto next = [](int k) { for (int x : kSizes) if (x > k) return x; return 0; };
     std::vector<int> C(P);
     long long total = 0;
     for (int p = 0; p < P; ++p) {
         const int nb = pb[p + 1] - pb[p];
         int k = 1;
-        while (k <= 8 && (nb + k - 1) / k > cap1) k <<= 1;
-        if (k > 8) return false;
+        while (k && (nb + k - 1) / k > cap1) k = next(k);
+        if (!k) return false;
         C[p] = k;
         total += k;
     }
@@ -429,9 +431,10 @@ bool plan_solve_classes(ovl_ctx *c, const SolveShape &shape, std::vector<SolveCl
         while (!heap.empty()) {
             std::pop_heap(heap.begin(), heap.end(), less);
             const int p = heap.back();
-            if (C[p] >= OVL_SOLVE_MAX_DOUBLE || total + C[p] > budget) break;
-            total += C[p];
-            C[p] <<= 1;
+            const int up = next(C[p]);
+            if (!up || up > OVL_SOLVE_MAX_GROW || total + (up - C[p]) > budget) break;
+            total += up - C[p];
+            C[p] = up;
             std::push_heap(heap.begin(), heap.end(), less);
         }
     }

@@ -89,8 +89,8 @@ struct ovl_ctx {
     DBuf<int2> lb_pairs;
     DBuf<uint32_t> worker_order, wk, wk2, wv2;   // workers longest first (launch order)
     DBuf<uint32_t> class_order;                  // solve: workers grouped by CTAs per worker
-    cudaStream_t aux[3] = {};                    // side streams of the per-class solve launches
-    cudaEvent_t fork = nullptr, join[3] = {};
+    cudaStream_t aux[5] = {};                    // side streams of the per-class solve launches
+    cudaEvent_t fork = nullptr, join[5] = {};
     int lb_threads = 1;            // host threads of the load balance (scenes run in parallel)
     std::vector<BallWorkspace> lb_ws;
     DBuf<int> lb_loads;

@@ -479,14 +479,18 @@ void launch_solve(const SolveArgs &a, int threads, int cluster, int unroll, cuda
     if (unroll == 2) {
         switch (cluster) {
             case 8: launch_solve_c<8, 2>(a, threads, s); break;
+            case 6: launch_solve_c<6, 2>(a, threads, s); break;
             case 4: launch_solve_c<4, 2>(a, threads, s); break;
+            case 3: launch_solve_c<3, 2>(a, threads, s); break;
             case 2: launch_solve_c<2, 2>(a, threads, s); break;
             default: launch_solve_c<1, 2>(a, threads, s); break;
         }
     } else {
         switch (cluster) {
             case 8: launch_solve_c<8, 1>(a, threads, s); break;
+            case 6: launch_solve_c<6, 1>(a, threads, s); break;
             case 4: launch_solve_c<4, 1>(a, threads, s); break;
+            case 3: launch_solve_c<3, 1>(a, threads, s); break;
             case 2: launch_solve_c<2, 1>(a, threads, s); break;
             default: launch_solve_c<1, 1>(a, threads, s); break;
         }
