@@ -39,11 +39,10 @@ CONTACT_ROW_BYTES = 80   # per constraint per sweep: 56 B record (2 slots, n, t1
 JOINT_ROW_BYTES = 80     # per joint per sweep: 56 B record (2 slots, r_A, r_B, k[3], target[3]) + 24 B lambda r/w
 ENTRY_BYTES = 120        # per (body, worker) per step: 60 B state + params read, 52 B copy write, 8 B index
 PAIR_ONCE_BYTES = 24     # per constraint per step: warm-start lambda read + final lambda write
-# DRAM bytes of one k_solve launch over its algorithmic bytes, from the ncu
-# capture summarised in profiles/k_solve_pile_large.md (k_solve<2,2>, step 151):
-# 2.77 GB of DRAM traffic for ~3.71 GB of algorithmic bytes.  Used to scale the
-# captured traffic to the timed launches; to be re-taken when k_solve changes.
-SOLVE_DRAM_PER_ALGORITHMIC_BYTE = 0.747
+# DRAM bytes of the solve over its algorithmic bytes, from the ncu capture
+# summarised in profiles/k_solve_pile_large.md; None until the current
+# k_solve has been captured (the figure is only valid for the captured code).
+SOLVE_DRAM_PER_ALGORITHMIC_BYTE = None
 
 
 def parse():
@@ -274,7 +273,8 @@ def gpu_arm(args, rank, world, local_rank):
         return
     peak, peak_kind = measured_peaks()
     achieved = bytes_solve / solve_s / 1e9
-    profile_traffic = SOLVE_DRAM_PER_ALGORITHMIC_BYTE * bytes_solve / args.steps if args.workload == "pile_large" else None
+    profile_traffic = (SOLVE_DRAM_PER_ALGORITHMIC_BYTE * bytes_solve / args.steps
+                       if SOLVE_DRAM_PER_ALGORITHMIC_BYTE is not None and args.workload == "pile_large" else None)
     cpu = None
     if not args.no_cpu_baseline:
         r = oracle_run(args.workload, steps=80, warmup=1, max_seconds=15.0)

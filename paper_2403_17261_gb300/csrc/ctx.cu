@@ -242,6 +242,12 @@ void phase_membership(ovl_ctx *c, float dt_override) {
     bool alt = false;
     radix_sort_u32(c->wk.p, c->worker_order.p, c->wk2.p, c->wv2.p, P, 24, c->sort_hist, c->sort_tmp, s, &alt);
     if (alt) std::swap(c->worker_order, c->wv2);
+    // per-worker bodies and constraints on the host, for the launch plans
+    c->h_pb.resize((size_t)P + 1);
+    c->h_pp.resize((size_t)P + 1);
+    download(c->h_pb.data(), c->part_bstart.p, (size_t)P + 1, s);
+    download(c->h_pp.data(), c->part_pstart.p, (size_t)P + 1, s);
+    CK(cudaStreamSynchronize(s));
 }
 
 int colour_smem_capacity(ovl_ctx *c) {
@@ -272,6 +278,125 @@ int solve_slot_capacity(ovl_ctx *c, int ctas_per_sm) {
     return c->P.smem_slot_limit > 0 ? std::min(n, c->P.smem_slot_limit) : n;
 }
 
+// Per-worker CTA counts for the default launch: every worker starts at the
+// fewest CTAs (1, 2, 3, 4, 6 or 8) whose shares of its bodies fit one CTA's
+// shared memory; while all CTAs still fit the SMs, the worker with the most
+// rows per CTA moves to the next count.  Workers with the same count form one launch, and
+// the launches run side by side on the context's streams.  Every launch
+// shape gives the same bits (the solver is built without FMA contraction),
+// so the plan changes only the time.  Returns false when some worker does
+// not fit even 8 CTAs (the uniform launch then takes it to global memory).
+struct SolveClass { int C, first, count, slots; };
+
+// the growth stops at this many CTAs per worker (more only where a
+// worker's bodies need them), and leaves this many SMs unclaimed: clusters
+// must fit inside one GPC, so a launch that claims every SM can leave a
+// cluster waiting for a second wave
+#ifndef OVL_SOLVE_MAX_GROW
+#define OVL_SOLVE_MAX_GROW 4
+#endif
+#ifndef OVL_SOLVE_SM_SLACK
+#define OVL_SOLVE_SM_SLACK 8
+#endif
+
+// CTA shapes of the per-class launches: threads, rows per thread, CTAs per SM
+struct SolveShape { int threads, unroll, per_sm; };
+constexpr SolveShape kSolveShapes[3] = {{512, 2, 1}, {512, 1, 2}, {256, 2, 2}};
+
+// the shape without tuning: one CTA per SM while the workers do not
+// outnumber the SMs, else two smaller CTAs per SM
+int default_solve_shape(const ovl_ctx *c) { return c->n_parts <= c->num_sms ? 0 : 2; }
+
+// Per-worker CTA counts (shared by the colouring and the solve): each worker
+// starts at the fewest CTAs of kClusterSizes whose shares of its bodies fit
+// `cap` slots; while the total stays within `budget` CTAs, the worker with
+// the most constraints per CTA moves to the next size (up to OVL_SOLVE_MAX_GROW
+// unless its bodies need more).  Workers with equal counts form one class,
+// listed by count, then most constraints first; their order goes to `buf`.
+// Returns false if some worker does not fit 8 CTAs.
+bool plan_worker_classes(ovl_ctx *c, int cap, long long budget, std::vector<SolveClass> &classes,
+                         DBuf<uint32_t> &buf) {
+    const int P = c->n_parts;
+    const std::vector<int> &pb = c->h_pb, &pp = c->h_pp;
+    static const int kSizes[] = {1, 2, 3, 4, 6, 8};
+    auto next = [](int k) { for (int x : kSizes) if (x > k) return x; return 0; };
+    std::vector<int> C(P);
+    long long total = 0;
+    for (int p = 0; p < P; ++p) {
+        const int nb = pb[p + 1] - pb[p];
+        int k = 1;
+        while (k && (nb + k - 1) / k > cap) k = next(k);
+        if (!k) return false;
+        C[p] = k;
+        total += k;
+    }
+    auto load = [&](int p) { return (double)(pp[p + 1] - pp[p]) / C[p]; };
+    if (total <= budget) {
+        std::vector<int> heap(P);
+        std::iota(heap.begin(), heap.end(), 0);
+        auto less = [&](int x, int y) { return load(x) < load(y) || (load(x) == load(y) && x > y); };
+        std::make_heap(heap.begin(), heap.end(), less);
+        while (!heap.empty()) {
+            std::pop_heap(heap.begin(), heap.end(), less);
+            const int p = heap.back();
+            const int up = next(C[p]);
+            if (!up || up > OVL_SOLVE_MAX_GROW || total + (up - C[p]) > budget) break;
+            total += up - C[p];
+            C[p] = up;
+            std::push_heap(heap.begin(), heap.end(), less);
+        }
+    }
+    std::vector<int> order(P);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (C[x] != C[y]) return C[x] > C[y];
+        return pp[x + 1] - pp[x] > pp[y + 1] - pp[y];
+    });
+    classes.clear();
+    for (int i = 0; i < P; ++i) {
+        const int p = order[i], nb = pb[p + 1] - pb[p];
+        if (classes.empty() || classes.back().C != C[p]) classes.push_back({C[p], i, 0, 1});
+        SolveClass &k = classes.back();
+        k.count++;
+        k.slots = std::max(k.slots, (nb + C[p] - 1) / C[p]);
+    }
+    std::vector<uint32_t> o(order.begin(), order.end());
+    upload(buf, o.data(), o.size(), c->stream);
+    return true;
+}
+
+bool plan_solve_classes(ovl_ctx *c, const SolveShape &shape, std::vector<SolveClass> &classes) {
+    return plan_worker_classes(c, solve_slot_capacity(c, shape.per_sm),
+                               (long long)shape.per_sm * c->num_sms - OVL_SOLVE_SM_SLACK, classes,
+                               c->class_order);
+}
+
+// launches on the context's stream and its side streams, then joins them
+template <class F>
+void run_on_streams(ovl_ctx *c, size_t n, F &&launch) {
+    CK(cudaEventRecord(c->fork, c->stream));
+    for (size_t k = 0; k < n; ++k) {
+        cudaStream_t sk = k == 0 ? c->stream : c->aux[k - 1];
+        if (k) CK(cudaStreamWaitEvent(sk, c->fork, 0));
+        launch(k, sk);
+    }
+    for (size_t k = 1; k < n; ++k) {
+        CK(cudaEventRecord(c->join[k - 1], c->aux[k - 1]));
+        CK(cudaStreamWaitEvent(c->stream, c->join[k - 1], 0));
+    }
+}
+
+void launch_solve_classes(ovl_ctx *c, const SolveArgs &a, const SolveShape &shape,
+                          const std::vector<SolveClass> &classes) {
+    run_on_streams(c, classes.size(), [&](size_t k, cudaStream_t sk) {
+        SolveArgs b = a;
+        b.n_parts = classes[k].count;
+        b.order = c->class_order.p + classes[k].first;
+        b.smem_slots = classes[k].slots;
+        launch_solve(b, shape.threads, classes[k].C, shape.unroll, sk);
+    });
+}
+
 void phase_colour(ovl_ctx *c) {
     const int P = c->n_parts, npr = c->npairs;
     c->p_colour.ensure(npr + 1);
@@ -290,11 +415,26 @@ void phase_colour(ovl_ctx *c) {
     a.p_key = c->p_key.p; a.p_slot = c->p_slot.p; a.p_colour = c->p_colour.p;
     a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p; a.pair_of_row = c->pair_of_row.p;
     a.part_rounds = c->part_rounds.p;
-    int cluster = 1, slots = 0;
-    colour_config(c, &cluster, &slots);
-    a.scratch = c->colour_scratch.p; a.smem_slots = slots; a.status = c->status.p;
+    a.scratch = c->colour_scratch.p; a.status = c->status.p;
     a.worklist = c->worklist.p; a.worklist2 = c->worklist2.p;
     a.wprio = c->wprio.p; a.wprio2 = c->wprio2.p;
+    const bool fixed = c->P.pgs_cluster > 0 || c->P.smem_slot_limit > 0;
+    std::vector<SolveClass> classes;
+    if (!fixed && P > 0 &&
+        plan_worker_classes(c, colour_smem_capacity(c), (long long)c->num_sms - OVL_SOLVE_SM_SLACK,
+                            classes, c->colour_order)) {
+        run_on_streams(c, classes.size(), [&](size_t k, cudaStream_t sk) {
+            ColourArgs b = a;
+            b.n_parts = classes[k].count;
+            b.order = c->colour_order.p + classes[k].first;
+            b.smem_slots = classes[k].slots;
+            launch_colour(b, classes[k].C, sk);
+        });
+        return;
+    }
+    int cluster = 1, slots = 0;
+    colour_config(c, &cluster, &slots);
+    a.smem_slots = slots;
     launch_colour(a, cluster, c->stream);
 }
 
@@ -370,110 +510,6 @@ SolveArgs solve_args(ovl_ctx *c, float dt_override, int iters) {
     a.res_tol = c->P.res_tol; a.res_check_every = c->P.res_check_every;
     a.part_iters = c->part_iters.p; a.part_res_sq = c->part_res_sq.p; a.status = c->status.p;
     return a;
-}
-
-// Per-worker CTA counts for the default launch: every worker starts at the
-// fewest CTAs (1, 2, 3, 4, 6 or 8) whose shares of its bodies fit one CTA's
-// shared memory; while all CTAs still fit the SMs, the worker with the most
-// rows per CTA moves to the next count.  Workers with the same count form one launch, and
-// the launches run side by side on the context's streams.  Every launch
-// shape gives the same bits (the solver is built without FMA contraction),
-// so the plan changes only the time.  Returns false when some worker does
-// not fit even 8 CTAs (the uniform launch then takes it to global memory).
-struct SolveClass { int C, first, count, slots; };
-
-// the growth stops at this many CTAs per worker (more only where a
-// worker's bodies need them), and leaves this many SMs unclaimed: clusters
-// must fit inside one GPC, so a launch that claims every SM can leave a
-// cluster waiting for a second wave
-#ifndef OVL_SOLVE_MAX_GROW
-#define OVL_SOLVE_MAX_GROW 4
-#endif
-#ifndef OVL_SOLVE_SM_SLACK
-#define OVL_SOLVE_SM_SLACK 8
-#endif
-
-// CTA shapes of the per-class launches: threads, rows per thread, CTAs per SM
-struct SolveShape { int threads, unroll, per_sm; };
-constexpr SolveShape kSolveShapes[3] = {{512, 2, 1}, {512, 1, 2}, {256, 2, 2}};
-
-// the shape without tuning: one CTA per SM while the workers do not
-// outnumber the SMs, else two smaller CTAs per SM
-int default_solve_shape(const ovl_ctx *c) { return c->n_parts <= c->num_sms ? 0 : 2; }
-
-bool plan_solve_classes(ovl_ctx *c, const SolveShape &shape, std::vector<SolveClass> &classes) {
-    const int P = c->n_parts;
-    std::vector<int> pb(P + 1), pp(P + 1);
-    download(pb.data(), c->part_bstart.p, (size_t)P + 1, c->stream);
-    download(pp.data(), c->part_pstart.p, (size_t)P + 1, c->stream);
-    CK(cudaStreamSynchronize(c->stream));
-    const int cap1 = solve_slot_capacity(c, shape.per_sm);
-    static const int kSizes[] = {1, 2, 3, 4, 6, 8};
-    auto next = [](int k) { for (int x : kSizes) if (x > k) return x; return 0; };
-    std::vector<int> C(P);
-    long long total = 0;
-    for (int p = 0; p < P; ++p) {
-        const int nb = pb[p + 1] - pb[p];
-        int k = 1;
-        while (k && (nb + k - 1) / k > cap1) k = next(k);
-        if (!k) return false;
-        C[p] = k;
-        total += k;
-    }
-    // rows per CTA, the solve time of a worker up to a constant
-    auto load = [&](int p) { return (double)(pp[p + 1] - pp[p]) / C[p]; };
-    const long long budget = (long long)shape.per_sm * c->num_sms - OVL_SOLVE_SM_SLACK;
-    if (total <= budget) {
-        std::vector<int> heap(P);
-        std::iota(heap.begin(), heap.end(), 0);
-        auto less = [&](int x, int y) { return load(x) < load(y) || (load(x) == load(y) && x > y); };
-        std::make_heap(heap.begin(), heap.end(), less);
-        while (!heap.empty()) {
-            std::pop_heap(heap.begin(), heap.end(), less);
-            const int p = heap.back();
-            const int up = next(C[p]);
-            if (!up || up > OVL_SOLVE_MAX_GROW || total + (up - C[p]) > budget) break;
-            total += up - C[p];
-            C[p] = up;
-            std::push_heap(heap.begin(), heap.end(), less);
-        }
-    }
-    // launch order: by CTA count, then most rows first
-    std::vector<int> order(P);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        if (C[x] != C[y]) return C[x] > C[y];
-        return pp[x + 1] - pp[x] > pp[y + 1] - pp[y];
-    });
-    classes.clear();
-    for (int i = 0; i < P; ++i) {
-        const int p = order[i], nb = pb[p + 1] - pb[p];
-        if (classes.empty() || classes.back().C != C[p]) classes.push_back({C[p], i, 0, 1});
-        SolveClass &k = classes.back();
-        k.count++;
-        k.slots = std::max(k.slots, (nb + C[p] - 1) / C[p]);
-    }
-    std::vector<uint32_t> o(order.begin(), order.end());
-    upload(c->class_order, o.data(), o.size(), c->stream);
-    return true;
-}
-
-void launch_solve_classes(ovl_ctx *c, const SolveArgs &a, const SolveShape &shape,
-                          const std::vector<SolveClass> &classes) {
-    CK(cudaEventRecord(c->fork, c->stream));
-    for (size_t k = 0; k < classes.size(); ++k) {
-        cudaStream_t sk = k == 0 ? c->stream : c->aux[k - 1];
-        if (k) CK(cudaStreamWaitEvent(sk, c->fork, 0));
-        SolveArgs b = a;
-        b.n_parts = classes[k].count;
-        b.order = c->class_order.p + classes[k].first;
-        b.smem_slots = classes[k].slots;
-        launch_solve(b, shape.threads, classes[k].C, shape.unroll, sk);
-    }
-    for (size_t k = 1; k < classes.size(); ++k) {
-        CK(cudaEventRecord(c->join[k - 1], c->aux[k - 1]));
-        CK(cudaStreamWaitEvent(c->stream, c->join[k - 1], 0));
-    }
 }
 
 // problem-size bucket of the autotuner: the number of workers and the largest
@@ -759,7 +795,7 @@ void release_all(ovl_ctx *c) {
     c->sort_hist.release(); c->sort_tmp.release();
     c->lb_flag.release(); c->lb_pos.release(); c->lb_pairs.release();
     c->worker_order.release(); c->wk.release(); c->wk2.release(); c->wv2.release();
-    c->class_order.release(); c->lb_loads.release();
+    c->class_order.release(); c->colour_order.release(); c->lb_loads.release();
 }
 
 

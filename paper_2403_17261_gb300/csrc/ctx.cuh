@@ -88,7 +88,8 @@ struct ovl_ctx {
     DBuf<int> lb_flag, lb_pos;
     DBuf<int2> lb_pairs;
     DBuf<uint32_t> worker_order, wk, wk2, wv2;   // workers longest first (launch order)
-    DBuf<uint32_t> class_order;                  // solve: workers grouped by CTAs per worker
+    DBuf<uint32_t> class_order, colour_order;    // solve / colouring: workers grouped by CTAs per worker
+    std::vector<int> h_pb, h_pp;                 // part_bstart, part_pstart of this step on the host
     cudaStream_t aux[5] = {};                    // side streams of the per-class solve launches
     cudaEvent_t fork = nullptr, join[5] = {};
     int lb_threads = 1;            // host threads of the load balance (scenes run in parallel)

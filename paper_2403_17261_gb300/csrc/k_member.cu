@@ -587,7 +587,9 @@ void launch_colour(const ColourArgs &a, int cluster, cudaStream_t s) {
     if (!a.n_parts) return;
     switch (cluster) {
         case 8: launch_colour_c<8>(a, s); break;
+        case 6: launch_colour_c<6>(a, s); break;
         case 4: launch_colour_c<4>(a, s); break;
+        case 3: launch_colour_c<3>(a, s); break;
         case 2: launch_colour_c<2>(a, s); break;
         default: launch_colour_c<1>(a, s); break;
     }
