@@ -40,9 +40,11 @@ JOINT_ROW_BYTES = 80     # per joint per sweep: 56 B record (2 slots, r_A, r_B, 
 ENTRY_BYTES = 120        # per (body, worker) per step: 60 B state + params read, 52 B copy write, 8 B index
 PAIR_ONCE_BYTES = 24     # per constraint per step: warm-start lambda read + final lambda write
 # DRAM bytes of the solve over its algorithmic bytes, from the ncu capture
-# summarised in profiles/k_solve_pile_large.md; None until the current
-# k_solve has been captured (the figure is only valid for the captured code).
-SOLVE_DRAM_PER_ALGORITHMIC_BYTE = None
+# summarised in profiles/k_solve_pile_large.md (all four per-class launches of
+# the first timed step: 0.675 GB of DRAM traffic for 3.74 GB of algorithmic
+# bytes; the row records stay in L2 across sweeps).  Valid for the captured
+# kernel only: set to None when k_solve changes, until it is captured again.
+SOLVE_DRAM_PER_ALGORITHMIC_BYTE = 0.18
 
 
 def parse():
@@ -202,10 +204,15 @@ def gpu_arm(args, rank, world, local_rank):
     params = dict(flags=ovl.OVL_FLAG_TIMING)
     sim = ovl.Simulation(sc, params, stream=stream.cuda_stream)
     settle = default_settle(args.workload) if args.settle is None else args.settle
+    # NVTX ranges let a profiler select the timed steps (ncu --nvtx --nvtx-include "timed/")
+    torch.cuda.nvtx.range_push("settle")
     for _ in range(settle):
         sim.step()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("warmup")
     for _ in range(args.warmup):
         sim.step()
+    torch.cuda.nvtx.range_pop()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -217,6 +224,7 @@ def gpu_arm(args, rank, world, local_rank):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     solve_ms, rows_iters, bytes_solve, launches = [], 0, 0.0, []
     barrier()
+    torch.cuda.nvtx.range_push("timed")
     with ClockSampler(local_rank) as clk:
         for k in range(args.steps):
             with torch.cuda.stream(stream):
@@ -233,6 +241,8 @@ def gpu_arm(args, rank, world, local_rank):
             bytes_solve += (sc.iters * CONTACT_ROW_BYTES * n_cons + PAIR_ONCE_BYTES * n_cons
                             + ENTRY_BYTES * st["n_entries"])
         barrier()
+    torch.cuda.nvtx.range_pop()
+    free_b, total_b = torch.cuda.mem_get_info()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_local = sum(step_ms) / 1e3
     t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
@@ -301,6 +311,7 @@ def gpu_arm(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(sum(launches)),
+        "device_memory_used_gb": round((total_b - free_b) / 1e9, 3),
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
