@@ -83,6 +83,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The largest of the ranks' values (their step times); every rank gets it."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, steps: int, t_max: float) -> float:
+    """Units processed by all ranks per second of the slowest rank (weak scaling)."""
+    return world * units_per_rank * steps / t_max
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons every 200 ms while running."""
 
@@ -244,12 +259,8 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.nvtx.range_pop()
     free_b, total_b = torch.cuda.mem_get_info()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_local = sum(step_ms) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
-    value = world * sc.n_bodies * args.steps / t_max
+    t_max = max_over_ranks(sum(step_ms) / 1e3, world)
+    value = whole_job_rate(world, sc.n_bodies, args.steps, t_max)
     solve_s = sum(solve_ms) / 1e3
     last = sim.stats()
 
@@ -271,12 +282,9 @@ def gpu_arm(args, rank, world, local_rank):
             host_in, host_out = host_out, host_in
         e_e.record(stream)
         barrier()
-        te = e_s.elapsed_time(e_e) / 1e3
-        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = max_over_ranks(e_s.elapsed_time(e_e) / 1e3, world)
         nbytes = sc.n_bodies * 13 * 4
-        e2e = {"value": world * sc.n_bodies * n_e2e / float(tt.item()), "unit": "body-steps/s",
+        e2e = {"value": whole_job_rate(world, sc.n_bodies, n_e2e, te), "unit": "body-steps/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": n_e2e}
 
     if rank != 0:

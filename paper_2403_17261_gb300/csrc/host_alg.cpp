@@ -38,6 +38,7 @@ class Membership {
         }
     }
     uint64_t W(int b) const { return mask_[b]; }
+    const uint64_t *mask_ptr() const { return mask_; }
     void activate(uint64_t workers, int b) {
         uint64_t add = workers & ~mask_[b];
         int base = sc_.part_base[sc_.sob[b]];
@@ -185,7 +186,16 @@ void load_balance_range(const HostScene &sc, Membership &mem, const int2 *ab, in
         for (int k = row_ptr[b]; k < row_ptr[b + 1]; ++k) u |= mem.W(col[k]);
         return popcount(u) > 1;
     };
+    constexpr int64_t kAhead = 16;   // candidates between a prefetch and its use
     for (int64_t i = i0; i < i1; ++i) {
+        if (i + kAhead < i1) {
+            // the second body of a contact is a random index: fetch its mask
+            // and adjacency range while earlier candidates are processed
+            const int Bn = ab[i + kAhead].y;
+            __builtin_prefetch(mem.mask_ptr() + Bn);
+            __builtin_prefetch(row_ptr + Bn);
+            __builtin_prefetch(sc.sob.data() + ab[i + kAhead].x);
+        }
         const int A = ab[i].x, B = ab[i].y;
         const uint64_t WA = mem.W(A), WB = mem.W(B);
         const int scene = sc.sob[A];
