@@ -123,6 +123,8 @@ struct ovl_ctx {
     DBuf<float> train_act, train_sample_loss, train_partials, train_loss_hist, infer_y;
     DBuf<float4> infer_feat;
     DBuf<double> loss_acc;
+    DBuf<float> train_c12;            // Adam bias corrections per step of a training call
+    DBuf<long long> train_step;       // step counter of a training call (graph replay)
 };
 
 namespace ovl {

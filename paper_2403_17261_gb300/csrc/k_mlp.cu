@@ -310,9 +310,9 @@ constexpr int TRAIN_THREADS = 256;
 constexpr int WGRAD_THREADS = 256, WGRAD_CHUNK = 128, WGRAD_TILE = 32;
 constexpr int WGRAD_PER_THREAD = (MLP_N_PARAMS + 1 + WGRAD_THREADS - 1) / WGRAD_THREADS;
 
-__device__ __forceinline__ long long sample_row(const TrainArgs &a, int j) {
-    if (a.sampling == 0) return a.first + (long long)(((unsigned long long)a.step * a.batch + j) % (unsigned long long)a.count);
-    const uint64_t z = mix64(a.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(a.step * (long long)a.batch + j + 1));
+__device__ __forceinline__ long long sample_row(const TrainArgs &a, long long step, int j) {
+    if (a.sampling == 0) return a.first + (long long)(((unsigned long long)step * a.batch + j) % (unsigned long long)a.count);
+    const uint64_t z = mix64(a.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(step * (long long)a.batch + j + 1));
     return a.first + (long long)(z % (uint64_t)a.count);
 }
 
@@ -340,8 +340,9 @@ __global__ void __launch_bounds__(TRAIN_THREADS) k_train_fwd(TrainArgs a) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     const unsigned full = 0xffffffffu;
+    const long long step = a.step_dev ? *a.step_dev : a.step;
     for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < a.batch; j += warps) {
-        const long long r = sample_row(a, j);
+        const long long r = sample_row(a, step, j);
         const float xraw = lane < 12 ? a.log_feat[12 * r + lane] : 0.f;
         const float xv = bf16r(xraw);
         float z1a = W[OFF_B1 + lane], z1b = W[OFF_B1 + lane + 32];
@@ -488,6 +489,30 @@ __global__ void k_train_reduce(const float *partials, int blocks, int batch, flo
     theta[p] -= lr * (mm * c1) / (sqrtf(vv * c2) + eps);
 }
 
+// the reduce of one Adam step with its step number read from device memory
+__global__ void k_train_reduce_dev(const float *partials, int blocks, int batch, float *loss_hist,
+                                   float *theta, float *m, float *v, float lr, float beta1,
+                                   float beta2, float eps, const float *c12,
+                                   const long long *step_dev) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > MLP_N_PARAMS) return;
+    const long long t = *step_dev;
+    float g = 0.f;
+    for (int b = 0; b < blocks; ++b) g += partials[(size_t)b * (MLP_N_PARAMS + 1) + p];
+    if (p == MLP_N_PARAMS) {
+        loss_hist[t] = g / (3.f * (float)batch);
+        return;
+    }
+    const float mm = beta1 * m[p] + (1.f - beta1) * g;
+    const float vv = beta2 * v[p] + (1.f - beta2) * g * g;
+    m[p] = mm;
+    v[p] = vv;
+    theta[p] -= lr * (mm * c12[2 * t]) / (sqrtf(vv * c12[2 * t + 1]) + eps);
+}
+
+// after every block of the reduce has read it
+__global__ void k_step_advance(long long *step_dev) { *step_dev += 1; }
+
 __global__ void k_loss_sum(const float *sample_loss, int n, double *acc) {
     __shared__ double part[256];
     double s = 0.0;
@@ -572,6 +597,17 @@ void launch_train_reduce(const float *partials, int blocks, int batch, float *gr
                          float beta1, float beta2, float eps, float c1, float c2, cudaStream_t s) {
     k_train_reduce<<<(MLP_N_PARAMS + 1 + 255) / 256, 256, 0, s>>>(
         partials, blocks, batch, grad_out, loss_out, adam, theta, m, v, lr, beta1, beta2, eps, c1, c2);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_train_reduce_dev(const float *partials, int blocks, int batch, float *loss_hist,
+                             float *theta, float *m, float *v, float lr, float beta1, float beta2,
+                             float eps, const float *c12, long long *step_dev, cudaStream_t s) {
+    k_train_reduce_dev<<<(MLP_N_PARAMS + 1 + 255) / 256, 256, 0, s>>>(
+        partials, blocks, batch, loss_hist, theta, m, v, lr, beta1, beta2, eps, c12, step_dev);
+    note_launch();
+    k_step_advance<<<1, 1, 0, s>>>(step_dev);
     note_launch();
     CK(cudaGetLastError());
 }

@@ -267,6 +267,7 @@ struct TrainArgs {
     int sampling;                       // 0 contiguous, 1 uniform with replacement
     unsigned long long seed;
     long long step;                     // Adam step within the call (sampling)
+    const long long *step_dev;          // if set: the step counter in device memory (graph replay)
     int backward;                       // 0: loss only
     const float *theta;                 // FP32 master parameters
     float *act;                         // [batch][MLP_ACT_STRIDE]
@@ -281,6 +282,11 @@ void launch_train_wgrad(const TrainArgs &a, cudaStream_t s);
 void launch_train_reduce(const float *partials, int blocks, int batch, float *grad_out,
                          float *loss_out, int adam, float *theta, float *m, float *v, float lr,
                          float beta1, float beta2, float eps, float c1, float c2, cudaStream_t s);
+// the same with the step taken from step_dev: loss to loss_hist[step], bias
+// corrections from c12[2 step], c12[2 step + 1]; then step_dev += 1
+void launch_train_reduce_dev(const float *partials, int blocks, int batch, float *loss_hist,
+                             float *theta, float *m, float *v, float lr, float beta1, float beta2,
+                             float eps, const float *c12, long long *step_dev, cudaStream_t s);
 void launch_loss_sum(const float *sample_loss, int n, double *acc, cudaStream_t s);
 
 }  // namespace ovl

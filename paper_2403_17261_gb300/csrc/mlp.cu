@@ -95,6 +95,7 @@ void release_mlp(ovl_ctx *c) {
     c->mlp_loss.release(); c->mlp_packed.release(); c->log_feat.release(); c->log_targ.release();
     c->train_act.release(); c->train_sample_loss.release(); c->train_partials.release();
     c->train_loss_hist.release(); c->infer_y.release(); c->infer_feat.release(); c->loss_acc.release();
+    c->train_c12.release(); c->train_step.release();
 }
 
 }  // namespace ovl
@@ -245,18 +246,58 @@ ovl_status ovl_mlp_train(ovl_ctx *c, const ovl_train_desc *d, float *loss_per_st
         const float eps = d->eps > 0.f ? d->eps : 1e-8f;
         if (b1 >= 1.f || b2 >= 1.f) return fail(c, OVL_ERR_ARG, "Adam betas must be below 1");
         ensure_train_buffers(c, d->batch);
-        c->train_loss_hist.ensure((size_t)d->steps + 1);
-        const int blocks = train_wgrad_blocks(d->batch);
-        for (int t = 0; t < d->steps; ++t) {
-            ++c->adam_t;
-            const float c1 = (float)(1.0 / (1.0 - std::pow((double)b1, (double)c->adam_t)));
-            const float c2 = (float)(1.0 / (1.0 - std::pow((double)b2, (double)c->adam_t)));
-            TrainArgs a = train_args(c, d->first, d->count, d->batch, d->sampling, d->seed, t, 1);
-            launch_train_fwd(a, c->stream);
-            launch_train_wgrad(a, c->stream);
-            launch_train_reduce(c->train_partials.p, blocks, d->batch, nullptr, c->train_loss_hist.p + t, 1,
-                                c->mlp_theta.p, c->mlp_m.p, c->mlp_v.p, lr, b1, b2, eps, c1, c2, c->stream);
+        const int steps = d->steps;
+        c->train_loss_hist.ensure((size_t)steps + 1);
+        // Adam's bias corrections of every step of the call, and the step
+        // counter, live in device memory, so every step launches the same
+        // kernels with the same arguments: a block of steps is captured once
+        // as a CUDA graph and replayed
+        std::vector<float> c12(2 * (size_t)steps + 2);
+        for (int t = 0; t < steps; ++t) {
+            const double k = (double)(c->adam_t + 1 + t);
+            c12[2 * t] = (float)(1.0 / (1.0 - std::pow((double)b1, k)));
+            c12[2 * t + 1] = (float)(1.0 / (1.0 - std::pow((double)b2, k)));
         }
+        upload(c->train_c12, c12.data(), c12.size(), c->stream);
+        c->train_step.ensure(1);
+        CK(cudaMemsetAsync(c->train_step.p, 0, sizeof(long long), c->stream));
+        const int blocks = train_wgrad_blocks(d->batch);
+        TrainArgs a = train_args(c, d->first, d->count, d->batch, d->sampling, d->seed, 0, 1);
+        a.step_dev = c->train_step.p;
+        auto one_step = [&](cudaStream_t st) {
+            launch_train_fwd(a, st);
+            launch_train_wgrad(a, st);
+            launch_train_reduce_dev(c->train_partials.p, blocks, d->batch, c->train_loss_hist.p,
+                                    c->mlp_theta.p, c->mlp_m.p, c->mlp_v.p, lr, b1, b2, eps,
+                                    c->train_c12.p, c->train_step.p, st);
+        };
+        constexpr int kGraphSteps = 50;
+        int done = 0;
+        if (steps >= 2 * kGraphSteps) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            try {
+                for (int t = 0; t < kGraphSteps; ++t) one_step(c->stream);
+            } catch (...) {
+                cudaGraph_t partial = nullptr;
+                cudaStreamEndCapture(c->stream, &partial);   // leave the stream usable
+                if (partial) cudaGraphDestroy(partial);
+                throw;
+            }
+            CK(cudaStreamEndCapture(c->stream, &g));
+            cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            CK(e);
+            for (; done + kGraphSteps <= steps; done += kGraphSteps) {
+                e = cudaGraphLaunch(ge, c->stream);
+                if (e != cudaSuccess) break;
+            }
+            cudaGraphExecDestroy(ge);
+            CK(e);
+        }
+        for (; done < steps; ++done) one_step(c->stream);
+        c->adam_t += steps;
         launch_mlp_pack(c->mlp_theta.p, c->mlp_packed.p, c->stream);
         if (loss_per_step && d->steps > 0) download(loss_per_step, c->train_loss_hist.p, (size_t)d->steps, c->stream);
         CK(cudaStreamSynchronize(c->stream));

@@ -151,6 +151,28 @@ def test_adam_first_step_and_training():
         sim.close()
 
 
+def test_graph_replayed_training_matches_single_steps():
+    """Calls of 100 or more Adam steps replay a captured CUDA graph of 50
+    steps; with every row in every batch, that must equal 100 calls of one
+    step launched directly, bit for bit."""
+    th = S.mlp_init_params(29, bias_scale=0.2)
+    X, T = S.synthetic_rows(2048, seed=30)
+    sims = [_sim_with_params(th), _sim_with_params(th)]
+    try:
+        for sim in sims:
+            sim.log_reserve(2048)
+            sim.log_append(X, T)
+        h_graph = sims[0].mlp_train(0, 2048, batch=2048, steps=120, sampling=0, lr=1e-3)
+        h_single = np.concatenate([sims[1].mlp_train(0, 2048, batch=2048, steps=1, sampling=0, lr=1e-3)
+                                   for _ in range(120)])
+        np.testing.assert_array_equal(sims[0].mlp_params(), sims[1].mlp_params())
+        np.testing.assert_array_equal(h_graph, h_single)
+        assert h_graph[-1] < h_graph[0]
+    finally:
+        for sim in sims:
+            sim.close()
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_mlp_warm_start_in_a_step(mode):
     from paper_2403_17261_gb300 import ovl
