@@ -235,6 +235,9 @@ def gpu_arm(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # the end-to-end run below replays the same steps from this snapshot
+    snapshot = None if args.no_e2e else (sim.state(), sim.membership(), sim.warmstart(),
+                                         sim.step_index_value())
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     solve_ms, rows_iters, bytes_solve, launches = [], 0, 0.0, []
@@ -264,15 +267,19 @@ def gpu_arm(args, rank, world, local_rank):
     solve_s = sum(solve_ms) / 1e3
     last = sim.stats()
 
-    # end to end through the C ABI with host buffers: pinned state in, state out
+    # end to end through the C ABI with host buffers, over the same steps as
+    # the timed run (restored from the snapshot): pinned state in, state out
     e2e = None
     if not args.no_e2e:
         host_in = torch.empty((sc.n_bodies, 13), dtype=torch.float32, pin_memory=True).numpy()
         host_out = torch.empty((sc.n_bodies, 13), dtype=torch.float32, pin_memory=True).numpy()
-        sim.state(out=host_in)
+        host_in[:] = snapshot[0]
+        sim.set_membership(snapshot[1])
+        sim.set_warmstart(*snapshot[2])
+        sim.set_step_index(snapshot[3])
         e_s = torch.cuda.Event(enable_timing=True)
         e_e = torch.cuda.Event(enable_timing=True)
-        n_e2e = max(3, args.steps // 2)
+        n_e2e = args.steps
         barrier()
         e_s.record(stream)
         for _ in range(n_e2e):
