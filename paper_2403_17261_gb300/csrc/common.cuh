@@ -84,6 +84,7 @@ struct HBuf {
 
 // kernel launches issued by this library (counted by every launcher)
 void note_launch();
+void note_launches(long long k);   // k kernels of a graph replay
 long long launch_count();
 
 // ---------------------------------------------------------------------------

@@ -618,15 +618,13 @@ void phase_solve(ovl_ctx *c, float dt_override, int iters) {
     launch_solve(a, threads, cluster, unroll, c->stream);
 }
 
-void phase_geodesics(ovl_ctx *c) {
-    cudaStream_t s = c->stream;
-    c->D.ensure(c->ne + 1);
-    c->visited.ensure((size_t)((c->vb_bits + 31) / 32) + 1);
-    c->queue.ensure((size_t)c->vb_bits + 1);
-    c->qctl.ensure((size_t)c->beta_max + 4);
+// The geodesic phase is 2 beta + 4 small launches whose arguments change only
+// when a buffer is reallocated or the entry count changes, so it is captured
+// once as a CUDA graph and replayed while they stay the same.
+void enqueue_geodesics(ovl_ctx *c, cudaStream_t s) {
     CK(cudaMemsetAsync(c->visited.p, 0, sizeof(uint32_t) * ((size_t)((c->vb_bits + 31) / 32) + 1), s));
     CK(cudaMemsetAsync(c->qctl.p, 0, sizeof(int) * ((size_t)c->beta_max + 4), s));
-    fill_u8(c->D.p, 255, c->ne, s);
+    fill_u8(c->D.p, 255, c->D.cap, s);   // the whole buffer: the graph then outlives entry counts
     GeoArgs a{};
     a.n = c->n; a.mask = c->mask.p; a.sob = c->sob.p; a.scene_beta = c->scene_beta.p;
     a.body_base = c->body_base.p; a.vb_base = c->vb_base.p; a.row_ptr = c->row_ptr.p; a.col = c->col.p;
@@ -634,6 +632,42 @@ void phase_geodesics(ovl_ctx *c) {
     a.D = c->D.p;
     launch_geo_sources(a, s);
     for (int L = 1; L <= c->beta_max; ++L) launch_geo_level(a, L, s);
+}
+
+void phase_geodesics(ovl_ctx *c) {
+    cudaStream_t s = c->stream;
+    c->D.ensure(c->ne + 1);
+    c->visited.ensure((size_t)((c->vb_bits + 31) / 32) + 1);
+    c->queue.ensure((size_t)c->vb_bits + 1);
+    c->qctl.ensure((size_t)c->beta_max + 4);
+    const std::vector<const void *> key = {
+        c->D.p, c->visited.p, c->queue.p, c->qctl.p, c->mask.p, c->row_ptr.p, c->col.p,
+        c->entry_ptr.p, c->sob.p, c->scene_beta.p, c->body_base.p, c->vb_base.p,
+        (const void *)(intptr_t)c->D.cap, (const void *)(intptr_t)c->n, (const void *)(intptr_t)c->beta_max,
+        (const void *)(intptr_t)c->vb_bits};
+    if (!c->geo_exec || key != c->geo_key) {
+        if (c->geo_exec) { cudaGraphExecDestroy(c->geo_exec); c->geo_exec = nullptr; }
+        const long long l0 = launch_count();
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        try {
+            enqueue_geodesics(c, s);
+        } catch (...) {
+            cudaGraph_t partial = nullptr;
+            cudaStreamEndCapture(s, &partial);   // leave the stream usable
+            if (partial) cudaGraphDestroy(partial);
+            throw;
+        }
+        CK(cudaStreamEndCapture(s, &g));
+        cudaError_t e = cudaGraphInstantiate(&c->geo_exec, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        c->geo_key = key;
+        c->geo_kernels = launch_count() - l0;
+        note_launches(-c->geo_kernels);   // counted when replayed below
+    }
+    CK(cudaGraphLaunch(c->geo_exec, s));
+    note_launches(c->geo_kernels);
 }
 
 void phase_blend(ovl_ctx *c, float dt_override) {
@@ -836,6 +870,7 @@ ovl_status ovl_destroy(ovl_ctx *c) {
     for (auto &x : c->aux)
         if (x) { cudaStreamSynchronize(x); cudaStreamDestroy(x); }
     if (c->fork) cudaEventDestroy(c->fork);
+    if (c->geo_exec) cudaGraphExecDestroy(c->geo_exec);
     for (auto &e : c->join)
         if (e) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -92,6 +92,9 @@ struct ovl_ctx {
     std::vector<int> h_pb, h_pp;                 // part_bstart, part_pstart of this step on the host
     cudaStream_t aux[5] = {};                    // side streams of the per-class solve launches
     cudaEvent_t fork = nullptr, join[5] = {};
+    cudaGraphExec_t geo_exec = nullptr;          // the geodesic phase, captured
+    std::vector<const void *> geo_key;           // its arguments when captured
+    long long geo_kernels = 0;
     int lb_threads = 1;            // host threads of the load balance (scenes run in parallel)
     std::vector<BallWorkspace> lb_ws;
     DBuf<int> lb_loads;
