@@ -273,7 +273,8 @@ void colour_config(ovl_ctx *c, int *cluster, int *slots) {
 
 // Shared-memory body slots per CTA (24 B each) for 1 or 2 resident CTAs per SM
 int solve_slot_capacity(ovl_ctx *c, int ctas_per_sm) {
-    int avail = ctas_per_sm == 1 ? c->smem_optin - 1024 : (c->smem_per_sm / 2) - 2048;
+    // the solver's static shared memory (row-bucket offsets, reductions) is under 1 KB
+    int avail = ctas_per_sm == 1 ? c->smem_optin - 2 * 1024 : (c->smem_per_sm / 2) - 3 * 1024;
     int n = std::max(0, avail / 24);
     return c->P.smem_slot_limit > 0 ? std::min(n, c->P.smem_slot_limit) : n;
 }
@@ -362,6 +363,7 @@ bool plan_worker_classes(ovl_ctx *c, int cap, long long budget, std::vector<Solv
     }
     std::vector<uint32_t> o(order.begin(), order.end());
     upload(buf, o.data(), o.size(), c->stream);
+    c->h_class_C.assign(C.begin(), C.end());
     return true;
 }
 
@@ -443,7 +445,7 @@ void phase_rows(ovl_ctx *c, float dt_override) {
     c->r0.ensure(npr + 1); c->r1.ensure(npr + 1); c->r2.ensure(npr + 1); c->r3.ensure(npr + 1);
     c->rpair.ensure(npr + 1); c->rlam.ensure(npr + 1);
     RowArgs a{};
-    a.n = c->n; a.nc = c->nc; a.np = npr; a.pair_of_row = c->pair_of_row.p; a.ps_cons = c->ps_cons.p;
+    a.n = c->n; a.nc = c->nc; a.np = npr; a.pair_of_row = c->pair_of_row2.p; a.ps_cons = c->ps_cons.p;
     a.ps_part = c->ps_part.p; a.p_slot = c->p_slot.p; a.p_lam0 = c->p_lam0.p; a.c_ab = c->c_ab.p;
     a.c_n = c->c_n.p; a.c_t1 = c->c_t1.p; a.jab = c->jab.p; a.janc = c->janc.p;
     a.joint_scene = c->joint_scene.p; a.st = c->st.p; a.sob = c->sob.p; a.part_scene = c->part_scene.p;
@@ -500,7 +502,7 @@ SolveArgs solve_args(ovl_ctx *c, float dt_override, int iters) {
     SolveArgs a{};
     a.n_parts = c->n_parts; a.part_bstart = c->part_bstart.p; a.part_list = c->part_list.p;
     a.order = c->worker_order.p;
-    a.entry_body = c->entry_body.p; a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p;
+    a.entry_body = c->entry_body.p; a.part_ncol = c->part_ncol.p; a.col_off = c->col_off2.p;
     a.part_scene = c->part_scene.p; a.scene_dt = c->scene_dt.p; a.dt_override = dt_override;
     a.gravity = make_float3(c->P.gravity[0], c->P.gravity[1], c->P.gravity[2]);
     a.st = c->st.p; a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
@@ -534,44 +536,30 @@ int solve_slots_for(ovl_ctx *c, int cluster) {
 // step's rows and keep the fastest for the bucket.
 // Rows of one colour are independent, so every candidate computes the same
 // bits; re-running the row build restores the warm-start impulses.
-void autotune(ovl_ctx *c, float dt_override, int iters, const std::string &key) {
-    cudaStream_t s = c->stream;
-    ovl_ctx::TuneCfg best{0, 0, 0, 1e30f, 0};
-    cudaEvent_t e0 = c->ev[10], e1 = c->ev[11];
-    for (int cl : {1, 2, 4, 8})
-        for (int th : {256, 512})
-            for (int un : {1, 2}) {
-                int slots = solve_slots_for(c, cl);
-                if (!slots) continue;
-                SolveArgs a = solve_args(c, dt_override, iters);
-                a.smem_slots = slots;
-                phase_rows(c, dt_override);
-                CK(cudaEventRecord(e0, s));
-                launch_solve(a, th, cl, un, s);
-                CK(cudaEventRecord(e1, s));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best.ms) best = {cl, th, un, ms, 0};
-            }
-    for (int sh = 0; sh < 3; ++sh) {
-        std::vector<SolveClass> classes;
-        if (!plan_solve_classes(c, kSolveShapes[sh], classes)) continue;
-        SolveArgs a = solve_args(c, dt_override, iters);
-        phase_rows(c, dt_override);
-        CK(cudaEventRecord(e0, s));
-        launch_solve_classes(c, a, kSolveShapes[sh], classes);
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best.ms) best = {0, kSolveShapes[sh].threads, kSolveShapes[sh].unroll, ms, sh + 1};
-    }
-    if (best.cluster || best.shape) c->tuned[key] = best;
-    phase_rows(c, dt_override);   // fresh impulses for the real solve
+// How this step's solve is launched: per-worker classes (shape >= 0) or one
+// uniform launch.
+struct SolvePlan {
+    int shape = -1;
+    std::vector<SolveClass> classes;
+    int cluster = 1, threads = 512, unroll = 1, slots = 0;
+};
+
+// Every worker's CTA count goes to the device and the rows of every colour
+// are regrouped by the CTA that owns them (it holds the row's first dynamic
+// body); the row build then follows that order.
+void apply_solve_order(ovl_ctx *c, const SolvePlan &pl) {
+    const int P = c->n_parts;
+    std::vector<int> C(P, pl.cluster);
+    if (pl.shape >= 0) C = c->h_class_C;
+    upload(c->solve_C, C.data(), (size_t)P, c->stream);
+    c->col_off2.ensure((size_t)P * OWNER_NB + 1);
+    c->pair_of_row2.ensure((size_t)c->npairs + 1);
+    c->row_owner.ensure((size_t)c->npairs + 1);
+    launch_row_owner(P, c->part_bstart.p, c->part_ncol.p, c->solve_C.p, c->col_off.p, c->pair_of_row.p,
+                     c->p_slot.p, c->row_owner.p, c->pair_of_row2.p, c->col_off2.p, c->stream);
 }
 
-void phase_solve(ovl_ctx *c, float dt_override, int iters) {
+void launch_solve_plan(ovl_ctx *c, const SolvePlan &pl, float dt_override, int iters) {
     const int P = c->n_parts, npr = c->npairs;
     c->lam_out.ensure(npr + 1);
     c->copies.ensure(4 * (size_t)c->ne + 1);
@@ -579,9 +567,71 @@ void phase_solve(ovl_ctx *c, float dt_override, int iters) {
     c->part_iters.ensure((size_t)P + 1);
     c->part_res_sq.ensure((size_t)P + 1);
     CK(cudaMemsetAsync(c->part_res_sq.p, 0, sizeof(double) * ((size_t)P + 1), c->stream));
+    SolveArgs a = solve_args(c, dt_override, iters);
+    if (pl.shape >= 0) {
+        launch_solve_classes(c, a, kSolveShapes[pl.shape], pl.classes);
+        c->last_cluster = pl.classes.front().C;
+        c->last_threads = kSolveShapes[pl.shape].threads;
+        c->last_unroll = kSolveShapes[pl.shape].unroll;
+        return;
+    }
+    a.smem_slots = pl.slots;
+    launch_solve(a, pl.threads, pl.cluster, pl.unroll, c->stream);
+    c->last_cluster = pl.cluster;
+    c->last_threads = pl.threads;
+    c->last_unroll = pl.unroll;
+}
+
+// K13: time every feasible uniform launch (CTAs per worker, threads per CTA,
+// rows per thread and colour step) and every per-worker plan shape on this
+// step's rows and keep the fastest for the bucket.  Rows of one colour are
+// independent, so every candidate computes the same bits; rebuilding the
+// rows restores the warm-start impulses.
+void autotune(ovl_ctx *c, float dt_override, int iters, const std::string &key) {
+    cudaStream_t s = c->stream;
+    ovl_ctx::TuneCfg best{0, 0, 0, 1e30f, 0};
+    cudaEvent_t e0 = c->ev[10], e1 = c->ev[11];
+    auto time_plan = [&](const SolvePlan &pl) {
+        apply_solve_order(c, pl);
+        phase_rows(c, dt_override);
+        CK(cudaEventRecord(e0, s));
+        launch_solve_plan(c, pl, dt_override, iters);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        return ms;
+    };
+    for (int cl : {1, 2, 4, 8})
+        for (int th : {256, 512})
+            for (int un : {1, 2}) {
+                SolvePlan pl;
+                pl.cluster = cl; pl.threads = th; pl.unroll = un;
+                pl.slots = solve_slots_for(c, cl);
+                if (!pl.slots) continue;
+                const float ms = time_plan(pl);
+                if (ms < best.ms) best = {cl, th, un, ms, 0};
+            }
+    for (int sh = 0; sh < 3; ++sh) {
+        SolvePlan pl;
+        if (!plan_solve_classes(c, kSolveShapes[sh], pl.classes)) continue;
+        pl.shape = sh;
+        const float ms = time_plan(pl);
+        if (ms < best.ms) best = {0, kSolveShapes[sh].threads, kSolveShapes[sh].unroll, ms, sh + 1};
+    }
+    if (best.cluster || best.shape) c->tuned[key] = best;
+}
+
+// The launch of this step's solve: the autotuner's choice for the bucket
+// (OVL_FLAG_AUTOTUNE), else the per-worker plan with the default shape, else
+// (fixed shapes, or workers too large for 8 CTAs) one uniform launch.
+SolvePlan plan_solve(ovl_ctx *c, float dt_override, int iters) {
+    const int P = c->n_parts;
+    SolvePlan pl;
+    pl.threads = solve_threads(c);
     const bool fixed = c->P.pgs_cluster > 0 || c->P.pgs_threads > 0 || c->P.smem_slot_limit > 0;
-    int cluster = 1, slots = 0, threads = solve_threads(c), unroll = 1;
-    int shape = fixed ? -1 : default_solve_shape(c);   // >= 0: per-worker plan with that shape
+    int shape = fixed ? -1 : default_solve_shape(c);
+    bool tuned_uniform = false;
     if (!fixed && (c->P.flags & OVL_FLAG_AUTOTUNE) && P > 0) {
         std::string key = tune_key(c);
         auto it = c->tuned.find(key);
@@ -594,28 +644,20 @@ void phase_solve(ovl_ctx *c, float dt_override, int iters) {
                 shape = it->second.shape - 1;
             } else if (int sl = solve_slots_for(c, it->second.cluster)) {
                 shape = -1;
-                cluster = it->second.cluster;
-                threads = it->second.threads;
-                unroll = it->second.unroll;
-                slots = sl;
+                pl.cluster = it->second.cluster;
+                pl.threads = it->second.threads;
+                pl.unroll = it->second.unroll;
+                pl.slots = sl;
+                tuned_uniform = true;
             }
         }
     }
-    std::vector<SolveClass> classes;
-    if (shape >= 0 && P > 0 && plan_solve_classes(c, kSolveShapes[shape], classes)) {
-        launch_solve_classes(c, solve_args(c, dt_override, iters), kSolveShapes[shape], classes);
-        c->last_cluster = classes.front().C;
-        c->last_threads = kSolveShapes[shape].threads;
-        c->last_unroll = kSolveShapes[shape].unroll;
-        return;
+    if (shape >= 0 && P > 0 && plan_solve_classes(c, kSolveShapes[shape], pl.classes)) {
+        pl.shape = shape;
+        return pl;
     }
-    if (slots == 0) solve_config(c, &cluster, &slots, &unroll);
-    c->last_cluster = cluster;
-    c->last_threads = threads;
-    c->last_unroll = unroll;
-    SolveArgs a = solve_args(c, dt_override, iters);
-    a.smem_slots = slots;
-    launch_solve(a, threads, cluster, unroll, c->stream);
+    if (!tuned_uniform) solve_config(c, &pl.cluster, &pl.slots, &pl.unroll);
+    return pl;
 }
 
 // The geodesic phase is 2 beta + 4 small launches whose arguments change only
@@ -705,9 +747,11 @@ ovl_status run_step(ovl_ctx *c, float dt, int iters) {
     mark(c, 4);
     phase_colour(c);
     mark(c, 5);
+    const SolvePlan plan = plan_solve(c, dt, iters);
+    apply_solve_order(c, plan);
     phase_rows(c, dt);
     mark(c, 6);
-    phase_solve(c, dt, iters);
+    launch_solve_plan(c, plan, dt, iters);
     phase_log(c);
     mark(c, 7);
     phase_geodesics(c);
@@ -829,7 +873,9 @@ void release_all(ovl_ctx *c) {
     c->sort_hist.release(); c->sort_tmp.release();
     c->lb_flag.release(); c->lb_pos.release(); c->lb_pairs.release();
     c->worker_order.release(); c->wk.release(); c->wk2.release(); c->wv2.release();
-    c->class_order.release(); c->colour_order.release(); c->lb_loads.release();
+    c->class_order.release(); c->colour_order.release(); c->solve_C.release(); c->col_off2.release();
+    c->row_owner.release();
+    c->pair_of_row2.release(); c->lb_loads.release();
 }
 
 

@@ -90,6 +90,9 @@ struct ovl_ctx {
     DBuf<uint32_t> worker_order, wk, wk2, wv2;   // workers longest first (launch order)
     DBuf<uint32_t> class_order, colour_order;    // solve / colouring: workers grouped by CTAs per worker
     std::vector<int> h_pb, h_pp;                 // part_bstart, part_pstart of this step on the host
+    std::vector<int> h_class_C;                  // CTAs per worker of the last per-worker plan
+    DBuf<int> solve_C, col_off2, pair_of_row2;   // solve: CTAs per worker, rows grouped by owner CTA
+    DBuf<uint8_t> row_owner;                     // owner CTA of every row (scratch of the grouping)
     cudaStream_t aux[5] = {};                    // side streams of the per-class solve launches
     cudaEvent_t fork = nullptr, join[5] = {};
     cudaGraphExec_t geo_exec = nullptr;          // the geodesic phase, captured

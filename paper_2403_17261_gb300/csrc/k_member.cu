@@ -102,6 +102,79 @@ __device__ __forceinline__ int body_slot(const MemberArgs &a, int x, int w) {
     return a.entry_slot[e];
 }
 
+// One block per (worker, colour); warp w takes the w-th contiguous chunk of
+// the colour's rows.  The warps count their rows per (kind, owner rank), the
+// buckets are laid out rank by rank (contacts, then joints) with the warps'
+// shares in warp order, and every warp scatters its chunk -- rows keep their
+// order inside a bucket.
+constexpr int OWNER_THREADS = 256, OWNER_WARPS = OWNER_THREADS / 32;
+
+__global__ void __launch_bounds__(OWNER_THREADS)
+k_row_owner(int P, const int *part_bstart, const int *part_ncol, const int *solve_C,
+            const int *off_in, const int *pair_of_row, const int2 *p_slot, uint8_t *owner_of_row,
+            int *pair_of_row_out, int *off_out) {
+    __shared__ int cnt[OWNER_WARPS][2 * OWNER_RANKS];
+    __shared__ int base[OWNER_WARPS][2 * OWNER_RANKS];
+    const int p = blockIdx.x, c = blockIdx.y;
+    if (p >= P) return;
+    const int ncol = part_ncol[p];
+    const int *off = off_in + (size_t)p * (2 * OVL_MAX_COLOURS + 1);
+    int *o2 = off_out + (size_t)p * OWNER_NB;
+    const int end = off[2 * ncol];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (c >= ncol) {
+        if (tid < 2 * OWNER_RANKS) o2[c * OWNER_RANKS * 2 + tid] = end;
+        if (c == OVL_MAX_COLOURS - 1 && tid == 0) o2[OWNER_NB - 1] = end;
+        return;
+    }
+    const int nb = part_bstart[p + 1] - part_bstart[p];
+    const int C = max(1, min(solve_C[p], OWNER_RANKS));
+    const int per = max(1, (nb + C - 1) / C);
+    const int s0 = off[2 * c], s1 = off[2 * c + 1], s2 = off[2 * c + 2];
+    const int chunk = (s2 - s0 + OWNER_WARPS - 1) / OWNER_WARPS;
+    const int w0 = min(s2, s0 + warp * chunk), w1 = min(s2, w0 + chunk);
+    if (lane < 2 * OWNER_RANKS) cnt[warp][lane] = 0;
+    __syncwarp();
+    const unsigned full = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
+    // bucket of a row: 2 owner + kind (0 contact, 1 joint)
+    for (int b = w0; b < w1; b += 32) {
+        const int r = b + lane;
+        int key = -1;
+        if (r < w1) {
+            const int2 sl = p_slot[pair_of_row[r]];
+            const int sa = sl.x >= 0 ? sl.x : max(sl.y, 0);
+            key = 2 * min(sa / per, C - 1) + (r >= s1 ? 1 : 0);
+            owner_of_row[r] = (uint8_t)key;
+        }
+        const unsigned peers = __match_any_sync(full, key);
+        if (key >= 0 && (peers & lt) == 0) cnt[warp][key] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int pos = s0;
+        for (int k = 0; k < 2 * OWNER_RANKS; ++k) {
+            o2[c * OWNER_RANKS * 2 + k] = pos;
+            for (int w = 0; w < OWNER_WARPS; ++w) {
+                base[w][k] = pos;
+                pos += cnt[w][k];
+            }
+        }
+        if (c == OVL_MAX_COLOURS - 1) o2[OWNER_NB - 1] = end;
+    }
+    __syncthreads();
+    for (int b = w0; b < w1; b += 32) {
+        const int r = b + lane;
+        const int key = r < w1 ? (int)owner_of_row[r] : -1;
+        const unsigned peers = __match_any_sync(full, key);
+        if (key >= 0) pair_of_row_out[base[warp][key] + __popc(peers & lt)] = pair_of_row[r];
+        __syncwarp();
+        if (key >= 0 && (peers & lt) == 0) base[warp][key] += __popc(peers);
+        __syncwarp();
+    }
+}
+
 __global__ void k_worker_cost_keys(const int *part_pstart, int P, uint32_t *keys, uint32_t *vals) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         const uint32_t cost = (uint32_t)min(part_pstart[p + 1] - part_pstart[p], (1 << 24) - 1);
@@ -552,6 +625,17 @@ void launch_pair_gather(const MemberArgs &a, const uint32_t *order, int np, cuda
 void launch_pair_setup(const MemberArgs &a, const WarmArgs &w, int np, cudaStream_t s) {
     if (!np) return;
     k_pair_setup<<<grid1d(np, 256), 256, 0, s>>>(a, w, np);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_row_owner(int P, const int *part_bstart, const int *part_ncol, const int *solve_C,
+                      const int *off_in, const int *pair_of_row, const int2 *p_slot,
+                      uint8_t *owner_of_row, int *pair_of_row_out, int *off_out, cudaStream_t s) {
+    if (P <= 0) return;
+    k_row_owner<<<dim3(P, OVL_MAX_COLOURS), OWNER_THREADS, 0, s>>>(P, part_bstart, part_ncol, solve_C, off_in,
+                                                                   pair_of_row, p_slot, owner_of_row,
+                                                                   pair_of_row_out, off_out);
     note_launch();
     CK(cudaGetLastError());
 }

@@ -5,13 +5,16 @@
 //
 // A worker is solved by a group of C CTAs (a thread-block cluster when C > 1).
 // Its body velocities (24 B per body: v and w) live in the shared memory of
-// the group -- slot s in CTA s % C at index s / C, reached through
-// distributed shared memory (mapa + ld/st.shared::cluster) -- or, for workers
-// too large for that, in a global scratch area solved by one CTA.  Rows are
-// streamed from HBM/L2 in colour order: constraints of one colour share no
-// dynamic body, so a colour is solved by all threads of the group at once and
-// a group barrier separates colours -- the same result as sweeping the
-// constraints one by one in colour order.  Inverse masses and inertias come
+// the group -- CTA k holds the contiguous slots [k per, (k + 1) per), per =
+// ceil(nb / C), and other CTAs reach them through distributed shared memory
+// (mapa + ld/st.shared::cluster) -- or, for workers too large for that, in a
+// global scratch area solved by one CTA.  Rows are streamed from HBM/L2 in
+// colour order: constraints of one colour share no dynamic body, so a colour
+// is solved by all CTAs of the group at once and a group barrier separates
+// colours -- the same result as sweeping the constraints one by one in colour
+// order.  Inside a colour every CTA takes the rows whose first dynamic body
+// it holds (the rows are grouped that way beforehand), so most body accesses
+// stay in the CTA's own shared memory.  Inverse masses and inertias come
 // with every row record so the body state stays small enough for two groups'
 // CTAs to share an SM.
 //
@@ -40,7 +43,6 @@ namespace ovl {
 
 namespace {
 
-constexpr int NB1 = 2 * OVL_MAX_COLOURS + 1;
 constexpr int SOLVE_THREADS = 512;
 
 __device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
@@ -81,14 +83,22 @@ __device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
     return r;
 }
 
-// Distributed over the C CTAs of a cluster: slot s in CTA s % C at index s / C.
-// The accesses are volatile asm, so they keep their order among themselves and
-// with the cluster barriers; ordinary loads of row records may move around them.
+// Distributed over the C CTAs of a cluster: slot s in CTA k = s / per at
+// index s - k per.  The accesses are volatile asm, so they keep their order
+// among themselves and with the cluster barriers; ordinary loads of row
+// records may move around them.
 template <int C>
 struct ClusterSlots {
     uint32_t A, B;   // shared-window offsets of this CTA's arrays (same in every CTA)
+    int per;         // slots per CTA
+    __device__ __forceinline__ uint32_t owner(int s) const {
+        uint32_t r = 0;
+#pragma unroll
+        for (int k = 1; k < C; ++k) r += s >= k * per ? 1u : 0u;
+        return r;
+    }
     __device__ __forceinline__ void load(int s, Body &b) const {
-        const uint32_t r = (uint32_t)s % C, i = (uint32_t)s / C;
+        const uint32_t r = owner(s), i = (uint32_t)s - r * (uint32_t)per;
         const uint32_t a = mapa(A + 16u * i, r), c = mapa(B + 8u * i, r);
         float4 x;
         float2 y;
@@ -99,7 +109,7 @@ struct ClusterSlots {
         b.w = make_float3(x.w, y.x, y.y);
     }
     __device__ __forceinline__ void store(int s, const Body &b) const {
-        const uint32_t r = (uint32_t)s % C, i = (uint32_t)s / C;
+        const uint32_t r = owner(s), i = (uint32_t)s - r * (uint32_t)per;
         const uint32_t a = mapa(A + 16u * i, r), c = mapa(B + 8u * i, r);
         asm volatile("st.shared::cluster.v4.f32 [%0], {%1,%2,%3,%4};"
                      :: "r"(a), "f"(b.v.x), "f"(b.v.y), "f"(b.v.z), "f"(b.w.x));
@@ -273,39 +283,54 @@ __device__ float group_sum(float v, float *red, float *slot) {
     return tot;
 }
 
+// row buckets of colour c: off[(c OWNER_RANKS + k) 2 + kind], contacts then
+// joints, for the owner ranks k in [k0, k1)
+// Row buckets of this CTA: bucket k of colour c spans rows [tab[c cs + 2k],
+// tab[c cs + 2k + 2]), contacts up to tab[c cs + 2k + 1], for k < nbk.
+struct Buckets {
+    const int *tab;
+    int cs, nbk;
+};
+
 template <class S>
-__device__ float rows_residual_sq(const SolveArgs &a, const S &st, const int *off, int ncol, float mu,
-                                  int g, int G) {
+__device__ float rows_residual_sq(const SolveArgs &a, const S &st, const Buckets &bk, int ncol, float mu,
+                                  int tid, int T) {
     float sq = 0.f;
-    for (int c = 0; c < ncol; ++c) {
-        const int jb = off[2 * c + 1], ce = off[2 * c + 2];
-        for (int r = off[2 * c] + g; r < ce; r += G) {
-            float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r], m = a.r3[r], lam = a.rlam[r];
-            Body A, B;
-            int slots = __float_as_int(r2.w);
-            load_pair(st, slots, m, A, B);
-            sq += r < jb ? contact_residual_sq(A, B, r0, r1, r2, mu, lam) : joint_residual_sq(A, B, r0, r1, r2);
+    for (int c = 0; c < ncol; ++c)
+        for (int k = 0; k < bk.nbk; ++k) {
+            const int o = c * bk.cs + 2 * k;
+            const int jb = bk.tab[o + 1], ce = bk.tab[o + 2];
+            for (int r = bk.tab[o] + tid; r < ce; r += T) {
+                float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r], m = a.r3[r], lam = a.rlam[r];
+                Body A, B;
+                int slots = __float_as_int(r2.w);
+                load_pair(st, slots, m, A, B);
+                sq += r < jb ? contact_residual_sq(A, B, r0, r1, r2, mu, lam) : joint_residual_sq(A, B, r0, r1, r2);
+            }
         }
-    }
     return sq;
 }
 
-// One worker solved by a group of C CTAs; threads are numbered g = rank T + tid
-// and in every colour thread g takes rows off + g, off + g + G, ... (G = C T),
-// U of them at a time.
+// One worker solved by a group of C CTAs.  CTA `rank` holds the body slots
+// [rank per, min(nb, (rank + 1) per)) and, in every colour, takes the rows of
+// its owner bucket, thread tid the rows tid, tid + T, ..., U of them at a
+// time.  With C = 1 (one CTA, or the global-memory path) the CTA holds every
+// slot and takes every bucket.
 template <int C, int U, class S>
-__device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank) {
+__device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, int per, const Buckets &bk,
+                             int row0, int row1) {
     __shared__ float red[32];
     __shared__ float part_sum;
     const int tid = threadIdx.x, T = blockDim.x;
     const int g = rank * T + tid, G = C * T;
     const int b0 = a.part_bstart[p], nb = a.part_bstart[p + 1] - b0;
+    const int s_lo = C == 1 ? 0 : rank * per, s_hi = C == 1 ? nb : min(nb, (rank + 1) * per);
     const int scene = a.part_scene[p];
     const float h = a.dt_override > 0.f ? a.dt_override : a.scene_dt[scene];
     const float mu = a.scene_mu[scene];
     // velocities after the external force (h f), from the blended state; each
     // CTA loads the slots it holds
-    for (int s = rank + C * tid; s < nb; s += C * T) {
+    for (int s = s_lo + tid; s < s_hi; s += T) {
         int b = a.entry_body[a.part_list[b0 + s]];
         float4 v = a.st[4 * b + 2], w = a.st[4 * b + 3];
         Body x;
@@ -315,11 +340,12 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank) {
     }
     group_sync<C>();
     const int ncol = a.part_ncol[p];
-    const int *off = a.col_off + (size_t)p * NB1;
     // warm start: apply the previous impulses, colour by colour
     for (int c = 0; c < ncol; ++c) {
-        const int jb = off[2 * c + 1], ce = off[2 * c + 2];
-        for (int r = off[2 * c] + g; r < ce; r += G) {
+      for (int k = 0; k < bk.nbk; ++k) {
+        const int o = c * bk.cs + 2 * k;
+        const int jb = bk.tab[o + 1], ce = bk.tab[o + 2];
+        for (int r = bk.tab[o] + tid; r < ce; r += T) {
             float4 lam = a.rlam[r];
             if (lam.x == 0.f && lam.y == 0.f && lam.z == 0.f) continue;
             float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r], m = a.r3[r];
@@ -336,18 +362,21 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank) {
             }
             store_pair(st, slots, A, B);
         }
-        group_sync<C>();
+      }
+      group_sync<C>();
     }
     // Gauss-Seidel sweeps
     int it_done = 0;
     for (int it = 0; it < a.iters; ++it) {
         for (int c = 0; c < ncol; ++c) {
-            const int jb = off[2 * c + 1], ce = off[2 * c + 2];
-            int r = off[2 * c] + g;
+          for (int k = 0; k < bk.nbk; ++k) {
+            const int o = c * bk.cs + 2 * k;
+            const int jb = bk.tab[o + 1], ce = bk.tab[o + 2];
+            int r = bk.tab[o] + tid;
             if (U == 2) {
                 // two rows of the colour at once (independent: no shared body)
-                for (; r + G < ce; r += 2 * G) {
-                    const int q = r + G;
+                for (; r + T < ce; r += 2 * T) {
+                    const int q = r + T;
                     float4 x0 = a.r0[r], x1 = a.r1[r], x2 = a.r2[r], xm = a.r3[r], xl = a.rlam[r];
                     float4 y0 = a.r0[q], y1 = a.r1[q], y2 = a.r2[q], ym = a.r3[q], yl = a.rlam[q];
                     const int sx = __float_as_int(x2.w), sy = __float_as_int(y2.w);
@@ -364,7 +393,7 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank) {
                     a.rlam[q] = yl;
                 }
             }
-            for (; r < ce; r += G) {
+            for (; r < ce; r += T) {
                 float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r], m = a.r3[r], lam = a.rlam[r];
                 int slots = __float_as_int(r2.w);
                 Body A, B;
@@ -374,26 +403,27 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank) {
                 store_pair(st, slots, A, B);
                 a.rlam[r] = lam;
             }
-            group_sync<C>();
+          }
+          group_sync<C>();
         }
         it_done = it + 1;
         if (a.res_tol > 0.f && a.res_check_every > 0 && it_done % a.res_check_every == 0 && it_done < a.iters) {
-            float tot = group_sum<C>(rows_residual_sq(a, st, off, ncol, mu, g, G), red, &part_sum);
-            int nrows = 3 * (off[2 * ncol] - off[0]);
+            float tot = group_sum<C>(rows_residual_sq(a, st, bk, ncol, mu, tid, T), red, &part_sum);
+            int nrows = 3 * (row1 - row0);
             if (nrows == 0 || sqrtf(tot / nrows) <= a.res_tol) break;   // the same total in every CTA
         }
     }
     // residual of every row at the final iterate
     if (a.flags & OVL_FLAG_RESIDUAL) {
-        float tot = group_sum<C>(rows_residual_sq(a, st, off, ncol, mu, g, G), red, &part_sum);
+        float tot = group_sum<C>(rows_residual_sq(a, st, bk, ncol, mu, tid, T), red, &part_sum);
         if (rank == 0 && tid == 0) a.part_res_sq[p] = (double)tot;
     }
     if (rank == 0 && tid == 0) a.part_iters[p] = it_done;
     // impulses back in canonical pair order (next step's warm start)
-    for (int r = off[0] + g; r < off[2 * ncol]; r += G) a.lam_out[a.rpair[r]] = a.rlam[r];
+    for (int r = row0 + g; r < row1; r += G) a.lam_out[a.rpair[r]] = a.rlam[r];
     // integrate: x += h v; q <- normalise(q + h/2 (0, w) (x) q); write this
     // worker's copy of each body the CTA holds
-    for (int s = rank + C * tid; s < nb; s += C * T) {
+    for (int s = s_lo + tid; s < s_hi; s += T) {
         int e = a.part_list[b0 + s];
         int b = a.entry_body[e];
         float4 x = a.st[4 * b], q = a.st[4 * b + 1], v0 = a.st[4 * b + 2], w0 = a.st[4 * b + 3];
@@ -433,19 +463,29 @@ __global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveAr
         if (rank == 0 && threadIdx.x == 0) atomicCAS(a.status, DEV_OK, DEV_ERR_CAPACITY);
         return;
     }
+    // this CTA's row buckets (three offsets per colour), read in every colour
+    // of every sweep
+    const int *goff = a.col_off + (size_t)p * OWNER_NB;
+    __shared__ int boff[3 * OVL_MAX_COLOURS];
+    const int ncol = a.part_ncol[p];
+    for (int i = threadIdx.x; i < 3 * ncol; i += blockDim.x)
+        boff[i] = goff[((i / 3) * OWNER_RANKS + rank) * 2 + i % 3];
+    __syncthreads();
+    const int row0 = goff[0], row1 = goff[OWNER_NB - 1];
     if (per <= a.smem_slots) {
         float4 *A = sm;
         float2 *B = reinterpret_cast<float2 *>(sm + per);
         if (C == 1) {
             LocalSlots st{A, B};
-            solve_worker<C, U>(a, st, p, rank);
+            solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
         } else {
-            ClusterSlots<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B)};
-            solve_worker<C, U>(a, st, p, rank);
+            ClusterSlots<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B), per};
+            solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
         }
     } else if (rank == 0) {
+        // one CTA takes the whole worker: every owner bucket of every colour
         LocalSlots st{a.scratch + (size_t)b0, reinterpret_cast<float2 *>(a.scratch + (size_t)a.n_entries) + b0};
-        solve_worker<1, U>(a, st, p, 0);
+        solve_worker<1, U>(a, st, p, 0, nb, Buckets{goff, 2 * OWNER_RANKS, OWNER_RANKS}, row0, row1);
     }
 }
 

@@ -99,6 +99,17 @@ struct WarmArgs {
     float factor;
 };
 void launch_pair_setup(const MemberArgs &a, const WarmArgs &w, int np, cudaStream_t s);
+// Rows of every colour regrouped by the CTA that owns them in the solve:
+// worker p's bodies are split into solve_C[p] contiguous slot ranges of
+// ceil(nb / C) slots, one per CTA, and a row belongs to the CTA holding its
+// first dynamic body.  off_in: [P][2*OVL_MAX_COLOURS+1] (colour, kind)
+// offsets of pair_of_row; off_out: [P][OWNER_NB] offsets of (colour, owner
+// rank, kind) buckets, ranks 0..7, contacts before joints, then the end.
+#define OWNER_RANKS 8
+#define OWNER_NB (OVL_MAX_COLOURS * OWNER_RANKS * 2 + 1)
+void launch_row_owner(int P, const int *part_bstart, const int *part_ncol, const int *solve_C,
+                      const int *off_in, const int *pair_of_row, const int2 *p_slot,
+                      uint8_t *owner_of_row, int *pair_of_row_out, int *off_out, cudaStream_t s);
 // keys[p] = 2^24 - 1 - min(pairs of worker p, 2^24 - 1), vals[p] = p: an
 // ascending stable sort of the keys lists the workers longest first
 void launch_worker_cost_keys(const int *part_pstart, int P, uint32_t *keys, uint32_t *vals,
@@ -159,7 +170,7 @@ struct SolveArgs {
     const int *part_list;
     const int *entry_body;
     const int *part_ncol;
-    const int *col_off;
+    const int *col_off;        // [P][OWNER_NB] (colour, owner rank, kind) row offsets
     const int *part_scene;
     const float *scene_dt;
     float dt_override;
