@@ -414,6 +414,7 @@ void phase_colour(ovl_ctx *c) {
     ColourArgs a{};
     a.n_parts = P; a.part_bstart = c->part_bstart.p; a.part_pstart = c->part_pstart.p;
     a.order = c->worker_order.p;
+    a.part_list = c->part_list.p; a.entry_body = c->entry_body.p;
     a.p_key = c->p_key.p; a.p_slot = c->p_slot.p; a.p_colour = c->p_colour.p;
     a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p; a.pair_of_row = c->pair_of_row.p;
     a.part_rounds = c->part_rounds.p;

@@ -242,7 +242,8 @@ __device__ __forceinline__ uint32_t mapa_u32(uint32_t a, uint32_t rank) {
 // Per-slot colouring state of one worker: the maximum priority of the
 // uncoloured constraints posted this round (array 0) and the mask of colours
 // taken (array 1).
-// C > 1: spread over the cluster's shared memory, slot s in CTA s % C.  The
+// C > 1: spread over the cluster's shared memory, CTA k holding the
+// contiguous slots [k per, (k + 1) per).  The
 // maximum is taken in two 32-bit stages (high words, then low words among the
 // constraints whose high word won), which is the 64-bit maximum: 64-bit atomic
 // max into another CTA's shared memory lost updates in a standalone test on
@@ -251,9 +252,13 @@ template <int C>
 struct ColourSlots {
     static constexpr bool two_stage = true;
     uint32_t b0, b1;   // shared-window offsets of this CTA's arrays (hi/lo words, used mask)
+    int per;           // slots per CTA
     __device__ __forceinline__ uint32_t at(int arr, int s) const {
         uint32_t base = arr == 0 ? b0 : b1;
-        return mapa_u32(base + 8u * (uint32_t)(s / C), (uint32_t)(s % C));
+        uint32_t r = 0;
+#pragma unroll
+        for (int k = 1; k < C; ++k) r += s >= k * per ? 1u : 0u;
+        return mapa_u32(base + 8u * ((uint32_t)s - r * (uint32_t)per), r);
     }
     // stage 1: high word (at offset +4 of the little-endian 64-bit slot)
     __device__ __forceinline__ void amax_hi(int s, unsigned long long v) const {
@@ -313,11 +318,14 @@ __device__ __forceinline__ int cluster_int_sum(int *v) {
     return t;
 }
 
-// Colours one worker with a group of C CTAs.  CTA `rank` owns the
-// constraints [i0, i1) of the worker (a contiguous share, so the final sort is
-// stable across CTAs) and the slots s with s % C == rank.
+// Colours one worker with a group of C CTAs.  CTA `rank` holds the slots
+// [rank per, (rank + 1) per) and takes two contiguous shares of the worker's
+// constraints (canonical order: contacts by their first body, then joints):
+// the contacts whose first body falls in its slot range, so most of their
+// slot accesses stay local, and an equal share of the joints.  The shares
+// follow rank order, so the final sort is stable across CTAs.
 template <int C, class SL>
-__device__ void colour_worker(const ColourArgs &a, const SL &S, int p, int rank, int per_slots) {
+__device__ void colour_worker(const ColourArgs &a, const SL &S, int p, int rank, int per) {
     __shared__ int n_next, ncol_sh, pub_left, pub_ncol;
     __shared__ int counts[NBUCKET + 1];
     __shared__ int base_b[NBUCKET + 1];
@@ -326,27 +334,46 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, int p, int rank,
     const int tid = threadIdx.x, T = blockDim.x;
     const int b0 = a.part_bstart[p], nb = a.part_bstart[p + 1] - b0;
     const int q0 = a.part_pstart[p], nq = a.part_pstart[p + 1] - q0;
-    const int chunk = (nq + C - 1) / C;
-    const int i0 = min(nq, rank * chunk), i1 = min(nq, i0 + chunk);
-    (void)per_slots;
+    const int s_lo = C == 1 ? 0 : min(nb, rank * per), s_hi = C == 1 ? nb : min(nb, (rank + 1) * per);
+    // contacts [0, ncw) are sorted by (first body, second body), joints [ncw, nq) by index
+    const uint64_t *key = a.p_key + q0;
+    auto key_bound = [&](int lo, int hi, uint64_t x) {
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (key[mid] < x) lo = mid + 1; else hi = mid; }
+        return lo;
+    };
+    const int ncw = key_bound(0, nq, 1ull << 62);
+    auto first_contact = [&](int k) {   // first contact whose first body is in slot range k or later
+        if (k <= 0) return 0;
+        if (k * per >= nb) return ncw;
+        const uint64_t body = (uint64_t)a.entry_body[a.part_list[b0 + k * per]];
+        return key_bound(0, ncw, body << 32);
+    };
+    const int c0 = C == 1 ? 0 : first_contact(rank), c1 = C == 1 ? ncw : first_contact(rank + 1);
+    const int jchunk = (nq - ncw + C - 1) / C;
+    const int j0 = min(nq, ncw + rank * jchunk), j1 = min(nq, j0 + jchunk);
+    const int nC = c1 - c0, m0 = nC + (j1 - j0);
+    auto item = [&](int v) { return v < nC ? c0 + v : j0 + (v - nC); };
     // worklists of this CTA's uncoloured constraints: (index in worker,
-    // slot a, slot b) and the priority, ping-pong, read contiguously
-    int4 *wl_cur = a.worklist + q0 + i0, *wl_next = a.worklist2 + q0 + i0;
-    unsigned long long *pr_cur = a.wprio + q0 + i0, *pr_next = a.wprio2 + q0 + i0;
-    for (int s = rank + C * tid; s < nb; s += C * T) S.st(1, s, 0ull);
-    for (int k = i0 + tid; k < i1; k += T) {
+    // slot a, slot b) and the priority, ping-pong, read contiguously; the
+    // CTA's region follows the regions of the lower ranks
+    const int wbase = c0 + (j0 - ncw);
+    int4 *wl_cur = a.worklist + q0 + wbase, *wl_next = a.worklist2 + q0 + wbase;
+    unsigned long long *pr_cur = a.wprio + q0 + wbase, *pr_next = a.wprio2 + q0 + wbase;
+    for (int s = s_lo + tid; s < s_hi; s += T) S.st(1, s, 0ull);
+    for (int v = tid; v < m0; v += T) {
+        const int k = item(v);
         int2 sl = a.p_slot[q0 + k];
-        wl_cur[k - i0] = make_int4(k, sl.x, sl.y, 0);
-        pr_cur[k - i0] = mix64(a.p_key[q0 + k]);
+        wl_cur[v] = make_int4(k, sl.x, sl.y, 0);
+        pr_cur[v] = mix64(key[k]);
     }
     if (tid == 0) { n_next = 0; ncol_sh = 0; }
-    int m = i1 - i0;
+    int m = m0;
     int rounds = 0;
     // Every round: each CTA zeroes the maxima of the slots it holds, all
     // uncoloured constraints post their priority at their slots, and those
     // holding the maximum at both slots take their colour.
     while (rounds <= nq + 1) {
-        for (int s = rank + C * tid; s < nb; s += C * T) S.st(0, s, 0ull);
+        for (int s = s_lo + tid; s < s_hi; s += T) S.st(0, s, 0ull);
         csync<C>();
         for (int i = tid; i < m; i += T) {
             const int4 w = wl_cur[i];
@@ -409,9 +436,10 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, int p, int rank,
     for (int j = tid; j < NBUCKET; j += T) running[j] = 0;
     for (int j = tid; j < COLOUR_WARPS * NBUCKET; j += T) (&wcnt[0][0])[j] = 0;
     __syncthreads();
-    for (int k = i0 + tid; k < i1; k += T) {
+    for (int v = tid; v < m0; v += T) {
+        const int k = item(v);
         int c = a.p_colour[q0 + k];
-        int kind = (int)(a.p_key[q0 + k] >> 62) & 1;
+        int kind = (int)(key[k] >> 62) & 1;
         atomicAdd(&counts[2 * c + kind], 1);
     }
     if (tid == 0) pub_ncol = ncol_sh;
@@ -446,11 +474,12 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, int p, int rank,
     __syncthreads();
     const int lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    for (int base = i0; base < i1; base += T) {
-        int k = base + tid;
-        bool valid = k < i1;
+    for (int base = 0; base < m0; base += T) {
+        const int v = base + tid;
+        bool valid = v < m0;
+        const int k = valid ? item(v) : 0;
         int bucket = NBUCKET;
-        if (valid) bucket = 2 * a.p_colour[q0 + k] + ((int)(a.p_key[q0 + k] >> 62) & 1);
+        if (valid) bucket = 2 * a.p_colour[q0 + k] + ((int)(key[k] >> 62) & 1);
         unsigned peers = __match_any_sync(0xffffffffu, bucket);
         int lrank = __popc(peers & lt);
         if (valid && lrank == 0) wcnt[warp][bucket] = __popc(peers);
@@ -485,7 +514,7 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
             ColourPtrs S{mx, u};
             colour_worker<1>(a, S, p, 0, per);
         } else {
-            ColourSlots<C> S{(uint32_t)__cvta_generic_to_shared(mx), (uint32_t)__cvta_generic_to_shared(u)};
+            ColourSlots<C> S{(uint32_t)__cvta_generic_to_shared(mx), (uint32_t)__cvta_generic_to_shared(u), per};
             colour_worker<C>(a, S, p, rank, per);
         }
     } else if (rank == 0) {

@@ -118,6 +118,8 @@ void launch_worker_cost_keys(const int *part_pstart, int P, uint32_t *keys, uint
 struct ColourArgs {
     int n_parts;
     const uint32_t *order;     // [P] worker of each CTA group, longest first (NULL: identity)
+    const int *part_list;      // [ne] entries grouped by worker, bodies ascending
+    const int *entry_body;     // [ne]
     const int *part_bstart;
     const int *part_pstart;
     const uint64_t *p_key;
