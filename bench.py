@@ -16,6 +16,13 @@ iterations/s, a roofline entry for the solver kernel, the FP64 oracle timed on
 the host as CPU baseline, an end-to-end figure through the C ABI with host
 buffers, SM clocks sampled during the timed region.
 
+``--workload pile_mixed``: 1250 big spheres (radius 1.5, two layers) on the
+floor of a box under the same 64^3 lattice of small ones; each big sphere takes
+tens of contacts.  With ``--lb-load contacts`` Algorithm 6 compares loads that
+count 1 + contacts per active body instead of bodies (Section 6's proposal);
+the line then reports the per-worker row imbalance (max / mean) next to the
+throughput.
+
 --impl reference times the FP64 oracle instead (the CPU reference arm).
 """
 from __future__ import annotations
@@ -54,20 +61,23 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ovl", choices=["ovl", "reference"])
     ap.add_argument("--workload", default="pile_large",
-                    choices=["pile_large", "chain", "pile_small", "batched", "warmstart"],
+                    choices=["pile_large", "pile_mixed", "chain", "pile_small", "batched", "warmstart"],
                     help="warmstart: the learned warm start on the large pile (log, train, "
                          "sweeps to RMS residual 1e-4 against the previous-step warm start)")
     ap.add_argument("--ws-log-steps", type=int, default=6)
     ap.add_argument("--ws-eval-steps", type=int, default=50)
     ap.add_argument("--ws-train-steps", type=int, default=20000)
     ap.add_argument("--settle", type=int, default=None, help="untimed steps before the warm-up")
+    ap.add_argument("--lb-load", default="bodies", choices=["bodies", "contacts"],
+                    help="load Algorithm 6 compares: active bodies (the paper's) or 1 + contacts per body")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
 def default_settle(workload):
-    return {"pile_large": 150, "chain": 0, "pile_small": 0, "batched": 0, "warmstart": 150}[workload]
+    return {"pile_large": 150, "pile_mixed": 150, "chain": 0, "pile_small": 0, "batched": 0,
+            "warmstart": 150}[workload]
 
 
 def make_scene(workload):
@@ -152,6 +162,8 @@ def oracle_sample_scene(workload):
     from paper_2403_17261_gb300 import scenes as S
     if workload in ("pile_large", "warmstart"):
         return S.pile_large(side=16, n_sets=16), 150, "pile_large generator at 16^3 = 4096 bodies, 16 k-means workers, settled 150 steps by the oracle itself (untimed)"
+    if workload == "pile_mixed":
+        return S.pile_mixed(side=12, n_sets=16), 150, "pile_mixed generator at 12^3 small + 50 big spheres, 16 k-means workers, settled 150 steps by the oracle itself (untimed)"
     if workload == "chain":
         return S.chain(), 0, "the full 4096-sphere chain"
     if workload == "batched":
@@ -159,10 +171,10 @@ def oracle_sample_scene(workload):
     return S.pile_small(), 0, "the full 256-sphere pile"
 
 
-def oracle_run(workload, steps, warmup, max_seconds=None):
+def oracle_run(workload, steps, warmup, max_seconds=None, params=None):
     from oracle import oracle as O
     sc, settle, desc = oracle_sample_scene(workload)
-    sim = O.OracleSim(sc)
+    sim = O.OracleSim(sc, params)
     if sc.assign_overlap:
         sim.assign_overlap()
     for _ in range(settle):
@@ -187,7 +199,8 @@ def oracle_run(workload, steps, warmup, max_seconds=None):
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    r = oracle_run(args.workload, args.steps, args.warmup, max_seconds=240.0)
+    r = oracle_run(args.workload, args.steps, args.warmup, max_seconds=240.0,
+                   params=dict(lb_load=1 if args.lb_load == "contacts" else 0))
     line = {
         "impl": "reference", "metric": "body-steps/s", "value": r["value"], "unit": "body-steps/s",
         "n_gpus": args.gpus, "steps": r["steps"], "warmup": args.warmup,
@@ -216,7 +229,8 @@ def gpu_arm(args, rank, world, local_rank):
     g.build()
     sc = make_scene(args.workload)
     stream = torch.cuda.Stream()
-    params = dict(flags=ovl.OVL_FLAG_TIMING)
+    lb_load = ovl.OVL_LB_CONTACTS if args.lb_load == "contacts" else ovl.OVL_LB_BODIES
+    params = dict(flags=ovl.OVL_FLAG_TIMING, lb_load=lb_load)
     sim = ovl.Simulation(sc, params, stream=stream.cuda_stream)
     settle = default_settle(args.workload) if args.settle is None else args.settle
     # NVTX ranges let a profiler select the timed steps (ncu --nvtx --nvtx-include "timed/")
@@ -240,7 +254,7 @@ def gpu_arm(args, rank, world, local_rank):
                                          sim.step_index_value())
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    solve_ms, rows_iters, bytes_solve, launches = [], 0, 0.0, []
+    solve_ms, rows_iters, bytes_solve, launches, imbalance = [], 0, 0.0, [], []
     barrier()
     torch.cuda.nvtx.range_push("timed")
     with ClockSampler(local_rank) as clk:
@@ -252,6 +266,8 @@ def gpu_arm(args, rank, world, local_rank):
             with torch.cuda.stream(stream):
                 ends[k].record(stream)
             st = sim.stats()
+            rows_w = sim.worker_stats()["rows"]
+            imbalance.append(float(rows_w.max() / max(rows_w.mean(), 1e-9)))
             solve_ms.append(st["phase_ms"]["solve"])
             launches.append(st["n_launches"])
             n_cons = st["n_pairs"]
@@ -302,7 +318,7 @@ def gpu_arm(args, rank, world, local_rank):
                        if SOLVE_DRAM_PER_ALGORITHMIC_BYTE is not None and args.workload == "pile_large" else None)
     cpu = None
     if not args.no_cpu_baseline:
-        r = oracle_run(args.workload, steps=80, warmup=1, max_seconds=15.0)
+        r = oracle_run(args.workload, steps=80, warmup=1, max_seconds=15.0, params=dict(lb_load=lb_load))
         cpu = {"value": r["value"], "unit": "body-steps/s", "cores": r["cores"], "kind": "oracle",
                "sample": r["sample"]}
     line = {
@@ -315,7 +331,9 @@ def gpu_arm(args, rank, world, local_rank):
                    "l2": "flushed between timed steps (write of 2x L2)",
                    "contacts_last_step": last["n_contacts"], "pairs_last_step": last["n_pairs"],
                    "overlap_bodies_last_step": last["n_overlap"], "max_colours_last_step": last["max_colours"],
-                   "parallelism": f"replicas x{world}"},
+                   "lb_load": args.lb_load, "parallelism": f"replicas x{world}"},
+        "worker_rows_max_over_mean": float(np.mean(imbalance)),
+        "solve_ms_mean": sum(solve_ms) / len(solve_ms),
         "row_iters_per_s": rows_iters / solve_s,
         "phase_ms_last_step": {k: round(v, 4) for k, v in last["phase_ms"].items()},
         "roofline": {"bound": "hbm", "kernel": "k_solve", "achieved": achieved, "peak": peak,

@@ -64,7 +64,17 @@ typedef struct ovl_params {
     int32_t pgs_cluster;     /* CTAs per worker, 1, 2 or 4 (0 = automatic from the SM count) */
     int32_t smem_slot_limit; /* > 0: at most this many bodies per CTA in shared memory (larger
                                 workers use the global-memory path); 0 = as many as fit */
+    int32_t lb_load;         /* the load <W_x> Algorithm 6 compares: OVL_LB_BODIES (default) or
+                                OVL_LB_CONTACTS; any other value is OVL_ERR_ARG at ovl_create */
 } ovl_params;
+
+/* Loads of Algorithm 6.  BODIES is the paper's: <W_x> counts the active
+ * bodies of the workers in W_x (Table 1).  CONTACTS is the contact-following
+ * load Section 6 proposes for scenes whose bodies carry very different
+ * numbers of contacts: every active body counts 1 + the number of this
+ * step's contacts it is an end of (planes and static ends included). */
+#define OVL_LB_BODIES 0
+#define OVL_LB_CONTACTS 1
 
 #define OVL_FLAG_RESIDUAL 1  /* compute the complementarity residual of every row after the sweeps */
 #define OVL_FLAG_TIMING 2    /* record per-phase times with CUDA events (ovl_read_stats) */

@@ -23,14 +23,14 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libovl_oracle.so")
 
 DEFAULT_PARAMS = dict(gravity=(0.0, 0.0, -9.81), margin=0.05, erp=0.2, slop=0.001, warmstart=1.0,
-                      lb_activate=1, lb_deact_every=1, res_tol=0.0, res_check_every=0)
+                      lb_activate=1, lb_deact_every=1, res_tol=0.0, res_check_every=0, lb_load=0)
 
 
 class OrcParams(C.Structure):
     _fields_ = [("gravity", C.c_double * 3), ("margin", C.c_double), ("erp", C.c_double),
                 ("slop", C.c_double), ("warmstart", C.c_double), ("lb_activate", C.c_int),
                 ("lb_deact_every", C.c_int), ("res_tol", C.c_double),
-                ("res_check_every", C.c_int)]
+                ("res_check_every", C.c_int), ("lb_load", C.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -89,7 +89,7 @@ def lib():
         L.orc_graph.restype = C.c_int64
         L.orc_graph.argtypes = [C.c_int, dp, C.c_int64, ip, ip, C.c_int64, ip, ip]
         L.orc_load_balance.argtypes = [C.c_int, u64p, ip, ip, C.c_int, ip, ip, C.c_int64, ip, ip, ip,
-                                       C.c_int, C.c_int]
+                                       C.c_int, C.c_int, i64p]
         L.orc_is_bridge.restype = C.c_int
         L.orc_is_bridge.argtypes = [C.c_int, u64p, ip, ip, C.c_int]
         L.orc_assign_overlap.argtypes = [C.c_int, u64p, ip, ip, C.c_int, dp, C.c_int, ip, ip]
@@ -165,8 +165,10 @@ def graph(n, inv_mass, edges):
 
 
 def load_balance(masks, scene_of_body, n_sets, row_ptr, col, contact_pairs, scene_gamma,
-                 do_activate=True, do_deactivate=True):
-    """Algorithm 6 on a copy of the masks; returns the new masks."""
+                 do_activate=True, do_deactivate=True, weights=None):
+    """Algorithm 6 on a copy of the masks; returns the new masks.  ``weights``
+    (int64 per body) replaces the body count in the loads <W>; None counts
+    every active body once (Table 1)."""
     m = _u64(masks).copy()
     n = m.shape[0]
     sob = _i32(scene_of_body)
@@ -175,9 +177,12 @@ def load_balance(masks, scene_of_body, n_sets, row_ptr, col, contact_pairs, scen
     cp = _i32(contact_pairs).reshape(-1, 2)
     ca, cb = _i32(cp[:, 0]), _i32(cp[:, 1])
     rp, cl, sg = _i32(row_ptr), _i32(col), _i32(scene_gamma)
+    wt = None if weights is None else np.ascontiguousarray(weights, dtype=np.int64)
+    assert wt is None or wt.shape == (n,)
     lib().orc_load_balance(n, _ptr(m, u64p), _ptr(sob, ip), _ptr(base, ip), int(base[-1]),
                            _ptr(rp, ip), _ptr(cl, ip), cp.shape[0], _ptr(ca, ip), _ptr(cb, ip),
-                           _ptr(sg, ip), int(do_activate), int(do_deactivate))
+                           _ptr(sg, ip), int(do_activate), int(do_deactivate),
+                           None if weights is None else _ptr(wt, i64p))
     return m
 
 
@@ -259,6 +264,7 @@ class OracleSim:
         cp.margin, cp.erp, cp.slop, cp.warmstart = p["margin"], p["erp"], p["slop"], p["warmstart"]
         cp.lb_activate, cp.lb_deact_every = int(p["lb_activate"]), int(p["lb_deact_every"])
         cp.res_tol, cp.res_check_every = float(p["res_tol"]), int(p["res_check_every"])
+        cp.lb_load = int(p["lb_load"])
         self._params = cp
         self.scene = scene
         self.n = scene.n_bodies

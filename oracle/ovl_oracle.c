@@ -41,6 +41,11 @@
  *    ties to the lower index).  Everything after the decision is FP64.
  *  - Alg 6 input = every current contact between two dynamic bodies in
  *    canonical (key) order; <W_x> = sum over workers in W_x of |P_w|, live;
+ *    with the contact load (lb_load = 1; Section 6 proposes a load that
+ *    follows contacts for scenes where bodies carry unequal contact counts)
+ *    every active body counts 1 + the number of this step's contacts it is an
+ *    end of (planes and static ends included), so <W_x> sums that weight over
+ *    the active bodies of the workers in W_x;
  *    a load tie in the activation branch activates B in W_A; the gamma-ball
  *    activation uses W_A, W_B as read when the contact is taken up; the
  *    least-loaded choice of the equal-mask branch breaks ties towards the
@@ -97,6 +102,7 @@ typedef struct {
     int lb_deact_every;  /* Alg 6 removal branches on steps with index % k == 0; 0 = never */
     double res_tol;      /* > 0: a worker stops sweeping once its RMS residual <= res_tol */
     int res_check_every; /* sweeps between residual checks when res_tol > 0 */
+    int lb_load;         /* 0: <W> counts active bodies (Table 1); 1: contact load (above) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -496,24 +502,28 @@ typedef struct {
     uint64_t *mask;        /* per body, bit w = scene-local worker w */
     const int *sob;        /* scene of body */
     const int *part_base;  /* global index of worker 0 of each scene */
-    int64_t *count;        /* |P_w| per global worker */
+    int64_t *count;        /* load per global worker: sum of the weights of its active bodies */
+    const int64_t *weight; /* per body; NULL: every body weighs 1, the count |P_w| */
 } membership;
+
+static int64_t body_weight(const membership *m, int b) { return m->weight ? m->weight[b] : 1; }
 
 static void activate(membership *m, uint64_t W, int b) {
     uint64_t add = W & ~m->mask[b];
     int base = m->part_base[m->sob[b]];
-    for (int w = 0; w < 64; ++w) if (add >> w & 1u) m->count[base + w]++;
+    for (int w = 0; w < 64; ++w) if (add >> w & 1u) m->count[base + w] += body_weight(m, b);
     m->mask[b] |= add;
 }
 
 static void deactivate(membership *m, uint64_t W, int b) {
     uint64_t rem = W & m->mask[b];
     int base = m->part_base[m->sob[b]];
-    for (int w = 0; w < 64; ++w) if (rem >> w & 1u) m->count[base + w]--;
+    for (int w = 0; w < 64; ++w) if (rem >> w & 1u) m->count[base + w] -= body_weight(m, b);
     m->mask[b] &= ~rem;
 }
 
-/* <W_x>: total number of active bodies over the workers in W_x (Table 1) */
+/* <W_x>: total number of active bodies over the workers in W_x (Table 1),
+ * each body counted with its weight */
 static int64_t load_of(const membership *m, uint64_t W, int scene) {
     int64_t s = 0;
     int base = m->part_base[scene];
@@ -577,28 +587,28 @@ static void load_balance_impl(membership *m, int n, const int *row_ptr, const in
 }
 
 static int64_t *counts_from_masks(int n, const uint64_t *mask, const int *sob, const int *part_base,
-                                  int n_parts_total) {
+                                  int n_parts_total, const int64_t *weight) {
     int64_t *count = xcalloc((size_t)n_parts_total + 1, sizeof(int64_t));
     for (int b = 0; b < n; ++b)
         for (int w = 0; w < 64; ++w)
-            if (mask[b] >> w & 1u) count[part_base[sob[b]] + w]++;
+            if (mask[b] >> w & 1u) count[part_base[sob[b]] + w] += weight ? weight[b] : 1;
     return count;
 }
 
-/* Standalone Alg 6: masks updated in place. */
+/* Standalone Alg 6: masks updated in place; weight NULL = body counts. */
 void orc_load_balance(int n, uint64_t *mask, const int *scene_of_body, const int *part_base,
                       int n_parts_total, const int *row_ptr, const int *col, int64_t nc,
                       const int *ca, const int *cb, const int *scene_gamma, int do_activate,
-                      int do_deactivate) {
-    int64_t *count = counts_from_masks(n, mask, scene_of_body, part_base, n_parts_total);
-    membership m = {mask, scene_of_body, part_base, count};
+                      int do_deactivate, const int64_t *weight) {
+    int64_t *count = counts_from_masks(n, mask, scene_of_body, part_base, n_parts_total, weight);
+    membership m = {mask, scene_of_body, part_base, count, weight};
     load_balance_impl(&m, n, row_ptr, col, nc, ca, cb, scene_gamma, do_activate, do_deactivate);
     free(count);
 }
 
 int orc_is_bridge(int n, const uint64_t *mask, const int *row_ptr, const int *col, int b) {
     (void)n;
-    membership m = {(uint64_t *)mask, NULL, NULL, NULL};
+    membership m = {(uint64_t *)mask, NULL, NULL, NULL, NULL};
     return is_bridge(&m, row_ptr, col, b);
 }
 
@@ -625,8 +635,8 @@ void orc_assign_overlap(int n, uint64_t *mask, const int *scene_of_body, const i
     for (int j = 0; j < nj; ++j) { eu[j] = joint_ab[2 * j]; ev[j] = joint_ab[2 * j + 1]; }
     int *row_ptr, *col;
     build_graph(n, inv_mass, nj, eu, ev, &row_ptr, &col);
-    int64_t *count = counts_from_masks(n, mask, scene_of_body, part_base, n_parts_total);
-    membership m = {mask, scene_of_body, part_base, count};
+    int64_t *count = counts_from_masks(n, mask, scene_of_body, part_base, n_parts_total, NULL);
+    membership m = {mask, scene_of_body, part_base, count, NULL};
     bfs_ws ws;
     bfs_ws_init(&ws, n);
     for (int j = 0; j < nj; ++j) {                              /* Alg 2: joints in order */
@@ -1322,11 +1332,20 @@ int orc_step(orc_sim *s, double dt, int iters) {
             ca[m] = a; cb[m] = b; ++m;
         }
         int do_deact = s->P.lb_deact_every > 0 && (s->step_index % s->P.lb_deact_every) == 0;
-        int64_t *count = counts_from_masks(n, s->mask, s->sob, s->part_base, s->n_parts);
-        membership mem = {s->mask, s->sob, s->part_base, count};
+        int64_t *weight = NULL;
+        if (s->P.lb_load == 1) {   /* 1 + contacts per body, every contact of the step */
+            weight = xcalloc((size_t)n + 1, sizeof(int64_t));
+            for (int b = 0; b < n; ++b) weight[b] = 1;
+            for (int64_t i = 0; i < s->nc; ++i) {
+                weight[s->con[i].a]++;
+                if (s->con[i].b < n) weight[s->con[i].b]++;
+            }
+        }
+        int64_t *count = counts_from_masks(n, s->mask, s->sob, s->part_base, s->n_parts, weight);
+        membership mem = {s->mask, s->sob, s->part_base, count, weight};
         if (s->P.lb_activate || do_deact)
             load_balance_impl(&mem, n, s->row_ptr, s->col, m, ca, cb, s->sgamma, s->P.lb_activate, do_deact);
-        free(count); free(ca); free(cb);
+        free(count); free(weight); free(ca); free(cb);
     }
     for (int b = 0; b < n; ++b)
         if (s->im[b] > 0 && s->mask[b] == 0) return ORC_ERR_MEMBERSHIP;

@@ -124,7 +124,7 @@ void host_assign_overlap(const HostScene &sc, std::vector<uint64_t> &mask);
 // contacts ab: pairs of dynamic bodies in canonical order; graph CSR of G^t;
 // mask [n] updated in place; loads [n_parts]: |P_w| of every worker for
 // these masks; scenes spread over up to `threads` threads (ws.size())
-void host_load_balance(const HostScene &sc, uint64_t *mask, const int *loads, int64_t nc,
+void host_load_balance(const HostScene &sc, uint64_t *mask, const int *loads, const int *deg, int64_t nc,
                        const int2 *ab, const int *row_ptr, const int *col, bool do_activate,
                        bool do_deactivate, std::vector<BallWorkspace> &ws);
 

@@ -143,12 +143,20 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
     CK(cudaMemcpyAsync(c->h_mask.p, c->mask.p, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, s));
     c->lb_loads.ensure((size_t)c->n_parts + 1);
     c->h_loads.ensure((size_t)c->n_parts + 1);
-    launch_worker_loads(c->mask.p, c->sob.p, c->part_base.p, n, c->n_parts, c->lb_loads.p, s);
+    const bool by_contacts = c->P.lb_load == OVL_LB_CONTACTS;
+    if (by_contacts) {
+        c->lb_deg.ensure((size_t)n + 1);
+        c->h_deg.ensure((size_t)n + 1);
+        launch_contact_degree(c->c_ab.p, c->nc, n, c->lb_deg.p, s);
+        CK(cudaMemcpyAsync(c->h_deg.p, c->lb_deg.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+    }
+    launch_worker_loads(c->mask.p, c->sob.p, c->part_base.p, by_contacts ? c->lb_deg.p : nullptr, n,
+                        c->n_parts, c->lb_loads.p, s);
     CK(cudaMemcpyAsync(c->h_loads.p, c->lb_loads.p, sizeof(int) * c->n_parts, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if ((int)c->lb_ws.size() != c->lb_threads) c->lb_ws.resize(c->lb_threads);
-    host_load_balance(c->hs, c->h_mask.p, c->h_loads.p, m, c->h_ab.p, c->h_rp.p, c->h_col.p, act,
-                      deact, c->lb_ws);
+    host_load_balance(c->hs, c->h_mask.p, c->h_loads.p, by_contacts ? c->h_deg.p : nullptr, m, c->h_ab.p,
+                      c->h_rp.p, c->h_col.p, act, deact, c->lb_ws);
     CK(cudaMemcpyAsync(c->mask.p, c->h_mask.p, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     c->lb_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -808,6 +816,10 @@ ovl_status ovl_create(ovl_ctx **out, const ovl_params *p, void *cuda_stream) {
     ovl_ctx *c = new (std::nothrow) ovl_ctx();
     if (!c) return OVL_ERR_ARG;
     if (p) c->P = *p; else ovl_default_params(&c->P);
+    if (c->P.lb_load != OVL_LB_BODIES && c->P.lb_load != OVL_LB_CONTACTS) {
+        delete c;
+        return OVL_ERR_ARG;
+    }
     ovl_status st = guarded(c, [&]() -> ovl_status {
         CK(cudaGetDevice(&c->device));
         CK(cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));

@@ -102,6 +102,8 @@ struct ovl_ctx {
     std::vector<BallWorkspace> lb_ws;
     DBuf<int> lb_loads;
     HBuf<int> h_loads;
+    DBuf<int> lb_deg;          // contacts per body (contact load)
+    HBuf<int> h_deg;
 
     // last step
     int64_t step_index = 0;

@@ -17,22 +17,23 @@ namespace {
 
 inline int popcount(uint64_t x) { return __builtin_popcountll(x); }
 
-// Live |P_w| per global worker plus the activate / deactivate primitives of
-// Table 1.  Workers and bodies of different scenes are disjoint index ranges,
-// so one instance may be used by several threads that each touch only their
-// own scenes.
+// Live load per global worker plus the activate / deactivate primitives of
+// Table 1.  The load is |P_w|, or with contact counts deg the sum of
+// 1 + deg[b] over the worker's active bodies.  Workers and bodies of
+// different scenes are disjoint index ranges, so one instance may be used by
+// several threads that each touch only their own scenes.
 class Membership {
   public:
     Membership(const HostScene &sc, uint64_t *mask) : sc_(sc), mask_(mask), load_(sc.n_parts, 0) {}
-    Membership(const HostScene &sc, uint64_t *mask, const int *loads)
-        : sc_(sc), mask_(mask), load_(loads, loads + sc.n_parts) {}
+    Membership(const HostScene &sc, uint64_t *mask, const int *loads, const int *deg)
+        : sc_(sc), mask_(mask), deg_(deg), load_(loads, loads + sc.n_parts) {}
     // |P_w| of the workers of scenes [s0, s1) from the masks
     void count(int s0, int s1) {
         for (int b = sc_.body_base[s0]; b < sc_.body_base[s1]; ++b) {
             uint64_t m = mask_[b];
             int base = sc_.part_base[sc_.sob[b]];
             while (m) {
-                ++load_[base + __builtin_ctzll(m)];
+                load_[base + __builtin_ctzll(m)] += weight(b);
                 m &= m - 1;
             }
         }
@@ -42,23 +43,23 @@ class Membership {
     void activate(uint64_t workers, int b) {
         uint64_t add = workers & ~mask_[b];
         int base = sc_.part_base[sc_.sob[b]];
-        for (uint64_t m = add; m; m &= m - 1) ++load_[base + __builtin_ctzll(m)];
+        for (uint64_t m = add; m; m &= m - 1) load_[base + __builtin_ctzll(m)] += weight(b);
         mask_[b] |= add;
     }
     void deactivate(uint64_t workers, int b) {
         uint64_t rem = workers & mask_[b];
         int base = sc_.part_base[sc_.sob[b]];
-        for (uint64_t m = rem; m; m &= m - 1) --load_[base + __builtin_ctzll(m)];
+        for (uint64_t m = rem; m; m &= m - 1) load_[base + __builtin_ctzll(m)] -= weight(b);
         mask_[b] &= ~rem;
     }
-    // <W>: active bodies summed over the workers of W (Table 1)
+    // <W>: active bodies (or their weights) summed over the workers of W (Table 1)
     int64_t load(uint64_t workers, int scene) const {
         int64_t s = 0;
         int base = sc_.part_base[scene];
         for (uint64_t m = workers; m; m &= m - 1) s += load_[base + __builtin_ctzll(m)];
         return s;
     }
-    // worker of W with the fewest active bodies, lowest index on ties
+    // worker of W with the smallest load, lowest index on ties
     int least_loaded(uint64_t workers, int scene) const {
         int base = sc_.part_base[scene];
         int best = -1;
@@ -74,8 +75,10 @@ class Membership {
     }
 
   private:
+    int64_t weight(int b) const { return deg_ ? 1 + (int64_t)deg_[b] : 1; }
     const HostScene &sc_;
     uint64_t *mask_;
+    const int *deg_ = nullptr;
     std::vector<int64_t> load_;
 };
 
@@ -235,12 +238,12 @@ void load_balance_range(const HostScene &sc, Membership &mem, const int2 *ab, in
 // Contacts of one scene are contiguous in that order and touch only that
 // scene's masks and worker loads, so runs of whole scenes go to up to
 // `threads` host threads; the result is the sequential one.
-void host_load_balance(const HostScene &sc, uint64_t *mask, const int *loads, int64_t nc,
+void host_load_balance(const HostScene &sc, uint64_t *mask, const int *loads, const int *deg, int64_t nc,
                        const int2 *ab, const int *row_ptr, const int *col, bool do_activate,
                        bool do_deactivate, std::vector<BallWorkspace> &ws) {
     if (nc == 0 || (!do_activate && !do_deactivate) || ws.empty()) return;
     const int threads = (int)ws.size();
-    Membership mem(sc, mask, loads);
+    Membership mem(sc, mask, loads, deg);
     // candidate range of every scene
     std::vector<int64_t> first(sc.ns + 1, nc);
     for (int64_t i = nc - 1; i >= 0; --i) first[sc.sob[ab[i].x]] = i;

@@ -344,8 +344,16 @@ namespace {
 
 // |P_w| of every worker: one count per set bit of every mask; a block-local
 // histogram when the workers fit shared memory
-__global__ void k_worker_loads(const uint64_t *mask, const int *sob, const int *part_base, int n,
-                               int P, int *loads) {
+__global__ void k_contact_degree(const int2 *__restrict__ c_ab, int nc, int n, int *__restrict__ deg) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        const int2 e = c_ab[i];
+        atomicAdd(&deg[e.x], 1);
+        if (e.y < n) atomicAdd(&deg[e.y], 1);
+    }
+}
+
+__global__ void k_worker_loads(const uint64_t *mask, const int *sob, const int *part_base,
+                               const int *deg, int n, int P, int *loads) {
     extern __shared__ int hist[];
     const bool local = P <= 8192;
     if (local) {
@@ -356,10 +364,11 @@ __global__ void k_worker_loads(const uint64_t *mask, const int *sob, const int *
         uint64_t m = mask[b];
         if (!m) continue;
         const int base = part_base[sob[b]];
+        const int wt = deg ? 1 + deg[b] : 1;
         while (m) {
             const int w = __ffsll((long long)m) - 1;
             m &= m - 1;
-            atomicAdd(local ? &hist[base + w] : &loads[base + w], 1);
+            atomicAdd(local ? &hist[base + w] : &loads[base + w], wt);
         }
     }
     if (local) {
@@ -371,12 +380,20 @@ __global__ void k_worker_loads(const uint64_t *mask, const int *sob, const int *
 
 }  // namespace
 
-void launch_worker_loads(const uint64_t *mask, const int *sob, const int *part_base, int n, int P,
-                         int *loads, cudaStream_t s) {
+void launch_contact_degree(const int2 *c_ab, int nc, int n, int *deg, cudaStream_t s) {
+    CK(cudaMemsetAsync(deg, 0, sizeof(int) * (size_t)n, s));
+    if (nc <= 0) return;
+    k_contact_degree<<<grid1d(nc, 256), 256, 0, s>>>(c_ab, nc, n, deg);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_worker_loads(const uint64_t *mask, const int *sob, const int *part_base, const int *deg, int n,
+                         int P, int *loads, cudaStream_t s) {
     CK(cudaMemsetAsync(loads, 0, sizeof(int) * (size_t)P, s));
     if (n <= 0) return;
     const int smem = P <= 8192 ? P * (int)sizeof(int) : 0;
-    k_worker_loads<<<std::min(grid1d(n, 256), 152 * 2), 256, smem, s>>>(mask, sob, part_base, n, P, loads);
+    k_worker_loads<<<std::min(grid1d(n, 256), 152 * 2), 256, smem, s>>>(mask, sob, part_base, deg, n, P, loads);
     note_launch();
     CK(cudaGetLastError());
 }

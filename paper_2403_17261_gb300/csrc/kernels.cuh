@@ -44,7 +44,10 @@ void launch_edge_fill(const int2 *c_ab, int nc, const int2 *jab, int nj, const f
                       const int *tptr, int *cursor, int *tcol, cudaStream_t s);
 void launch_adj_unique(const int *tptr, int n, int *tcol, int *ucount, cudaStream_t s);
 // loads [P] := |P_w| of every worker from the masks
-void launch_worker_loads(const uint64_t *mask, const int *sob, const int *part_base, int n, int P,
+// number of contacts each body is an end of (planes and static ends included)
+void launch_contact_degree(const int2 *c_ab, int nc, int n, int *deg, cudaStream_t s);
+// load of every worker: sum over its active bodies of 1 (+ deg[b] when deg != NULL)
+void launch_worker_loads(const uint64_t *mask, const int *sob, const int *part_base, const int *deg, int n, int P,
                          int *loads, cudaStream_t s);
 void launch_lb_flags(const int2 *c_ab, int nc, const float *im, int n, const uint64_t *mask,
                      int disjoint_only, int *flag, cudaStream_t s);

@@ -30,6 +30,7 @@ OVL_FLAG_TIMING = 2
 OVL_FLAG_AUTOTUNE = 4
 OVL_FLAG_FEATURES = 8
 OVL_WS_PREVIOUS, OVL_WS_MLP, OVL_WS_MLP_NEW = 0, 1, 2
+OVL_LB_BODIES, OVL_LB_CONTACTS = 0, 1
 OVL_MLP_N_PARAMS = 5187
 OVL_N_FEATURES = 12
 
@@ -57,7 +58,8 @@ class ovl_params(C.Structure):
                 ("slop", C.c_float), ("warmstart", C.c_float), ("lb_activate", C.c_int32),
                 ("lb_deact_every", C.c_int32), ("res_tol", C.c_float),
                 ("res_check_every", C.c_int32), ("pgs_threads", C.c_int32), ("flags", C.c_int32),
-                ("pgs_cluster", C.c_int32), ("smem_slot_limit", C.c_int32)]
+                ("pgs_cluster", C.c_int32), ("smem_slot_limit", C.c_int32),
+                ("lb_load", C.c_int32)]
 
 
 _fp, _ip, _u64p, _u8p = C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint8)

@@ -275,6 +275,39 @@ def pile_large(seed: int = 2, side: int = 64, n_sets: int = 64, z0: float = 24.0
                    steps=300, lb_deact_every=10)
 
 
+def box_planes(half: float) -> np.ndarray:
+    """Floor z = 0 and four walls at x, y = +-half, facing inwards."""
+    return np.array([[0, 0, 1, 0], [1, 0, 0, -half], [-1, 0, 0, -half],
+                     [0, 1, 0, -half], [0, -1, 0, -half]], dtype=np.float64)
+
+
+def pile_mixed(seed: int = 5, side: int = 64, n_sets: int = 64, big_radius: float = 1.5,
+               big_layers: int = 2) -> Scene:
+    """Bodies with very unequal contact counts, standing in for the floor
+    pieces of the paper's Building scene (Section 6): big_layers layers of big
+    spheres (radius big_radius, square lattice of spacing 2 big_radius + 0.25)
+    resting on the floor of a box, under side^3 small spheres (spacing 1.25,
+    r~U(0.4,0.6)); density 1.  A big sphere ends up touching tens of small
+    ones, a small one about six.  mu=0.6, dt=1/60, 30 iterations; sets from
+    k-means on the initial positions; growth depth 2, weight search depth 6;
+    load-balance removals every 10 steps."""
+    rng = SplitMix64(seed)
+    width = side * 1.25
+    sp_big = 2.0 * big_radius + 0.25
+    nbig = max(1, int(round(width / sp_big)))
+    half = max(width, nbig * sp_big) / 2.0 + 0.25
+    big = _lattice_pile(nbig, nbig, big_layers, sp_big, big_radius + 0.01, 0.0, rng)
+    small = _lattice_pile(side, side, side, 1.25, big_layers * sp_big + 0.5, 0.0, rng)
+    pos = np.concatenate([big, small])
+    r = np.concatenate([np.full(big.shape[0], big_radius),
+                        rng.uniform(small.shape[0], 0.4, 0.6).astype(np.float32).astype(np.float64)])
+    mass = (4.0 / 3.0) * math.pi * r ** 3
+    sets = kmeans_sets(pos.astype(np.float32), n_sets, seed)
+    return _single("pile_mixed", pos, r, 1.0 / mass, box_planes(half), mu=0.6, dt=1.0 / 60.0,
+                   flags=1, gamma=2, beta=6, n_sets=n_sets, set_of_body=sets, iters=30,
+                   steps=300, lb_deact_every=10)
+
+
 def _uneven_sets(rng: SplitMix64, order: np.ndarray, n_sets: int) -> np.ndarray:
     """Cut the given body order at sorted U(0,1) fractions into n_sets pieces."""
     n = order.shape[0]
@@ -527,5 +560,6 @@ WORKLOADS = {
     "pile_small": pile_small,
     "chain": chain,
     "pile_large": pile_large,
+    "pile_mixed": pile_mixed,
     "batched": batched,
 }

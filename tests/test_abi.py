@@ -38,3 +38,28 @@ def test_binding_fails_loudly_without_library(tmp_path):
 def test_oracle_builds():
     from oracle import oracle as O
     assert os.path.exists(O.build())
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structures have the header's size and field
+    offsets (a field added on one side only would shift every later one)."""
+    import subprocess
+    from paper_2403_17261_gb300 import ovl
+    structs = {"ovl_params": ovl.ovl_params, "ovl_scene_desc": ovl.ovl_scene_desc,
+               "ovl_stats": ovl.ovl_stats, "ovl_train_desc": ovl.ovl_train_desc}
+    lines = []
+    for name, py in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in py._fields_:
+            lines.append(f'printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ovl.h"\nint main(void) {\n'
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, py in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(py), name
+        for f in py._fields_:
+            assert got[(name, f[0])] == getattr(py, f[0]).offset, (name, f[0])

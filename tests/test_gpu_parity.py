@@ -65,6 +65,30 @@ def test_batched_scenes(n_scenes, hi):
     assert rep["contacts"] > 100
 
 
+@pytest.mark.parametrize("warm", [45, 60, 70])
+def test_contact_load_balance(warm):
+    """Algorithm 6 with the contact load on a pile of big and small spheres
+    (bodies with very unequal contact counts): the step's records match the
+    oracle, membership bit for bit, and from the same inputs the body-count
+    load decides differently (so the weights are what is being checked)."""
+    from oracle import oracle as O
+    P = _parity()
+    sc = S.pile_mixed(seed=5, side=8, n_sets=4)
+    orc, gpu = P.prepare(sc, warm_steps=warm, params=dict(lb_load=1))
+    try:
+        by_count = O.OracleSim(sc, dict(lb_load=0))
+        by_count.set_state(orc.state())
+        by_count.set_masks(orc.masks())
+        by_count.set_warmstart(*orc.warmstart())
+        by_count.set_step_index(orc.step_index())
+        rep = P.compare_step(orc, gpu)
+        assert rep["contacts"] > 300
+        by_count.step()
+        assert not np.array_equal(by_count.masks(), gpu.membership())
+    finally:
+        gpu.close()
+
+
 def test_closed_forms_on_gpu():
     from paper_2403_17261_gb300 import ovl
     sc = S.resting_sphere()

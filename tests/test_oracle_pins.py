@@ -161,6 +161,84 @@ def test_lb_removal_branches_respect_cadence():
 
 
 # ---------------------------------------------------------------------------
+# The contact load (Section 6): <W> sums 1 + contacts over active bodies
+# ---------------------------------------------------------------------------
+
+def _lb_w(masks, n_sets, contacts, weights, act=True, deact=True):
+    masks = np.array(masks, dtype=np.uint64)
+    n = masks.shape[0]
+    rp, col = O.graph(n, np.ones(n), list(contacts))
+    return O.load_balance(masks, np.zeros(n, np.int32), [n_sets], rp, col,
+                          np.array(contacts, dtype=np.int32).reshape(-1, 2), [0], act, deact,
+                          weights=np.array(weights, dtype=np.int64))
+
+
+def test_contact_load_flips_the_activation_side():
+    # the case of test_lb_inter_worker_goes_to_lighter_side with B carrying
+    # weight 10: <W_A> = 4 <= <W_B> = 10, so now B joins W_A
+    out = _lb_w([1, 2, 1, 1, 1], 2, [(0, 1)], [1, 10, 1, 1, 1])
+    assert list(out) == [1, 3, 1, 1, 1]
+    # unit weights are the body count
+    assert list(_lb_w([1, 2, 1, 1, 1], 2, [(0, 1)], [1] * 5)) == [3, 2, 1, 1, 1]
+
+
+def test_contact_load_is_live():
+    # worker 0 = {0, 2} (load 2), worker 1 = {1, 3} (weights 5 + 1 = 6).
+    # Contact (0, 1): 2 <= 6, body 1 joins worker 0, whose load becomes 7 --
+    # by body 1's weight, not by 1.  Contact (2, 3): 7 > 6, so body 2 joins
+    # worker 1.  (Adding 1 instead would give 3 <= 6 and body 3 joining worker 0.)
+    out = _lb_w([1, 2, 1, 2], 2, [(0, 1), (2, 3)], [1, 5, 1, 1])
+    assert list(out) == [1, 3, 3, 2]
+
+
+def test_contact_load_least_loaded_keep():
+    # the case of test_lb_two_overlap_bodies_keep_least_loaded: by count
+    # worker 1 is kept; with body 4 (worker 1 only) weighing 5, worker 0's
+    # load 4 is below worker 1's 7 and worker 0 is kept
+    out = _lb_w([3, 3, 1, 1, 2], 2, [(0, 1)], [1, 1, 1, 1, 5])
+    assert list(out) == [1, 1, 1, 1, 2]
+
+
+def _corner_scene(extra_w1):
+    """Sphere A (worker 0) in the corner of a floor z = 0 and a wall x = 0,
+    touching both; sphere B (worker 1) resting on A along the diagonal, clear
+    of both planes; free spheres far above: one in worker 0, extra_w1 in
+    worker 1.  A's contacts: floor, wall, B (weight 4); B's: A (weight 2)."""
+    h = 1.0 / np.sqrt(2.0)
+    pos = [(0.5, 5.0, 0.5), (0.5 + h, 5.0, 0.5 + h), (20.0, 5.0, 30.0)]
+    sets = [0, 1, 0]
+    for k in range(extra_w1):
+        pos.append((20.0 + 3.0 * (k + 1), 5.0, 30.0))
+        sets.append(1)
+    n = len(pos)
+    planes = [(0.0, 0.0, 1.0, 0.0), (1.0, 0.0, 0.0, 0.0)]
+    return S._single("corner", np.array(pos), np.full(n, 0.5), np.ones(n), planes, mu=0.5,
+                     dt=1.0 / 60.0, flags=1, gamma=0, beta=2, n_sets=2, set_of_body=sets,
+                     iters=10, steps=1)
+
+
+def test_contact_load_counts_every_contact_of_the_step():
+    # bodies: <W_0> = 2 <= <W_1> = 3, B joins worker 0.  Contacts: <W_0> =
+    # 4 + 1 = 5 > <W_1> = 2 + 1 + 1 = 4, A joins worker 1 -- only if both plane
+    # contacts of A count (without them A weighs 2 and <W_0> = 3).
+    out = {}
+    for load in (0, 1):
+        sim = O.OracleSim(_corner_scene(2), dict(lb_load=load))
+        sim.step()
+        out[load] = [int(m) for m in sim.masks()[:2]]
+    assert out[0] == [1, 3]
+    assert out[1] == [3, 2]
+
+
+def test_contact_load_counts_the_body_itself():
+    # four free spheres in worker 1: <W_0> = 4 + 1 = 5 <= <W_1> = 2 + 4 = 6 and
+    # B joins worker 0 -- only with the 1 per body (contacts alone: 3 > 1)
+    sim = O.OracleSim(_corner_scene(4), dict(lb_load=1))
+    sim.step()
+    assert [int(m) for m in sim.masks()[:2]] == [1, 3]
+
+
+# ---------------------------------------------------------------------------
 # Geodesic distances and weights (Eq 15-16, Algorithm 5)
 # ---------------------------------------------------------------------------
 
