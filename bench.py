@@ -16,9 +16,9 @@ iterations/s, a roofline entry for the solver kernel, the FP64 oracle timed on
 the host as CPU baseline, an end-to-end figure through the C ABI with host
 buffers, SM clocks sampled during the timed region.
 
-``--workload pile_mixed``: 1250 big spheres (radius 1.5, two layers) on the
-floor of a box under the same 64^3 lattice of small ones; each big sphere takes
-tens of contacts.  With ``--lb-load contacts`` Algorithm 6 compares loads that
+``--workload pile_mixed``: 6728 big spheres (radius 1.25, two layers) on the
+floor of a box under a 128 x 128 x 16 lattice of small ones (r ~ U(0.4,0.6));
+each big sphere takes tens of contacts.  With ``--lb-load contacts`` Algorithm 6 compares loads that
 count 1 + contacts per active body instead of bodies (Section 6's proposal);
 the line then reports the per-worker row imbalance (max / mean) next to the
 throughput.
@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ovl", choices=["ovl", "reference"])
     ap.add_argument("--workload", default="pile_large",
-                    choices=["pile_large", "pile_mixed", "chain", "pile_small", "batched", "warmstart"],
+                    choices=["pile_large", "pile_mixed", "chain", "pile_small", "batched", "warmstart", "gamma"],
                     help="warmstart: the learned warm start on the large pile (log, train, "
                          "sweeps to RMS residual 1e-4 against the previous-step warm start)")
     ap.add_argument("--ws-log-steps", type=int, default=6)
@@ -77,7 +77,7 @@ def parse():
 
 def default_settle(workload):
     return {"pile_large": 150, "pile_mixed": 150, "chain": 0, "pile_small": 0, "batched": 0,
-            "warmstart": 150}[workload]
+            "warmstart": 150, "gamma": 0}[workload]
 
 
 def make_scene(workload):
@@ -163,7 +163,7 @@ def oracle_sample_scene(workload):
     if workload in ("pile_large", "warmstart"):
         return S.pile_large(side=16, n_sets=16), 150, "pile_large generator at 16^3 = 4096 bodies, 16 k-means workers, settled 150 steps by the oracle itself (untimed)"
     if workload == "pile_mixed":
-        return S.pile_mixed(side=12, n_sets=16), 150, "pile_mixed generator at 12^3 small + 50 big spheres, 16 k-means workers, settled 150 steps by the oracle itself (untimed)"
+        return S.pile_mixed(side=16, layers=8, n_sets=16), 150, "pile_mixed generator at 16 x 16 x 8 small + 98 big spheres, 16 k-means workers, settled 150 steps by the oracle itself (untimed)"
     if workload == "chain":
         return S.chain(), 0, "the full 4096-sphere chain"
     if workload == "batched":
@@ -420,6 +420,36 @@ def warmstart_arm(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def gamma_arm(args, rank, world, local_rank):
+    """Growth depth sweep and computed-versus-uniform weights on a hanging
+    chain of 512 links in 8 workers, 1000 sweeps (the paper's error-study
+    setting): from 20 states of a single-worker run, one partitioned step per
+    configuration; the joint violation it adds over the single-worker step
+    (per chain length) and the largest velocity deviation."""
+    import torch
+    import __graft_entry__ as g
+    from paper_2403_17261_gb300 import experiments
+
+    torch.cuda.set_device(local_rank)
+    g.build()
+    with ClockSampler(local_rank) as clk:
+        r = experiments.partition_error()
+    if rank != 0:
+        return
+    default = next(t for t in r["runs"] if t["gamma"] == 2 and t["weights"] == "geodesic")
+    line = {
+        "metric": "joint violation added by partitioning in one step / chain length",
+        "value": default["added_violation_over_length"], "unit": "m/m", "higher_is_better": False,
+        "n_gpus": 1, "steps": r["samples"], "warmup": 0, "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"chain {r['chain_links']} spheres, {r['workers']} workers, {r['sweeps']} sweeps, "
+                               "dt 1/120; value at gamma 2, geodesic weights"},
+        "sweep": r["runs"], "single_worker_violation_over_length": r["single_worker_violation_over_length"],
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -430,6 +460,9 @@ def main():
         return
     if args.workload == "warmstart":
         warmstart_arm(args, rank, world, local_rank)
+        return
+    if args.workload == "gamma":
+        gamma_arm(args, rank, world, local_rank)
         return
     if world > 1:
         import torch

@@ -40,7 +40,9 @@ typedef int32_t ovl_status;
 #define OVL_OK 0
 #define OVL_ERR_ARG (-1)        /* bad argument or call order */
 #define OVL_ERR_CUDA (-2)       /* a CUDA call failed */
-#define OVL_ERR_CAPACITY (-3)   /* a fixed limit was exceeded (colours > 64, neighbours > 32, ...) */
+#define OVL_ERR_CAPACITY (-3)   /* a fixed limit was exceeded: colours > 64 in a worker, sphere
+                                   neighbours beyond a body's capacity (set from the radii), a
+                                   worker of 65535 bodies or more, ... */
 #define OVL_ERR_TIMEOUT (-4)    /* a bounded device-side wait gave up */
 #define OVL_ERR_NONFINITE (-5)  /* NaN or Inf in a state */
 #define OVL_ERR_MEMBERSHIP (-6) /* dynamic body with empty W, or a worker index >= n_sets */
@@ -66,7 +68,16 @@ typedef struct ovl_params {
                                 workers use the global-memory path); 0 = as many as fit */
     int32_t lb_load;         /* the load <W_x> Algorithm 6 compares: OVL_LB_BODIES (default) or
                                 OVL_LB_CONTACTS; any other value is OVL_ERR_ARG at ovl_create */
+    int32_t weights;         /* blending weights of overlap bodies: OVL_WEIGHTS_GEODESIC (default)
+                                or OVL_WEIGHTS_UNIFORM; any other value is OVL_ERR_ARG */
 } ovl_params;
+
+/* Blending weights (Section 5.3).  GEODESIC is the method's: Eq 15 weights
+ * proportional to 1 / D(o,i) of Eq 16.  UNIFORM is the naive choice the
+ * paper compares against (Figure 8): every worker of an overlap body weighs
+ * 1 / |W_b|.  The geodesic distances are computed (and readable) either way. */
+#define OVL_WEIGHTS_GEODESIC 0
+#define OVL_WEIGHTS_UNIFORM 1
 
 /* Loads of Algorithm 6.  BODIES is the paper's: <W_x> counts the active
  * bodies of the workers in W_x (Table 1).  CONTACTS is the contact-following
@@ -193,6 +204,15 @@ ovl_status ovl_read_warmstart(ovl_ctx *ctx, int64_t cap, int64_t *n, int32_t *pa
  * weights (Algorithm 5, Eq 15-16) and the blend (Algorithm 4).  dt > 0
  * overrides every scene's timestep; iters = PGS sweeps per worker. */
 ovl_status ovl_step(ovl_ctx *ctx, float dt, int32_t iters);
+
+/* Position-level joint violation of the current blended state (the error
+ * measure of Section 6 for jointed scenes): for every ball joint the gap
+ * |p_B - p_A| between its two pivots, p = x + R(q) anchor for a body end and
+ * the anchor itself for a world end.  *sum gets the sum over all joints,
+ * *max_gap the largest gap (metres); either pointer may be NULL.  FP32 gaps,
+ * summed in FP64 in a fixed order (the result does not depend on timing).
+ * Synchronises the context's stream. */
+ovl_status ovl_joint_error(ovl_ctx *ctx, double *sum, double *max_gap);
 
 /* LOADBALANCE (Algorithm 6 with BRIDGE, Algorithm 7) alone on the contacts
  * of the current state.  flags bit 0: activation branch, bit 1: removal

@@ -23,14 +23,16 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libovl_oracle.so")
 
 DEFAULT_PARAMS = dict(gravity=(0.0, 0.0, -9.81), margin=0.05, erp=0.2, slop=0.001, warmstart=1.0,
-                      lb_activate=1, lb_deact_every=1, res_tol=0.0, res_check_every=0, lb_load=0)
+                      lb_activate=1, lb_deact_every=1, res_tol=0.0, res_check_every=0, lb_load=0,
+                      weights=0)
 
 
 class OrcParams(C.Structure):
     _fields_ = [("gravity", C.c_double * 3), ("margin", C.c_double), ("erp", C.c_double),
                 ("slop", C.c_double), ("warmstart", C.c_double), ("lb_activate", C.c_int),
                 ("lb_deact_every", C.c_int), ("res_tol", C.c_double),
-                ("res_check_every", C.c_int), ("lb_load", C.c_int)]
+                ("res_check_every", C.c_int), ("lb_load", C.c_int),
+                ("weights", C.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -83,6 +85,7 @@ def lib():
         L.orc_get_part_stats.argtypes = [C.c_void_p, ip, dp, i64p, ip]
         L.orc_get_features.argtypes = [C.c_void_p, dp, dp, ip, u8p]
         L.orc_get_metrics.argtypes = [C.c_void_p, dp]
+        L.orc_joint_error.argtypes = [C.c_void_p, dp]
         L.orc_contacts.restype = C.c_int64
         L.orc_contacts.argtypes = [C.c_int, dp, dp, dp, C.c_int, dp, ip, ip, ip, C.c_double, C.c_int,
                                    C.c_int64, ip, dp, dp, dp]
@@ -265,6 +268,7 @@ class OracleSim:
         cp.lb_activate, cp.lb_deact_every = int(p["lb_activate"]), int(p["lb_deact_every"])
         cp.res_tol, cp.res_check_every = float(p["res_tol"]), int(p["res_check_every"])
         cp.lb_load = int(p["lb_load"])
+        cp.weights = int(p["weights"])
         self._params = cp
         self.scene = scene
         self.n = scene.n_bodies
@@ -404,6 +408,12 @@ class OracleSim:
         return dict(iters=it, res_sq=rs, rows=rows, colours=cols)
 
     def metrics(self):
-        out = np.zeros(3)
+        out = np.zeros(4)
         lib().orc_get_metrics(self._h, _ptr(out, dp))
-        return dict(residual_rms=out[0], residual_max=out[1], joint_gap_max=out[2])
+        return dict(residual_rms=out[0], residual_max=out[1], joint_gap_max=out[2], joint_gap_sum=out[3])
+
+    def joint_error(self):
+        """Sum and largest pivot gap over the joints of the current state (m)."""
+        out = np.zeros(2)
+        lib().orc_joint_error(self._h, _ptr(out, dp))
+        return dict(sum=float(out[0]), max=float(out[1]))

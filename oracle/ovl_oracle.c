@@ -103,6 +103,7 @@ typedef struct {
     double res_tol;      /* > 0: a worker stops sweeping once its RMS residual <= res_tol */
     int res_check_every; /* sweeps between residual checks when res_tol > 0 */
     int lb_load;         /* 0: <W> counts active bodies (Table 1); 1: contact load (above) */
+    int weights;         /* 0: Eq 15-16 weights; 1: uniform 1/|W_b| (the naive weights of Fig 8) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -840,8 +841,14 @@ typedef struct {
     uint8_t *depth;     /* n: BFS distance in G^t to O, capped at ORC_DEPTH_CAP */
     int *part_iters; double *part_res_sq; int64_t *part_rows; int *part_colours;
     double res_sq_total; double res_max; int64_t res_rows;
-    double joint_violation_max;
+    double joint_violation_max, joint_violation_sum;
 } orc_sim;
+
+/* Position-level joint violation of the current state (Section 6's error
+ * measure for jointed scenes): per ball joint the gap |p_B - p_A| between its
+ * pivots, p = x + R(q) anchor for a body end, the anchor for a world end.
+ * out[0] = sum over joints, out[1] = largest gap. */
+void orc_joint_error(const orc_sim *s, double *out);
 
 orc_sim *orc_create(const orc_params *P, int n, const double *state13, const double *radius,
                     const double *inv_mass, int n_planes, const double *planes,
@@ -1367,6 +1374,7 @@ int orc_step(orc_sim *s, double dt, int iters) {
         int64_t e0 = s->entry_ptr[b];
         int k = (int)(s->entry_ptr[b + 1] - e0);
         if (k == 1) s->weight[e0] = 1.0;
+        else if (k > 1 && s->P.weights == 1) for (int i = 0; i < k; ++i) s->weight[e0 + i] = 1.0 / k;
         else if (k > 1) orc_weights(k, s->D + e0, s->weight + e0);
     }
     /* constraints of every worker: all dynamic ends active there; contacts
@@ -1469,18 +1477,11 @@ int orc_step(orc_sim *s, double dt, int iters) {
         }
     }
     /* joint error after the step (position level) */
-    s->joint_violation_max = 0;
-    for (int j = 0; j < s->nj; ++j) {
-        int a = s->jab[2 * j], b = s->jab[2 * j + 1];
-        const double *anc = s->janc + 6 * (size_t)j;
-        double pA[3], pB[3], r[3], R[9];
-        if (a >= 0) { const double *x = s->st + 13 * (size_t)a; quat_to_matrix(x + 3, R); mat_vec(R, anc, r); for (int k = 0; k < 3; ++k) pA[k] = x[k] + r[k]; }
-        else for (int k = 0; k < 3; ++k) pA[k] = anc[k];
-        if (b >= 0) { const double *x = s->st + 13 * (size_t)b; quat_to_matrix(x + 3, R); mat_vec(R, anc + 3, r); for (int k = 0; k < 3; ++k) pB[k] = x[k] + r[k]; }
-        else for (int k = 0; k < 3; ++k) pB[k] = anc[3 + k];
-        double d[3] = {pB[0] - pA[0], pB[1] - pA[1], pB[2] - pA[2]};
-        double L = sqrt(dot3(d, d));
-        if (L > s->joint_violation_max) s->joint_violation_max = L;
+    {
+        double je[2];
+        orc_joint_error(s, je);
+        s->joint_violation_sum = je[0];
+        s->joint_violation_max = je[1];
     }
     /* keep impulses for the next step's warm start */
     free(s->ws);
@@ -1554,9 +1555,41 @@ void orc_get_part_stats(const orc_sim *s, int *iters, double *res_sq, int64_t *r
     memcpy(colours, s->part_colours, (size_t)s->n_parts * sizeof(int));
 }
 
-/* [rms residual over all rows of all workers, max |residual|, max joint gap] */
+/* [rms residual over all rows of all workers, max |residual|, max joint gap,
+ *  sum of joint gaps] after the last step */
 void orc_get_metrics(const orc_sim *s, double *out) {
     out[0] = s->res_rows > 0 ? sqrt(s->res_sq_total / (double)s->res_rows) : 0.0;
     out[1] = s->res_max;
     out[2] = s->joint_violation_max;
+    out[3] = s->joint_violation_sum;
+}
+
+void orc_joint_error(const orc_sim *s, double *out) {
+    out[0] = 0.0;
+    out[1] = 0.0;
+    for (int j = 0; j < s->nj; ++j) {
+        int a = s->jab[2 * j], b = s->jab[2 * j + 1];
+        const double *anc = s->janc + 6 * (size_t)j;
+        double pA[3], pB[3], r[3], R[9];
+        if (a >= 0) {
+            const double *x = s->st + 13 * (size_t)a;
+            quat_to_matrix(x + 3, R);
+            mat_vec(R, anc, r);
+            for (int k = 0; k < 3; ++k) pA[k] = x[k] + r[k];
+        } else {
+            for (int k = 0; k < 3; ++k) pA[k] = anc[k];
+        }
+        if (b >= 0) {
+            const double *x = s->st + 13 * (size_t)b;
+            quat_to_matrix(x + 3, R);
+            mat_vec(R, anc + 3, r);
+            for (int k = 0; k < 3; ++k) pB[k] = x[k] + r[k];
+        } else {
+            for (int k = 0; k < 3; ++k) pB[k] = anc[3 + k];
+        }
+        double d[3] = {pB[0] - pA[0], pB[1] - pA[1], pB[2] - pA[2]};
+        double L = sqrt(dot3(d, d));
+        out[0] += L;
+        if (L > out[1]) out[1] = L;
+    }
 }

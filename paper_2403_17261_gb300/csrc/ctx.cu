@@ -40,11 +40,15 @@ ovl_status check_device_status(ovl_ctx *c) {
     switch (s) {
         case DEV_OK: return OVL_OK;
         case DEV_ERR_CAPACITY:
-            return fail(c, OVL_ERR_CAPACITY, "a body has more than 32 sphere neighbours of larger index");
+            return fail(c, OVL_ERR_CAPACITY,
+                        "a body touches more spheres of larger index than its neighbour capacity "
+                        "(set from the radii: deep interpenetration)");
+        case DEV_ERR_SLOTS: return fail(c, OVL_ERR_CAPACITY, "a worker holds 65535 bodies or more");
         case DEV_ERR_NONFINITE: return fail(c, OVL_ERR_NONFINITE, "non-finite value in the blended state");
         case DEV_ERR_MEMBERSHIP:
             return fail(c, OVL_ERR_MEMBERSHIP, "dynamic body with no worker, or a worker index out of range");
-        case DEV_ERR_COLOURS: return fail(c, OVL_ERR_CAPACITY, "a worker needs more than 128 colours");
+        case DEV_ERR_COLOURS:
+            return fail(c, OVL_ERR_CAPACITY, "a worker needs more than 64 colours (bodies in about 64 or more constraints)");
         case DEV_ERR_TIMEOUT: return fail(c, OVL_ERR_TIMEOUT, "colouring did not finish within its round limit");
         default: return fail(c, OVL_ERR_CUDA, "unknown device status");
     }
@@ -64,7 +68,7 @@ void phase_contacts(ovl_ctx *c) {
     c->bucket_start.ensure((size_t)c->tsize + 1);
     c->cursor.ensure(c->tsize);
     c->items.ensure(n);
-    c->nb_list.ensure((size_t)n * OVL_MAX_NEIGH);
+    c->nb_list.ensure((size_t)c->nb_total + 1);
     c->nb_count.ensure(n);
     c->ccount.ensure((size_t)n + 1);
     c->cstart.ensure((size_t)n + 1);
@@ -76,7 +80,8 @@ void phase_contacts(ovl_ctx *c) {
     a.cell = c->cell.p; a.bucket_count = c->bucket_count.p; a.bucket_start = c->bucket_start.p;
     a.cursor = c->cursor.p; a.items = c->items.p; a.planes = c->planes.p;
     a.plane_ptr = c->plane_ptr.p; a.plane_list = c->plane_list.p; a.margin = c->P.margin;
-    a.nb_list = c->nb_list.p; a.nb_count = c->nb_count.p; a.contact_count = c->ccount.p;
+    a.nb_list = c->nb_list.p; a.nb_off = c->nb_off.p; a.nb_count = c->nb_count.p;
+    a.contact_count = c->ccount.p;
     a.contact_start = c->cstart.p; a.status = c->status.p;
     launch_cells(a, s);
     scan_i32(c->bucket_count.p, c->bucket_start.p, (int)c->tsize, c->scan_tmp, s);
@@ -728,6 +733,7 @@ void phase_blend(ovl_ctx *c, float dt_override) {
     a.n = c->n; a.entry_ptr = c->entry_ptr.p; a.D = c->D.p; a.copies = c->copies.p; a.st_in = c->st.p;
     a.st_out = c->st_alt.p; a.weight = c->weight.p; a.status = c->status.p;
     a.sob = c->sob.p; a.scene_dt = c->scene_dt.p; a.dt_override = dt_override;
+    a.uniform = c->P.weights == OVL_WEIGHTS_UNIFORM;
     launch_blend(a, c->stream);
     std::swap(c->st, c->st_alt);
     // the impulses of this step become the next step's warm-start cache
@@ -816,7 +822,8 @@ ovl_status ovl_create(ovl_ctx **out, const ovl_params *p, void *cuda_stream) {
     ovl_ctx *c = new (std::nothrow) ovl_ctx();
     if (!c) return OVL_ERR_ARG;
     if (p) c->P = *p; else ovl_default_params(&c->P);
-    if (c->P.lb_load != OVL_LB_BODIES && c->P.lb_load != OVL_LB_CONTACTS) {
+    if ((c->P.lb_load != OVL_LB_BODIES && c->P.lb_load != OVL_LB_CONTACTS) ||
+        (c->P.weights != OVL_WEIGHTS_GEODESIC && c->P.weights != OVL_WEIGHTS_UNIFORM)) {
         delete c;
         return OVL_ERR_ARG;
     }
@@ -868,7 +875,7 @@ void release_all(ovl_ctx *c) {
     c->joint_scene.release(); c->part_scene.release(); c->planes.release(); c->plane_ptr.release();
     c->plane_list.release(); c->jab.release(); c->janc.release(); c->vb_base.release();
     c->mask.release(); c->cell.release(); c->bucket_count.release(); c->bucket_start.release();
-    c->cursor.release(); c->items.release(); c->nb_list.release(); c->nb_count.release();
+    c->cursor.release(); c->items.release(); c->nb_list.release(); c->nb_count.release(); c->nb_off.release();
     c->ccount.release(); c->cstart.release(); c->c_ab.release(); c->c_n.release(); c->c_t1.release();
     c->deg.release(); c->tptr.release(); c->cursor2.release(); c->tcol.release(); c->ucount.release();
     c->row_ptr.release(); c->col.release(); c->entry_count.release(); c->entry_ptr.release();
@@ -1019,6 +1026,25 @@ ovl_status ovl_scene_upload(ovl_ctx *c, const ovl_scene_desc *d) {
         float rmax = 0.f;
         for (int b = 0; b < n; ++b) rmax = std::max(rmax, d->radius[b]);
         c->cs = (2.f * rmax + c->P.margin) * 1.01f;
+        // Neighbour capacity per body.  Spheres that touch body a (centres
+        // within r_a + r_b + margin) and barely overlap one another are seen
+        // from a's centre under disjoint cones of half-angle at least
+        // asin(r_min / (r_a + r_min + margin)), so at most
+        // 2 / (1 - cos(theta)) of them fit around it; 25 % slack covers the
+        // small penetrations the solver leaves.  Never below OVL_MAX_NEIGH.
+        {
+            std::vector<float> rmin(ns, INFINITY);
+            for (int b = 0; b < n; ++b) rmin[sob[b]] = std::min(rmin[sob[b]], d->radius[b]);
+            std::vector<long long> off(n + 1, 0);
+            for (int b = 0; b < n; ++b) {
+                const double rm = rmin[sob[b]];
+                const double sn = rm / ((double)d->radius[b] + rm + (double)c->P.margin);
+                const double cap = 1.25 * 2.0 / (1.0 - std::sqrt(std::max(0.0, 1.0 - sn * sn)));
+                off[b + 1] = off[b] + std::max<long long>(OVL_MAX_NEIGH, (long long)std::ceil(cap));
+            }
+            c->nb_total = off[n];
+            upload(c->nb_off, off.data(), (size_t)n + 1, s);
+        }
         c->tsize = next_pow2(2ull * (uint64_t)n);
         // host scene for the sequential algorithms
         c->hs.n = n; c->hs.ns = ns; c->hs.n_parts = c->n_parts;
@@ -1144,6 +1170,22 @@ ovl_status ovl_read_state(ovl_ctx *c, float *state13, int32_t on_device) {
         launch_unpack_state(c->st.p, c->n, c->stage13.p, c->stream);
         download(state13, c->stage13.p, 13 * (size_t)c->n, c->stream);
         CK(cudaStreamSynchronize(c->stream));
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_joint_error(ovl_ctx *c, double *sum, double *max_gap) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->has_scene) return fail(c, OVL_ERR_ARG, "no scene");
+        double h[2] = {0.0, 0.0};
+        if (c->nj > 0) {
+            c->jerr.ensure(2);
+            launch_joint_error(c->jab.p, c->janc.p, c->st.p, c->nj, c->jerr.p, c->stream);
+            download(h, c->jerr.p, 2, c->stream);
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        if (sum) *sum = h[0];
+        if (max_gap) *max_gap = h[1];
         return OVL_OK;
     });
 }

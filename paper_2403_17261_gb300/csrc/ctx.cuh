@@ -52,6 +52,8 @@ struct ovl_ctx {
     DBuf<int> status;
     DBuf<int4> cell;
     DBuf<int> bucket_count, bucket_start, cursor, items, nb_list, nb_count, ccount, cstart;
+    DBuf<long long> nb_off;    // per-body neighbour capacity offsets (set at scene upload)
+    long long nb_total = 0;
     DBuf<int2> c_ab;
     DBuf<float4> c_n, c_t1;
     DBuf<int> deg, tptr, cursor2, tcol, ucount, row_ptr, col;
@@ -103,6 +105,7 @@ struct ovl_ctx {
     DBuf<int> lb_loads;
     HBuf<int> h_loads;
     DBuf<int> lb_deg;          // contacts per body (contact load)
+    DBuf<double> jerr;         // joint error: sum, max
     HBuf<int> h_deg;
 
     // last step

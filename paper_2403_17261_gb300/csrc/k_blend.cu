@@ -19,6 +19,7 @@
 // Bodies in one worker take their copy unchanged.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "quat.cuh"
 
 namespace ovl {
 
@@ -109,7 +110,8 @@ __global__ void k_blend(BlendArgs a) {
             for (int i = 0; i < k; ++i) {
                 const size_t e = (size_t)(e0 + i);
                 uint8_t d = a.D[e];
-                float wi = s > 0.f ? (d != 255 ? (1.0f / (float)d) / s : 0.f) : 1.0f / (float)k;
+                float wi = (s > 0.f && !a.uniform) ? (d != 255 ? (1.0f / (float)d) / s : 0.f)
+                                                   : 1.0f / (float)k;
                 a.weight[e] = wi;
                 float4 qi = a.copies[4 * e + 1], vi = a.copies[4 * e + 2], wv = a.copies[4 * e + 3];
                 v.x += wi * vi.x; v.y += wi * vi.y; v.z += wi * vi.z;
@@ -132,6 +134,54 @@ __global__ void k_blend(BlendArgs a) {
         if (!finite) atomicCAS(a.status, DEV_OK, DEV_ERR_NONFINITE);
         a.st_out[4 * b] = o0; a.st_out[4 * b + 1] = o1; a.st_out[4 * b + 2] = o2; a.st_out[4 * b + 3] = o3;
     }
+}
+
+constexpr int JERR_THREADS = 512;
+
+// one CTA: thread t sums the joints t, t + T, ... in FP64, then a fixed tree
+// over the threads, so the sum does not depend on scheduling
+__global__ void __launch_bounds__(JERR_THREADS)
+k_joint_error(const int2 *jab, const float4 *janc, const float4 *st, int nj, double *out) {
+    __shared__ double s_sum[JERR_THREADS];
+    __shared__ float s_max[JERR_THREADS];
+    double sum = 0.0;
+    float mx = 0.f;
+    for (int j = threadIdx.x; j < nj; j += JERR_THREADS) {
+        const int2 ab = jab[j];
+        const float4 anA = janc[2 * j], anB = janc[2 * j + 1];
+        float3 xA, xB, rA = make_float3(0.f, 0.f, 0.f), rB = rA;
+        if (ab.x >= 0) {
+            const float4 x = st[4 * ab.x];
+            xA = make_float3(x.x, x.y, x.z);
+            rA = quat_rotate(st[4 * ab.x + 1], make_float3(anA.x, anA.y, anA.z));
+        } else {
+            xA = make_float3(anA.x, anA.y, anA.z);
+        }
+        if (ab.y >= 0) {
+            const float4 x = st[4 * ab.y];
+            xB = make_float3(x.x, x.y, x.z);
+            rB = quat_rotate(st[4 * ab.y + 1], make_float3(anB.x, anB.y, anB.z));
+        } else {
+            xB = make_float3(anB.x, anB.y, anB.z);
+        }
+        // nearby large coordinates subtracted first, as in the joint rows
+        const float dx = (xB.x - xA.x) + (rB.x - rA.x), dy = (xB.y - xA.y) + (rB.y - rA.y),
+                    dz = (xB.z - xA.z) + (rB.z - rA.z);
+        const float g = sqrtf(dx * dx + dy * dy + dz * dz);
+        sum += (double)g;
+        mx = fmaxf(mx, g);
+    }
+    s_sum[threadIdx.x] = sum;
+    s_max[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = JERR_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s_sum[threadIdx.x] += s_sum[threadIdx.x + w];
+            s_max[threadIdx.x] = fmaxf(s_max[threadIdx.x], s_max[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[0] = s_sum[0]; out[1] = (double)s_max[0]; }
 }
 
 __global__ void k_pack(const float *in, const float *radius, const float *im, int n, float4 *st) {
@@ -171,6 +221,13 @@ void launch_geo_level(const GeoArgs &a, int level, cudaStream_t s) {
     k_geo_level<<<152 * 8, 256, 0, s>>>(a, level);
     note_launch();
     k_geo_mark<<<1, 1, 0, s>>>(a.qctl, level + 1);
+    note_launch();
+    CK(cudaGetLastError());
+}
+
+void launch_joint_error(const int2 *jab, const float4 *janc, const float4 *st, int nj, double *out,
+                        cudaStream_t s) {
+    k_joint_error<<<1, JERR_THREADS, 0, s>>>(jab, janc, st, nj, out);
     note_launch();
     CK(cudaGetLastError());
 }

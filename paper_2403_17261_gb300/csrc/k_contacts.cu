@@ -68,14 +68,18 @@ __global__ void k_find_pairs(const float4 *__restrict__ st, const float *__restr
                              const int *__restrict__ items, uint32_t tmask,
                              const float4 *__restrict__ planes, const int *__restrict__ plane_ptr,
                              const int *__restrict__ plane_list, float margin,
-                             int *__restrict__ nb_list, int *__restrict__ nb_count,
-                             int *__restrict__ contact_count, int *__restrict__ status) {
+                             int *__restrict__ nb_list, const long long *__restrict__ nb_off,
+                             int *__restrict__ nb_count, int *__restrict__ contact_count,
+                             int *__restrict__ status) {
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
         const int s = sob[a];
         const float4 pa = st[4 * a];   // .w = radius
         const bool dyn_a = im[a] > 0.0f;
         int cnt = 0;
         int local[OVL_MAX_NEIGH];
+        int *const gl = nb_list + nb_off[a];
+        const int cap = (int)(nb_off[a + 1] - nb_off[a]);
+        bool spilled = false;   // the list continues in gl (more than OVL_MAX_NEIGH neighbours)
         bool overflow = false;
         if (scene_flags[s] & 1) {
             const int4 ca = cell[a];
@@ -91,23 +95,29 @@ __global__ void k_find_pairs(const float4 *__restrict__ st, const float *__restr
                             if (cb.x != cx || cb.y != cy || cb.z != cz || sob[b] != s) continue;
                             if (!dyn_a && !(im[b] > 0.0f)) continue;
                             if (!pair_touches(pa, st[4 * b], margin)) continue;
-                            if (cnt < OVL_MAX_NEIGH) {
-                                // insertion into the sorted local list
-                                int j = cnt;
-                                while (j > 0 && local[j - 1] > b) {
-                                    local[j] = local[j - 1];
-                                    --j;
-                                }
-                                local[j] = b;
-                                ++cnt;
-                            } else {
-                                overflow = true;
+                            if (!spilled && cnt == OVL_MAX_NEIGH && cap > OVL_MAX_NEIGH) {
+                                for (int j = 0; j < cnt; ++j) gl[j] = local[j];
+                                spilled = true;
                             }
+                            if (cnt >= (spilled ? cap : OVL_MAX_NEIGH)) {
+                                overflow = true;
+                                continue;
+                            }
+                            // insertion into the sorted list
+                            int *lst = spilled ? gl : local;
+                            int j = cnt;
+                            while (j > 0 && lst[j - 1] > b) {
+                                lst[j] = lst[j - 1];
+                                --j;
+                            }
+                            lst[j] = b;
+                            ++cnt;
                         }
                     }
         }
         if (overflow) atomicCAS(status, DEV_OK, DEV_ERR_CAPACITY);
-        for (int j = 0; j < cnt; ++j) nb_list[(size_t)a * OVL_MAX_NEIGH + j] = local[j];
+        if (!spilled)
+            for (int j = 0; j < cnt; ++j) gl[j] = local[j];
         nb_count[a] = cnt;
         int np_ = 0;
         if (dyn_a) {
@@ -142,6 +152,7 @@ __global__ void k_write_contacts(const float4 *__restrict__ st, const float *__r
                                  const int *__restrict__ sob, const float4 *__restrict__ planes,
                                  const int *__restrict__ plane_ptr, const int *__restrict__ plane_list,
                                  float margin, const int *__restrict__ nb_list,
+                                 const long long *__restrict__ nb_off,
                                  const int *__restrict__ nb_count, const int *__restrict__ cstart,
                                  int2 *__restrict__ c_ab, float4 *__restrict__ c_n,
                                  float4 *__restrict__ c_t1) {
@@ -150,7 +161,7 @@ __global__ void k_write_contacts(const float4 *__restrict__ st, const float *__r
         int o = cstart[a];
         const int cnt = nb_count[a];
         for (int j = 0; j < cnt; ++j) {
-            const int b = nb_list[(size_t)a * OVL_MAX_NEIGH + j];
+            const int b = nb_list[nb_off[a] + j];
             const float4 pb = st[4 * b];
             float dx = __fsub_rn(pb.x, pa.x), dy = __fsub_rn(pb.y, pa.y), dz = __fsub_rn(pb.z, pa.z);
             float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
@@ -296,14 +307,14 @@ void launch_bucket_fill(const ContactArgs &a, cudaStream_t s) {
 void launch_find_pairs(const ContactArgs &a, cudaStream_t s) {
     k_find_pairs<<<grid1d(a.n, 128), 128, 0, s>>>(
         a.st, a.im, a.n, a.sob, a.scene_flags, a.cell, a.bucket_start, a.items, a.tmask, a.planes,
-        a.plane_ptr, a.plane_list, a.margin, a.nb_list, a.nb_count, a.contact_count, a.status);
+        a.plane_ptr, a.plane_list, a.margin, a.nb_list, a.nb_off, a.nb_count, a.contact_count, a.status);
     note_launch();
     CK(cudaGetLastError());
 }
 
 void launch_write_contacts(const ContactArgs &a, cudaStream_t s) {
     k_write_contacts<<<grid1d(a.n, 128), 128, 0, s>>>(a.st, a.im, a.n, a.sob, a.planes, a.plane_ptr,
-                                                      a.plane_list, a.margin, a.nb_list,
+                                                      a.plane_list, a.margin, a.nb_list, a.nb_off,
                                                       a.nb_count, a.contact_start, a.c_ab, a.c_n,
                                                       a.c_t1);
     note_launch();

@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "quat.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -532,19 +533,9 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
 // with r_A, r_B the pivot offsets from each body's centre in the world frame.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ float3 quat_rotate(float4 q, float3 v) {
-    // v + 2 w (u x v) + 2 u x (u x v), q = (w, u)
-    float3 u = make_float3(q.y, q.z, q.w);
-    float3 t = make_float3(2.f * (u.y * v.z - u.z * v.y), 2.f * (u.z * v.x - u.x * v.z),
-                           2.f * (u.x * v.y - u.y * v.x));
-    return make_float3(v.x + q.x * t.x + (u.y * t.z - u.z * t.y),
-                       v.y + q.x * t.y + (u.z * t.x - u.x * t.z),
-                       v.z + q.x * t.z + (u.x * t.y - u.y * t.x));
-}
-
 // two 16-bit worker slots in one word (0xffff: static end)
 __device__ __forceinline__ int pack_slots(int2 sl, int *status) {
-    if (sl.x >= 0xffff || sl.y >= 0xffff) atomicCAS(status, DEV_OK, DEV_ERR_CAPACITY);
+    if (sl.x >= 0xffff || sl.y >= 0xffff) atomicCAS(status, DEV_OK, DEV_ERR_SLOTS);
     unsigned a = sl.x < 0 ? 0xffffu : (unsigned)sl.x & 0xffffu;
     unsigned b = sl.y < 0 ? 0xffffu : (unsigned)sl.y & 0xffffu;
     return (int)(a | (b << 16));

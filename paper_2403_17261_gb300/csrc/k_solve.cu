@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveAr
     const int b0 = a.part_bstart[p], nb = a.part_bstart[p + 1] - b0;
     const int per = (nb + C - 1) / C;
     if (nb >= 0xffff) {
-        if (rank == 0 && threadIdx.x == 0) atomicCAS(a.status, DEV_OK, DEV_ERR_CAPACITY);
+        if (rank == 0 && threadIdx.x == 0) atomicCAS(a.status, DEV_OK, DEV_ERR_SLOTS);
         return;
     }
     // this CTA's row buckets (three offsets per colour), read in every colour

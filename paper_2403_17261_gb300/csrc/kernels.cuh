@@ -25,7 +25,8 @@ struct ContactArgs {
     const int *plane_ptr;  // [n_scenes+1]
     const int *plane_list; // plane indices grouped by scene, ascending
     float margin;
-    int *nb_list;          // [n][OVL_MAX_NEIGH]
+    int *nb_list;          // per body a range of nb_off[b + 1] - nb_off[b] entries
+    const long long *nb_off; // [n+1] neighbour-list offsets (per-body capacity from the radii)
     int *nb_count;         // [n]
     int *contact_count;    // [n+1]
     int *contact_start;    // [n+1]
@@ -232,9 +233,14 @@ struct BlendArgs {
     const int *sob;
     const float *scene_dt;
     float dt_override;
+    int uniform;               // 1: weights 1 / |W_b| instead of Eq 15-16
     int *status;
 };
 void launch_blend(const BlendArgs &a, cudaStream_t s);
+// sum and max of the pivot gaps of nj ball joints over a [n] x 4 float4 state
+// (out[0] = sum, out[1] = max); one CTA, fixed reduction order
+void launch_joint_error(const int2 *jab, const float4 *janc, const float4 *st, int nj, double *out,
+                        cudaStream_t s);
 
 // state conversion [n][13] <-> 64-byte records
 void launch_pack_state(const float *in13, const float *radius, const float *im, int n, float4 *st,

@@ -31,6 +31,7 @@ OVL_FLAG_AUTOTUNE = 4
 OVL_FLAG_FEATURES = 8
 OVL_WS_PREVIOUS, OVL_WS_MLP, OVL_WS_MLP_NEW = 0, 1, 2
 OVL_LB_BODIES, OVL_LB_CONTACTS = 0, 1
+OVL_WEIGHTS_GEODESIC, OVL_WEIGHTS_UNIFORM = 0, 1
 OVL_MLP_N_PARAMS = 5187
 OVL_N_FEATURES = 12
 
@@ -38,7 +39,7 @@ EXPORTED = [
     "ovl_default_params", "ovl_create", "ovl_destroy", "ovl_last_error", "ovl_phase_name",
     "ovl_scene_upload", "ovl_set_partition", "ovl_set_membership", "ovl_read_membership",
     "ovl_assign_overlap", "ovl_set_state", "ovl_read_state", "ovl_set_step_index",
-    "ovl_set_warmstart", "ovl_read_warmstart", "ovl_step", "ovl_load_balance", "ovl_sync",
+    "ovl_set_warmstart", "ovl_read_warmstart", "ovl_step", "ovl_load_balance", "ovl_sync", "ovl_joint_error",
     "ovl_read_stats", "ovl_read_contacts", "ovl_read_graph", "ovl_read_entries", "ovl_read_pairs",
     "ovl_read_worker_stats", "ovl_autotune_export", "ovl_autotune_import",
     "ovl_geodesics_static", "ovl_set_warmstart_mode", "ovl_read_features", "ovl_mlp_set_params",
@@ -59,7 +60,7 @@ class ovl_params(C.Structure):
                 ("lb_deact_every", C.c_int32), ("res_tol", C.c_float),
                 ("res_check_every", C.c_int32), ("pgs_threads", C.c_int32), ("flags", C.c_int32),
                 ("pgs_cluster", C.c_int32), ("smem_slot_limit", C.c_int32),
-                ("lb_load", C.c_int32)]
+                ("lb_load", C.c_int32), ("weights", C.c_int32)]
 
 
 _fp, _ip, _u64p, _u8p = C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint8)
@@ -121,6 +122,7 @@ def load_library(path: str | None = None):
         "ovl_read_warmstart": [vp, C.c_int64, C.POINTER(C.c_int64), _ip, _u64p, _fp],
         "ovl_step": [vp, C.c_float, C.c_int32],
         "ovl_load_balance": [vp, C.c_int32],
+        "ovl_joint_error": [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "ovl_sync": [vp],
         "ovl_read_stats": [vp, C.POINTER(ovl_stats)],
         "ovl_read_contacts": [vp, _ip, _fp, _fp, _fp],
@@ -437,6 +439,12 @@ class Simulation:
 
     def load_balance(self, flags: int = 3):
         ovl_load_balance(self.ctx, flags)
+
+    def joint_error(self) -> dict:
+        """Sum and largest pivot gap over the joints of the current state (m)."""
+        s, m = C.c_double(), C.c_double()
+        _check(self.ctx, load_library().ovl_joint_error(self.ctx, C.byref(s), C.byref(m)))
+        return dict(sum=s.value, max=m.value)
 
     def sync(self):
         ovl_sync(self.ctx)

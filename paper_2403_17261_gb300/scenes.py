@@ -207,18 +207,21 @@ def _chain_geometry(n, span, drop, ground_z, radius):
     return centres, np.array(joints, dtype=np.int32), np.array(anchors), ell
 
 
-def chain(seed: int = 1, n: int = 4096, n_sets: int = 8) -> Scene:
+def chain(seed: int = 1, n: int = 4096, n_sets: int = 8, gamma: int = 2, beta: int | None = None,
+          iters: int = 50) -> Scene:
     """Hanging chain: n spheres r=0.1, m~U(0.5,2), ball joints, ends fixed to
     world anchors 300 m apart, ground plane at z=-50 (the lower run rests on it).
-    8 contiguous sets; articulated overlap assignment with growth depth 2,
-    weight search depth 6; dt=1/120, 50 iterations, 120 steps."""
+    8 contiguous sets; articulated overlap assignment with growth depth gamma
+    (2), weight search depth beta (2 gamma + 2); dt=1/120, 50 iterations, 120
+    steps."""
     rng = SplitMix64(seed)
     centres, joints, anchors, ell = _chain_geometry(n, 300.0, 50.0, -50.0, 0.1)
     mass = rng.uniform(n, 0.5, 2.0)
     sets = (np.arange(n) * n_sets) // n
     sc = _single("chain", centres, np.full(n, 0.1), 1.0 / mass, [[0, 0, 1, -50.0]],
-                 mu=0.5, dt=1.0 / 120.0, flags=0, gamma=2, beta=6, n_sets=n_sets,
-                 set_of_body=sets, joints=joints, anchors=anchors, iters=50, steps=120,
+                 mu=0.5, dt=1.0 / 120.0, flags=0, gamma=gamma,
+                 beta=2 * gamma + 2 if beta is None else beta, n_sets=n_sets,
+                 set_of_body=sets, joints=joints, anchors=anchors, iters=iters, steps=120,
                  lb_deact_every=1, assign_overlap=True)
     sc.meta["link_length"] = ell
     return sc
@@ -281,23 +284,24 @@ def box_planes(half: float) -> np.ndarray:
                      [0, 1, 0, -half], [0, -1, 0, -half]], dtype=np.float64)
 
 
-def pile_mixed(seed: int = 5, side: int = 64, n_sets: int = 64, big_radius: float = 1.5,
-               big_layers: int = 2) -> Scene:
+def pile_mixed(seed: int = 5, side: int = 128, layers: int = 16, n_sets: int = 64,
+               big_radius: float = 1.25, big_layers: int = 2) -> Scene:
     """Bodies with very unequal contact counts, standing in for the floor
     pieces of the paper's Building scene (Section 6): big_layers layers of big
     spheres (radius big_radius, square lattice of spacing 2 big_radius + 0.25)
-    resting on the floor of a box, under side^3 small spheres (spacing 1.25,
-    r~U(0.4,0.6)); density 1.  A big sphere ends up touching tens of small
-    ones, a small one about six.  mu=0.6, dt=1/60, 30 iterations; sets from
-    k-means on the initial positions; growth depth 2, weight search depth 6;
-    load-balance removals every 10 steps."""
+    resting on the floor of a box, under a side x side x layers lattice of
+    small spheres (spacing 1.25, r~U(0.4,0.6)); density 1.  The default has
+    262,144 small and 6728 big spheres; a settled big sphere touches tens of
+    small ones, a small one about six.  mu=0.6, dt=1/60, 30 iterations; sets
+    from k-means on the initial positions; growth depth 2, weight search
+    depth 6; load-balance removals every 10 steps."""
     rng = SplitMix64(seed)
     width = side * 1.25
     sp_big = 2.0 * big_radius + 0.25
     nbig = max(1, int(round(width / sp_big)))
     half = max(width, nbig * sp_big) / 2.0 + 0.25
     big = _lattice_pile(nbig, nbig, big_layers, sp_big, big_radius + 0.01, 0.0, rng)
-    small = _lattice_pile(side, side, side, 1.25, big_layers * sp_big + 0.5, 0.0, rng)
+    small = _lattice_pile(side, side, layers, 1.25, big_layers * sp_big + 0.5, 0.0, rng)
     pos = np.concatenate([big, small])
     r = np.concatenate([np.full(big.shape[0], big_radius),
                         rng.uniform(small.shape[0], 0.4, 0.6).astype(np.float32).astype(np.float64)])

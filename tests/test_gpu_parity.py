@@ -1,5 +1,7 @@
 """GPU parity: the CUDA path against the FP64 oracle, one step from identical
 inputs, every record compared (see tests/parity.py for the tolerances)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -73,7 +75,7 @@ def test_contact_load_balance(warm):
     load decides differently (so the weights are what is being checked)."""
     from oracle import oracle as O
     P = _parity()
-    sc = S.pile_mixed(seed=5, side=8, n_sets=4)
+    sc = S.pile_mixed(seed=5, side=8, layers=8, n_sets=4)
     orc, gpu = P.prepare(sc, warm_steps=warm, params=dict(lb_load=1))
     try:
         by_count = O.OracleSim(sc, dict(lb_load=0))
@@ -85,6 +87,66 @@ def test_contact_load_balance(warm):
         assert rep["contacts"] > 300
         by_count.step()
         assert not np.array_equal(by_count.masks(), gpu.membership())
+    finally:
+        gpu.close()
+
+
+@pytest.mark.parametrize("weights", [0, 1])
+def test_chain_weights_and_joint_error(weights):
+    """The chain with Eq 15-16 weights or uniform ones: the step matches the
+    oracle and uniform weights are exactly 1/|W_b|.  The joint violation the
+    library measures matches the oracle's on the same FP32 state, before and
+    after the step: the pivot differences of nearby coordinates are exact in
+    FP32, so each gap is off by rotation and square-root rounding only
+    (well below 1e-7 m for pivots 0.05 m from their centres)."""
+    P = _parity()
+    sc = S.chain()
+    nj = sc.joints.shape[0]
+    orc, gpu = P.prepare(sc, warm_steps=3, params=dict(weights=weights))
+    try:
+        def same_state_check():
+            jo, jg = orc.joint_error(), gpu.joint_error()
+            assert jo["sum"] > 1e-3
+            assert abs(jg["sum"] - jo["sum"]) <= nj * 1e-7 and abs(jg["max"] - jo["max"]) <= 1e-7, (jo, jg)
+
+        same_state_check()
+        P.compare_step(orc, gpu)
+        e = gpu.entries()
+        k = np.diff(e["entry_ptr"])
+        kk = np.repeat(k, k)
+        shared = kk > 1
+        assert shared.sum() > 20
+        if weights == 1:
+            np.testing.assert_array_equal(e["weight"][shared], (1.0 / kk[shared]).astype(np.float32))
+        assert abs(orc.metrics()["joint_gap_sum"] - orc.joint_error()["sum"]) <= 1e-12
+        orc.set_state(orc.state().astype(np.float32).astype(np.float64))
+        gpu.set_state(orc.state().astype(np.float32))
+        same_state_check()
+    finally:
+        gpu.close()
+
+
+def test_contacts_beyond_the_register_list():
+    """A sphere of radius 2 ringed by 60 spheres of radius 0.4 on its surface
+    (golden-angle spiral): its neighbour list outgrows the 32 entries kept in
+    registers and continues in its own global range; contacts, colours and
+    the step still match the oracle."""
+    P = _parity()
+    k = 60
+    i = np.arange(k) + 0.5
+    z = 1.0 - 2.0 * i / k
+    phi = i * math.pi * (3.0 - math.sqrt(5.0))
+    rr = np.sqrt(1.0 - z * z)
+    u = np.stack([rr * np.cos(phi), rr * np.sin(phi), z], axis=1)
+    pos = np.concatenate([[[0.0, 0.0, 10.0]], [0.0, 0.0, 10.0] + 2.399 * u])
+    rad = np.concatenate([[2.0], np.full(k, 0.4)])
+    sc = S._single("ringed", pos, rad, np.ones(k + 1), [], mu=0.5, dt=1.0 / 60.0, flags=1, gamma=0,
+                   beta=2, n_sets=1, set_of_body=np.zeros(k + 1, np.int32))
+    orc, gpu = P.prepare(sc, params=dict(gravity=(0.0, 0.0, 0.0)))
+    try:
+        rep = P.compare_step(orc, gpu)
+        ab = orc.contacts()[0]
+        assert (ab[:, 0] == 0).sum() == k and rep["contacts"] >= k
     finally:
         gpu.close()
 

@@ -239,6 +239,71 @@ def test_contact_load_counts_the_body_itself():
 
 
 # ---------------------------------------------------------------------------
+# Joint violation (Section 6's error measure) and uniform weights (Figure 8)
+# ---------------------------------------------------------------------------
+
+def _pair_scene(pos, joints, anchors):
+    n = len(pos)
+    return S._single("pair", np.array(pos, dtype=np.float64), np.full(n, 0.1), np.ones(n), [],
+                     mu=0.5, dt=1.0 / 60.0, flags=0, gamma=0, beta=2, n_sets=1,
+                     set_of_body=np.zeros(n, np.int32), joints=joints, anchors=anchors)
+
+
+def test_joint_error_closed_forms():
+    # bodies at (0,0,0) and (2,0,0), pivot halfway: no gap
+    sc = _pair_scene([(0, 0, 0), (2, 0, 0)], [(0, 1)], [(1, 0, 0, -1, 0, 0)])
+    sim = O.OracleSim(sc)
+    assert sim.joint_error() == dict(sum=0.0, max=0.0)
+    st = sim.state()
+    st[1, 1] += 0.3                                   # B moved sideways: gap 0.3
+    sim.set_state(st)
+    assert sim.joint_error()["sum"] == pytest.approx(0.3, abs=1e-15)
+    st = sim.state()
+    st[1, 1] -= 0.3
+    c = math.cos(math.pi / 4)
+    st[0, 3:7] = (c, 0.0, 0.0, c)                     # A turned 90 degrees about z
+    sim.set_state(st)
+    # A's pivot moves from (1,0,0) to (0,1,0); B's stays at (1,0,0)
+    assert sim.joint_error()["max"] == pytest.approx(math.sqrt(2.0), abs=1e-12)
+    # a world end: the world pivot itself
+    sc = _pair_scene([(0, 0, 0), (3, 0, 0)], [(-1, 0), (1, -1)],
+                     [(-1, 0, 0, -1, 0, 0), (0, 0, 0.5, 3, 0, 0)])
+    sim = O.OracleSim(sc)
+    e = sim.joint_error()
+    assert e["sum"] == pytest.approx(0.5, abs=1e-15) and e["max"] == pytest.approx(0.5, abs=1e-15)
+
+
+def _weight_chain(weights):
+    # six bodies in a jointed row; workers {0}, {0}, {0,1}, {0,1}, {1}, {1}
+    pos = [(float(i), 0.0, 5.0) for i in range(6)]
+    joints = [(i, i + 1) for i in range(5)]
+    anchors = [(0.5, 0, 0, -0.5, 0, 0)] * 5
+    n = 6
+    sc = S._single("row", np.array(pos), np.full(n, 0.1), np.ones(n), [], mu=0.5, dt=1.0 / 60.0,
+                   flags=0, gamma=0, beta=3, n_sets=2, set_of_body=[0, 0, 0, 1, 1, 1],
+                   joints=joints, anchors=anchors, lb_activate=0, lb_deact_every=0)
+    sim = O.OracleSim(sc, dict(weights=weights))
+    sim.set_masks(np.array([1, 1, 3, 3, 2, 2], np.uint64))
+    sim.step()
+    return sim.entries()
+
+
+def test_uniform_weights_against_geodesic():
+    g, u = _weight_chain(0), _weight_chain(1)
+    assert np.array_equal(g["D"], u["D"])
+    # body 2: one hop from worker 0's body 1, two from worker 1's body 4
+    e2 = slice(int(g["entry_ptr"][2]), int(g["entry_ptr"][3]))
+    assert list(g["D"][e2]) == [1, 2]
+    np.testing.assert_allclose(g["weight"][e2], [2 / 3, 1 / 3], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(u["weight"][e2], [0.5, 0.5], rtol=0, atol=0)
+    e3 = slice(int(g["entry_ptr"][3]), int(g["entry_ptr"][4]))
+    np.testing.assert_allclose(g["weight"][e3], [1 / 3, 2 / 3], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(u["weight"][e3], [0.5, 0.5], rtol=0, atol=0)
+    # single-worker bodies weigh 1 either way
+    assert u["weight"][0] == 1.0 and u["weight"][-1] == 1.0
+
+
+# ---------------------------------------------------------------------------
 # Geodesic distances and weights (Eq 15-16, Algorithm 5)
 # ---------------------------------------------------------------------------
 
