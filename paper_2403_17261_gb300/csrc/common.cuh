@@ -51,10 +51,13 @@ template <class T>
 struct DBuf {
     T *p = nullptr;
     size_t cap = 0;
+    // grows to twice the request: per-step sizes (pairs, entries) keep
+    // rising while a pile settles, and every reallocation frees and maps
+    // device memory (cudaFree waits for the device)
     void ensure(size_t n) {
         if (n <= cap && p) return;
         if (p) CK(cudaFree(p));
-        size_t c = n < 16 ? 16 : n + n / 4;
+        size_t c = n < 16 ? 16 : 2 * n;
         CK(cudaMalloc(&p, c * sizeof(T)));
         cap = c;
     }
@@ -73,7 +76,7 @@ struct HBuf {
     void ensure(size_t n) {
         if (n <= cap && p) return;
         if (p) CK(cudaFreeHost(p));
-        size_t c = n < 16 ? 16 : n + n / 4;
+        size_t c = n < 16 ? 16 : 2 * n;
         CK(cudaMallocHost(&p, c * sizeof(T)));
         cap = c;
     }
@@ -118,7 +121,7 @@ struct HostScene {
 // breadth-first workspaces of the load balance, one per host thread, kept
 // across steps (epoch-stamped, so never cleared)
 struct BallWorkspace {
-    std::vector<int> seen, depth, out;
+    std::vector<int> seen, out;
     int epoch = 0;
 };
 

@@ -90,7 +90,6 @@ class Ball {
     Ball(BallWorkspace &w, int n, int lo = 0) : w_(w), lo_(lo) {
         if ((int)w_.seen.size() < n) {
             w_.seen.assign(n, 0);
-            w_.depth.assign(n, 0);
             w_.epoch = 0;
         }
     }
@@ -101,20 +100,24 @@ class Ball {
         }
         const int ep = w_.epoch;
         std::vector<int> &out = w_.out;
+        int *seen = w_.seen.data() - lo_;
         out.clear();
         out.push_back(root);
-        w_.seen[root - lo_] = ep;
-        w_.depth[root - lo_] = 0;
-        for (size_t head = 0; head < out.size(); ++head) {
-            int u = out[head];
-            if (w_.depth[u - lo_] == depth) continue;
-            for (int k = row_ptr[u]; k < row_ptr[u + 1]; ++k) {
-                int v = col[k];
-                if (w_.seen[v - lo_] == ep) continue;
-                w_.seen[v - lo_] = ep;
-                w_.depth[v - lo_] = w_.depth[u - lo_] + 1;
-                out.push_back(v);
+        seen[root] = ep;
+        // level by level: [lvl0, lvl1) holds the vertices at distance d
+        size_t lvl0 = 0, lvl1 = 1;
+        for (int d = 0; d < depth && lvl0 < lvl1; ++d) {
+            for (size_t i = lvl0; i < lvl1; ++i) {
+                const int u = out[i];
+                for (int k = row_ptr[u]; k < row_ptr[u + 1]; ++k) {
+                    const int v = col[k];
+                    if (seen[v] == ep) continue;
+                    seen[v] = ep;
+                    out.push_back(v);
+                }
             }
+            lvl0 = lvl1;
+            lvl1 = out.size();
         }
         return out;
     }
@@ -185,9 +188,14 @@ void load_balance_range(const HostScene &sc, Membership &mem, const int2 *ab, in
     Ball ball(bw, widest, sc.body_base[s0]);
     int ball_scene = -1;
     auto bridge = [&](int b) {                                  // Algorithm 7
+        // the union of the neighbours' workers has more than one worker:
+        // decided as soon as two different workers have been seen
         uint64_t u = 0;
-        for (int k = row_ptr[b]; k < row_ptr[b + 1]; ++k) u |= mem.W(col[k]);
-        return popcount(u) > 1;
+        for (int k = row_ptr[b]; k < row_ptr[b + 1]; ++k) {
+            u |= mem.W(col[k]);
+            if (u & (u - 1)) return true;
+        }
+        return false;
     };
     constexpr int64_t kAhead = 16;   // candidates between a prefetch and its use
     for (int64_t i = i0; i < i1; ++i) {
