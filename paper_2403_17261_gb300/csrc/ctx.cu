@@ -284,12 +284,24 @@ void colour_config(ovl_ctx *c, int *cluster, int *slots) {
     *slots = cap;
 }
 
-// Shared-memory body slots per CTA (24 B each) for 1 or 2 resident CTAs per SM
+// Dynamic shared memory a solver CTA may use with 1 or 2 resident CTAs per SM
+// (the solver's static shared memory -- row-bucket offsets, reductions -- is
+// under 1 KB)
+int solve_smem_budget(ovl_ctx *c, int ctas_per_sm) {
+    return ctas_per_sm == 1 ? c->smem_optin - 2 * 1024 : (c->smem_per_sm / 2) - 3 * 1024;
+}
+
+// Shared-memory body slots per CTA (24 B each, the layout without masses: the
+// CTA counts are planned with it, so adding the masses never adds CTAs)
 int solve_slot_capacity(ovl_ctx *c, int ctas_per_sm) {
-    // the solver's static shared memory (row-bucket offsets, reductions) is under 1 KB
-    int avail = ctas_per_sm == 1 ? c->smem_optin - 2 * 1024 : (c->smem_per_sm / 2) - 3 * 1024;
-    int n = std::max(0, avail / 24);
+    int n = std::max(0, solve_smem_budget(c, ctas_per_sm) / solve_smem_bytes(1, false));
     return c->P.smem_slot_limit > 0 ? std::min(n, c->P.smem_slot_limit) : n;
+}
+
+// a launch keeps the masses in shared memory (32 B per slot) when its slots
+// still fit that way
+bool solve_masses_fit(ovl_ctx *c, int slots, int ctas_per_sm) {
+    return c->P.smem_slot_limit <= 0 && solve_smem_bytes(slots, true) <= solve_smem_budget(c, ctas_per_sm);
 }
 
 // Per-worker CTA counts for the default launch: every worker starts at the
@@ -328,8 +340,11 @@ int default_solve_shape(const ovl_ctx *c) { return c->n_parts <= c->num_sms ? 0 
 // unless its bodies need more).  Workers with equal counts form one class,
 // listed by count, then most constraints first; their order goes to `buf`.
 // Returns false if some worker does not fit 8 CTAs.
-bool plan_worker_classes(ovl_ctx *c, int cap, long long budget, std::vector<SolveClass> &classes,
-                         DBuf<uint32_t> &buf) {
+// CTA count of every worker: the fewest of 1, 2, 3, 4, 6, 8 whose shares fit
+// `cap` slots; then, while the total stays within `budget`, the worker with
+// the most rows per CTA moves up (at most OVL_SOLVE_MAX_GROW).  Empty if some
+// worker needs more than 8.
+std::vector<int> plan_worker_counts(ovl_ctx *c, int cap, long long budget) {
     const int P = c->n_parts;
     const std::vector<int> &pb = c->h_pb, &pp = c->h_pp;
     static const int kSizes[] = {1, 2, 3, 4, 6, 8};
@@ -340,7 +355,7 @@ bool plan_worker_classes(ovl_ctx *c, int cap, long long budget, std::vector<Solv
         const int nb = pb[p + 1] - pb[p];
         int k = 1;
         while (k && (nb + k - 1) / k > cap) k = next(k);
-        if (!k) return false;
+        if (!k) return {};
         C[p] = k;
         total += k;
     }
@@ -360,6 +375,15 @@ bool plan_worker_classes(ovl_ctx *c, int cap, long long budget, std::vector<Solv
             std::push_heap(heap.begin(), heap.end(), less);
         }
     }
+    return C;
+}
+
+// launch classes of a CTA-count plan: workers with equal counts, most CTAs
+// first and longest first inside; the worker order goes to buf
+void plan_classes_from(ovl_ctx *c, const std::vector<int> &C, std::vector<SolveClass> &classes,
+                       DBuf<uint32_t> &buf) {
+    const int P = c->n_parts;
+    const std::vector<int> &pb = c->h_pb, &pp = c->h_pp;
     std::vector<int> order(P);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -377,13 +401,53 @@ bool plan_worker_classes(ovl_ctx *c, int cap, long long budget, std::vector<Solv
     std::vector<uint32_t> o(order.begin(), order.end());
     upload(buf, o.data(), o.size(), c->stream);
     c->h_class_C.assign(C.begin(), C.end());
+}
+
+bool plan_worker_classes(ovl_ctx *c, int cap, long long budget, std::vector<SolveClass> &classes,
+                         DBuf<uint32_t> &buf) {
+    const std::vector<int> C = plan_worker_counts(c, cap, budget);
+    if (C.empty() && c->n_parts > 0) return false;
+    plan_classes_from(c, C, classes, buf);
     return true;
 }
 
+// fewest CTAs of a plan before any growth (sum of the minimal counts)
+long long fewest_ctas(ovl_ctx *c, int cap) {
+    static const int kSizes[] = {1, 2, 3, 4, 6, 8};
+    long long total = 0;
+    for (int p = 0; p < c->n_parts; ++p) {
+        const int nb = c->h_pb[p + 1] - c->h_pb[p];
+        int k = 0;
+        for (int x : kSizes)
+            if ((nb + x - 1) / x <= cap) { k = x; break; }
+        if (!k) return -1;
+        total += k;
+    }
+    return total;
+}
+
+// The per-worker plan keeps the masses in shared memory (32 B per body; two
+// records per contact row, about 15 % less time per row) when the fewest CTAs
+// that hold every worker that way fit the SMs at once, or when even 24 B per
+// body (masses in the rows) needs several waves of CTAs (many small workers).
+// Otherwise -- large workers that overflow one wave only slightly at 24 B per
+// body -- it plans 24 B per body, and classes whose slots still fit take the
+// masses.  (Measured on the large pile: planning 32 B per body past one wave
+// made the solve up to 40 % slower than the 24 B plan.)
 bool plan_solve_classes(ovl_ctx *c, const SolveShape &shape, std::vector<SolveClass> &classes) {
-    return plan_worker_classes(c, solve_slot_capacity(c, shape.per_sm),
-                               (long long)shape.per_sm * c->num_sms - OVL_SOLVE_SM_SLACK, classes,
-                               c->class_order);
+    const long long budget = (long long)shape.per_sm * c->num_sms - OVL_SOLVE_SM_SLACK;
+    const long long slots = (long long)shape.per_sm * c->num_sms;
+    const int cap_plain = solve_slot_capacity(c, shape.per_sm);
+    int cap = cap_plain;
+    if (c->P.smem_slot_limit <= 0) {
+        const int cap_m = solve_smem_budget(c, shape.per_sm) / solve_smem_bytes(1, true);
+        const long long with_m = fewest_ctas(c, cap_m), plain = fewest_ctas(c, cap_plain);
+        if (with_m > 0 && (with_m <= slots || plain < 0 || plain > 2 * slots)) cap = cap_m;
+    }
+    const std::vector<int> C = plan_worker_counts(c, cap, budget);
+    if (C.empty() && c->n_parts > 0) return false;
+    plan_classes_from(c, C, classes, c->class_order);
+    return true;
 }
 
 // launches on the context's stream and its side streams, then joins them
@@ -408,7 +472,8 @@ void launch_solve_classes(ovl_ctx *c, const SolveArgs &a, const SolveShape &shap
         b.n_parts = classes[k].count;
         b.order = c->class_order.p + classes[k].first;
         b.smem_slots = classes[k].slots;
-        launch_solve(b, shape.threads, classes[k].C, shape.unroll, sk);
+        launch_solve(b, shape.threads, classes[k].C, shape.unroll,
+                     solve_masses_fit(c, classes[k].slots, shape.per_sm), sk);
     });
 }
 
@@ -457,6 +522,7 @@ void phase_colour(ovl_ctx *c) {
 void phase_rows(ovl_ctx *c, float dt_override) {
     const int npr = c->npairs;
     c->r0.ensure(npr + 1); c->r1.ensure(npr + 1); c->r2.ensure(npr + 1); c->r3.ensure(npr + 1);
+    c->r4.ensure(npr + 1);
     c->rpair.ensure(npr + 1); c->rlam.ensure(npr + 1);
     RowArgs a{};
     a.n = c->n; a.nc = c->nc; a.np = npr; a.pair_of_row = c->pair_of_row2.p; a.ps_cons = c->ps_cons.p;
@@ -465,7 +531,7 @@ void phase_rows(ovl_ctx *c, float dt_override) {
     a.joint_scene = c->joint_scene.p; a.st = c->st.p; a.sob = c->sob.p; a.part_scene = c->part_scene.p;
     a.scene_dt = c->scene_dt.p; a.scene_mu = c->scene_mu.p; a.dt_override = dt_override;
     a.erp = c->P.erp; a.slop = c->P.slop;
-    a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
+    a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.r4 = c->r4.p; a.rlam = c->rlam.p;
     a.rpair = c->rpair.p; a.status = c->status.p;
     launch_rows(a, c->stream);
 }
@@ -519,7 +585,8 @@ SolveArgs solve_args(ovl_ctx *c, float dt_override, int iters) {
     a.entry_body = c->entry_body.p; a.part_ncol = c->part_ncol.p; a.col_off = c->col_off2.p;
     a.part_scene = c->part_scene.p; a.scene_dt = c->scene_dt.p; a.dt_override = dt_override;
     a.gravity = make_float3(c->P.gravity[0], c->P.gravity[1], c->P.gravity[2]);
-    a.st = c->st.p; a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
+    a.st = c->st.p; a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.r4 = c->r4.p;
+    a.rlam = c->rlam.p;
     a.rpair = c->rpair.p; a.scene_mu = c->scene_mu.p; a.n_entries = c->ne;
     a.lam_out = c->lam_out.p; a.copies = c->copies.p; a.scratch = c->solve_scratch.p;
     a.iters = iters; a.flags = c->P.flags;
@@ -590,7 +657,8 @@ void launch_solve_plan(ovl_ctx *c, const SolvePlan &pl, float dt_override, int i
         return;
     }
     a.smem_slots = pl.slots;
-    launch_solve(a, pl.threads, pl.cluster, pl.unroll, c->stream);
+    launch_solve(a, pl.threads, pl.cluster, pl.unroll,
+                 solve_masses_fit(c, pl.slots, solve_ctas_per_sm(pl.unroll)), c->stream);
     c->last_cluster = pl.cluster;
     c->last_threads = pl.threads;
     c->last_unroll = pl.unroll;
@@ -886,7 +954,7 @@ void release_all(ovl_ctx *c) {
     c->part_pcount.release(); c->part_pstart.release(); c->p_colour.release(); c->part_ncol.release(); c->part_rounds.release();
     c->col_off.release(); c->pair_of_row.release(); c->p_key.release(); c->p_slot.release();
     c->p_lam0.release(); c->colour_scratch.release(); c->worklist.release(); c->worklist2.release(); c->wprio.release(); c->wprio2.release(); c->r0.release(); c->r1.release();
-    c->r2.release(); c->rlam.release(); c->lam_out.release(); c->r3.release(); c->rpair.release(); c->ws_pstart.release();
+    c->r2.release(); c->rlam.release(); c->lam_out.release(); c->r3.release(); c->r4.release(); c->rpair.release(); c->ws_pstart.release();
     c->ws_key.release(); c->ws_lam.release(); c->copies.release(); c->solve_scratch.release();
     c->part_iters.release(); c->part_res_sq.release(); c->visited.release(); c->queue.release();
     c->qctl.release(); c->D.release(); c->weight.release(); c->stage13.release(); c->scan_tmp.release();

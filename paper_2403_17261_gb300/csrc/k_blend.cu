@@ -19,7 +19,7 @@
 // Bodies in one worker take their copy unchanged.
 #include "common.cuh"
 #include "kernels.cuh"
-#include "quat.cuh"
+#include "geom.cuh"
 
 namespace ovl {
 

@@ -15,6 +15,7 @@
 // slot range, and each body sorts its own (few) partners.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "geom.cuh"
 
 namespace ovl {
 
@@ -128,24 +129,6 @@ __global__ void k_find_pairs(const float4 *__restrict__ st, const float *__restr
         }
         contact_count[a] = cnt + np_;
     }
-}
-
-// tangent axis: smallest |n_k| of the FP32 normal, ties to the lower index
-__device__ __forceinline__ int tangent_axis(float nx, float ny, float nz) {
-    float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
-    int k = 0;
-    float m = ax;
-    if (ay < m) { k = 1; m = ay; }
-    if (az < m) { k = 2; }
-    return k;
-}
-
-__device__ __forceinline__ float3 tangent_from(float3 n, int k) {
-    float nk = k == 0 ? n.x : (k == 1 ? n.y : n.z);
-    float3 t = make_float3(-nk * n.x, -nk * n.y, -nk * n.z);
-    if (k == 0) t.x += 1.0f; else if (k == 1) t.y += 1.0f; else t.z += 1.0f;
-    float inv = rsqrtf(t.x * t.x + t.y * t.y + t.z * t.z);
-    return make_float3(t.x * inv, t.y * inv, t.z * inv);
 }
 
 __global__ void k_write_contacts(const float4 *__restrict__ st, const float *__restrict__ im, int n,

@@ -7,7 +7,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
-#include "quat.cuh"
+#include "geom.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -526,10 +526,11 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Row records in colour order.  Contacts (sphere-sphere or sphere-plane):
-//   r0 = (n, k_n)  r1 = (t1, k_t)  r2 = (r_a, r_b, target_n, mu)  r3 = (slot_a, slot_b, pair, 0)
+// Row records in colour order (the solver forms t1, t2, k_n and the joint
+// k's itself).  Contacts (sphere-sphere or sphere-plane):
+//   r0 = (n, k_t)  r1 = (r_a, r_b, target_n, slots)  r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b)  r4 = (t1, k_n)
 // Ball joints (rows along the world axes):
-//   r0 = (r_A, target_x)  r1 = (r_B, target_y)  r2 = (k_x, k_y, k_z, target_z)  r3 = (.., .., pair, 1)
+//   r0 = (r_A, target_x)  r1 = (r_B, target_y)  r2 = (target_z, 0, 0, slots)  r3 as for contacts
 // with r_A, r_B the pivot offsets from each body's centre in the world frame.
 // ---------------------------------------------------------------------------
 
@@ -559,14 +560,13 @@ __global__ void k_rows(RowArgs a) {
                 rb = a.st[4 * ab.y].w;
                 if (sl.y >= 0) { imb = a.st[4 * ab.y + 2].w; iib = a.st[4 * ab.y + 3].w; }
             }
-            float kn = 1.0f / (ima + imb);
             float kt = 1.0f / (ima + imb + iia * ra * ra + iib * rb * rb);
             float phi = nphi.w;
             float target = phi > 0.f ? -phi / h : a.erp * fmaxf(-phi - a.slop, 0.f) / h;
-            a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, kn);
-            a.r1[r] = make_float4(t1.x, t1.y, t1.z, kt);
-            a.r2[r] = make_float4(ra, rb, target, __int_as_float(pack_slots(sl, a.status)));
+            a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, kt);
+            a.r1[r] = make_float4(ra, rb, target, __int_as_float(pack_slots(sl, a.status)));
             a.r3[r] = make_float4(ima, imb, iia, iib);
+            a.r4[r] = make_float4(t1.x, t1.y, t1.z, 1.0f / (ima + imb));
         } else {
             const int j = i - a.nc;
             const int2 ab = a.jab[j];

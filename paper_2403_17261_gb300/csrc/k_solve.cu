@@ -4,8 +4,9 @@
 // the new velocities), writing the worker's copy of each body.
 //
 // A worker is solved by a group of C CTAs (a thread-block cluster when C > 1).
-// Its body velocities (24 B per body: v and w) live in the shared memory of
-// the group -- CTA k holds the contiguous slots [k per, (k + 1) per), per =
+// Its bodies live in the shared memory of the group (32 B each: v with 1/m,
+// w with 1/I; or, when that does not fit, 24 B of v and w with the masses in
+// the row records) -- CTA k holds the contiguous slots [k per, (k + 1) per), per =
 // ceil(nb / C), and other CTAs reach them through distributed shared memory
 // (mapa + ld/st.shared::cluster) -- or, for workers too large for that, in a
 // global scratch area solved by one CTA.  Rows are streamed from HBM/L2 in
@@ -14,9 +15,7 @@
 // colours -- the same result as sweeping the constraints one by one in colour
 // order.  Inside a colour every CTA takes the rows whose first dynamic body
 // it holds (the rows are grouped that way beforehand), so most body accesses
-// stay in the CTA's own shared memory.  Inverse masses and inertias come
-// with every row record so the body state stays small enough for two groups'
-// CTAs to share an SM.
+// stay in the CTA's own shared memory.
 //
 // Row model (sphere contact, normal n from a to b, lever arms r_a n and
 // -r_b n, tangents t1 and t2 = n x t1):
@@ -28,13 +27,18 @@
 // Ball joint: three rows along the world axes, w = (v_b + w_b x r_B - v_a - w_a x r_A)_k,
 // k = 1 / (1/m_a + 1/m_b + |r_A x e_k|^2 / I_a + |r_B x e_k|^2 / I_b).
 //
-// Row records (float4 each): contact r0 = (n, k_n), r1 = (t1, k_t),
-// r2 = (r_a, r_b, target, slots), r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b);
-// joint r0 = (r_A, target_x), r1 = (r_B, target_y), r2 = (target_z, 0, 0, slots),
-// r3 as for contacts.  slots = slot_a | slot_b << 16 (0xffff: static end).
+// Row records (float4 each): contact r0 = (n, k_t), r1 = (r_a, r_b, target,
+// slots), r4 = (t1, k_n); joint r0 = (r_A, target_x), r1 = (r_B, target_y),
+// r2 = (target_z, 0, 0, slots); both r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b).
+// slots = slot_a | slot_b << 16 (0xffff: static end).  With the masses in
+// shared memory a contact reads r0 and r1 only, forming t1 = normalise(e_k -
+// (n . e_k) n) (k the axis of the smallest |n_k|) and k_n = 1 / (1/m_a +
+// 1/m_b) with the same operations that wrote r4, so both layouts compute the
+// same bits.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "geom.cuh"
 #include "kernels.cuh"
 
 namespace cg = cooperative_groups;
@@ -61,8 +65,10 @@ __device__ __forceinline__ int slot_a(int s) { int x = s & 0xffff; return x == 0
 __device__ __forceinline__ int slot_b(int s) { int x = (int)((unsigned)s >> 16); return x == 0xffff ? -1 : x; }
 
 // ---- body storage --------------------------------------------------------
-// Plain pointers: one CTA, shared or global memory.
+// Plain pointers: one CTA, shared or global memory.  kMasses: the slots hold
+// the inverse mass and inertia too (else they come with the row).
 struct LocalSlots {
+    static constexpr bool kMasses = false;
     float4 *A;   // (vx, vy, vz, wx)
     float2 *B;   // (wy, wz)
     __device__ __forceinline__ void load(int s, Body &b) const {
@@ -74,6 +80,23 @@ struct LocalSlots {
     __device__ __forceinline__ void store(int s, const Body &b) const {
         A[s] = make_float4(b.v.x, b.v.y, b.v.z, b.w.x);
         B[s] = make_float2(b.w.y, b.w.z);
+    }
+};
+
+struct LocalSlotsM {
+    static constexpr bool kMasses = true;
+    float4 *A;   // (vx, vy, vz, 1/m)
+    float4 *B;   // (wx, wy, wz, 1/I)
+    __device__ __forceinline__ void load(int s, Body &b) const {
+        const float4 x = A[s], y = B[s];
+        b.v = make_float3(x.x, x.y, x.z);
+        b.w = make_float3(y.x, y.y, y.z);
+        b.im = x.w;
+        b.ii = y.w;
+    }
+    __device__ __forceinline__ void store(int s, const Body &b) const {
+        A[s] = make_float4(b.v.x, b.v.y, b.v.z, b.im);
+        B[s] = make_float4(b.w.x, b.w.y, b.w.z, b.ii);
     }
 };
 
@@ -89,6 +112,7 @@ __device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
 // records may move around them.
 template <int C>
 struct ClusterSlots {
+    static constexpr bool kMasses = false;
     uint32_t A, B;   // shared-window offsets of this CTA's arrays (same in every CTA)
     int per;         // slots per CTA
     __device__ __forceinline__ uint32_t owner(int s) const {
@@ -117,12 +141,85 @@ struct ClusterSlots {
     }
 };
 
+// the same with the masses: 2 x 16 B per slot
+template <int C>
+struct ClusterSlotsM {
+    static constexpr bool kMasses = true;
+    uint32_t A, B;
+    int per;
+    __device__ __forceinline__ uint32_t owner(int s) const {
+        uint32_t r = 0;
+#pragma unroll
+        for (int k = 1; k < C; ++k) r += s >= k * per ? 1u : 0u;
+        return r;
+    }
+    __device__ __forceinline__ void load(int s, Body &b) const {
+        const uint32_t r = owner(s), i = (uint32_t)s - r * (uint32_t)per;
+        const uint32_t a = mapa(A + 16u * i, r), c = mapa(B + 16u * i, r);
+        float4 x, y;
+        asm volatile("ld.shared::cluster.v4.f32 {%0,%1,%2,%3}, [%4];"
+                     : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w) : "r"(a));
+        asm volatile("ld.shared::cluster.v4.f32 {%0,%1,%2,%3}, [%4];"
+                     : "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w) : "r"(c));
+        b.v = make_float3(x.x, x.y, x.z);
+        b.w = make_float3(y.x, y.y, y.z);
+        b.im = x.w;
+        b.ii = y.w;
+    }
+    __device__ __forceinline__ void store(int s, const Body &b) const {
+        const uint32_t r = owner(s), i = (uint32_t)s - r * (uint32_t)per;
+        const uint32_t a = mapa(A + 16u * i, r), c = mapa(B + 16u * i, r);
+        asm volatile("st.shared::cluster.v4.f32 [%0], {%1,%2,%3,%4};"
+                     :: "r"(a), "f"(b.v.x), "f"(b.v.y), "f"(b.v.z), "f"(b.im));
+        asm volatile("st.shared::cluster.v4.f32 [%0], {%1,%2,%3,%4};"
+                     :: "r"(c), "f"(b.w.x), "f"(b.w.y), "f"(b.w.z), "f"(b.ii));
+    }
+};
+
+// One row as the solver reads it: x = r0, y = r1, z = r2 (joints), m = r3
+// and t = r4 (contacts) when the slots do not carry the masses.
+struct Row {
+    float4 x, y, z, m, t;
+    bool joint;
+};
+
 template <class S>
-__device__ __forceinline__ void load_pair(const S &st, int slots, float4 m, Body &A, Body &B) {
+__device__ __forceinline__ void fetch_row(const SolveArgs &a, int r, bool joint, Row &w) {
+    w.joint = joint;
+    w.x = a.r0[r];
+    w.y = a.r1[r];
+    if (joint) w.z = a.r2[r];
+    if (!S::kMasses) {
+        w.m = a.r3[r];
+        if (!joint) w.t = a.r4[r];
+    }
+}
+
+__device__ __forceinline__ int row_slots(const Row &w) { return __float_as_int(w.joint ? w.z.w : w.y.w); }
+
+// a static end (or a body not active in this worker) has zero velocity,
+// inverse mass and inverse inertia
+template <class S>
+__device__ __forceinline__ void load_pair(const S &st, const Row &w, Body &A, Body &B) {
+    const int slots = row_slots(w);
     const int sa = slot_a(slots), sb = slot_b(slots);
-    if (sa >= 0) st.load(sa, A); else { A.v = make_float3(0.f, 0.f, 0.f); A.w = A.v; }
-    if (sb >= 0) st.load(sb, B); else { B.v = make_float3(0.f, 0.f, 0.f); B.w = B.v; }
-    A.im = m.x; B.im = m.y; A.ii = m.z; B.ii = m.w;
+    if (sa >= 0) st.load(sa, A); else { A.v = make_float3(0.f, 0.f, 0.f); A.w = A.v; A.im = 0.f; A.ii = 0.f; }
+    if (sb >= 0) st.load(sb, B); else { B.v = make_float3(0.f, 0.f, 0.f); B.w = B.v; B.im = 0.f; B.ii = 0.f; }
+    if (!S::kMasses) { A.im = w.m.x; B.im = w.m.y; A.ii = w.m.z; B.ii = w.m.w; }
+}
+
+// t1 and k_n of a contact: read, or formed as the row build forms them
+template <class S>
+__device__ __forceinline__ void contact_frame(const Row &w, const Body &A, const Body &B, float3 &t1,
+                                              float &kn) {
+    if (S::kMasses) {
+        const float3 n = make_float3(w.x.x, w.x.y, w.x.z);
+        t1 = tangent_from(n, tangent_axis(n.x, n.y, n.z));
+        kn = 1.0f / (A.im + B.im);
+    } else {
+        t1 = make_float3(w.t.x, w.t.y, w.t.z);
+        kn = w.t.w;
+    }
 }
 
 template <class S>
@@ -146,11 +243,11 @@ __device__ __forceinline__ void contact_impulse(Body &A, Body &B, float3 n, floa
     axpy(B.w, B.ii * rb, L);
 }
 
-__device__ __forceinline__ void contact_row(Body &A, Body &B, float4 r0, float4 r1, float4 r2, float mu,
-                                            float4 &lam) {
-    const float3 n = f3(r0), t1 = f3(r1);
-    const float kn = r0.w, kt = r1.w;
-    const float ra = r2.x, rb = r2.y, target = r2.z;
+__device__ __forceinline__ void contact_row(Body &A, Body &B, float4 r0, float4 r1, float3 t1, float kn,
+                                            float mu, float4 &lam) {
+    const float3 n = f3(r0);
+    const float kt = r0.w;
+    const float ra = r1.x, rb = r1.y, target = r1.z;
     const float3 t2 = cross3(n, t1);
     // normal row
     float3 dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
@@ -220,15 +317,28 @@ __device__ __forceinline__ void joint_rows(Body &A, Body &B, float4 r0, float4 r
     lam = make_float4(l[0], l[1], l[2], lam.w);
 }
 
+// one constraint's rows in the sweep
+template <class S>
+__device__ __forceinline__ void solve_row(Body &A, Body &B, const Row &w, float mu, float4 &lam) {
+    if (w.joint) {
+        joint_rows(A, B, w.x, w.y, w.z, lam);
+    } else {
+        float3 t1;
+        float kn;
+        contact_frame<S>(w, A, B, t1, kn);
+        contact_row(A, B, w.x, w.y, t1, kn, mu, lam);
+    }
+}
+
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 
 // residual (lambda - clamp(lambda + k (target - w), lo, hi)) / k of a row
 // group, squared and summed
 __device__ __forceinline__ float contact_residual_sq(const Body &A, const Body &B, float4 r0, float4 r1,
-                                                     float4 r2, float mu, float4 lam) {
-    const float3 n = f3(r0), t1 = f3(r1);
-    const float kn = r0.w, kt = r1.w;
-    const float ra = r2.x, rb = r2.y, target = r2.z;
+                                                     float3 t1, float kn, float mu, float4 lam) {
+    const float3 n = f3(r0);
+    const float kt = r0.w;
+    const float ra = r1.x, rb = r1.y, target = r1.z;
     const float3 t2 = cross3(n, t1);
     float3 dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
     float3 u = make_float3(ra * A.w.x + rb * B.w.x, ra * A.w.y + rb * B.w.y, ra * A.w.z + rb * B.w.z);
@@ -301,11 +411,19 @@ __device__ float rows_residual_sq(const SolveArgs &a, const S &st, const Buckets
             const int o = c * bk.cs + 2 * k;
             const int jb = bk.tab[o + 1], ce = bk.tab[o + 2];
             for (int r = bk.tab[o] + tid; r < ce; r += T) {
-                float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r], m = a.r3[r], lam = a.rlam[r];
+                Row w;
+                fetch_row<S>(a, r, r >= jb, w);
+                const float4 lam = a.rlam[r];
                 Body A, B;
-                int slots = __float_as_int(r2.w);
-                load_pair(st, slots, m, A, B);
-                sq += r < jb ? contact_residual_sq(A, B, r0, r1, r2, mu, lam) : joint_residual_sq(A, B, r0, r1, r2);
+                load_pair(st, w, A, B);
+                if (w.joint) {
+                    sq += joint_residual_sq(A, B, w.x, w.y, w.z);
+                } else {
+                    float3 t1;
+                    float kn;
+                    contact_frame<S>(w, A, B, t1, kn);
+                    sq += contact_residual_sq(A, B, w.x, w.y, t1, kn, mu, lam);
+                }
             }
         }
     return sq;
@@ -336,6 +454,8 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
         Body x;
         x.v = make_float3(v.x + h * a.gravity.x, v.y + h * a.gravity.y, v.z + h * a.gravity.z);
         x.w = make_float3(w.x, w.y, w.z);
+        x.im = v.w;
+        x.ii = w.w;
         st.store(s, x);
     }
     group_sync<C>();
@@ -348,19 +468,22 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
         for (int r = bk.tab[o] + tid; r < ce; r += T) {
             float4 lam = a.rlam[r];
             if (lam.x == 0.f && lam.y == 0.f && lam.z == 0.f) continue;
-            float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r], m = a.r3[r];
-            int slots = __float_as_int(r2.w);
+            Row w;
+            fetch_row<S>(a, r, r >= jb, w);
             Body A, B;
-            load_pair(st, slots, m, A, B);
-            if (r < jb) {
-                float3 n = f3(r0), t1 = f3(r1);
-                contact_impulse(A, B, n, t1, cross3(n, t1), r2.x, r2.y, lam.x, lam.y, lam.z);
+            load_pair(st, w, A, B);
+            if (!w.joint) {
+                float3 t1;
+                float kn;
+                contact_frame<S>(w, A, B, t1, kn);
+                const float3 n = f3(w.x);
+                contact_impulse(A, B, n, t1, cross3(n, t1), w.y.x, w.y.y, lam.x, lam.y, lam.z);
             } else {
-                joint_impulse(A, B, f3(r0), f3(r1), 0, lam.x);
-                joint_impulse(A, B, f3(r0), f3(r1), 1, lam.y);
-                joint_impulse(A, B, f3(r0), f3(r1), 2, lam.z);
+                joint_impulse(A, B, f3(w.x), f3(w.y), 0, lam.x);
+                joint_impulse(A, B, f3(w.x), f3(w.y), 1, lam.y);
+                joint_impulse(A, B, f3(w.x), f3(w.y), 2, lam.z);
             }
-            store_pair(st, slots, A, B);
+            store_pair(st, row_slots(w), A, B);
         }
       }
       group_sync<C>();
@@ -377,30 +500,29 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                 // two rows of the colour at once (independent: no shared body)
                 for (; r + T < ce; r += 2 * T) {
                     const int q = r + T;
-                    float4 x0 = a.r0[r], x1 = a.r1[r], x2 = a.r2[r], xm = a.r3[r], xl = a.rlam[r];
-                    float4 y0 = a.r0[q], y1 = a.r1[q], y2 = a.r2[q], ym = a.r3[q], yl = a.rlam[q];
-                    const int sx = __float_as_int(x2.w), sy = __float_as_int(y2.w);
+                    Row u, w;
+                    fetch_row<S>(a, r, r >= jb, u);
+                    fetch_row<S>(a, q, q >= jb, w);
+                    float4 xl = a.rlam[r], yl = a.rlam[q];
                     Body A, B, D, E;
-                    load_pair(st, sx, xm, A, B);
-                    load_pair(st, sy, ym, D, E);
-                    if (r < jb) contact_row(A, B, x0, x1, x2, mu, xl);
-                    else joint_rows(A, B, x0, x1, x2, xl);
-                    if (q < jb) contact_row(D, E, y0, y1, y2, mu, yl);
-                    else joint_rows(D, E, y0, y1, y2, yl);
-                    store_pair(st, sx, A, B);
-                    store_pair(st, sy, D, E);
+                    load_pair(st, u, A, B);
+                    load_pair(st, w, D, E);
+                    solve_row<S>(A, B, u, mu, xl);
+                    solve_row<S>(D, E, w, mu, yl);
+                    store_pair(st, row_slots(u), A, B);
+                    store_pair(st, row_slots(w), D, E);
                     a.rlam[r] = xl;
                     a.rlam[q] = yl;
                 }
             }
             for (; r < ce; r += T) {
-                float4 r0 = a.r0[r], r1 = a.r1[r], r2 = a.r2[r], m = a.r3[r], lam = a.rlam[r];
-                int slots = __float_as_int(r2.w);
+                Row w;
+                fetch_row<S>(a, r, r >= jb, w);
+                float4 lam = a.rlam[r];
                 Body A, B;
-                load_pair(st, slots, m, A, B);
-                if (r < jb) contact_row(A, B, r0, r1, r2, mu, lam);
-                else joint_rows(A, B, r0, r1, r2, lam);
-                store_pair(st, slots, A, B);
+                load_pair(st, w, A, B);
+                solve_row<S>(A, B, w, mu, lam);
+                store_pair(st, row_slots(w), A, B);
                 a.rlam[r] = lam;
             }
           }
@@ -451,8 +573,9 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
 
 // C CTAs per worker; a worker's slots are spread over their shared memory when
 // they fit (ceil(nb / C) <= smem_slots), else CTA rank 0 solves it alone with
-// its body state in the global scratch area.
-template <int C, int U>
+// its body state in the global scratch area.  M: the shared-memory slots hold
+// the masses (32 B per slot) and contact rows are read as two records.
+template <int C, int U, bool M>
 __global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveArgs a) {
     extern __shared__ float4 sm[];
     const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
@@ -474,13 +597,24 @@ __global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveAr
     const int row0 = goff[0], row1 = goff[OWNER_NB - 1];
     if (per <= a.smem_slots) {
         float4 *A = sm;
-        float2 *B = reinterpret_cast<float2 *>(sm + per);
-        if (C == 1) {
-            LocalSlots st{A, B};
-            solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+        if (M) {
+            float4 *B = sm + per;
+            if (C == 1) {
+                LocalSlotsM st{A, B};
+                solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+            } else {
+                ClusterSlotsM<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B), per};
+                solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+            }
         } else {
-            ClusterSlots<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B), per};
-            solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+            float2 *B = reinterpret_cast<float2 *>(sm + per);
+            if (C == 1) {
+                LocalSlots st{A, B};
+                solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+            } else {
+                ClusterSlots<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B), per};
+                solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+            }
         }
     } else if (rank == 0) {
         // one CTA takes the whole worker: every owner bucket of every colour
@@ -491,12 +625,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveAr
 
 }  // namespace
 
-int solve_smem_bytes(int slots) { return slots * (int)(sizeof(float4) + sizeof(float2)); }
+int solve_smem_bytes(int slots, bool masses) {
+    return slots * (int)(masses ? 2 * sizeof(float4) : sizeof(float4) + sizeof(float2));
+}
 
-template <int C, int U>
+template <int C, int U, bool M>
 static void launch_solve_c(const SolveArgs &a, int threads, cudaStream_t s) {
-    int smem = solve_smem_bytes(a.smem_slots);
-    CK(cudaFuncSetAttribute(k_solve<C, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int smem = solve_smem_bytes(a.smem_slots, M);
+    CK(cudaFuncSetAttribute(k_solve<C, U, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.n_parts * C);
     cfg.blockDim = dim3(threads);
@@ -509,31 +645,31 @@ static void launch_solve_c(const SolveArgs &a, int threads, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, k_solve<C, U>, a));
+    CK(cudaLaunchKernelEx(&cfg, k_solve<C, U, M>, a));
     note_launch();
 }
 
-void launch_solve(const SolveArgs &a, int threads, int cluster, int unroll, cudaStream_t s) {
+template <int U, bool M>
+static void launch_solve_u(const SolveArgs &a, int threads, int cluster, cudaStream_t s) {
+    switch (cluster) {
+        case 8: launch_solve_c<8, U, M>(a, threads, s); break;
+        case 6: launch_solve_c<6, U, M>(a, threads, s); break;
+        case 4: launch_solve_c<4, U, M>(a, threads, s); break;
+        case 3: launch_solve_c<3, U, M>(a, threads, s); break;
+        case 2: launch_solve_c<2, U, M>(a, threads, s); break;
+        default: launch_solve_c<1, U, M>(a, threads, s); break;
+    }
+}
+
+void launch_solve(const SolveArgs &a, int threads, int cluster, int unroll, bool masses, cudaStream_t s) {
     if (!a.n_parts) return;
     if (threads > SOLVE_THREADS) threads = SOLVE_THREADS;
     if (unroll == 2) {
-        switch (cluster) {
-            case 8: launch_solve_c<8, 2>(a, threads, s); break;
-            case 6: launch_solve_c<6, 2>(a, threads, s); break;
-            case 4: launch_solve_c<4, 2>(a, threads, s); break;
-            case 3: launch_solve_c<3, 2>(a, threads, s); break;
-            case 2: launch_solve_c<2, 2>(a, threads, s); break;
-            default: launch_solve_c<1, 2>(a, threads, s); break;
-        }
+        if (masses) launch_solve_u<2, true>(a, threads, cluster, s);
+        else launch_solve_u<2, false>(a, threads, cluster, s);
     } else {
-        switch (cluster) {
-            case 8: launch_solve_c<8, 1>(a, threads, s); break;
-            case 6: launch_solve_c<6, 1>(a, threads, s); break;
-            case 4: launch_solve_c<4, 1>(a, threads, s); break;
-            case 3: launch_solve_c<3, 1>(a, threads, s); break;
-            case 2: launch_solve_c<2, 1>(a, threads, s); break;
-            default: launch_solve_c<1, 1>(a, threads, s); break;
-        }
+        if (masses) launch_solve_u<1, true>(a, threads, cluster, s);
+        else launch_solve_u<1, false>(a, threads, cluster, s);
     }
     CK(cudaGetLastError());
 }

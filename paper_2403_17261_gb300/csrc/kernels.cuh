@@ -161,7 +161,7 @@ struct RowArgs {
     const float *scene_mu;
     float dt_override;
     float erp, slop;
-    float4 *r0, *r1, *r2, *r3;
+    float4 *r0, *r1, *r2, *r3, *r4;   // r2: joints only; r4: contacts only
     int *rpair;                // [np] pair index of every row (canonical order)
     float4 *rlam;
     int *status;
@@ -183,7 +183,7 @@ struct SolveArgs {
     float3 gravity;
     const float4 *st;
     const float *scene_mu;
-    const float4 *r0, *r1, *r2, *r3;
+    const float4 *r0, *r1, *r2, *r3, *r4;
     const int *rpair;
     float4 *rlam;
     int n_entries;
@@ -199,9 +199,11 @@ struct SolveArgs {
     double *part_res_sq;       // [P]
     int *status;
 };
-void launch_solve(const SolveArgs &a, int threads, int cluster, int unroll, cudaStream_t s);
+// masses: the shared-memory slots hold the inverse masses and inertias (32 B
+// per slot; contact rows read as two records); else 24 B per slot
+void launch_solve(const SolveArgs &a, int threads, int cluster, int unroll, bool masses, cudaStream_t s);
 int solve_ctas_per_sm(int unroll);
-int solve_smem_bytes(int slots);
+int solve_smem_bytes(int slots, bool masses);
 
 // ---- geodesics, weights, blend (k_blend.cu) --------------------------------
 struct GeoArgs {
