@@ -47,9 +47,11 @@ JOINT_ROW_BYTES = 80     # per joint per sweep: 56 B record (2 slots, r_A, r_B, 
 ENTRY_BYTES = 120        # per (body, worker) per step: 60 B state + params read, 52 B copy write, 8 B index
 PAIR_ONCE_BYTES = 24     # per constraint per step: warm-start lambda read + final lambda write
 # DRAM bytes of the solve over its algorithmic bytes, from the ncu capture
-# summarised in profiles/k_solve_pile_large.md.  Valid for the captured
-# kernel only: None while k_solve has changed since the capture.
-SOLVE_DRAM_PER_ALGORITHMIC_BYTE = None
+# summarised in profiles/k_solve_pile_large.md (every solver launch of the two
+# timed steps: 0.273 GB of DRAM traffic for 7.40 GB of algorithmic bytes; the
+# row records stay in L2 across sweeps).  Valid for the captured kernel only:
+# set to None when k_solve changes, until it is captured again.
+SOLVE_DRAM_PER_ALGORITHMIC_BYTE = 0.037
 
 
 def parse():
