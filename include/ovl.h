@@ -149,6 +149,9 @@ typedef struct ovl_stats {
     int32_t colour_rounds_max; /* most colouring rounds any worker needed */
     int64_t lb_candidates;     /* contacts handed to the host load balance in the last step */
     double lb_host_ms;         /* host time of the load balance in the last step (copies included) */
+    int64_t solve_ctas;        /* CTAs the last solve launched */
+    int64_t solve_ctas_masses; /* of those, CTAs holding the inverse masses in shared memory (two-record
+                                  contact rows) */
 } ovl_stats;
 
 /* Fills *p with the defaults listed in ovl_params. */

@@ -331,24 +331,22 @@ constexpr SolveShape kSolveShapes[3] = {{512, 2, 1}, {512, 1, 2}, {256, 2, 2}};
 
 // the shape without tuning: one CTA per SM while the workers do not
 // outnumber the SMs, else two smaller CTAs per SM
+// CTAs per worker the plans choose from (each a cluster size both the solver
+// and the colouring are built for)
+constexpr int kClusterSizes[] = {1, 2, 3, 4, 6, 8};
+
 int default_solve_shape(const ovl_ctx *c) { return c->n_parts <= c->num_sms ? 0 : 2; }
 
-// Per-worker CTA counts (shared by the colouring and the solve): each worker
-// starts at the fewest CTAs of kClusterSizes whose shares of its bodies fit
-// `cap` slots; while the total stays within `budget` CTAs, the worker with
-// the most constraints per CTA moves to the next size (up to OVL_SOLVE_MAX_GROW
-// unless its bodies need more).  Workers with equal counts form one class,
-// listed by count, then most constraints first; their order goes to `buf`.
-// Returns false if some worker does not fit 8 CTAs.
-// CTA count of every worker: the fewest of 1, 2, 3, 4, 6, 8 whose shares fit
-// `cap` slots; then, while the total stays within `budget`, the worker with
-// the most rows per CTA moves up (at most OVL_SOLVE_MAX_GROW).  Empty if some
-// worker needs more than 8.
+// CTA count of every worker (shared by the colouring and the solve): the
+// fewest of kClusterSizes whose shares of its bodies fit `cap` slots; then,
+// while the total stays within `budget`, the worker with the most rows per
+// CTA moves to the next size (at most OVL_SOLVE_MAX_GROW).  Empty if some
+// worker needs more than 8.  (Sizes 5 and 7 were tried: the workers of the
+// large pile need 1-4 CTAs each, so they changed no plan.)
 std::vector<int> plan_worker_counts(ovl_ctx *c, int cap, long long budget) {
     const int P = c->n_parts;
     const std::vector<int> &pb = c->h_pb, &pp = c->h_pp;
-    static const int kSizes[] = {1, 2, 3, 4, 6, 8};
-    auto next = [](int k) { for (int x : kSizes) if (x > k) return x; return 0; };
+    auto next = [](int k) { for (int x : kClusterSizes) if (x > k) return x; return 0; };
     std::vector<int> C(P);
     long long total = 0;
     for (int p = 0; p < P; ++p) {
@@ -413,12 +411,11 @@ bool plan_worker_classes(ovl_ctx *c, int cap, long long budget, std::vector<Solv
 
 // fewest CTAs of a plan before any growth (sum of the minimal counts)
 long long fewest_ctas(ovl_ctx *c, int cap) {
-    static const int kSizes[] = {1, 2, 3, 4, 6, 8};
     long long total = 0;
     for (int p = 0; p < c->n_parts; ++p) {
         const int nb = c->h_pb[p + 1] - c->h_pb[p];
         int k = 0;
-        for (int x : kSizes)
+        for (int x : kClusterSizes)
             if ((nb + x - 1) / x <= cap) { k = x; break; }
         if (!k) return -1;
         total += k;
@@ -649,16 +646,23 @@ void launch_solve_plan(ovl_ctx *c, const SolvePlan &pl, float dt_override, int i
     c->part_res_sq.ensure((size_t)P + 1);
     CK(cudaMemsetAsync(c->part_res_sq.p, 0, sizeof(double) * ((size_t)P + 1), c->stream));
     SolveArgs a = solve_args(c, dt_override, iters);
+    c->last_ctas = c->last_ctas_masses = 0;
     if (pl.shape >= 0) {
         launch_solve_classes(c, a, kSolveShapes[pl.shape], pl.classes);
+        for (const SolveClass &k : pl.classes) {
+            c->last_ctas += (long long)k.C * k.count;
+            if (solve_masses_fit(c, k.slots, kSolveShapes[pl.shape].per_sm)) c->last_ctas_masses += (long long)k.C * k.count;
+        }
         c->last_cluster = pl.classes.front().C;
         c->last_threads = kSolveShapes[pl.shape].threads;
         c->last_unroll = kSolveShapes[pl.shape].unroll;
         return;
     }
     a.smem_slots = pl.slots;
-    launch_solve(a, pl.threads, pl.cluster, pl.unroll,
-                 solve_masses_fit(c, pl.slots, solve_ctas_per_sm(pl.unroll)), c->stream);
+    const bool masses = solve_masses_fit(c, pl.slots, solve_ctas_per_sm(pl.unroll));
+    launch_solve(a, pl.threads, pl.cluster, pl.unroll, masses, c->stream);
+    c->last_ctas = (long long)pl.cluster * P;
+    c->last_ctas_masses = masses ? c->last_ctas : 0;
     c->last_cluster = pl.cluster;
     c->last_threads = pl.threads;
     c->last_unroll = pl.unroll;
@@ -1377,6 +1381,8 @@ ovl_status ovl_read_stats(ovl_ctx *c, ovl_stats *out) {
         out->solve_cluster = c->last_cluster;
         out->solve_threads = c->last_threads;
         out->solve_rows_per_thread = c->last_unroll;
+        out->solve_ctas = c->last_ctas;
+        out->solve_ctas_masses = c->last_ctas_masses;
         out->lb_candidates = c->lb_candidates;
         out->lb_host_ms = c->lb_host_ms;
         return OVL_OK;

@@ -90,7 +90,8 @@ class ovl_stats(C.Structure):
                 ("residual_max", C.c_double), ("phase_ms", C.c_float * 12),
                 ("n_launches", C.c_int64), ("solve_cluster", C.c_int32), ("solve_threads", C.c_int32),
                 ("solve_rows_per_thread", C.c_int32), ("colour_rounds_max", C.c_int32),
-                ("lb_candidates", C.c_int64), ("lb_host_ms", C.c_double)]
+                ("lb_candidates", C.c_int64), ("lb_host_ms", C.c_double),
+                ("solve_ctas", C.c_int64), ("solve_ctas_masses", C.c_int64)]
 
 
 _lib = None
