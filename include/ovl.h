@@ -141,7 +141,10 @@ typedef struct ovl_stats {
     double residual_max;       /* max |residual| */
     float phase_ms[12];        /* per-phase device times (OVL_FLAG_TIMING); see ovl_phase_name;
                                   index 10 = learned warm start (features + network), which the
-                                  membership phase (index 3) includes */
+                                  membership phase (index 3) includes; index 7 (geodesics) runs on
+                                  its own stream beside the colouring and the solve when the
+                                  workers do not outnumber the SMs, and the phases then add up to
+                                  more than the total (index 9) */
     int64_t n_launches;        /* CUDA kernels the library launched during the last step */
     int32_t solve_cluster;     /* CTAs per worker of the last solve */
     int32_t solve_threads;     /* threads per CTA of the last solve */

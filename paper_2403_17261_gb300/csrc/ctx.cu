@@ -762,8 +762,8 @@ void enqueue_geodesics(ovl_ctx *c, cudaStream_t s) {
     for (int L = 1; L <= c->beta_max; ++L) launch_geo_level(a, L, s);
 }
 
-void phase_geodesics(ovl_ctx *c) {
-    cudaStream_t s = c->stream;
+// s: the stream the weights are computed on
+void phase_geodesics(ovl_ctx *c, cudaStream_t s) {
     c->D.ensure(c->ne + 1);
     c->visited.ensure((size_t)((c->vb_bits + 31) / 32) + 1);
     c->queue.ensure((size_t)c->vb_bits + 1);
@@ -831,6 +831,24 @@ ovl_status run_step(ovl_ctx *c, float dt, int iters) {
     mark(c, 3);
     phase_membership(c, dt);
     phase_warmstart(c, dt);
+    // The geodesic weights need only the membership and the graph.  When the
+    // workers do not outnumber the SMs (the solve is one wave), they run on
+    // their own stream while the colouring and the solve proceed, and the
+    // blend waits for them; with more workers the solve's waves would lose
+    // SMs to them, so they run after the solve.
+    const bool geo_beside = c->n_parts <= c->num_sms;
+    cudaStream_t gs = geo_beside ? c->geo_stream : s;
+    auto geodesics = [&]() {
+        if (geo_beside) {
+            CK(cudaEventRecord(c->geo_fork, s));
+            CK(cudaStreamWaitEvent(c->geo_stream, c->geo_fork, 0));
+        }
+        if (c->P.flags & OVL_FLAG_TIMING) CK(cudaEventRecord(c->ev[14], gs));
+        phase_geodesics(c, gs);
+        if (c->P.flags & OVL_FLAG_TIMING) CK(cudaEventRecord(c->ev[15], gs));
+        if (geo_beside) CK(cudaEventRecord(c->geo_join, c->geo_stream));
+    };
+    if (geo_beside) geodesics();
     mark(c, 4);
     phase_colour(c);
     mark(c, 5);
@@ -841,7 +859,8 @@ ovl_status run_step(ovl_ctx *c, float dt, int iters) {
     launch_solve_plan(c, plan, dt, iters);
     phase_log(c);
     mark(c, 7);
-    phase_geodesics(c);
+    if (geo_beside) CK(cudaStreamWaitEvent(s, c->geo_join, 0));
+    else geodesics();
     mark(c, 8);
     phase_blend(c, dt);
     mark(c, 9);
@@ -851,6 +870,8 @@ ovl_status run_step(ovl_ctx *c, float dt, int iters) {
     if (c->P.flags & OVL_FLAG_TIMING) {
         CK(cudaEventSynchronize(c->ev[9]));
         for (int i = 0; i < 9; ++i) CK(cudaEventElapsedTime(&c->phase_ms[i], c->ev[i], c->ev[i + 1]));
+        // geodesics: their own stream's time (they overlap colouring and solve)
+        CK(cudaEventElapsedTime(&c->phase_ms[7], c->ev[14], c->ev[15]));
         CK(cudaEventElapsedTime(&c->phase_ms[9], c->ev[0], c->ev[9]));
         c->phase_ms[10] = 0.f;
         if (c->feat_valid) CK(cudaEventElapsedTime(&c->phase_ms[10], c->ev[12], c->ev[13]));
@@ -912,6 +933,9 @@ ovl_status ovl_create(ovl_ctx **out, const ovl_params *p, void *cuda_stream) {
         }
         for (auto &e : c->ev) CK(cudaEventCreate(&e));
         for (auto &x : c->aux) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&c->geo_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->geo_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->geo_join, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
         for (auto &e : c->join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         c->lb_threads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
@@ -1007,6 +1031,9 @@ ovl_status ovl_destroy(ovl_ctx *c) {
         if (e) cudaEventDestroy(e);
     for (auto &x : c->aux)
         if (x) { cudaStreamSynchronize(x); cudaStreamDestroy(x); }
+    if (c->geo_stream) { cudaStreamSynchronize(c->geo_stream); cudaStreamDestroy(c->geo_stream); }
+    if (c->geo_fork) cudaEventDestroy(c->geo_fork);
+    if (c->geo_join) cudaEventDestroy(c->geo_join);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->geo_exec) cudaGraphExecDestroy(c->geo_exec);
     for (auto &e : c->join)

@@ -97,6 +97,8 @@ struct ovl_ctx {
     DBuf<int> solve_C, col_off2, pair_of_row2;   // solve: CTAs per worker, rows grouped by owner CTA
     DBuf<uint8_t> row_owner;                     // owner CTA of every row (scratch of the grouping)
     cudaStream_t aux[5] = {};                    // side streams of the per-class solve launches
+    cudaStream_t geo_stream = nullptr;           // the geodesic weights, beside colouring and solve
+    cudaEvent_t geo_fork = nullptr, geo_join = nullptr;
     cudaEvent_t fork = nullptr, join[5] = {};
     cudaGraphExec_t geo_exec = nullptr;          // the geodesic phase, captured
     std::vector<const void *> geo_key;           // its arguments when captured
