@@ -131,21 +131,22 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
     c->lb_flag.ensure(c->nc + 1);
     c->lb_pos.ensure(c->nc + 1);
     c->lb_pairs.ensure(c->nc + 1);
+    const auto t0 = std::chrono::steady_clock::now();
     launch_lb_flags(c->c_ab.p, c->nc, c->im.p, n, c->mask.p, deact ? 0 : 1, c->lb_flag.p, s);
     scan_i32(c->lb_flag.p, c->lb_pos.p, c->nc, c->scan_tmp, s);
-    const int m = read_i32(c, c->lb_pos.p + c->nc);
-    c->lb_candidates = m;
-    if (m == 0) return;
-    const auto t0 = std::chrono::steady_clock::now();
-    launch_lb_compact(c->c_ab.p, c->nc, c->lb_flag.p, c->lb_pos.p, c->lb_pairs.p, s);
-    c->h_ab.ensure(m + 1);
+    // the graph and the masks go to the host while the candidate count is read
     c->h_rp.ensure((size_t)n + 1);
     c->h_col.ensure((size_t)c->nadj + 1);
     c->h_mask.ensure(n);
-    CK(cudaMemcpyAsync(c->h_ab.p, c->lb_pairs.p, sizeof(int2) * m, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->h_rp.p, c->row_ptr.p, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->h_col.p, c->col.p, sizeof(int) * c->nadj, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->h_mask.p, c->mask.p, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, s));
+    const int m = read_i32(c, c->lb_pos.p + c->nc);
+    c->lb_candidates = m;
+    if (m == 0) return;
+    launch_lb_compact(c->c_ab.p, c->nc, c->lb_flag.p, c->lb_pos.p, c->lb_pairs.p, s);
+    c->h_ab.ensure(m + 1);
+    CK(cudaMemcpyAsync(c->h_ab.p, c->lb_pairs.p, sizeof(int2) * m, cudaMemcpyDeviceToHost, s));
     c->lb_loads.ensure((size_t)c->n_parts + 1);
     c->h_loads.ensure((size_t)c->n_parts + 1);
     const bool by_contacts = c->P.lb_load == OVL_LB_CONTACTS;
@@ -216,13 +217,6 @@ void phase_membership(ovl_ctx *c, float dt_override) {
     scan_i32(c->part_count.p, c->part_bstart.p, P, c->scan_tmp, s);
     a = member_args(c);
     launch_entry_slot(a, ne, s);
-    {
-        std::vector<int> pb(P + 1);
-        CK(cudaMemcpyAsync(pb.data(), c->part_bstart.p, sizeof(int) * (P + 1), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        c->nb_max = 0;
-        for (int p = 0; p < P; ++p) c->nb_max = std::max(c->nb_max, pb[p + 1] - pb[p]);
-    }
     // (worker, constraint) pairs
     const int K = c->nc + c->nj;
     c->cons_count.ensure((size_t)K + 1); c->cons_start.ensure((size_t)K + 1);
@@ -261,6 +255,8 @@ void phase_membership(ovl_ctx *c, float dt_override) {
     download(c->h_pb.data(), c->part_bstart.p, (size_t)P + 1, s);
     download(c->h_pp.data(), c->part_pstart.p, (size_t)P + 1, s);
     CK(cudaStreamSynchronize(s));
+    c->nb_max = 0;
+    for (int p = 0; p < P; ++p) c->nb_max = std::max(c->nb_max, c->h_pb[p + 1] - c->h_pb[p]);
 }
 
 int colour_smem_capacity(ovl_ctx *c) {
