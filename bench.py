@@ -51,7 +51,7 @@ PAIR_ONCE_BYTES = 24     # per constraint per step: warm-start lambda read + fin
 # timed steps: 0.273 GB of DRAM traffic for 7.40 GB of algorithmic bytes; the
 # row records stay in L2 across sweeps).  Valid for the captured kernel only:
 # set to None when k_solve changes, until it is captured again.
-SOLVE_DRAM_PER_ALGORITHMIC_BYTE = 0.037
+SOLVE_DRAM_PER_ALGORITHMIC_BYTE = None
 
 
 def parse():
