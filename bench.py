@@ -38,6 +38,10 @@ import time
 
 import numpy as np
 
+# more hardware queues than the library's streams, set before CUDA starts
+# (the per-class solve and colouring launches otherwise share queues)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -48,10 +52,10 @@ ENTRY_BYTES = 120        # per (body, worker) per step: 60 B state + params read
 PAIR_ONCE_BYTES = 24     # per constraint per step: warm-start lambda read + final lambda write
 # DRAM bytes of the solve over its algorithmic bytes, from the ncu capture
 # summarised in profiles/k_solve_pile_large.md (every solver launch of the two
-# timed steps: 0.273 GB of DRAM traffic for 7.40 GB of algorithmic bytes; the
+# timed steps: 0.292 GB of DRAM traffic for 7.40 GB of algorithmic bytes; the
 # row records stay in L2 across sweeps).  Valid for the captured kernel only:
 # set to None when k_solve changes, until it is captured again.
-SOLVE_DRAM_PER_ALGORITHMIC_BYTE = None
+SOLVE_DRAM_PER_ALGORITHMIC_BYTE = 0.039
 
 
 def parse():

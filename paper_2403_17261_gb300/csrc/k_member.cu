@@ -230,7 +230,7 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-constexpr int COLOUR_THREADS = 512;
+constexpr int COLOUR_THREADS = 1024;
 constexpr int COLOUR_WARPS = COLOUR_THREADS / 32;
 constexpr int NBUCKET = 2 * OVL_MAX_COLOURS;
 
@@ -325,13 +325,24 @@ __device__ __forceinline__ int cluster_int_sum(int *v) {
 // the contacts whose first body falls in its slot range, so most of their
 // slot accesses stay local, and an equal share of the joints.  The shares
 // follow rank order, so the final sort is stable across CTAs.
+// The CTA's static shared state, declared once in the kernel: both
+// instantiations of colour_worker (cluster slots and the global-memory
+// fallback) share it instead of each holding its own copy.
+struct ColourShared {
+    int n_next, ncol_sh, pub_left, pub_ncol;
+    int counts[NBUCKET + 1];
+    int base_b[NBUCKET + 1];
+    int running[NBUCKET];
+    int wcnt[COLOUR_WARPS][NBUCKET];
+};
+
 template <int C, class SL>
-__device__ void colour_worker(const ColourArgs &a, const SL &S, int p, int rank, int per) {
-    __shared__ int n_next, ncol_sh, pub_left, pub_ncol;
-    __shared__ int counts[NBUCKET + 1];
-    __shared__ int base_b[NBUCKET + 1];
-    __shared__ int running[NBUCKET];
-    __shared__ int wcnt[COLOUR_WARPS][NBUCKET];
+__device__ void colour_worker(const ColourArgs &a, const SL &S, ColourShared &sh, int p, int rank, int per) {
+    int &n_next = sh.n_next, &ncol_sh = sh.ncol_sh, &pub_left = sh.pub_left, &pub_ncol = sh.pub_ncol;
+    int (&counts)[NBUCKET + 1] = sh.counts;
+    int (&base_b)[NBUCKET + 1] = sh.base_b;
+    int (&running)[NBUCKET] = sh.running;
+    int (&wcnt)[COLOUR_WARPS][NBUCKET] = sh.wcnt;
     const int tid = threadIdx.x, T = blockDim.x;
     const int b0 = a.part_bstart[p], nb = a.part_bstart[p + 1] - b0;
     const int q0 = a.part_pstart[p], nq = a.part_pstart[p + 1] - q0;
@@ -505,6 +516,7 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, int p, int rank,
 template <int C>
 __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
     extern __shared__ unsigned long long dyn_smem[];
+    __shared__ ColourShared sh;
     const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
     const int p = a.order ? (int)a.order[blockIdx.x / C] : (int)(blockIdx.x / C);
     const int nb = a.part_bstart[p + 1] - a.part_bstart[p];
@@ -513,15 +525,15 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
         unsigned long long *mx = dyn_smem, *u = dyn_smem + per;
         if (C == 1) {
             ColourPtrs S{mx, u};
-            colour_worker<1>(a, S, p, 0, per);
+            colour_worker<1>(a, S, sh, p, 0, per);
         } else {
             ColourSlots<C> S{(uint32_t)__cvta_generic_to_shared(mx), (uint32_t)__cvta_generic_to_shared(u), per};
-            colour_worker<C>(a, S, p, rank, per);
+            colour_worker<C>(a, S, sh, p, rank, per);
         }
     } else if (rank == 0) {
         unsigned long long *mx = a.scratch + 2 * (size_t)a.part_bstart[p];
         ColourPtrs S{mx, mx + nb};
-        colour_worker<1>(a, S, p, 0, nb);
+        colour_worker<1>(a, S, sh, p, 0, nb);
     }
 }
 
@@ -685,6 +697,21 @@ static void launch_colour_c(const ColourArgs &a, cudaStream_t s) {
     cfg.numAttrs = 1;
     CK(cudaLaunchKernelEx(&cfg, k_colour<C>, a));
     note_launch();
+}
+
+// largest static shared memory of the colouring kernels (the per-warp bucket
+// counts dominate); the dynamic slot arrays get what is left of the opt-in limit
+int colour_static_smem() {
+    static int bytes = -1;
+    if (bytes < 0) {
+        int mx = 0;
+        cudaFuncAttributes fa;
+        auto take = [&](const void *f) { CK(cudaFuncGetAttributes(&fa, f)); mx = std::max(mx, (int)fa.sharedSizeBytes); };
+        take((const void *)k_colour<1>); take((const void *)k_colour<2>); take((const void *)k_colour<3>);
+        take((const void *)k_colour<4>); take((const void *)k_colour<6>); take((const void *)k_colour<8>);
+        bytes = mx;
+    }
+    return bytes;
 }
 
 void launch_colour(const ColourArgs &a, int cluster, cudaStream_t s) {

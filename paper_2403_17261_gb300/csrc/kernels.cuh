@@ -140,6 +140,7 @@ struct ColourArgs {
     int *status;
 };
 void launch_colour(const ColourArgs &a, int cluster, cudaStream_t s);
+int colour_static_smem();
 
 struct RowArgs {
     int n, nc, np;

@@ -15,6 +15,12 @@ import os
 
 import numpy as np
 
+# The library launches a step's per-class kernels on up to seven streams; with
+# CUDA's default of 8 hardware queues some of them would share one and run in
+# turn.  The setting counts only if it is in place before the process first
+# uses CUDA (importing this module before torch initialises CUDA is enough).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libovl.so")
 
