@@ -306,7 +306,7 @@ bool solve_masses_fit(ovl_ctx *c, int slots, int ctas_per_sm) {
 // shared memory; while all CTAs still fit the SMs, the worker with the most
 // rows per CTA moves to the next count.  Workers with the same count form one launch, and
 // the launches run side by side on the context's streams.  Every launch
-// shape gives the same bits (the solver is built without FMA contraction),
+// shape gives the same bits (no implicit FMA contraction in the solver),
 // so the plan changes only the time.  Returns false when some worker does
 // not fit even 8 CTAs (the uniform launch then takes it to global memory).
 struct SolveClass { int C, first, count, slots; };

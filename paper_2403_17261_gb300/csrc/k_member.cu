@@ -578,7 +578,7 @@ __global__ void k_rows(RowArgs a) {
             a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, kt);
             a.r1[r] = make_float4(ra, rb, target, __int_as_float(pack_slots(sl, a.status)));
             a.r3[r] = make_float4(ima, imb, iia, iib);
-            a.r4[r] = make_float4(t1.x, t1.y, t1.z, 1.0f / (ima + imb));
+            a.r4[r] = make_float4(t1.x, t1.y, t1.z, __frcp_rn(ima + imb));   // as the solver forms k_n
         } else {
             const int j = i - a.nc;
             const int2 ab = a.jab[j];

@@ -53,12 +53,23 @@ constexpr int SOLVE_THREADS = 512;
 // 124; with the masses in the rows the extra spills made it slower.
 constexpr int SOLVE_THREADS_WIDE = 640;
 
+// The file is built without FMA contraction, and its fused multiply-adds are
+// written out (fmaf): every instantiation (cluster size, rows per thread,
+// slot layout, CTA width) then rounds the same way and gives the same bits.
 __device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+    return make_float3(fmaf(a.y, b.z, -(a.z * b.y)), fmaf(a.z, b.x, -(a.x * b.z)), fmaf(a.x, b.y, -(a.y * b.x)));
 }
-__device__ __forceinline__ void axpy(float3 &v, float s, float3 d) { v.x += s * d.x; v.y += s * d.y; v.z += s * d.z; }
+__device__ __forceinline__ void axpy(float3 &v, float s, float3 d) {
+    v.x = fmaf(s, d.x, v.x);
+    v.y = fmaf(s, d.y, v.y);
+    v.z = fmaf(s, d.z, v.z);
+}
+// ra a + rb b
+__device__ __forceinline__ float3 lever_sum(float ra, float3 a, float rb, float3 b) {
+    return make_float3(fmaf(ra, a.x, rb * b.x), fmaf(ra, a.y, rb * b.y), fmaf(ra, a.z, rb * b.z));
+}
 
 struct Body {
     float3 v, w;
@@ -219,7 +230,7 @@ __device__ __forceinline__ void contact_frame(const Row &w, const Body &A, const
     if (S::kMasses) {
         const float3 n = make_float3(w.x.x, w.x.y, w.x.z);
         t1 = tangent_from(n, tangent_axis(n.x, n.y, n.z));
-        kn = 1.0f / (A.im + B.im);
+        kn = __frcp_rn(A.im + B.im);
     } else {
         t1 = make_float3(w.t.x, w.t.y, w.t.z);
         kn = w.t.w;
@@ -237,12 +248,12 @@ __device__ __forceinline__ void store_pair(const S &st, int slots, const Body &A
 // impulses (n, t1, t2) components (ln, l1, l2) of a contact
 __device__ __forceinline__ void contact_impulse(Body &A, Body &B, float3 n, float3 t1, float3 t2,
                                                 float ra, float rb, float ln, float l1, float l2) {
-    float3 P = make_float3(n.x * ln + t1.x * l1 + t2.x * l2, n.y * ln + t1.y * l1 + t2.y * l2,
-                           n.z * ln + t1.z * l1 + t2.z * l2);
+    float3 P = make_float3(fmaf(n.x, ln, fmaf(t1.x, l1, t2.x * l2)), fmaf(n.y, ln, fmaf(t1.y, l1, t2.y * l2)),
+                           fmaf(n.z, ln, fmaf(t1.z, l1, t2.z * l2)));
     axpy(A.v, -A.im, P);
     axpy(B.v, B.im, P);
     // angular: -(r_A x P) on a, (r_B x P) on b with r_A = r_a n, r_B = -r_b n
-    float3 L = make_float3(t1.x * l2 - t2.x * l1, t1.y * l2 - t2.y * l1, t1.z * l2 - t2.z * l1);
+    float3 L = make_float3(fmaf(t1.x, l2, -(t2.x * l1)), fmaf(t1.y, l2, -(t2.y * l1)), fmaf(t1.z, l2, -(t2.z * l1)));
     axpy(A.w, A.ii * ra, L);
     axpy(B.w, B.ii * rb, L);
 }
@@ -255,7 +266,7 @@ __device__ __forceinline__ void contact_row(Body &A, Body &B, float4 r0, float4 
     const float3 t2 = cross3(n, t1);
     // normal row
     float3 dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
-    float ln = fmaxf(lam.x + kn * (target - dot3(n, dv)), 0.f);
+    float ln = fmaxf(fmaf(kn, target - dot3(n, dv), lam.x), 0.f);
     float d = ln - lam.x;
     lam.x = ln;
     axpy(A.v, -A.im * d, n);
@@ -263,9 +274,9 @@ __device__ __forceinline__ void contact_row(Body &A, Body &B, float4 r0, float4 
     const float lim = mu * ln;
     // first tangent
     dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
-    float3 u = make_float3(ra * A.w.x + rb * B.w.x, ra * A.w.y + rb * B.w.y, ra * A.w.z + rb * B.w.z);
+    float3 u = lever_sum(ra, A.w, rb, B.w);
     float wt = dot3(t1, dv) - dot3(t2, u);
-    float l1 = fminf(fmaxf(lam.y - kt * wt, -lim), lim);
+    float l1 = fminf(fmaxf(fmaf(-kt, wt, lam.y), -lim), lim);
     d = l1 - lam.y;
     lam.y = l1;
     axpy(A.v, -A.im * d, t1);
@@ -274,9 +285,9 @@ __device__ __forceinline__ void contact_row(Body &A, Body &B, float4 r0, float4 
     axpy(B.w, -B.ii * rb * d, t2);
     // second tangent
     dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
-    u = make_float3(ra * A.w.x + rb * B.w.x, ra * A.w.y + rb * B.w.y, ra * A.w.z + rb * B.w.z);
+    u = lever_sum(ra, A.w, rb, B.w);
     wt = dot3(t2, dv) + dot3(t1, u);
-    float l2 = fminf(fmaxf(lam.z - kt * wt, -lim), lim);
+    float l2 = fminf(fmaxf(fmaf(-kt, wt, lam.z), -lim), lim);
     d = l2 - lam.z;
     lam.z = l2;
     axpy(A.v, -A.im * d, t2);
@@ -303,9 +314,9 @@ __device__ __forceinline__ void joint_impulse(Body &A, Body &B, float3 rA, float
 
 // k_kk = 1 / (1/m_a + 1/m_b + |r_A x e_k|^2 / I_a + |r_B x e_k|^2 / I_b)
 __device__ __forceinline__ float joint_k(const Body &A, const Body &B, float3 rA, float3 rB, int ax) {
-    float a2 = ax == 0 ? rA.y * rA.y + rA.z * rA.z : (ax == 1 ? rA.x * rA.x + rA.z * rA.z : rA.x * rA.x + rA.y * rA.y);
-    float b2 = ax == 0 ? rB.y * rB.y + rB.z * rB.z : (ax == 1 ? rB.x * rB.x + rB.z * rB.z : rB.x * rB.x + rB.y * rB.y);
-    return 1.0f / (A.im + B.im + A.ii * a2 + B.ii * b2);
+    float a2 = ax == 0 ? fmaf(rA.y, rA.y, rA.z * rA.z) : (ax == 1 ? fmaf(rA.x, rA.x, rA.z * rA.z) : fmaf(rA.x, rA.x, rA.y * rA.y));
+    float b2 = ax == 0 ? fmaf(rB.y, rB.y, rB.z * rB.z) : (ax == 1 ? fmaf(rB.x, rB.x, rB.z * rB.z) : fmaf(rB.x, rB.x, rB.y * rB.y));
+    return __frcp_rn(fmaf(B.ii, b2, fmaf(A.ii, a2, A.im + B.im)));
 }
 
 __device__ __forceinline__ void joint_rows(Body &A, Body &B, float4 r0, float4 r1, float4 r2, float4 &lam) {
@@ -345,7 +356,7 @@ __device__ __forceinline__ float contact_residual_sq(const Body &A, const Body &
     const float ra = r1.x, rb = r1.y, target = r1.z;
     const float3 t2 = cross3(n, t1);
     float3 dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
-    float3 u = make_float3(ra * A.w.x + rb * B.w.x, ra * A.w.y + rb * B.w.y, ra * A.w.z + rb * B.w.z);
+    float3 u = lever_sum(ra, A.w, rb, B.w);
     float wn = dot3(n, dv), w1 = dot3(t1, dv) - dot3(t2, u), w2 = dot3(t2, dv) + dot3(t1, u);
     float lim = mu * lam.x;
     float e0 = (lam.x - fmaxf(lam.x + kn * (target - wn), 0.f)) / kn;
