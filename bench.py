@@ -52,7 +52,7 @@ ENTRY_BYTES = 120        # per (body, worker) per step: 60 B state + params read
 PAIR_ONCE_BYTES = 24     # per constraint per step: warm-start lambda read + final lambda write
 # DRAM bytes of the solve over its algorithmic bytes, from the ncu capture
 # summarised in profiles/k_solve_pile_large.md (every solver launch of the two
-# timed steps: 0.292 GB of DRAM traffic for 7.40 GB of algorithmic bytes; the
+# timed steps: 0.294 GB of DRAM traffic for 7.52 GB of algorithmic bytes; the
 # row records stay in L2 across sweeps).  Valid for the captured kernel only:
 # set to None when k_solve changes, until it is captured again.
 SOLVE_DRAM_PER_ALGORITHMIC_BYTE = 0.039

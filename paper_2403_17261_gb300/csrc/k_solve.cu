@@ -48,10 +48,6 @@ namespace ovl {
 namespace {
 
 constexpr int SOLVE_THREADS = 512;
-// Two rows per thread with the masses in shared memory: 640 threads at 96
-// registers (20 warps per SM instead of 16) measured 5 % faster than 512 at
-// 124; with the masses in the rows the extra spills made it slower.
-constexpr int SOLVE_THREADS_WIDE = 640;
 
 // The file is built without FMA contraction, and its fused multiply-adds are
 // written out (fmaf): every instantiation (cluster size, rows per thread,
@@ -203,6 +199,17 @@ __device__ __forceinline__ void fetch_row(const SolveArgs &a, int r, bool joint,
     w.joint = joint;
     w.x = a.r0[r];
     w.y = a.r1[r];
+    if (joint) w.z = a.r2[r];
+    if (!S::kMasses) {
+        w.m = a.r3[r];
+        if (!joint) w.t = a.r4[r];
+    }
+}
+
+// the records after r0 and r1 (those come from a RowPre)
+template <class S>
+__device__ __forceinline__ void fetch_row_rest(const SolveArgs &a, int r, bool joint, Row &w) {
+    w.joint = joint;
     if (joint) w.z = a.r2[r];
     if (!S::kMasses) {
         w.m = a.r3[r];
@@ -394,6 +401,44 @@ __device__ __forceinline__ void group_sync() {
     else cg::this_cluster().sync();
 }
 
+// The group barrier in two halves: arrive releases this thread's body
+// stores, wait acquires the other threads'.  Loads issued between the two
+// wait for neither.
+template <int C>
+__device__ __forceinline__ void group_arrive() {
+    if (C > 1) asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+template <int C>
+__device__ __forceinline__ void group_wait() {
+    if (C == 1) __syncthreads();
+    else asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// r0, r1 and the impulse of a thread's next two rows of a bucket (rows r and
+// r + T of a bucket ending at ce).  Row records are read-only during the
+// solve and a row's impulse is read and written by one thread only, so they
+// may be loaded a pass, or a colour, ahead.
+struct RowPre {
+    float4 x0, y0, l0, x1, y1, l1;
+};
+
+__device__ __forceinline__ void pre_rows(const SolveArgs &a, int r, int ce, int T, RowPre &p) {
+    // every field is written on every path, so the previous values are dead
+    // once used
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    p.x0 = p.y0 = p.l0 = p.x1 = p.y1 = p.l1 = z;
+    if (r < ce) {
+        p.x0 = a.r0[r];
+        p.y0 = a.r1[r];
+        p.l0 = a.rlam[r];
+    }
+    if (r + T < ce) {
+        p.x1 = a.r0[r + T];
+        p.y1 = a.r1[r + T];
+        p.l1 = a.rlam[r + T];
+    }
+}
+
 // group-wide sum of one value per thread (every thread gets the total)
 template <int C>
 __device__ float group_sum(float v, float *red, float *slot) {
@@ -449,7 +494,7 @@ __device__ float rows_residual_sq(const SolveArgs &a, const S &st, const Buckets
 // its owner bucket, thread tid the rows tid, tid + T, ..., U of them at a
 // time.  With C = 1 (one CTA, or the global-memory path) the CTA holds every
 // slot and takes every bucket.
-template <int C, int U, class S>
+template <int C, int U, bool P, class S>
 __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, int per, const Buckets &bk,
                              int row0, int row1) {
     __shared__ float red[32];
@@ -503,22 +548,36 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
       }
       group_sync<C>();
     }
-    // Gauss-Seidel sweeps
+    // Gauss-Seidel sweeps.  P (full-size CTAs, one per SM, with the masses in
+    // shared memory and two rows per thread): a pass takes r0, r1 and the
+    // impulses of its rows from registers loaded ahead, at the end of the
+    // previous pass or, for a colour's first pass, between the two halves of
+    // the previous colour's barrier.  (Measured: 4 % faster there, 7 % slower
+    // in the 256-thread CTAs that share an SM, which keep the plain loop.)
     int it_done = 0;
+    constexpr bool piped = P && U == 2 && S::kMasses;
+    const bool ahead = piped && bk.nbk == 1;
+    RowPre pf;
+    if (ahead && a.iters > 0 && ncol > 0) pre_rows(a, bk.tab[0] + tid, bk.tab[2], T, pf);
     for (int it = 0; it < a.iters; ++it) {
         for (int c = 0; c < ncol; ++c) {
           for (int k = 0; k < bk.nbk; ++k) {
             const int o = c * bk.cs + 2 * k;
             const int jb = bk.tab[o + 1], ce = bk.tab[o + 2];
             int r = bk.tab[o] + tid;
-            if (U == 2) {
+            if constexpr (piped) {
+                RowPre cur;
+                if (ahead) cur = pf;
+                else pre_rows(a, r, ce, T, cur);
                 // two rows of the colour at once (independent: no shared body)
                 for (; r + T < ce; r += 2 * T) {
                     const int q = r + T;
                     Row u, w;
-                    fetch_row<S>(a, r, r >= jb, u);
-                    fetch_row<S>(a, q, q >= jb, w);
-                    float4 xl = a.rlam[r], yl = a.rlam[q];
+                    u.x = cur.x0; u.y = cur.y0;
+                    w.x = cur.x1; w.y = cur.y1;
+                    fetch_row_rest<S>(a, r, r >= jb, u);
+                    fetch_row_rest<S>(a, q, q >= jb, w);
+                    float4 xl = cur.l0, yl = cur.l1;
                     Body A, B, D, E;
                     load_pair(st, u, A, B);
                     load_pair(st, w, D, E);
@@ -528,20 +587,62 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                     store_pair(st, row_slots(w), D, E);
                     a.rlam[r] = xl;
                     a.rlam[q] = yl;
+                    pre_rows(a, r + 2 * T, ce, T, cur);
+                }
+                if (r < ce) {
+                    Row w;
+                    w.x = cur.x0; w.y = cur.y0;
+                    fetch_row_rest<S>(a, r, r >= jb, w);
+                    float4 lam = cur.l0;
+                    Body A, B;
+                    load_pair(st, w, A, B);
+                    solve_row<S>(A, B, w, mu, lam);
+                    store_pair(st, row_slots(w), A, B);
+                    a.rlam[r] = lam;
+                }
+            } else {
+                if (U == 2) {
+                    // two rows of the colour at once (independent: no shared body)
+                    for (; r + T < ce; r += 2 * T) {
+                        const int q = r + T;
+                        Row u, w;
+                        fetch_row<S>(a, r, r >= jb, u);
+                        fetch_row<S>(a, q, q >= jb, w);
+                        float4 xl = a.rlam[r], yl = a.rlam[q];
+                        Body A, B, D, E;
+                        load_pair(st, u, A, B);
+                        load_pair(st, w, D, E);
+                        solve_row<S>(A, B, u, mu, xl);
+                        solve_row<S>(D, E, w, mu, yl);
+                        store_pair(st, row_slots(u), A, B);
+                        store_pair(st, row_slots(w), D, E);
+                        a.rlam[r] = xl;
+                        a.rlam[q] = yl;
+                    }
+                }
+                for (; r < ce; r += T) {
+                    Row w;
+                    fetch_row<S>(a, r, r >= jb, w);
+                    float4 lam = a.rlam[r];
+                    Body A, B;
+                    load_pair(st, w, A, B);
+                    solve_row<S>(A, B, w, mu, lam);
+                    store_pair(st, row_slots(w), A, B);
+                    a.rlam[r] = lam;
                 }
             }
-            for (; r < ce; r += T) {
-                Row w;
-                fetch_row<S>(a, r, r >= jb, w);
-                float4 lam = a.rlam[r];
-                Body A, B;
-                load_pair(st, w, A, B);
-                solve_row<S>(A, B, w, mu, lam);
-                store_pair(st, row_slots(w), A, B);
-                a.rlam[r] = lam;
-            }
           }
-          group_sync<C>();
+          if (ahead) {
+              group_arrive<C>();
+              const bool last = c + 1 == ncol;
+              if (!last || it + 1 < a.iters) {
+                  const int on = last ? 0 : (c + 1) * bk.cs;
+                  pre_rows(a, bk.tab[on] + tid, bk.tab[on + 2], T, pf);
+              }
+              group_wait<C>();
+          } else {
+              group_sync<C>();
+          }
         }
         it_done = it + 1;
         if (a.res_tol > 0.f && a.res_check_every > 0 && it_done % a.res_check_every == 0 && it_done < a.iters) {
@@ -589,11 +690,10 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
 // C CTAs per worker; a worker's slots are spread over their shared memory when
 // they fit (ceil(nb / C) <= smem_slots), else CTA rank 0 solves it alone with
 // its body state in the global scratch area.  M: the shared-memory slots hold
-// the masses (32 B per slot) and contact rows are read as two records.  W:
-// the wide launch (SOLVE_THREADS_WIDE threads, one CTA per SM).
-template <int C, int U, bool M, bool W>
-__global__ void __launch_bounds__(W ? SOLVE_THREADS_WIDE : SOLVE_THREADS, U == 1 ? 2 : 1)
-k_solve(SolveArgs a) {
+// the masses (32 B per slot) and contact rows are read as two records.  P:
+// rows loaded ahead (launches of SOLVE_THREADS threads, one CTA per SM).
+template <int C, int U, bool M, bool P>
+__global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveArgs a) {
     extern __shared__ float4 sm[];
     const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
     const int p = a.order ? (int)a.order[blockIdx.x / C] : (int)(blockIdx.x / C);
@@ -618,25 +718,25 @@ k_solve(SolveArgs a) {
             float4 *B = sm + per;
             if (C == 1) {
                 LocalSlotsM st{A, B};
-                solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+                solve_worker<C, U, P>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             } else {
                 ClusterSlotsM<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B), per};
-                solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+                solve_worker<C, U, P>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             }
         } else {
             float2 *B = reinterpret_cast<float2 *>(sm + per);
             if (C == 1) {
                 LocalSlots st{A, B};
-                solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+                solve_worker<C, U, P>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             } else {
                 ClusterSlots<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B), per};
-                solve_worker<C, U>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+                solve_worker<C, U, P>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             }
         }
     } else if (rank == 0) {
         // one CTA takes the whole worker: every owner bucket of every colour
         LocalSlots st{a.scratch + (size_t)b0, reinterpret_cast<float2 *>(a.scratch + (size_t)a.n_entries) + b0};
-        solve_worker<1, U>(a, st, p, 0, nb, Buckets{goff, 2 * OWNER_RANKS, OWNER_RANKS}, row0, row1);
+        solve_worker<1, U, false>(a, st, p, 0, nb, Buckets{goff, 2 * OWNER_RANKS, OWNER_RANKS}, row0, row1);
     }
 }
 
@@ -646,10 +746,10 @@ int solve_smem_bytes(int slots, bool masses) {
     return slots * (int)(masses ? 2 * sizeof(float4) : sizeof(float4) + sizeof(float2));
 }
 
-template <int C, int U, bool M, bool W>
+template <int C, int U, bool M, bool P>
 static void launch_solve_c(const SolveArgs &a, int threads, cudaStream_t s) {
     int smem = solve_smem_bytes(a.smem_slots, M);
-    CK(cudaFuncSetAttribute(k_solve<C, U, M, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaFuncSetAttribute(k_solve<C, U, M, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.n_parts * C);
     cfg.blockDim = dim3(threads);
@@ -662,19 +762,19 @@ static void launch_solve_c(const SolveArgs &a, int threads, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, k_solve<C, U, M, W>, a));
+    CK(cudaLaunchKernelEx(&cfg, k_solve<C, U, M, P>, a));
     note_launch();
 }
 
-template <int U, bool M, bool W>
+template <int U, bool M, bool P>
 static void launch_solve_u(const SolveArgs &a, int threads, int cluster, cudaStream_t s) {
     switch (cluster) {
-        case 8: launch_solve_c<8, U, M, W>(a, threads, s); break;
-        case 6: launch_solve_c<6, U, M, W>(a, threads, s); break;
-        case 4: launch_solve_c<4, U, M, W>(a, threads, s); break;
-        case 3: launch_solve_c<3, U, M, W>(a, threads, s); break;
-        case 2: launch_solve_c<2, U, M, W>(a, threads, s); break;
-        default: launch_solve_c<1, U, M, W>(a, threads, s); break;
+        case 8: launch_solve_c<8, U, M, P>(a, threads, s); break;
+        case 6: launch_solve_c<6, U, M, P>(a, threads, s); break;
+        case 4: launch_solve_c<4, U, M, P>(a, threads, s); break;
+        case 3: launch_solve_c<3, U, M, P>(a, threads, s); break;
+        case 2: launch_solve_c<2, U, M, P>(a, threads, s); break;
+        default: launch_solve_c<1, U, M, P>(a, threads, s); break;
     }
 }
 
@@ -682,8 +782,8 @@ void launch_solve(const SolveArgs &a, int threads, int cluster, int unroll, bool
     if (!a.n_parts) return;
     if (threads > SOLVE_THREADS) threads = SOLVE_THREADS;
     if (unroll == 2) {
-        // a full-size CTA (one per SM) with the masses in shared memory goes wide
-        if (masses && threads == SOLVE_THREADS) launch_solve_u<2, true, true>(a, SOLVE_THREADS_WIDE, cluster, s);
+        // a full-size CTA (one per SM) with the masses in shared memory loads rows ahead
+        if (masses && threads == SOLVE_THREADS) launch_solve_u<2, true, true>(a, threads, cluster, s);
         else if (masses) launch_solve_u<2, true, false>(a, threads, cluster, s);
         else launch_solve_u<2, false, false>(a, threads, cluster, s);
     } else {
