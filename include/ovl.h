@@ -225,6 +225,43 @@ ovl_status ovl_step(ovl_ctx *ctx, float dt, int32_t iters);
  * Synchronises the context's stream. */
 ovl_status ovl_joint_error(ovl_ctx *ctx, double *sum, double *max_gap);
 
+/* ---- host-only entry points (no context, no CUDA call) -------------------
+ * The library's own host implementations of the membership algorithms, run
+ * on caller-supplied arrays; a step runs the same code after reading its
+ * contacts back from the device.  Scenes are contiguous body ranges:
+ * scene_of_body[n] is non-decreasing with values in [0, n_scenes); scene s
+ * has n_sets[s] workers (1..64) and growth depth scene_gamma[s] >= 0.
+ * mask[n] (in/out): bit w of mask[b] = body b active in worker w of its
+ * scene; bits at or above the scene's n_sets give OVL_ERR_MEMBERSHIP.  Any
+ * other malformed input gives OVL_ERR_ARG and leaves mask unchanged.  The
+ * caller owns every array. */
+
+/* LOADBALANCE (Algorithm 6, Section 5.4) with BRIDGE (Algorithm 7).
+ * row_ptr[n + 1], col: CSR of the constraint graph G^t (edges inside one
+ * scene).  contact_bodies[2 n_contacts]: the candidate contacts (a, b), in
+ * the order they are processed (the step uses canonical order: ascending
+ * (a, b), dynamic ends only); scenes must appear in ascending order.
+ * contact_count[n]: NULL counts every active body once in the loads <W>
+ * (Table 1); else body b counts 1 + contact_count[b] (the contact load).
+ * do_activate / do_deactivate select the activation and the removal
+ * branches.  threads (1..64): whole scenes go to up to that many host
+ * threads; the result is the sequential one. */
+ovl_status ovl_host_load_balance(int32_t n, const int32_t *scene_of_body, int32_t n_scenes,
+                                 const int32_t *n_sets, const int32_t *scene_gamma, uint64_t *mask,
+                                 const int32_t *row_ptr, const int32_t *col, int64_t n_contacts,
+                                 const int32_t *contact_bodies, const int32_t *contact_count,
+                                 int32_t do_activate, int32_t do_deactivate, int32_t threads);
+
+/* ASSIGNTOOVERLAPSET (Algorithm 2) and GROWOVERLAP (Algorithm 3, Section
+ * 5.1) over the joints in index order: a joint between two dynamic bodies
+ * (inv_mass > 0) of different single workers makes each end active in the
+ * other's worker and grows the overlap to depth gamma over the articulated
+ * structure.  joint_bodies[2 n_joints]: body indices, -1 for the world. */
+ovl_status ovl_host_assign_overlap(int32_t n, const int32_t *scene_of_body, int32_t n_scenes,
+                                   const int32_t *n_sets, const int32_t *scene_gamma,
+                                   const float *inv_mass, int32_t n_joints,
+                                   const int32_t *joint_bodies, uint64_t *mask);
+
 /* LOADBALANCE (Algorithm 6 with BRIDGE, Algorithm 7) alone on the contacts
  * of the current state.  flags bit 0: activation branch, bit 1: removal
  * branches. */

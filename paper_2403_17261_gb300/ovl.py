@@ -51,6 +51,7 @@ EXPORTED = [
     "ovl_geodesics_static", "ovl_set_warmstart_mode", "ovl_read_features", "ovl_mlp_set_params",
     "ovl_mlp_get_params", "ovl_mlp_forward", "ovl_log_reserve", "ovl_log_enable", "ovl_log_size",
     "ovl_log_append", "ovl_log_read", "ovl_mlp_train", "ovl_mlp_grad", "ovl_mlp_loss",
+    "ovl_host_load_balance", "ovl_host_assign_overlap",
 ]
 
 
@@ -154,6 +155,9 @@ def load_library(path: str | None = None):
         "ovl_mlp_loss": [vp, C.c_int64, C.c_int64, C.POINTER(C.c_double)],
         "ovl_geodesics_static": [C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_int32, vp, vp,
                                  C.c_int32, vp, vp, C.c_char_p, C.c_int32],
+        "ovl_host_load_balance": [C.c_int32, _ip, C.c_int32, _ip, _ip, _u64p, _ip, _ip, C.c_int64, _ip, _ip,
+                                  C.c_int32, C.c_int32, C.c_int32],
+        "ovl_host_assign_overlap": [C.c_int32, _ip, C.c_int32, _ip, _ip, _fp, C.c_int32, _ip, _u64p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -346,6 +350,42 @@ def ovl_geodesics_static(n_bodies: int, n_workers: int, beta: int, row_ptr, col,
         buf, len(buf))
     if rc != OVL_OK:
         raise OvlError(rc, buf.value.decode())
+
+
+def _i32c(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def ovl_host_load_balance(masks, scene_of_body, n_sets, scene_gamma, row_ptr, col, contact_pairs,
+                          contact_count=None, do_activate: bool = True, do_deactivate: bool = True,
+                          threads: int = 1):
+    """Algorithm 6 (with Algorithm 7) by the library's host code, no GPU
+    needed; returns the new masks (the input is not modified)."""
+    m = np.array(masks, dtype=np.uint64, copy=True)
+    sob, ns, sg = _i32c(scene_of_body), _i32c(n_sets), _i32c(scene_gamma)
+    rp, cl = _i32c(row_ptr), _i32c(col)
+    cp = _i32c(contact_pairs).reshape(-1, 2)
+    cc = None if contact_count is None else _i32c(contact_count)
+    rc = load_library().ovl_host_load_balance(
+        m.shape[0], _ptr(sob, _ip), ns.shape[0], _ptr(ns, _ip), _ptr(sg, _ip), _ptr(m, _u64p),
+        _ptr(rp, _ip), _ptr(cl, _ip), cp.shape[0], _ptr(cp, _ip), None if cc is None else _ptr(cc, _ip),
+        int(do_activate), int(do_deactivate), int(threads))
+    _check(None, rc)
+    return m
+
+
+def ovl_host_assign_overlap(masks, scene_of_body, n_sets, scene_gamma, inv_mass, joints):
+    """Algorithms 2-3 by the library's host code, no GPU needed; returns the
+    new masks (the input is not modified)."""
+    m = np.array(masks, dtype=np.uint64, copy=True)
+    sob, ns, sg = _i32c(scene_of_body), _i32c(n_sets), _i32c(scene_gamma)
+    im = np.ascontiguousarray(inv_mass, dtype=np.float32)
+    j = _i32c(joints).reshape(-1, 2)
+    rc = load_library().ovl_host_assign_overlap(
+        m.shape[0], _ptr(sob, _ip), ns.shape[0], _ptr(ns, _ip), _ptr(sg, _ip),
+        _ptr(im, _fp), j.shape[0], _ptr(j, _ip), _ptr(m, _u64p))
+    _check(None, rc)
+    return m
 
 
 def ovl_read_stats(ctx) -> dict:
