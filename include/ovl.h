@@ -262,6 +262,49 @@ ovl_status ovl_host_assign_overlap(int32_t n, const int32_t *scene_of_body, int3
                                    const float *inv_mass, int32_t n_joints,
                                    const int32_t *joint_bodies, uint64_t *mask);
 
+/* ---- box contact geometry (no context) -----------------------------------
+ * Contacts of the box bodies of the paper's Building and Bridge scenes
+ * (Section 6), one pair per index, computed by the library's FP32 contact
+ * functions: on the GPU (on_gpu != 0: one thread per pair; the inputs are
+ * copied to the device and the results back) or with the same functions on
+ * the host (on_gpu == 0: no CUDA call).  Both runs give the same bits.  All
+ * arrays are host arrays the caller owns.  A box is pose[7] = (x, y, z, qw,
+ * qx, qy, qz) (unit quaternion) and half[3] (half extents).  The normal
+ * points from the first shape towards the second; a gap is positive when
+ * apart; a contact when gap <= margin.  Outputs per pair i: count[i] (0..4),
+ * points[i][4][3] and gaps[i][4] (the first count[i] entries; the rest
+ * zero), normal[i][3].  The step does not use these contacts yet.
+ * n < 0 or a NULL array with n > 0 is OVL_ERR_ARG; a CUDA failure
+ * OVL_ERR_CUDA. */
+
+/* Box (first) against the plane n.x = d, plane[i] = (n, d) with n unit out
+ * of the solid: the box's vertices within the margin, the 4 deepest (ties to
+ * the lower vertex index, vertex v at (+-h0, +-h1, +-h2) by bits 0-2 of v).
+ * normal = -n. */
+ovl_status ovl_box_plane_contacts(int32_t n, const float *pose, const float *half, const float *plane,
+                                  float margin, int32_t on_gpu, int32_t *count, float *points, float *gaps,
+                                  float *normal);
+
+/* Sphere (first; sphere[i] = (centre, radius)) against a box (second): the
+ * box point nearest the centre, or with the centre inside the box its
+ * projection on the face of least penetration.  gaps[i][0] holds the gap
+ * even when count[i] == 0. */
+ovl_status ovl_sphere_box_contacts(int32_t n, const float *sphere, const float *pose, const float *half,
+                                   float margin, int32_t on_gpu, int32_t *count, float *points, float *gaps,
+                                   float *normal);
+
+/* Box A (first) against box B (second): the separating-axis test over the
+ * 15 candidate axes; axis[i] = the chosen one (0-2 A's faces, 3-5 B's, 6 +
+ * 3 i + j for a_i x b_j) or -1 when an axis separates them by more than the
+ * margin.  A face axis gives the incident face clipped against the
+ * reference face's sides (the 4 deepest points); an edge axis one point
+ * midway between the supporting edges.  An edge axis is chosen over the best
+ * face axis only when its separation exceeds 0.95 x the face's + 0.01 x the
+ * smallest half extent. */
+ovl_status ovl_box_box_contacts(int32_t n, const float *pose_a, const float *half_a, const float *pose_b,
+                                const float *half_b, float margin, int32_t on_gpu, int32_t *count,
+                                float *points, float *gaps, float *normal, int32_t *axis);
+
 /* LOADBALANCE (Algorithm 6 with BRIDGE, Algorithm 7) alone on the contacts
  * of the current state.  flags bit 0: activation branch, bit 1: removal
  * branches. */

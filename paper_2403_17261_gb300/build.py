@@ -23,7 +23,11 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The solver is compiled without fused multiply-add contraction so that every
 # launch shape (CTAs per worker, threads, rows per thread) executes the same
 # IEEE operations and produces the same bits.
-PER_FILE_FLAGS = {"k_solve.cu": ["-fmad=false"]}
+PER_FILE_FLAGS = {
+    "k_solve.cu": ["-fmad=false"],
+    # host and device runs of the box geometry must round alike
+    "k_box.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"],
+}
 
 
 def _nvcc() -> str:

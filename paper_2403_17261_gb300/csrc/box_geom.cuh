@@ -1,0 +1,249 @@
+// box_geom.cuh -- contact geometry of boxes (FP32), for the box and plank
+// bodies of the paper's Building and Bridge scenes (Section 6): box-plane,
+// sphere-box and box-box (separating axes of two oriented boxes, then a
+// clipped face manifold of up to 4 points or one edge point).  The
+// functions are __host__ __device__ and use only IEEE-rounded operations
+// (no rsqrt, no implicit contraction in the files that include this), so
+// host and device runs give the same bits.
+//
+// Conventions: the normal points from the first shape towards the second;
+// gap > 0 when apart; a contact when gap <= margin; quaternions as float4
+// (x = w, y..w = vector part).  Selection rules: the 4 deepest points, ties
+// to the lower candidate index; an edge axis is taken over the best face
+// axis only if its separation exceeds 0.95 x the face's + 0.01 x the
+// smallest half extent; ties between axes go to the lower index (A's faces,
+// B's faces, then a_i x b_j with i major).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace ovl {
+namespace box {
+
+#define OVL_HD __host__ __device__ __forceinline__
+
+OVL_HD float3 v3(float x, float y, float z) { return make_float3(x, y, z); }
+OVL_HD float3 add(float3 a, float3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+OVL_HD float3 sub(float3 a, float3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+OVL_HD float3 scl(float3 a, float s) { return v3(a.x * s, a.y * s, a.z * s); }
+OVL_HD float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+OVL_HD float3 crs(float3 a, float3 b) { return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+OVL_HD float comp(float3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+// an oriented box: centre, world directions of its three axes, half extents
+struct Obb {
+    float3 c, u[3];
+    float h[3];
+};
+
+OVL_HD Obb make_obb(float3 c, float4 q, float3 h) {
+    const float w = q.x, x = q.y, y = q.z, z = q.w;
+    Obb b;
+    b.c = c;
+    b.u[0] = v3(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
+    b.u[1] = v3(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
+    b.u[2] = v3(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
+    b.h[0] = h.x; b.h[1] = h.y; b.h[2] = h.z;
+    return b;
+}
+
+// point of the box for local coordinates (a, b, c)
+OVL_HD float3 at(const Obb &B, float a, float b, float c) {
+    return add(B.c, add(add(scl(B.u[0], a), scl(B.u[1], b)), scl(B.u[2], c)));
+}
+
+// candidates (points, gaps) kept: the k deepest, ties to the lower index;
+// n <= 16, written back compacted in order of depth
+OVL_HD int keep_deepest(float3 *P, float *G, int n, int k) {
+    for (int i = 0; i < n && i < k; ++i) {            // selection by (gap, index)
+        int m = i;
+        for (int j = i + 1; j < n; ++j)
+            if (G[j] < G[m]) m = j;
+        if (m != i) {
+            // rotate [i, m] right by one so that equal gaps keep their order
+            const float3 pm = P[m];
+            const float gm = G[m];
+            for (int j = m; j > i; --j) { P[j] = P[j - 1]; G[j] = G[j - 1]; }
+            P[i] = pm;
+            G[i] = gm;
+        }
+    }
+    return n < k ? n : k;
+}
+
+// Box (first) against the plane n.x = d (plane = (n, d), n unit, out of the
+// solid).  normal = -n.  Returns the count (<= 4).
+OVL_HD int box_plane(const Obb &B, float4 plane, float margin, float3 pts[4], float gaps[4], float3 &normal) {
+    const float3 n = v3(plane.x, plane.y, plane.z);
+    float3 P[8];
+    float G[8];
+    int m = 0;
+    for (int v = 0; v < 8; ++v) {
+        const float3 p = at(B, (v & 1) ? B.h[0] : -B.h[0], (v & 2) ? B.h[1] : -B.h[1], (v & 4) ? B.h[2] : -B.h[2]);
+        const float g = dot(n, p) - plane.w;
+        if (g <= margin) { P[m] = p; G[m] = g; ++m; }
+    }
+    m = keep_deepest(P, G, m, 4);
+    for (int i = 0; i < m; ++i) { pts[i] = P[i]; gaps[i] = G[i]; }
+    normal = scl(n, -1.f);
+    return m;
+}
+
+// Sphere (first: centre s, radius r) against a box (second): the point of
+// the box nearest the centre, or with the centre inside its projection on
+// the face of least penetration.  Returns 1 when gap <= margin (outputs are
+// written either way).
+OVL_HD int sphere_box(float3 s, float r, const Obb &B, float margin, float3 &pt, float3 &normal, float &gap) {
+    const float3 d = sub(s, B.c);
+    float loc[3], cl[3];
+    bool inside = true;
+    for (int k = 0; k < 3; ++k) {
+        loc[k] = dot(d, B.u[k]);
+        cl[k] = fminf(fmaxf(loc[k], -B.h[k]), B.h[k]);
+        if (cl[k] != loc[k]) inside = false;
+    }
+    float3 nb;                                        // box -> sphere, world
+    if (!inside) {
+        const float e0 = loc[0] - cl[0], e1 = loc[1] - cl[1], e2 = loc[2] - cl[2];
+        const float len = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
+        nb = add(add(scl(B.u[0], e0 / len), scl(B.u[1], e1 / len)), scl(B.u[2], e2 / len));
+        gap = len - r;
+    } else {
+        int k = 0;
+        float pen = B.h[0] - fabsf(loc[0]);
+        for (int j = 1; j < 3; ++j) {
+            const float pj = B.h[j] - fabsf(loc[j]);
+            if (pj < pen) { pen = pj; k = j; }
+        }
+        const float sg = loc[k] >= 0.f ? 1.f : -1.f;
+        cl[k] = sg * B.h[k];
+        nb = scl(B.u[k], sg);
+        gap = -pen - r;
+    }
+    pt = at(B, cl[0], cl[1], cl[2]);
+    normal = scl(nb, -1.f);
+    return gap <= margin;
+}
+
+// separation along the unit axis L: |T.L| minus both boxes' half widths
+OVL_HD float axis_sep(const Obb &A, const Obb &B, float3 T, float3 L) {
+    float s = fabsf(dot(T, L));
+    for (int k = 0; k < 3; ++k) s -= A.h[k] * fabsf(dot(A.u[k], L)) + B.h[k] * fabsf(dot(B.u[k], L));
+    return s;
+}
+
+// keep the part of polygon P (n points) with dot(x, e) <= off (convex clip)
+OVL_HD int clip_half(const float3 *P, int n, float3 e, float off, float3 *Q) {
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        const float3 a = P[i], b = P[i + 1 == n ? 0 : i + 1];
+        const float da = dot(a, e) - off, db = dot(b, e) - off;
+        if (da <= 0.f) Q[m++] = a;
+        if ((da <= 0.f) != (db <= 0.f)) Q[m++] = add(a, scl(sub(b, a), da / (da - db)));
+    }
+    return m;
+}
+
+// Box A (first) against box B (second).  Returns the count (0 when an axis
+// separates them by more than the margin; axis = -1 then).  normal: A -> B.
+OVL_HD int box_box(const Obb &A, const Obb &B, float margin, float3 pts[4], float gaps[4], float3 &normal,
+                   int &axis, float &sep) {
+    axis = -1;
+    const float3 T = sub(B.c, A.c);
+    float3 L[15];
+    float s[15];
+    bool ok[15];
+    for (int k = 0; k < 3; ++k) {
+        L[k] = A.u[k];
+        L[3 + k] = B.u[k];
+        ok[k] = ok[3 + k] = true;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const int k = 6 + 3 * i + j;
+            const float3 x = crs(A.u[i], B.u[j]);
+            const float len = sqrtf(dot(x, x));
+            ok[k] = len > 1e-6f;
+            L[k] = ok[k] ? scl(x, 1.f / len) : v3(0.f, 0.f, 0.f);
+        }
+    for (int k = 0; k < 15; ++k) {
+        s[k] = ok[k] ? axis_sep(A, B, T, L[k]) : -INFINITY;
+        if (s[k] > margin) return 0;
+    }
+    int face = 0, edge = -1;
+    for (int k = 1; k < 6; ++k)
+        if (s[k] > s[face]) face = k;
+    for (int k = 6; k < 15; ++k)
+        if (ok[k] && (edge < 0 || s[k] > s[edge])) edge = k;
+    float hmin = A.h[0];
+    for (int k = 0; k < 3; ++k) hmin = fminf(hmin, fminf(A.h[k], B.h[k]));
+    const int best = (edge >= 0 && s[edge] > 0.95f * s[face] + 0.01f * hmin) ? edge : face;
+    axis = best;
+    sep = s[best];
+    normal = dot(T, L[best]) < 0.f ? scl(L[best], -1.f) : L[best];
+
+    if (best >= 6) {
+        // the two supporting edges: A's along a_i nearest B, B's along b_j nearest A
+        const int i = (best - 6) / 3, j = (best - 6) % 3;
+        float3 pa = A.c, pb = B.c;
+        for (int k = 0; k < 3; ++k) {
+            if (k != i) pa = add(pa, scl(A.u[k], dot(A.u[k], normal) >= 0.f ? A.h[k] : -A.h[k]));
+            if (k != j) pb = add(pb, scl(B.u[k], dot(B.u[k], normal) <= 0.f ? B.h[k] : -B.h[k]));
+        }
+        // nearest points of pa + t a_i (|t| <= h) and pb + v b_j (|v| <= h)
+        const float3 w = sub(pa, pb);
+        const float c = dot(A.u[i], B.u[j]), e = dot(A.u[i], w), f = dot(B.u[j], w);
+        const float den = 1.f - c * c;
+        float t = den > 1e-10f ? (c * f - e) / den : 0.f;
+        t = fminf(fmaxf(t, -A.h[i]), A.h[i]);
+        const float v = fminf(fmaxf(c * t + f, -B.h[j]), B.h[j]);
+        t = fminf(fmaxf(c * v - e, -A.h[i]), A.h[i]);
+        pts[0] = scl(add(add(pa, scl(A.u[i], t)), add(pb, scl(B.u[j], v))), 0.5f);
+        gaps[0] = sep;
+        return 1;
+    }
+
+    // face axis: the owner is the reference box, the other the incident one
+    const bool refA = best < 3;
+    const Obb &R = refA ? A : B, &I = refA ? B : A;
+    const int f = best % 3;
+    const float3 nr = refA ? normal : scl(normal, -1.f);   // reference face normal, towards I
+    int fi = 0;
+    float most = -1.f;
+    for (int k = 0; k < 3; ++k) {
+        const float d = fabsf(dot(I.u[k], nr));
+        if (d > most) { most = d; fi = k; }
+    }
+    const float si = dot(I.u[fi], nr) > 0.f ? -1.f : 1.f;
+    const int a1 = fi == 0 ? 1 : 0, a2 = fi == 2 ? 1 : 2;
+    float3 poly[16], tmp[16];
+    const float3 fc = add(I.c, scl(I.u[fi], si * I.h[fi]));
+    const float su[4] = {-1.f, 1.f, 1.f, -1.f}, sv[4] = {-1.f, -1.f, 1.f, 1.f};
+    for (int k = 0; k < 4; ++k)
+        poly[k] = add(fc, add(scl(I.u[a1], su[k] * I.h[a1]), scl(I.u[a2], sv[k] * I.h[a2])));
+    int m = 4;
+    const int r1 = f == 0 ? 1 : 0, r2 = f == 2 ? 1 : 2;
+    const int side[2] = {r1, r2};
+    for (int t = 0; t < 2 && m > 0; ++t) {
+        const float3 e = R.u[side[t]];
+        m = clip_half(poly, m, e, dot(R.c, e) + R.h[side[t]], tmp);
+        if (m > 0) m = clip_half(tmp, m, scl(e, -1.f), -dot(R.c, e) + R.h[side[t]], poly);
+    }
+    const float3 rc = add(R.c, scl(nr, R.h[f]));          // reference face centre
+    float3 P[16];
+    float G[16];
+    int kept = 0;
+    for (int k = 0; k < m; ++k) {
+        const float g = dot(sub(poly[k], rc), nr);
+        if (g <= margin) { P[kept] = poly[k]; G[kept] = g; ++kept; }
+    }
+    kept = keep_deepest(P, G, kept, 4);
+    for (int k = 0; k < kept; ++k) { pts[k] = P[k]; gaps[k] = G[k]; }
+    return kept;
+}
+
+#undef OVL_HD
+
+}  // namespace box
+}  // namespace ovl

@@ -52,6 +52,7 @@ EXPORTED = [
     "ovl_mlp_get_params", "ovl_mlp_forward", "ovl_log_reserve", "ovl_log_enable", "ovl_log_size",
     "ovl_log_append", "ovl_log_read", "ovl_mlp_train", "ovl_mlp_grad", "ovl_mlp_loss",
     "ovl_host_load_balance", "ovl_host_assign_overlap",
+    "ovl_box_plane_contacts", "ovl_sphere_box_contacts", "ovl_box_box_contacts",
 ]
 
 
@@ -158,6 +159,9 @@ def load_library(path: str | None = None):
         "ovl_host_load_balance": [C.c_int32, _ip, C.c_int32, _ip, _ip, _u64p, _ip, _ip, C.c_int64, _ip, _ip,
                                   C.c_int32, C.c_int32, C.c_int32],
         "ovl_host_assign_overlap": [C.c_int32, _ip, C.c_int32, _ip, _ip, _fp, C.c_int32, _ip, _u64p],
+        "ovl_box_plane_contacts": [C.c_int32, _fp, _fp, _fp, C.c_float, C.c_int32, _ip, _fp, _fp, _fp],
+        "ovl_sphere_box_contacts": [C.c_int32, _fp, _fp, _fp, C.c_float, C.c_int32, _ip, _fp, _fp, _fp],
+        "ovl_box_box_contacts": [C.c_int32, _fp, _fp, _fp, _fp, C.c_float, C.c_int32, _ip, _fp, _fp, _fp, _ip],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -386,6 +390,53 @@ def ovl_host_assign_overlap(masks, scene_of_body, n_sets, scene_gamma, inv_mass,
         _ptr(im, _fp), j.shape[0], _ptr(j, _ip), _ptr(m, _u64p))
     _check(None, rc)
     return m
+
+
+def _f32c(a, cols):
+    return np.ascontiguousarray(a, dtype=np.float32).reshape(-1, cols)
+
+
+def _box_out(n):
+    return (np.zeros(n, np.int32), np.zeros((n, 4, 3), np.float32), np.zeros((n, 4), np.float32),
+            np.zeros((n, 3), np.float32))
+
+
+def ovl_box_plane_contacts(pose, half, plane, margin: float, on_gpu: bool = True):
+    """Box-plane contacts per pair (pose [n,7], half [n,3], plane [n,4]).
+    Returns (count, points [n,4,3], gaps [n,4], normal [n,3])."""
+    pose, half, plane = _f32c(pose, 7), _f32c(half, 3), _f32c(plane, 4)
+    n = pose.shape[0]
+    cnt, pts, gaps, nrm = _box_out(n)
+    _check(None, load_library().ovl_box_plane_contacts(
+        n, _ptr(pose, _fp), _ptr(half, _fp), _ptr(plane, _fp), float(margin), int(on_gpu), _ptr(cnt, _ip),
+        _ptr(pts, _fp), _ptr(gaps, _fp), _ptr(nrm, _fp)))
+    return cnt, pts, gaps, nrm
+
+
+def ovl_sphere_box_contacts(sphere, pose, half, margin: float, on_gpu: bool = True):
+    """Sphere-box contacts per pair (sphere [n,4] = centre, radius).  Returns
+    (count, points [n,4,3], gaps [n,4], normal [n,3]); gaps[:, 0] always
+    holds the gap."""
+    sphere, pose, half = _f32c(sphere, 4), _f32c(pose, 7), _f32c(half, 3)
+    n = pose.shape[0]
+    cnt, pts, gaps, nrm = _box_out(n)
+    _check(None, load_library().ovl_sphere_box_contacts(
+        n, _ptr(sphere, _fp), _ptr(pose, _fp), _ptr(half, _fp), float(margin), int(on_gpu), _ptr(cnt, _ip),
+        _ptr(pts, _fp), _ptr(gaps, _fp), _ptr(nrm, _fp)))
+    return cnt, pts, gaps, nrm
+
+
+def ovl_box_box_contacts(pose_a, half_a, pose_b, half_b, margin: float, on_gpu: bool = True):
+    """Box-box contacts per pair.  Returns (count, points [n,4,3], gaps [n,4],
+    normal [n,3], axis [n])."""
+    pa, ha, pb, hb = _f32c(pose_a, 7), _f32c(half_a, 3), _f32c(pose_b, 7), _f32c(half_b, 3)
+    n = pa.shape[0]
+    cnt, pts, gaps, nrm = _box_out(n)
+    axis = np.zeros(n, np.int32)
+    _check(None, load_library().ovl_box_box_contacts(
+        n, _ptr(pa, _fp), _ptr(ha, _fp), _ptr(pb, _fp), _ptr(hb, _fp), float(margin), int(on_gpu),
+        _ptr(cnt, _ip), _ptr(pts, _fp), _ptr(gaps, _fp), _ptr(nrm, _fp), _ptr(axis, _ip)))
+    return cnt, pts, gaps, nrm, axis
 
 
 def ovl_read_stats(ctx) -> dict:
