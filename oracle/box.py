@@ -46,6 +46,11 @@ def lib():
         L.box_box.restype = C.c_int
         L.box_box_axes.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp, _dp]
         L.box_box_axes.restype = None
+        L.box_inv_inertia_world.argtypes = [_dp, _dp, C.c_double, _dp]
+        L.box_inv_inertia_world.restype = None
+        L.box_plane_step.argtypes = [_dp, _dp, _dp, C.c_double, _dp, C.c_double, C.c_double, _dp, C.c_double,
+                                     C.c_double, C.c_double, C.c_int, _dp, _dp, _dp]
+        L.box_plane_step.restype = C.c_int
         _lib = L
     return _lib
 
@@ -94,3 +99,26 @@ def box_box_axes(cA, qA, hA, cB, qB, hB):
     out = np.zeros(15)
     lib().box_box_axes(*[p for _, p in args], out.ctypes.data_as(_dp))
     return out
+
+
+def box_inv_inertia_world(q, h, inv_mass):
+    """World inverse inertia (3x3) of a solid box."""
+    (q, pq), (h, ph) = _v(q, 4), _v(h, 3)
+    out = np.zeros(9)
+    lib().box_inv_inertia_world(pq, ph, float(inv_mass), out.ctypes.data_as(_dp))
+    return out.reshape(3, 3)
+
+
+def box_plane_step(x, q, h, inv_mass, plane, v, w, mu=0.5, dt=1 / 60, g=(0.0, 0.0, -9.81), erp=0.2, slop=0.0,
+                   margin=0.02, iters=200):
+    """One PGS velocity step of a box on a static plane.  Returns
+    (v', w', impulses [k,3] as (n, t1, t2) per contact, contact points,
+    gaps)."""
+    (x, px), (q, pq), (h, ph), (pl, pp), (gg, pg) = _v(x, 3), _v(q, 4), _v(h, 3), _v(plane, 4), _v(g, 3)
+    v2, w2 = np.array(v, dtype=np.float64).copy(), np.array(w, dtype=np.float64).copy()
+    lam = np.zeros(12)
+    k = lib().box_plane_step(px, pq, ph, float(inv_mass), pp, float(mu), float(dt), pg, float(erp), float(slop),
+                             float(margin), int(iters), v2.ctypes.data_as(_dp), w2.ctypes.data_as(_dp),
+                             lam.ctypes.data_as(_dp))
+    pts, gaps, _ = box_plane(x, q, h, plane, margin)
+    return v2, w2, lam[: 3 * k].reshape(k, 3), pts, gaps

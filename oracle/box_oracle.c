@@ -337,3 +337,85 @@ void box_box_axes(const double cA[3], const double qA[4], const double hA[3], co
             }
         }
 }
+
+/* ---- box rows ------------------------------------------------------------
+ * World inverse inertia of a solid box of inverse mass inv_mass and half
+ * extents h: R diag(1 / I_k) R^T with I_k = m/3 (h_j^2 + h_l^2) (j, l the
+ * other two axes).  Iw row-major. */
+void box_inv_inertia_world(const double q[4], const double h[3], double inv_mass, double Iw[9]) {
+    double R[9], d[3];
+    quat_R(q, R);
+    for (int k = 0; k < 3; ++k) {
+        const double a = h[(k + 1) % 3], b = h[(k + 2) % 3];
+        d[k] = inv_mass > 0 ? 3.0 * inv_mass / (a * a + b * b) : 0.0;   /* 1 / I_k */
+    }
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            Iw[3 * r + c] = R[3 * r] * d[0] * R[3 * c] + R[3 * r + 1] * d[1] * R[3 * c + 1] +
+                            R[3 * r + 2] * d[2] * R[3 * c + 2];
+}
+
+static void mat3_vec(const double M[9], const double v[3], double o[3]) {
+    for (int r = 0; r < 3; ++r) o[r] = M[3 * r] * v[0] + M[3 * r + 1] * v[1] + M[3 * r + 2] * v[2];
+}
+
+/* One velocity step (Algorithm 1's solve, Eq 1-7) of a single dynamic box
+ * (first body) against a static plane (second): v += dt g, then `iters`
+ * Gauss-Seidel sweeps over the rows of the box_plane contacts, in their
+ * order, each as normal, t1, t2.  Row d at lever r (contact point minus the
+ * centre): w = -d.v - (r x d).omega, k = 1 / (1/m + (r x d).Iw^-1 (r x d)),
+ * lambda' = clamp(lambda + k (target - w)), and the box takes the impulse
+ * -d (lambda' - lambda).  Normal bounds [0, inf), target -phi/dt when phi >
+ * 0 else erp max(-phi - slop, 0)/dt; tangents bounded by +-mu lambda_n
+ * (current), t1 = normalise(e_k - n_k n) for the axis k of the smallest
+ * |n_k| (ties to the lower index), t2 = n x t1.  v[3], w[3] in/out;
+ * lam[12] = (n, t1, t2) impulses per contact.  Returns the contact count. */
+int box_plane_step(const double x[3], const double q[4], const double h[3], double inv_mass,
+                   const double plane[4], double mu, double dt, const double g[3], double erp, double slop,
+                   double margin, int iters, double v[3], double w[3], double lam[12]) {
+    double pts[12], gaps[4], n[3], Iw[9];
+    const int m = box_plane(x, q, h, plane, margin, pts, gaps, n);
+    box_inv_inertia_world(q, h, inv_mass, Iw);
+    for (int k = 0; k < 3; ++k) v[k] += dt * g[k];
+    /* tangent axis of the normal */
+    int ka = 0;
+    double mn = fabs(n[0]);
+    for (int k = 1; k < 3; ++k)
+        if (fabs(n[k]) < mn) { mn = fabs(n[k]); ka = k; }
+    double t1[3] = {-n[ka] * n[0], -n[ka] * n[1], -n[ka] * n[2]}, t2[3];
+    t1[ka] += 1.0;
+    const double l1 = sqrt(dot3(t1, t1));
+    for (int k = 0; k < 3; ++k) t1[k] /= l1;
+    cross3(n, t1, t2);
+    const double *dirs[3] = {n, t1, t2};
+    double rxd[12][3], Irxd[12][3], kk[12], tgt[12];
+    for (int c = 0; c < m; ++c) {
+        const double r[3] = {pts[3 * c] - x[0], pts[3 * c + 1] - x[1], pts[3 * c + 2] - x[2]};
+        for (int j = 0; j < 3; ++j) {
+            const int i = 3 * c + j;
+            cross3(r, dirs[j], rxd[i]);
+            mat3_vec(Iw, rxd[i], Irxd[i]);
+            kk[i] = 1.0 / (inv_mass + dot3(rxd[i], Irxd[i]));
+            tgt[i] = 0.0;
+            lam[i] = 0.0;
+        }
+        tgt[3 * c] = gaps[c] > 0 ? -gaps[c] / dt : erp * fmax(-gaps[c] - slop, 0.0) / dt;
+    }
+    for (int it = 0; it < iters; ++it)
+        for (int c = 0; c < m; ++c)
+            for (int j = 0; j < 3; ++j) {
+                const int i = 3 * c + j;
+                const double wv = -dot3(dirs[j], v) - dot3(rxd[i], w);
+                double lo = 0.0, hi = INFINITY;
+                if (j > 0) { hi = mu * lam[3 * c]; lo = -hi; }
+                double ln = lam[i] + kk[i] * (tgt[i] - wv);
+                ln = ln < lo ? lo : (ln > hi ? hi : ln);
+                const double dl = ln - lam[i];
+                lam[i] = ln;
+                for (int k = 0; k < 3; ++k) {
+                    v[k] -= inv_mass * dirs[j][k] * dl;
+                    w[k] -= Irxd[i][k] * dl;
+                }
+            }
+    return m;
+}

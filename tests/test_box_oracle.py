@@ -337,3 +337,59 @@ def test_box_box_rigid_motion_invariance():
         np.testing.assert_allclose(out2[2], R2 @ out[2], atol=1e-12)
         np.testing.assert_allclose(out2[1], out[1], atol=1e-11)
         np.testing.assert_allclose(out2[0], out[0] @ R2.T + t2, atol=1e-11)
+
+
+# ---- box rows: inertia and one box on a plane ------------------------------
+def test_box_inertia_matches_a_dense_solid_grid():
+    """R diag(1/I) R^T against the inverse of the inertia tensor summed over
+    a 40^3 grid of the rotated solid (cell centres)."""
+    rng = np.random.default_rng(13)
+    k = 40
+    u = (np.arange(k) + 0.5) / k * 2 - 1
+    G = np.stack(np.meshgrid(u, u, u, indexing="ij"), axis=-1).reshape(-1, 3)
+    for _ in range(4):
+        h, q, m = rng.uniform(0.2, 1.5, 3), random_q(rng), rng.uniform(0.5, 5.0)
+        P = (G * h) @ rot(q).T
+        I = m / P.shape[0] * (np.sum(P * P) * np.eye(3) - P.T @ P)
+        np.testing.assert_allclose(X.box_inv_inertia_world(q, h, 1.0 / m), np.linalg.inv(I),
+                                   rtol=0, atol=2e-3 * np.abs(np.linalg.inv(I)).max())
+
+
+M, G9, DT = 2.0, 9.81, 1.0 / 60.0
+
+
+@pytest.mark.parametrize("yaw", [0.0, 0.7])
+def test_box_resting_on_a_plane_carries_its_weight(yaw):
+    h = [1.0, 0.5, 0.25]
+    v, w, lam, pts, gaps = X.box_plane_step([0.3, -0.2, 0.25], qaxis([0, 0, 1], yaw), h, 1 / M, FLOOR,
+                                            [0, 0, 0], [0, 0, 0], iters=500, dt=DT)
+    assert lam.shape == (4, 3) and np.all(lam[:, 0] >= 0)
+    np.testing.assert_allclose(lam[:, 0].sum(), M * G9 * DT, rtol=1e-12)
+    np.testing.assert_allclose(v, 0, atol=1e-12)
+    np.testing.assert_allclose(w, 0, atol=1e-12)
+
+
+def test_box_sliding_decelerates_by_mu_g_dt_and_loads_its_front():
+    """Sliding along x (t1 of a floor contact): Coulomb friction takes mu g dt
+    off the speed; the friction's tipping moment about the centre is balanced
+    by the normal impulses, so the front pair carries hz mu m g dt / hx more
+    than the back pair, and the box does not turn."""
+    hx, hy, hz, mu, v0 = 1.0, 0.5, 0.25, 0.5, 3.0
+    v, w, lam, pts, gaps = X.box_plane_step([0, 0, hz], ID, [hx, hy, hz], 1 / M, FLOOR, [v0, 0, 0], [0, 0, 0],
+                                            mu=mu, iters=3000, dt=DT)
+    np.testing.assert_allclose(v, [v0 - mu * G9 * DT, 0, 0], atol=1e-10)
+    np.testing.assert_allclose(w, 0, atol=1e-10)
+    np.testing.assert_allclose(lam[:, 1].sum(), mu * lam[:, 0].sum(), rtol=1e-10)
+    front = lam[pts[:, 0] > 0, 0].sum()
+    back = lam[pts[:, 0] < 0, 0].sum()
+    np.testing.assert_allclose(front - back, hz * mu * M * G9 * DT / hx, rtol=1e-8)
+
+
+def test_box_push_out_of_a_penetration():
+    """Every contact 0.01 deep: with erp 0.2 and no slop the normal rows aim
+    at a separating speed of erp 0.01 / dt on top of cancelling gravity."""
+    v, w, lam, pts, gaps = X.box_plane_step([0, 0, 0.25 - 0.01], ID, [1.0, 0.5, 0.25], 1 / M, FLOOR,
+                                            [0, 0, 0], [0, 0, 0], erp=0.2, slop=0.0, iters=500, dt=DT)
+    np.testing.assert_allclose(gaps, -0.01, atol=1e-15)
+    np.testing.assert_allclose(v, [0, 0, 0.2 * 0.01 / DT], atol=1e-12)
+    np.testing.assert_allclose(w, 0, atol=1e-12)
