@@ -305,6 +305,23 @@ ovl_status ovl_box_box_contacts(int32_t n, const float *pose_a, const float *hal
                                 const float *half_b, float margin, int32_t on_gpu, int32_t *count,
                                 float *points, float *gaps, float *normal, int32_t *axis);
 
+/* Box rows (the solve of Eq 1-7 with a box's general lever arms and full
+ * world inverse inertia R diag(1/I) R^T, I_k = m/3 (h_j^2 + h_l^2)): one
+ * velocity step of each of n independent boxes on its own static plane.  v
+ * += dt gravity, then `iters` Gauss-Seidel sweeps over the rows (normal, t1,
+ * t2) of every ovl_box_plane_contacts contact in order: row d at lever r
+ * has w = -d.v - (r x d).omega and k = 1 / (1/m + (r x d).Iw (r x d)); the
+ * box takes -d (lambda' - lambda).  Normal bounds [0, inf), target -phi/dt
+ * when phi > 0 else erp max(-phi - slop, 0)/dt; tangents within +-mu
+ * lambda_n (current); t1 = normalise(e_k - n_k n) for the axis k of the
+ * smallest |n_k|, t2 = n x t1.  inv_mass[n]; vel[n][6] = (v, omega) in and
+ * out; count[n]; lam[n][12] = (n, t1, t2) impulses per contact (zero past
+ * count).  On the GPU one thread per box, else the same functions on the
+ * host; both give the same bits.  OVL_ERR_ARG / OVL_ERR_CUDA as above. */
+ovl_status ovl_box_plane_step(int32_t n, const float *pose, const float *half, const float *inv_mass,
+                              const float *plane, float mu, float dt, const float *gravity, float erp, float slop,
+                              float margin, int32_t iters, int32_t on_gpu, float *vel, int32_t *count, float *lam);
+
 /* LOADBALANCE (Algorithm 6 with BRIDGE, Algorithm 7) alone on the contacts
  * of the current state.  flags bit 0: activation branch, bit 1: removal
  * branches. */

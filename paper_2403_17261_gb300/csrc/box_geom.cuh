@@ -243,6 +243,99 @@ OVL_HD int box_box(const Obb &A, const Obb &B, float margin, float3 pts[4], floa
     return kept;
 }
 
+// ---- box rows ------------------------------------------------------------
+// world inverse inertia of a solid box (inverse mass im, half extents h):
+// R diag(1 / I_k) R^T, I_k = m/3 (h_j^2 + h_l^2); row-major 3 x 3
+OVL_HD void inv_inertia_world(const Obb &B, float im, float Iw[9]) {
+    float d[3];
+    for (int k = 0; k < 3; ++k) {
+        const float a = B.h[(k + 1) % 3], b = B.h[(k + 2) % 3];
+        d[k] = im > 0.f ? 3.f * im / (a * a + b * b) : 0.f;
+    }
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            Iw[3 * r + c] = comp(B.u[0], r) * d[0] * comp(B.u[0], c) + comp(B.u[1], r) * d[1] * comp(B.u[1], c) +
+                            comp(B.u[2], r) * d[2] * comp(B.u[2], c);
+}
+
+OVL_HD float3 mul(const float Iw[9], float3 v) {
+    return v3(Iw[0] * v.x + Iw[1] * v.y + Iw[2] * v.z, Iw[3] * v.x + Iw[4] * v.y + Iw[5] * v.z,
+              Iw[6] * v.x + Iw[7] * v.y + Iw[8] * v.z);
+}
+
+// One constraint row of the first body against a static second one: along
+// direction d at lever r, w = -d.v - (r x d).omega; the row keeps r x d,
+// Iw^-1 (r x d) and k = 1 / (1/m + (r x d).Iw^-1 (r x d)).
+struct Row1 {
+    float3 d, rxd, irxd;
+    float k, target;
+};
+
+OVL_HD Row1 make_row(float3 d, float3 r, float im, const float Iw[9], float target) {
+    Row1 row;
+    row.d = d;
+    row.rxd = crs(r, d);
+    row.irxd = mul(Iw, row.rxd);
+    row.k = 1.f / (im + dot(row.rxd, row.irxd));
+    row.target = target;
+    return row;
+}
+
+// projected Gauss-Seidel update of one row: the body takes -d (l' - l)
+OVL_HD void solve_row(const Row1 &row, float lo, float hi, float im, float3 &v, float3 &w, float &lam) {
+    const float wv = -dot(row.d, v) - dot(row.rxd, w);
+    const float ln = fminf(fmaxf(lam + row.k * (row.target - wv), lo), hi);
+    const float dl = ln - lam;
+    lam = ln;
+    v = sub(v, scl(row.d, im * dl));
+    w = sub(w, scl(row.irxd, dl));
+}
+
+// tangent t1 of a contact normal: normalise(e_k - n_k n) for the axis k of
+// the smallest |n_k| (ties to the lower index)
+OVL_HD float3 tangent1(float3 n) {
+    int k = 0;
+    float m = fabsf(n.x);
+    if (fabsf(n.y) < m) { m = fabsf(n.y); k = 1; }
+    if (fabsf(n.z) < m) k = 2;
+    const float nk = comp(n, k);
+    float3 t = scl(n, -nk);
+    if (k == 0) t.x += 1.f; else if (k == 1) t.y += 1.f; else t.z += 1.f;
+    return scl(t, 1.f / sqrtf(dot(t, t)));
+}
+
+// One velocity step of a single box (first) on a static plane (second):
+// gravity, then `iters` sweeps over (normal, t1, t2) of every box_plane
+// contact in order.  Normal bounds [0, inf) with target -phi/dt when phi > 0
+// else erp max(-phi - slop, 0)/dt; tangents within +-mu lambda_n.
+// lam[12]: (n, t1, t2) per contact.  Returns the contact count.
+OVL_HD int box_plane_step(const Obb &B, float im, float4 plane, float mu, float dt, float3 g, float erp,
+                          float slop, float margin, int iters, float3 &v, float3 &w, float lam[12]) {
+    float3 pts[4], n;
+    float gaps[4], Iw[9];
+    const int m = box_plane(B, plane, margin, pts, gaps, n);
+    inv_inertia_world(B, im, Iw);
+    v = add(v, scl(g, dt));
+    const float3 t1 = tangent1(n), t2 = crs(n, t1);
+    Row1 rows[12];
+    for (int c = 0; c < m; ++c) {
+        const float3 r = sub(pts[c], B.c);
+        const float tn = gaps[c] > 0.f ? -gaps[c] / dt : erp * fmaxf(-gaps[c] - slop, 0.f) / dt;
+        rows[3 * c] = make_row(n, r, im, Iw, tn);
+        rows[3 * c + 1] = make_row(t1, r, im, Iw, 0.f);
+        rows[3 * c + 2] = make_row(t2, r, im, Iw, 0.f);
+        lam[3 * c] = lam[3 * c + 1] = lam[3 * c + 2] = 0.f;
+    }
+    for (int it = 0; it < iters; ++it)
+        for (int c = 0; c < m; ++c) {
+            solve_row(rows[3 * c], 0.f, INFINITY, im, v, w, lam[3 * c]);
+            const float lim = mu * lam[3 * c];
+            solve_row(rows[3 * c + 1], -lim, lim, im, v, w, lam[3 * c + 1]);
+            solve_row(rows[3 * c + 2], -lim, lim, im, v, w, lam[3 * c + 2]);
+        }
+    return m;
+}
+
 #undef OVL_HD
 
 }  // namespace box

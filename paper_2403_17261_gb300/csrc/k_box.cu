@@ -90,6 +90,35 @@ __host__ __device__ void box_box_one(const BoxBoxArgs &a, int i) {
     a.o.axis[i] = axis;
 }
 
+struct BoxStepArgs {
+    int n;
+    const float *pose, *half, *inv_mass, *plane;
+    float mu, dt, gx, gy, gz, erp, slop, margin;
+    int iters;
+    float *vel;      // [n][6] v, omega (in/out)
+    int32_t *count;  // [n]
+    float *lam;      // [n][12]
+};
+
+__host__ __device__ void box_step_one(const BoxStepArgs &a, int i) {
+    const box::Obb B = obb_of(a.pose + 7 * (size_t)i, a.half + 3 * (size_t)i);
+    const float *pl = a.plane + 4 * (size_t)i;
+    float *vw = a.vel + 6 * (size_t)i;
+    float3 v = make_float3(vw[0], vw[1], vw[2]), w = make_float3(vw[3], vw[4], vw[5]);
+    float lam[12] = {0.f};
+    const int k = box::box_plane_step(B, a.inv_mass[i], make_float4(pl[0], pl[1], pl[2], pl[3]), a.mu, a.dt,
+                                      make_float3(a.gx, a.gy, a.gz), a.erp, a.slop, a.margin, a.iters, v, w, lam);
+    vw[0] = v.x; vw[1] = v.y; vw[2] = v.z;
+    vw[3] = w.x; vw[4] = w.y; vw[5] = w.z;
+    a.count[i] = k;
+    for (int j = 0; j < 12; ++j) a.lam[12 * (size_t)i + j] = j < 3 * k ? lam[j] : 0.f;
+}
+
+__global__ void k_box_plane_step(BoxStepArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) box_step_one(a, i);
+}
+
 __global__ void k_box_plane(BoxPlaneArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) box_plane_one(a, i);
@@ -237,6 +266,40 @@ extern "C" ovl_status ovl_box_box_contacts(int32_t n, const float *pose_a, const
         fetch(gaps, g.o.gaps, 4 * (size_t)n);
         fetch(normal, g.o.normal, 3 * (size_t)n);
         fetch(axis, g.o.axis, n);
+        return OVL_OK;
+    });
+}
+
+extern "C" ovl_status ovl_box_plane_step(int32_t n, const float *pose, const float *half, const float *inv_mass,
+                                         const float *plane, float mu, float dt, const float *gravity, float erp,
+                                         float slop, float margin, int32_t iters, int32_t on_gpu, float *vel,
+                                         int32_t *count, float *lam) {
+    if (n < 0 || iters < 0 || !gravity ||
+        (n > 0 && (!pose || !half || !inv_mass || !plane || !vel || !count || !lam)))
+        return OVL_ERR_ARG;
+    return guard([&]() -> ovl_status {
+        if (n == 0) return OVL_OK;
+        BoxStepArgs a{n, pose, half, inv_mass, plane, mu, dt, gravity[0], gravity[1], gravity[2], erp, slop, margin,
+                      iters, vel, count, lam};
+        if (!on_gpu) {
+            for (int i = 0; i < n; ++i) box_step_one(a, i);
+            return OVL_OK;
+        }
+        DevArena d;
+        BoxStepArgs g = a;
+        g.pose = d.in(pose, 7 * (size_t)n);
+        g.half = d.in(half, 3 * (size_t)n);
+        g.inv_mass = d.in(inv_mass, (size_t)n);
+        g.plane = d.in(plane, 4 * (size_t)n);
+        g.vel = d.in(vel, 6 * (size_t)n);
+        g.count = d.out<int32_t>(n);
+        g.lam = d.out<float>(12 * (size_t)n);
+        k_box_plane_step<<<(n + 127) / 128, 128>>>(g);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+        fetch(vel, g.vel, 6 * (size_t)n);
+        fetch(count, g.count, n);
+        fetch(lam, g.lam, 12 * (size_t)n);
         return OVL_OK;
     });
 }

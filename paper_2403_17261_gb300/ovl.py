@@ -52,7 +52,7 @@ EXPORTED = [
     "ovl_mlp_get_params", "ovl_mlp_forward", "ovl_log_reserve", "ovl_log_enable", "ovl_log_size",
     "ovl_log_append", "ovl_log_read", "ovl_mlp_train", "ovl_mlp_grad", "ovl_mlp_loss",
     "ovl_host_load_balance", "ovl_host_assign_overlap",
-    "ovl_box_plane_contacts", "ovl_sphere_box_contacts", "ovl_box_box_contacts",
+    "ovl_box_plane_contacts", "ovl_sphere_box_contacts", "ovl_box_box_contacts", "ovl_box_plane_step",
 ]
 
 
@@ -162,6 +162,8 @@ def load_library(path: str | None = None):
         "ovl_box_plane_contacts": [C.c_int32, _fp, _fp, _fp, C.c_float, C.c_int32, _ip, _fp, _fp, _fp],
         "ovl_sphere_box_contacts": [C.c_int32, _fp, _fp, _fp, C.c_float, C.c_int32, _ip, _fp, _fp, _fp],
         "ovl_box_box_contacts": [C.c_int32, _fp, _fp, _fp, _fp, C.c_float, C.c_int32, _ip, _fp, _fp, _fp, _ip],
+        "ovl_box_plane_step": [C.c_int32, _fp, _fp, _fp, _fp, C.c_float, C.c_float, _fp, C.c_float, C.c_float,
+                               C.c_float, C.c_int32, C.c_int32, _fp, _ip, _fp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -437,6 +439,24 @@ def ovl_box_box_contacts(pose_a, half_a, pose_b, half_b, margin: float, on_gpu: 
         n, _ptr(pa, _fp), _ptr(ha, _fp), _ptr(pb, _fp), _ptr(hb, _fp), float(margin), int(on_gpu),
         _ptr(cnt, _ip), _ptr(pts, _fp), _ptr(gaps, _fp), _ptr(nrm, _fp), _ptr(axis, _ip)))
     return cnt, pts, gaps, nrm, axis
+
+
+def ovl_box_plane_step(pose, half, inv_mass, plane, vel, mu=0.5, dt=1 / 60, gravity=(0.0, 0.0, -9.81), erp=0.2,
+                       slop=0.0, margin=0.02, iters=200, on_gpu: bool = True):
+    """One velocity step of independent boxes on their static planes (box
+    rows).  vel [n,6] = (v, omega).  Returns (vel' [n,6], count [n],
+    impulses [n,4,3] as (n, t1, t2) per contact)."""
+    pose, half, plane = _f32c(pose, 7), _f32c(half, 3), _f32c(plane, 4)
+    im = np.ascontiguousarray(inv_mass, dtype=np.float32).reshape(-1)
+    v = np.array(vel, dtype=np.float32, copy=True).reshape(-1, 6)
+    g = np.ascontiguousarray(gravity, dtype=np.float32).reshape(3)
+    n = pose.shape[0]
+    cnt, lam = np.zeros(n, np.int32), np.zeros((n, 4, 3), np.float32)
+    _check(None, load_library().ovl_box_plane_step(
+        n, _ptr(pose, _fp), _ptr(half, _fp), _ptr(im, _fp), _ptr(plane, _fp), float(mu), float(dt), _ptr(g, _fp),
+        float(erp), float(slop), float(margin), int(iters), int(on_gpu), _ptr(v, _fp), _ptr(cnt, _ip),
+        _ptr(lam, _fp)))
+    return v, cnt, lam
 
 
 def ovl_read_stats(ctx) -> dict:

@@ -68,3 +68,4 @@ def test_stacked_boxes_on_gpu():
     np.testing.assert_allclose(gaps[0], -0.01, atol=2e-6)
     np.testing.assert_allclose(nrm[0], [0, 0, 1], atol=1e-6)
     np.testing.assert_allclose(np.sort(pts[0, :, 0]), [-0.3, -0.3, 0.5, 0.5], atol=2e-6)
+
