@@ -255,6 +255,9 @@ class OracleSim:
     """FP64 simulation of a scene; ``step`` runs one timestep of Algorithm 1."""
 
     def __init__(self, scene, params: dict | None = None):
+        he = getattr(scene, "half_extents", None)
+        if he is not None and np.any(np.asarray(he) > 0):
+            raise ValueError("box bodies: the oracle step is sphere-only (box geometry and rows: oracle/box.py)")
         p = dict(DEFAULT_PARAMS)
         p["lb_activate"] = scene.lb_activate
         p["lb_deact_every"] = scene.lb_deact_every

@@ -221,6 +221,10 @@ class _SceneArrays:
     """Keeps the contiguous host arrays alive for the duration of the upload."""
 
     def __init__(self, scene):
+        he = getattr(scene, "half_extents", None)
+        if he is not None and np.any(np.asarray(he) > 0):
+            raise OvlError(OVL_ERR_ARG, "box bodies are not simulated by the step yet (only their contact "
+                                        "functions and rows exist)")
         f32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float32))
         i32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.int32))
         self.state = f32(scene.state).reshape(-1, 13)

@@ -92,6 +92,10 @@ class Scene:
     lb_deact_every: int = 1
     assign_overlap: bool = False  # run the articulated assignment at setup
     meta: dict = field(default_factory=dict)
+    # float32 [n,3] half extents, or None: every body a sphere.  A row of
+    # zeros is a sphere; a positive row is a box (radius = its bounding
+    # radius).  The step does not simulate boxes yet.
+    half_extents: np.ndarray | None = None
 
     @property
     def n_bodies(self) -> int:
@@ -513,6 +517,96 @@ def head_on(speed: float = 1.0, gap: float = 0.0, radius: float = 0.5, mass: flo
 
 MLP_LAYERS = (12, 64, 64, 3)
 MLP_N_PARAMS = 12 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
+
+
+def _box_body(c, h, density=1.0):
+    """state row, bounding radius and inverse mass of a resting solid box"""
+    h = np.asarray(h, np.float64)
+    return c, float(np.linalg.norm(h)), 1.0 / (8.0 * h[0] * h[1] * h[2] * density)
+
+
+def _box_scene(name, bodies, joints, anchors, planes, mu, dt, n_sets, gamma, beta, seed, iters):
+    """bodies: (centre, half extents (zeros = sphere of radius r), radius,
+    inverse mass, velocity)"""
+    pos = np.array([b[0] for b in bodies], np.float64)
+    st = _identity_state(pos)
+    st[:, 7:10] = np.array([b[4] for b in bodies], np.float32)
+    he = np.array([b[1] for b in bodies], np.float32)
+    sc = _single(name, pos, np.array([b[2] for b in bodies]), np.array([b[3] for b in bodies]), planes, mu=mu,
+                 dt=dt, flags=1, gamma=gamma, beta=beta, n_sets=n_sets,
+                 set_of_body=kmeans_sets(pos, n_sets, seed), joints=joints, anchors=anchors, iters=iters)
+    sc.state = st
+    sc.half_extents = he
+    return sc
+
+
+def box_building(seed: int = 7, storeys: int = 12, cells: int = 10, cell: float = 2.0, col_half: float = 0.15,
+                 storey_h: float = 1.6, slab_half: float = 0.1, balls: int = 2, n_sets: int = 16,
+                 mu: float = 0.6, dt: float = 1.0 / 60.0, iters: int = 30) -> Scene:
+    """Stand-in for the Building scene (Section 6: floors, walls and columns
+    brought down by two cannon balls, gamma = 0).  Storey s has a column at
+    every vertex of a cells x cells grid (pitch `cell`) and a slab over every
+    cell, resting on the column tops; the next storey's columns stand on
+    the slabs.  Everything touches (gap 0) on a ground plane z = 0.  Then
+    `balls` spheres of radius 0.8 fly at the building's side at 15 m/s.
+    Defaults: 12 storeys, 2652 boxes and 2 balls (the paper's scene has
+    2408 bodies)."""
+    hcol = storey_h - 2.0 * slab_half
+    bodies = []
+    for s in range(storeys):
+        base = s * storey_h
+        for i in range(cells + 1):
+            for j in range(cells + 1):
+                c, r, im = _box_body([i * cell, j * cell, base + hcol / 2], [col_half, col_half, hcol / 2])
+                bodies.append((c, [col_half, col_half, hcol / 2], r, im, [0, 0, 0]))
+        for i in range(cells):
+            for j in range(cells):
+                h = [cell / 2, cell / 2, slab_half]
+                c, r, im = _box_body([(i + 0.5) * cell, (j + 0.5) * cell, base + hcol + slab_half], h)
+                bodies.append((c, h, r, im, [0, 0, 0]))
+    rb = 0.8
+    for k in range(balls):
+        y = cells * cell * (k + 1) / (balls + 1)
+        bodies.append(([-6.0, y, 3.0 + 2.0 * k], [0, 0, 0], rb, 1.0 / (4.0 / 3.0 * np.pi * rb ** 3 * 8.0),
+                       [15.0, 0, 0]))
+    planes = np.array([[0.0, 0.0, 1.0, 0.0]])
+    return _box_scene("box_building", bodies, np.zeros((0, 2), np.int32), np.zeros((0, 6), np.float32), planes,
+                      mu, dt, n_sets, 0, 6, seed, iters)
+
+
+def plank_bridge(seed: int = 8, planks: int = 1589, half=(0.5, 1.0, 0.05), gap: float = 0.02, height: float = 4.0,
+                 balls: int = 2, n_sets: int = 8, gamma: int = 6, beta: int = 14, mu: float = 0.5,
+                 dt: float = 1.0 / 60.0, iters: int = 50) -> Scene:
+    """Stand-in for the Two-way bridge (Section 6: a long bridge of 3180
+    joint constraints, gamma = 6).  Planks of half extents `half` lie in a
+    row along x, `gap` apart; ball joints join neighbours at both y edges,
+    and the two end planks are jointed to the world the same way: 2 planks
+    + 2 joints (3180 at the default 1589 planks).  `balls` spheres of radius
+    0.6 fall onto the deck from 2 m above it."""
+    hx, hy, hz = half
+    pitch = 2 * hx + gap
+    bodies = []
+    for i in range(planks):
+        c, r, im = _box_body([i * pitch, 0.0, height], half)
+        bodies.append((c, list(half), r, im, [0, 0, 0]))
+    joints, anchors = [], []
+    e = hx + gap / 2
+    for sy in (-hy, hy):
+        joints.append((-1, 0))
+        anchors.append([-e, sy, height, -e, sy, 0.0])          # world pivot, plank 0's own
+        for i in range(planks - 1):
+            joints.append((i, i + 1))
+            anchors.append([e, sy, 0.0, -e, sy, 0.0])
+        joints.append((planks - 1, -1))
+        anchors.append([e, sy, 0.0, (planks - 1) * pitch + e, sy, height])
+    rb = 0.6
+    for k in range(balls):
+        x = (planks - 1) * pitch * (k + 1) / (balls + 1)
+        bodies.append(([x, 0.0, height + hz + 2.0], [0, 0, 0], rb, 1.0 / (4.0 / 3.0 * np.pi * rb ** 3 * 4.0),
+                       [0, 0, 0]))
+    planes = np.zeros((0, 4))
+    return _box_scene("plank_bridge", bodies, np.array(joints, np.int32), np.array(anchors, np.float32), planes,
+                      mu, dt, n_sets, gamma, beta, seed, iters)
 
 
 def bf16_grid(x) -> np.ndarray:
