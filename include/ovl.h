@@ -169,8 +169,15 @@ ovl_status ovl_default_params(ovl_params *p);
  * process has not yet created its CUDA context; otherwise, set the variable
  * before the first CUDA call. */
 ovl_status ovl_create(ovl_ctx **out, const ovl_params *p, void *cuda_stream);
+/* Frees the context's device and host memory, streams and events (after
+ * finishing its work); NULL is OVL_ERR_ARG. */
 ovl_status ovl_destroy(ovl_ctx *ctx);
+/* Message of the context's last failed call (empty when none; "null
+ * context" for NULL); the string belongs to the context and lives until
+ * its next failing call. */
 const char *ovl_last_error(const ovl_ctx *ctx);
+/* Name of entry `phase` of ovl_stats.phase_ms (a static string; empty out
+ * of range). */
 const char *ovl_phase_name(int32_t phase);
 
 /* Copies a scene to the device (Section 4: all bodies are loaded into every
