@@ -50,6 +50,8 @@ CONTACT_ROW_BYTES = 80   # per constraint per sweep: 56 B record (2 slots, n, t1
 JOINT_ROW_BYTES = 80     # per joint per sweep: 56 B record (2 slots, r_A, r_B, k[3], target[3]) + 24 B lambda r/w
 ENTRY_BYTES = 120        # per (body, worker) per step: 60 B state + params read, 52 B copy write, 8 B index
 PAIR_ONCE_BYTES = 24     # per constraint per step: warm-start lambda read + final lambda write
+BLEND_ENTRY_BYTES = 53   # per (body, worker) entry: its 52 B copy read + D(o,i) 1 B
+BLEND_BODY_BYTES = 64    # per body: 52 B blended state written + 12 B of the start position read
 # DRAM bytes of the solve over its algorithmic bytes, from the ncu capture
 # summarised in profiles/k_solve_pile_large.md (every solver launch of the two
 # timed steps: 0.294 GB of DRAM traffic for 7.52 GB of algorithmic bytes; the
@@ -110,6 +112,21 @@ def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
 def whole_job_rate(world: int, units_per_rank: int, steps: int, t_max: float) -> float:
     """Units processed by all ranks per second of the slowest rank (weak scaling)."""
     return world * units_per_rank * steps / t_max
+
+
+def blend_roofline(blend_ms, bytes_blend, steps, peak, peak_kind):
+    """HBM roofline of k_blend from the step's own phase timer (events around
+    the blend phase, launch included); None if the inputs are unusable."""
+    try:
+        t = sum(blend_ms) / 1e3
+        if t <= 0 or steps <= 0 or not peak:
+            return None
+        achieved = bytes_blend / t / 1e9
+        return {"bound": "hbm", "kernel": "k_blend", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_blend / steps,
+                "avg_launch_ms": 1e3 * t / steps, "timer": "phase events around the blend launch"}
+    except Exception:
+        return None
 
 
 class ClockSampler:
@@ -259,6 +276,7 @@ def gpu_arm(args, rank, world, local_rank):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     solve_ms, rows_iters, bytes_solve, launches, imbalance = [], 0, 0.0, [], []
+    blend_ms, bytes_blend = [], 0.0
     barrier()
     torch.cuda.nvtx.range_push("timed")
     with ClockSampler(local_rank) as clk:
@@ -278,6 +296,8 @@ def gpu_arm(args, rank, world, local_rank):
             rows_iters += st["n_rows"] * sc.iters
             bytes_solve += (sc.iters * CONTACT_ROW_BYTES * n_cons + PAIR_ONCE_BYTES * n_cons
                             + ENTRY_BYTES * st["n_entries"])
+            blend_ms.append(st["phase_ms"].get("blend", 0.0))
+            bytes_blend += BLEND_ENTRY_BYTES * st["n_entries"] + BLEND_BODY_BYTES * sc.n_bodies
         barrier()
     torch.cuda.nvtx.range_pop()
     free_b, total_b = torch.cuda.mem_get_info()
@@ -345,6 +365,7 @@ def gpu_arm(args, rank, world, local_rank):
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_solve / args.steps,
                      "avg_launch_ms": 1e3 * solve_s / args.steps},
+        "blend_roofline": blend_roofline(blend_ms, bytes_blend, args.steps, peak, peak_kind),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(sum(launches)),

@@ -27,3 +27,15 @@ def test_reference_arm_prints_the_contract_line():
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "pile_large"
+
+
+def test_blend_roofline_arithmetic():
+    sys.path.insert(0, ROOT)
+    import bench
+    # 2 steps of 37 MB in 0.02 ms each against a 6800 GB/s peak
+    r = bench.blend_roofline([0.02, 0.02], 2 * 37e6, 2, 6800.0, "measured")
+    assert abs(r["achieved"] - 37e6 / 0.02e-3 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 6800.0) < 1e-12
+    assert r["kernel"] == "k_blend" and r["unit"] == "GB/s" and abs(r["avg_launch_ms"] - 0.02) < 1e-12
+    assert bench.blend_roofline([], 0.0, 0, 6800.0, "measured") is None
+    assert bench.blend_roofline([0.0], 1.0, 1, None, "none") is None
