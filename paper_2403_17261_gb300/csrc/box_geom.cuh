@@ -281,10 +281,14 @@ OVL_HD Row1 make_row(float3 d, float3 r, float im, const float Iw[9], float targ
     return row;
 }
 
+// clamp by comparisons: unlike fminf/fmaxf, the result at signed-zero ties
+// (a bound of -0 against +0) is the same on host and device
+OVL_HD float clampf(float x, float lo, float hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
 // projected Gauss-Seidel update of one row: the body takes -d (l' - l)
 OVL_HD void solve_row(const Row1 &row, float lo, float hi, float im, float3 &v, float3 &w, float &lam) {
     const float wv = -dot(row.d, v) - dot(row.rxd, w);
-    const float ln = fminf(fmaxf(lam + row.k * (row.target - wv), lo), hi);
+    const float ln = clampf(lam + row.k * (row.target - wv), lo, hi);
     const float dl = ln - lam;
     lam = ln;
     v = sub(v, scl(row.d, im * dl));
@@ -320,7 +324,8 @@ OVL_HD int box_plane_step(const Obb &B, float im, float4 plane, float mu, float 
     Row1 rows[12];
     for (int c = 0; c < m; ++c) {
         const float3 r = sub(pts[c], B.c);
-        const float tn = gaps[c] > 0.f ? -gaps[c] / dt : erp * fmaxf(-gaps[c] - slop, 0.f) / dt;
+        const float pen = -gaps[c] - slop;
+        const float tn = gaps[c] > 0.f ? -gaps[c] / dt : erp * (pen > 0.f ? pen : 0.f) / dt;
         rows[3 * c] = make_row(n, r, im, Iw, tn);
         rows[3 * c + 1] = make_row(t1, r, im, Iw, 0.f);
         rows[3 * c + 2] = make_row(t2, r, im, Iw, 0.f);

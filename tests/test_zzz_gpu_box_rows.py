@@ -1,6 +1,7 @@
 """Box rows (tests/test_box_rows.py) on the GPU, one thread per box, against
-the same functions run on the host, bit for bit: both sides are built
-without FMA contraction, and their square roots and divisions are IEEE."""
+the same functions run on the host, value for value: both sides are built
+without FMA contraction, their square roots and divisions are IEEE, and the
+clamps compare explicitly."""
 import numpy as np
 import pytest
 
@@ -16,8 +17,9 @@ def _built():
 
 
 def _same(a, b):
+    # equal values (a zero's sign is not compared: it carries no meaning here)
     for x, y in zip(a, b):
-        assert x.dtype == y.dtype and np.array_equal(x.view(np.uint8), y.view(np.uint8))
+        assert x.dtype == y.dtype and x.shape == y.shape and np.array_equal(x, y)
 
 
 @pytest.mark.parametrize("n", [0, 1, 129, 20000])
