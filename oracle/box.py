@@ -51,6 +51,14 @@ def lib():
         L.box_plane_step.argtypes = [_dp, _dp, _dp, C.c_double, _dp, C.c_double, C.c_double, _dp, C.c_double,
                                      C.c_double, C.c_double, C.c_int, _dp, _dp, _dp]
         L.box_plane_step.restype = C.c_int
+        _fpp = C.POINTER(C.c_float)
+        L.box_plane_f32.argtypes = [_fpp, _fpp, _fpp, _fpp, C.c_float, _fpp, _fpp, _fpp]
+        L.box_plane_f32.restype = C.c_int
+        L.sphere_box_f32.argtypes = [_fpp, C.c_float, _fpp, _fpp, _fpp, C.c_float, _fpp, _fpp, _fpp]
+        L.sphere_box_f32.restype = C.c_int
+        L.box_box_f32.argtypes = [_fpp, _fpp, _fpp, _fpp, _fpp, _fpp, C.c_float, _fpp, _fpp, _fpp,
+                                  C.POINTER(C.c_int), _fpp]
+        L.box_box_f32.restype = C.c_int
         _lib = L
     return _lib
 
@@ -122,3 +130,40 @@ def box_plane_step(x, q, h, inv_mass, plane, v, w, mu=0.5, dt=1 / 60, g=(0.0, 0.
                              lam.ctypes.data_as(_dp))
     pts, gaps, _ = box_plane(x, q, h, plane, margin)
     return v2, w2, lam[: 3 * k].reshape(k, 3), pts, gaps
+
+
+# ---- FP32 decisions (the kernels' precision and operation order) ----------
+_fp32 = C.POINTER(C.c_float)
+
+
+def _w(x, n):
+    a = np.ascontiguousarray(x, dtype=np.float32).reshape(n)
+    return a, a.ctypes.data_as(_fp32)
+
+
+def box_plane_f32(c, q, h, plane, margin=0.0):
+    """box_plane in FP32 with the kernels' operation order."""
+    (c, pc), (q, pq), (h, ph), (pl, pp) = _w(c, 3), _w(q, 4), _w(h, 3), _w(plane, 4)
+    pts, gaps, nrm = np.zeros(12, np.float32), np.zeros(4, np.float32), np.zeros(3, np.float32)
+    k = lib().box_plane_f32(pc, pq, ph, pp, float(margin), pts.ctypes.data_as(_fp32), gaps.ctypes.data_as(_fp32),
+                            nrm.ctypes.data_as(_fp32))
+    return pts[: 3 * k].reshape(k, 3), gaps[:k], nrm
+
+
+def sphere_box_f32(s, r, c, q, h, margin=0.0):
+    """sphere_box in FP32 with the kernels' operation order."""
+    (s, ps), (c, pc), (q, pq), (h, ph) = _w(s, 3), _w(c, 3), _w(q, 4), _w(h, 3)
+    pt, nrm, gap = np.zeros(3, np.float32), np.zeros(3, np.float32), C.c_float()
+    hit = lib().sphere_box_f32(ps, float(r), pc, pq, ph, float(margin), pt.ctypes.data_as(_fp32),
+                               nrm.ctypes.data_as(_fp32), C.byref(gap))
+    return bool(hit), pt, nrm, np.float32(gap.value)
+
+
+def box_box_f32(cA, qA, hA, cB, qB, hB, margin=0.0):
+    """box_box in FP32 with the kernels' operation order."""
+    args = [_w(cA, 3), _w(qA, 4), _w(hA, 3), _w(cB, 3), _w(qB, 4), _w(hB, 3)]
+    pts, gaps, nrm = np.zeros(12, np.float32), np.zeros(4, np.float32), np.zeros(3, np.float32)
+    axis, sep = C.c_int(-1), C.c_float(np.nan)
+    k = lib().box_box_f32(*[p for _, p in args], float(margin), pts.ctypes.data_as(_fp32), gaps.ctypes.data_as(_fp32),
+                          nrm.ctypes.data_as(_fp32), C.byref(axis), C.byref(sep))
+    return pts[: 3 * k].reshape(k, 3), gaps[:k], nrm, axis.value, np.float32(sep.value)

@@ -419,3 +419,239 @@ int box_plane_step(const double x[3], const double q[4], const double h[3], doub
             }
     return m;
 }
+
+/* ---- FP32 decisions ------------------------------------------------------
+ * Which box contacts exist, which axis and which clipped points are kept are
+ * integer outcomes; like the sphere contact test, they are taken in the
+ * kernels' precision (FP32) with the kernels' operation order, written out
+ * here:
+ *   box axes  u_k = the columns of R(q), each entry formed as in quat_R in
+ *             float (1 - 2 (y y + z z), 2 (x y + w z), ...);
+ *   points    c + ((u0 a + u1 b) + u2 c);  dots ((a.x b.x + a.y b.y) + a.z b.z);
+ *   crosses   (a.y b.z - a.z b.y, ...);  normalise: x * (1 / sqrt(x.x));
+ *   axis sep  |T.L| - sum_k (hA_k |uA_k.L| + hB_k |uB_k.L|), k ascending;
+ *   clips     P_a + (P_b - P_a) * (d_a / (d_a - d_b)).
+ * The f32 functions return the same records as their FP64 counterparts. */
+typedef struct { float x, y, z; } f3;
+
+static f3 f3v(float x, float y, float z) { f3 r = {x, y, z}; return r; }
+static f3 f3add(f3 a, f3 b) { return f3v(a.x + b.x, a.y + b.y, a.z + b.z); }
+static f3 f3sub(f3 a, f3 b) { return f3v(a.x - b.x, a.y - b.y, a.z - b.z); }
+static f3 f3mul(f3 a, float s) { return f3v(a.x * s, a.y * s, a.z * s); }
+static float f3dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static f3 f3cross(f3 a, f3 b) { return f3v(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+static float f3at(f3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+typedef struct { f3 c, u[3]; float h[3]; } obb32;
+
+static obb32 obb32_make(const float c[3], const float q[4], const float h[3]) {
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    obb32 b;
+    b.c = f3v(c[0], c[1], c[2]);
+    b.u[0] = f3v(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
+    b.u[1] = f3v(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
+    b.u[2] = f3v(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
+    for (int k = 0; k < 3; ++k) b.h[k] = h[k];
+    return b;
+}
+
+static f3 obb32_point(const obb32 *B, float a, float b, float c) {
+    return f3add(B->c, f3add(f3add(f3mul(B->u[0], a), f3mul(B->u[1], b)), f3mul(B->u[2], c)));
+}
+
+/* the k deepest of m candidates by (gap, candidate order) */
+static int keep32(f3 *P, float *G, int m, int k) {
+    int order[16];
+    for (int i = 0; i < m; ++i) order[i] = i;
+    for (int i = 1; i < m; ++i) {
+        int o = order[i], j = i - 1;
+        while (j >= 0 && G[order[j]] > G[o]) { order[j + 1] = order[j]; --j; }
+        order[j + 1] = o;
+    }
+    const int n = m < k ? m : k;
+    f3 P2[16];
+    float G2[16];
+    for (int i = 0; i < n; ++i) { P2[i] = P[order[i]]; G2[i] = G[order[i]]; }
+    for (int i = 0; i < n; ++i) { P[i] = P2[i]; G[i] = G2[i]; }
+    return n;
+}
+
+int box_plane_f32(const float c[3], const float q[4], const float h[3], const float plane[4], float margin,
+                  float pts[12], float gaps[4], float normal[3]) {
+    const obb32 B = obb32_make(c, q, h);
+    const f3 n = f3v(plane[0], plane[1], plane[2]);
+    f3 P[8];
+    float G[8];
+    int m = 0;
+    for (int v = 0; v < 8; ++v) {
+        const f3 p = obb32_point(&B, (v & 1) ? h[0] : -h[0], (v & 2) ? h[1] : -h[1], (v & 4) ? h[2] : -h[2]);
+        const float g = f3dot(n, p) - plane[3];
+        if (g <= margin) { P[m] = p; G[m] = g; ++m; }
+    }
+    m = keep32(P, G, m, 4);
+    for (int i = 0; i < m; ++i) {
+        pts[3 * i] = P[i].x; pts[3 * i + 1] = P[i].y; pts[3 * i + 2] = P[i].z;
+        gaps[i] = G[i];
+    }
+    normal[0] = -n.x; normal[1] = -n.y; normal[2] = -n.z;
+    return m;
+}
+
+int sphere_box_f32(const float s[3], float r, const float c[3], const float q[4], const float h[3], float margin,
+                   float pt[3], float normal[3], float *gap) {
+    const obb32 B = obb32_make(c, q, h);
+    const f3 d = f3sub(f3v(s[0], s[1], s[2]), B.c);
+    float loc[3], cl[3];
+    int inside = 1;
+    for (int k = 0; k < 3; ++k) {
+        loc[k] = f3dot(d, B.u[k]);
+        const float lo = -h[k];
+        cl[k] = loc[k] < lo ? lo : loc[k];
+        cl[k] = cl[k] > h[k] ? h[k] : cl[k];
+        if (cl[k] != loc[k]) inside = 0;
+    }
+    f3 nb;
+    if (!inside) {
+        const float e0 = loc[0] - cl[0], e1 = loc[1] - cl[1], e2 = loc[2] - cl[2];
+        const float len = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
+        nb = f3add(f3add(f3mul(B.u[0], e0 / len), f3mul(B.u[1], e1 / len)), f3mul(B.u[2], e2 / len));
+        *gap = len - r;
+    } else {
+        int k = 0;
+        float pen = h[0] - fabsf(loc[0]);
+        for (int j = 1; j < 3; ++j) {
+            const float pj = h[j] - fabsf(loc[j]);
+            if (pj < pen) { pen = pj; k = j; }
+        }
+        const float sg = loc[k] >= 0.f ? 1.f : -1.f;
+        cl[k] = sg * h[k];
+        nb = f3mul(B.u[k], sg);
+        *gap = -pen - r;
+    }
+    const f3 p = obb32_point(&B, cl[0], cl[1], cl[2]);
+    pt[0] = p.x; pt[1] = p.y; pt[2] = p.z;
+    normal[0] = -nb.x; normal[1] = -nb.y; normal[2] = -nb.z;
+    return *gap <= margin;
+}
+
+static float sep32(const obb32 *A, const obb32 *B, f3 T, f3 L) {
+    float s = fabsf(f3dot(T, L));
+    for (int k = 0; k < 3; ++k) s -= A->h[k] * fabsf(f3dot(A->u[k], L)) + B->h[k] * fabsf(f3dot(B->u[k], L));
+    return s;
+}
+
+static float clamp32(float x, float lo, float hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+/* part of polygon P (n points) with dot(x, e) <= off */
+static int clip32(const f3 *P, int n, f3 e, float off, f3 *Q) {
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        const f3 a = P[i], b = P[i + 1 == n ? 0 : i + 1];
+        const float da = f3dot(a, e) - off, db = f3dot(b, e) - off;
+        if (da <= 0.f) Q[m++] = a;
+        if ((da <= 0.f) != (db <= 0.f)) Q[m++] = f3add(a, f3mul(f3sub(b, a), da / (da - db)));
+    }
+    return m;
+}
+
+int box_box_f32(const float cA[3], const float qA[4], const float hA[3], const float cB[3], const float qB[4],
+                const float hB[3], float margin, float pts[12], float gaps[4], float normal[3], int *axis,
+                float *sep) {
+    const obb32 A = obb32_make(cA, qA, hA), B = obb32_make(cB, qB, hB);
+    *axis = -1;
+    const f3 T = f3sub(B.c, A.c);
+    f3 L[15];
+    float s[15];
+    int ok[15];
+    for (int k = 0; k < 3; ++k) {
+        L[k] = A.u[k];
+        L[3 + k] = B.u[k];
+        ok[k] = ok[3 + k] = 1;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const int k = 6 + 3 * i + j;
+            const f3 x = f3cross(A.u[i], B.u[j]);
+            const float len = sqrtf(f3dot(x, x));
+            ok[k] = len > 1e-6f;
+            L[k] = ok[k] ? f3mul(x, 1.f / len) : f3v(0.f, 0.f, 0.f);
+        }
+    for (int k = 0; k < 15; ++k) {
+        s[k] = ok[k] ? sep32(&A, &B, T, L[k]) : -INFINITY;
+        if (s[k] > margin) return 0;
+    }
+    int face = 0, edge = -1;
+    for (int k = 1; k < 6; ++k)
+        if (s[k] > s[face]) face = k;
+    for (int k = 6; k < 15; ++k)
+        if (ok[k] && (edge < 0 || s[k] > s[edge])) edge = k;
+    float hmin = A.h[0];
+    for (int k = 0; k < 3; ++k) {
+        if (A.h[k] < hmin) hmin = A.h[k];
+        if (B.h[k] < hmin) hmin = B.h[k];
+    }
+    const int best = (edge >= 0 && s[edge] > 0.95f * s[face] + 0.01f * hmin) ? edge : face;
+    *axis = best;
+    *sep = s[best];
+    const f3 n = f3dot(T, L[best]) < 0.f ? f3mul(L[best], -1.f) : L[best];
+    normal[0] = n.x; normal[1] = n.y; normal[2] = n.z;
+
+    if (best >= 6) {
+        const int i = (best - 6) / 3, j = (best - 6) % 3;
+        f3 pa = A.c, pb = B.c;
+        for (int k = 0; k < 3; ++k) {
+            if (k != i) pa = f3add(pa, f3mul(A.u[k], f3dot(A.u[k], n) >= 0.f ? A.h[k] : -A.h[k]));
+            if (k != j) pb = f3add(pb, f3mul(B.u[k], f3dot(B.u[k], n) <= 0.f ? B.h[k] : -B.h[k]));
+        }
+        const f3 w = f3sub(pa, pb);
+        const float c = f3dot(A.u[i], B.u[j]), e = f3dot(A.u[i], w), f = f3dot(B.u[j], w);
+        const float den = 1.f - c * c;
+        float t = den > 1e-10f ? (c * f - e) / den : 0.f;
+        t = clamp32(t, -A.h[i], A.h[i]);
+        const float v = clamp32(c * t + f, -B.h[j], B.h[j]);
+        t = clamp32(c * v - e, -A.h[i], A.h[i]);
+        const f3 p = f3mul(f3add(f3add(pa, f3mul(A.u[i], t)), f3add(pb, f3mul(B.u[j], v))), 0.5f);
+        pts[0] = p.x; pts[1] = p.y; pts[2] = p.z;
+        gaps[0] = *sep;
+        return 1;
+    }
+
+    const int refA = best < 3;
+    const obb32 *R = refA ? &A : &B, *I = refA ? &B : &A;
+    const int f = best % 3;
+    const f3 nr = refA ? n : f3mul(n, -1.f);
+    int fi = 0;
+    float most = -1.f;
+    for (int k = 0; k < 3; ++k) {
+        const float d = fabsf(f3dot(I->u[k], nr));
+        if (d > most) { most = d; fi = k; }
+    }
+    const float si = f3dot(I->u[fi], nr) > 0.f ? -1.f : 1.f;
+    const int a1 = fi == 0 ? 1 : 0, a2 = fi == 2 ? 1 : 2;
+    f3 poly[16], tmp[16];
+    const f3 fc = f3add(I->c, f3mul(I->u[fi], si * I->h[fi]));
+    const float su[4] = {-1.f, 1.f, 1.f, -1.f}, sv[4] = {-1.f, -1.f, 1.f, 1.f};
+    for (int k = 0; k < 4; ++k)
+        poly[k] = f3add(fc, f3add(f3mul(I->u[a1], su[k] * I->h[a1]), f3mul(I->u[a2], sv[k] * I->h[a2])));
+    int m = 4;
+    const int side[2] = {f == 0 ? 1 : 0, f == 2 ? 1 : 2};
+    for (int t = 0; t < 2 && m > 0; ++t) {
+        const f3 e = R->u[side[t]];
+        m = clip32(poly, m, e, f3dot(R->c, e) + R->h[side[t]], tmp);
+        if (m > 0) m = clip32(tmp, m, f3mul(e, -1.f), -f3dot(R->c, e) + R->h[side[t]], poly);
+    }
+    const f3 rc = f3add(R->c, f3mul(nr, R->h[f]));
+    f3 P[16];
+    float G[16];
+    int kept = 0;
+    for (int k = 0; k < m; ++k) {
+        const float g = f3dot(f3sub(poly[k], rc), nr);
+        if (g <= margin) { P[kept] = poly[k]; G[kept] = g; ++kept; }
+    }
+    kept = keep32(P, G, kept, 4);
+    for (int k = 0; k < kept; ++k) {
+        pts[3 * k] = P[k].x; pts[3 * k + 1] = P[k].y; pts[3 * k + 2] = P[k].z;
+        gaps[k] = G[k];
+    }
+    return kept;
+}
