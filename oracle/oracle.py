@@ -19,6 +19,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "ovl_oracle.c")
+BOX_SRC = os.path.join(HERE, "box_oracle.c")   # box contact decisions the step takes in FP32
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libovl_oracle.so")
 
@@ -37,10 +38,11 @@ class OrcParams(C.Structure):
 
 def build(force: bool = False) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
-    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < os.path.getmtime(SRC):
+    if (force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < os.path.getmtime(SRC)
+            or os.path.getmtime(LIB_PATH) < os.path.getmtime(BOX_SRC)):
         tmp = LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-shared", "-fPIC",
-                               "-o", tmp, SRC, "-lm"])
+                               "-o", tmp, SRC, BOX_SRC, "-lm"])
         os.replace(tmp, LIB_PATH)
     return LIB_PATH
 
@@ -62,6 +64,8 @@ def lib():
         L.orc_set_partition.argtypes = [C.c_void_p, ip]
         L.orc_set_partition.restype = C.c_int
         L.orc_set_masks.argtypes = [C.c_void_p, u64p]
+        L.orc_set_shapes.argtypes = [C.c_void_p, dp]
+        L.orc_set_shapes.restype = C.c_int
         L.orc_set_masks.restype = C.c_int
         L.orc_get_masks.argtypes = [C.c_void_p, u64p]
         L.orc_set_state.argtypes = [C.c_void_p, dp]
@@ -255,9 +259,6 @@ class OracleSim:
     """FP64 simulation of a scene; ``step`` runs one timestep of Algorithm 1."""
 
     def __init__(self, scene, params: dict | None = None):
-        he = getattr(scene, "half_extents", None)
-        if he is not None and np.any(np.asarray(he) > 0):
-            raise ValueError("box bodies: the oracle step is sphere-only (box geometry and rows: oracle/box.py)")
         p = dict(DEFAULT_PARAMS)
         p["lb_activate"] = scene.lb_activate
         p["lb_deact_every"] = scene.lb_deact_every
@@ -288,6 +289,11 @@ class OracleSim:
                                scene.joints.shape[0], _ptr(k[5], ip), _ptr(k[6], dp),
                                scene.n_scenes, _ptr(k[7], ip), _ptr(k[8], dp), _ptr(k[9], dp),
                                _ptr(k[10], ip), _ptr(k[11], ip), _ptr(k[12], ip), _ptr(k[13], ip))
+        he = getattr(scene, "half_extents", None)
+        if he is not None and np.any(np.asarray(he) > 0):
+            self._half = _f64(np.asarray(he).reshape(self.n, 3))
+            if L.orc_set_shapes(self._h, _ptr(self._half, dp)) != 0:
+                raise ValueError("negative half extent")
         rc = L.orc_set_partition(self._h, _ptr(_i32(scene.set_of_body), ip))
         if rc != 0:
             raise ValueError(f"invalid partition ({rc})")

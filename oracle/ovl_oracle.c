@@ -173,6 +173,9 @@ typedef struct {
     double phi;      /* signed gap */
     double n[3];     /* unit normal from a towards b */
     double t1[3];    /* first tangent; t2 = n x t1 */
+    int k;           /* point of a box manifold (0 for spheres) */
+    int at_point;    /* box contact: both lever arms reach the point p */
+    double p[3];
 } orc_contact;
 
 typedef struct { int64_t cx, cy, cz; int scene; int body; } cell_entry;
@@ -189,7 +192,8 @@ static int cmp_cell(const void *pa, const void *pb) {
 static int cmp_contact_key(const void *pa, const void *pb) {
     const orc_contact *a = pa, *b = pb;
     if (a->a != b->a) return a->a < b->a ? -1 : 1;
-    return a->b < b->b ? -1 : (a->b > b->b);
+    if (a->b != b->b) return a->b < b->b ? -1 : 1;
+    return a->k < b->k ? -1 : (a->k > b->k);
 }
 
 /* FP32 contact decision for two spheres (integer outcome, evaluated in the
@@ -237,7 +241,7 @@ static void tangent_from_axis(const double n[3], int k, double t1[3]) {
 
 static void fill_sphere_contact(orc_contact *c, int a, int b, const double *ca, const double *cb,
                                 double ra, double rb) {
-    c->a = a; c->b = b;
+    c->a = a; c->b = b; c->k = 0; c->at_point = 0;
     double d[3] = {cb[0] - ca[0], cb[1] - ca[1], cb[2] - ca[2]};
     double L = sqrt(dot3(d, d));
     c->phi = L - ra - rb;
@@ -260,7 +264,7 @@ static void fill_sphere_contact(orc_contact *c, int a, int b, const double *ca, 
 
 static void fill_plane_contact(orc_contact *c, int a, int b, const double *ca, double ra,
                                const double *pl) {
-    c->a = a; c->b = b;
+    c->a = a; c->b = b; c->k = 0; c->at_point = 0;
     c->phi = dot3(pl, ca) - pl[3] - ra;
     /* normal from the sphere (a) towards the plane (b): minus the plane normal */
     c->n[0] = -pl[0]; c->n[1] = -pl[1]; c->n[2] = -pl[2];
@@ -279,7 +283,83 @@ typedef struct {
     const int *scene_of_body;
     const int *scene_flags;
     double margin;
+    const double *half;    /* n x 3 half extents (zeros: a sphere), or NULL: all spheres */
 } contact_input;
+
+/* box contact decisions in FP32 (box_oracle.c, the kernels' operation order) */
+int box_plane_f32(const float c[3], const float q[4], const float h[3], const float plane[4], float margin,
+                  float pts[12], float gaps[4], float normal[3]);
+int sphere_box_f32(const float s[3], float r, const float c[3], const float q[4], const float h[3], float margin,
+                   float pt[3], float normal[3], float *gap);
+int box_box_f32(const float cA[3], const float qA[4], const float hA[3], const float cB[3], const float qB[4],
+                const float hB[3], float margin, float pts[12], float gaps[4], float normal[3], int *axis,
+                float *sep);
+
+static int is_box(const contact_input *in, int b) {
+    return in->half && (in->half[3 * (size_t)b] > 0 || in->half[3 * (size_t)b + 1] > 0 ||
+                        in->half[3 * (size_t)b + 2] > 0);
+}
+
+/* one point of a box contact: FP32 geometry as decided, FP64 record */
+static void fill_box_point(orc_contact *c, int a, int b, int k, const float p[3], float gap, const float nf[3],
+                           double sgn) {
+    c->a = a; c->b = b; c->k = k; c->at_point = 1;
+    c->phi = (double)gap;
+    for (int j = 0; j < 3; ++j) { c->p[j] = (double)p[j]; c->n[j] = sgn * (double)nf[j]; }
+    const float fx = (float)(sgn * nf[0]), fy = (float)(sgn * nf[1]), fz = (float)(sgn * nf[2]);
+    tangent_from_axis(c->n, tangent_axis_f32(fx, fy, fz), c->t1);
+}
+
+static void box_f32_pose(const double *st, float c[3], float q[4]) {
+    for (int j = 0; j < 3; ++j) c[j] = (float)st[j];
+    for (int j = 0; j < 4; ++j) q[j] = (float)st[3 + j];
+}
+
+typedef struct { orc_contact *list; size_t cnt, cap; } contact_buf;
+
+static orc_contact *cb_next(contact_buf *B) {
+    if (B->cnt == B->cap) { B->cap *= 2; B->list = realloc(B->list, B->cap * sizeof(orc_contact)); }
+    return &B->list[B->cnt++];
+}
+
+/* the contacts of a body pair with at least one box: the bounding spheres
+ * must meet (the same FP32 test as for spheres), then the box functions
+ * decide in FP32; the normal runs from a towards b */
+static void box_pair_contacts(const contact_input *in, int a, int b, contact_buf *B) {
+    const double *ca = in->state + 13 * (size_t)a, *cb = in->state + 13 * (size_t)b;
+    if (!sphere_pair_touches_f32(ca, cb, in->radius[a], in->radius[b], in->margin)) return;
+    float pa[3], qa[4], pb[3], qb[4], ha[3], hb[3], pts[12], gaps[4], nf[3];
+    box_f32_pose(ca, pa, qa);
+    box_f32_pose(cb, pb, qb);
+    for (int j = 0; j < 3; ++j) { ha[j] = (float)in->half[3 * (size_t)a + j]; hb[j] = (float)in->half[3 * (size_t)b + j]; }
+    const float m = (float)in->margin;
+    if (is_box(in, a) && is_box(in, b)) {
+        int axis;
+        float sep;
+        const int k = box_box_f32(pa, qa, ha, pb, qb, hb, m, pts, gaps, nf, &axis, &sep);
+        for (int i = 0; i < k; ++i) fill_box_point(cb_next(B), a, b, i, pts + 3 * i, gaps[i], nf, 1.0);
+    } else {
+        /* one sphere, one box: sphere_box's normal runs from the sphere to the box */
+        const int sph = is_box(in, a) ? b : a, bx = sph == a ? b : a;
+        float sc[3], sq[4], bc[3], bq[4], bh[3], gap;
+        box_f32_pose(sph == a ? ca : cb, sc, sq);
+        box_f32_pose(bx == a ? ca : cb, bc, bq);
+        for (int j = 0; j < 3; ++j) bh[j] = bx == a ? ha[j] : hb[j];
+        if (sphere_box_f32(sc, (float)in->radius[sph], bc, bq, bh, m, pts, nf, &gap))
+            fill_box_point(cb_next(B), a, b, 0, pts, gap, nf, sph == a ? 1.0 : -1.0);
+    }
+}
+
+static void box_plane_contacts(const contact_input *in, int a, int p, contact_buf *B) {
+    const double *ca = in->state + 13 * (size_t)a, *pl = in->planes + 4 * (size_t)p;
+    if (!sphere_plane_touches_f32(ca, in->radius[a], pl, in->margin)) return;
+    float c[3], q[4], h[3], plf[4], pts[12], gaps[4], nf[3];
+    box_f32_pose(ca, c, q);
+    for (int j = 0; j < 3; ++j) h[j] = (float)in->half[3 * (size_t)a + j];
+    for (int j = 0; j < 4; ++j) plf[j] = (float)pl[j];
+    const int k = box_plane_f32(c, q, h, plf, (float)in->margin, pts, gaps, nf);
+    for (int i = 0; i < k; ++i) fill_box_point(cb_next(B), a, in->n + p, i, pts + 3 * i, gaps[i], nf, 1.0);
+}
 
 /* All contacts of the current state in canonical order (ascending (a, b)).
  * Sphere pairs are found through a uniform grid whose cells are at least as
@@ -335,7 +415,11 @@ static int64_t contacts_impl(const contact_input *in, int use_grid, orc_contact 
                             if (b <= a) continue;
                             if (in->inv_mass[a] == 0 && in->inv_mass[b] == 0) continue;
                             const double *cb = in->state + 13 * (size_t)b;
-                            if (sphere_pair_touches_f32(ca, cb, in->radius[a], in->radius[b], in->margin))
+                            if (is_box(in, a) || is_box(in, b)) {
+                                contact_buf B = {list, cnt, cap};
+                                box_pair_contacts(in, a, b, &B);
+                                list = B.list; cnt = B.cnt; cap = B.cap;
+                            } else if (sphere_pair_touches_f32(ca, cb, in->radius[a], in->radius[b], in->margin))
                                 PUSH_CONTACT(fill_sphere_contact(&list[cnt], a, b, ca, cb, in->radius[a], in->radius[b]));
                         }
                     }
@@ -350,7 +434,11 @@ static int64_t contacts_impl(const contact_input *in, int use_grid, orc_contact 
                 if (in->scene_of_body[b] != s) continue;
                 if (in->inv_mass[a] == 0 && in->inv_mass[b] == 0) continue;
                 const double *cb = in->state + 13 * (size_t)b;
-                if (sphere_pair_touches_f32(ca, cb, in->radius[a], in->radius[b], in->margin))
+                if (is_box(in, a) || is_box(in, b)) {
+                    contact_buf B = {list, cnt, cap};
+                    box_pair_contacts(in, a, b, &B);
+                    list = B.list; cnt = B.cnt; cap = B.cap;
+                } else if (sphere_pair_touches_f32(ca, cb, in->radius[a], in->radius[b], in->margin))
                     PUSH_CONTACT(fill_sphere_contact(&list[cnt], a, b, ca, cb, in->radius[a], in->radius[b]));
             }
         }
@@ -361,7 +449,11 @@ static int64_t contacts_impl(const contact_input *in, int use_grid, orc_contact 
         for (int p = 0; p < in->n_planes; ++p) {
             if (in->plane_scene[p] != in->scene_of_body[a]) continue;
             const double *pl = in->planes + 4 * (size_t)p;
-            if (sphere_plane_touches_f32(ca, in->radius[a], pl, in->margin))
+            if (is_box(in, a)) {
+                contact_buf B = {list, cnt, cap};
+                box_plane_contacts(in, a, p, &B);
+                list = B.list; cnt = B.cnt; cap = B.cap;
+            } else if (sphere_plane_touches_f32(ca, in->radius[a], pl, in->margin))
                 PUSH_CONTACT(fill_plane_contact(&list[cnt], a, n + p, ca, in->radius[a], pl));
         }
     }
@@ -842,6 +934,7 @@ typedef struct {
     int *part_iters; double *part_res_sq; int64_t *part_rows; int *part_colours;
     double res_sq_total; double res_max; int64_t res_rows;
     double joint_violation_max, joint_violation_sum;
+    double *half;       /* n x 3 half extents (zeros: a sphere); NULL until orc_set_shapes */
 } orc_sim;
 
 /* Position-level joint violation of the current state (Section 6's error
@@ -897,6 +990,23 @@ orc_sim *orc_create(const orc_params *P, int n, const double *state13, const dou
     return s;
 }
 
+/* Box bodies (row f1): half extents per body, zeros for a sphere.  Inverse
+ * masses stay as given; a box's world inverse inertia R diag(1/I) R^T, I_k =
+ * m/3 (h_j^2 + h_l^2), is formed from its orientation at every step.
+ * Returns 0, or -1 for a negative extent. */
+int orc_set_shapes(orc_sim *s, const double *half) {
+    for (int i = 0; i < 3 * s->n; ++i)
+        if (half[i] < 0) return -1;
+    free(s->half);
+    s->half = xcalloc((size_t)s->n * 3 + 1, sizeof(double));
+    memcpy(s->half, half, (size_t)s->n * 3 * sizeof(double));
+    return 0;
+}
+
+static int body_is_box(const orc_sim *s, int b) {
+    return s->half && (s->half[3 * (size_t)b] > 0 || s->half[3 * (size_t)b + 1] > 0 || s->half[3 * (size_t)b + 2] > 0);
+}
+
 static void free_step_records(orc_sim *s) {
     free(s->con); s->con = NULL;
     free(s->row_ptr); free(s->col); s->row_ptr = s->col = NULL;
@@ -918,6 +1028,7 @@ void orc_destroy(orc_sim *s) {
     free(s->st); free(s->rad); free(s->im); free(s->iI); free(s->planes); free(s->plane_scene);
     free(s->jab); free(s->janc); free(s->sob); free(s->mu); free(s->dt); free(s->sflags);
     free(s->sgamma); free(s->sbeta); free(s->nsets); free(s->part_base); free(s->mask); free(s->ws);
+    free(s->half);
     free(s);
 }
 
@@ -998,6 +1109,8 @@ typedef struct {
     int friction_of;     /* row index of the normal row for friction rows, else -1 */
     double mu;
     int bilateral;       /* joint rows: bounds +-inf */
+    int full;            /* a box end: angular response through its 3 x 3 inverse inertia */
+    double IA[3], IB[3]; /* with full: Iw_A JA_ang, Iw_B JB_ang */
 } pgs_row;
 
 static void row_bounds(const pgs_row *r, const double *lam, double *lo, double *hi) {
@@ -1021,6 +1134,19 @@ static double row_velocity(const pgs_row *r, const double *vel) {
 }
 
 static void apply_impulse(const pgs_row *r, double *vel, const double *minv, double dl) {
+    if (r->full) {
+        if (r->la >= 0)
+            for (int a = 0; a < 3; ++a) {
+                vel[6 * r->la + a] += minv[6 * r->la + a] * r->JA[a] * dl;
+                vel[6 * r->la + 3 + a] += r->IA[a] * dl;
+            }
+        if (r->lb >= 0)
+            for (int a = 0; a < 3; ++a) {
+                vel[6 * r->lb + a] += minv[6 * r->lb + a] * r->JB[a] * dl;
+                vel[6 * r->lb + 3 + a] += r->IB[a] * dl;
+            }
+        return;
+    }
     if (r->la >= 0) for (int a = 0; a < 6; ++a) vel[6 * r->la + a] += minv[6 * r->la + a] * r->JA[a] * dl;
     if (r->lb >= 0) for (int a = 0; a < 6; ++a) vel[6 * r->lb + a] += minv[6 * r->lb + a] * r->JB[a] * dl;
 }
@@ -1050,6 +1176,48 @@ static void make_row(pgs_row *row, int la, int lb, const double d[3], const doub
     if (lb >= 0) for (int a = 0; a < 6; ++a) s += row->JB[a] * minv[6 * lb + a] * row->JB[a];
     row->k = 1.0 / s;
     row->friction_of = -1; row->bilateral = 0; row->mu = 0; row->target = 0;
+    row->full = 0;
+}
+
+/* make_row with a box at either end: that end's angular response is its
+ * world inverse inertia (Iw, row-major; NULL for a sphere, which keeps the
+ * isotropic minv entries) applied to the angular Jacobian block */
+static void make_row_full(pgs_row *row, int la, int lb, const double d[3], const double rA[3], const double rB[3],
+                          const double *minv, const double *IwA, const double *IwB) {
+    make_row(row, la, lb, d, rA, rB, minv);
+    row->full = 1;
+    double s = 0;
+    for (int a = 0; a < 3; ++a) { row->IA[a] = 0; row->IB[a] = 0; }
+    if (la >= 0) {
+        for (int a = 0; a < 3; ++a) {
+            s += row->JA[a] * minv[6 * la + a] * row->JA[a];
+            row->IA[a] = IwA ? IwA[3 * a] * row->JA[3] + IwA[3 * a + 1] * row->JA[4] + IwA[3 * a + 2] * row->JA[5]
+                             : minv[6 * la + 3 + a] * row->JA[3 + a];
+        }
+        for (int a = 0; a < 3; ++a) s += row->JA[3 + a] * row->IA[a];
+    }
+    if (lb >= 0) {
+        for (int a = 0; a < 3; ++a) {
+            s += row->JB[a] * minv[6 * lb + a] * row->JB[a];
+            row->IB[a] = IwB ? IwB[3 * a] * row->JB[3] + IwB[3 * a + 1] * row->JB[4] + IwB[3 * a + 2] * row->JB[5]
+                             : minv[6 * lb + 3 + a] * row->JB[3 + a];
+        }
+        for (int a = 0; a < 3; ++a) s += row->JB[3 + a] * row->IB[a];
+    }
+    row->k = 1.0 / s;
+}
+
+/* world inverse inertia of a solid box: R diag(1/I) R^T */
+static void box_world_inv_inertia(const double q[4], const double h[3], double im, double Iw[9]) {
+    double R[9], dI[3];
+    quat_to_matrix(q, R);
+    for (int k = 0; k < 3; ++k) {
+        const double a = h[(k + 1) % 3], b = h[(k + 2) % 3];
+        dI[k] = im > 0 ? 3.0 * im / (a * a + b * b) : 0.0;
+    }
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            Iw[3 * r + c] = R[3 * r] * dI[0] * R[3 * c] + R[3 * r + 1] * dI[1] * R[3 * c + 1] + R[3 * r + 2] * dI[2] * R[3 * c + 2];
 }
 
 typedef struct {
@@ -1081,6 +1249,16 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
             minv[6 * i + 3 + a] = s->iI[b];
         }
     }
+    /* box bodies: world inverse inertia from the blended orientation */
+    double *iw = NULL;
+    if (s->half) {
+        iw = xcalloc((size_t)nb * 9 + 1, sizeof(double));
+        for (int i = 0; i < nb; ++i)
+            if (body_is_box(s, bodies[i]))
+                box_world_inv_inertia(s->st + 13 * (size_t)bodies[i] + 3, s->half + 3 * (size_t)bodies[i],
+                                      s->im[bodies[i]], iw + 9 * (size_t)i);
+    }
+#define IW_OF(l, body) ((l) >= 0 && iw && body_is_box(s, (body)) ? iw + 9 * (size_t)(l) : NULL)
     int64_t np_ = p1 - p0;
     pgs_row *rows = xcalloc((size_t)np_ * 3 + 1, sizeof(pgs_row));
     double *lam = xcalloc((size_t)np_ * 3 + 1, sizeof(double));
@@ -1101,9 +1279,23 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
             if (b < s->n) { double rb = s->rad[b]; for (int k = 0; k < 3; ++k) rB[k] = -rb * c->n[k]; }
             double t2[3];
             cross3(c->n, c->t1, t2);
-            make_row(&r3[0], la, lb, c->n, rA, rB, minv);
-            make_row(&r3[1], la, lb, c->t1, rA, rB, minv);
-            make_row(&r3[2], la, lb, t2, rA, rB, minv);
+            if (c->at_point) {
+                /* box contact: both lever arms reach the contact point */
+                const double *xa = s->st + 13 * (size_t)a;
+                for (int k = 0; k < 3; ++k) rA[k] = c->p[k] - xa[k];
+                if (b < s->n) {
+                    const double *xb = s->st + 13 * (size_t)b;
+                    for (int k = 0; k < 3; ++k) rB[k] = c->p[k] - xb[k];
+                }
+                const double *IwA = IW_OF(la, a), *IwB = b < s->n ? IW_OF(lb, b) : NULL;
+                make_row_full(&r3[0], la, lb, c->n, rA, rB, minv, IwA, IwB);
+                make_row_full(&r3[1], la, lb, c->t1, rA, rB, minv, IwA, IwB);
+                make_row_full(&r3[2], la, lb, t2, rA, rB, minv, IwA, IwB);
+            } else {
+                make_row(&r3[0], la, lb, c->n, rA, rB, minv);
+                make_row(&r3[1], la, lb, c->t1, rA, rB, minv);
+                make_row(&r3[2], la, lb, t2, rA, rB, minv);
+            }
             r3[0].target = c->phi > 0 ? -c->phi / h : P->erp * fmax(-c->phi - P->slop, 0.0) / h;
             r3[1].friction_of = (int)(3 * q); r3[1].mu = mu;
             r3[2].friction_of = (int)(3 * q); r3[2].mu = mu;
@@ -1134,10 +1326,12 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
             } else {
                 for (int k = 0; k < 3; ++k) pB[k] = anc[3 + k];
             }
+            const double *IwA = a >= 0 ? IW_OF(la, a) : NULL, *IwB = b >= 0 ? IW_OF(lb, b) : NULL;
             for (int ax = 0; ax < 3; ++ax) {
                 double e[3] = {0, 0, 0};
                 e[ax] = 1.0;
-                make_row(&r3[ax], la, lb, e, rA, rB, minv);
+                if (IwA || IwB) make_row_full(&r3[ax], la, lb, e, rA, rB, minv, IwA, IwB);
+                else make_row(&r3[ax], la, lb, e, rA, rB, minv);
                 r3[ax].bilateral = 1;
                 r3[ax].target = -P->erp * (pB[ax] - pA[ax]) / h;
             }
@@ -1229,7 +1423,8 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
         for (int a = 0; a < 3; ++a) { out[7 + a] = vel[6 * i + a]; out[10 + a] = vel[6 * i + 3 + a]; }
     }
     free(vel); free(minv); free(rows); free(lam); free(slots); free(prio); free(colour);
-    free(by_colour); free(col_start);
+    free(by_colour); free(col_start); free(iw);
+#undef IW_OF
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1320,7 +1515,7 @@ int orc_step(orc_sim *s, double dt, int iters) {
     s->res_sq_total = 0; s->res_max = 0; s->res_rows = 0;
     /* contacts */
     contact_input in = {n, s->st, s->rad, s->im, s->np, s->planes, s->plane_scene, s->sob,
-                        s->sflags, s->P.margin};
+                        s->sflags, s->P.margin, s->half};
     s->nc = contacts_impl(&in, 1, &s->con);
     /* constraint graph G^t from contacts and joints */
     int64_t nedge = s->nc + s->nj;
@@ -1335,7 +1530,7 @@ int orc_step(orc_sim *s, double dt, int iters) {
         int *ca = xcalloc((size_t)s->nc + 1, sizeof(int)), *cb = xcalloc((size_t)s->nc + 1, sizeof(int));
         for (int64_t i = 0; i < s->nc; ++i) {
             int a = s->con[i].a, b = s->con[i].b;
-            if (b >= n || s->im[a] == 0 || s->im[b] == 0) continue;
+            if (b >= n || s->im[a] == 0 || s->im[b] == 0 || s->con[i].k != 0) continue;   /* one per body pair */
             ca[m] = a; cb[m] = b; ++m;
         }
         int do_deact = s->P.lb_deact_every > 0 && (s->step_index % s->P.lb_deact_every) == 0;
@@ -1344,6 +1539,7 @@ int orc_step(orc_sim *s, double dt, int iters) {
             weight = xcalloc((size_t)n + 1, sizeof(int64_t));
             for (int b = 0; b < n; ++b) weight[b] = 1;
             for (int64_t i = 0; i < s->nc; ++i) {
+                if (s->con[i].k != 0) continue;   /* a box manifold counts once */
                 weight[s->con[i].a]++;
                 if (s->con[i].b < n) weight[s->con[i].b]++;
             }
@@ -1424,7 +1620,8 @@ int orc_step(orc_sim *s, double dt, int iters) {
                 if (i < s->nc) {
                     s->pair_kind[q] = 0;
                     s->pair_cidx[q] = i;
-                    s->pair_key[q] = ((uint64_t)(uint32_t)s->con[i].a << 32) | (uint32_t)s->con[i].b;
+                    s->pair_key[q] = ((uint64_t)(uint32_t)s->con[i].k << 60) |
+                                     ((uint64_t)(uint32_t)s->con[i].a << 32) | (uint32_t)s->con[i].b;
                 } else {
                     s->pair_kind[q] = 1;
                     s->pair_cidx[q] = i - s->nc;

@@ -525,7 +525,7 @@ def _box_body(c, h, density=1.0):
     return c, float(np.linalg.norm(h)), 1.0 / (8.0 * h[0] * h[1] * h[2] * density)
 
 
-def _box_scene(name, bodies, joints, anchors, planes, mu, dt, n_sets, gamma, beta, seed, iters):
+def _box_scene(name, bodies, joints, anchors, planes, mu, dt, n_sets, gamma, beta, seed, iters, **kw):
     """bodies: (centre, half extents (zeros = sphere of radius r), radius,
     inverse mass, velocity)"""
     pos = np.array([b[0] for b in bodies], np.float64)
@@ -534,7 +534,7 @@ def _box_scene(name, bodies, joints, anchors, planes, mu, dt, n_sets, gamma, bet
     he = np.array([b[1] for b in bodies], np.float32)
     sc = _single(name, pos, np.array([b[2] for b in bodies]), np.array([b[3] for b in bodies]), planes, mu=mu,
                  dt=dt, flags=1, gamma=gamma, beta=beta, n_sets=n_sets,
-                 set_of_body=kmeans_sets(pos, n_sets, seed), joints=joints, anchors=anchors, iters=iters)
+                 set_of_body=kmeans_sets(pos, n_sets, seed), joints=joints, anchors=anchors, iters=iters, **kw)
     sc.state = st
     sc.half_extents = he
     return sc
@@ -582,7 +582,10 @@ def plank_bridge(seed: int = 8, planks: int = 1589, half=(0.5, 1.0, 0.05), gap: 
     row along x, `gap` apart; ball joints join neighbours at both y edges,
     and the two end planks are jointed to the world the same way: 2 planks
     + 2 joints (3180 at the default 1589 planks).  `balls` spheres of radius
-    0.6 fall onto the deck from 2 m above it."""
+    0.6 fall onto the deck from 2 m above it.  The setup runs the articulated
+    assignment (Algorithms 2-3), so that joints across workers start in the
+    overlap.  The deck starts straight and taut; it settles by stretching its
+    joints a few millimetres."""
     hx, hy, hz = half
     pitch = 2 * hx + gap
     bodies = []
@@ -606,7 +609,7 @@ def plank_bridge(seed: int = 8, planks: int = 1589, half=(0.5, 1.0, 0.05), gap: 
                        [0, 0, 0]))
     planes = np.zeros((0, 4))
     return _box_scene("plank_bridge", bodies, np.array(joints, np.int32), np.array(anchors, np.float32), planes,
-                      mu, dt, n_sets, gamma, beta, seed, iters)
+                      mu, dt, n_sets, gamma, beta, seed, iters, assign_overlap=True)
 
 
 def bf16_grid(x) -> np.ndarray:

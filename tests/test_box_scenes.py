@@ -2,8 +2,8 @@
 scenes, Section 6) are well formed, checked with the box reference geometry:
 the building stands with every box supported and nothing interpenetrating;
 the bridge's joints have coincident pivots and chain every plank to the
-world at both ends.  Neither can be stepped yet, and both step entry points
-say so."""
+world at both ends.  The library's step does not take box bodies yet and
+says so; the oracle's step does (tests/test_box_oracle_step.py)."""
 import numpy as np
 import pytest
 
@@ -67,9 +67,7 @@ def test_bridge_joints_chain_every_plank_to_the_world():
     assert S.plank_bridge().joints.shape[0] == 3180
 
 
-def test_box_scenes_are_refused_by_the_steps():
+def test_box_scenes_are_refused_by_the_library_step():
     sc = S.plank_bridge(planks=10)
     with pytest.raises(ovl.OvlError):
         ovl._SceneArrays(sc)
-    with pytest.raises(ValueError):
-        O.OracleSim(sc)
