@@ -130,3 +130,18 @@ def test_partitioned_bridge_keeps_every_joint():
     joints = set(int(k) & ((1 << 62) - 1) for k in keys if int(k) >> 62 == 1)
     assert joints == set(range(sc.joints.shape[0]))
     assert sim.joint_error()["max"] < 2e-3
+
+
+def test_sphere_on_a_static_box_platform():
+    """A static box (inverse mass 0) as a platform: the sphere on it carries
+    its weight, the box does not move and takes no rows of its own."""
+    ms, r = 0.5, 0.3
+    sim = O.OracleSim(_scene([[0, 0, 2.0], [0.2, 0.1, 2.25 + r]], [[1.0, 1.0, 0.25], [0, 0, 0]],
+                             [0.0, 1 / ms], radius=[np.sqrt(2.0625), r], iters=500))
+    x0 = sim.state()[0].copy()
+    sim.step()
+    st, pr = sim.state(), sim.pairs()
+    np.testing.assert_array_equal(st[0], x0)
+    np.testing.assert_allclose(st[1, 7:13], 0, atol=1e-9)
+    assert len(pr["key"]) == 1
+    np.testing.assert_allclose(pr["lam"][0, 0], ms * G * DT, rtol=1e-6)
