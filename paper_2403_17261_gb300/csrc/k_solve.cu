@@ -15,7 +15,10 @@
 // colours -- the same result as sweeping the constraints one by one in colour
 // order.  Inside a colour every CTA takes the rows whose first dynamic body
 // it holds (the rows are grouped that way beforehand), so most body accesses
-// stay in the CTA's own shared memory.
+// stay in the CTA's own shared memory.  In full-size CTAs (one per SM) with
+// the masses in shared memory, a thread loads its next rows' records and
+// impulses into registers ahead of use: the next pass's during the current
+// one, the next colour's between the two halves of the colour barrier.
 //
 // Row model (sphere contact, normal n from a to b, lever arms r_a n and
 // -r_b n, tangents t1 and t2 = n x t1):
