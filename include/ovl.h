@@ -312,6 +312,29 @@ ovl_status ovl_box_box_contacts(int32_t n, const float *pose_a, const float *hal
                                 const float *half_b, float margin, int32_t on_gpu, int32_t *count,
                                 float *points, float *gaps, float *normal, int32_t *axis);
 
+/* All contacts of a scene with box bodies (Algorithm 1's contact step for
+ * row f1), in canonical order: every body a, then b > a of its scene
+ * (pairs with scene_flags bit 0), then its scene's planes (b = n + plane),
+ * and for a box manifold its points k = 0..3.  A pair is tested when its
+ * bounding spheres (radius[]) meet in FP32, ((dx dx + dy dy) + dz dz) <=
+ * ((ra + rb) + margin)^2 (a plane: ((n.p) - d) - r <= margin), the same
+ * decision the sphere contacts take; then the box functions above decide
+ * (two spheres: one contact, gap |d| - ra - rb).  Pairs of two static
+ * bodies and planes of static bodies are skipped.  state13[n][13] (x, q, v,
+ * w), radius[n], inv_mass[n], half[n][3] (zeros: a sphere),
+ * scene_of_body[n], scene_flags[n_scenes], planes[n_planes][4],
+ * plane_scene[n_planes].  Outputs, up to cap contacts: ab[][2], k[], phi[],
+ * normal[][3] (from a towards b), point[][3]; *total = the number found
+ * (more than cap: OVL_ERR_CAPACITY, the lists unwritten).  A brute-force
+ * pair search: for tests and modest scenes.  GPU and host runs give the
+ * same bits. */
+ovl_status ovl_box_scene_contacts(int32_t n, const float *state13, const float *radius, const float *inv_mass,
+                                  const float *half, const int32_t *scene_of_body, int32_t n_scenes,
+                                  const int32_t *scene_flags, int32_t n_planes, const float *planes,
+                                  const int32_t *plane_scene, float margin, int32_t on_gpu, int64_t cap,
+                                  int64_t *total, int32_t *ab, int32_t *k, float *phi, float *normal,
+                                  float *point);
+
 /* Box rows (the solve of Eq 1-7 with a box's general lever arms and full
  * world inverse inertia R diag(1/I) R^T, I_k = m/3 (h_j^2 + h_l^2)): one
  * velocity step of each of n independent boxes on its own static plane.  v

@@ -83,6 +83,7 @@ def lib():
         L.orc_step.restype = C.c_int
         L.orc_get_counts.argtypes = [C.c_void_p, i64p]
         L.orc_get_contacts.argtypes = [C.c_void_p, ip, dp, dp, dp]
+        L.orc_get_contact_points.argtypes = [C.c_void_p, ip, dp]
         L.orc_get_graph.argtypes = [C.c_void_p, ip, ip]
         L.orc_get_entries.argtypes = [C.c_void_p, i64p, ip, u8p, dp, dp]
         L.orc_get_pairs.argtypes = [C.c_void_p, ip, ip, i64p, u64p, ip, dp]
@@ -367,6 +368,14 @@ class OracleSim:
         lib().orc_get_contacts(self._h, _ptr(ab, ip), _ptr(phi, dp), _ptr(nn, dp), _ptr(t1, dp))
         return ab[:m], phi[:m], nn[:m], t1[:m]
 
+
+    def contact_points(self):
+        """(manifold index [m], contact point [m,3]) of the last step's
+        contacts; points are zero for sphere contacts."""
+        m = self.counts()["contacts"]
+        k, p = np.zeros(m, np.int32), np.zeros((m, 3))
+        lib().orc_get_contact_points(self._h, _ptr(k, ip), _ptr(p, dp))
+        return k, p
     def graph(self):
         m = self.counts()["adjacency"]
         rp = np.zeros(self.n + 1, np.int32)

@@ -1711,6 +1711,15 @@ void orc_get_contacts(const orc_sim *s, int *ab, double *phi, double *nrm, doubl
     }
 }
 
+/* manifold index and contact point of every contact (box contacts; the
+ * point is zero for sphere contacts, whose rows use the radii) */
+void orc_get_contact_points(const orc_sim *s, int *k, double *p) {
+    for (int64_t i = 0; i < s->nc; ++i) {
+        k[i] = s->con[i].k;
+        for (int j = 0; j < 3; ++j) p[3 * i + j] = s->con[i].at_point ? s->con[i].p[j] : 0.0;
+    }
+}
+
 void orc_get_graph(const orc_sim *s, int *row_ptr, int *col) {
     memcpy(row_ptr, s->row_ptr, ((size_t)s->n + 1) * sizeof(int));
     memcpy(col, s->col, (size_t)s->nadj * sizeof(int));

@@ -243,6 +243,21 @@ OVL_HD int box_box(const Obb &A, const Obb &B, float margin, float3 pts[4], floa
     return kept;
 }
 
+// ---- bounding tests (the step's FP32 contact decisions for spheres) -------
+// two spheres (or bounding spheres): ((dx dx + dy dy) + dz dz) <= ((ra + rb) + margin)^2
+OVL_HD bool spheres_touch(float3 a, float3 b, float ra, float rb, float margin) {
+    const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+    const float d2 = (dx * dx + dy * dy) + dz * dz;
+    const float rs = (ra + rb) + margin;
+    return d2 <= rs * rs;
+}
+
+// a sphere (or bounding sphere) and the plane n.x = d: ((n.p) - d) - r <= margin
+OVL_HD bool sphere_plane_touch(float3 c, float r, float4 pl, float margin) {
+    const float dotp = (pl.x * c.x + pl.y * c.y) + pl.z * c.z;
+    return (dotp - pl.w) - r <= margin;
+}
+
 // ---- box rows ------------------------------------------------------------
 // world inverse inertia of a solid box (inverse mass im, half extents h):
 // R diag(1 / I_k) R^T, I_k = m/3 (h_j^2 + h_l^2); row-major 3 x 3

@@ -114,6 +114,100 @@ __host__ __device__ void box_step_one(const BoxStepArgs &a, int i) {
     for (int j = 0; j < 12; ++j) a.lam[12 * (size_t)i + j] = j < 3 * k ? lam[j] : 0.f;
 }
 
+// ---- all contacts of a scene with boxes --------------------------------------
+struct SceneArgs {
+    int n, n_planes;
+    const float *state, *radius, *inv_mass, *half, *planes;   // [n][13], [n], [n], [n][3], [np][4]
+    const int32_t *sob, *scene_flags, *plane_scene;
+    float margin;
+    // outputs (write pass): from offset[a], in (a, b, k) order
+    const int64_t *offset;
+    int32_t *count_of;                  // count pass: contacts of each body a
+    int32_t *ab, *k;
+    float *phi, *normal, *point;
+};
+
+__host__ __device__ __forceinline__ bool is_box3(const float *h) { return h[0] > 0.f || h[1] > 0.f || h[2] > 0.f; }
+
+__host__ __device__ __forceinline__ float3 pos_of(const float *st) { return make_float3(st[0], st[1], st[2]); }
+
+// contacts of body a with the bodies after it in its scene, then with its
+// scene's planes; write == false only counts
+__host__ __device__ int scene_contacts_of(const SceneArgs &A, int a, bool write) {
+    const float *sa = A.state + 13 * (size_t)a;
+    const float3 ca = pos_of(sa);
+    const int s = A.sob[a];
+    const bool boxa = is_box3(A.half + 3 * (size_t)a);
+    int64_t o = write ? A.offset[a] : 0;
+    int cnt = 0;
+    auto put = [&](int b, int kk, float gap, float3 n, float3 p) {
+        if (write) {
+            A.ab[2 * o] = a; A.ab[2 * o + 1] = b; A.k[o] = kk; A.phi[o] = gap;
+            A.normal[3 * o] = n.x; A.normal[3 * o + 1] = n.y; A.normal[3 * o + 2] = n.z;
+            A.point[3 * o] = p.x; A.point[3 * o + 1] = p.y; A.point[3 * o + 2] = p.z;
+            ++o;
+        }
+        ++cnt;
+    };
+    if (A.scene_flags[s] & 1) {
+        for (int b = a + 1; b < A.n; ++b) {
+            if (A.sob[b] != s || (A.inv_mass[a] == 0.f && A.inv_mass[b] == 0.f)) continue;
+            const float *sb = A.state + 13 * (size_t)b;
+            const float3 cb = pos_of(sb);
+            if (!box::spheres_touch(ca, cb, A.radius[a], A.radius[b], A.margin)) continue;
+            const bool boxb = is_box3(A.half + 3 * (size_t)b);
+            if (!boxa && !boxb) {
+                // two spheres: one contact at the midpoint of the surfaces' gap
+                const float3 d = box::sub(cb, ca);
+                const float L = sqrtf(box::dot(d, d));
+                const float3 n = L > 0.f ? box::scl(d, 1.f / L) : make_float3(0.f, 0.f, 1.f);
+                put(b, 0, L - A.radius[a] - A.radius[b], n, box::add(ca, box::scl(n, A.radius[a])));
+                continue;
+            }
+            float3 pts[4], n;
+            float gaps[4];
+            if (boxa && boxb) {
+                const box::Obb Ba = obb_of(sa, A.half + 3 * (size_t)a), Bb = obb_of(sb, A.half + 3 * (size_t)b);
+                int axis;
+                float sep;
+                const int m = box::box_box(Ba, Bb, A.margin, pts, gaps, n, axis, sep);
+                for (int i = 0; i < m; ++i) put(b, i, gaps[i], n, pts[i]);
+            } else {
+                // sphere_box's normal runs from the sphere to the box
+                const int sph = boxa ? b : a, bx = boxa ? a : b;
+                const float *ss = A.state + 13 * (size_t)sph, *sx = A.state + 13 * (size_t)bx;
+                const box::Obb B = obb_of(sx, A.half + 3 * (size_t)bx);
+                float gap;
+                if (box::sphere_box(pos_of(ss), A.radius[sph], B, A.margin, pts[0], n, gap))
+                    put(b, 0, gap, sph == a ? n : box::scl(n, -1.f), pts[0]);
+            }
+        }
+    }
+    if (A.inv_mass[a] > 0.f)
+        for (int p = 0; p < A.n_planes; ++p) {
+            if (A.plane_scene[p] != s) continue;
+            const float4 pl = make_float4(A.planes[4 * p], A.planes[4 * p + 1], A.planes[4 * p + 2], A.planes[4 * p + 3]);
+            if (!box::sphere_plane_touch(ca, A.radius[a], pl, A.margin)) continue;
+            if (boxa) {
+                float3 pts[4], n;
+                float gaps[4];
+                const int m = box::box_plane(obb_of(sa, A.half + 3 * (size_t)a), pl, A.margin, pts, gaps, n);
+                for (int i = 0; i < m; ++i) put(A.n + p, i, gaps[i], n, pts[i]);
+            } else {
+                const float dotp = (pl.x * ca.x + pl.y * ca.y) + pl.z * ca.z;
+                const float3 n = make_float3(-pl.x, -pl.y, -pl.z);
+                put(A.n + p, 0, (dotp - pl.w) - A.radius[a], n, box::add(ca, box::scl(n, A.radius[a])));
+            }
+        }
+    if (!write) A.count_of[a] = cnt;
+    return cnt;
+}
+
+__global__ void k_scene_contacts(SceneArgs A, int write) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < A.n) scene_contacts_of(A, a, write != 0);
+}
+
 __global__ void k_box_plane_step(BoxStepArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) box_step_one(a, i);
@@ -300,6 +394,71 @@ extern "C" ovl_status ovl_box_plane_step(int32_t n, const float *pose, const flo
         fetch(vel, g.vel, 6 * (size_t)n);
         fetch(count, g.count, n);
         fetch(lam, g.lam, 12 * (size_t)n);
+        return OVL_OK;
+    });
+}
+
+extern "C" ovl_status ovl_box_scene_contacts(int32_t n, const float *state13, const float *radius,
+                                             const float *inv_mass, const float *half, const int32_t *scene_of_body,
+                                             int32_t n_scenes, const int32_t *scene_flags, int32_t n_planes,
+                                             const float *planes, const int32_t *plane_scene, float margin,
+                                             int32_t on_gpu, int64_t cap, int64_t *total, int32_t *ab, int32_t *k,
+                                             float *phi, float *normal, float *point) {
+    if (n < 0 || n_planes < 0 || n_scenes < 1 || cap < 0 || !total || !scene_flags ||
+        (n > 0 && (!state13 || !radius || !inv_mass || !half || !scene_of_body)) ||
+        (n_planes > 0 && (!planes || !plane_scene)) || (cap > 0 && (!ab || !k || !phi || !normal || !point)))
+        return OVL_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (scene_of_body[i] < 0 || scene_of_body[i] >= n_scenes) return OVL_ERR_ARG;
+    return guard([&]() -> ovl_status {
+        *total = 0;
+        if (n == 0) return OVL_OK;
+        std::vector<int32_t> cnt(n);
+        std::vector<int64_t> off(n + 1, 0);
+        SceneArgs A{n, n_planes, state13, radius, inv_mass, half, planes, scene_of_body, scene_flags, plane_scene,
+                    margin, nullptr, cnt.data(), nullptr, nullptr, nullptr, nullptr, nullptr};
+        if (!on_gpu) {
+            for (int a = 0; a < n; ++a) scene_contacts_of(A, a, false);
+            for (int a = 0; a < n; ++a) off[a + 1] = off[a] + cnt[a];
+            *total = off[n];
+            if (off[n] > cap) return OVL_ERR_CAPACITY;
+            A.offset = off.data(); A.ab = ab; A.k = k; A.phi = phi; A.normal = normal; A.point = point;
+            for (int a = 0; a < n; ++a) scene_contacts_of(A, a, true);
+            return OVL_OK;
+        }
+        DevArena d;
+        SceneArgs G = A;
+        G.state = d.in(state13, 13 * (size_t)n);
+        G.radius = d.in(radius, (size_t)n);
+        G.inv_mass = d.in(inv_mass, (size_t)n);
+        G.half = d.in(half, 3 * (size_t)n);
+        G.sob = d.in(scene_of_body, (size_t)n);
+        G.scene_flags = d.in(scene_flags, (size_t)n_scenes);
+        G.planes = d.in(planes, 4 * (size_t)n_planes);
+        G.plane_scene = d.in(plane_scene, (size_t)n_planes);
+        G.count_of = d.out<int32_t>(n);
+        k_scene_contacts<<<(n + 127) / 128, 128>>>(G, 0);
+        CK(cudaGetLastError());
+        fetch(cnt.data(), G.count_of, n);
+        for (int a = 0; a < n; ++a) off[a + 1] = off[a] + cnt[a];
+        *total = off[n];
+        if (off[n] > cap) return OVL_ERR_CAPACITY;
+        if (off[n] == 0) return OVL_OK;
+        const size_t m = (size_t)off[n];
+        G.offset = d.in(off.data(), (size_t)n + 1);
+        G.ab = d.out<int32_t>(2 * m);
+        G.k = d.out<int32_t>(m);
+        G.phi = d.out<float>(m);
+        G.normal = d.out<float>(3 * m);
+        G.point = d.out<float>(3 * m);
+        k_scene_contacts<<<(n + 127) / 128, 128>>>(G, 1);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+        fetch(ab, G.ab, 2 * m);
+        fetch(k, G.k, m);
+        fetch(phi, G.phi, m);
+        fetch(normal, G.normal, 3 * m);
+        fetch(point, G.point, 3 * m);
         return OVL_OK;
     });
 }

@@ -53,6 +53,7 @@ EXPORTED = [
     "ovl_log_append", "ovl_log_read", "ovl_mlp_train", "ovl_mlp_grad", "ovl_mlp_loss",
     "ovl_host_load_balance", "ovl_host_assign_overlap",
     "ovl_box_plane_contacts", "ovl_sphere_box_contacts", "ovl_box_box_contacts", "ovl_box_plane_step",
+    "ovl_box_scene_contacts",
 ]
 
 
@@ -164,6 +165,8 @@ def load_library(path: str | None = None):
         "ovl_box_box_contacts": [C.c_int32, _fp, _fp, _fp, _fp, C.c_float, C.c_int32, _ip, _fp, _fp, _fp, _ip],
         "ovl_box_plane_step": [C.c_int32, _fp, _fp, _fp, _fp, C.c_float, C.c_float, _fp, C.c_float, C.c_float,
                                C.c_float, C.c_int32, C.c_int32, _fp, _ip, _fp],
+        "ovl_box_scene_contacts": [C.c_int32, _fp, _fp, _fp, _fp, _ip, C.c_int32, _ip, C.c_int32, _fp, _ip,
+                                   C.c_float, C.c_int32, C.c_int64, C.POINTER(C.c_int64), _ip, _ip, _fp, _fp, _fp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -461,6 +464,37 @@ def ovl_box_plane_step(pose, half, inv_mass, plane, vel, mu=0.5, dt=1 / 60, grav
         float(erp), float(slop), float(margin), int(iters), int(on_gpu), _ptr(v, _fp), _ptr(cnt, _ip),
         _ptr(lam, _fp)))
     return v, cnt, lam
+
+
+def ovl_box_scene_contacts(scene, margin: float = 0.05, on_gpu: bool = True, cap: int | None = None):
+    """All contacts of a scene with boxes (Scene with half_extents), in
+    canonical order.  Returns dict(ab [m,2], k [m], phi [m], normal [m,3],
+    point [m,3])."""
+    st = np.ascontiguousarray(scene.state, dtype=np.float32).reshape(-1, 13)
+    n = st.shape[0]
+    rad = np.ascontiguousarray(scene.radius, dtype=np.float32)
+    im = np.ascontiguousarray(scene.inv_mass, dtype=np.float32)
+    he = np.zeros((n, 3), np.float32) if scene.half_extents is None else _f32c(scene.half_extents, 3)
+    sob = np.ascontiguousarray(scene.scene_of_body, dtype=np.int32)
+    sf = np.ascontiguousarray(scene.scene_flags, dtype=np.int32)
+    pl = _f32c(scene.planes, 4)
+    ps = np.ascontiguousarray(scene.plane_scene, dtype=np.int32)
+    L = load_library()
+    total = C.c_int64(0)
+    cap = 16 * n + 64 if cap is None else cap
+    while True:
+        ab, k = np.zeros((cap, 2), np.int32), np.zeros(cap, np.int32)
+        phi, nrm, pt = np.zeros(cap, np.float32), np.zeros((cap, 3), np.float32), np.zeros((cap, 3), np.float32)
+        rc = L.ovl_box_scene_contacts(n, _ptr(st, _fp), _ptr(rad, _fp), _ptr(im, _fp), _ptr(he, _fp), _ptr(sob, _ip),
+                                      sf.shape[0], _ptr(sf, _ip), pl.shape[0], _ptr(pl, _fp), _ptr(ps, _ip),
+                                      float(margin), int(on_gpu), cap, C.byref(total), _ptr(ab, _ip), _ptr(k, _ip),
+                                      _ptr(phi, _fp), _ptr(nrm, _fp), _ptr(pt, _fp))
+        if rc == OVL_ERR_CAPACITY:
+            cap = int(total.value)
+            continue
+        _check(None, rc)
+        m = int(total.value)
+        return dict(ab=ab[:m], k=k[:m], phi=phi[:m], normal=nrm[:m], point=pt[:m])
 
 
 def ovl_read_stats(ctx) -> dict:

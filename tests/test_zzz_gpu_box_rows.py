@@ -1,7 +1,7 @@
-"""Box rows (tests/test_box_rows.py) on the GPU, one thread per box, against
-the same functions run on the host, value for value: both sides are built
-without FMA contraction, their square roots and divisions are IEEE, and the
-clamps compare explicitly."""
+"""Box rows (tests/test_box_rows.py) and the scene contact step for boxes
+on the GPU, one thread per box, against the same functions run on the host,
+value for value: both sides are built without FMA contraction, their square
+roots and divisions are IEEE, and the row clamps compare explicitly."""
 import numpy as np
 import pytest
 
@@ -36,3 +36,16 @@ def test_box_rows_gpu_equal_host(n):
     g = ovl.ovl_box_plane_step(P, H, IM, PL, V, iters=100, on_gpu=True)
     h = ovl.ovl_box_plane_step(P, H, IM, PL, V, iters=100, on_gpu=False)
     _same(g, h)
+
+
+def test_scene_contacts_gpu_equal_host():
+    """The scene contact step for boxes on the GPU (one thread per body)
+    against the same functions on the host."""
+    from paper_2403_17261_gb300 import scenes as S
+    for sc in (S.box_building(storeys=3, cells=4, balls=2, n_sets=1), S.plank_bridge(planks=200, balls=2, n_sets=1)):
+        g = ovl.ovl_box_scene_contacts(sc, on_gpu=True)
+        h = ovl.ovl_box_scene_contacts(sc, on_gpu=False)
+        assert set(g) == set(h)
+        for key in g:
+            assert np.array_equal(g[key], h[key]), key
+        assert len(h["ab"]) > 100
