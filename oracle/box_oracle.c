@@ -440,7 +440,6 @@ static f3 f3sub(f3 a, f3 b) { return f3v(a.x - b.x, a.y - b.y, a.z - b.z); }
 static f3 f3mul(f3 a, float s) { return f3v(a.x * s, a.y * s, a.z * s); }
 static float f3dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 static f3 f3cross(f3 a, f3 b) { return f3v(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
-static float f3at(f3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
 
 typedef struct { f3 c, u[3]; float h[3]; } obb32;
 

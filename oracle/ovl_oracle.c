@@ -470,7 +470,7 @@ int64_t orc_contacts(int n, const double *state, const double *radius, const dou
                      const int *scene_of_body, const int *scene_flags, double margin, int use_grid,
                      int64_t cap, int *out_ab, double *out_phi, double *out_n, double *out_t1) {
     contact_input in = {n, state, radius, inv_mass, n_planes, planes, plane_scene, scene_of_body,
-                        scene_flags, margin};
+                        scene_flags, margin, NULL};
     orc_contact *list = NULL;
     int64_t cnt = contacts_impl(&in, use_grid, &list);
     for (int64_t i = 0; i < cnt && i < cap; ++i) {
