@@ -145,3 +145,35 @@ def test_sphere_on_a_static_box_platform():
     np.testing.assert_allclose(st[1, 7:13], 0, atol=1e-9)
     assert len(pr["key"]) == 1
     np.testing.assert_allclose(pr["lam"][0, 0], ms * G * DT, rtol=1e-6)
+
+
+def _incline(theta, mu):
+    """a box resting flat on a plane tilted by theta about x"""
+    h = np.array([0.5, 0.4, 0.2])
+    n = np.array([0.0, -np.sin(theta), np.cos(theta)])
+    c = n * h[2]                                        # bottom face on the plane through the origin
+    sc = _scene([c], [h], [0.5], iters=2000, mu=mu)
+    sc.planes = np.array([[n[0], n[1], n[2], 0.0]], np.float32)
+    q = np.array([np.cos(theta / 2), np.sin(theta / 2), 0.0, 0.0])   # the box turned with the plane
+    sc.state[0, 3:7] = q.astype(np.float32)
+    return sc, n
+
+
+def test_box_on_an_incline_sticks_below_the_friction_angle():
+    sc, n = _incline(np.radians(20.0), mu=0.5)     # tan 20 = 0.36 < 0.5
+    sim = O.OracleSim(sc)
+    sim.step()
+    # the FP32 contact points leave the four gaps ~1e-8 m uneven: a few 1e-6 of spin
+    np.testing.assert_allclose(sim.state()[0, 7:13], 0, atol=1e-5)
+
+
+def test_box_on_an_incline_slides_above_the_friction_angle():
+    theta, mu = np.radians(35.0), 0.5               # tan 35 = 0.70 > 0.5
+    sc, n = _incline(theta, mu)
+    sim = O.OracleSim(sc)
+    sim.step()
+    v = sim.state()[0, 7:10]
+    down = np.array([0.0, -np.cos(theta), -np.sin(theta)])   # down the slope
+    np.testing.assert_allclose(v @ down, G * DT * (np.sin(theta) - mu * np.cos(theta)), rtol=1e-3)
+    np.testing.assert_allclose(v @ n, 0, atol=1e-5)
+    np.testing.assert_allclose(sim.state()[0, 10:13], 0, atol=1e-5)
