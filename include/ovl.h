@@ -123,6 +123,9 @@ typedef struct ovl_scene_desc {
     const int32_t *scene_gamma;  /* [n_scenes] overlap growth depth gamma (Alg 3, Alg 6) */
     const int32_t *scene_beta;   /* [n_scenes] weight search depth beta (Alg 5), <= 254 */
     const int32_t *n_sets;       /* [n_scenes] workers per scene, 1..64 */
+    const float *half_extents;   /* [n][3] box half extents (zeros: a sphere), or NULL: all spheres.
+                                    The step does not simulate box bodies yet: a positive extent is
+                                    OVL_ERR_ARG at upload (their contacts: ovl_box_scene_contacts) */
 } ovl_scene_desc;
 
 /* Last-step statistics. */

@@ -88,7 +88,7 @@ class ovl_scene_desc(C.Structure):
                 ("n_joints", C.c_int32), ("joint_bodies", _ip), ("joint_anchors", _fp),
                 ("n_scenes", C.c_int32), ("scene_of_body", _ip), ("scene_mu", _fp),
                 ("scene_dt", _fp), ("scene_flags", _ip), ("scene_gamma", _ip), ("scene_beta", _ip),
-                ("n_sets", _ip)]
+                ("n_sets", _ip), ("half_extents", _fp)]
 
 
 class ovl_stats(C.Structure):
