@@ -483,8 +483,8 @@ ovl_status ovl_mlp_loss(ovl_ctx *ctx, int64_t first, int64_t count, double *loss
  * Geodesic distances without allocation
  *
  * No counterpart in the paper.  Computes the same D(o,i) as the geodesic
- * phase of ovl_step (Eq 16, Algorithm 5: breadth-first search over the
- * constraint graph G^t from the bodies that only worker i simulates, cut at
+ * phase of ovl_step (the distance, in edges of the constraint graph, from
+ * overlap body o to the nearest body that only worker i simulates, cut at
  * depth beta), for one scene whose graph, masks and entries the caller
  * already holds on the device.  It exists for callers that must not allocate
  * device memory: fixed-rate control loops, where cudaFree synchronises the
@@ -494,7 +494,9 @@ ovl_status ovl_mlp_loss(ovl_ctx *ctx, int64_t first, int64_t count, double *loss
  * function calls neither cudaMalloc nor cudaFree nor any
  * allocating library routine: its search bitmap, frontier queue and level
  * counters live in one statically sized __device__ array of the library
- * (about 16.5 MiB), whose device address is looked up once per device.
+ * (about 16.5 MiB) that every GPU which loads the library holds until the
+ * process exits.  Its device address is looked up in the current device's
+ * context on every call, so a device reset needs no special handling.
  *
  * Limits: n_bodies * n_workers <= OVL_GEO_STATIC_MAX_PAIRS and
  * beta <= OVL_GEO_STATIC_MAX_BETA; larger problems are rejected with
@@ -519,9 +521,11 @@ ovl_status ovl_mlp_loss(ovl_ctx *ctx, int64_t first, int64_t count, double *loss
  * Concurrency: the scratch array is shared by every call on a device, so
  * two calls whose work can overlap on the device (other streams, other
  * threads, or other processes sharing a context) race and give wrong D.
- * Serialise them, e.g. on one stream.  The first call on each device looks
- * up the scratch address (cudaGetSymbolAddress, which may load the module);
- * make that first call before any stream capture begins. */
+ * Serialise them, e.g. on one stream.  The array keeps the last call's
+ * contents; each call clears the parts it reads before it uses them.  The
+ * first call on each device (and the first after a device reset) may load
+ * the library's module while it looks up the address
+ * (cudaGetSymbolAddress); make that call before any stream capture begins. */
 #define OVL_GEO_STATIC_MAX_PAIRS 4194304
 #define OVL_GEO_STATIC_MAX_BETA 254
 ovl_status ovl_geodesics_static(int32_t n_bodies, int32_t n_workers, int32_t beta,

@@ -1060,10 +1060,14 @@ ovl_status ovl_scene_upload(ovl_ctx *c, const ovl_scene_desc *d) {
         if (!d->scene_mu || !d->scene_dt || !d->scene_flags || !d->scene_gamma || !d->scene_beta || !d->n_sets)
             return fail(c, OVL_ERR_ARG, "scene: per-scene arrays are required");
         if (d->half_extents)
-            for (size_t i = 0; i < 3 * (size_t)n; ++i)
-                if (d->half_extents[i] > 0.f)
+            for (size_t i = 0; i < 3 * (size_t)n; ++i) {
+                const float h = d->half_extents[i];
+                if (!(h >= 0.f) || !std::isfinite(h))
+                    return fail(c, OVL_ERR_ARG, "scene: half extents must be finite and >= 0");
+                if (h > 0.f)
                     return fail(c, OVL_ERR_ARG, "scene: box bodies are not simulated by the step yet "
                                                 "(their contacts: ovl_box_scene_contacts)");
+            }
         std::vector<int> sob(n, 0);
         if (d->scene_of_body) std::copy(d->scene_of_body, d->scene_of_body + n, sob.begin());
         for (int b = 0; b < n; ++b) {

@@ -7,6 +7,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <cmath>
+
 #include <vector>
 
 #include "box_geom.cuh"
@@ -410,6 +412,9 @@ extern "C" ovl_status ovl_box_scene_contacts(int32_t n, const float *state13, co
         return OVL_ERR_ARG;
     for (int i = 0; i < n; ++i)
         if (scene_of_body[i] < 0 || scene_of_body[i] >= n_scenes) return OVL_ERR_ARG;
+    // a NaN or negative extent would otherwise read as a sphere
+    for (size_t i = 0; i < 3 * (size_t)n; ++i)
+        if (!(half[i] >= 0.f) || !std::isfinite(half[i])) return OVL_ERR_ARG;
     return guard([&]() -> ovl_status {
         *total = 0;
         if (n == 0) return OVL_OK;

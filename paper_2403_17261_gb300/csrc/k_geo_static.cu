@@ -12,10 +12,8 @@
 // range-checked before it is used.
 #include <cuda_runtime.h>
 
-#include <atomic>
 #include <cstdint>
 #include <cstdio>
-#include <mutex>
 
 #include "ovl.h"
 
@@ -23,7 +21,6 @@ namespace {
 
 constexpr long long kMaxPairs = OVL_GEO_STATIC_MAX_PAIRS;
 constexpr int kMaxBeta = OVL_GEO_STATIC_MAX_BETA;
-constexpr int kMaxDevices = 64;
 static_assert(kMaxPairs % 32 == 0, "bitmap words");
 static_assert(kMaxPairs <= (1ll << 26), "queue items hold a body index in 26 bits");
 static_assert(kMaxBeta <= 254, "D is a byte and 255 means not reached");
@@ -36,9 +33,6 @@ struct GeoScratch {
 
 // 16.5 MiB of device memory, reserved when the module is loaded.
 static __device__ __align__(256) GeoScratch g_geo_scratch;
-
-std::atomic<GeoScratch *> g_scratch_of_device[kMaxDevices];
-std::mutex g_setup_mutex;
 
 struct GeoIn {
     int n, nw, n_adj, ne;
@@ -113,27 +107,19 @@ int report(char *err, int cap, int code, const char *msg) {
     return code;
 }
 
-// The device address of the scratch array on the current device, looked up
-// once per device.
+// The device address of the scratch array in the current device's context.
+// It is looked up on every call, not cached per device number: a device reset
+// (cudaDeviceReset) or a released and re-created primary context reloads the
+// module, and the array may then sit at another address.  After the module is
+// loaded the lookup is a table read.
 int scratch_of_current_device(GeoScratch **out, char *err, int cap) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return report(err, cap, OVL_ERR_CUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return report(err, cap, OVL_ERR_CAPACITY, "device index >= 64");
-    GeoScratch *p = g_scratch_of_device[dev].load(std::memory_order_acquire);
-    if (!p) {
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        p = g_scratch_of_device[dev].load(std::memory_order_acquire);
-        if (!p) {
-            e = cudaGetSymbolAddress((void **)&p, g_geo_scratch);
-            if (e != cudaSuccess || !p) {
-                char msg[160];
-                snprintf(msg, sizeof msg, "cudaGetSymbolAddress of the geodesic scratch failed: %s",
-                         cudaGetErrorString(e));
-                return report(err, cap, OVL_ERR_CUDA, msg);
-            }
-            g_scratch_of_device[dev].store(p, std::memory_order_release);
-        }
+    GeoScratch *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&p, g_geo_scratch);
+    if (e != cudaSuccess || !p) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "cudaGetSymbolAddress of the geodesic scratch failed: %s",
+                 cudaGetErrorString(e));
+        return report(err, cap, OVL_ERR_CUDA, msg);
     }
     *out = p;
     return OVL_OK;

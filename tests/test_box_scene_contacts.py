@@ -62,3 +62,14 @@ def test_scene_contacts_capacity():
     sc = SCENES["building"]()
     r = ovl.ovl_box_scene_contacts(sc, margin=MARGIN, on_gpu=False, cap=3)   # grows to the total
     assert len(r["ab"]) > 3
+
+
+@pytest.mark.parametrize("bad", [np.nan, -0.25, np.inf])
+def test_scene_contacts_refuse_bad_half_extents(bad):
+    # a NaN or negative extent must not be read as a sphere
+    sc = SCENES["building"]()
+    sc.half_extents = sc.half_extents.copy()
+    sc.half_extents[3, 1] = bad
+    with pytest.raises(ovl.OvlError) as e:
+        ovl.ovl_box_scene_contacts(sc, margin=MARGIN, on_gpu=False)
+    assert e.value.code == ovl.OVL_ERR_ARG

@@ -19,23 +19,36 @@ def _built():
     g.build()
 
 
-def _static_D(sim, scene, torch):
-    from paper_2403_17261_gb300 import ovl
+def _inputs(sim, torch):
+    """The step's graph, masks and entries as device tensors, and a D buffer
+    filled with a value every entry must overwrite."""
     row_ptr, col = sim.graph()
     mask = sim.membership()
     ent = sim.entries()
-    n, ne = sim.n, len(ent["D"])
     dev = torch.device("cuda", 0)
-    t_rp = torch.from_numpy(row_ptr.astype(np.int32)).to(dev)
-    t_col = torch.from_numpy(np.ascontiguousarray(col, dtype=np.int32)).to(dev)
-    t_mask = torch.from_numpy(np.ascontiguousarray(mask, dtype=np.uint64).view(np.int64)).to(dev)
-    t_ep = torch.from_numpy(ent["entry_ptr"].astype(np.int32)).to(dev)
-    t_D = torch.full((max(ne, 1),), 7, dtype=torch.uint8, device=dev)  # must be overwritten
+    t = dict(
+        rp=torch.from_numpy(row_ptr.astype(np.int32)).to(dev),
+        col=torch.from_numpy(np.ascontiguousarray(col, dtype=np.int32)).to(dev),
+        mask=torch.from_numpy(np.ascontiguousarray(mask, dtype=np.uint64).view(np.int64)).to(dev),
+        ep=torch.from_numpy(ent["entry_ptr"].astype(np.int32)).to(dev),
+        D=torch.full((max(len(ent["D"]), 1),), 7, dtype=torch.uint8, device=dev),
+        n_adj=len(col), ne=len(ent["D"]))
+    return t, ent["D"], mask
+
+
+def _call(sim, scene, t, torch):
+    from paper_2403_17261_gb300 import ovl
+    dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    ovl.ovl_geodesics_static(n, int(scene.n_sets[0]), int(scene.scene_beta[0]), t_rp, t_col,
-                             len(col), t_mask, t_ep, ne, t_D, stream=stream.cuda_stream)
+    ovl.ovl_geodesics_static(sim.n, int(scene.n_sets[0]), int(scene.scene_beta[0]), t["rp"], t["col"],
+                             t["n_adj"], t["mask"], t["ep"], t["ne"], t["D"], stream=stream.cuda_stream)
     torch.cuda.synchronize(dev)
-    return t_D.cpu().numpy()[:ne], ent["D"], mask
+    return t["D"].cpu().numpy()[:t["ne"]]
+
+
+def _static_D(sim, scene, torch):
+    t, want, mask = _inputs(sim, torch)
+    return _call(sim, scene, t, torch), want, mask
 
 
 def test_static_geodesics_match_step_twice_in_a_row():
@@ -51,6 +64,32 @@ def test_static_geodesics_match_step_twice_in_a_row():
             assert multi.any()                       # the overlap is not empty
             assert (want != 255).any()
             np.testing.assert_array_equal(got, want, err_msg=f"call {call}")
+    finally:
+        sim.close()
+
+
+def test_static_geodesics_allocate_no_device_memory():
+    """After one call (the module is loaded and the address looked up), a
+    further call and its synchronize leave the device's free memory as it was."""
+    torch = pytest.importorskip("torch")
+    from paper_2403_17261_gb300 import ovl
+    sc = S.random_pile(1500, 12, n_sets=5, box=0.3 * 1500 ** (1 / 3) + 1.0)
+    sim = ovl.Simulation(sc)
+    try:
+        sim.step()
+        t, want, _ = _inputs(sim, torch)
+        np.testing.assert_array_equal(_call(sim, sc, t, torch), want)
+        t["D"].fill_(7)
+        torch.cuda.synchronize()
+        free_before, _ = torch.cuda.mem_get_info()
+        dev = torch.device("cuda", 0)
+        ovl.ovl_geodesics_static(sim.n, int(sc.n_sets[0]), int(sc.scene_beta[0]), t["rp"], t["col"],
+                               t["n_adj"], t["mask"], t["ep"], t["ne"], t["D"],
+                               stream=torch.cuda.current_stream(dev).cuda_stream)
+        torch.cuda.synchronize(dev)
+        free_after, _ = torch.cuda.mem_get_info()
+        assert free_after == free_before, (free_before, free_after)
+        np.testing.assert_array_equal(t["D"].cpu().numpy()[:t["ne"]], want)
     finally:
         sim.close()
 
