@@ -86,6 +86,13 @@ def default_settle(workload):
             "warmstart": 150, "gamma": 0}[workload]
 
 
+def step_params(ovl, lb_load: str = "bodies") -> dict:
+    """Context parameters of the timed step (the full-size parity test uses
+    the same ones, so it checks the launch plan this file times)."""
+    return dict(flags=ovl.OVL_FLAG_TIMING,
+                lb_load=ovl.OVL_LB_CONTACTS if lb_load == "contacts" else ovl.OVL_LB_BODIES)
+
+
 def make_scene(workload):
     from paper_2403_17261_gb300 import scenes as S
     return S.WORKLOADS[workload]()
@@ -251,8 +258,7 @@ def gpu_arm(args, rank, world, local_rank):
     sc = make_scene(args.workload)
     stream = torch.cuda.Stream()
     lb_load = ovl.OVL_LB_CONTACTS if args.lb_load == "contacts" else ovl.OVL_LB_BODIES
-    params = dict(flags=ovl.OVL_FLAG_TIMING, lb_load=lb_load)
-    sim = ovl.Simulation(sc, params, stream=stream.cuda_stream)
+    sim = ovl.Simulation(sc, step_params(ovl, args.lb_load), stream=stream.cuda_stream)
     settle = default_settle(args.workload) if args.settle is None else args.settle
     # NVTX ranges let a profiler select the timed steps (ncu --nvtx --nvtx-include "timed/")
     torch.cuda.nvtx.range_push("settle")

@@ -391,6 +391,13 @@ ovl_status ovl_autotune_import(ovl_ctx *ctx, const char *json);
 ovl_status ovl_read_worker_stats(ovl_ctx *ctx, int32_t *iters, double *res_sq, int64_t *rows,
                                  int32_t *colours);
 
+/* The launch plan of the last step's solve (no counterpart in the paper: the
+ * paper's workers are processes).  ctas [n_workers] (host, caller-owned):
+ * how many CTAs, one thread-block cluster, solved each worker.  Every plan
+ * computes the same bits; the plan changes only the time.  OVL_ERR_ARG before
+ * the first step. */
+ovl_status ovl_read_solve_plan(ovl_ctx *ctx, int32_t *ctas);
+
 /* ------------------------------------------------------------------------
  * Learned warm start (not in the paper)
  *

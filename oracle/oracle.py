@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
     if (force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < os.path.getmtime(SRC)
             or os.path.getmtime(LIB_PATH) < os.path.getmtime(BOX_SRC)):
         tmp = LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-shared", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-std=c11", "-shared", "-fPIC",
                                "-o", tmp, SRC, BOX_SRC, "-lm"])
         os.replace(tmp, LIB_PATH)
     return LIB_PATH
@@ -106,6 +106,8 @@ def lib():
         L.orc_blend.argtypes = [C.c_int, dp, dp, dp]
         L.orc_colour.restype = C.c_int
         L.orc_colour.argtypes = [C.c_int, ip, u64p, C.c_int, ip]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_get_threads.restype = C.c_int
         L.orc_mix64.restype = C.c_uint64
         L.orc_mix64.argtypes = [C.c_uint64]
         _lib = L
@@ -114,6 +116,16 @@ def lib():
 
 def _ptr(a, t):
     return a.ctypes.data_as(t)
+
+
+def set_threads(n: int) -> None:
+    """Threads for the per-body contact search and the per-worker solve
+    (1 = the caller's thread only).  Results do not depend on it."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
 
 
 def _f64(a):

@@ -9,8 +9,13 @@
  * generator with the CUDA library; both are fed from the seeded scene
  * generators only.
  *
- * Every step is written in the paper's order and notation, single-threaded,
- * with no blocking, fusion or reordering:
+ * Every step is written in the paper's order and notation, with no blocking,
+ * fusion or reordering.  Three loops whose iterations are independent -- the
+ * contacts of each body, the solve of each worker (workers share nothing
+ * during a step, Section 4) and the search of D(o, i) from each overlap body
+ * -- may run on several threads (orc_set_threads; default 1); each
+ * iteration's arithmetic is the same, so no result depends on the thread
+ * count:
  *
  *   contacts  (Alg 1 contact generation, Section 5.4)      orc_contacts
  *   graph G^t (Section 5.1, constraint graph)              orc_graph
@@ -75,13 +80,16 @@
  *    the impulse that cancels one step of gravity on the normal row.  Joint
  *    pairs have all-zero features and s = 0.
  *
- * Build: gcc -O2 -ffp-contract=off -std=c11 -shared -fPIC (no fused
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -std=c11 -shared -fPIC (no fused
  * multiply-add, so FP32 decisions round exactly as written).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_ERR_ARG (-1)
@@ -109,6 +117,31 @@ typedef struct {
 /* ------------------------------------------------------------------------ */
 /* small helpers                                                             */
 /* ------------------------------------------------------------------------ */
+
+/* Threads for the loops whose iterations are independent (contacts per
+ * body, PGS per worker, geodesic search per body); 1 (the default) runs
+ * everything on the caller's thread.  No result depends on this number. */
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+
+int orc_get_threads(void) { return g_threads; }
+
+static int orc_thread_count(void) {
+#ifdef _OPENMP
+    return g_threads;
+#else
+    return 1;
+#endif
+}
+
+static int orc_thread_id(void) {
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
 
 static void *xcalloc(size_t n, size_t sz) {
     void *p = calloc(n ? n : 1, sz ? sz : 1);
@@ -367,6 +400,38 @@ static void box_plane_contacts(const contact_input *in, int a, int p, contact_bu
  * neighbouring cells; the grid only prunes, every candidate is tested.
  * Pairs where both ends are static are skipped. Returns the count, or
  * ORC_ERR_CAPACITY if more than cap contacts exist (out is then partial). */
+/* Sphere-sphere (or box) contacts (a, b > a) of body a through the sorted
+ * cell list: for each of the 3 x 3 neighbouring (x, y) columns, one search
+ * for the lowest cell z - 1, then a scan up to cell z + 1. */
+static void grid_contacts_of(const contact_input *in, const cell_entry *cells, int n, double cs, int a,
+                             contact_buf *B) {
+    int s = in->scene_of_body[a];
+    if (!(in->scene_flags[s] & 1)) return;
+    const double *ca = in->state + 13 * (size_t)a;
+    int64_t cx = (int64_t)floor(ca[0] / cs), cy = (int64_t)floor(ca[1] / cs), cz = (int64_t)floor(ca[2] / cs);
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy) {
+            cell_entry key = {cx + dx, cy + dy, cz - 1, s, -1};
+            int lo = 0, hi = n;   /* lower bound of key */
+            while (lo < hi) {
+                int mid = (lo + hi) / 2;
+                if (cmp_cell(&cells[mid], &key) < 0) lo = mid + 1; else hi = mid;
+            }
+            for (int k = lo; k < n; ++k) {
+                const cell_entry *e = &cells[k];
+                if (e->scene != s || e->cx != key.cx || e->cy != key.cy || e->cz > cz + 1) break;
+                int b = e->body;
+                if (b <= a) continue;
+                if (in->inv_mass[a] == 0 && in->inv_mass[b] == 0) continue;
+                const double *cb = in->state + 13 * (size_t)b;
+                if (is_box(in, a) || is_box(in, b))
+                    box_pair_contacts(in, a, b, B);
+                else if (sphere_pair_touches_f32(ca, cb, in->radius[a], in->radius[b], in->margin))
+                    fill_sphere_contact(cb_next(B), a, b, ca, cb, in->radius[a], in->radius[b]);
+            }
+        }
+}
+
 static int64_t contacts_impl(const contact_input *in, int use_grid, orc_contact **out_list) {
     int n = in->n;
     size_t cap = 1024, cnt = 0;
@@ -391,39 +456,18 @@ static int64_t contacts_impl(const contact_input *in, int use_grid, orc_contact 
             cells[i].body = i;
         }
         qsort(cells, n, sizeof(cell_entry), cmp_cell);
-        for (int i = 0; i < n; ++i) {
-            int a = i;
-            int s = in->scene_of_body[a];
-            if (!(in->scene_flags[s] & 1)) continue;
-            const double *ca = in->state + 13 * (size_t)a;
-            int64_t cx = (int64_t)floor(ca[0] / cs), cy = (int64_t)floor(ca[1] / cs),
-                    cz = (int64_t)floor(ca[2] / cs);
-            for (int dx = -1; dx <= 1; ++dx)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dz = -1; dz <= 1; ++dz) {
-                        cell_entry key = {cx + dx, cy + dy, cz + dz, s, -1};
-                        /* lower bound */
-                        int lo = 0, hi = n;
-                        while (lo < hi) {
-                            int mid = (lo + hi) / 2;
-                            if (cmp_cell(&cells[mid], &key) < 0) lo = mid + 1; else hi = mid;
-                        }
-                        for (int k = lo; k < n; ++k) {
-                            const cell_entry *e = &cells[k];
-                            if (e->scene != s || e->cx != key.cx || e->cy != key.cy || e->cz != key.cz) break;
-                            int b = e->body;
-                            if (b <= a) continue;
-                            if (in->inv_mass[a] == 0 && in->inv_mass[b] == 0) continue;
-                            const double *cb = in->state + 13 * (size_t)b;
-                            if (is_box(in, a) || is_box(in, b)) {
-                                contact_buf B = {list, cnt, cap};
-                                box_pair_contacts(in, a, b, &B);
-                                list = B.list; cnt = B.cnt; cap = B.cap;
-                            } else if (sphere_pair_touches_f32(ca, cb, in->radius[a], in->radius[b], in->margin))
-                                PUSH_CONTACT(fill_sphere_contact(&list[cnt], a, b, ca, cb, in->radius[a], in->radius[b]));
-                        }
-                    }
+        /* bodies are independent here: each thread collects its own list and
+         * the lists are joined before the canonical sort below */
+        int nt = orc_thread_count();
+        contact_buf *part = calloc((size_t)nt, sizeof(contact_buf));
+        for (int t = 0; t < nt; ++t) { part[t].cap = 1024; part[t].list = malloc(1024 * sizeof(orc_contact)); }
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nt)
+        for (int a = 0; a < n; ++a) grid_contacts_of(in, cells, n, cs, a, &part[orc_thread_id()]);
+        for (int t = 0; t < nt; ++t) {
+            for (size_t i = 0; i < part[t].cnt; ++i) PUSH_CONTACT(list[cnt] = part[t].list[i]);
+            free(part[t].list);
         }
+        free(part);
         free(cells);
     } else {
         for (int a = 0; a < n; ++a) {
@@ -754,47 +798,57 @@ void orc_assign_overlap(int n, uint64_t *mask, const int *scene_of_body, const i
 /* where the worker is not met within beta (and for bodies outside O).        */
 /* ------------------------------------------------------------------------ */
 
+/* D(o, i) of one body o (its entries of D); ws is the caller's workspace */
+static void geodesics_of(bfs_ws *ws, int o, const uint64_t *mask, const int *sob, const int *scene_beta,
+                         const int *row_ptr, const int *col, const int64_t *entry_ptr, uint8_t *D) {
+    uint64_t Wo = mask[o];
+    for (int64_t e = entry_ptr[o]; e < entry_ptr[o + 1]; ++e) D[e] = 255;
+    if (popc64(Wo) < 2) return;
+    int beta = scene_beta[sob[o]];
+    /* breadth-first from o, depth 1..beta (Alg 5); the first body met
+     * that is active only in worker i, with i in W_o, gives the minimum
+     * of Eq 16 for i */
+    ws->cur++;
+    int head = 0, tail = 0;
+    ws->queue[tail++] = o;
+    ws->stamp[o] = ws->cur;
+    ws->dist[o] = 0;
+    uint64_t found = 0;
+    while (head < tail && found != Wo) {
+        int u = ws->queue[head++];
+        if (ws->dist[u] >= beta) continue;
+        for (int k = row_ptr[u]; k < row_ptr[u + 1]; ++k) {
+            int v = col[k];
+            if (ws->stamp[v] == ws->cur) continue;
+            ws->stamp[v] = ws->cur;
+            ws->dist[v] = ws->dist[u] + 1;
+            ws->queue[tail++] = v;
+            uint64_t Wv = mask[v];
+            if (popc64(Wv) == 1 && (Wv & Wo) == Wv && !(found & Wv)) {
+                found |= Wv;
+                int w = lowest_bit(Wv);
+                int rank = popc64(Wo & (((uint64_t)1 << w) - 1));
+                D[entry_ptr[o] + rank] = (uint8_t)ws->dist[v];
+            }
+        }
+    }
+    /* stopping once every worker is met (as Alg 5 does) changes nothing:
+     * later hits are at the same or a larger depth and are not recorded */
+}
+
+/* every body's search is its own (it writes only its entries of D), so the
+ * bodies may be taken by several threads, each with its own workspace */
 static void geodesics_impl(int n, const uint64_t *mask, const int *sob, const int *scene_beta,
                            const int *row_ptr, const int *col, const int64_t *entry_ptr,
                            uint8_t *D) {
-    bfs_ws ws;
-    bfs_ws_init(&ws, n);
-    for (int o = 0; o < n; ++o) {
-        uint64_t Wo = mask[o];
-        for (int64_t e = entry_ptr[o]; e < entry_ptr[o + 1]; ++e) D[e] = 255;
-        if (popc64(Wo) < 2) continue;
-        int beta = scene_beta[sob[o]];
-        /* breadth-first from o, depth 1..beta (Alg 5); the first body met
-         * that is active only in worker i, with i in W_o, gives the minimum
-         * of Eq 16 for i */
-        ws.cur++;
-        int head = 0, tail = 0;
-        ws.queue[tail++] = o;
-        ws.stamp[o] = ws.cur;
-        ws.dist[o] = 0;
-        uint64_t found = 0;
-        while (head < tail && found != Wo) {
-            int u = ws.queue[head++];
-            if (ws.dist[u] >= beta) continue;
-            for (int k = row_ptr[u]; k < row_ptr[u + 1]; ++k) {
-                int v = col[k];
-                if (ws.stamp[v] == ws.cur) continue;
-                ws.stamp[v] = ws.cur;
-                ws.dist[v] = ws.dist[u] + 1;
-                ws.queue[tail++] = v;
-                uint64_t Wv = mask[v];
-                if (popc64(Wv) == 1 && (Wv & Wo) == Wv && !(found & Wv)) {
-                    found |= Wv;
-                    int w = lowest_bit(Wv);
-                    int rank = popc64(Wo & (((uint64_t)1 << w) - 1));
-                    D[entry_ptr[o] + rank] = (uint8_t)ws.dist[v];
-                }
-            }
-        }
-        /* stopping once every worker is met (as Alg 5 does) changes nothing:
-         * later hits are at the same or a larger depth and are not recorded */
+#pragma omp parallel num_threads(orc_thread_count())
+    {
+        bfs_ws ws;
+        bfs_ws_init(&ws, n);
+#pragma omp for schedule(dynamic, 64)
+        for (int o = 0; o < n; ++o) geodesics_of(&ws, o, mask, sob, scene_beta, row_ptr, col, entry_ptr, D);
+        bfs_ws_free(&ws);
     }
-    bfs_ws_free(&ws);
 }
 
 void orc_geodesics(int n, const uint64_t *mask, const int *scene_of_body, const int *scene_beta,
@@ -931,7 +985,7 @@ typedef struct {
     double *pair_scale; /* npairs: s = k_n g_ref h (0 for joints) */
     int *pair_found;    /* npairs: 1 if the previous step left impulses for it */
     uint8_t *depth;     /* n: BFS distance in G^t to O, capped at ORC_DEPTH_CAP */
-    int *part_iters; double *part_res_sq; int64_t *part_rows; int *part_colours;
+    int *part_iters; double *part_res_sq, *part_res_max; int64_t *part_rows; int *part_colours;
     double res_sq_total; double res_max; int64_t res_rows;
     double joint_violation_max, joint_violation_sum;
     double *half;       /* n x 3 half extents (zeros: a sphere); NULL until orc_set_shapes */
@@ -1018,8 +1072,8 @@ static void free_step_records(orc_sim *s) {
     s->pair_lam = NULL;
     free(s->pair_feat); free(s->pair_scale); free(s->pair_found); free(s->depth);
     s->pair_feat = NULL; s->pair_scale = NULL; s->pair_found = NULL; s->depth = NULL;
-    free(s->part_iters); free(s->part_res_sq); free(s->part_rows); free(s->part_colours);
-    s->part_iters = NULL; s->part_res_sq = NULL; s->part_rows = NULL; s->part_colours = NULL;
+    free(s->part_iters); free(s->part_res_sq); free(s->part_res_max); free(s->part_rows); free(s->part_colours);
+    s->part_iters = NULL; s->part_res_sq = NULL; s->part_res_max = NULL; s->part_rows = NULL; s->part_colours = NULL;
 }
 
 void orc_destroy(orc_sim *s) {
@@ -1393,17 +1447,16 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
         }
     }
     /* c10: residual at the final iterate */
-    double sq = 0;
+    double sq = 0, rmax = 0;
     for (int64_t i = 0; i < 3 * np_; ++i) {
         double rr = row_residual(&rows[i], vel, lam, (int)i);
         sq += rr * rr;
-        if (fabs(rr) > s->res_max) s->res_max = fabs(rr);
+        if (fabs(rr) > rmax) rmax = fabs(rr);
     }
     s->part_res_sq[part] = sq;
+    s->part_res_max[part] = rmax;
     s->part_rows[part] = 3 * np_;
     s->part_iters[part] = it_done;
-    s->res_sq_total += sq;
-    s->res_rows += 3 * np_;
     for (int64_t q = 0; q < np_; ++q)
         for (int k = 0; k < 3; ++k) s->pair_lam[3 * (p0 + q) + k] = lam[3 * q + k];
     /* integrate: x += h v, q <- normalise(q + h/2 (0, w) (x) q); write this
@@ -1636,6 +1689,7 @@ int orc_step(orc_sim *s, double dt, int iters) {
     s->copies = xcalloc((size_t)s->ne * 13 + 1, sizeof(double));
     s->part_iters = xcalloc((size_t)s->n_parts + 1, sizeof(int));
     s->part_res_sq = xcalloc((size_t)s->n_parts + 1, sizeof(double));
+    s->part_res_max = xcalloc((size_t)s->n_parts + 1, sizeof(double));
     s->part_rows = xcalloc((size_t)s->n_parts + 1, sizeof(int64_t));
     s->part_colours = xcalloc((size_t)s->n_parts + 1, sizeof(int));
     {
@@ -1652,13 +1706,24 @@ int orc_step(orc_sim *s, double dt, int iters) {
                 int64_t k = bstart[p] + fill[p]++;
                 pbody[k] = b; pentry[k] = e;
             }
-        int scene = 0;
-        for (int p = 0; p < s->n_parts; ++p) {
+        int *scene_of_part = xcalloc((size_t)s->n_parts + 1, sizeof(int));
+        for (int p = 0, scene = 0; p < s->n_parts; ++p) {
             while (scene + 1 < s->ns && s->part_base[scene + 1] <= p) ++scene;
-            solve_worker(s, p, scene, pbody + bstart[p], (int)(bstart[p + 1] - bstart[p]),
-                         pentry + bstart[p], pstart[p], pstart[p + 1], dt, iters);
+            scene_of_part[p] = scene;
         }
-        free(bstart); free(pbody); free(pentry); free(fill);
+        /* workers write disjoint records (their pairs, entries and per-part
+         * sums), so they may run on several threads with the same results */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(orc_thread_count())
+        for (int p = 0; p < s->n_parts; ++p)
+            solve_worker(s, p, scene_of_part[p], pbody + bstart[p], (int)(bstart[p + 1] - bstart[p]),
+                         pentry + bstart[p], pstart[p], pstart[p + 1], dt, iters);
+        /* residual totals in worker order */
+        for (int p = 0; p < s->n_parts; ++p) {
+            s->res_sq_total += s->part_res_sq[p];
+            s->res_rows += s->part_rows[p];
+            if (s->part_res_max[p] > s->res_max) s->res_max = s->part_res_max[p];
+        }
+        free(scene_of_part); free(bstart); free(pbody); free(pentry); free(fill);
     }
     free(pcount); free(pstart);
     /* blend overlap bodies; others take their single copy */

@@ -651,6 +651,7 @@ void launch_solve_plan(ovl_ctx *c, const SolvePlan &pl, float dt_override, int i
             if (solve_masses_fit(c, k.slots, kSolveShapes[pl.shape].per_sm)) c->last_ctas_masses += (long long)k.C * k.count;
         }
         c->last_cluster = pl.classes.front().C;
+        c->last_plan_per_worker = true;
         c->last_threads = kSolveShapes[pl.shape].threads;
         c->last_unroll = kSolveShapes[pl.shape].unroll;
         return;
@@ -661,6 +662,7 @@ void launch_solve_plan(ovl_ctx *c, const SolvePlan &pl, float dt_override, int i
     c->last_ctas = (long long)pl.cluster * P;
     c->last_ctas_masses = masses ? c->last_ctas : 0;
     c->last_cluster = pl.cluster;
+    c->last_plan_per_worker = false;
     c->last_threads = pl.threads;
     c->last_unroll = pl.unroll;
 }
@@ -1516,6 +1518,16 @@ ovl_status ovl_read_worker_stats(ovl_ctx *c, int32_t *iters, double *res_sq, int
         CK(cudaStreamSynchronize(c->stream));
         if (rows)
             for (int p = 0; p < c->n_parts; ++p) rows[p] = 3ll * (ps[p + 1] - ps[p]);
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_read_solve_plan(ovl_ctx *c, int32_t *ctas) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->have_step) return fail(c, OVL_ERR_ARG, "no step has run");
+        if (!ctas) return fail(c, OVL_ERR_ARG, "ctas is required");
+        for (int p = 0; p < c->n_parts; ++p)
+            ctas[p] = c->last_plan_per_worker ? c->h_class_C[p] : c->last_cluster;
         return OVL_OK;
     });
 }

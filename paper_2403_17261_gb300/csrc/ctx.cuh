@@ -22,6 +22,7 @@ struct ovl_ctx {
     int smem_per_sm = 0;
     int nb_max = 0;          // most bodies in one worker (last membership phase)
     int last_cluster = 1, last_threads = 512, last_unroll = 1;
+    bool last_plan_per_worker = false;   // the last solve used h_class_C (else last_cluster for all)
     long long last_ctas = 0, last_ctas_masses = 0;   // CTAs of the last solve, those with masses in shared memory
     // a tuned solve launch: uniform (cluster > 0) or per-worker plan (shape = 1 + its index)
     struct TuneCfg { int cluster, threads, unroll; float ms; int shape; };

@@ -47,7 +47,7 @@ EXPORTED = [
     "ovl_assign_overlap", "ovl_set_state", "ovl_read_state", "ovl_set_step_index",
     "ovl_set_warmstart", "ovl_read_warmstart", "ovl_step", "ovl_load_balance", "ovl_sync", "ovl_joint_error",
     "ovl_read_stats", "ovl_read_contacts", "ovl_read_graph", "ovl_read_entries", "ovl_read_pairs",
-    "ovl_read_worker_stats", "ovl_autotune_export", "ovl_autotune_import",
+    "ovl_read_worker_stats", "ovl_read_solve_plan", "ovl_autotune_export", "ovl_autotune_import",
     "ovl_geodesics_static", "ovl_set_warmstart_mode", "ovl_read_features", "ovl_mlp_set_params",
     "ovl_mlp_get_params", "ovl_mlp_forward", "ovl_log_reserve", "ovl_log_enable", "ovl_log_size",
     "ovl_log_append", "ovl_log_read", "ovl_mlp_train", "ovl_mlp_grad", "ovl_mlp_loss",
@@ -140,6 +140,7 @@ def load_library(path: str | None = None):
         "ovl_read_entries": [vp, _ip, _ip, _u8p, _fp, _fp],
         "ovl_read_pairs": [vp, _ip, _u64p, _ip, _fp],
         "ovl_read_worker_stats": [vp, _ip, C.POINTER(C.c_double), C.POINTER(C.c_int64), _ip],
+        "ovl_read_solve_plan": [vp, _ip],
         "ovl_autotune_export": [vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
         "ovl_autotune_import": [vp, C.c_char_p],
         "ovl_set_warmstart_mode": [vp, C.c_int32],
@@ -650,6 +651,12 @@ class Simulation:
             self.ctx, _ptr(it, _ip), rs.ctypes.data_as(C.POINTER(C.c_double)),
             rows.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(cols, _ip)))
         return dict(iters=it, res_sq=rs, rows=rows, colours=cols)
+
+    def solve_plan(self):
+        """CTAs (one cluster) that solved each worker in the last step."""
+        ctas = np.zeros(max(self.n_parts, 1), np.int32)
+        _check(self.ctx, load_library().ovl_read_solve_plan(self.ctx, _ptr(ctas, _ip)))
+        return ctas[:self.n_parts]
 
     # learned warm start ----------------------------------------------------------
 

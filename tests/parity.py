@@ -8,15 +8,20 @@ then takes one step on both and checks every record element by element.
 
 Tolerances (FP32 kernel vs FP64 oracle from identical inputs):
   integers (contacts, graph, masks, entries, D, pair order, colours): exact
-  velocities, angular velocities:   1e-4 m/s (rad/s) + 1e-5 x the step's largest speed
-                                    (the absolute part is the method's target; the relative
-                                    part, ~170 FP32 unit roundoffs, covers FP32 accumulation
-                                    over the sweeps of fast, deeply penetrating stress scenes)
+  velocities, angular velocities:   1e-4 m/s (rad/s), the method's stated bound
   positions:                        1e-5 m
   quaternions:                      1e-5
   contact gap, normal, tangent:     1e-5
   weights:                          1e-6
   impulses:                         the velocity bound x max(1, body mass) (Delta v = Delta lambda / m)
+
+Random stress piles (``stress=True``: spheres dropped into overlapping
+random positions, so that they meet at up to ~18 m/s with deep penetration)
+add 1e-5 x the step's largest speed to the velocity bound: about 170 FP32
+unit roundoffs of that speed, which FP32 accumulation over the sweeps of such
+impacts can reach.  Every configuration of the method's workloads (the small
+pile, the chain, the large pile and the batch) is held to the plain bound.
+"""
 """
 from __future__ import annotations
 
@@ -33,26 +38,30 @@ TOL_GEOM = 1e-5
 TOL_W = 1e-6
 
 
+def load_identical(orc, gpu):
+    """Rounds the oracle's current state and warm-start impulses to FP32 once
+    and loads the same rounded values, masks and step index into both sides."""
+    st32 = orc.state().astype(np.float32)
+    part, key, lam = orc.warmstart()
+    lam32 = lam.astype(np.float32)
+    orc.set_state(st32.astype(np.float64))
+    orc.set_warmstart(part, key, lam32.astype(np.float64))
+    gpu.set_membership(orc.masks())
+    gpu.set_state(st32)
+    gpu.set_warmstart(part, key, lam32)
+    gpu.set_step_index(orc.step_index())
+
+
 def prepare(scene, warm_steps: int = 0, params: dict | None = None, gpu_params: dict | None = None):
     orc = O.OracleSim(scene, params)
     if scene.assign_overlap:
         orc.assign_overlap()
     for _ in range(warm_steps):
         orc.step()
-    st32 = orc.state().astype(np.float32)
-    part, key, lam = orc.warmstart()
-    lam32 = lam.astype(np.float32)
-    masks = orc.masks()
-    k = orc.step_index()
-    orc.set_state(st32.astype(np.float64))
-    orc.set_warmstart(part, key, lam32.astype(np.float64))
     gp = dict(params or {})
     gp.update(gpu_params or {})
     gpu = ovl.Simulation(scene, gp, partition=False)
-    gpu.set_membership(masks)
-    gpu.set_state(st32)
-    gpu.set_warmstart(part, key, lam32)
-    gpu.set_step_index(k)
+    load_identical(orc, gpu)
     return orc, gpu
 
 
@@ -72,7 +81,8 @@ def _qdist(qa, qb):
     return float(np.minimum(d1, d2).max())
 
 
-def compare_step(orc, gpu, dt: float = 0.0, iters: int | None = None, check_lambda: bool = True):
+def compare_step(orc, gpu, dt: float = 0.0, iters: int | None = None, check_lambda: bool = True,
+                 stress: bool = False):
     """One step on both sides; asserts parity of every record; returns a report."""
     orc.step(dt, iters)
     gpu.step(dt, iters)
@@ -112,7 +122,7 @@ def compare_step(orc, gpu, dt: float = 0.0, iters: int | None = None, check_lamb
     assert np.array_equal(po["colour"], pg["colour"]), "colours differ"
     so, sg = orc.state(), gpu.state()
     vmax = float(np.abs(so[:, 7:13]).max()) if so.size else 0.0
-    tol_v = TOL_V + TOL_V_REL * vmax
+    tol_v = TOL_V + (TOL_V_REL * vmax if stress else 0.0)
     rep["tol_v"] = tol_v
     mmax = float(np.max(1.0 / sc.inv_mass[sc.inv_mass > 0])) if np.any(sc.inv_mass > 0) else 1.0
     rep["lambda"] = _maxabs(po["lam"], pg["lam"])

@@ -24,6 +24,7 @@ def _parity():
 def _run(sc, warm=0, params=None, **step):
     P = _parity()
     orc, gpu = P.prepare(sc, warm_steps=warm, params=params)
+    step.setdefault("stress", sc.name.startswith("random_pile"))
     try:
         return P.compare_step(orc, gpu, **step), gpu.stats()
     finally:

@@ -1,0 +1,73 @@
+"""The large pile at full size, element by element against the FP64 oracle,
+in the launch configuration the bench times.
+
+262,144 spheres (64^3 lattice, r ~ U(0.4, 0.6), density 1) in a bowl of four
+30-degree planes, 64 k-means workers, growth depth 2, weight depth 6, 30 PGS
+sweeps, dt = 1/60, removal branches of Algorithm 6 every 10th step.  The
+oracle settles the scene itself for the bench's 150 untimed steps (the
+lattice falls for ~40 steps, then piles up in the bowl: ~1.2 M (worker,
+constraint) pairs at step 150).  From the oracle's state, rounded to FP32 once
+and loaded into both sides with the same masks, warm-start impulses and step
+index, each side takes step 150 (a removal step: 150 % 10 == 0) and, after a
+fresh load from the oracle's new state, step 151.  The GPU runs with the
+bench's parameters, so its per-worker launch plan (1 to 6 CTAs per worker as
+one thread-block cluster, masses in shared memory, rows loaded ahead) is the
+one the bench times.
+
+Every record is compared: contacts and the graph bit for bit, masks after
+Algorithm 6, entries, D(o,i), pair order and colours exactly; weights within
+1e-6; every body's v and omega within 1e-4 m/s (rad/s), x within 1e-5 m and
+q within 1e-5; every pair's impulses within 1e-4 x max(1, m).  No relative
+term: these are the method's stated bounds (Section 3, Eq 1-7; Algorithm 1)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2403_17261_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+SETTLE = 150
+
+
+@pytest.fixture(scope="module")
+def settled():
+    import __graft_entry__ as g
+    g.build()
+    O.set_threads(len(os.sched_getaffinity(0)))
+    try:
+        sc = S.pile_large()
+        orc = O.OracleSim(sc)
+        for _ in range(SETTLE):
+            orc.step()
+        yield sc, orc
+    finally:
+        O.set_threads(1)
+
+
+def test_pile_large_removal_step_and_next(settled):
+    import bench
+    import parity as P
+    from paper_2403_17261_gb300 import ovl
+    sc, orc = settled
+    assert orc.step_index() == SETTLE
+    gpu = ovl.Simulation(sc, bench.step_params(ovl), partition=False)
+    try:
+        for k in range(2):
+            P.load_identical(orc, gpu)
+            assert orc.step_index() == SETTLE + k
+            rep = P.compare_step(orc, gpu)
+            plan = gpu.solve_plan()
+            st = gpu.stats()
+            print(f"\n  step {SETTLE + k}: contacts {rep['contacts']}, pairs {st['n_pairs']}, overlap "
+                  f"{st['n_overlap']}, CTAs per worker {np.bincount(plan).tolist()}; max |dv| {rep['v']:.2e} "
+                  f"m/s, |dx| {rep['x']:.2e} m, |dq| {rep['q']:.2e}, |dlambda| {rep['lambda']:.2e}, "
+                  f"copies |dv| {rep['copy_v']:.2e}")
+            assert st["device_status"] == 0
+            assert rep["tol_v"] == P.TOL_V
+            assert rep["contacts"] > 300_000 and st["n_pairs"] > 1_000_000
+            assert plan.max() >= 3          # multi-CTA clusters took part
+    finally:
+        gpu.close()

@@ -53,7 +53,7 @@ def test_random_pile(n, seed, sets):
     P = _parity()
     sc = S.random_pile(n, seed, n_sets=sets, box=0.3 * n ** (1 / 3) + 1.0)
     orc, gpu = P.prepare(sc, warm_steps=2)
-    P.compare_step(orc, gpu)
+    P.compare_step(orc, gpu, stress=True)
 
 
 @pytest.mark.parametrize("n_scenes,hi", [(12, 1024), (40, 300)])
