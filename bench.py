@@ -46,18 +46,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 L2_BYTES = 129 * 1024 * 1024
-CONTACT_ROW_BYTES = 80   # per constraint per sweep: 56 B record (2 slots, n, t1, k_n, k_t, r_a, r_b, target, mu) + 12 B lambda read + 12 B lambda write
+CONTACT_ROW_BYTES = 84   # per contact per sweep: 60 B read (2 ids, n, t1, lever scalars, k_n, k_t1, k_t2, target, mu) + 12 B lambda read + 12 B lambda write
 JOINT_ROW_BYTES = 80     # per joint per sweep: 56 B record (2 slots, r_A, r_B, k[3], target[3]) + 24 B lambda r/w
 ENTRY_BYTES = 120        # per (body, worker) per step: 60 B state + params read, 52 B copy write, 8 B index
 PAIR_ONCE_BYTES = 24     # per constraint per step: warm-start lambda read + final lambda write
 BLEND_ENTRY_BYTES = 53   # per (body, worker) entry: its 52 B copy read + D(o,i) 1 B
 BLEND_BODY_BYTES = 64    # per body: 52 B blended state written + 12 B of the start position read
-# DRAM bytes of the solve over its algorithmic bytes, from the ncu capture
-# summarised in profiles/k_solve_pile_large.md (every solver launch of the two
-# timed steps: 0.294 GB of DRAM traffic for 7.52 GB of algorithmic bytes; the
-# row records stay in L2 across sweeps).  Valid for the captured kernel only:
-# set to None when k_solve changes, until it is captured again.
-SOLVE_DRAM_PER_ALGORITHMIC_BYTE = 0.039
+# DRAM bytes (read + write) of every solver launch of one timed step of the
+# large pile, from one ncu capture of this file's default command; None until
+# a capture matches the current kernel and the timed steps' pair counts.
+SOLVE_DRAM_BYTES_PER_STEP = None
 
 
 def parse():
@@ -78,6 +76,8 @@ def parse():
                     help="load Algorithm 6 compares: active bodies (the paper's) or 1 + contacts per body")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-late-window", dest="late_window", action="store_false",
+                    help="skip timing the configuration's last --steps steps")
     return ap.parse_args()
 
 
@@ -186,10 +186,20 @@ class ClockSampler:
 # CPU arm: the FP64 oracle, as it stands, on a bounded sample of the workload
 # ---------------------------------------------------------------------------
 
-def oracle_sample_scene(workload):
+def host_cores() -> int:
+    """Host cores this process may run on (its affinity set)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample_scene(workload, scene=None):
+    """The scene the oracle times, its untimed settle, and a description.  The
+    large pile is the benched configuration itself (the oracle settles it)."""
     from paper_2403_17261_gb300 import scenes as S
     if workload in ("pile_large", "warmstart"):
-        return S.pile_large(side=16, n_sets=16), 150, "pile_large generator at 16^3 = 4096 bodies, 16 k-means workers, settled 150 steps by the oracle itself (untimed)"
+        return (S.pile_large() if scene is None else scene), 150, "the full pile_large configuration (262,144 spheres, 64 workers), settled 150 steps by the oracle itself (untimed)"
     if workload == "pile_mixed":
         return S.pile_mixed(side=16, layers=8, n_sets=16), 150, "pile_mixed generator at 16 x 16 x 8 small + 98 big spheres, 16 k-means workers, settled 150 steps by the oracle itself (untimed)"
     if workload == "chain":
@@ -199,42 +209,66 @@ def oracle_sample_scene(workload):
     return S.pile_small(), 0, "the full 256-sphere pile"
 
 
-def oracle_run(workload, steps, warmup, max_seconds=None, params=None):
+def oracle_run(workload, steps, warmup, max_seconds=None, params=None, threads=None, single_core_steps=0,
+               scene=None):
+    """Times the FP64 oracle as it stands on `threads` host threads (default:
+    every core of this process), after its own untimed settle.  With
+    single_core_steps > 0 the same state is also stepped that many times on
+    one thread (the oracle as written, single-threaded)."""
     from oracle import oracle as O
-    sc, settle, desc = oracle_sample_scene(workload)
-    sim = O.OracleSim(sc, params)
-    if sc.assign_overlap:
-        sim.assign_overlap()
-    for _ in range(settle):
-        sim.step()
-    for _ in range(warmup):
-        sim.step()
-    t_total, body_steps, row_iters, done = 0.0, 0, 0, 0
-    for k in range(steps):
-        t0 = time.perf_counter()
-        sim.step()
-        t_total += time.perf_counter() - t0
-        body_steps += sc.n_bodies
-        row_iters += 3 * sim.counts()["pairs"] * sc.iters
-        done += 1
-        if max_seconds is not None and t_total > max_seconds:
-            break
-    return {"value": body_steps / t_total, "row_iters_per_s": row_iters / t_total, "steps": done,
-            "seconds": t_total, "sample": desc + f"; {done} timed steps after {warmup} warm-up",
-            "cores": 1}
+    threads = host_cores() if threads is None else threads
+    sc, settle, desc = oracle_sample_scene(workload, scene)
+    O.set_threads(threads)
+    try:
+        sim = O.OracleSim(sc, params)
+        if sc.assign_overlap:
+            sim.assign_overlap()
+        for _ in range(settle + warmup):
+            sim.step()
+        snap = (sim.state(), sim.masks(), sim.warmstart(), sim.step_index())
+        t_total, body_steps, row_iters, done = 0.0, 0, 0, 0
+        for k in range(steps):
+            t0 = time.perf_counter()
+            sim.step()
+            t_total += time.perf_counter() - t0
+            body_steps += sc.n_bodies
+            row_iters += 3 * sim.counts()["pairs"] * sc.iters
+            done += 1
+            if max_seconds is not None and t_total > max_seconds:
+                break
+        out = {"value": body_steps / t_total, "row_iters_per_s": row_iters / t_total, "steps": done,
+               "seconds": t_total, "cores": threads,
+               "sample": desc + f"; steps {snap[3]}..{snap[3] + done - 1} timed after {warmup} warm-up step(s)"}
+        if single_core_steps > 0:
+            O.set_threads(1)
+            sim.set_state(snap[0])
+            sim.set_masks(snap[1])
+            sim.set_warmstart(*snap[2])
+            sim.set_step_index(snap[3])
+            t1 = 0.0
+            for _ in range(single_core_steps):
+                t0 = time.perf_counter()
+                sim.step()
+                t1 += time.perf_counter() - t0
+            out["single_core"] = {"value": sc.n_bodies * single_core_steps / t1, "unit": "body-steps/s",
+                                  "cores": 1, "steps": single_core_steps,
+                                  "sample": f"the same state, steps {snap[3]}..{snap[3] + single_core_steps - 1}"}
+        return out
+    finally:
+        O.set_threads(1)
 
 
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    r = oracle_run(args.workload, args.steps, args.warmup, max_seconds=240.0,
+    r = oracle_run(args.workload, args.steps, args.warmup, max_seconds=150.0,
                    params=dict(lb_load=1 if args.lb_load == "contacts" else 0))
     line = {
         "impl": "reference", "metric": "body-steps/s", "value": r["value"], "unit": "body-steps/s",
         "n_gpus": args.gpus, "steps": r["steps"], "warmup": args.warmup,
         "ms_per_step": 1e3 * r["seconds"] / max(r["steps"], 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": r["sample"]},
+        "config": {"workload": args.workload, "sample": r["sample"], "host_threads": r["cores"]},
         "cpu_baseline": {"value": r["value"], "unit": "body-steps/s", "cores": r["cores"], "kind": "oracle",
                          "sample": r["sample"]},
         "e2e": {"value": r["value"], "unit": "body-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -279,37 +313,48 @@ def gpu_arm(args, rank, world, local_rank):
     # the end-to-end run below replays the same steps from this snapshot
     snapshot = None if args.no_e2e else (sim.state(), sim.membership(), sim.warmstart(),
                                          sim.step_index_value())
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    solve_ms, rows_iters, bytes_solve, launches, imbalance = [], 0, 0.0, [], []
-    blend_ms, bytes_blend = [], 0.0
-    barrier()
-    torch.cuda.nvtx.range_push("timed")
-    with ClockSampler(local_rank) as clk:
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(k))          # L2 flush, outside the timed interval
-                starts[k].record(stream)
-            sim.step()
-            with torch.cuda.stream(stream):
-                ends[k].record(stream)
-            st = sim.stats()
-            rows_w = sim.worker_stats()["rows"]
-            imbalance.append(float(rows_w.max() / max(rows_w.mean(), 1e-9)))
-            solve_ms.append(st["phase_ms"]["solve"])
-            launches.append(st["n_launches"])
-            n_cons = st["n_pairs"]
-            rows_iters += st["n_rows"] * sc.iters
-            bytes_solve += (sc.iters * CONTACT_ROW_BYTES * n_cons + PAIR_ONCE_BYTES * n_cons
-                            + ENTRY_BYTES * st["n_entries"])
-            blend_ms.append(st["phase_ms"].get("blend", 0.0))
-            bytes_blend += BLEND_ENTRY_BYTES * st["n_entries"] + BLEND_BODY_BYTES * sc.n_bodies
+    def time_window(k_steps):
+        """k_steps timed steps (L2 flushed before each, outside its interval)."""
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(k_steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(k_steps)]
+        w = dict(solve_ms=[], rows_iters=0, bytes_solve=0.0, launches=[], imbalance=[], blend_ms=[],
+                 bytes_blend=0.0, first_step=sim.step_index_value(), pairs=[])
         barrier()
+        with ClockSampler(local_rank) as clk:
+            for k in range(k_steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(float(k))          # L2 flush, outside the timed interval
+                    starts[k].record(stream)
+                sim.step()
+                with torch.cuda.stream(stream):
+                    ends[k].record(stream)
+                st = sim.stats()
+                rows_w = sim.worker_stats()["rows"]
+                w["imbalance"].append(float(rows_w.max() / max(rows_w.mean(), 1e-9)))
+                w["solve_ms"].append(st["phase_ms"]["solve"])
+                w["launches"].append(st["n_launches"])
+                n_cons = st["n_pairs"]
+                w["pairs"].append(n_cons)
+                w["rows_iters"] += st["n_rows"] * sc.iters
+                w["bytes_solve"] += (sc.iters * CONTACT_ROW_BYTES * n_cons + PAIR_ONCE_BYTES * n_cons
+                                     + ENTRY_BYTES * st["n_entries"])
+                w["blend_ms"].append(st["phase_ms"].get("blend", 0.0))
+                w["bytes_blend"] += BLEND_ENTRY_BYTES * st["n_entries"] + BLEND_BODY_BYTES * sc.n_bodies
+            barrier()
+        w["step_ms"] = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        w["clocks"] = clk.summary()
+        w["plan"] = np.bincount(sim.solve_plan()).tolist()
+        return w
+
+    torch.cuda.nvtx.range_push("timed")
+    win = time_window(args.steps)
     torch.cuda.nvtx.range_pop()
     free_b, total_b = torch.cuda.mem_get_info()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_max = max_over_ranks(sum(step_ms) / 1e3, world)
+    t_max = max_over_ranks(sum(win["step_ms"]) / 1e3, world)
     value = whole_job_rate(world, sc.n_bodies, args.steps, t_max)
+    solve_ms, launches, imbalance = win["solve_ms"], win["launches"], win["imbalance"]
+    rows_iters, bytes_solve = win["rows_iters"], win["bytes_solve"]
+    blend_ms, bytes_blend = win["blend_ms"], win["bytes_blend"]
     solve_s = sum(solve_ms) / 1e3
     last = sim.stats()
 
@@ -340,17 +385,37 @@ def gpu_arm(args, rank, world, local_rank):
         e2e = {"value": whole_job_rate(world, sc.n_bodies, n_e2e, te), "unit": "body-steps/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": n_e2e}
 
+    # the config's last steps (the overlap has grown under Algorithm 6 by then)
+    late = None
+    if args.late_window and sc.steps > sim.step_index_value() + args.steps:
+        while sim.step_index_value() < sc.steps - args.steps:
+            sim.step()
+        lw = time_window(args.steps)
+        t_late = max_over_ranks(sum(lw["step_ms"]) / 1e3, world)
+        late_solve_s = sum(lw["solve_ms"]) / 1e3
+        late = {"value": whole_job_rate(world, sc.n_bodies, args.steps, t_late), "unit": "body-steps/s",
+                "steps": f"{lw['first_step']}..{lw['first_step'] + args.steps - 1} of {sc.steps}",
+                "ms_per_step": 1e3 * t_late / args.steps, "solve_ms_mean": 1e3 * late_solve_s / args.steps,
+                "pairs_mean": float(np.mean(lw["pairs"])),
+                "solve_effective_gbs": lw["bytes_solve"] / late_solve_s / 1e9,
+                "row_iters_per_s": lw["rows_iters"] / late_solve_s,
+                "worker_rows_max_over_mean": float(np.mean(lw["imbalance"])),
+                "ctas_per_worker_histogram": lw["plan"], "clocks": lw["clocks"]}
+
     if rank != 0:
         return
     peak, peak_kind = measured_peaks()
     achieved = bytes_solve / solve_s / 1e9
-    profile_traffic = (SOLVE_DRAM_PER_ALGORITHMIC_BYTE * bytes_solve / args.steps
-                       if SOLVE_DRAM_PER_ALGORITHMIC_BYTE is not None and args.workload == "pile_large" else None)
+    if late is not None:
+        late["solve_frac_of_peak"] = late["solve_effective_gbs"] / peak
+    profile_traffic = SOLVE_DRAM_BYTES_PER_STEP if args.workload == "pile_large" else None
     cpu = None
     if not args.no_cpu_baseline:
-        r = oracle_run(args.workload, steps=80, warmup=1, max_seconds=15.0, params=dict(lb_load=lb_load))
+        r = oracle_run(args.workload, steps=5, warmup=args.warmup, max_seconds=20.0, params=dict(lb_load=lb_load),
+                       single_core_steps=1, scene=sc if args.workload == "pile_large" else None)
         cpu = {"value": r["value"], "unit": "body-steps/s", "cores": r["cores"], "kind": "oracle",
-               "sample": r["sample"]}
+               "sample": r["sample"], "threads": "workers, bodies and geodesic searches split over the cores",
+               "single_core": r.get("single_core")}
     line = {
         "metric": "body-steps/s", "value": value, "unit": "body-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
@@ -368,6 +433,10 @@ def gpu_arm(args, rank, world, local_rank):
         "phase_ms_last_step": {k: round(v, 4) for k, v in last["phase_ms"].items()},
         "roofline": {"bound": "hbm", "kernel": "k_solve", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": profile_traffic,
+                     "achieved_is": "effective: algorithmic bytes (84 B per contact per sweep, 24 B per pair, "
+                                    "120 B per entry) / solve time",
+                     "dram_frac": (profile_traffic / (solve_s / args.steps) / 1e9 / peak
+                                   if profile_traffic else None),
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_solve / args.steps,
                      "avg_launch_ms": 1e3 * solve_s / args.steps},
@@ -376,7 +445,9 @@ def gpu_arm(args, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": int(sum(launches)),
         "device_memory_used_gb": round((total_b - free_b) / 1e9, 3),
-        "clocks": clk.summary(),
+        "clocks": win["clocks"],
+        "ctas_per_worker_histogram": win["plan"],
+        "late_window": late,
     }
     print(json.dumps(line), flush=True)
 

@@ -22,7 +22,6 @@ unit roundoffs of that speed, which FP32 accumulation over the sweeps of such
 impacts can reach.  Every configuration of the method's workloads (the small
 pile, the chain, the large pile and the batch) is held to the plain bound.
 """
-"""
 from __future__ import annotations
 
 import numpy as np
