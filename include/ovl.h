@@ -387,6 +387,33 @@ ovl_status ovl_read_pairs(ovl_ctx *ctx, int32_t *part, uint64_t *key, int32_t *c
 ovl_status ovl_autotune_export(ovl_ctx *ctx, char *buf, size_t cap, size_t *len);
 ovl_status ovl_autotune_import(ovl_ctx *ctx, const char *json);
 
+/* nsteps timesteps, as nsteps calls of ovl_step with the same dt and iters
+ * (Algorithm 1's loop over t).  Each step reads a few counts back to size its
+ * buffers and runs Algorithm 6 on the host, so the steps are issued one after
+ * another from the host, not captured as one graph.  *done (optional)
+ * receives the number of steps completed; the first failing step's status is
+ * returned and the state is that of the last completed step. */
+ovl_status ovl_step_n(ovl_ctx *ctx, float dt, int32_t iters, int32_t nsteps, int32_t *done);
+
+/* Checkpoint of what a step reads (the paper's get/reset of a worker's state,
+ * Section 4 and Table 1, for the whole simulation): the blended body state,
+ * every mask W_b, the warm-start cache, the step index (Algorithm 6's
+ * removal cadence), the warm-start mode, the network parameters with Adam's
+ * moments (when set) and the autotuner's table.  Scene arrays are not in it.
+ *
+ * ovl_save: *len receives the checkpoint's size in bytes; with buf != NULL
+ *   and cap >= *len the checkpoint is written to buf (host memory, caller-
+ *   owned), else OVL_ERR_CAPACITY.  buf = NULL asks only for the size.
+ *   Synchronises the context's stream.
+ * ovl_load: restores a checkpoint into a context whose uploaded scene is the
+ *   one it was saved from (same sizes and the same host arrays, checked by a
+ *   hash; OVL_ERR_ARG otherwise, or when the bytes are not a checkpoint of
+ *   this version).  Continuing from a load computes the same bits as
+ *   continuing the saved run.  Records of the last step (ovl_read_contacts
+ *   and the other per-step reads) are unavailable until the next step. */
+ovl_status ovl_save(ovl_ctx *ctx, void *buf, size_t cap, size_t *len);
+ovl_status ovl_load(ovl_ctx *ctx, const void *buf, size_t len);
+
 /* Per worker: sweeps run, residual sum of squares, rows, colours. */
 ovl_status ovl_read_worker_stats(ovl_ctx *ctx, int32_t *iters, double *res_sq, int64_t *rows,
                                  int32_t *colours);

@@ -22,6 +22,9 @@ SRC = os.path.join(HERE, "ovl_oracle.c")
 BOX_SRC = os.path.join(HERE, "box_oracle.c")   # box contact decisions the step takes in FP32
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libovl_oracle.so")
+# the same source with FP32 sweeps (-DORC_REAL=float): the precision floor of
+# the algorithm itself, for comparisons only
+LIB_PATH_F32 = os.path.join(BUILD_DIR, "libovl_oracle_f32sweeps.so")
 
 DEFAULT_PARAMS = dict(gravity=(0.0, 0.0, -9.81), margin=0.05, erp=0.2, slop=0.001, warmstart=1.0,
                       lb_activate=1, lb_deact_every=1, res_tol=0.0, res_check_every=0, lb_load=0,
@@ -36,27 +39,44 @@ class OrcParams(C.Structure):
                 ("weights", C.c_int)]
 
 
-def build(force: bool = False) -> str:
+def _build_one(path: str, defines: list[str], force: bool) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
-    if (force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < os.path.getmtime(SRC)
-            or os.path.getmtime(LIB_PATH) < os.path.getmtime(BOX_SRC)):
-        tmp = LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-std=c11", "-shared", "-fPIC",
-                               "-o", tmp, SRC, BOX_SRC, "-lm"])
-        os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    if (force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(SRC)
+            or os.path.getmtime(path) < os.path.getmtime(BOX_SRC)):
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-std=c11", "-shared", "-fPIC"]
+                              + defines + ["-o", tmp, SRC, BOX_SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    _build_one(LIB_PATH_F32, ["-DORC_REAL=float"], force)
+    return _build_one(LIB_PATH, [], force)
 
 
 _lib = None
+_lib_f32 = None
 
 P = C.POINTER
 dp, ip, i64p, u64p, u8p = P(C.c_double), P(C.c_int), P(C.c_int64), P(C.c_uint64), P(C.c_uint8)
 
 
-def lib():
-    global _lib
+def lib(sweeps: str = "f64"):
+    """The oracle library; sweeps="f32" gives the FP32-sweep build."""
+    global _lib, _lib_f32
+    if sweeps == "f32":
+        if _lib_f32 is None:
+            build()
+            _lib_f32 = _declare(C.CDLL(LIB_PATH_F32))
+        return _lib_f32
     if _lib is None:
-        L = C.CDLL(build())
+        _lib = _declare(C.CDLL(build()))
+    return _lib
+
+
+def _declare(L):
+    if True:
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [P(OrcParams), C.c_int, dp, dp, dp, C.c_int, dp, ip, C.c_int, ip, dp,
                                  C.c_int, ip, dp, dp, ip, ip, ip, ip]
@@ -110,8 +130,7 @@ def lib():
         L.orc_get_threads.restype = C.c_int
         L.orc_mix64.restype = C.c_uint64
         L.orc_mix64.argtypes = [C.c_uint64]
-        _lib = L
-    return _lib
+    return L
 
 
 def _ptr(a, t):
@@ -269,9 +288,11 @@ def mix64(x: int) -> int:
 # ---------------------------------------------------------------------------
 
 class OracleSim:
-    """FP64 simulation of a scene; ``step`` runs one timestep of Algorithm 1."""
+    """FP64 simulation of a scene; ``step`` runs one timestep of Algorithm 1.
+    sweeps="f32": the same algorithm with its PGS sweeps in FP32 (the
+    precision floor of the method's own arithmetic, for comparisons)."""
 
-    def __init__(self, scene, params: dict | None = None):
+    def __init__(self, scene, params: dict | None = None, sweeps: str = "f64"):
         p = dict(DEFAULT_PARAMS)
         p["lb_activate"] = scene.lb_activate
         p["lb_deact_every"] = scene.lb_deact_every
@@ -296,7 +317,7 @@ class OracleSim:
                       _f64(scene.scene_dt), _i32(scene.scene_flags), _i32(scene.scene_gamma),
                       _i32(scene.scene_beta), _i32(scene.n_sets)]
         k = self._keep
-        L = lib()
+        self._L = L = lib(sweeps)
         self._h = L.orc_create(C.byref(cp), self.n, _ptr(k[0], dp), _ptr(k[1], dp), _ptr(k[2], dp),
                                scene.planes.shape[0], _ptr(k[3], dp), _ptr(k[4], ip),
                                scene.joints.shape[0], _ptr(k[5], ip), _ptr(k[6], dp),
@@ -313,61 +334,61 @@ class OracleSim:
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h:
-            lib().orc_destroy(h)
+        if h and getattr(self, "_L", None) is not None:
+            self._L.orc_destroy(h)
             self._h = None
 
     # setup / state -----------------------------------------------------------
     def assign_overlap(self):
-        lib().orc_assign(self._h)
+        self._L.orc_assign(self._h)
 
     def set_masks(self, masks):
-        rc = lib().orc_set_masks(self._h, _ptr(_u64(masks), u64p))
+        rc = self._L.orc_set_masks(self._h, _ptr(_u64(masks), u64p))
         if rc != 0:
             raise ValueError(f"invalid membership ({rc})")
 
     def masks(self):
         out = np.zeros(self.n, np.uint64)
-        lib().orc_get_masks(self._h, _ptr(out, u64p))
+        self._L.orc_get_masks(self._h, _ptr(out, u64p))
         return out
 
     def set_state(self, st):
-        lib().orc_set_state(self._h, _ptr(_f64(st).reshape(-1, 13), dp))
+        self._L.orc_set_state(self._h, _ptr(_f64(st).reshape(-1, 13), dp))
 
     def state(self):
         out = np.zeros((self.n, 13), np.float64)
-        lib().orc_get_state(self._h, _ptr(out, dp))
+        self._L.orc_get_state(self._h, _ptr(out, dp))
         return out
 
     def set_step_index(self, k):
-        lib().orc_set_step_index(self._h, int(k))
+        self._L.orc_set_step_index(self._h, int(k))
 
     def step_index(self):
-        return int(lib().orc_get_step_index(self._h))
+        return int(self._L.orc_get_step_index(self._h))
 
     def set_warmstart(self, part, key, lam):
         part, key, lam = _i32(part), _u64(key), _f64(lam).reshape(-1, 3)
-        lib().orc_set_warmstart(self._h, part.shape[0], _ptr(part, ip), _ptr(key, u64p), _ptr(lam, dp))
+        self._L.orc_set_warmstart(self._h, part.shape[0], _ptr(part, ip), _ptr(key, u64p), _ptr(lam, dp))
 
     def warmstart(self):
-        n = lib().orc_warmstart_size(self._h)
+        n = self._L.orc_warmstart_size(self._h)
         part = np.zeros(max(n, 1), np.int32)
         key = np.zeros(max(n, 1), np.uint64)
         lam = np.zeros((max(n, 1), 3), np.float64)
-        lib().orc_get_warmstart(self._h, _ptr(part, ip), _ptr(key, u64p), _ptr(lam, dp))
+        self._L.orc_get_warmstart(self._h, _ptr(part, ip), _ptr(key, u64p), _ptr(lam, dp))
         return part[:n], key[:n], lam[:n]
 
     # stepping ----------------------------------------------------------------
     def step(self, dt: float = 0.0, iters: int | None = None):
         it = self.scene.iters if iters is None else iters
-        rc = lib().orc_step(self._h, float(dt), int(it))
+        rc = self._L.orc_step(self._h, float(dt), int(it))
         if rc != 0:
             raise RuntimeError(f"oracle step failed ({rc})")
 
     # last-step records -------------------------------------------------------
     def counts(self):
         c = np.zeros(5, np.int64)
-        lib().orc_get_counts(self._h, _ptr(c, i64p))
+        self._L.orc_get_counts(self._h, _ptr(c, i64p))
         return dict(contacts=int(c[0]), adjacency=int(c[1]), entries=int(c[2]), pairs=int(c[3]),
                     parts=int(c[4]))
 
@@ -377,7 +398,7 @@ class OracleSim:
         phi = np.zeros(max(m, 1))
         nn = np.zeros((max(m, 1), 3))
         t1 = np.zeros((max(m, 1), 3))
-        lib().orc_get_contacts(self._h, _ptr(ab, ip), _ptr(phi, dp), _ptr(nn, dp), _ptr(t1, dp))
+        self._L.orc_get_contacts(self._h, _ptr(ab, ip), _ptr(phi, dp), _ptr(nn, dp), _ptr(t1, dp))
         return ab[:m], phi[:m], nn[:m], t1[:m]
 
 
@@ -386,13 +407,13 @@ class OracleSim:
         contacts; points are zero for sphere contacts."""
         m = self.counts()["contacts"]
         k, p = np.zeros(m, np.int32), np.zeros((m, 3))
-        lib().orc_get_contact_points(self._h, _ptr(k, ip), _ptr(p, dp))
+        self._L.orc_get_contact_points(self._h, _ptr(k, ip), _ptr(p, dp))
         return k, p
     def graph(self):
         m = self.counts()["adjacency"]
         rp = np.zeros(self.n + 1, np.int32)
         col = np.zeros(max(m, 1), np.int32)
-        lib().orc_get_graph(self._h, _ptr(rp, ip), _ptr(col, ip))
+        self._L.orc_get_graph(self._h, _ptr(rp, ip), _ptr(col, ip))
         return rp, col[:m]
 
     def entries(self):
@@ -402,7 +423,7 @@ class OracleSim:
         D = np.zeros(max(ne, 1), np.uint8)
         w = np.zeros(max(ne, 1))
         cp = np.zeros((max(ne, 1), 13))
-        lib().orc_get_entries(self._h, _ptr(ep, i64p), _ptr(part, ip), _ptr(D, u8p), _ptr(w, dp),
+        self._L.orc_get_entries(self._h, _ptr(ep, i64p), _ptr(part, ip), _ptr(D, u8p), _ptr(w, dp),
                               _ptr(cp, dp))
         return dict(entry_ptr=ep, part=part[:ne], D=D[:ne], weight=w[:ne], copies=cp[:ne])
 
@@ -412,7 +433,7 @@ class OracleSim:
         part, kind = np.zeros(mm, np.int32), np.zeros(mm, np.int32)
         cidx, key = np.zeros(mm, np.int64), np.zeros(mm, np.uint64)
         colour_, lam = np.zeros(mm, np.int32), np.zeros((mm, 3))
-        lib().orc_get_pairs(self._h, _ptr(part, ip), _ptr(kind, ip), _ptr(cidx, i64p),
+        self._L.orc_get_pairs(self._h, _ptr(part, ip), _ptr(kind, ip), _ptr(cidx, i64p),
                             _ptr(key, u64p), _ptr(colour_, ip), _ptr(lam, dp))
         return dict(part=part[:m], kind=kind[:m], cidx=cidx[:m], key=key[:m], colour=colour_[:m],
                     lam=lam[:m])
@@ -427,23 +448,23 @@ class OracleSim:
         mm = max(m, 1)
         f, sc, found = np.zeros((mm, 12)), np.zeros(mm), np.zeros(mm, np.int32)
         depth = np.zeros(max(self.n, 1), np.uint8)
-        lib().orc_get_features(self._h, _ptr(f, dp), _ptr(sc, dp), _ptr(found, ip), _ptr(depth, u8p))
+        self._L.orc_get_features(self._h, _ptr(f, dp), _ptr(sc, dp), _ptr(found, ip), _ptr(depth, u8p))
         return dict(feat=f[:m], scale=sc[:m], found=found[:m].astype(bool), depth=depth[:self.n])
 
     def part_stats(self):
         n = self.n_parts
         it, rs = np.zeros(n, np.int32), np.zeros(n)
         rows, cols = np.zeros(n, np.int64), np.zeros(n, np.int32)
-        lib().orc_get_part_stats(self._h, _ptr(it, ip), _ptr(rs, dp), _ptr(rows, i64p), _ptr(cols, ip))
+        self._L.orc_get_part_stats(self._h, _ptr(it, ip), _ptr(rs, dp), _ptr(rows, i64p), _ptr(cols, ip))
         return dict(iters=it, res_sq=rs, rows=rows, colours=cols)
 
     def metrics(self):
         out = np.zeros(4)
-        lib().orc_get_metrics(self._h, _ptr(out, dp))
+        self._L.orc_get_metrics(self._h, _ptr(out, dp))
         return dict(residual_rms=out[0], residual_max=out[1], joint_gap_max=out[2], joint_gap_sum=out[3])
 
     def joint_error(self):
         """Sum and largest pivot gap over the joints of the current state (m)."""
         out = np.zeros(2)
-        lib().orc_joint_error(self._h, _ptr(out, dp))
+        self._L.orc_joint_error(self._h, _ptr(out, dp))
         return dict(sum=float(out[0]), max=float(out[1]))

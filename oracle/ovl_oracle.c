@@ -1155,21 +1155,31 @@ static const double *ws_lookup(const orc_sim *s, int part, uint64_t key) {
 /* then positions with the new velocities).                                   */
 /* ------------------------------------------------------------------------ */
 
+/* Arithmetic type of the PGS arrays (velocities, impulses, row
+ * coefficients).  FP64 is the oracle.  Built with -DORC_REAL=float, the same
+ * algorithm in the same order runs its sweeps in FP32: a measure of how far
+ * FP32 arithmetic alone can stay from the FP64 result on a given step (the
+ * contact geometry, weights and blend stay FP64). */
+#ifndef ORC_REAL
+#define ORC_REAL double
+#endif
+typedef ORC_REAL real;
+
 typedef struct {
     int la, lb;          /* local body indices, -1 = static end */
-    double JA[6], JB[6]; /* (linear, angular) Jacobian blocks */
-    double k;            /* 1 / (J M^-1 J^T) */
-    double target;
+    real JA[6], JB[6];   /* (linear, angular) Jacobian blocks */
+    real k;              /* 1 / (J M^-1 J^T) */
+    real target;
     int friction_of;     /* row index of the normal row for friction rows, else -1 */
-    double mu;
+    real mu;
     int bilateral;       /* joint rows: bounds +-inf */
     int full;            /* a box end: angular response through its 3 x 3 inverse inertia */
-    double IA[3], IB[3]; /* with full: Iw_A JA_ang, Iw_B JB_ang */
+    real IA[3], IB[3];   /* with full: Iw_A JA_ang, Iw_B JB_ang */
 } pgs_row;
 
-static void row_bounds(const pgs_row *r, const double *lam, double *lo, double *hi) {
+static void row_bounds(const pgs_row *r, const real *lam, real *lo, real *hi) {
     if (r->friction_of >= 0) {
-        double ln = lam[r->friction_of];
+        real ln = lam[r->friction_of];
         *lo = -r->mu * ln; *hi = r->mu * ln;
     } else if (r->bilateral) {
         *lo = -INFINITY; *hi = INFINITY;
@@ -1178,16 +1188,16 @@ static void row_bounds(const pgs_row *r, const double *lam, double *lo, double *
     }
 }
 
-static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+static real clampd(real x, real lo, real hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
-static double row_velocity(const pgs_row *r, const double *vel) {
-    double w = 0;
+static real row_velocity(const pgs_row *r, const real *vel) {
+    real w = 0;
     if (r->la >= 0) for (int a = 0; a < 6; ++a) w += r->JA[a] * vel[6 * r->la + a];
     if (r->lb >= 0) for (int a = 0; a < 6; ++a) w += r->JB[a] * vel[6 * r->lb + a];
     return w;
 }
 
-static void apply_impulse(const pgs_row *r, double *vel, const double *minv, double dl) {
+static void apply_impulse(const pgs_row *r, real *vel, const real *minv, real dl) {
     if (r->full) {
         if (r->la >= 0)
             for (int a = 0; a < 3; ++a) {
@@ -1205,18 +1215,18 @@ static void apply_impulse(const pgs_row *r, double *vel, const double *minv, dou
     if (r->lb >= 0) for (int a = 0; a < 6; ++a) vel[6 * r->lb + a] += minv[6 * r->lb + a] * r->JB[a] * dl;
 }
 
-static double row_residual(const pgs_row *r, const double *vel, const double *lam, int i) {
-    double lo, hi;
+static double row_residual(const pgs_row *r, const real *vel, const real *lam, int i) {
+    real lo, hi;
     row_bounds(r, lam, &lo, &hi);
-    double w = row_velocity(r, vel);
-    double proj = clampd(lam[i] + r->k * (r->target - w), lo, hi);
+    real w = row_velocity(r, vel);
+    real proj = clampd(lam[i] + r->k * (r->target - w), lo, hi);
     return (lam[i] - proj) / r->k;
 }
 
 /* one row of a rigid constraint along direction d between lever arms rA, rB
  * (vectors from each body's centre to the constraint point) */
 static void make_row(pgs_row *row, int la, int lb, const double d[3], const double rA[3],
-                     const double rB[3], const double *minv) {
+                     const double rB[3], const real *minv) {
     double ca[3], cb[3];
     cross3(rA, d, ca);
     cross3(rB, d, cb);
@@ -1237,7 +1247,7 @@ static void make_row(pgs_row *row, int la, int lb, const double d[3], const doub
  * world inverse inertia (Iw, row-major; NULL for a sphere, which keeps the
  * isotropic minv entries) applied to the angular Jacobian block */
 static void make_row_full(pgs_row *row, int la, int lb, const double d[3], const double rA[3], const double rB[3],
-                          const double *minv, const double *IwA, const double *IwB) {
+                          const real *minv, const double *IwA, const double *IwB) {
     make_row(row, la, lb, d, rA, rB, minv);
     row->full = 1;
     double s = 0;
@@ -1291,8 +1301,8 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
     const orc_params *P = &s->P;
     double h = h_override > 0 ? h_override : s->dt[scene];
     double mu = s->mu[scene];
-    double *vel = xcalloc((size_t)nb * 6 + 1, sizeof(double));
-    double *minv = xcalloc((size_t)nb * 6 + 1, sizeof(double));
+    real *vel = xcalloc((size_t)nb * 6 + 1, sizeof(real));
+    real *minv = xcalloc((size_t)nb * 6 + 1, sizeof(real));
     for (int i = 0; i < nb; ++i) {
         int b = bodies[i];
         const double *x = s->st + 13 * (size_t)b;
@@ -1315,7 +1325,7 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
 #define IW_OF(l, body) ((l) >= 0 && iw && body_is_box(s, (body)) ? iw + 9 * (size_t)(l) : NULL)
     int64_t np_ = p1 - p0;
     pgs_row *rows = xcalloc((size_t)np_ * 3 + 1, sizeof(pgs_row));
-    double *lam = xcalloc((size_t)np_ * 3 + 1, sizeof(double));
+    real *lam = xcalloc((size_t)np_ * 3 + 1, sizeof(real));
     int *slots = xcalloc((size_t)np_ * 2 + 1, sizeof(int));
     uint64_t *prio = xcalloc((size_t)np_ + 1, sizeof(uint64_t));
     /* rows, fixed for the step from the blended state (Alg 1) */
@@ -1404,7 +1414,7 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
     for (int64_t q = 0; q < np_; ++q) {
         const double *prev = ws_lookup(s, part, s->pair_key[p0 + q]);
         for (int k = 0; k < 3; ++k) {
-            double l0 = prev ? prev[k] * P->warmstart : 0.0;
+            real l0 = prev ? (real)(prev[k] * P->warmstart) : (real)0;
             lam[3 * q + k] = l0;
             if (l0 != 0.0) apply_impulse(&rows[3 * q + k], vel, minv, l0);
         }
@@ -1428,11 +1438,11 @@ static void solve_worker(orc_sim *s, int part, int scene, const int *bodies, int
                 for (int k = 0; k < 3; ++k) {
                     int i = (int)(3 * q + k);
                     const pgs_row *r = &rows[i];
-                    double lo, hi;
+                    real lo, hi;
                     row_bounds(r, lam, &lo, &hi);
-                    double w = row_velocity(r, vel);
-                    double lnew = clampd(lam[i] + r->k * (r->target - w), lo, hi);
-                    double dl = lnew - lam[i];
+                    real w = row_velocity(r, vel);
+                    real lnew = clampd(lam[i] + r->k * (r->target - w), lo, hi);
+                    real dl = lnew - lam[i];
                     lam[i] = lnew;
                     apply_impulse(r, vel, minv, dl);
                 }

@@ -1370,6 +1370,19 @@ ovl_status ovl_step(ovl_ctx *c, float dt, int32_t iters) {
     return guarded(c, [&]() -> ovl_status { return run_step(c, dt, iters); });
 }
 
+ovl_status ovl_step_n(ovl_ctx *c, float dt, int32_t iters, int32_t nsteps, int32_t *done) {
+    return guarded(c, [&]() -> ovl_status {
+        if (done) *done = 0;
+        if (nsteps < 0) return fail(c, OVL_ERR_ARG, "nsteps must be >= 0");
+        for (int32_t k = 0; k < nsteps; ++k) {
+            const ovl_status rc = run_step(c, dt, iters);
+            if (rc != OVL_OK) return rc;
+            if (done) *done = k + 1;
+        }
+        return OVL_OK;
+    });
+}
+
 ovl_status ovl_load_balance(ovl_ctx *c, int32_t flags) {
     return guarded(c, [&]() -> ovl_status {
         if (!c->has_scene) return fail(c, OVL_ERR_ARG, "no scene");

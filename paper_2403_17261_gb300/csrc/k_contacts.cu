@@ -159,7 +159,14 @@ __global__ void k_write_contacts(const float4 *__restrict__ st, const float *__r
                 k = tangent_axis(nn.x, nn.y, nn.z);
             }
             float3 t = tangent_from(nn, k);
-            float phi = L - pa.w - pb.w;
+            // The gap from the exact FP64 differences of the FP32 centres and an
+            // FP64 square root, rounded once: it enters the speculative target
+            // -phi / h, which multiplies an FP32 rounding of |d| (~1e-7 m)
+            // into ~1e-5 m/s of velocity.
+            const double ex = (double)pb.x - (double)pa.x, ey = (double)pb.y - (double)pa.y,
+                         ez = (double)pb.z - (double)pa.z;
+            const double L64 = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+            const float phi = (float)((L64 - (double)pa.w) - (double)pb.w);
             c_ab[o] = make_int2(a, b);
             c_n[o] = make_float4(nn.x, nn.y, nn.z, phi);
             c_t1[o] = make_float4(t.x, t.y, t.z, 0.f);

@@ -47,7 +47,7 @@ EXPORTED = [
     "ovl_assign_overlap", "ovl_set_state", "ovl_read_state", "ovl_set_step_index",
     "ovl_set_warmstart", "ovl_read_warmstart", "ovl_step", "ovl_load_balance", "ovl_sync", "ovl_joint_error",
     "ovl_read_stats", "ovl_read_contacts", "ovl_read_graph", "ovl_read_entries", "ovl_read_pairs",
-    "ovl_read_worker_stats", "ovl_read_solve_plan", "ovl_autotune_export", "ovl_autotune_import",
+    "ovl_read_worker_stats", "ovl_read_solve_plan", "ovl_step_n", "ovl_save", "ovl_load", "ovl_autotune_export", "ovl_autotune_import",
     "ovl_geodesics_static", "ovl_set_warmstart_mode", "ovl_read_features", "ovl_mlp_set_params",
     "ovl_mlp_get_params", "ovl_mlp_forward", "ovl_log_reserve", "ovl_log_enable", "ovl_log_size",
     "ovl_log_append", "ovl_log_read", "ovl_mlp_train", "ovl_mlp_grad", "ovl_mlp_loss",
@@ -141,6 +141,9 @@ def load_library(path: str | None = None):
         "ovl_read_pairs": [vp, _ip, _u64p, _ip, _fp],
         "ovl_read_worker_stats": [vp, _ip, C.POINTER(C.c_double), C.POINTER(C.c_int64), _ip],
         "ovl_read_solve_plan": [vp, _ip],
+        "ovl_step_n": [vp, C.c_float, C.c_int32, C.c_int32, _ip],
+        "ovl_save": [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)],
+        "ovl_load": [vp, vp, C.c_size_t],
         "ovl_autotune_export": [vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
         "ovl_autotune_import": [vp, C.c_char_p],
         "ovl_set_warmstart_mode": [vp, C.c_int32],
@@ -498,6 +501,34 @@ def ovl_box_scene_contacts(scene, margin: float = 0.05, on_gpu: bool = True, cap
         return dict(ab=ab[:m], k=k[:m], phi=phi[:m], normal=nrm[:m], point=pt[:m])
 
 
+def ovl_step_n(ctx, dt: float, iters: int, nsteps: int) -> int:
+    """nsteps timesteps; returns the number completed (raises on an error)."""
+    done = C.c_int32(0)
+    rc = load_library().ovl_step_n(ctx, float(dt), int(iters), int(nsteps), C.byref(done))
+    _check(ctx, rc)
+    return int(done.value)
+
+
+def ovl_save(ctx) -> bytes:
+    """Checkpoint of the simulation state (host bytes)."""
+    L = load_library()
+    n = C.c_size_t(0)
+    _check(ctx, L.ovl_save(ctx, None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(ctx, L.ovl_save(ctx, buf, n.value, C.byref(n)))
+    return buf.raw[:n.value]
+
+
+def ovl_load(ctx, blob: bytes) -> None:
+    buf = C.create_string_buffer(bytes(blob), len(blob))
+    _check(ctx, load_library().ovl_load(ctx, buf, len(blob)))
+
+
+def checkpoint_step_index(blob: bytes) -> int:
+    """The step index stored in a checkpoint's header."""
+    return int(np.frombuffer(bytes(blob[32:40]), dtype=np.int64)[0])
+
+
 def ovl_read_stats(ctx) -> dict:
     s = ovl_stats()
     _check(ctx, load_library().ovl_read_stats(ctx, C.byref(s)))
@@ -587,6 +618,21 @@ class Simulation:
     def step(self, dt: float = 0.0, iters: int | None = None):
         ovl_step(self.ctx, dt, self.scene.iters if iters is None else iters)
         self._step_index += 1
+
+    def step_n(self, nsteps: int, dt: float = 0.0, iters: int | None = None) -> int:
+        done = C.c_int32(0)
+        rc = load_library().ovl_step_n(self.ctx, float(dt), int(self.scene.iters if iters is None else iters),
+                                       int(nsteps), C.byref(done))
+        self._step_index += int(done.value)   # steps completed before any error
+        _check(self.ctx, rc)
+        return int(done.value)
+
+    def save(self) -> bytes:
+        return ovl_save(self.ctx)
+
+    def load(self, blob: bytes):
+        ovl_load(self.ctx, blob)
+        self._step_index = checkpoint_step_index(blob)
 
     def autotune_export(self) -> str:
         return ovl_autotune_export(self.ctx)
