@@ -37,12 +37,12 @@ def lib():
     global _lib
     if _lib is None:
         L = C.CDLL(build())
-        L.box_plane.argtypes = [_dp, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp]
+        L.box_plane.argtypes = [_dp, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp, _dp]
         L.box_plane.restype = C.c_int
-        L.sphere_box.argtypes = [_dp, C.c_double, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp]
+        L.sphere_box.argtypes = [_dp, C.c_double, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp, _dp]
         L.sphere_box.restype = C.c_int
         L.box_box.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp,
-                              C.POINTER(C.c_int), _dp]
+                              C.POINTER(C.c_int), _dp, _dp]
         L.box_box.restype = C.c_int
         L.box_box_axes.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp, _dp]
         L.box_box_axes.restype = None
@@ -51,14 +51,6 @@ def lib():
         L.box_plane_step.argtypes = [_dp, _dp, _dp, C.c_double, _dp, C.c_double, C.c_double, _dp, C.c_double,
                                      C.c_double, C.c_double, C.c_int, _dp, _dp, _dp]
         L.box_plane_step.restype = C.c_int
-        _fpp = C.POINTER(C.c_float)
-        L.box_plane_f32.argtypes = [_fpp, _fpp, _fpp, _fpp, C.c_float, _fpp, _fpp, _fpp]
-        L.box_plane_f32.restype = C.c_int
-        L.sphere_box_f32.argtypes = [_fpp, C.c_float, _fpp, _fpp, _fpp, C.c_float, _fpp, _fpp, _fpp]
-        L.sphere_box_f32.restype = C.c_int
-        L.box_box_f32.argtypes = [_fpp, _fpp, _fpp, _fpp, _fpp, _fpp, C.c_float, _fpp, _fpp, _fpp,
-                                  C.POINTER(C.c_int), _fpp]
-        L.box_box_f32.restype = C.c_int
         _lib = L
     return _lib
 
@@ -68,36 +60,42 @@ def _v(x, n):
     return a, a.ctypes.data_as(_dp)
 
 
-def box_plane(c, q, h, plane, margin=0.0):
+def box_plane(c, q, h, plane, margin=0.0, with_amb=False):
     """Vertices of the box within the margin of the plane n.x = d (plane =
     (n, d), n unit out of the solid), the 4 deepest at most.  Returns
-    (points [k,3], gaps [k], normal [3] = -n)."""
+    (points [k,3], gaps [k], normal [3] = -n), and with with_amb the
+    closeness of its decisions to their thresholds in bands (< 1: an FP32
+    computation may decide otherwise)."""
     (c, pc), (q, pq), (h, ph), (pl, pp) = _v(c, 3), _v(q, 4), _v(h, 3), _v(plane, 4)
-    pts, gaps, nrm = np.zeros(12), np.zeros(4), np.zeros(3)
+    pts, gaps, nrm, amb = np.zeros(12), np.zeros(4), np.zeros(3), C.c_double(np.inf)
     k = lib().box_plane(pc, pq, ph, pp, float(margin), pts.ctypes.data_as(_dp), gaps.ctypes.data_as(_dp),
-                        nrm.ctypes.data_as(_dp))
-    return pts[: 3 * k].reshape(k, 3), gaps[:k], nrm
+                        nrm.ctypes.data_as(_dp), C.byref(amb))
+    out = (pts[: 3 * k].reshape(k, 3), gaps[:k], nrm)
+    return out + (amb.value,) if with_amb else out
 
 
-def sphere_box(s, r, c, q, h, margin=0.0):
-    """Returns (hit, point on the box [3], normal sphere->box [3], gap)."""
+def sphere_box(s, r, c, q, h, margin=0.0, with_amb=False):
+    """Returns (hit, point on the box [3], normal sphere->box [3], gap)
+    (+ amb with with_amb, as box_plane)."""
     (s, ps), (c, pc), (q, pq), (h, ph) = _v(s, 3), _v(c, 3), _v(q, 4), _v(h, 3)
-    pt, nrm, gap = np.zeros(3), np.zeros(3), C.c_double()
+    pt, nrm, gap, amb = np.zeros(3), np.zeros(3), C.c_double(), C.c_double(np.inf)
     hit = lib().sphere_box(ps, float(r), pc, pq, ph, float(margin), pt.ctypes.data_as(_dp),
-                           nrm.ctypes.data_as(_dp), C.byref(gap))
-    return bool(hit), pt, nrm, gap.value
+                           nrm.ctypes.data_as(_dp), C.byref(gap), C.byref(amb))
+    out = (bool(hit), pt, nrm, gap.value)
+    return out + (amb.value,) if with_amb else out
 
 
-def box_box(cA, qA, hA, cB, qB, hB, margin=0.0):
-    """Returns (points [k,3], gaps [k], normal A->B [3], axis, separation);
-    k = 0 when some axis separates the boxes by more than the margin (axis
-    and separation are then undefined)."""
+def box_box(cA, qA, hA, cB, qB, hB, margin=0.0, with_amb=False):
+    """Returns (points [k,3], gaps [k], normal A->B [3], axis, separation)
+    (+ amb with with_amb, as box_plane); k = 0 when some axis separates the
+    boxes by more than the margin (axis and separation are then undefined)."""
     args = [_v(cA, 3), _v(qA, 4), _v(hA, 3), _v(cB, 3), _v(qB, 4), _v(hB, 3)]
     pts, gaps, nrm = np.zeros(12), np.zeros(4), np.zeros(3)
-    axis, sep = C.c_int(-1), C.c_double(np.nan)
+    axis, sep, amb = C.c_int(-1), C.c_double(np.nan), C.c_double(np.inf)
     k = lib().box_box(*[p for _, p in args], float(margin), pts.ctypes.data_as(_dp), gaps.ctypes.data_as(_dp),
-                      nrm.ctypes.data_as(_dp), C.byref(axis), C.byref(sep))
-    return pts[: 3 * k].reshape(k, 3), gaps[:k], nrm, axis.value, sep.value
+                      nrm.ctypes.data_as(_dp), C.byref(axis), C.byref(sep), C.byref(amb))
+    out = (pts[: 3 * k].reshape(k, 3), gaps[:k], nrm, axis.value, sep.value)
+    return out + (amb.value,) if with_amb else out
 
 
 def box_box_axes(cA, qA, hA, cB, qB, hB):
@@ -130,40 +128,3 @@ def box_plane_step(x, q, h, inv_mass, plane, v, w, mu=0.5, dt=1 / 60, g=(0.0, 0.
                              lam.ctypes.data_as(_dp))
     pts, gaps, _ = box_plane(x, q, h, plane, margin)
     return v2, w2, lam[: 3 * k].reshape(k, 3), pts, gaps
-
-
-# ---- FP32 decisions (the kernels' precision and operation order) ----------
-_fp32 = C.POINTER(C.c_float)
-
-
-def _w(x, n):
-    a = np.ascontiguousarray(x, dtype=np.float32).reshape(n)
-    return a, a.ctypes.data_as(_fp32)
-
-
-def box_plane_f32(c, q, h, plane, margin=0.0):
-    """box_plane in FP32 with the kernels' operation order."""
-    (c, pc), (q, pq), (h, ph), (pl, pp) = _w(c, 3), _w(q, 4), _w(h, 3), _w(plane, 4)
-    pts, gaps, nrm = np.zeros(12, np.float32), np.zeros(4, np.float32), np.zeros(3, np.float32)
-    k = lib().box_plane_f32(pc, pq, ph, pp, float(margin), pts.ctypes.data_as(_fp32), gaps.ctypes.data_as(_fp32),
-                            nrm.ctypes.data_as(_fp32))
-    return pts[: 3 * k].reshape(k, 3), gaps[:k], nrm
-
-
-def sphere_box_f32(s, r, c, q, h, margin=0.0):
-    """sphere_box in FP32 with the kernels' operation order."""
-    (s, ps), (c, pc), (q, pq), (h, ph) = _w(s, 3), _w(c, 3), _w(q, 4), _w(h, 3)
-    pt, nrm, gap = np.zeros(3, np.float32), np.zeros(3, np.float32), C.c_float()
-    hit = lib().sphere_box_f32(ps, float(r), pc, pq, ph, float(margin), pt.ctypes.data_as(_fp32),
-                               nrm.ctypes.data_as(_fp32), C.byref(gap))
-    return bool(hit), pt, nrm, np.float32(gap.value)
-
-
-def box_box_f32(cA, qA, hA, cB, qB, hB, margin=0.0):
-    """box_box in FP32 with the kernels' operation order."""
-    args = [_w(cA, 3), _w(qA, 4), _w(hA, 3), _w(cB, 3), _w(qB, 4), _w(hB, 3)]
-    pts, gaps, nrm = np.zeros(12, np.float32), np.zeros(4, np.float32), np.zeros(3, np.float32)
-    axis, sep = C.c_int(-1), C.c_float(np.nan)
-    k = lib().box_box_f32(*[p for _, p in args], float(margin), pts.ctypes.data_as(_fp32), gaps.ctypes.data_as(_fp32),
-                          nrm.ctypes.data_as(_fp32), C.byref(axis), C.byref(sep))
-    return pts[: 3 * k].reshape(k, 3), gaps[:k], nrm, axis.value, np.float32(sep.value)

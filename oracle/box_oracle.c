@@ -26,12 +26,42 @@
  *    (sphere-box), the clipped incident-face point (box-box, face axis), the
  *    midpoint of the closest points of the two edges (box-box, edge axis);
  *  - an edge axis is chosen over the best face axis only when its
- *    separation exceeds 0.95 x the face separation + 0.01 x the smallest half
- *    extent (faces give stable 4-point manifolds; near-ties go to them);
- *  - ties: lowest axis index (A's faces, B's faces, then a_i x b_j in
- *    i-major order), lowest vertex index, lowest clipped-point order. */
+ *    separation exceeds the face separation by more than 5 % of its
+ *    magnitude + 0.01 x the smallest half extent (faces give stable 4-point
+ *    manifolds; near-ties go to them, separated or penetrating);
+ *  - decisions with a tolerance, so that a computation in any precision
+ *    that is accurate to well under the tolerance decides alike (exactly
+ *    aligned boxes, as in a building, tie in exact arithmetic):
+ *      axes: scanning A's faces, B's faces, then a_i x b_j (i major), a
+ *        later axis replaces the best so far only if its separation exceeds
+ *        it by more than ORC_BOX_TIE_LEN (0.3 mm); an a_i x b_j axis exists
+ *        only when |a_i x b_j| > ORC_BOX_EDGE_MIN;
+ *      the incident face: the most anti-parallel face, a later one winning
+ *        only by more than ORC_BOX_TIE_DIR in |cosine|;
+ *      the least-penetrated face of a box holding a sphere's centre: a later
+ *        face wins only by more than ORC_BOX_TIE_LEN;
+ *      clipping keeps the points within ORC_BOX_TIE_LEN outside a side plane
+ *        of the reference face (it clips at that distance);
+ *      the 4 deepest: a selection that takes, in candidate order, the first
+ *        candidate not deeper than the deepest remaining one by more than
+ *        ORC_BOX_TIE_LEN;
+ *  - every decision reports how close its quantity came to the threshold, in
+ *    units of a band (ORC_BOX_BAND_LEN for lengths, ORC_BOX_BAND_DIR for
+ *    cosines): *amb receives the smallest such distance.  amb < 1 marks a
+ *    pair whose decisions an FP32 computation may take differently. */
+#define ORC_BOX_TIE_LEN 3e-4
+#define ORC_BOX_TIE_DIR 1e-4
+#define ORC_BOX_EDGE_MIN 1e-3
+#define ORC_BOX_BAND_LEN 3e-5
+#define ORC_BOX_BAND_DIR 1e-5
 #include <math.h>
 #include <string.h>
+
+/* distance of x from a decision threshold, in bands, into *amb */
+static void note(double *amb, double x, double thr, double band) {
+    const double d = fabs(x - thr) / band;
+    if (amb && d < *amb) *amb = d;
+}
 
 static void quat_R(const double q[4], double R[9]) {
     /* R[3 r + c]; column k is the box's axis k in world coordinates */
@@ -53,17 +83,27 @@ static void cross3(const double a[3], const double b[3], double o[3]) {
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-/* keep the k deepest of m candidates (gap ascending, then candidate order);
- * pts/gaps are compacted in place; returns the kept count */
-static int keep_deepest(double *pts, double *gaps, int m, int k) {
+/* keep the k deepest of m candidates: k times, among the remaining
+ * candidates in their order, the first one whose gap is not more than
+ * ORC_BOX_TIE_LEN above the smallest remaining gap; pts/gaps are compacted
+ * in place in that order; returns the kept count */
+static int keep_deepest(double *pts, double *gaps, int m, int k, double *amb) {
     int order[16];
     for (int i = 0; i < m; ++i) order[i] = i;
-    for (int i = 1; i < m; ++i) {                      /* stable insertion sort */
-        int o = order[i], j = i - 1;
-        while (j >= 0 && gaps[order[j]] > gaps[o]) { order[j + 1] = order[j]; --j; }
-        order[j + 1] = o;
+    const int n = m < k ? m : k;
+    for (int i = 0; i < n; ++i) {
+        double gmin = gaps[order[i]];
+        for (int j = i + 1; j < m; ++j)
+            if (gaps[order[j]] < gmin) gmin = gaps[order[j]];
+        int pick = i;
+        for (int j = i; j < m; ++j) {
+            note(amb, gaps[order[j]], gmin + ORC_BOX_TIE_LEN, ORC_BOX_BAND_LEN);
+            if (gaps[order[j]] <= gmin + ORC_BOX_TIE_LEN) { pick = j; break; }
+        }
+        const int o = order[pick];
+        for (int j = pick; j > i; --j) order[j] = order[j - 1];
+        order[i] = o;
     }
-    int n = m < k ? m : k;
     double p2[48], g2[16];
     for (int i = 0; i < n; ++i) {
         memcpy(p2 + 3 * i, pts + 3 * order[i], 3 * sizeof(double));
@@ -77,7 +117,7 @@ static int keep_deepest(double *pts, double *gaps, int m, int k) {
 /* Box (first) against the plane {x : n.x = d} (second; n unit, pointing out
  * of the solid).  pts[4][3], gaps[4]; normal[3] = -n.  Returns the count. */
 int box_plane(const double c[3], const double q[4], const double h[3], const double plane[4],
-              double margin, double pts[12], double gaps[4], double normal[3]) {
+              double margin, double pts[12], double gaps[4], double normal[3], double *amb) {
     double R[9], P[24], G[8];
     quat_R(q, R);
     int m = 0;
@@ -87,12 +127,13 @@ int box_plane(const double c[3], const double q[4], const double h[3], const dou
         for (int r = 0; r < 3; ++r)
             p[r] = c[r] + R[3 * r] * s[0] * h[0] + R[3 * r + 1] * s[1] * h[1] + R[3 * r + 2] * s[2] * h[2];
         const double g = plane[0] * p[0] + plane[1] * p[1] + plane[2] * p[2] - plane[3];
+        note(amb, g, margin, ORC_BOX_BAND_LEN);
         if (g <= margin) {
             memcpy(P + 3 * m, p, sizeof p);
             G[m++] = g;
         }
     }
-    m = keep_deepest(P, G, m, 4);
+    m = keep_deepest(P, G, m, 4, amb);
     memcpy(pts, P, (size_t)m * 3 * sizeof(double));
     memcpy(gaps, G, (size_t)m * sizeof(double));
     normal[0] = -plane[0]; normal[1] = -plane[1]; normal[2] = -plane[2];
@@ -103,7 +144,7 @@ int box_plane(const double c[3], const double q[4], const double h[3], const dou
  * pt[3] on the box surface, normal[3] from the sphere towards the box,
  * *gap.  Returns 1 when gap <= margin, else 0 (outputs still written). */
 int sphere_box(const double s[3], double r, const double c[3], const double q[4], const double h[3],
-               double margin, double pt[3], double normal[3], double *gap) {
+               double margin, double pt[3], double normal[3], double *gap, double *amb) {
     double R[9], p[3], cl[3], nb[3];
     quat_R(q, R);
     const double d[3] = {s[0] - c[0], s[1] - c[1], s[2] - c[2]};
@@ -111,6 +152,7 @@ int sphere_box(const double s[3], double r, const double c[3], const double q[4]
     int inside = 1;
     for (int k = 0; k < 3; ++k) {
         cl[k] = p[k] < -h[k] ? -h[k] : (p[k] > h[k] ? h[k] : p[k]);
+        note(amb, fabs(p[k]), h[k], ORC_BOX_BAND_LEN);
         if (cl[k] != p[k]) inside = 0;
     }
     if (!inside) {
@@ -121,8 +163,11 @@ int sphere_box(const double s[3], double r, const double c[3], const double q[4]
     } else {
         int kk = 0;
         double pen = h[0] - fabs(p[0]);
-        for (int k = 1; k < 3; ++k)
-            if (h[k] - fabs(p[k]) < pen) { pen = h[k] - fabs(p[k]); kk = k; }
+        for (int k = 1; k < 3; ++k) {
+            note(amb, h[k] - fabs(p[k]), pen - ORC_BOX_TIE_LEN, ORC_BOX_BAND_LEN);
+            if (h[k] - fabs(p[k]) < pen - ORC_BOX_TIE_LEN) { pen = h[k] - fabs(p[k]); kk = k; }
+        }
+        note(amb, p[kk], 0.0, ORC_BOX_BAND_LEN);
         const double sg = p[kk] >= 0 ? 1.0 : -1.0;
         nb[0] = nb[1] = nb[2] = 0.0;
         nb[kk] = sg;
@@ -133,6 +178,7 @@ int sphere_box(const double s[3], double r, const double c[3], const double q[4]
         pt[r3] = c[r3] + R[3 * r3] * cl[0] + R[3 * r3 + 1] * cl[1] + R[3 * r3 + 2] * cl[2];
         normal[r3] = -(R[3 * r3] * nb[0] + R[3 * r3 + 1] * nb[1] + R[3 * r3 + 2] * nb[2]);
     }
+    note(amb, *gap, margin, ORC_BOX_BAND_LEN);
     return *gap <= margin;
 }
 
@@ -150,13 +196,15 @@ static double separation(const double T[3], const double L[3], const double RA[9
     return s;
 }
 
-/* Sutherland-Hodgman: clip polygon P (n points) by {x : dot(x, e) <= off};
- * returns the new count (at most n + 1 per plane, <= 8 here) */
-static int clip_plane(const double *P, int n, const double e[3], double off, double *out) {
+/* Sutherland-Hodgman: clip polygon P (n points) by {x : dot(x, e) <= off}
+ * (the caller widens off by ORC_BOX_TIE_LEN); returns the new count (at most
+ * n + 1 per plane, <= 8 here) */
+static int clip_plane(const double *P, int n, const double e[3], double off, double *out, double *amb) {
     int m = 0;
     for (int i = 0; i < n; ++i) {
         const double *a = P + 3 * i, *b = P + 3 * ((i + 1) % n);
         const double da = dot3(a, e) - off, db = dot3(b, e) - off;
+        note(amb, da, 0.0, ORC_BOX_BAND_LEN);
         if (da <= 0) { memcpy(out + 3 * m, a, 3 * sizeof(double)); ++m; }
         if ((da <= 0) != (db <= 0)) {
             const double t = da / (da - db);
@@ -174,7 +222,7 @@ static int clip_plane(const double *P, int n, const double e[3], double off, dou
  * than the margin). */
 int box_box(const double cA[3], const double qA[4], const double hA[3], const double cB[3],
             const double qB[4], const double hB[3], double margin, double pts[12], double gaps[4],
-            double normal[3], int *axis, double *sep) {
+            double normal[3], int *axis, double *sep, double *amb) {
     double RA[9], RB[9];
     quat_R(qA, RA);
     quat_R(qB, RB);
@@ -195,26 +243,36 @@ int box_box(const double cA[3], const double qA[4], const double hA[3], const do
             cross3(a, b, x);
             const double len = sqrt(dot3(x, x));
             const int k = 6 + 3 * i + j;
-            valid[k] = len > 1e-9;                         /* parallel edges: the faces cover them */
+            note(amb, len, ORC_BOX_EDGE_MIN, ORC_BOX_BAND_DIR);
+            valid[k] = len > ORC_BOX_EDGE_MIN;             /* near-parallel edges: the faces cover them */
             for (int r = 0; r < 3; ++r) L[k][r] = valid[k] ? x[r] / len : 0.0;
         }
     for (int k = 0; k < 15; ++k) {
         s[k] = valid[k] ? separation(T, L[k], RA, hA, RB, hB) : -INFINITY;
+        if (valid[k]) note(amb, s[k], margin, ORC_BOX_BAND_LEN);
         if (valid[k] && s[k] > margin) return 0;
     }
     int bf = 0, be = -1;
-    for (int k = 1; k < 6; ++k)
-        if (s[k] > s[bf]) bf = k;
-    for (int k = 6; k < 15; ++k)
-        if (valid[k] && (be < 0 || s[k] > s[be])) be = k;
+    for (int k = 1; k < 6; ++k) {
+        note(amb, s[k], s[bf] + ORC_BOX_TIE_LEN, ORC_BOX_BAND_LEN);
+        if (s[k] > s[bf] + ORC_BOX_TIE_LEN) bf = k;
+    }
+    for (int k = 6; k < 15; ++k) {
+        if (!valid[k]) continue;
+        if (be >= 0) note(amb, s[k], s[be] + ORC_BOX_TIE_LEN, ORC_BOX_BAND_LEN);
+        if (be < 0 || s[k] > s[be] + ORC_BOX_TIE_LEN) be = k;
+    }
     double hmin = hA[0];
     for (int k = 0; k < 3; ++k) {
         if (hA[k] < hmin) hmin = hA[k];
         if (hB[k] < hmin) hmin = hB[k];
     }
-    const int best = (be >= 0 && s[be] > 0.95 * s[bf] + 0.01 * hmin) ? be : bf;
+    const double edge_thr = s[bf] + 0.05 * fabs(s[bf]) + 0.01 * hmin;
+    if (be >= 0) note(amb, s[be], edge_thr, ORC_BOX_BAND_LEN);
+    const int best = (be >= 0 && s[be] > edge_thr) ? be : bf;
     *axis = best;
     *sep = s[best];
+    note(amb, dot3(T, L[best]), 0.0, ORC_BOX_BAND_LEN);
     const double sgn = dot3(T, L[best]) < 0 ? -1.0 : 1.0;
     for (int r = 0; r < 3; ++r) normal[r] = sgn * L[best][r];     /* A -> B */
 
@@ -227,11 +285,13 @@ int box_box(const double cA[3], const double qA[4], const double hA[3], const do
         for (int k = 0; k < 3; ++k) {
             if (k != i) {
                 axis_of(RA, k, ax);
+                note(amb, dot3(ax, normal), 0.0, ORC_BOX_BAND_DIR);
                 const double sg = dot3(ax, normal) >= 0 ? 1.0 : -1.0;
                 for (int r = 0; r < 3; ++r) pA[r] += sg * hA[k] * ax[r];
             }
             if (k != j) {
                 axis_of(RB, k, ax);
+                note(amb, dot3(ax, normal), 0.0, ORC_BOX_BAND_DIR);
                 const double sg = dot3(ax, normal) <= 0 ? 1.0 : -1.0;
                 for (int r = 0; r < 3; ++r) pB[r] += sg * hB[k] * ax[r];
             }
@@ -242,7 +302,7 @@ int box_box(const double cA[3], const double qA[4], const double hA[3], const do
         const double w0[3] = {pA[0] - pB[0], pA[1] - pB[1], pA[2] - pB[2]};
         const double b = dot3(ai, bj), cc = dot3(ai, w0), f = dot3(bj, w0);
         const double den = 1.0 - b * b;
-        double u = den > 1e-12 ? (b * f - cc) / den : 0.0;
+        double u = (b * f - cc) / den;                     /* den >= ORC_BOX_EDGE_MIN^2 on an edge axis */
         u = u < -hA[i] ? -hA[i] : (u > hA[i] ? hA[i] : u);
         double v = b * u + f;
         v = v < -hB[j] ? -hB[j] : (v > hB[j] ? hB[j] : v);
@@ -267,7 +327,8 @@ int box_box(const double cA[3], const double qA[4], const double hA[3], const do
     for (int k = 0; k < 3; ++k) {
         axis_of(Ri, k, ax);
         const double d = fabs(dot3(ax, nref));
-        if (d > best_d) { best_d = d; fi = k; }
+        if (k > 0) note(amb, d, best_d + ORC_BOX_TIE_DIR, ORC_BOX_BAND_DIR);
+        if (k == 0 || d > best_d + ORC_BOX_TIE_DIR) { best_d = d; fi = k; }
     }
     axis_of(Ri, fi, ax);
     const double si = dot3(ax, nref) > 0 ? -1.0 : 1.0;
@@ -287,9 +348,9 @@ int box_box(const double cA[3], const double qA[4], const double hA[3], const do
         double e[3], ne[3];
         axis_of(Rr, sides[t], e);
         for (int r = 0; r < 3; ++r) ne[r] = -e[r];
-        m = clip_plane(poly, m, e, dot3(cr, e) + hr[sides[t]], tmp);
+        m = clip_plane(poly, m, e, dot3(cr, e) + hr[sides[t]] + ORC_BOX_TIE_LEN, tmp, amb);
         if (m == 0) break;
-        m = clip_plane(tmp, m, ne, dot3(cr, ne) + hr[sides[t]], poly);
+        m = clip_plane(tmp, m, ne, dot3(cr, ne) + hr[sides[t]] + ORC_BOX_TIE_LEN, poly, amb);
     }
     /* depth of each point below the reference face */
     double fc[3], P[3 * 16], G[16];
@@ -298,12 +359,13 @@ int box_box(const double cA[3], const double qA[4], const double hA[3], const do
     for (int k = 0; k < m; ++k) {
         const double d[3] = {poly[3 * k] - fc[0], poly[3 * k + 1] - fc[1], poly[3 * k + 2] - fc[2]};
         const double g = dot3(d, nref);
+        note(amb, g, margin, ORC_BOX_BAND_LEN);
         if (g <= margin) {
             memcpy(P + 3 * kept, poly + 3 * k, 3 * sizeof(double));
             G[kept++] = g;
         }
     }
-    kept = keep_deepest(P, G, kept, 4);
+    kept = keep_deepest(P, G, kept, 4, amb);
     memcpy(pts, P, (size_t)kept * 3 * sizeof(double));
     memcpy(gaps, G, (size_t)kept * sizeof(double));
     return kept;
@@ -329,7 +391,7 @@ void box_box_axes(const double cA[3], const double qA[4], const double hA[3], co
             axis_of(RB, j, b);
             cross3(a, b, L);
             const double len = sqrt(dot3(L, L));
-            if (len > 1e-9) {
+            if (len > ORC_BOX_EDGE_MIN) {
                 for (int r = 0; r < 3; ++r) L[r] /= len;
                 s[6 + 3 * i + j] = separation(T, L, RA, hA, RB, hB);
             } else {
@@ -374,7 +436,7 @@ int box_plane_step(const double x[3], const double q[4], const double h[3], doub
                    const double plane[4], double mu, double dt, const double g[3], double erp, double slop,
                    double margin, int iters, double v[3], double w[3], double lam[12]) {
     double pts[12], gaps[4], n[3], Iw[9];
-    const int m = box_plane(x, q, h, plane, margin, pts, gaps, n);
+    const int m = box_plane(x, q, h, plane, margin, pts, gaps, n, NULL);
     box_inv_inertia_world(q, h, inv_mass, Iw);
     for (int k = 0; k < 3; ++k) v[k] += dt * g[k];
     /* tangent axis of the normal */
@@ -418,239 +480,4 @@ int box_plane_step(const double x[3], const double q[4], const double h[3], doub
                 }
             }
     return m;
-}
-
-/* ---- FP32 decisions ------------------------------------------------------
- * Which box contacts exist, which axis and which clipped points are kept are
- * integer outcomes; like the sphere contact test, they are taken in the
- * kernels' precision (FP32) with the kernels' operation order, written out
- * here:
- *   box axes  u_k = the columns of R(q), each entry formed as in quat_R in
- *             float (1 - 2 (y y + z z), 2 (x y + w z), ...);
- *   points    c + ((u0 a + u1 b) + u2 c);  dots ((a.x b.x + a.y b.y) + a.z b.z);
- *   crosses   (a.y b.z - a.z b.y, ...);  normalise: x * (1 / sqrt(x.x));
- *   axis sep  |T.L| - sum_k (hA_k |uA_k.L| + hB_k |uB_k.L|), k ascending;
- *   clips     P_a + (P_b - P_a) * (d_a / (d_a - d_b)).
- * The f32 functions return the same records as their FP64 counterparts. */
-typedef struct { float x, y, z; } f3;
-
-static f3 f3v(float x, float y, float z) { f3 r = {x, y, z}; return r; }
-static f3 f3add(f3 a, f3 b) { return f3v(a.x + b.x, a.y + b.y, a.z + b.z); }
-static f3 f3sub(f3 a, f3 b) { return f3v(a.x - b.x, a.y - b.y, a.z - b.z); }
-static f3 f3mul(f3 a, float s) { return f3v(a.x * s, a.y * s, a.z * s); }
-static float f3dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-static f3 f3cross(f3 a, f3 b) { return f3v(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
-
-typedef struct { f3 c, u[3]; float h[3]; } obb32;
-
-static obb32 obb32_make(const float c[3], const float q[4], const float h[3]) {
-    const float w = q[0], x = q[1], y = q[2], z = q[3];
-    obb32 b;
-    b.c = f3v(c[0], c[1], c[2]);
-    b.u[0] = f3v(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
-    b.u[1] = f3v(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
-    b.u[2] = f3v(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
-    for (int k = 0; k < 3; ++k) b.h[k] = h[k];
-    return b;
-}
-
-static f3 obb32_point(const obb32 *B, float a, float b, float c) {
-    return f3add(B->c, f3add(f3add(f3mul(B->u[0], a), f3mul(B->u[1], b)), f3mul(B->u[2], c)));
-}
-
-/* the k deepest of m candidates by (gap, candidate order) */
-static int keep32(f3 *P, float *G, int m, int k) {
-    int order[16];
-    for (int i = 0; i < m; ++i) order[i] = i;
-    for (int i = 1; i < m; ++i) {
-        int o = order[i], j = i - 1;
-        while (j >= 0 && G[order[j]] > G[o]) { order[j + 1] = order[j]; --j; }
-        order[j + 1] = o;
-    }
-    const int n = m < k ? m : k;
-    f3 P2[16];
-    float G2[16];
-    for (int i = 0; i < n; ++i) { P2[i] = P[order[i]]; G2[i] = G[order[i]]; }
-    for (int i = 0; i < n; ++i) { P[i] = P2[i]; G[i] = G2[i]; }
-    return n;
-}
-
-int box_plane_f32(const float c[3], const float q[4], const float h[3], const float plane[4], float margin,
-                  float pts[12], float gaps[4], float normal[3]) {
-    const obb32 B = obb32_make(c, q, h);
-    const f3 n = f3v(plane[0], plane[1], plane[2]);
-    f3 P[8];
-    float G[8];
-    int m = 0;
-    for (int v = 0; v < 8; ++v) {
-        const f3 p = obb32_point(&B, (v & 1) ? h[0] : -h[0], (v & 2) ? h[1] : -h[1], (v & 4) ? h[2] : -h[2]);
-        const float g = f3dot(n, p) - plane[3];
-        if (g <= margin) { P[m] = p; G[m] = g; ++m; }
-    }
-    m = keep32(P, G, m, 4);
-    for (int i = 0; i < m; ++i) {
-        pts[3 * i] = P[i].x; pts[3 * i + 1] = P[i].y; pts[3 * i + 2] = P[i].z;
-        gaps[i] = G[i];
-    }
-    normal[0] = -n.x; normal[1] = -n.y; normal[2] = -n.z;
-    return m;
-}
-
-int sphere_box_f32(const float s[3], float r, const float c[3], const float q[4], const float h[3], float margin,
-                   float pt[3], float normal[3], float *gap) {
-    const obb32 B = obb32_make(c, q, h);
-    const f3 d = f3sub(f3v(s[0], s[1], s[2]), B.c);
-    float loc[3], cl[3];
-    int inside = 1;
-    for (int k = 0; k < 3; ++k) {
-        loc[k] = f3dot(d, B.u[k]);
-        const float lo = -h[k];
-        cl[k] = loc[k] < lo ? lo : loc[k];
-        cl[k] = cl[k] > h[k] ? h[k] : cl[k];
-        if (cl[k] != loc[k]) inside = 0;
-    }
-    f3 nb;
-    if (!inside) {
-        const float e0 = loc[0] - cl[0], e1 = loc[1] - cl[1], e2 = loc[2] - cl[2];
-        const float len = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
-        nb = f3add(f3add(f3mul(B.u[0], e0 / len), f3mul(B.u[1], e1 / len)), f3mul(B.u[2], e2 / len));
-        *gap = len - r;
-    } else {
-        int k = 0;
-        float pen = h[0] - fabsf(loc[0]);
-        for (int j = 1; j < 3; ++j) {
-            const float pj = h[j] - fabsf(loc[j]);
-            if (pj < pen) { pen = pj; k = j; }
-        }
-        const float sg = loc[k] >= 0.f ? 1.f : -1.f;
-        cl[k] = sg * h[k];
-        nb = f3mul(B.u[k], sg);
-        *gap = -pen - r;
-    }
-    const f3 p = obb32_point(&B, cl[0], cl[1], cl[2]);
-    pt[0] = p.x; pt[1] = p.y; pt[2] = p.z;
-    normal[0] = -nb.x; normal[1] = -nb.y; normal[2] = -nb.z;
-    return *gap <= margin;
-}
-
-static float sep32(const obb32 *A, const obb32 *B, f3 T, f3 L) {
-    float s = fabsf(f3dot(T, L));
-    for (int k = 0; k < 3; ++k) s -= A->h[k] * fabsf(f3dot(A->u[k], L)) + B->h[k] * fabsf(f3dot(B->u[k], L));
-    return s;
-}
-
-static float clamp32(float x, float lo, float hi) { return x < lo ? lo : (x > hi ? hi : x); }
-
-/* part of polygon P (n points) with dot(x, e) <= off */
-static int clip32(const f3 *P, int n, f3 e, float off, f3 *Q) {
-    int m = 0;
-    for (int i = 0; i < n; ++i) {
-        const f3 a = P[i], b = P[i + 1 == n ? 0 : i + 1];
-        const float da = f3dot(a, e) - off, db = f3dot(b, e) - off;
-        if (da <= 0.f) Q[m++] = a;
-        if ((da <= 0.f) != (db <= 0.f)) Q[m++] = f3add(a, f3mul(f3sub(b, a), da / (da - db)));
-    }
-    return m;
-}
-
-int box_box_f32(const float cA[3], const float qA[4], const float hA[3], const float cB[3], const float qB[4],
-                const float hB[3], float margin, float pts[12], float gaps[4], float normal[3], int *axis,
-                float *sep) {
-    const obb32 A = obb32_make(cA, qA, hA), B = obb32_make(cB, qB, hB);
-    *axis = -1;
-    const f3 T = f3sub(B.c, A.c);
-    f3 L[15];
-    float s[15];
-    int ok[15];
-    for (int k = 0; k < 3; ++k) {
-        L[k] = A.u[k];
-        L[3 + k] = B.u[k];
-        ok[k] = ok[3 + k] = 1;
-    }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            const int k = 6 + 3 * i + j;
-            const f3 x = f3cross(A.u[i], B.u[j]);
-            const float len = sqrtf(f3dot(x, x));
-            ok[k] = len > 1e-6f;
-            L[k] = ok[k] ? f3mul(x, 1.f / len) : f3v(0.f, 0.f, 0.f);
-        }
-    for (int k = 0; k < 15; ++k) {
-        s[k] = ok[k] ? sep32(&A, &B, T, L[k]) : -INFINITY;
-        if (s[k] > margin) return 0;
-    }
-    int face = 0, edge = -1;
-    for (int k = 1; k < 6; ++k)
-        if (s[k] > s[face]) face = k;
-    for (int k = 6; k < 15; ++k)
-        if (ok[k] && (edge < 0 || s[k] > s[edge])) edge = k;
-    float hmin = A.h[0];
-    for (int k = 0; k < 3; ++k) {
-        if (A.h[k] < hmin) hmin = A.h[k];
-        if (B.h[k] < hmin) hmin = B.h[k];
-    }
-    const int best = (edge >= 0 && s[edge] > 0.95f * s[face] + 0.01f * hmin) ? edge : face;
-    *axis = best;
-    *sep = s[best];
-    const f3 n = f3dot(T, L[best]) < 0.f ? f3mul(L[best], -1.f) : L[best];
-    normal[0] = n.x; normal[1] = n.y; normal[2] = n.z;
-
-    if (best >= 6) {
-        const int i = (best - 6) / 3, j = (best - 6) % 3;
-        f3 pa = A.c, pb = B.c;
-        for (int k = 0; k < 3; ++k) {
-            if (k != i) pa = f3add(pa, f3mul(A.u[k], f3dot(A.u[k], n) >= 0.f ? A.h[k] : -A.h[k]));
-            if (k != j) pb = f3add(pb, f3mul(B.u[k], f3dot(B.u[k], n) <= 0.f ? B.h[k] : -B.h[k]));
-        }
-        const f3 w = f3sub(pa, pb);
-        const float c = f3dot(A.u[i], B.u[j]), e = f3dot(A.u[i], w), f = f3dot(B.u[j], w);
-        const float den = 1.f - c * c;
-        float t = den > 1e-10f ? (c * f - e) / den : 0.f;
-        t = clamp32(t, -A.h[i], A.h[i]);
-        const float v = clamp32(c * t + f, -B.h[j], B.h[j]);
-        t = clamp32(c * v - e, -A.h[i], A.h[i]);
-        const f3 p = f3mul(f3add(f3add(pa, f3mul(A.u[i], t)), f3add(pb, f3mul(B.u[j], v))), 0.5f);
-        pts[0] = p.x; pts[1] = p.y; pts[2] = p.z;
-        gaps[0] = *sep;
-        return 1;
-    }
-
-    const int refA = best < 3;
-    const obb32 *R = refA ? &A : &B, *I = refA ? &B : &A;
-    const int f = best % 3;
-    const f3 nr = refA ? n : f3mul(n, -1.f);
-    int fi = 0;
-    float most = -1.f;
-    for (int k = 0; k < 3; ++k) {
-        const float d = fabsf(f3dot(I->u[k], nr));
-        if (d > most) { most = d; fi = k; }
-    }
-    const float si = f3dot(I->u[fi], nr) > 0.f ? -1.f : 1.f;
-    const int a1 = fi == 0 ? 1 : 0, a2 = fi == 2 ? 1 : 2;
-    f3 poly[16], tmp[16];
-    const f3 fc = f3add(I->c, f3mul(I->u[fi], si * I->h[fi]));
-    const float su[4] = {-1.f, 1.f, 1.f, -1.f}, sv[4] = {-1.f, -1.f, 1.f, 1.f};
-    for (int k = 0; k < 4; ++k)
-        poly[k] = f3add(fc, f3add(f3mul(I->u[a1], su[k] * I->h[a1]), f3mul(I->u[a2], sv[k] * I->h[a2])));
-    int m = 4;
-    const int side[2] = {f == 0 ? 1 : 0, f == 2 ? 1 : 2};
-    for (int t = 0; t < 2 && m > 0; ++t) {
-        const f3 e = R->u[side[t]];
-        m = clip32(poly, m, e, f3dot(R->c, e) + R->h[side[t]], tmp);
-        if (m > 0) m = clip32(tmp, m, f3mul(e, -1.f), -f3dot(R->c, e) + R->h[side[t]], poly);
-    }
-    const f3 rc = f3add(R->c, f3mul(nr, R->h[f]));
-    f3 P[16];
-    float G[16];
-    int kept = 0;
-    for (int k = 0; k < m; ++k) {
-        const float g = f3dot(f3sub(poly[k], rc), nr);
-        if (g <= margin) { P[kept] = poly[k]; G[kept] = g; ++kept; }
-    }
-    kept = keep32(P, G, kept, 4);
-    for (int k = 0; k < kept; ++k) {
-        pts[3 * k] = P[k].x; pts[3 * k + 1] = P[k].y; pts[3 * k + 2] = P[k].z;
-        gaps[k] = G[k];
-    }
-    return kept;
 }

@@ -104,6 +104,7 @@ def _declare(L):
         L.orc_get_counts.argtypes = [C.c_void_p, i64p]
         L.orc_get_contacts.argtypes = [C.c_void_p, ip, dp, dp, dp]
         L.orc_get_contact_points.argtypes = [C.c_void_p, ip, dp]
+        L.orc_get_contact_amb.argtypes = [C.c_void_p, dp]
         L.orc_get_graph.argtypes = [C.c_void_p, ip, ip]
         L.orc_get_entries.argtypes = [C.c_void_p, i64p, ip, u8p, dp, dp]
         L.orc_get_pairs.argtypes = [C.c_void_p, ip, ip, i64p, u64p, ip, dp]
@@ -409,6 +410,16 @@ class OracleSim:
         k, p = np.zeros(m, np.int32), np.zeros((m, 3))
         self._L.orc_get_contact_points(self._h, _ptr(k, ip), _ptr(p, dp))
         return k, p
+
+    def contact_ambiguity(self):
+        """Per contact of the last step: how close its box decisions came to
+        their thresholds, in bands (< 1: an FP32 computation may decide the
+        pair otherwise); inf for sphere contacts."""
+        m = self.counts()["contacts"]
+        a = np.zeros(max(m, 1))
+        self._L.orc_get_contact_amb(self._h, _ptr(a, dp))
+        return a[:m]
+
     def graph(self):
         m = self.counts()["adjacency"]
         rp = np.zeros(self.n + 1, np.int32)

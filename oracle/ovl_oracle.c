@@ -41,9 +41,9 @@
  *    order inside a colour does not change any result.
  *  - Contact test: a pair is in contact when its gap phi <= margin.  Because
  *    that test decides an integer, it is evaluated in FP32 on FP32-rounded
- *    positions with the operation order written below; so is the choice of
- *    the tangent axis (the axis of the smallest |n_k| of the FP32 normal,
- *    ties to the lower index).  Everything after the decision is FP64.
+ *    positions with the operation order written below.  Everything after
+ *    the decision is FP64.  The tangent axis is the axis of the smallest
+ *    |n_k|, a later axis winning only by more than ORC_TANGENT_TIE.
  *  - Alg 6 input = every current contact between two dynamic bodies in
  *    canonical (key) order; <W_x> = sum over workers in W_x of |P_w|, live;
  *    with the contact load (lb_load = 1; Section 6 proposes a load that
@@ -209,6 +209,7 @@ typedef struct {
     int k;           /* point of a box manifold (0 for spheres) */
     int at_point;    /* box contact: both lever arms reach the point p */
     double p[3];
+    double amb;      /* box contact: closeness of its decisions to their thresholds (bands) */
 } orc_contact;
 
 typedef struct { int64_t cx, cy, cz; int scene; int body; } cell_entry;
@@ -253,13 +254,16 @@ static int sphere_plane_touches_f32(const double *c, double r, const double *pl,
     return phi <= (float)margin;
 }
 
-/* tangent axis: smallest |n_k| of the FP32 normal, ties to the lower index */
-static int tangent_axis_f32(float nx, float ny, float nz) {
-    float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
+/* tangent axis: the smallest |n_k|, scanning x, y, z, a later axis winning
+ * only when smaller by more than ORC_TANGENT_TIE (axis-aligned normals tie
+ * exactly in two components; any precision accurate to well under the
+ * tolerance picks the same axis) */
+#define ORC_TANGENT_TIE 1e-4
+static int tangent_axis(const double n[3]) {
     int k = 0;
-    float m = ax;
-    if (ay < m) { k = 1; m = ay; }
-    if (az < m) { k = 2; m = az; }
+    double m = fabs(n[0]);
+    if (fabs(n[1]) < m - ORC_TANGENT_TIE) { k = 1; m = fabs(n[1]); }
+    if (fabs(n[2]) < m - ORC_TANGENT_TIE) k = 2;
     return k;
 }
 
@@ -274,35 +278,25 @@ static void tangent_from_axis(const double n[3], int k, double t1[3]) {
 
 static void fill_sphere_contact(orc_contact *c, int a, int b, const double *ca, const double *cb,
                                 double ra, double rb) {
-    c->a = a; c->b = b; c->k = 0; c->at_point = 0;
+    c->a = a; c->b = b; c->k = 0; c->at_point = 0; c->amb = INFINITY;
     double d[3] = {cb[0] - ca[0], cb[1] - ca[1], cb[2] - ca[2]};
     double L = sqrt(dot3(d, d));
     c->phi = L - ra - rb;
-    /* FP32 normal for the axis decision, mirroring the contact test's rounding */
-    float fdx = (float)cb[0] - (float)ca[0];
-    float fdy = (float)cb[1] - (float)ca[1];
-    float fdz = (float)cb[2] - (float)ca[2];
-    float fxx = fdx * fdx, fyy = fdy * fdy, fzz = fdz * fdz;
-    float fL = sqrtf((fxx + fyy) + fzz);
-    int k;
-    if (L < 1e-12 || fL == 0.0f) {
+    if (L < 1e-12) {
         c->n[0] = 0; c->n[1] = 0; c->n[2] = 1;
-        k = 0;
     } else {
         c->n[0] = d[0] / L; c->n[1] = d[1] / L; c->n[2] = d[2] / L;
-        k = tangent_axis_f32(fdx / fL, fdy / fL, fdz / fL);
     }
-    tangent_from_axis(c->n, k, c->t1);
+    tangent_from_axis(c->n, tangent_axis(c->n), c->t1);
 }
 
 static void fill_plane_contact(orc_contact *c, int a, int b, const double *ca, double ra,
                                const double *pl) {
-    c->a = a; c->b = b; c->k = 0; c->at_point = 0;
+    c->a = a; c->b = b; c->k = 0; c->at_point = 0; c->amb = INFINITY;
     c->phi = dot3(pl, ca) - pl[3] - ra;
     /* normal from the sphere (a) towards the plane (b): minus the plane normal */
     c->n[0] = -pl[0]; c->n[1] = -pl[1]; c->n[2] = -pl[2];
-    int k = tangent_axis_f32(-(float)pl[0], -(float)pl[1], -(float)pl[2]);
-    tangent_from_axis(c->n, k, c->t1);
+    tangent_from_axis(c->n, tangent_axis(c->n), c->t1);
 }
 
 typedef struct {
@@ -319,33 +313,29 @@ typedef struct {
     const double *half;    /* n x 3 half extents (zeros: a sphere), or NULL: all spheres */
 } contact_input;
 
-/* box contact decisions in FP32 (box_oracle.c, the kernels' operation order) */
-int box_plane_f32(const float c[3], const float q[4], const float h[3], const float plane[4], float margin,
-                  float pts[12], float gaps[4], float normal[3]);
-int sphere_box_f32(const float s[3], float r, const float c[3], const float q[4], const float h[3], float margin,
-                   float pt[3], float normal[3], float *gap);
-int box_box_f32(const float cA[3], const float qA[4], const float hA[3], const float cB[3], const float qB[4],
-                const float hB[3], float margin, float pts[12], float gaps[4], float normal[3], int *axis,
-                float *sep);
+/* FP64 box geometry (box_oracle.c); *amb: how close its decisions came to
+ * their thresholds, in bands (< 1: an FP32 computation may decide otherwise) */
+int box_plane(const double c[3], const double q[4], const double h[3], const double plane[4],
+              double margin, double pts[12], double gaps[4], double normal[3], double *amb);
+int sphere_box(const double s[3], double r, const double c[3], const double q[4], const double h[3],
+               double margin, double pt[3], double normal[3], double *gap, double *amb);
+int box_box(const double cA[3], const double qA[4], const double hA[3], const double cB[3],
+            const double qB[4], const double hB[3], double margin, double pts[12], double gaps[4],
+            double normal[3], int *axis, double *sep, double *amb);
 
 static int is_box(const contact_input *in, int b) {
     return in->half && (in->half[3 * (size_t)b] > 0 || in->half[3 * (size_t)b + 1] > 0 ||
                         in->half[3 * (size_t)b + 2] > 0);
 }
 
-/* one point of a box contact: FP32 geometry as decided, FP64 record */
-static void fill_box_point(orc_contact *c, int a, int b, int k, const float p[3], float gap, const float nf[3],
-                           double sgn) {
+/* one point of a box contact (normal n from a towards b after the sign) */
+static void fill_box_point(orc_contact *c, int a, int b, int k, const double p[3], double gap, const double n[3],
+                           double sgn, double amb) {
     c->a = a; c->b = b; c->k = k; c->at_point = 1;
-    c->phi = (double)gap;
-    for (int j = 0; j < 3; ++j) { c->p[j] = (double)p[j]; c->n[j] = sgn * (double)nf[j]; }
-    const float fx = (float)(sgn * nf[0]), fy = (float)(sgn * nf[1]), fz = (float)(sgn * nf[2]);
-    tangent_from_axis(c->n, tangent_axis_f32(fx, fy, fz), c->t1);
-}
-
-static void box_f32_pose(const double *st, float c[3], float q[4]) {
-    for (int j = 0; j < 3; ++j) c[j] = (float)st[j];
-    for (int j = 0; j < 4; ++j) q[j] = (float)st[3 + j];
+    c->phi = gap;
+    c->amb = amb;
+    for (int j = 0; j < 3; ++j) { c->p[j] = p[j]; c->n[j] = sgn * n[j]; }
+    tangent_from_axis(c->n, tangent_axis(c->n), c->t1);
 }
 
 typedef struct { orc_contact *list; size_t cnt, cap; } contact_buf;
@@ -356,42 +346,34 @@ static orc_contact *cb_next(contact_buf *B) {
 }
 
 /* the contacts of a body pair with at least one box: the bounding spheres
- * must meet (the same FP32 test as for spheres), then the box functions
- * decide in FP32; the normal runs from a towards b */
+ * must meet (the same FP32 test as for spheres), then the FP64 box
+ * geometry decides; the normal runs from a towards b */
 static void box_pair_contacts(const contact_input *in, int a, int b, contact_buf *B) {
     const double *ca = in->state + 13 * (size_t)a, *cb = in->state + 13 * (size_t)b;
     if (!sphere_pair_touches_f32(ca, cb, in->radius[a], in->radius[b], in->margin)) return;
-    float pa[3], qa[4], pb[3], qb[4], ha[3], hb[3], pts[12], gaps[4], nf[3];
-    box_f32_pose(ca, pa, qa);
-    box_f32_pose(cb, pb, qb);
-    for (int j = 0; j < 3; ++j) { ha[j] = (float)in->half[3 * (size_t)a + j]; hb[j] = (float)in->half[3 * (size_t)b + j]; }
-    const float m = (float)in->margin;
+    const double *ha = in->half + 3 * (size_t)a, *hb = in->half + 3 * (size_t)b;
+    double pts[12], gaps[4], nrm[3], amb = INFINITY;
     if (is_box(in, a) && is_box(in, b)) {
         int axis;
-        float sep;
-        const int k = box_box_f32(pa, qa, ha, pb, qb, hb, m, pts, gaps, nf, &axis, &sep);
-        for (int i = 0; i < k; ++i) fill_box_point(cb_next(B), a, b, i, pts + 3 * i, gaps[i], nf, 1.0);
+        double sep;
+        const int k = box_box(ca, ca + 3, ha, cb, cb + 3, hb, in->margin, pts, gaps, nrm, &axis, &sep, &amb);
+        for (int i = 0; i < k; ++i) fill_box_point(cb_next(B), a, b, i, pts + 3 * i, gaps[i], nrm, 1.0, amb);
     } else {
         /* one sphere, one box: sphere_box's normal runs from the sphere to the box */
         const int sph = is_box(in, a) ? b : a, bx = sph == a ? b : a;
-        float sc[3], sq[4], bc[3], bq[4], bh[3], gap;
-        box_f32_pose(sph == a ? ca : cb, sc, sq);
-        box_f32_pose(bx == a ? ca : cb, bc, bq);
-        for (int j = 0; j < 3; ++j) bh[j] = bx == a ? ha[j] : hb[j];
-        if (sphere_box_f32(sc, (float)in->radius[sph], bc, bq, bh, m, pts, nf, &gap))
-            fill_box_point(cb_next(B), a, b, 0, pts, gap, nf, sph == a ? 1.0 : -1.0);
+        const double *cs = in->state + 13 * (size_t)sph, *cx = in->state + 13 * (size_t)bx;
+        double gap;
+        if (sphere_box(cs, in->radius[sph], cx, cx + 3, in->half + 3 * (size_t)bx, in->margin, pts, nrm, &gap, &amb))
+            fill_box_point(cb_next(B), a, b, 0, pts, gap, nrm, sph == a ? 1.0 : -1.0, amb);
     }
 }
 
 static void box_plane_contacts(const contact_input *in, int a, int p, contact_buf *B) {
     const double *ca = in->state + 13 * (size_t)a, *pl = in->planes + 4 * (size_t)p;
     if (!sphere_plane_touches_f32(ca, in->radius[a], pl, in->margin)) return;
-    float c[3], q[4], h[3], plf[4], pts[12], gaps[4], nf[3];
-    box_f32_pose(ca, c, q);
-    for (int j = 0; j < 3; ++j) h[j] = (float)in->half[3 * (size_t)a + j];
-    for (int j = 0; j < 4; ++j) plf[j] = (float)pl[j];
-    const int k = box_plane_f32(c, q, h, plf, (float)in->margin, pts, gaps, nf);
-    for (int i = 0; i < k; ++i) fill_box_point(cb_next(B), a, in->n + p, i, pts + 3 * i, gaps[i], nf, 1.0);
+    double pts[12], gaps[4], nrm[3], amb = INFINITY;
+    const int k = box_plane(ca, ca + 3, in->half + 3 * (size_t)a, pl, in->margin, pts, gaps, nrm, &amb);
+    for (int i = 0; i < k; ++i) fill_box_point(cb_next(B), a, in->n + p, i, pts + 3 * i, gaps[i], nrm, 1.0, amb);
 }
 
 /* All contacts of the current state in canonical order (ascending (a, b)).
@@ -1793,6 +1775,13 @@ void orc_get_contact_points(const orc_sim *s, int *k, double *p) {
         k[i] = s->con[i].k;
         for (int j = 0; j < 3; ++j) p[3 * i + j] = s->con[i].at_point ? s->con[i].p[j] : 0.0;
     }
+}
+
+/* per contact: how close the decisions of a box contact came to their
+ * thresholds, in bands (< 1: a pair an FP32 computation may decide
+ * otherwise); +inf for sphere contacts */
+void orc_get_contact_amb(const orc_sim *s, double *amb) {
+    for (int64_t i = 0; i < s->nc; ++i) amb[i] = s->con[i].amb;
 }
 
 void orc_get_graph(const orc_sim *s, int *row_ptr, int *col) {

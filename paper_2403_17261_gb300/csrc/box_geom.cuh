@@ -8,11 +8,22 @@
 //
 // Conventions: the normal points from the first shape towards the second;
 // gap > 0 when apart; a contact when gap <= margin; quaternions as float4
-// (x = w, y..w = vector part).  Selection rules: the 4 deepest points, ties
-// to the lower candidate index; an edge axis is taken over the best face
-// axis only if its separation exceeds 0.95 x the face's + 0.01 x the
-// smallest half extent; ties between axes go to the lower index (A's faces,
-// B's faces, then a_i x b_j with i major).
+// (x = w, y..w = vector part).  Decisions with a tolerance, so that exactly
+// aligned boxes (which tie in exact arithmetic) decide the same in any
+// precision accurate to well under it:
+//  - axes: scanning A's faces, B's faces, then a_i x b_j (i major), a later
+//    axis replaces the best so far only if its separation is larger by more
+//    than kTieLen (0.3 mm); an a_i x b_j axis exists when |a_i x b_j| >
+//    kEdgeMin; an edge axis is taken over the best face axis only if its
+//    separation exceeds the face's by more than 5 % of the face's magnitude
+//    + 0.01 x the smallest half extent;
+//  - the incident face: the most anti-parallel, a later face winning only by
+//    more than kTieDir in |cosine|;
+//  - a sphere's centre inside a box: the least-penetrated face, a later face
+//    winning only by more than kTieLen;
+//  - clipping keeps points within kTieLen outside a reference side plane;
+//  - the 4 deepest: k times, among the remaining candidates in order, the
+//    first whose gap is within kTieLen of the smallest remaining gap.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -48,20 +59,26 @@ OVL_HD Obb make_obb(float3 c, float4 q, float3 h) {
     return b;
 }
 
+constexpr float kTieLen = 3e-4f;
+constexpr float kTieDir = 1e-4f;
+constexpr float kEdgeMin = 1e-3f;
+
 // point of the box for local coordinates (a, b, c)
 OVL_HD float3 at(const Obb &B, float a, float b, float c) {
     return add(B.c, add(add(scl(B.u[0], a), scl(B.u[1], b)), scl(B.u[2], c)));
 }
 
-// candidates (points, gaps) kept: the k deepest, ties to the lower index;
-// n <= 16, written back compacted in order of depth
+// candidates (points, gaps) kept: k times, the first remaining candidate
+// (in order) whose gap is within kTieLen of the smallest remaining gap;
+// n <= 16, written back compacted in the order taken
 OVL_HD int keep_deepest(float3 *P, float *G, int n, int k) {
-    for (int i = 0; i < n && i < k; ++i) {            // selection by (gap, index)
+    for (int i = 0; i < n && i < k; ++i) {
+        float gmin = G[i];
+        for (int j = i + 1; j < n; ++j) gmin = fminf(gmin, G[j]);
         int m = i;
-        for (int j = i + 1; j < n; ++j)
-            if (G[j] < G[m]) m = j;
+        while (m < n - 1 && !(G[m] <= gmin + kTieLen)) ++m;   // bounded even with NaN gaps
         if (m != i) {
-            // rotate [i, m] right by one so that equal gaps keep their order
+            // rotate [i, m] right by one so that the others keep their order
             const float3 pm = P[m];
             const float gm = G[m];
             for (int j = m; j > i; --j) { P[j] = P[j - 1]; G[j] = G[j - 1]; }
@@ -114,7 +131,7 @@ OVL_HD int sphere_box(float3 s, float r, const Obb &B, float margin, float3 &pt,
         float pen = B.h[0] - fabsf(loc[0]);
         for (int j = 1; j < 3; ++j) {
             const float pj = B.h[j] - fabsf(loc[j]);
-            if (pj < pen) { pen = pj; k = j; }
+            if (pj < pen - kTieLen) { pen = pj; k = j; }
         }
         const float sg = loc[k] >= 0.f ? 1.f : -1.f;
         cl[k] = sg * B.h[k];
@@ -164,7 +181,7 @@ OVL_HD int box_box(const Obb &A, const Obb &B, float margin, float3 pts[4], floa
             const int k = 6 + 3 * i + j;
             const float3 x = crs(A.u[i], B.u[j]);
             const float len = sqrtf(dot(x, x));
-            ok[k] = len > 1e-6f;
+            ok[k] = len > kEdgeMin;
             L[k] = ok[k] ? scl(x, 1.f / len) : v3(0.f, 0.f, 0.f);
         }
     for (int k = 0; k < 15; ++k) {
@@ -173,12 +190,13 @@ OVL_HD int box_box(const Obb &A, const Obb &B, float margin, float3 pts[4], floa
     }
     int face = 0, edge = -1;
     for (int k = 1; k < 6; ++k)
-        if (s[k] > s[face]) face = k;
+        if (s[k] > s[face] + kTieLen) face = k;
     for (int k = 6; k < 15; ++k)
-        if (ok[k] && (edge < 0 || s[k] > s[edge])) edge = k;
+        if (ok[k] && (edge < 0 || s[k] > s[edge] + kTieLen)) edge = k;
     float hmin = A.h[0];
     for (int k = 0; k < 3; ++k) hmin = fminf(hmin, fminf(A.h[k], B.h[k]));
-    const int best = (edge >= 0 && s[edge] > 0.95f * s[face] + 0.01f * hmin) ? edge : face;
+    const float edge_thr = s[face] + 0.05f * fabsf(s[face]) + 0.01f * hmin;
+    const int best = (edge >= 0 && s[edge] > edge_thr) ? edge : face;
     axis = best;
     sep = s[best];
     normal = dot(T, L[best]) < 0.f ? scl(L[best], -1.f) : L[best];
@@ -194,8 +212,8 @@ OVL_HD int box_box(const Obb &A, const Obb &B, float margin, float3 pts[4], floa
         // nearest points of pa + t a_i (|t| <= h) and pb + v b_j (|v| <= h)
         const float3 w = sub(pa, pb);
         const float c = dot(A.u[i], B.u[j]), e = dot(A.u[i], w), f = dot(B.u[j], w);
-        const float den = 1.f - c * c;
-        float t = den > 1e-10f ? (c * f - e) / den : 0.f;
+        const float den = 1.f - c * c;                  // >= kEdgeMin^2 on an edge axis
+        float t = (c * f - e) / den;
         t = fminf(fmaxf(t, -A.h[i]), A.h[i]);
         const float v = fminf(fmaxf(c * t + f, -B.h[j]), B.h[j]);
         t = fminf(fmaxf(c * v - e, -A.h[i]), A.h[i]);
@@ -210,10 +228,10 @@ OVL_HD int box_box(const Obb &A, const Obb &B, float margin, float3 pts[4], floa
     const int f = best % 3;
     const float3 nr = refA ? normal : scl(normal, -1.f);   // reference face normal, towards I
     int fi = 0;
-    float most = -1.f;
-    for (int k = 0; k < 3; ++k) {
+    float most = fabsf(dot(I.u[0], nr));
+    for (int k = 1; k < 3; ++k) {
         const float d = fabsf(dot(I.u[k], nr));
-        if (d > most) { most = d; fi = k; }
+        if (d > most + kTieDir) { most = d; fi = k; }
     }
     const float si = dot(I.u[fi], nr) > 0.f ? -1.f : 1.f;
     const int a1 = fi == 0 ? 1 : 0, a2 = fi == 2 ? 1 : 2;
@@ -227,8 +245,8 @@ OVL_HD int box_box(const Obb &A, const Obb &B, float margin, float3 pts[4], floa
     const int side[2] = {r1, r2};
     for (int t = 0; t < 2 && m > 0; ++t) {
         const float3 e = R.u[side[t]];
-        m = clip_half(poly, m, e, dot(R.c, e) + R.h[side[t]], tmp);
-        if (m > 0) m = clip_half(tmp, m, scl(e, -1.f), -dot(R.c, e) + R.h[side[t]], poly);
+        m = clip_half(poly, m, e, dot(R.c, e) + R.h[side[t]] + kTieLen, tmp);
+        if (m > 0) m = clip_half(tmp, m, scl(e, -1.f), -dot(R.c, e) + R.h[side[t]] + kTieLen, poly);
     }
     const float3 rc = add(R.c, scl(nr, R.h[f]));          // reference face centre
     float3 P[16];
@@ -311,12 +329,12 @@ OVL_HD void solve_row(const Row1 &row, float lo, float hi, float im, float3 &v, 
 }
 
 // tangent t1 of a contact normal: normalise(e_k - n_k n) for the axis k of
-// the smallest |n_k| (ties to the lower index)
+// the smallest |n_k|, a later axis winning only by more than kTieDir
 OVL_HD float3 tangent1(float3 n) {
     int k = 0;
     float m = fabsf(n.x);
-    if (fabsf(n.y) < m) { m = fabsf(n.y); k = 1; }
-    if (fabsf(n.z) < m) k = 2;
+    if (fabsf(n.y) < m - kTieDir) { m = fabsf(n.y); k = 1; }
+    if (fabsf(n.z) < m - kTieDir) k = 2;
     const float nk = comp(n, k);
     float3 t = scl(n, -nk);
     if (k == 0) t.x += 1.f; else if (k == 1) t.y += 1.f; else t.z += 1.f;

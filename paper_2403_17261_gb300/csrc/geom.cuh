@@ -15,14 +15,17 @@ __device__ __forceinline__ float3 quat_rotate(float4 q, float3 v) {
                        v.z + q.x * t.z + (u.x * t.y - u.y * t.x));
 }
 
-// tangent axis of a contact: the axis of the smallest |n_k|, ties to the
-// lower index
+// tangent axis of a contact: the axis of the smallest |n_k|, scanning x, y,
+// z, a later axis winning only when smaller by more than 1e-4 (axis-aligned
+// normals tie exactly in two components; the FP64 reference, with the same
+// rule, then picks the same axis)
 __device__ __forceinline__ int tangent_axis(float nx, float ny, float nz) {
+    const float tie = 1e-4f;
     float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
     int k = 0;
     float m = ax;
-    if (ay < m) { k = 1; m = ay; }
-    if (az < m) { k = 2; }
+    if (ay < m - tie) { k = 1; m = ay; }
+    if (az < m - tie) { k = 2; }
     return k;
 }
 

@@ -189,8 +189,11 @@ def test_box_box_large_on_small_is_clipped():
     hA, hB = [0.4, 0.3, 0.2], [1.0, 1.0, 0.5]
     pts, gaps, n, axis, sep = X.box_box([0, 0, 0], ID, hA, [0.05, 0.0, 0.69], ID, hB, margin=0.02)
     assert axis == 2 and pts.shape == (4, 3)
-    # B's bottom face (z = 0.19) clipped to A's top face: A's top corners at z = 0.19
-    want = [[sx * 0.4, sy * 0.3, 0.19] for sx in (-1, 1) for sy in (-1, 1)]
+    # the two z faces tie (-0.01 each): A's, the first scanned, is the reference.
+    # B's bottom face (z = 0.19) clipped to A's top face, whose side planes are
+    # moved out by the clipping tolerance (3e-4): A's top corners at z = 0.19
+    tol = 3e-4
+    want = [[sx * (0.4 + tol), sy * (0.3 + tol), 0.19] for sx in (-1, 1) for sy in (-1, 1)]
     assert same_points(pts, want, 1e-13)
     np.testing.assert_allclose(gaps, -0.01, atol=1e-14)
 
