@@ -124,8 +124,12 @@ typedef struct ovl_scene_desc {
     const int32_t *scene_beta;   /* [n_scenes] weight search depth beta (Alg 5), <= 254 */
     const int32_t *n_sets;       /* [n_scenes] workers per scene, 1..64 */
     const float *half_extents;   /* [n][3] box half extents (zeros: a sphere), or NULL: all spheres.
-                                    The step does not simulate box bodies yet: a positive extent is
-                                    OVL_ERR_ARG at upload (their contacts: ovl_box_scene_contacts) */
+                                    Finite and >= 0; a body with a positive extent is a solid box
+                                    (inertia I_k = m (h_j^2 + h_l^2) / 3) whose radius must bound it
+                                    (radius >= |h|: the broad phase tests bounding spheres).  Boxes
+                                    are the bodies of the paper's Building and Bridge scenes
+                                    (Section 6).  The learned warm start's contact features treat
+                                    every contact as a sphere contact. */
 } ovl_scene_desc;
 
 /* Last-step statistics. */
@@ -374,6 +378,11 @@ ovl_status ovl_sync(ovl_ctx *ctx);
  *            colour, lambda[3] after the sweeps. */
 ovl_status ovl_read_stats(ovl_ctx *ctx, ovl_stats *out);
 ovl_status ovl_read_contacts(ovl_ctx *ctx, int32_t *ab, float *phi, float *normal, float *t1);
+/* Box contacts of the last step (the manifolds of Section 6's box bodies):
+ * per contact its point index k in the pair's manifold (0..3; 0 for sphere
+ * contacts) and its point [3] (zeros for sphere contacts).  Host arrays of
+ * n_contacts entries (either may be NULL); OVL_ERR_ARG before a step. */
+ovl_status ovl_read_contact_points(ovl_ctx *ctx, int32_t *k, float *point);
 ovl_status ovl_read_graph(ovl_ctx *ctx, int32_t *row_ptr, int32_t *col);
 ovl_status ovl_read_entries(ovl_ctx *ctx, int32_t *entry_ptr, int32_t *part, uint8_t *D,
                             float *weight, float *copies13);

@@ -1665,8 +1665,10 @@ int orc_step(orc_sim *s, double dt, int iters) {
                 if (i < s->nc) {
                     s->pair_kind[q] = 0;
                     s->pair_cidx[q] = i;
-                    s->pair_key[q] = ((uint64_t)(uint32_t)s->con[i].k << 60) |
-                                     ((uint64_t)(uint32_t)s->con[i].a << 32) | (uint32_t)s->con[i].b;
+                    /* (a, b, k) packed so that key order is the canonical
+                                     * contact order: a << 32 | b << 2 | k */
+                    s->pair_key[q] = ((uint64_t)(uint32_t)s->con[i].a << 32) |
+                                     ((uint64_t)(uint32_t)s->con[i].b << 2) | (uint64_t)(uint32_t)s->con[i].k;
                 } else {
                     s->pair_kind[q] = 1;
                     s->pair_cidx[q] = i - s->nc;

@@ -53,6 +53,7 @@ uint64_t scene_hash(const ovl_ctx *c) {
     f.add(c->hs.scene_gamma);
     f.add(c->hs.jab);
     f.add(c->h_plane_ptr);
+    f.add(c->h_half);
     return f.h;
 }
 

@@ -61,6 +61,9 @@ void mark(ovl_ctx *c, int i) {
 
 // ---- phases ----------------------------------------------------------------
 
+// contact points and manifold indices (contexts with box bodies), else NULL
+float4 *contact_points(ovl_ctx *c) { return c->has_boxes ? c->c_p.p : nullptr; }
+
 void phase_contacts(ovl_ctx *c) {
     cudaStream_t s = c->stream;
     const int n = c->n;
@@ -84,6 +87,7 @@ void phase_contacts(ovl_ctx *c) {
     a.nb_list = c->nb_list.p; a.nb_off = c->nb_off.p; a.nb_count = c->nb_count.p;
     a.contact_count = c->ccount.p;
     a.contact_start = c->cstart.p; a.status = c->status.p;
+    a.half = c->has_boxes ? c->half.p : nullptr;
     launch_cells(a, s);
     scan_i32(c->bucket_count.p, c->bucket_start.p, (int)c->tsize, c->scan_tmp, s);
     launch_bucket_fill(a, s);
@@ -93,7 +97,9 @@ void phase_contacts(ovl_ctx *c) {
     c->c_ab.ensure(c->nc + 1);
     c->c_n.ensure(c->nc + 1);
     c->c_t1.ensure(c->nc + 1);
+    if (c->has_boxes) c->c_p.ensure(c->nc + 1);
     a.c_ab = c->c_ab.p; a.c_n = c->c_n.p; a.c_t1 = c->c_t1.p;
+    a.c_p = contact_points(c);
     launch_write_contacts(a, s);
 }
 
@@ -133,7 +139,7 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
     c->lb_pos.ensure(c->nc + 1);
     c->lb_pairs.ensure(c->nc + 1);
     const auto t0 = std::chrono::steady_clock::now();
-    launch_lb_flags(c->c_ab.p, c->nc, c->im.p, n, c->mask.p, deact ? 0 : 1, c->lb_flag.p, s);
+    launch_lb_flags(c->c_ab.p, c->nc, c->im.p, n, c->mask.p, deact ? 0 : 1, c->lb_flag.p, contact_points(c), s);
     scan_i32(c->lb_flag.p, c->lb_pos.p, c->nc, c->scan_tmp, s);
     // the graph and the masks go to the host while the candidate count is read
     c->h_rp.ensure((size_t)n + 1);
@@ -154,7 +160,7 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
     if (by_contacts) {
         c->lb_deg.ensure((size_t)n + 1);
         c->h_deg.ensure((size_t)n + 1);
-        launch_contact_degree(c->c_ab.p, c->nc, n, c->lb_deg.p, s);
+        launch_contact_degree(c->c_ab.p, c->nc, n, c->lb_deg.p, contact_points(c), s);
         CK(cudaMemcpyAsync(c->h_deg.p, c->lb_deg.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
     }
     launch_worker_loads(c->mask.p, c->sob.p, c->part_base.p, by_contacts ? c->lb_deg.p : nullptr, n,
@@ -171,6 +177,7 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
 
 MemberArgs member_args(ovl_ctx *c) {
     MemberArgs a{};
+    a.c_p = contact_points(c);
     a.n = c->n; a.nc = c->nc; a.nj = c->nj; a.n_parts = c->n_parts;
     a.im = c->im.p; a.sob = c->sob.p; a.n_sets = c->n_sets.p; a.part_base = c->part_base.p;
     a.joint_scene = c->joint_scene.p; a.mask = c->mask.p; a.c_ab = c->c_ab.p; a.jab = c->jab.p;
@@ -527,6 +534,12 @@ void phase_rows(ovl_ctx *c, float dt_override) {
     a.erp = c->P.erp; a.slop = c->P.slop;
     a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.r4 = c->r4.p; a.rlam = c->rlam.p;
     a.rpair = c->rpair.p; a.status = c->status.p;
+    if (c->has_boxes) {
+        c->row_full.ensure(npr + 1);
+        c->rfull.ensure((size_t)FULL_ROW_WORDS * npr + 1);
+        a.c_p = c->c_p.p; a.half = c->half.p; a.iib = c->iib.p;
+        a.row_full = c->row_full.p; a.rfull = c->rfull.p;
+    }
     launch_rows(a, c->stream);
 }
 
@@ -586,6 +599,7 @@ SolveArgs solve_args(ovl_ctx *c, float dt_override, int iters) {
     a.iters = iters; a.flags = c->P.flags;
     a.res_tol = c->P.res_tol; a.res_check_every = c->P.res_check_every;
     a.part_iters = c->part_iters.p; a.part_res_sq = c->part_res_sq.p; a.status = c->status.p;
+    if (c->has_boxes) { a.row_full = c->row_full.p; a.rfull = c->rfull.p; }
     return a;
 }
 
@@ -998,6 +1012,7 @@ void release_all(ovl_ctx *c) {
     c->class_order.release(); c->colour_order.release(); c->solve_C.release(); c->col_off2.release();
     c->row_owner.release();
     c->pair_of_row2.release(); c->lb_loads.release();
+    c->half.release(); c->iib.release(); c->c_p.release(); c->row_full.release(); c->rfull.release();
 }
 
 
@@ -1061,14 +1076,21 @@ ovl_status ovl_scene_upload(ovl_ctx *c, const ovl_scene_desc *d) {
             return fail(c, OVL_ERR_ARG, "scene: joints missing");
         if (!d->scene_mu || !d->scene_dt || !d->scene_flags || !d->scene_gamma || !d->scene_beta || !d->n_sets)
             return fail(c, OVL_ERR_ARG, "scene: per-scene arrays are required");
+        // boxes: extents finite and >= 0; a box's radius bounds it (the broad
+        // phase tests bounding spheres)
+        bool boxes = false;
         if (d->half_extents)
-            for (size_t i = 0; i < 3 * (size_t)n; ++i) {
-                const float h = d->half_extents[i];
-                if (!(h >= 0.f) || !std::isfinite(h))
-                    return fail(c, OVL_ERR_ARG, "scene: half extents must be finite and >= 0");
-                if (h > 0.f)
-                    return fail(c, OVL_ERR_ARG, "scene: box bodies are not simulated by the step yet "
-                                                "(their contacts: ovl_box_scene_contacts)");
+            for (int b = 0; b < n; ++b) {
+                const float *h = d->half_extents + 3 * (size_t)b;
+                for (int k = 0; k < 3; ++k)
+                    if (!(h[k] >= 0.f) || !std::isfinite(h[k]))
+                        return fail(c, OVL_ERR_ARG, "scene: half extents must be finite and >= 0");
+                if (h[0] > 0.f || h[1] > 0.f || h[2] > 0.f) {
+                    boxes = true;
+                    const double hh = std::sqrt((double)h[0] * h[0] + (double)h[1] * h[1] + (double)h[2] * h[2]);
+                    if ((double)d->radius[b] < hh * (1.0 - 1e-6))
+                        return fail(c, OVL_ERR_ARG, "scene: a box's radius must bound it (>= |half extents|)");
+                }
             }
         std::vector<int> sob(n, 0);
         if (d->scene_of_body) std::copy(d->scene_of_body, d->scene_of_body + n, sob.begin());
@@ -1199,6 +1221,29 @@ ovl_status ovl_scene_upload(ovl_ctx *c, const ovl_scene_desc *d) {
         reset_warmstart(c);
         CK(cudaMemsetAsync(c->status.p, 0, 4 * sizeof(int), s));
         CK(cudaStreamSynchronize(s));
+        // boxes: half extents and the body-frame inverse inertia of a solid box,
+        // 1/I_k = 3 (1/m) / (h_j^2 + h_l^2)
+        c->has_boxes = boxes;
+        c->h_half.assign(3 * (size_t)n, 0.f);
+        if (boxes) {
+            std::copy(d->half_extents, d->half_extents + 3 * (size_t)n, c->h_half.begin());
+            std::vector<float4> hv(n), iv(n);
+            for (int b = 0; b < n; ++b) {
+                const float *h = d->half_extents + 3 * (size_t)b;
+                const float im = d->inv_mass[b];
+                hv[b] = make_float4(h[0], h[1], h[2], 0.f);
+                float i3[3] = {0.f, 0.f, 0.f};
+                if (h[0] > 0.f || h[1] > 0.f || h[2] > 0.f)
+                    for (int k = 0; k < 3; ++k) {
+                        const float a = h[(k + 1) % 3], e = h[(k + 2) % 3];
+                        i3[k] = im > 0.f ? 3.f * im / (a * a + e * e) : 0.f;
+                    }
+                iv[b] = make_float4(i3[0], i3[1], i3[2], 0.f);
+            }
+            upload(c->half, hv.data(), (size_t)n, s);
+            upload(c->iib, iv.data(), (size_t)n, s);
+            CK(cudaStreamSynchronize(s));
+        }
         c->step_index = 0;
         c->have_step = false;
         c->has_scene = true;
@@ -1440,6 +1485,22 @@ ovl_status ovl_read_stats(ovl_ctx *c, ovl_stats *out) {
         out->solve_ctas_masses = c->last_ctas_masses;
         out->lb_candidates = c->lb_candidates;
         out->lb_host_ms = c->lb_host_ms;
+        return OVL_OK;
+    });
+}
+
+ovl_status ovl_read_contact_points(ovl_ctx *c, int32_t *k, float *point) {
+    return guarded(c, [&]() -> ovl_status {
+        if (!c->have_step) return fail(c, OVL_ERR_ARG, "no step has run");
+        std::vector<float4> h_p(c->nc, make_float4(0.f, 0.f, 0.f, 0.f));
+        if (c->has_boxes) download(h_p.data(), c->c_p.p, c->nc, c->stream);
+        CK(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < c->nc; ++i) {
+            int32_t kk = 0;
+            std::memcpy(&kk, &h_p[i].w, sizeof kk);   // stored as the float's bits
+            if (k) k[i] = c->has_boxes ? kk : 0;
+            if (point) { point[3 * i] = h_p[i].x; point[3 * i + 1] = h_p[i].y; point[3 * i + 2] = h_p[i].z; }
+        }
         return OVL_OK;
     });
 }

@@ -31,6 +31,8 @@ struct ovl_ctx {
 
     // scene (host copies)
     bool has_scene = false;
+    bool has_boxes = false;          // some body has positive half extents
+    std::vector<float> h_half;       // [n][3] half extents (zeros: a sphere)
     HostScene hs;
     int n = 0, np = 0, nj = 0, ns = 0, n_parts = 0, beta_max = 0;
     std::vector<float> h_radius, h_im;
@@ -49,6 +51,7 @@ struct ovl_ctx {
     DBuf<float4> janc;
     DBuf<long long> vb_base;
     DBuf<uint64_t> mask;
+    DBuf<float4> half, iib;   // boxes: half extents; body-frame inverse inertia diagonal (1/I_x, 1/I_y, 1/I_z)
 
     // step buffers
     DBuf<int> status;
@@ -58,6 +61,7 @@ struct ovl_ctx {
     long long nb_total = 0;
     DBuf<int2> c_ab;
     DBuf<float4> c_n, c_t1;
+    DBuf<float4> c_p;          // contact point, manifold index in w (contexts with boxes)
     DBuf<int> deg, tptr, cursor2, tcol, ucount, row_ptr, col;
     DBuf<int> entry_count, entry_ptr, entry_body, entry_part, entry_slot, part_list, part_count,
         part_bstart;
@@ -97,6 +101,8 @@ struct ovl_ctx {
     std::vector<int> h_class_C;                  // CTAs per worker of the last per-worker plan
     DBuf<int> solve_C, col_off2, pair_of_row2;   // solve: CTAs per worker, rows grouped by owner CTA
     DBuf<uint8_t> row_owner;                     // owner CTA of every row (scratch of the grouping)
+    DBuf<uint8_t> row_full;                      // rows with a box end (contexts with boxes)
+    DBuf<float4> rfull;                          // their records, FULL_ROW_WORDS float4 per row
     cudaStream_t aux[5] = {};                    // side streams of the per-class solve launches
     cudaStream_t geo_stream = nullptr;           // the geodesic weights, beside colouring and solve
     cudaEvent_t geo_fork = nullptr, geo_join = nullptr;

@@ -1,7 +1,8 @@
 // k_box.cu -- box contact geometry (box-plane, sphere-box, box-box) over
 // arrays of pairs, one thread per pair on the GPU, or the same functions on
-// the host.  This file is built without FMA contraction on either side, so
-// the two runs give the same bits.  The boxes are the bodies of the paper's
+// the host, computed in FP64 from the FP32 inputs and rounded once.  This
+// file is built without FMA contraction on either side, so the two runs
+// give the same bits.  The boxes are the bodies of the paper's
 // Building and Bridge scenes (Section 6); the step does not use these
 // contacts yet.
 #include <stdint.h>
@@ -49,24 +50,25 @@ struct BoxBoxArgs {
     PairOut o;
 };
 
-__host__ __device__ void write_points(const PairOut &o, int i, int k, const float3 *p, const float *g, float3 nrm) {
+// the FP64 results, each rounded once to FP32
+__host__ __device__ void write_points(const PairOut &o, int i, int k, const double3 *p, const double *g, double3 nrm) {
     o.count[i] = k;
     for (int j = 0; j < k; ++j) {
-        o.points[12 * (size_t)i + 3 * j] = p[j].x;
-        o.points[12 * (size_t)i + 3 * j + 1] = p[j].y;
-        o.points[12 * (size_t)i + 3 * j + 2] = p[j].z;
-        o.gaps[4 * (size_t)i + j] = g[j];
+        o.points[12 * (size_t)i + 3 * j] = (float)p[j].x;
+        o.points[12 * (size_t)i + 3 * j + 1] = (float)p[j].y;
+        o.points[12 * (size_t)i + 3 * j + 2] = (float)p[j].z;
+        o.gaps[4 * (size_t)i + j] = (float)g[j];
     }
-    o.normal[3 * (size_t)i] = nrm.x;
-    o.normal[3 * (size_t)i + 1] = nrm.y;
-    o.normal[3 * (size_t)i + 2] = nrm.z;
+    o.normal[3 * (size_t)i] = (float)nrm.x;
+    o.normal[3 * (size_t)i + 1] = (float)nrm.y;
+    o.normal[3 * (size_t)i + 2] = (float)nrm.z;
 }
 
 __host__ __device__ void box_plane_one(const BoxPlaneArgs &a, int i) {
     const box::Obb B = obb_of(a.pose + 7 * (size_t)i, a.half + 3 * (size_t)i);
     const float *pl = a.plane + 4 * (size_t)i;
-    float3 p[4], n;
-    float g[4];
+    double3 p[4], n;
+    double g[4];
     const int k = box::box_plane(B, make_float4(pl[0], pl[1], pl[2], pl[3]), a.margin, p, g, n);
     write_points(a.o, i, k, p, g, n);
 }
@@ -74,18 +76,18 @@ __host__ __device__ void box_plane_one(const BoxPlaneArgs &a, int i) {
 __host__ __device__ void sphere_box_one(const SphereBoxArgs &a, int i) {
     const box::Obb B = obb_of(a.pose + 7 * (size_t)i, a.half + 3 * (size_t)i);
     const float *s = a.sphere + 4 * (size_t)i;
-    float3 p, n;
-    float g;
-    const int k = box::sphere_box(make_float3(s[0], s[1], s[2]), s[3], B, a.margin, p, n, g);
+    double3 p, n;
+    double g;
+    const int k = box::sphere_box(box::d3(s[0], s[1], s[2]), s[3], B, a.margin, p, n, g);
     write_points(a.o, i, k, &p, &g, n);
-    a.o.gaps[4 * (size_t)i] = g;   // the gap is reported with or without a contact
+    a.o.gaps[4 * (size_t)i] = (float)g;   // the gap is reported with or without a contact
 }
 
 __host__ __device__ void box_box_one(const BoxBoxArgs &a, int i) {
     const box::Obb A = obb_of(a.pose_a + 7 * (size_t)i, a.half_a + 3 * (size_t)i);
     const box::Obb B = obb_of(a.pose_b + 7 * (size_t)i, a.half_b + 3 * (size_t)i);
-    float3 p[4], n = make_float3(0.f, 0.f, 0.f);
-    float g[4], sep = 0.f;
+    double3 p[4], n = box::d3(0.0, 0.0, 0.0);
+    double g[4], sep = 0.0;
     int axis = -1;
     const int k = box::box_box(A, B, a.margin, p, g, n, axis, sep);
     write_points(a.o, i, k, p, g, n);
@@ -142,11 +144,11 @@ __host__ __device__ int scene_contacts_of(const SceneArgs &A, int a, bool write)
     const bool boxa = is_box3(A.half + 3 * (size_t)a);
     int64_t o = write ? A.offset[a] : 0;
     int cnt = 0;
-    auto put = [&](int b, int kk, float gap, float3 n, float3 p) {
+    auto put = [&](int b, int kk, double gap, double3 n, double3 p) {
         if (write) {
-            A.ab[2 * o] = a; A.ab[2 * o + 1] = b; A.k[o] = kk; A.phi[o] = gap;
-            A.normal[3 * o] = n.x; A.normal[3 * o + 1] = n.y; A.normal[3 * o + 2] = n.z;
-            A.point[3 * o] = p.x; A.point[3 * o + 1] = p.y; A.point[3 * o + 2] = p.z;
+            A.ab[2 * o] = a; A.ab[2 * o + 1] = b; A.k[o] = kk; A.phi[o] = (float)gap;
+            A.normal[3 * o] = (float)n.x; A.normal[3 * o + 1] = (float)n.y; A.normal[3 * o + 2] = (float)n.z;
+            A.point[3 * o] = (float)p.x; A.point[3 * o + 1] = (float)p.y; A.point[3 * o + 2] = (float)p.z;
             ++o;
         }
         ++cnt;
@@ -159,19 +161,20 @@ __host__ __device__ int scene_contacts_of(const SceneArgs &A, int a, bool write)
             if (!box::spheres_touch(ca, cb, A.radius[a], A.radius[b], A.margin)) continue;
             const bool boxb = is_box3(A.half + 3 * (size_t)b);
             if (!boxa && !boxb) {
-                // two spheres: one contact at the midpoint of the surfaces' gap
-                const float3 d = box::sub(cb, ca);
-                const float L = sqrtf(box::dot(d, d));
-                const float3 n = L > 0.f ? box::scl(d, 1.f / L) : make_float3(0.f, 0.f, 1.f);
-                put(b, 0, L - A.radius[a] - A.radius[b], n, box::add(ca, box::scl(n, A.radius[a])));
+                // two spheres: one contact, the gap in FP64
+                const double3 d = box::sub(box::to_d(cb), box::to_d(ca));
+                const double L = sqrt(box::dot(d, d));
+                const double3 n = L > 0.0 ? box::scl(d, 1.0 / L) : box::d3(0.0, 0.0, 1.0);
+                put(b, 0, (L - (double)A.radius[a]) - (double)A.radius[b], n,
+                    box::add(box::to_d(ca), box::scl(n, (double)A.radius[a])));
                 continue;
             }
-            float3 pts[4], n;
-            float gaps[4];
+            double3 pts[4], n;
+            double gaps[4];
             if (boxa && boxb) {
                 const box::Obb Ba = obb_of(sa, A.half + 3 * (size_t)a), Bb = obb_of(sb, A.half + 3 * (size_t)b);
                 int axis;
-                float sep;
+                double sep;
                 const int m = box::box_box(Ba, Bb, A.margin, pts, gaps, n, axis, sep);
                 for (int i = 0; i < m; ++i) put(b, i, gaps[i], n, pts[i]);
             } else {
@@ -179,9 +182,9 @@ __host__ __device__ int scene_contacts_of(const SceneArgs &A, int a, bool write)
                 const int sph = boxa ? b : a, bx = boxa ? a : b;
                 const float *ss = A.state + 13 * (size_t)sph, *sx = A.state + 13 * (size_t)bx;
                 const box::Obb B = obb_of(sx, A.half + 3 * (size_t)bx);
-                float gap;
-                if (box::sphere_box(pos_of(ss), A.radius[sph], B, A.margin, pts[0], n, gap))
-                    put(b, 0, gap, sph == a ? n : box::scl(n, -1.f), pts[0]);
+                double gap;
+                if (box::sphere_box(box::to_d(pos_of(ss)), A.radius[sph], B, A.margin, pts[0], n, gap))
+                    put(b, 0, gap, sph == a ? n : box::scl(n, -1.0), pts[0]);
             }
         }
     }
@@ -191,14 +194,15 @@ __host__ __device__ int scene_contacts_of(const SceneArgs &A, int a, bool write)
             const float4 pl = make_float4(A.planes[4 * p], A.planes[4 * p + 1], A.planes[4 * p + 2], A.planes[4 * p + 3]);
             if (!box::sphere_plane_touch(ca, A.radius[a], pl, A.margin)) continue;
             if (boxa) {
-                float3 pts[4], n;
-                float gaps[4];
+                double3 pts[4], n;
+                double gaps[4];
                 const int m = box::box_plane(obb_of(sa, A.half + 3 * (size_t)a), pl, A.margin, pts, gaps, n);
                 for (int i = 0; i < m; ++i) put(A.n + p, i, gaps[i], n, pts[i]);
             } else {
-                const float dotp = (pl.x * ca.x + pl.y * ca.y) + pl.z * ca.z;
-                const float3 n = make_float3(-pl.x, -pl.y, -pl.z);
-                put(A.n + p, 0, (dotp - pl.w) - A.radius[a], n, box::add(ca, box::scl(n, A.radius[a])));
+                const double dotp = ((double)pl.x * ca.x + (double)pl.y * ca.y) + (double)pl.z * ca.z;
+                const double3 n = box::d3(-pl.x, -pl.y, -pl.z);
+                put(A.n + p, 0, (dotp - (double)pl.w) - (double)A.radius[a], n,
+                    box::add(box::to_d(ca), box::scl(n, (double)A.radius[a])));
             }
         }
     if (!write) A.count_of[a] = cnt;

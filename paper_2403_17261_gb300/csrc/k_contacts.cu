@@ -13,6 +13,14 @@
 // Output order is canonical (ascending (a, b), planes numbered after the
 // bodies) without a global sort: a per-body count + scan gives each body a
 // slot range, and each body sorts its own (few) partners.
+//
+// Boxes (the paper's Building and Bridge bodies, Section 6): a pair with a
+// box end is a candidate when the bounding spheres (radius >= |h|) pass the
+// same FP32 test, and the FP64 box geometry of box_geom.cuh (this file is
+// built without contraction) then gives 0-4 contacts: the manifold, in
+// (a, b, k) order, each with its point.  Counting and writing run the same
+// functions on the same inputs, so they agree.
+#include "box_geom.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 #include "geom.cuh"
@@ -62,6 +70,55 @@ __device__ __forceinline__ float plane_gap(float4 p, float4 pl) {
     return __fsub_rn(__fsub_rn(dotp, pl.w), p.w);
 }
 
+// ---- boxes ------------------------------------------------------------------
+__device__ __forceinline__ bool is_box(const float4 *half, int b) {
+    if (!half) return false;
+    const float4 h = half[b];
+    return h.x > 0.f || h.y > 0.f || h.z > 0.f;
+}
+
+__device__ __forceinline__ box::Obb obb_at(const float4 *st, const float4 *half, int b) {
+    const float4 x = st[4 * b], q = st[4 * b + 1], h = half[b];
+    return box::make_obb(make_float3(x.x, x.y, x.z), q, make_float3(h.x, h.y, h.z));
+}
+
+// contacts of a pair with a box end (a < b, both bodies): points, gaps and
+// the normal from a towards b; returns the count (0-4)
+__device__ int box_pair(const float4 *st, const float4 *half, const float *radius_w, int a, int b, float margin,
+                        double3 *pts, double *gaps, double3 &nrm) {
+    const bool ba = is_box(half, a), bb = is_box(half, b);
+    if (ba && bb) {
+        int axis;
+        double sep;
+        return box::box_box(obb_at(st, half, a), obb_at(st, half, b), margin, pts, gaps, nrm, axis, sep);
+    }
+    // one sphere: sphere_box's normal runs from the sphere to the box
+    const int sph = ba ? b : a, bx = ba ? a : b;
+    const float4 s = st[4 * sph];
+    double gap;
+    const int hit = box::sphere_box(box::d3(s.x, s.y, s.z), s.w, obb_at(st, half, bx), margin, pts[0], nrm, gap);
+    if (sph != a) nrm = box::scl(nrm, -1.0);
+    gaps[0] = gap;
+    (void)radius_w;
+    return hit;
+}
+
+// a box against a plane (after the bounding-sphere test)
+__device__ int box_plane_pair(const float4 *st, const float4 *half, int a, float4 pl, float margin, double3 *pts,
+                              double *gaps, double3 &nrm) {
+    return box::box_plane(obb_at(st, half, a), pl, margin, pts, gaps, nrm);
+}
+
+__device__ __forceinline__ void write_box_contact(int o, int a, int b, int k, double3 p, double gap, double3 n,
+                                                  int2 *c_ab, float4 *c_n, float4 *c_t1, float4 *c_p) {
+    const float3 nf = box::to_f(n);
+    const float3 t = tangent_from(nf, tangent_axis(nf.x, nf.y, nf.z));
+    c_ab[o] = make_int2(a, b);
+    c_n[o] = make_float4(nf.x, nf.y, nf.z, (float)gap);
+    c_t1[o] = make_float4(t.x, t.y, t.z, 0.f);
+    c_p[o] = make_float4((float)p.x, (float)p.y, (float)p.z, __int_as_float(k));
+}
+
 // neighbours b > a of body a (sorted ascending) + its plane contacts
 __global__ void k_find_pairs(const float4 *__restrict__ st, const float *__restrict__ im, int n,
                              const int *__restrict__ sob, const int *__restrict__ scene_flags,
@@ -71,7 +128,7 @@ __global__ void k_find_pairs(const float4 *__restrict__ st, const float *__restr
                              const int *__restrict__ plane_list, float margin,
                              int *__restrict__ nb_list, const long long *__restrict__ nb_off,
                              int *__restrict__ nb_count, int *__restrict__ contact_count,
-                             int *__restrict__ status) {
+                             int *__restrict__ status, const float4 *__restrict__ half) {
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
         const int s = sob[a];
         const float4 pa = st[4 * a];   // .w = radius
@@ -120,14 +177,32 @@ __global__ void k_find_pairs(const float4 *__restrict__ st, const float *__restr
         if (!spilled)
             for (int j = 0; j < cnt; ++j) gl[j] = local[j];
         nb_count[a] = cnt;
-        int np_ = 0;
-        if (dyn_a) {
-            for (int k = plane_ptr[s]; k < plane_ptr[s + 1]; ++k) {
-                const float4 pl = planes[plane_list[k]];
-                if (plane_gap(pa, pl) <= margin) ++np_;
+        // contacts: one per sphere pair, 0-4 per pair with a box end
+        int nct = cnt;
+        if (half) {
+            const int *lst = spilled ? gl : local;
+            nct = 0;
+            for (int j = 0; j < cnt; ++j) {
+                const int b = lst[j];
+                if (!is_box(half, a) && !is_box(half, b)) { ++nct; continue; }
+                double3 pts[4], nrm;
+                double gaps[4];
+                nct += box_pair(st, half, nullptr, a, b, margin, pts, gaps, nrm);
             }
         }
-        contact_count[a] = cnt + np_;
+        int np_ = 0;
+        if (dyn_a) {
+            const bool box_a = is_box(half, a);
+            for (int k = plane_ptr[s]; k < plane_ptr[s + 1]; ++k) {
+                const float4 pl = planes[plane_list[k]];
+                if (plane_gap(pa, pl) > margin) continue;   // the (bounding) sphere test
+                if (!box_a) { ++np_; continue; }
+                double3 pts[4], nrm;
+                double gaps[4];
+                np_ += box_plane_pair(st, half, a, pl, margin, pts, gaps, nrm);
+            }
+        }
+        contact_count[a] = nct + np_;
     }
 }
 
@@ -138,7 +213,8 @@ __global__ void k_write_contacts(const float4 *__restrict__ st, const float *__r
                                  const long long *__restrict__ nb_off,
                                  const int *__restrict__ nb_count, const int *__restrict__ cstart,
                                  int2 *__restrict__ c_ab, float4 *__restrict__ c_n,
-                                 float4 *__restrict__ c_t1) {
+                                 float4 *__restrict__ c_t1, const float4 *__restrict__ half,
+                                 float4 *__restrict__ c_p) {
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
         const float4 pa = st[4 * a];
         int o = cstart[a];
@@ -146,6 +222,13 @@ __global__ void k_write_contacts(const float4 *__restrict__ st, const float *__r
         for (int j = 0; j < cnt; ++j) {
             const int b = nb_list[nb_off[a] + j];
             const float4 pb = st[4 * b];
+            if (is_box(half, a) || is_box(half, b)) {
+                double3 pts[4], nrm;
+                double gaps[4];
+                const int m = box_pair(st, half, nullptr, a, b, margin, pts, gaps, nrm);
+                for (int k = 0; k < m; ++k) write_box_contact(o++, a, b, k, pts[k], gaps[k], nrm, c_ab, c_n, c_t1, c_p);
+                continue;
+            }
             float dx = __fsub_rn(pb.x, pa.x), dy = __fsub_rn(pb.y, pa.y), dz = __fsub_rn(pb.z, pa.z);
             float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
             float L = __fsqrt_rn(d2);
@@ -170,14 +253,24 @@ __global__ void k_write_contacts(const float4 *__restrict__ st, const float *__r
             c_ab[o] = make_int2(a, b);
             c_n[o] = make_float4(nn.x, nn.y, nn.z, phi);
             c_t1[o] = make_float4(t.x, t.y, t.z, 0.f);
+            if (c_p) c_p[o] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
             ++o;
         }
         if (im[a] > 0.0f) {
             const int s = sob[a];
+            const bool box_a = is_box(half, a);
             for (int k2 = plane_ptr[s]; k2 < plane_ptr[s + 1]; ++k2) {
                 const int pidx = plane_list[k2];
                 const float4 pl = planes[pidx];
-                if (plane_gap(pa, pl) > margin) continue;   // the FP32 decision
+                if (plane_gap(pa, pl) > margin) continue;   // the FP32 (bounding-sphere) decision
+                if (box_a) {
+                    double3 pts[4], nrm;
+                    double gaps[4];
+                    const int m = box_plane_pair(st, half, a, pl, margin, pts, gaps, nrm);
+                    for (int k = 0; k < m; ++k)
+                        write_box_contact(o++, a, n + pidx, k, pts[k], gaps[k], nrm, c_ab, c_n, c_t1, c_p);
+                    continue;
+                }
                 // the gap itself from large coordinates: FP64, then rounded once
                 const float gap = (float)((double)pl.x * pa.x + (double)pl.y * pa.y +
                                           (double)pl.z * pa.z - (double)pl.w - (double)pa.w);
@@ -188,6 +281,7 @@ __global__ void k_write_contacts(const float4 *__restrict__ st, const float *__r
                 c_ab[o] = make_int2(a, n + pidx);
                 c_n[o] = make_float4(nn.x, nn.y, nn.z, gap);
                 c_t1[o] = make_float4(t.x, t.y, t.z, 0.f);
+                if (c_p) c_p[o] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
                 ++o;
             }
         }
@@ -257,10 +351,12 @@ __global__ void k_adj_compact(const int *__restrict__ tptr, const int *__restric
 // disjoint (activation-only steps: activations only add workers, so a pair
 // that shares a worker now can never reach Algorithm 6's activation branch later).
 __global__ void k_lb_flags(const int2 *__restrict__ c_ab, int nc, const float *__restrict__ im, int n,
-                           const uint64_t *__restrict__ mask, int disjoint_only, int *__restrict__ flag) {
+                           const uint64_t *__restrict__ mask, int disjoint_only, int *__restrict__ flag,
+                           const float4 *__restrict__ c_p) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
         int2 e = c_ab[i];
-        int f = e.y < n && im[e.x] > 0.0f && im[e.y] > 0.0f;
+        // a box pair's manifold takes part once (its first point)
+        int f = e.y < n && im[e.x] > 0.0f && im[e.y] > 0.0f && !(c_p && __float_as_int(c_p[i].w) != 0);
         if (f && disjoint_only) f = (mask[e.x] & mask[e.y]) == 0ull;
         flag[i] = f;
     }
@@ -297,7 +393,7 @@ void launch_bucket_fill(const ContactArgs &a, cudaStream_t s) {
 void launch_find_pairs(const ContactArgs &a, cudaStream_t s) {
     k_find_pairs<<<grid1d(a.n, 128), 128, 0, s>>>(
         a.st, a.im, a.n, a.sob, a.scene_flags, a.cell, a.bucket_start, a.items, a.tmask, a.planes,
-        a.plane_ptr, a.plane_list, a.margin, a.nb_list, a.nb_off, a.nb_count, a.contact_count, a.status);
+        a.plane_ptr, a.plane_list, a.margin, a.nb_list, a.nb_off, a.nb_count, a.contact_count, a.status, a.half);
     note_launch();
     CK(cudaGetLastError());
 }
@@ -306,7 +402,7 @@ void launch_write_contacts(const ContactArgs &a, cudaStream_t s) {
     k_write_contacts<<<grid1d(a.n, 128), 128, 0, s>>>(a.st, a.im, a.n, a.sob, a.planes, a.plane_ptr,
                                                       a.plane_list, a.margin, a.nb_list, a.nb_off,
                                                       a.nb_count, a.contact_start, a.c_ab, a.c_n,
-                                                      a.c_t1);
+                                                      a.c_t1, a.half, a.c_p);
     note_launch();
     CK(cudaGetLastError());
 }
@@ -345,8 +441,10 @@ namespace {
 
 // |P_w| of every worker: one count per set bit of every mask; a block-local
 // histogram when the workers fit shared memory
-__global__ void k_contact_degree(const int2 *__restrict__ c_ab, int nc, int n, int *__restrict__ deg) {
+__global__ void k_contact_degree(const int2 *__restrict__ c_ab, int nc, int n, int *__restrict__ deg,
+                                 const float4 *__restrict__ c_p) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        if (c_p && __float_as_int(c_p[i].w) != 0) continue;   // a box manifold counts once
         const int2 e = c_ab[i];
         atomicAdd(&deg[e.x], 1);
         if (e.y < n) atomicAdd(&deg[e.y], 1);
@@ -381,10 +479,10 @@ __global__ void k_worker_loads(const uint64_t *mask, const int *sob, const int *
 
 }  // namespace
 
-void launch_contact_degree(const int2 *c_ab, int nc, int n, int *deg, cudaStream_t s) {
+void launch_contact_degree(const int2 *c_ab, int nc, int n, int *deg, const float4 *c_p, cudaStream_t s) {
     CK(cudaMemsetAsync(deg, 0, sizeof(int) * (size_t)n, s));
     if (nc <= 0) return;
-    k_contact_degree<<<grid1d(nc, 256), 256, 0, s>>>(c_ab, nc, n, deg);
+    k_contact_degree<<<grid1d(nc, 256), 256, 0, s>>>(c_ab, nc, n, deg, c_p);
     note_launch();
     CK(cudaGetLastError());
 }
@@ -400,9 +498,9 @@ void launch_worker_loads(const uint64_t *mask, const int *sob, const int *part_b
 }
 
 void launch_lb_flags(const int2 *c_ab, int nc, const float *im, int n, const uint64_t *mask,
-                     int disjoint_only, int *flag, cudaStream_t s) {
+                     int disjoint_only, int *flag, const float4 *c_p, cudaStream_t s) {
     if (!nc) return;
-    k_lb_flags<<<grid1d(nc, 256), 256, 0, s>>>(c_ab, nc, im, n, mask, disjoint_only, flag);
+    k_lb_flags<<<grid1d(nc, 256), 256, 0, s>>>(c_ab, nc, im, n, mask, disjoint_only, flag, c_p);
     note_launch();
     CK(cudaGetLastError());
 }

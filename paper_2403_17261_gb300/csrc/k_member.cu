@@ -184,6 +184,11 @@ __global__ void k_worker_cost_keys(const int *part_pstart, int P, uint32_t *keys
     }
 }
 
+// manifold index of contact i (0 without boxes)
+__device__ __forceinline__ int contact_point(const MemberArgs &a, int i) {
+    return a.c_p ? __float_as_int(a.c_p[i].w) : 0;
+}
+
 __global__ void k_pair_setup(MemberArgs a, WarmArgs ws, int np) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
         int i = a.ps_cons[k], p = a.ps_part[k];
@@ -193,7 +198,8 @@ __global__ void k_pair_setup(MemberArgs a, WarmArgs ws, int np) {
         uint64_t key;
         if (i < a.nc) {
             e = a.c_ab[i];
-            key = ((uint64_t)(uint32_t)e.x << 32) | (uint32_t)e.y;
+            // a << 32 | b << 2 | k: key order is the canonical contact order
+            key = ((uint64_t)(uint32_t)e.x << 32) | ((uint64_t)(uint32_t)e.y << 2) | (uint64_t)contact_point(a, i);
         } else {
             e = a.jab[i - a.nc];
             key = (1ull << 62) | (uint64_t)(i - a.nc);
@@ -554,6 +560,47 @@ __device__ __forceinline__ int pack_slots(int2 sl, int *status) {
     return (int)(a | (b << 16));
 }
 
+__device__ __forceinline__ bool body_is_box(const float4 *half, int b) {
+    if (!half || b < 0) return false;
+    const float4 h = half[b];
+    return h.x > 0.f || h.y > 0.f || h.z > 0.f;
+}
+
+// I^-1 v for body b: a box's R diag(1/I) R^T (R from its blended
+// orientation), a sphere's isotropic 1/I
+__device__ float3 inv_inertia_times(const RowArgs &a, int b, float3 v) {
+    if (!body_is_box(a.half, b)) {
+        const float ii = a.st[4 * b + 3].w;
+        return make_float3(ii * v.x, ii * v.y, ii * v.z);
+    }
+    const float4 q = a.st[4 * b + 1], d = a.iib[b];
+    const float3 qc = make_float3(-q.y, -q.z, -q.w);                // conjugate: world -> body
+    const float3 lb = quat_rotate(make_float4(q.x, qc.x, qc.y, qc.z), v);
+    return quat_rotate(q, make_float3(d.x * lb.x, d.y * lb.y, d.z * lb.z));
+}
+
+// one full row (see FULL_ROW_WORDS): lever arms rA, rB (world), ends ea, eb
+// (-1: static or not in this worker), directions dir[3], targets tg[3]
+__device__ void write_full_row(const RowArgs &a, int r, int ea, int eb, float3 rA, float3 rB, const float3 *dir,
+                               const float *tg) {
+    float4 *F = a.rfull + (size_t)r * FULL_ROW_WORDS;
+    const float imA = ea >= 0 ? a.st[4 * ea + 2].w : 0.f, imB = eb >= 0 ? a.st[4 * eb + 2].w : 0.f;
+    for (int i = 0; i < 3; ++i) {
+        const float3 d = dir[i];
+        const float3 jA = make_float3(rA.y * d.z - rA.z * d.y, rA.z * d.x - rA.x * d.z, rA.x * d.y - rA.y * d.x);
+        const float3 jB = make_float3(rB.y * d.z - rB.z * d.y, rB.z * d.x - rB.x * d.z, rB.x * d.y - rB.y * d.x);
+        const float3 iA = ea >= 0 ? inv_inertia_times(a, ea, jA) : make_float3(0.f, 0.f, 0.f);
+        const float3 iB = eb >= 0 ? inv_inertia_times(a, eb, jB) : make_float3(0.f, 0.f, 0.f);
+        const float s = (imA + imB) + ((jA.x * iA.x + jA.y * iA.y + jA.z * iA.z) + (jB.x * iB.x + jB.y * iB.y + jB.z * iB.z));
+        F[i] = make_float4(d.x, d.y, d.z, tg[i]);
+        F[3 + i] = make_float4(jA.x, jA.y, jA.z, s > 0.f ? 1.f / s : 0.f);
+        F[6 + i] = make_float4(iA.x, iA.y, iA.z, 0.f);
+        F[9 + i] = make_float4(jB.x, jB.y, jB.z, 0.f);
+        F[12 + i] = make_float4(iB.x, iB.y, iB.z, 0.f);
+    }
+    F[15] = make_float4(imA, imB, 0.f, 0.f);
+}
+
 __global__ void k_rows(RowArgs a) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.np; r += gridDim.x * blockDim.x) {
         const int k = a.pair_of_row[r];
@@ -561,6 +608,72 @@ __global__ void k_rows(RowArgs a) {
         const int2 sl = a.p_slot[k];
         const int scene = a.part_scene[a.ps_part[k]];
         const float h = a.dt_override > 0.f ? a.dt_override : a.scene_dt[scene];
+        if (a.row_full) {
+            // a constraint with a box end: the full row, plus the slots in the
+            // plain records (the solver reads its bodies through them)
+            const int2 ab = i < a.nc ? a.c_ab[i] : a.jab[i - a.nc];
+            const bool full = body_is_box(a.half, ab.x) || (ab.y < a.n && body_is_box(a.half, ab.y));
+            a.row_full[r] = full ? 1 : 0;
+            if (full) {
+                const int ea = sl.x >= 0 ? ab.x : -1, eb = sl.y >= 0 ? ab.y : -1;
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                float3 dir[3], rA = make_float3(0.f, 0.f, 0.f), rB = rA;
+                float tg[3];
+                if (i < a.nc) {
+                    const float4 nphi = a.c_n[i], t1 = a.c_t1[i], p = a.c_p[i];
+                    dir[0] = make_float3(nphi.x, nphi.y, nphi.z);
+                    dir[1] = make_float3(t1.x, t1.y, t1.z);
+                    dir[2] = make_float3(dir[0].y * dir[1].z - dir[0].z * dir[1].y, dir[0].z * dir[1].x - dir[0].x * dir[1].z,
+                                         dir[0].x * dir[1].y - dir[0].y * dir[1].x);
+                    const float4 xa = a.st[4 * ab.x];
+                    rA = make_float3(p.x - xa.x, p.y - xa.y, p.z - xa.z);
+                    if (ab.y < a.n) {
+                        const float4 xb = a.st[4 * ab.y];
+                        rB = make_float3(p.x - xb.x, p.y - xb.y, p.z - xb.z);
+                    }
+                    const float phi = nphi.w;
+                    tg[0] = phi > 0.f ? -phi / h : a.erp * fmaxf(-phi - a.slop, 0.f) / h;
+                    tg[1] = tg[2] = 0.f;
+                    a.r0[r] = z;
+                    a.r1[r] = make_float4(0.f, 0.f, 0.f, __int_as_float(pack_slots(sl, a.status)));
+                    a.r3[r] = z;
+                    a.r4[r] = z;
+                } else {
+                    const int j = i - a.nc;
+                    const float4 anA = a.janc[2 * j], anB = a.janc[2 * j + 1];
+                    float3 xA, xB;
+                    if (ab.x >= 0) {
+                        const float4 x = a.st[4 * ab.x], q = a.st[4 * ab.x + 1];
+                        rA = quat_rotate(q, make_float3(anA.x, anA.y, anA.z));
+                        xA = make_float3(x.x, x.y, x.z);
+                    } else {
+                        xA = make_float3(anA.x, anA.y, anA.z);
+                    }
+                    if (ab.y >= 0) {
+                        const float4 x = a.st[4 * ab.y], q = a.st[4 * ab.y + 1];
+                        rB = quat_rotate(q, make_float3(anB.x, anB.y, anB.z));
+                        xB = make_float3(x.x, x.y, x.z);
+                    } else {
+                        xB = make_float3(anB.x, anB.y, anB.z);
+                    }
+                    const float g = -a.erp / h;
+                    tg[0] = g * ((xB.x - xA.x) + (rB.x - rA.x));
+                    tg[1] = g * ((xB.y - xA.y) + (rB.y - rA.y));
+                    tg[2] = g * ((xB.z - xA.z) + (rB.z - rA.z));
+                    dir[0] = make_float3(1.f, 0.f, 0.f);
+                    dir[1] = make_float3(0.f, 1.f, 0.f);
+                    dir[2] = make_float3(0.f, 0.f, 1.f);
+                    a.r0[r] = z;
+                    a.r1[r] = z;
+                    a.r2[r] = make_float4(0.f, 0.f, 0.f, __int_as_float(pack_slots(sl, a.status)));
+                    a.r3[r] = z;
+                }
+                write_full_row(a, r, ea, eb, rA, rB, dir, tg);
+                a.rpair[r] = k;
+                a.rlam[r] = a.p_lam0[k];
+                continue;
+            }
+        }
         if (i < a.nc) {
             const int2 ab = a.c_ab[i];
             const float4 nphi = a.c_n[i];

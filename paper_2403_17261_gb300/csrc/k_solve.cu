@@ -357,6 +357,72 @@ __device__ __forceinline__ void solve_row(Body &A, Body &B, const Row &w, float 
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 
+// ---- full rows (a box end: general lever arms and inertia responses) -------
+__device__ __forceinline__ bool is_full(const SolveArgs &a, int r) { return a.row_full != nullptr && a.row_full[r]; }
+
+// impulse dl along direction i of a full row
+__device__ __forceinline__ void full_impulse(const float4 *F, int i, float imA, float imB, Body &A, Body &B,
+                                             float dl) {
+    const float3 d = f3(F[i]);
+    axpy(A.v, -imA * dl, d);
+    axpy(B.v, imB * dl, d);
+    axpy(A.w, -dl, f3(F[6 + i]));
+    axpy(B.w, dl, f3(F[12 + i]));
+}
+
+__device__ __forceinline__ float full_w(const float4 *F, int i, const Body &A, const Body &B) {
+    const float3 dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
+    return dot3(f3(F[i]), dv) + (dot3(f3(F[9 + i]), B.w) - dot3(f3(F[3 + i]), A.w));
+}
+
+// the three rows of a constraint with a box end: contact (normal >= 0,
+// tangents within +-mu lambda_n) or ball joint (unbounded)
+__device__ void full_rows(const SolveArgs &a, int r, bool joint, Body &A, Body &B, float mu, float4 &lam) {
+    const float4 *F = a.rfull + (size_t)r * FULL_ROW_WORDS;
+    const float imA = F[15].x, imB = F[15].y;
+    float l[3] = {lam.x, lam.y, lam.z};
+    for (int i = 0; i < 3; ++i) {
+        const float k = F[3 + i].w, target = F[i].w;
+        float ln = fmaf(k, target - full_w(F, i, A, B), l[i]);
+        if (!joint) ln = i == 0 ? fmaxf(ln, 0.f) : fminf(fmaxf(ln, -mu * l[0]), mu * l[0]);
+        const float dl = ln - l[i];
+        l[i] = ln;
+        full_impulse(F, i, imA, imB, A, B, dl);
+    }
+    lam = make_float4(l[0], l[1], l[2], lam.w);
+}
+
+__device__ void full_warm(const SolveArgs &a, int r, Body &A, Body &B, float4 lam) {
+    const float4 *F = a.rfull + (size_t)r * FULL_ROW_WORDS;
+    const float imA = F[15].x, imB = F[15].y;
+    full_impulse(F, 0, imA, imB, A, B, lam.x);
+    full_impulse(F, 1, imA, imB, A, B, lam.y);
+    full_impulse(F, 2, imA, imB, A, B, lam.z);
+}
+
+// a row of the sweep: full (box end) or plain
+template <class S>
+__device__ __forceinline__ void solve_any(const SolveArgs &a, int r, Body &A, Body &B, const Row &w, float mu,
+                                          float4 &lam) {
+    if (is_full(a, r)) full_rows(a, r, w.joint, A, B, mu, lam);
+    else solve_row<S>(A, B, w, mu, lam);
+}
+
+__device__ float full_residual_sq(const SolveArgs &a, int r, bool joint, const Body &A, const Body &B, float mu,
+                                  float4 lam) {
+    const float4 *F = a.rfull + (size_t)r * FULL_ROW_WORDS;
+    const float l[3] = {lam.x, lam.y, lam.z};
+    float s = 0.f;
+    for (int i = 0; i < 3; ++i) {
+        const float k = F[3 + i].w;
+        float p = l[i] + k * (F[i].w - full_w(F, i, A, B));
+        if (!joint) p = i == 0 ? fmaxf(p, 0.f) : clampf(p, -mu * l[0], mu * l[0]);
+        const float e = k > 0.f ? (l[i] - p) / k : 0.f;
+        s += e * e;
+    }
+    return s;
+}
+
 // residual (lambda - clamp(lambda + k (target - w), lo, hi)) / k of a row
 // group, squared and summed
 __device__ __forceinline__ float contact_residual_sq(const Body &A, const Body &B, float4 r0, float4 r1,
@@ -479,7 +545,9 @@ __device__ float rows_residual_sq(const SolveArgs &a, const S &st, const Buckets
                 const float4 lam = a.rlam[r];
                 Body A, B;
                 load_pair(st, w, A, B);
-                if (w.joint) {
+                if (is_full(a, r)) {
+                    sq += full_residual_sq(a, r, w.joint, A, B, mu, lam);
+                } else if (w.joint) {
                     sq += joint_residual_sq(A, B, w.x, w.y, w.z);
                 } else {
                     float3 t1;
@@ -535,7 +603,9 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
             fetch_row<S>(a, r, r >= jb, w);
             Body A, B;
             load_pair(st, w, A, B);
-            if (!w.joint) {
+            if (is_full(a, r)) {
+                full_warm(a, r, A, B, lam);
+            } else if (!w.joint) {
                 float3 t1;
                 float kn;
                 contact_frame<S>(w, A, B, t1, kn);
@@ -584,8 +654,8 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                     Body A, B, D, E;
                     load_pair(st, u, A, B);
                     load_pair(st, w, D, E);
-                    solve_row<S>(A, B, u, mu, xl);
-                    solve_row<S>(D, E, w, mu, yl);
+                    solve_any<S>(a, r, A, B, u, mu, xl);
+                    solve_any<S>(a, q, D, E, w, mu, yl);
                     store_pair(st, row_slots(u), A, B);
                     store_pair(st, row_slots(w), D, E);
                     a.rlam[r] = xl;
@@ -599,7 +669,7 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                     float4 lam = cur.l0;
                     Body A, B;
                     load_pair(st, w, A, B);
-                    solve_row<S>(A, B, w, mu, lam);
+                    solve_any<S>(a, r, A, B, w, mu, lam);
                     store_pair(st, row_slots(w), A, B);
                     a.rlam[r] = lam;
                 }
@@ -615,8 +685,8 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                         Body A, B, D, E;
                         load_pair(st, u, A, B);
                         load_pair(st, w, D, E);
-                        solve_row<S>(A, B, u, mu, xl);
-                        solve_row<S>(D, E, w, mu, yl);
+                        solve_any<S>(a, r, A, B, u, mu, xl);
+                        solve_any<S>(a, q, D, E, w, mu, yl);
                         store_pair(st, row_slots(u), A, B);
                         store_pair(st, row_slots(w), D, E);
                         a.rlam[r] = xl;
@@ -629,7 +699,7 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                     float4 lam = a.rlam[r];
                     Body A, B;
                     load_pair(st, w, A, B);
-                    solve_row<S>(A, B, w, mu, lam);
+                    solve_any<S>(a, r, A, B, w, mu, lam);
                     store_pair(st, row_slots(w), A, B);
                     a.rlam[r] = lam;
                 }

@@ -34,6 +34,8 @@ struct ContactArgs {
     float4 *c_n;
     float4 *c_t1;
     int *status;
+    const float4 *half;    // [n] box half extents (w unused), or NULL: no box in the context
+    float4 *c_p;           // [nc] contact point and, as int bits in w, the manifold index (box contexts)
 };
 void launch_cells(const ContactArgs &a, cudaStream_t s);
 void launch_bucket_fill(const ContactArgs &a, cudaStream_t s);
@@ -46,12 +48,12 @@ void launch_edge_fill(const int2 *c_ab, int nc, const int2 *jab, int nj, const f
 void launch_adj_unique(const int *tptr, int n, int *tcol, int *ucount, cudaStream_t s);
 // loads [P] := |P_w| of every worker from the masks
 // number of contacts each body is an end of (planes and static ends included)
-void launch_contact_degree(const int2 *c_ab, int nc, int n, int *deg, cudaStream_t s);
+void launch_contact_degree(const int2 *c_ab, int nc, int n, int *deg, const float4 *c_p, cudaStream_t s);
 // load of every worker: sum over its active bodies of 1 (+ deg[b] when deg != NULL)
 void launch_worker_loads(const uint64_t *mask, const int *sob, const int *part_base, const int *deg, int n, int P,
                          int *loads, cudaStream_t s);
 void launch_lb_flags(const int2 *c_ab, int nc, const float *im, int n, const uint64_t *mask,
-                     int disjoint_only, int *flag, cudaStream_t s);
+                     int disjoint_only, int *flag, const float4 *c_p, cudaStream_t s);
 void launch_lb_compact(const int2 *c_ab, int nc, const int *flag, const int *pos, int2 *out,
                        cudaStream_t s);
 void launch_adj_compact(const int *tptr, const int *tcol, int n, const int *row_ptr, int *col,
@@ -60,6 +62,7 @@ void launch_adj_compact(const int *tptr, const int *tcol, int n, const int *row_
 // ---- membership, pairs, warm start, colouring, rows (k_member.cu) ----------
 struct MemberArgs {
     int n, nc, nj, n_parts;
+    const float4 *c_p;         // contexts with boxes: manifold index of every contact (w), else NULL
     const float *im;
     const int *sob;
     const int *n_sets;       // per scene
@@ -166,8 +169,27 @@ struct RowArgs {
     int *rpair;                // [np] pair index of every row (canonical order)
     float4 *rlam;
     int *status;
+    // contexts with boxes (else NULL): contact points, half extents, body-frame
+    // inverse inertia diagonals; out: the full-row flag and record of every row
+    const float4 *c_p, *half, *iib;
+    uint8_t *row_full;
+    float4 *rfull;
 };
 void launch_rows(const RowArgs &a, cudaStream_t s);
+
+// A constraint with a box end (a contact touching a box, or a ball joint with
+// a box end) is a "full" row: its lever arms reach the contact point (or the
+// pivots) and a box's angular response is its world inverse inertia
+// R diag(1/I) R^T.  Per constraint FULL_ROW_WORDS float4, for its three
+// directions d_i (contact: n, t1, t2 = n x t1; joint: the world axes):
+//   [i]      (d_i, target_i)
+//   [3 + i]  (r_A x d_i, k_i)                k_i = 1 / (J_i M^-1 J_i^T)
+//   [6 + i]  (I_A^-1 (r_A x d_i), 0)
+//   [9 + i]  (r_B x d_i, 0)
+//   [12 + i] (I_B^-1 (r_B x d_i), 0)
+//   [15]     (1/m_A, 1/m_B, 0, 0)            (0 for a static end or one not in the worker)
+// The row's velocity is d_i.(v_B - v_A) + (r_B x d_i).w_B - (r_A x d_i).w_A.
+#define FULL_ROW_WORDS 16
 
 // ---- PGS solve + integration (k_solve.cu) ----------------------------------
 struct SolveArgs {
@@ -199,6 +221,8 @@ struct SolveArgs {
     int *part_iters;           // [P]
     double *part_res_sq;       // [P]
     int *status;
+    const uint8_t *row_full;   // contexts with boxes: rows read from rfull (FULL_ROW_WORDS each), else NULL
+    const float4 *rfull;
 };
 // masses: the shared-memory slots hold the inverse masses and inertias (32 B
 // per slot; contact rows read as two records); else 24 B per slot

@@ -47,7 +47,7 @@ EXPORTED = [
     "ovl_assign_overlap", "ovl_set_state", "ovl_read_state", "ovl_set_step_index",
     "ovl_set_warmstart", "ovl_read_warmstart", "ovl_step", "ovl_load_balance", "ovl_sync", "ovl_joint_error",
     "ovl_read_stats", "ovl_read_contacts", "ovl_read_graph", "ovl_read_entries", "ovl_read_pairs",
-    "ovl_read_worker_stats", "ovl_read_solve_plan", "ovl_step_n", "ovl_save", "ovl_load", "ovl_autotune_export", "ovl_autotune_import",
+    "ovl_read_worker_stats", "ovl_read_solve_plan", "ovl_read_contact_points", "ovl_step_n", "ovl_save", "ovl_load", "ovl_autotune_export", "ovl_autotune_import",
     "ovl_geodesics_static", "ovl_set_warmstart_mode", "ovl_read_features", "ovl_mlp_set_params",
     "ovl_mlp_get_params", "ovl_mlp_forward", "ovl_log_reserve", "ovl_log_enable", "ovl_log_size",
     "ovl_log_append", "ovl_log_read", "ovl_mlp_train", "ovl_mlp_grad", "ovl_mlp_loss",
@@ -141,6 +141,7 @@ def load_library(path: str | None = None):
         "ovl_read_pairs": [vp, _ip, _u64p, _ip, _fp],
         "ovl_read_worker_stats": [vp, _ip, C.POINTER(C.c_double), C.POINTER(C.c_int64), _ip],
         "ovl_read_solve_plan": [vp, _ip],
+        "ovl_read_contact_points": [vp, _ip, _fp],
         "ovl_step_n": [vp, C.c_float, C.c_int32, C.c_int32, _ip],
         "ovl_save": [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)],
         "ovl_load": [vp, vp, C.c_size_t],
@@ -229,10 +230,8 @@ class _SceneArrays:
 
     def __init__(self, scene):
         he = getattr(scene, "half_extents", None)
-        if he is not None and np.any(np.asarray(he) > 0):
-            raise OvlError(OVL_ERR_ARG, "box bodies are not simulated by the step yet (only their contact "
-                                        "functions and rows exist)")
         f32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+        self.half = None if he is None else f32(he).reshape(-1, 3)
         i32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.int32))
         self.state = f32(scene.state).reshape(-1, 13)
         self.radius, self.inv_mass = f32(scene.radius), f32(scene.inv_mass)
@@ -256,6 +255,7 @@ class _SceneArrays:
         d.scene_mu, d.scene_dt = _ptr(self.mu, _fp), _ptr(self.dt, _fp)
         d.scene_flags, d.scene_gamma = _ptr(self.flags, _ip), _ptr(self.gamma, _ip)
         d.scene_beta, d.n_sets = _ptr(self.beta, _ip), _ptr(self.n_sets, _ip)
+        d.half_extents = _ptr(self.half, _fp) if self.half is not None else None
         self.desc = d
 
 
@@ -664,6 +664,15 @@ class Simulation:
         _check(self.ctx, load_library().ovl_read_contacts(self.ctx, _ptr(ab, _ip), _ptr(phi, _fp),
                                                           _ptr(nn, _fp), _ptr(t1, _fp)))
         return ab[:m], phi[:m], nn[:m], t1[:m]
+
+    def contact_points(self):
+        """(manifold index [m], point [m,3]) of the last step's contacts;
+        zeros for sphere contacts."""
+        m = self.stats()["n_contacts"]
+        mm = max(m, 1)
+        k, p = np.zeros(mm, np.int32), np.zeros((mm, 3), np.float32)
+        _check(self.ctx, load_library().ovl_read_contact_points(self.ctx, _ptr(k, _ip), _ptr(p, _fp)))
+        return k[:m], p[:m]
 
     def graph(self):
         m = self.stats()["n_adjacency"]

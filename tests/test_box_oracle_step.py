@@ -35,8 +35,8 @@ def test_resting_box_carries_its_weight_and_keys_its_points():
     np.testing.assert_allclose(st[0, 7:13], 0, atol=1e-9)
     np.testing.assert_allclose(pr["lam"][:, 0].sum(), m * G * DT, rtol=1e-6)
     keys = np.sort(pr["key"].astype(np.uint64))
-    assert [int(k) >> 60 for k in keys] == [0, 1, 2, 3]
-    assert all(int(k) & ((1 << 60) - 1) == (0 << 32) | 1 for k in keys)   # body 0 against plane 0 (index n + 0)
+    assert [int(k) & 3 for k in keys] == [0, 1, 2, 3]                     # the manifold's points
+    assert all(int(k) >> 2 == 1 for k in keys)   # a = 0 (bits 32-57) against plane 0 (index n + 0 = 1)
 
 
 def test_sliding_box_loses_mu_g_dt():
@@ -56,7 +56,7 @@ def test_stack_of_two_boxes():
     st, pr = sim.state(), sim.pairs()
     np.testing.assert_allclose(st[:, 7:13], 0, atol=1e-7)
     key = pr["key"].astype(np.uint64)
-    b = key & np.uint64(0xFFFFFFFF)
+    b = (key & np.uint64(0xFFFFFFFF)) >> np.uint64(2)
     ground = b == np.uint64(2)          # plane 0 is body index n + 0 = 2
     np.testing.assert_allclose(pr["lam"][ground, 0].sum(), (m1 + m2) * G * DT, rtol=1e-5)
     np.testing.assert_allclose(pr["lam"][~ground, 0].sum(), m2 * G * DT, rtol=1e-5)
@@ -70,7 +70,7 @@ def test_sphere_resting_on_a_box():
     sim.step()
     st, pr = sim.state(), sim.pairs()
     np.testing.assert_allclose(st[:, 7:13], 0, atol=1e-7)
-    b = pr["key"].astype(np.uint64) & np.uint64(0xFFFFFFFF)
+    b = (pr["key"].astype(np.uint64) & np.uint64(0xFFFFFFFF)) >> np.uint64(2)
     np.testing.assert_allclose(pr["lam"][b == np.uint64(1), 0].sum(), ms * G * DT, rtol=1e-5)
     np.testing.assert_allclose(pr["lam"][b == np.uint64(2), 0].sum(), (mb + ms) * G * DT, rtol=1e-5)
 

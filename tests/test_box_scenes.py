@@ -67,7 +67,11 @@ def test_bridge_joints_chain_every_plank_to_the_world():
     assert S.plank_bridge().joints.shape[0] == 3180
 
 
-def test_box_scenes_are_refused_by_the_library_step():
+def test_box_scenes_upload_their_half_extents():
     sc = S.plank_bridge(planks=10)
-    with pytest.raises(ovl.OvlError):
-        ovl._SceneArrays(sc)
+    arr = ovl._SceneArrays(sc)
+    assert arr.half is not None and np.array_equal(arr.half, sc.half_extents.astype(np.float32))
+    assert bool(arr.desc.half_extents)
+    # every box's radius bounds it (the step's broad phase tests bounding spheres)
+    box = (sc.half_extents > 0).any(1)
+    assert np.all(sc.radius[box] >= np.linalg.norm(sc.half_extents[box], axis=1) * (1 - 1e-6))

@@ -137,7 +137,7 @@ def _check_step(sim, sc, st0, rng, n_bodies=2000, n_workers=8, n_overlap=400):
             if key & joint_bit:
                 a_, b_ = sc.joints[int(key & ~joint_bit)]
             else:
-                a_, b_ = int(key >> np.uint64(32)), int(key & np.uint64(0xFFFFFFFF))
+                a_, b_ = int(key >> np.uint64(32)), int((key & np.uint64(0xFFFFFFFF)) >> np.uint64(2))
             for e, x in enumerate((a_, b_)):
                 if 0 <= x < n and dyn[x]:
                     bs[q, e] = slot[int(x)]

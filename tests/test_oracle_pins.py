@@ -530,7 +530,7 @@ def test_resting_sphere_takes_mgh():
     sim.step()
     assert abs(sim.pairs()["lam"][0, 0] - m * G * h) < 1e-12
     part, key, lam = sim.warmstart()
-    assert list(part) == [0] and int(key[0]) == (0 << 32 | 1) and abs(lam[0, 0] - m * G * h) < 1e-12
+    assert list(part) == [0] and int(key[0]) == (0 << 32 | 1 << 2) and abs(lam[0, 0] - m * G * h) < 1e-12
 
 
 def test_sphere_column_frictionless():
