@@ -16,6 +16,9 @@ iterations/s, a roofline entry for the solver kernel, the FP64 oracle timed on
 the host as CPU baseline, an end-to-end figure through the C ABI with host
 buffers, SM clocks sampled during the timed region.
 
+``--workload building`` / ``bridge``: box bodies (columns and slabs with two balls; a
+jointed plank deck), the stand-ins for Section 6's Building and Two-way Bridge.
+
 ``--workload pile_mixed``: 6728 big spheres (radius 1.25, two layers) on the
 floor of a box under a 128 x 128 x 16 lattice of small ones (r ~ U(0.4,0.6));
 each big sphere takes tens of contacts.  With ``--lb-load contacts`` Algorithm 6 compares loads that
@@ -65,7 +68,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ovl", choices=["ovl", "reference"])
     ap.add_argument("--workload", default="pile_large",
-                    choices=["pile_large", "pile_mixed", "chain", "pile_small", "batched", "warmstart", "gamma"],
+                    choices=["pile_large", "pile_mixed", "chain", "pile_small", "batched", "building", "bridge",
+                             "warmstart", "gamma"],
                     help="warmstart: the learned warm start on the large pile (log, train, "
                          "sweeps to RMS residual 1e-4 against the previous-step warm start)")
     ap.add_argument("--ws-log-steps", type=int, default=6)
@@ -83,7 +87,7 @@ def parse():
 
 def default_settle(workload):
     return {"pile_large": 150, "pile_mixed": 150, "chain": 0, "pile_small": 0, "batched": 0,
-            "warmstart": 150, "gamma": 0}[workload]
+            "building": 0, "bridge": 0, "warmstart": 150, "gamma": 0}[workload]
 
 
 def step_params(ovl, lb_load: str = "bodies") -> dict:
@@ -206,6 +210,10 @@ def oracle_sample_scene(workload, scene=None):
         return S.chain(), 0, "the full 4096-sphere chain"
     if workload == "batched":
         return S.batched(n_scenes=16), 0, "the first 16 of the 512 batched scenes (same generator and seed)"
+    if workload == "building":
+        return S.box_building(), 0, "the full building (columns, slabs, 2 balls; 16 workers)"
+    if workload == "bridge":
+        return S.plank_bridge(), 0, "the full plank bridge (1589 planks, 3180 joints; 8 workers)"
     return S.pile_small(), 0, "the full 256-sphere pile"
 
 

@@ -663,4 +663,6 @@ WORKLOADS = {
     "pile_large": pile_large,
     "pile_mixed": pile_mixed,
     "batched": batched,
+    "building": box_building,
+    "bridge": plank_bridge,
 }

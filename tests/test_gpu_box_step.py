@@ -4,11 +4,11 @@ columns and slabs with balls dropped on it, a jointed plank bridge (ball
 joints between box planks, the overlap grown over the joints by Algorithms
 2-3), and a pit of mixed spheres and boxes.
 
-The oracle decides every box contact in FP64 and reports how close each
-decision came to its threshold; the states used here have none within a
-band, and the library decides box contacts in FP64 too, so the contact lists
-(pairs, manifold index, order) must be equal and the geometry equal to FP32
-rounding.  Every other record as for spheres (tests/parity.py): graph,
+Both sides decide box contacts in FP64 with the same stated tolerance rules,
+so the contact lists (pairs, manifold index, order) must be equal -- also
+for the pairs the oracle reports as near a threshold (counted and printed;
+FP32 might decide those otherwise, FP64 computations in two orders agree far
+closer) -- and the geometry equal to FP32 rounding.  Every other record as for spheres (tests/parity.py): graph,
 masks after Algorithm 6, entries, D, pair order and colours bit for bit;
 velocities at the stated 1e-4 m/s, positions at 1e-5 m."""
 import numpy as np
@@ -58,7 +58,7 @@ def test_box_step_matches_oracle(name, warm):
     orc, gpu = P.prepare(sc, warm_steps=warm)
     try:
         rep = P.compare_step(orc, gpu)
-        assert np.all(orc.contact_ambiguity() >= 1.0)
+        near = int(np.sum(orc.contact_ambiguity() < 1.0))
         k_o, p_o = orc.contact_points()
         k_g, p_g = gpu.contact_points()
         assert np.array_equal(k_o, k_g)
@@ -68,8 +68,8 @@ def test_box_step_matches_oracle(name, warm):
         n = sc.n_bodies
         boxy = (he[ab[:, 0]] > 0).any(1) | ((ab[:, 1] < n) & (he[np.minimum(ab[:, 1], n - 1)] > 0).any(1))
         assert boxy.sum() > 10
-        print(f"\n  {name} after {warm} steps: {rep['contacts']} contacts ({int(boxy.sum())} with a box), "
-              f"|dv| {rep['v']:.2e} m/s, |dx| {rep['x']:.2e} m, |dlambda| {rep['lambda']:.2e}")
+        print(f"\n  {name} after {warm} steps: {rep['contacts']} contacts ({int(boxy.sum())} with a box, {near} near a "
+              f"decision threshold), |dv| {rep['v']:.2e} m/s, |dx| {rep['x']:.2e} m, |dlambda| {rep['lambda']:.2e}")
     finally:
         gpu.close()
 
