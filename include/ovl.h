@@ -40,9 +40,8 @@ typedef int32_t ovl_status;
 #define OVL_OK 0
 #define OVL_ERR_ARG (-1)        /* bad argument or call order */
 #define OVL_ERR_CUDA (-2)       /* a CUDA call failed */
-#define OVL_ERR_CAPACITY (-3)   /* a fixed limit was exceeded: colours > 64 in a worker, sphere
-                                   neighbours beyond a body's capacity (set from the radii), a
-                                   worker of 65535 bodies or more, ... */
+#define OVL_ERR_CAPACITY (-3)   /* a fixed limit was exceeded: colours > 128 in a worker, sphere
+                                   neighbours beyond a body's capacity (set from the radii), ... */
 #define OVL_ERR_TIMEOUT (-4)    /* a bounded device-side wait gave up */
 #define OVL_ERR_NONFINITE (-5)  /* NaN or Inf in a state */
 #define OVL_ERR_MEMBERSHIP (-6) /* dynamic body with empty W, or a worker index >= n_sets */

@@ -20,7 +20,7 @@
 
 #include "../../include/ovl.h"
 
-#define OVL_MAX_COLOURS 64
+#define OVL_MAX_COLOURS 128
 #define OVL_MAX_NEIGH 32   // sphere neighbours with larger index kept in registers per body; bodies
                            // whose neighbour capacity is larger continue in their global range
 
@@ -31,7 +31,7 @@
 #define DEV_ERR_MEMBERSHIP 3
 #define DEV_ERR_COLOURS 4
 #define DEV_ERR_TIMEOUT 5
-#define DEV_ERR_SLOTS 6        // a worker holds 65535 bodies or more
+#define DEV_ERR_SLOTS 6        // a worker slot out of range (reserved)
 
 namespace ovl {
 

@@ -44,12 +44,12 @@ ovl_status check_device_status(ovl_ctx *c) {
             return fail(c, OVL_ERR_CAPACITY,
                         "a body touches more spheres of larger index than its neighbour capacity "
                         "(set from the radii: deep interpenetration)");
-        case DEV_ERR_SLOTS: return fail(c, OVL_ERR_CAPACITY, "a worker holds 65535 bodies or more");
+        case DEV_ERR_SLOTS: return fail(c, OVL_ERR_CAPACITY, "worker slot out of range");
         case DEV_ERR_NONFINITE: return fail(c, OVL_ERR_NONFINITE, "non-finite value in the blended state");
         case DEV_ERR_MEMBERSHIP:
             return fail(c, OVL_ERR_MEMBERSHIP, "dynamic body with no worker, or a worker index out of range");
         case DEV_ERR_COLOURS:
-            return fail(c, OVL_ERR_CAPACITY, "a worker needs more than 64 colours (bodies in about 64 or more constraints)");
+            return fail(c, OVL_ERR_CAPACITY, "a worker needs more than 128 colours (bodies in about 128 or more constraints)");
         case DEV_ERR_TIMEOUT: return fail(c, OVL_ERR_TIMEOUT, "colouring did not finish within its round limit");
         default: return fail(c, OVL_ERR_CUDA, "unknown device status");
     }
@@ -269,12 +269,12 @@ void phase_membership(ovl_ctx *c, float dt_override) {
 
 int colour_smem_capacity(ovl_ctx *c) {
     int avail = c->smem_optin - colour_static_smem() - 1024;
-    int n = std::max(0, avail / 16);
+    int n = std::max(0, avail / 24);
     return c->P.smem_slot_limit > 0 ? std::min(n, c->P.smem_slot_limit) : n;
 }
 
 // CTAs per worker for the colouring: the smallest cluster whose share of the
-// largest worker's slots fits one CTA's shared memory (16 B per slot)
+// largest worker's slots fits one CTA's shared memory (24 B per slot)
 void colour_config(ovl_ctx *c, int *cluster, int *slots) {
     const int cap = colour_smem_capacity(c);
     const int fixed = (c->P.pgs_cluster == 1 || c->P.pgs_cluster == 2 || c->P.pgs_cluster == 4 ||
@@ -485,7 +485,7 @@ void phase_colour(ovl_ctx *c) {
     c->part_rounds.ensure((size_t)P + 1);
     c->col_off.ensure((size_t)P * (2 * OVL_MAX_COLOURS + 1) + 1);
     c->pair_of_row.ensure(npr + 1);
-    c->colour_scratch.ensure(2 * (size_t)c->ne + 1);
+    c->colour_scratch.ensure(3 * (size_t)c->ne + 1);
     c->worklist.ensure(npr + 1);
     c->worklist2.ensure(npr + 1);
     c->wprio.ensure(npr + 1);

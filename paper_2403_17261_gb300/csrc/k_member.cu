@@ -248,7 +248,7 @@ __device__ __forceinline__ uint32_t mapa_u32(uint32_t a, uint32_t rank) {
 
 // Per-slot colouring state of one worker: the maximum priority of the
 // uncoloured constraints posted this round (array 0) and the mask of colours
-// taken (array 1).
+// taken, colours 0-63 (array 1) and 64-127 (array 2).
 // C > 1: spread over the cluster's shared memory, CTA k holding the
 // contiguous slots [k per, (k + 1) per).  The
 // maximum is taken in two 32-bit stages (high words, then low words among the
@@ -258,10 +258,10 @@ __device__ __forceinline__ uint32_t mapa_u32(uint32_t a, uint32_t rank) {
 template <int C>
 struct ColourSlots {
     static constexpr bool two_stage = true;
-    uint32_t b0, b1;   // shared-window offsets of this CTA's arrays (hi/lo words, used mask)
-    int per;           // slots per CTA
+    uint32_t b0, b1, b2;   // shared-window offsets of this CTA's arrays (hi/lo words, used mask lo, hi)
+    int per;               // slots per CTA
     __device__ __forceinline__ uint32_t at(int arr, int s) const {
-        uint32_t base = arr == 0 ? b0 : b1;
+        uint32_t base = arr == 0 ? b0 : (arr == 1 ? b1 : b2);
         uint32_t r = 0;
 #pragma unroll
         for (int k = 1; k < C; ++k) r += s >= k * per ? 1u : 0u;
@@ -294,9 +294,9 @@ struct ColourSlots {
 // one 64-bit atomic max per slot.
 struct ColourPtrs {
     static constexpr bool two_stage = false;
-    unsigned long long *p0, *p1;
+    unsigned long long *p0, *p1, *p2;
     __device__ __forceinline__ unsigned long long *ptr(int arr, int s) const {
-        return (arr == 0 ? p0 : p1) + s;
+        return (arr == 0 ? p0 : (arr == 1 ? p1 : p2)) + s;
     }
     __device__ __forceinline__ void amax_hi(int s, unsigned long long v) const { atomicMax(ptr(0, s), v); }
     __device__ __forceinline__ void amax_lo(int, unsigned long long) const {}
@@ -339,7 +339,7 @@ struct ColourShared {
     int counts[NBUCKET + 1];
     int base_b[NBUCKET + 1];
     int running[NBUCKET];
-    int wcnt[COLOUR_WARPS][NBUCKET];
+    uint8_t wcnt[COLOUR_WARPS][NBUCKET];   // one warp's items per bucket (at most 32)
 };
 
 template <int C, class SL>
@@ -348,7 +348,7 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, ColourShared &sh
     int (&counts)[NBUCKET + 1] = sh.counts;
     int (&base_b)[NBUCKET + 1] = sh.base_b;
     int (&running)[NBUCKET] = sh.running;
-    int (&wcnt)[COLOUR_WARPS][NBUCKET] = sh.wcnt;
+    uint8_t (&wcnt)[COLOUR_WARPS][NBUCKET] = sh.wcnt;
     const int tid = threadIdx.x, T = blockDim.x;
     const int b0 = a.part_bstart[p], nb = a.part_bstart[p + 1] - b0;
     const int q0 = a.part_pstart[p], nq = a.part_pstart[p + 1] - q0;
@@ -377,7 +377,7 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, ColourShared &sh
     const int wbase = c0 + (j0 - ncw);
     int4 *wl_cur = a.worklist + q0 + wbase, *wl_next = a.worklist2 + q0 + wbase;
     unsigned long long *pr_cur = a.wprio + q0 + wbase, *pr_next = a.wprio2 + q0 + wbase;
-    for (int s = s_lo + tid; s < s_hi; s += T) S.st(1, s, 0ull);
+    for (int s = s_lo + tid; s < s_hi; s += T) { S.st(1, s, 0ull); S.st(2, s, 0ull); }
     for (int v = tid; v < m0; v += T) {
         const int k = item(v);
         int2 sl = a.p_slot[q0 + k];
@@ -421,16 +421,18 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, ColourShared &sh
                 continue;
             }
             // only this constraint touches its slots in this round
-            unsigned long long u = 0ull;
-            if (w.y >= 0) u |= S.ld(1, w.y);
-            if (w.z >= 0) u |= S.ld(1, w.z);
+            unsigned long long u0 = 0ull, u1 = 0ull;   // colours 0-63, 64-127 taken at its slots
+            if (w.y >= 0) { u0 |= S.ld(1, w.y); u1 |= S.ld(2, w.y); }
+            if (w.z >= 0) { u0 |= S.ld(1, w.z); u1 |= S.ld(2, w.z); }
             int c;
-            if (~u) c = __ffsll((long long)~u) - 1;
+            if (~u0) c = __ffsll((long long)~u0) - 1;
+            else if (~u1) c = 64 + __ffsll((long long)~u1) - 1;
             else { c = OVL_MAX_COLOURS - 1; atomicCAS(a.status, DEV_OK, DEV_ERR_COLOURS); }
             a.p_colour[q0 + w.x] = c;
-            const unsigned long long bit = 1ull << c;
-            if (w.y >= 0) S.st(1, w.y, S.ld(1, w.y) | bit);
-            if (w.z >= 0) S.st(1, w.z, S.ld(1, w.z) | bit);
+            const int arr = c < 64 ? 1 : 2;
+            const unsigned long long bit = 1ull << (c & 63);
+            if (w.y >= 0) S.st(arr, w.y, S.ld(arr, w.y) | bit);
+            if (w.z >= 0) S.st(arr, w.z, S.ld(arr, w.z) | bit);
             atomicMax(&ncol_sh, c + 1);
         }
         __syncthreads();
@@ -500,7 +502,7 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, ColourShared &sh
         if (valid) bucket = 2 * a.p_colour[q0 + k] + ((int)(key[k] >> 62) & 1);
         unsigned peers = __match_any_sync(0xffffffffu, bucket);
         int lrank = __popc(peers & lt);
-        if (valid && lrank == 0) wcnt[warp][bucket] = __popc(peers);
+        if (valid && lrank == 0) wcnt[warp][bucket] = (uint8_t)__popc(peers);
         __syncthreads();
         if (valid) {
             int pre = 0;
@@ -528,17 +530,18 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
     const int nb = a.part_bstart[p + 1] - a.part_bstart[p];
     const int per = (nb + C - 1) / C;
     if (per <= a.smem_slots) {
-        unsigned long long *mx = dyn_smem, *u = dyn_smem + per;
+        unsigned long long *mx = dyn_smem, *u = dyn_smem + per, *u2 = dyn_smem + 2 * per;
         if (C == 1) {
-            ColourPtrs S{mx, u};
+            ColourPtrs S{mx, u, u2};
             colour_worker<1>(a, S, sh, p, 0, per);
         } else {
-            ColourSlots<C> S{(uint32_t)__cvta_generic_to_shared(mx), (uint32_t)__cvta_generic_to_shared(u), per};
+            ColourSlots<C> S{(uint32_t)__cvta_generic_to_shared(mx), (uint32_t)__cvta_generic_to_shared(u),
+                             (uint32_t)__cvta_generic_to_shared(u2), per};
             colour_worker<C>(a, S, sh, p, rank, per);
         }
     } else if (rank == 0) {
-        unsigned long long *mx = a.scratch + 2 * (size_t)a.part_bstart[p];
-        ColourPtrs S{mx, mx + nb};
+        unsigned long long *mx = a.scratch + 3 * (size_t)a.part_bstart[p];
+        ColourPtrs S{mx, mx + nb, mx + 2 * (size_t)nb};
         colour_worker<1>(a, S, sh, p, 0, nb);
     }
 }
@@ -546,19 +549,15 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
 // ---------------------------------------------------------------------------
 // Row records in colour order (the solver forms t1, t2, k_n and the joint
 // k's itself).  Contacts (sphere-sphere or sphere-plane):
-//   r0 = (n, k_t)  r1 = (r_a, r_b, target_n, slots)  r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b)  r4 = (t1, k_n)
+//   r0 = (n, slot_b)  r1 = (r_a, r_b, target_n, slot_a)  r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b)  r4 = (t1, k_n)
 // Ball joints (rows along the world axes):
-//   r0 = (r_A, target_x)  r1 = (r_B, target_y)  r2 = (target_z, 0, 0, slots)  r3 as for contacts
+//   r0 = (r_A, target_x)  r1 = (r_B, target_y)  r2 = (target_z, 0, slot_a, slot_b)  r3 as for contacts
+// (a slot word holds the int bits of the worker slot, -1 for a static end).
 // with r_A, r_B the pivot offsets from each body's centre in the world frame.
 // ---------------------------------------------------------------------------
 
-// two 16-bit worker slots in one word (0xffff: static end)
-__device__ __forceinline__ int pack_slots(int2 sl, int *status) {
-    if (sl.x >= 0xffff || sl.y >= 0xffff) atomicCAS(status, DEV_OK, DEV_ERR_SLOTS);
-    unsigned a = sl.x < 0 ? 0xffffu : (unsigned)sl.x & 0xffffu;
-    unsigned b = sl.y < 0 ? 0xffffu : (unsigned)sl.y & 0xffffu;
-    return (int)(a | (b << 16));
-}
+// a worker slot stored in a record word (its int bits; -1: static end)
+__device__ __forceinline__ float slot_word(int s) { return __int_as_float(s < 0 ? -1 : s); }
 
 __device__ __forceinline__ bool body_is_box(const float4 *half, int b) {
     if (!half || b < 0) return false;
@@ -634,8 +633,8 @@ __global__ void k_rows(RowArgs a) {
                     const float phi = nphi.w;
                     tg[0] = phi > 0.f ? -phi / h : a.erp * fmaxf(-phi - a.slop, 0.f) / h;
                     tg[1] = tg[2] = 0.f;
-                    a.r0[r] = z;
-                    a.r1[r] = make_float4(0.f, 0.f, 0.f, __int_as_float(pack_slots(sl, a.status)));
+                    a.r0[r] = make_float4(0.f, 0.f, 0.f, slot_word(sl.y));
+                    a.r1[r] = make_float4(0.f, 0.f, 0.f, slot_word(sl.x));
                     a.r3[r] = z;
                     a.r4[r] = z;
                 } else {
@@ -665,7 +664,7 @@ __global__ void k_rows(RowArgs a) {
                     dir[2] = make_float3(0.f, 0.f, 1.f);
                     a.r0[r] = z;
                     a.r1[r] = z;
-                    a.r2[r] = make_float4(0.f, 0.f, 0.f, __int_as_float(pack_slots(sl, a.status)));
+                    a.r2[r] = make_float4(0.f, 0.f, slot_word(sl.x), slot_word(sl.y));
                     a.r3[r] = z;
                 }
                 write_full_row(a, r, ea, eb, rA, rB, dir, tg);
@@ -685,11 +684,10 @@ __global__ void k_rows(RowArgs a) {
                 rb = a.st[4 * ab.y].w;
                 if (sl.y >= 0) { imb = a.st[4 * ab.y + 2].w; iib = a.st[4 * ab.y + 3].w; }
             }
-            float kt = 1.0f / (ima + imb + iia * ra * ra + iib * rb * rb);
             float phi = nphi.w;
             float target = phi > 0.f ? -phi / h : a.erp * fmaxf(-phi - a.slop, 0.f) / h;
-            a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, kt);
-            a.r1[r] = make_float4(ra, rb, target, __int_as_float(pack_slots(sl, a.status)));
+            a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, slot_word(sl.y));
+            a.r1[r] = make_float4(ra, rb, target, slot_word(sl.x));
             a.r3[r] = make_float4(ima, imb, iia, iib);
             a.r4[r] = make_float4(t1.x, t1.y, t1.z, __frcp_rn(ima + imb));   // as the solver forms k_n
         } else {
@@ -723,7 +721,7 @@ __global__ void k_rows(RowArgs a) {
             float g = -a.erp / h;
             a.r0[r] = make_float4(rA.x, rA.y, rA.z, g * err.x);
             a.r1[r] = make_float4(rB.x, rB.y, rB.z, g * err.y);
-            a.r2[r] = make_float4(g * err.z, 0.f, 0.f, __int_as_float(pack_slots(sl, a.status)));
+            a.r2[r] = make_float4(g * err.z, 0.f, slot_word(sl.x), slot_word(sl.y));
             a.r3[r] = make_float4(ima, imb, iia, iib);
         }
         a.rpair[r] = k;
@@ -794,7 +792,7 @@ void launch_worker_cost_keys(const int *part_pstart, int P, uint32_t *keys, uint
 }
 template <int C>
 static void launch_colour_c(const ColourArgs &a, cudaStream_t s) {
-    size_t smem = (size_t)a.smem_slots * 2 * sizeof(unsigned long long);
+    size_t smem = (size_t)a.smem_slots * 3 * sizeof(unsigned long long);
     CK(cudaFuncSetAttribute(k_colour<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.n_parts * C);

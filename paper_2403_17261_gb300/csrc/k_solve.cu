@@ -30,14 +30,15 @@
 // Ball joint: three rows along the world axes, w = (v_b + w_b x r_B - v_a - w_a x r_A)_k,
 // k = 1 / (1/m_a + 1/m_b + |r_A x e_k|^2 / I_a + |r_B x e_k|^2 / I_b).
 //
-// Row records (float4 each): contact r0 = (n, k_t), r1 = (r_a, r_b, target,
-// slots), r4 = (t1, k_n); joint r0 = (r_A, target_x), r1 = (r_B, target_y),
-// r2 = (target_z, 0, 0, slots); both r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b).
-// slots = slot_a | slot_b << 16 (0xffff: static end).  With the masses in
-// shared memory a contact reads r0 and r1 only, forming t1 = normalise(e_k -
-// (n . e_k) n) (k the axis of the smallest |n_k|) and k_n = 1 / (1/m_a +
-// 1/m_b) with the same operations that wrote r4, so both layouts compute the
-// same bits.
+// Row records (float4 each): contact r0 = (n, slot_b), r1 = (r_a, r_b,
+// target, slot_a), r4 = (t1, k_n); joint r0 = (r_A, target_x), r1 = (r_B,
+// target_y), r2 = (target_z, 0, slot_a, slot_b); both r3 = (1/m_a, 1/m_b,
+// 1/I_a, 1/I_b).  A slot is a 32-bit worker slot (-1: static end).  With the
+// masses in shared memory a contact reads r0 and r1 only, forming t1 =
+// normalise(e_k - (n . e_k) n) (k the axis of the smallest |n_k|) and k_n =
+// 1 / (1/m_a + 1/m_b) with the same operations that wrote r4, so both layouts
+// compute the same bits; both form the tangents' k_t = 1 / (1/m_a + 1/m_b +
+// r_a^2 / I_a + r_b^2 / I_b) from the bodies' masses.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -75,8 +76,6 @@ struct Body {
     float im, ii;   // inverse mass and inertia (0 for a static end)
 };
 
-__device__ __forceinline__ int slot_a(int s) { int x = s & 0xffff; return x == 0xffff ? -1 : x; }
-__device__ __forceinline__ int slot_b(int s) { int x = (int)((unsigned)s >> 16); return x == 0xffff ? -1 : x; }
 
 // ---- body storage --------------------------------------------------------
 // Plain pointers: one CTA, shared or global memory.  kMasses: the slots hold
@@ -220,17 +219,26 @@ __device__ __forceinline__ void fetch_row_rest(const SolveArgs &a, int r, bool j
     }
 }
 
-__device__ __forceinline__ int row_slots(const Row &w) { return __float_as_int(w.joint ? w.z.w : w.y.w); }
+// the row's two worker slots (a, b); -1 for a static end
+__device__ __forceinline__ int2 row_slots(const Row &w) {
+    return w.joint ? make_int2(__float_as_int(w.z.z), __float_as_int(w.z.w))
+                   : make_int2(__float_as_int(w.y.w), __float_as_int(w.x.w));
+}
 
 // a static end (or a body not active in this worker) has zero velocity,
 // inverse mass and inverse inertia
 template <class S>
 __device__ __forceinline__ void load_pair(const S &st, const Row &w, Body &A, Body &B) {
-    const int slots = row_slots(w);
-    const int sa = slot_a(slots), sb = slot_b(slots);
+    const int2 slots = row_slots(w);
+    const int sa = slots.x, sb = slots.y;
     if (sa >= 0) st.load(sa, A); else { A.v = make_float3(0.f, 0.f, 0.f); A.w = A.v; A.im = 0.f; A.ii = 0.f; }
     if (sb >= 0) st.load(sb, B); else { B.v = make_float3(0.f, 0.f, 0.f); B.w = B.v; B.im = 0.f; B.ii = 0.f; }
     if (!S::kMasses) { A.im = w.m.x; B.im = w.m.y; A.ii = w.m.z; B.ii = w.m.w; }
+}
+
+// k_t of a contact's tangent rows from the bodies' masses and lever radii
+__device__ __forceinline__ float contact_kt(const Body &A, const Body &B, float ra, float rb) {
+    return __frcp_rn(fmaf(B.ii, rb * rb, fmaf(A.ii, ra * ra, A.im + B.im)));
 }
 
 // t1 and k_n of a contact: read, or formed as the row build forms them
@@ -248,8 +256,8 @@ __device__ __forceinline__ void contact_frame(const Row &w, const Body &A, const
 }
 
 template <class S>
-__device__ __forceinline__ void store_pair(const S &st, int slots, const Body &A, const Body &B) {
-    const int sa = slot_a(slots), sb = slot_b(slots);
+__device__ __forceinline__ void store_pair(const S &st, int2 slots, const Body &A, const Body &B) {
+    const int sa = slots.x, sb = slots.y;
     if (sa >= 0) st.store(sa, A);
     if (sb >= 0) st.store(sb, B);
 }
@@ -271,8 +279,8 @@ __device__ __forceinline__ void contact_impulse(Body &A, Body &B, float3 n, floa
 __device__ __forceinline__ void contact_row(Body &A, Body &B, float4 r0, float4 r1, float3 t1, float kn,
                                             float mu, float4 &lam) {
     const float3 n = f3(r0);
-    const float kt = r0.w;
     const float ra = r1.x, rb = r1.y, target = r1.z;
+    const float kt = contact_kt(A, B, ra, rb);
     const float3 t2 = cross3(n, t1);
     // normal row
     float3 dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
@@ -428,8 +436,8 @@ __device__ float full_residual_sq(const SolveArgs &a, int r, bool joint, const B
 __device__ __forceinline__ float contact_residual_sq(const Body &A, const Body &B, float4 r0, float4 r1,
                                                      float3 t1, float kn, float mu, float4 lam) {
     const float3 n = f3(r0);
-    const float kt = r0.w;
     const float ra = r1.x, rb = r1.y, target = r1.z;
+    const float kt = contact_kt(A, B, ra, rb);
     const float3 t2 = cross3(n, t1);
     float3 dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
     float3 u = lever_sum(ra, A.w, rb, B.w);
@@ -772,10 +780,6 @@ __global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveAr
     const int p = a.order ? (int)a.order[blockIdx.x / C] : (int)(blockIdx.x / C);
     const int b0 = a.part_bstart[p], nb = a.part_bstart[p + 1] - b0;
     const int per = (nb + C - 1) / C;
-    if (nb >= 0xffff) {
-        if (rank == 0 && threadIdx.x == 0) atomicCAS(a.status, DEV_OK, DEV_ERR_SLOTS);
-        return;
-    }
     // this CTA's row buckets (three offsets per colour), read in every colour
     // of every sweep
     const int *goff = a.col_off + (size_t)p * OWNER_NB;
