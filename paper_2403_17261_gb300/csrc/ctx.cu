@@ -523,7 +523,6 @@ void phase_colour(ovl_ctx *c) {
 void phase_rows(ovl_ctx *c, float dt_override) {
     const int npr = c->npairs;
     c->r0.ensure(npr + 1); c->r1.ensure(npr + 1); c->r2.ensure(npr + 1); c->r3.ensure(npr + 1);
-    c->r4.ensure(npr + 1);
     c->rpair.ensure(npr + 1); c->rlam.ensure(npr + 1);
     RowArgs a{};
     a.n = c->n; a.nc = c->nc; a.np = npr; a.pair_of_row = c->pair_of_row2.p; a.ps_cons = c->ps_cons.p;
@@ -532,7 +531,7 @@ void phase_rows(ovl_ctx *c, float dt_override) {
     a.joint_scene = c->joint_scene.p; a.st = c->st.p; a.sob = c->sob.p; a.part_scene = c->part_scene.p;
     a.scene_dt = c->scene_dt.p; a.scene_mu = c->scene_mu.p; a.dt_override = dt_override;
     a.erp = c->P.erp; a.slop = c->P.slop;
-    a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.r4 = c->r4.p; a.rlam = c->rlam.p;
+    a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
     a.rpair = c->rpair.p; a.status = c->status.p;
     if (c->has_boxes) {
         c->row_full.ensure(npr + 1);
@@ -592,7 +591,7 @@ SolveArgs solve_args(ovl_ctx *c, float dt_override, int iters) {
     a.entry_body = c->entry_body.p; a.part_ncol = c->part_ncol.p; a.col_off = c->col_off2.p;
     a.part_scene = c->part_scene.p; a.scene_dt = c->scene_dt.p; a.dt_override = dt_override;
     a.gravity = make_float3(c->P.gravity[0], c->P.gravity[1], c->P.gravity[2]);
-    a.st = c->st.p; a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.r4 = c->r4.p;
+    a.st = c->st.p; a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p;
     a.rlam = c->rlam.p;
     a.rpair = c->rpair.p; a.scene_mu = c->scene_mu.p; a.n_entries = c->ne;
     a.lam_out = c->lam_out.p; a.copies = c->copies.p; a.scratch = c->solve_scratch.p;
@@ -1002,7 +1001,7 @@ void release_all(ovl_ctx *c) {
     c->part_pcount.release(); c->part_pstart.release(); c->p_colour.release(); c->part_ncol.release(); c->part_rounds.release();
     c->col_off.release(); c->pair_of_row.release(); c->p_key.release(); c->p_slot.release();
     c->p_lam0.release(); c->colour_scratch.release(); c->worklist.release(); c->worklist2.release(); c->wprio.release(); c->wprio2.release(); c->r0.release(); c->r1.release();
-    c->r2.release(); c->rlam.release(); c->lam_out.release(); c->r3.release(); c->r4.release(); c->rpair.release(); c->ws_pstart.release();
+    c->r2.release(); c->rlam.release(); c->lam_out.release(); c->r3.release(); c->rpair.release(); c->ws_pstart.release();
     c->ws_key.release(); c->ws_lam.release(); c->copies.release(); c->solve_scratch.release();
     c->part_iters.release(); c->part_res_sq.release(); c->visited.release(); c->queue.release();
     c->qctl.release(); c->D.release(); c->weight.release(); c->stage13.release(); c->scan_tmp.release();

@@ -74,7 +74,7 @@ struct ovl_ctx {
     DBuf<unsigned long long> colour_scratch;
     DBuf<int4> worklist, worklist2;
     DBuf<unsigned long long> wprio, wprio2;
-    DBuf<float4> r0, r1, r2, r3, r4, rlam, lam_out;
+    DBuf<float4> r0, r1, r2, r3, rlam, lam_out;
     DBuf<int> rpair;
     DBuf<int> ws_pstart;
     DBuf<uint64_t> ws_key;

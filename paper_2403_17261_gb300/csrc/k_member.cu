@@ -547,9 +547,9 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Row records in colour order (the solver forms t1, t2, k_n and the joint
-// k's itself).  Contacts (sphere-sphere or sphere-plane):
-//   r0 = (n, slot_b)  r1 = (r_a, r_b, target_n, slot_a)  r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b)  r4 = (t1, k_n)
+// Row records in colour order (the solver forms t1, t2, k_n, k_t and the
+// joint k's itself).  Contacts (sphere-sphere or sphere-plane):
+//   r0 = (n, slot_b)  r1 = (r_a, r_b, target_n, slot_a)  r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b)
 // Ball joints (rows along the world axes):
 //   r0 = (r_A, target_x)  r1 = (r_B, target_y)  r2 = (target_z, 0, slot_a, slot_b)  r3 as for contacts
 // (a slot word holds the int bits of the worker slot, -1 for a static end).
@@ -636,7 +636,6 @@ __global__ void k_rows(RowArgs a) {
                     a.r0[r] = make_float4(0.f, 0.f, 0.f, slot_word(sl.y));
                     a.r1[r] = make_float4(0.f, 0.f, 0.f, slot_word(sl.x));
                     a.r3[r] = z;
-                    a.r4[r] = z;
                 } else {
                     const int j = i - a.nc;
                     const float4 anA = a.janc[2 * j], anB = a.janc[2 * j + 1];
@@ -676,7 +675,6 @@ __global__ void k_rows(RowArgs a) {
         if (i < a.nc) {
             const int2 ab = a.c_ab[i];
             const float4 nphi = a.c_n[i];
-            const float4 t1 = a.c_t1[i];
             const float4 sa = a.st[4 * ab.x + 2], wa = a.st[4 * ab.x + 3], pa = a.st[4 * ab.x];
             float ima = sl.x >= 0 ? sa.w : 0.f, iia = sl.x >= 0 ? wa.w : 0.f;
             float ra = pa.w, rb = 0.f, imb = 0.f, iib = 0.f;
@@ -689,7 +687,6 @@ __global__ void k_rows(RowArgs a) {
             a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, slot_word(sl.y));
             a.r1[r] = make_float4(ra, rb, target, slot_word(sl.x));
             a.r3[r] = make_float4(ima, imb, iia, iib);
-            a.r4[r] = make_float4(t1.x, t1.y, t1.z, __frcp_rn(ima + imb));   // as the solver forms k_n
         } else {
             const int j = i - a.nc;
             const int2 ab = a.jab[j];

@@ -31,14 +31,13 @@
 // k = 1 / (1/m_a + 1/m_b + |r_A x e_k|^2 / I_a + |r_B x e_k|^2 / I_b).
 //
 // Row records (float4 each): contact r0 = (n, slot_b), r1 = (r_a, r_b,
-// target, slot_a), r4 = (t1, k_n); joint r0 = (r_A, target_x), r1 = (r_B,
-// target_y), r2 = (target_z, 0, slot_a, slot_b); both r3 = (1/m_a, 1/m_b,
-// 1/I_a, 1/I_b).  A slot is a 32-bit worker slot (-1: static end).  With the
-// masses in shared memory a contact reads r0 and r1 only, forming t1 =
-// normalise(e_k - (n . e_k) n) (k the axis of the smallest |n_k|) and k_n =
-// 1 / (1/m_a + 1/m_b) with the same operations that wrote r4, so both layouts
-// compute the same bits; both form the tangents' k_t = 1 / (1/m_a + 1/m_b +
-// r_a^2 / I_a + r_b^2 / I_b) from the bodies' masses.
+// target, slot_a); joint r0 = (r_A, target_x), r1 = (r_B, target_y), r2 =
+// (target_z, 0, slot_a, slot_b); both r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b),
+// read only when the masses are not in shared memory.  A slot is a 32-bit
+// worker slot (-1: static end).  A contact forms t1 = normalise(e_k - (n .
+// e_k) n) (k the axis of the smallest |n_k|), k_n = 1 / (1/m_a + 1/m_b) and
+// the tangents' k_t = 1 / (1/m_a + 1/m_b + r_a^2 / I_a + r_b^2 / I_b) from
+// the bodies' masses, so both layouts compute the same bits.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -189,10 +188,10 @@ struct ClusterSlotsM {
     }
 };
 
-// One row as the solver reads it: x = r0, y = r1, z = r2 (joints), m = r3
-// and t = r4 (contacts) when the slots do not carry the masses.
+// One row as the solver reads it: x = r0, y = r1, z = r2 (joints) and m =
+// r3 when the slots do not carry the masses.
 struct Row {
-    float4 x, y, z, m, t;
+    float4 x, y, z, m;
     bool joint;
 };
 
@@ -202,21 +201,13 @@ __device__ __forceinline__ void fetch_row(const SolveArgs &a, int r, bool joint,
     w.x = a.r0[r];
     w.y = a.r1[r];
     if (joint) w.z = a.r2[r];
-    if (!S::kMasses) {
-        w.m = a.r3[r];
-        if (!joint) w.t = a.r4[r];
-    }
+    if (!S::kMasses) w.m = a.r3[r];
 }
 
-// the records after r0 and r1 (those come from a RowPre)
-template <class S>
+// a joint's r2 (r0, r1 and r3 come from a RowPre)
 __device__ __forceinline__ void fetch_row_rest(const SolveArgs &a, int r, bool joint, Row &w) {
     w.joint = joint;
     if (joint) w.z = a.r2[r];
-    if (!S::kMasses) {
-        w.m = a.r3[r];
-        if (!joint) w.t = a.r4[r];
-    }
 }
 
 // the row's two worker slots (a, b); -1 for a static end
@@ -241,18 +232,13 @@ __device__ __forceinline__ float contact_kt(const Body &A, const Body &B, float 
     return __frcp_rn(fmaf(B.ii, rb * rb, fmaf(A.ii, ra * ra, A.im + B.im)));
 }
 
-// t1 and k_n of a contact: read, or formed as the row build forms them
+// t1 and k_n of a contact, formed from its normal and the bodies' masses
 template <class S>
 __device__ __forceinline__ void contact_frame(const Row &w, const Body &A, const Body &B, float3 &t1,
                                               float &kn) {
-    if (S::kMasses) {
-        const float3 n = make_float3(w.x.x, w.x.y, w.x.z);
-        t1 = tangent_from(n, tangent_axis(n.x, n.y, n.z));
-        kn = __frcp_rn(A.im + B.im);
-    } else {
-        t1 = make_float3(w.t.x, w.t.y, w.t.z);
-        kn = w.t.w;
-    }
+    const float3 n = make_float3(w.x.x, w.x.y, w.x.z);
+    t1 = tangent_from(n, tangent_axis(n.x, n.y, n.z));
+    kn = __frcp_rn(A.im + B.im);
 }
 
 template <class S>
@@ -366,7 +352,10 @@ __device__ __forceinline__ void solve_row(Body &A, Body &B, const Row &w, float 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 
 // ---- full rows (a box end: general lever arms and inertia responses) -------
-__device__ __forceinline__ bool is_full(const SolveArgs &a, int r) { return a.row_full != nullptr && a.row_full[r]; }
+// Only the kernels of contexts with boxes (X) hold this code: in the sphere
+// kernels its registers would add to the rows' loop, which then spills.
+template <bool X>
+__device__ __forceinline__ bool is_full(const SolveArgs &a, int r) { return X && a.row_full[r]; }
 
 // impulse dl along direction i of a full row
 __device__ __forceinline__ void full_impulse(const float4 *F, int i, float imA, float imB, Body &A, Body &B,
@@ -409,10 +398,10 @@ __device__ void full_warm(const SolveArgs &a, int r, Body &A, Body &B, float4 la
 }
 
 // a row of the sweep: full (box end) or plain
-template <class S>
+template <class S, bool X>
 __device__ __forceinline__ void solve_any(const SolveArgs &a, int r, Body &A, Body &B, const Row &w, float mu,
                                           float4 &lam) {
-    if (is_full(a, r)) full_rows(a, r, w.joint, A, B, mu, lam);
+    if (is_full<X>(a, r)) full_rows(a, r, w.joint, A, B, mu, lam);
     else solve_row<S>(A, B, w, mu, lam);
 }
 
@@ -491,27 +480,31 @@ __device__ __forceinline__ void group_wait() {
     else asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
 }
 
-// r0, r1 and the impulse of a thread's next two rows of a bucket (rows r and
-// r + T of a bucket ending at ce).  Row records are read-only during the
-// solve and a row's impulse is read and written by one thread only, so they
-// may be loaded a pass, or a colour, ahead.
+// r0, r1 (and r3 without the masses in shared memory) and the impulse of a
+// thread's next two rows of a bucket (rows r and r + T of a bucket ending at
+// ce).  Row records are read-only during the solve and a row's impulse is
+// read and written by one thread only, so they may be loaded a pass, or a
+// colour, ahead.
 struct RowPre {
-    float4 x0, y0, l0, x1, y1, l1;
+    float4 x0, y0, m0, l0, x1, y1, m1, l1;
 };
 
+template <class S>
 __device__ __forceinline__ void pre_rows(const SolveArgs &a, int r, int ce, int T, RowPre &p) {
     // every field is written on every path, so the previous values are dead
     // once used
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    p.x0 = p.y0 = p.l0 = p.x1 = p.y1 = p.l1 = z;
+    p.x0 = p.y0 = p.m0 = p.l0 = p.x1 = p.y1 = p.m1 = p.l1 = z;
     if (r < ce) {
         p.x0 = a.r0[r];
         p.y0 = a.r1[r];
+        if (!S::kMasses) p.m0 = a.r3[r];
         p.l0 = a.rlam[r];
     }
     if (r + T < ce) {
         p.x1 = a.r0[r + T];
         p.y1 = a.r1[r + T];
+        if (!S::kMasses) p.m1 = a.r3[r + T];
         p.l1 = a.rlam[r + T];
     }
 }
@@ -539,7 +532,7 @@ struct Buckets {
     int cs, nbk;
 };
 
-template <class S>
+template <class S, bool X>
 __device__ float rows_residual_sq(const SolveArgs &a, const S &st, const Buckets &bk, int ncol, float mu,
                                   int tid, int T) {
     float sq = 0.f;
@@ -553,7 +546,7 @@ __device__ float rows_residual_sq(const SolveArgs &a, const S &st, const Buckets
                 const float4 lam = a.rlam[r];
                 Body A, B;
                 load_pair(st, w, A, B);
-                if (is_full(a, r)) {
+                if (is_full<X>(a, r)) {
                     sq += full_residual_sq(a, r, w.joint, A, B, mu, lam);
                 } else if (w.joint) {
                     sq += joint_residual_sq(A, B, w.x, w.y, w.z);
@@ -573,7 +566,7 @@ __device__ float rows_residual_sq(const SolveArgs &a, const S &st, const Buckets
 // its owner bucket, thread tid the rows tid, tid + T, ..., U of them at a
 // time.  With C = 1 (one CTA, or the global-memory path) the CTA holds every
 // slot and takes every bucket.
-template <int C, int U, bool P, class S>
+template <int C, int U, bool P, bool X, class S>
 __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, int per, const Buckets &bk,
                              int row0, int row1) {
     __shared__ float red[32];
@@ -611,7 +604,7 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
             fetch_row<S>(a, r, r >= jb, w);
             Body A, B;
             load_pair(st, w, A, B);
-            if (is_full(a, r)) {
+            if (is_full<X>(a, r)) {
                 full_warm(a, r, A, B, lam);
             } else if (!w.joint) {
                 float3 t1;
@@ -629,17 +622,17 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
       }
       group_sync<C>();
     }
-    // Gauss-Seidel sweeps.  P (full-size CTAs, one per SM, with the masses in
-    // shared memory and two rows per thread): a pass takes r0, r1 and the
-    // impulses of its rows from registers loaded ahead, at the end of the
-    // previous pass or, for a colour's first pass, between the two halves of
-    // the previous colour's barrier.  (Measured: 4 % faster there, 7 % slower
-    // in the 256-thread CTAs that share an SM, which keep the plain loop.)
+    // Gauss-Seidel sweeps.  P (full-size CTAs, one per SM, two rows per
+    // thread): a pass takes r0, r1 (r3) and the impulses of its rows from
+    // registers loaded ahead, at the end of the previous pass or, for a
+    // colour's first pass, between the two halves of the previous colour's
+    // barrier.  (Measured: 4 % faster there, 7 % slower in the 256-thread CTAs
+    // that share an SM, which keep the plain loop.)
     int it_done = 0;
-    constexpr bool piped = P && U == 2 && S::kMasses;
+    constexpr bool piped = P && U == 2;
     const bool ahead = piped && bk.nbk == 1;
     RowPre pf;
-    if (ahead && a.iters > 0 && ncol > 0) pre_rows(a, bk.tab[0] + tid, bk.tab[2], T, pf);
+    if (ahead && a.iters > 0 && ncol > 0) pre_rows<S>(a, bk.tab[0] + tid, bk.tab[2], T, pf);
     for (int it = 0; it < a.iters; ++it) {
         for (int c = 0; c < ncol; ++c) {
           for (int k = 0; k < bk.nbk; ++k) {
@@ -649,35 +642,35 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
             if constexpr (piped) {
                 RowPre cur;
                 if (ahead) cur = pf;
-                else pre_rows(a, r, ce, T, cur);
+                else pre_rows<S>(a, r, ce, T, cur);
                 // two rows of the colour at once (independent: no shared body)
                 for (; r + T < ce; r += 2 * T) {
                     const int q = r + T;
                     Row u, w;
-                    u.x = cur.x0; u.y = cur.y0;
-                    w.x = cur.x1; w.y = cur.y1;
-                    fetch_row_rest<S>(a, r, r >= jb, u);
-                    fetch_row_rest<S>(a, q, q >= jb, w);
+                    u.x = cur.x0; u.y = cur.y0; u.m = cur.m0;
+                    w.x = cur.x1; w.y = cur.y1; w.m = cur.m1;
+                    fetch_row_rest(a, r, r >= jb, u);
+                    fetch_row_rest(a, q, q >= jb, w);
                     float4 xl = cur.l0, yl = cur.l1;
                     Body A, B, D, E;
                     load_pair(st, u, A, B);
                     load_pair(st, w, D, E);
-                    solve_any<S>(a, r, A, B, u, mu, xl);
-                    solve_any<S>(a, q, D, E, w, mu, yl);
+                    solve_any<S, X>(a, r, A, B, u, mu, xl);
+                    solve_any<S, X>(a, q, D, E, w, mu, yl);
                     store_pair(st, row_slots(u), A, B);
                     store_pair(st, row_slots(w), D, E);
                     a.rlam[r] = xl;
                     a.rlam[q] = yl;
-                    pre_rows(a, r + 2 * T, ce, T, cur);
+                    pre_rows<S>(a, r + 2 * T, ce, T, cur);
                 }
                 if (r < ce) {
                     Row w;
-                    w.x = cur.x0; w.y = cur.y0;
-                    fetch_row_rest<S>(a, r, r >= jb, w);
+                    w.x = cur.x0; w.y = cur.y0; w.m = cur.m0;
+                    fetch_row_rest(a, r, r >= jb, w);
                     float4 lam = cur.l0;
                     Body A, B;
                     load_pair(st, w, A, B);
-                    solve_any<S>(a, r, A, B, w, mu, lam);
+                    solve_any<S, X>(a, r, A, B, w, mu, lam);
                     store_pair(st, row_slots(w), A, B);
                     a.rlam[r] = lam;
                 }
@@ -693,8 +686,8 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                         Body A, B, D, E;
                         load_pair(st, u, A, B);
                         load_pair(st, w, D, E);
-                        solve_any<S>(a, r, A, B, u, mu, xl);
-                        solve_any<S>(a, q, D, E, w, mu, yl);
+                        solve_any<S, X>(a, r, A, B, u, mu, xl);
+                        solve_any<S, X>(a, q, D, E, w, mu, yl);
                         store_pair(st, row_slots(u), A, B);
                         store_pair(st, row_slots(w), D, E);
                         a.rlam[r] = xl;
@@ -707,7 +700,7 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                     float4 lam = a.rlam[r];
                     Body A, B;
                     load_pair(st, w, A, B);
-                    solve_any<S>(a, r, A, B, w, mu, lam);
+                    solve_any<S, X>(a, r, A, B, w, mu, lam);
                     store_pair(st, row_slots(w), A, B);
                     a.rlam[r] = lam;
                 }
@@ -718,7 +711,7 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
               const bool last = c + 1 == ncol;
               if (!last || it + 1 < a.iters) {
                   const int on = last ? 0 : (c + 1) * bk.cs;
-                  pre_rows(a, bk.tab[on] + tid, bk.tab[on + 2], T, pf);
+                  pre_rows<S>(a, bk.tab[on] + tid, bk.tab[on + 2], T, pf);
               }
               group_wait<C>();
           } else {
@@ -727,14 +720,14 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
         }
         it_done = it + 1;
         if (a.res_tol > 0.f && a.res_check_every > 0 && it_done % a.res_check_every == 0 && it_done < a.iters) {
-            float tot = group_sum<C>(rows_residual_sq(a, st, bk, ncol, mu, tid, T), red, &part_sum);
+            float tot = group_sum<C>(rows_residual_sq<S, X>(a, st, bk, ncol, mu, tid, T), red, &part_sum);
             int nrows = 3 * (row1 - row0);
             if (nrows == 0 || sqrtf(tot / nrows) <= a.res_tol) break;   // the same total in every CTA
         }
     }
     // residual of every row at the final iterate
     if (a.flags & OVL_FLAG_RESIDUAL) {
-        float tot = group_sum<C>(rows_residual_sq(a, st, bk, ncol, mu, tid, T), red, &part_sum);
+        float tot = group_sum<C>(rows_residual_sq<S, X>(a, st, bk, ncol, mu, tid, T), red, &part_sum);
         if (rank == 0 && tid == 0) a.part_res_sq[p] = (double)tot;
     }
     if (rank == 0 && tid == 0) a.part_iters[p] = it_done;
@@ -771,9 +764,9 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
 // C CTAs per worker; a worker's slots are spread over their shared memory when
 // they fit (ceil(nb / C) <= smem_slots), else CTA rank 0 solves it alone with
 // its body state in the global scratch area.  M: the shared-memory slots hold
-// the masses (32 B per slot) and contact rows are read as two records.  P:
-// rows loaded ahead (launches of SOLVE_THREADS threads, one CTA per SM).
-template <int C, int U, bool M, bool P>
+// the masses (32 B per slot; else 24 B, and rows carry the masses in r3).
+// P: rows loaded ahead (launches of SOLVE_THREADS threads, one CTA per SM).
+template <int C, int U, bool M, bool P, bool X>
 __global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveArgs a) {
     extern __shared__ float4 sm[];
     const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
@@ -795,25 +788,25 @@ __global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveAr
             float4 *B = sm + per;
             if (C == 1) {
                 LocalSlotsM st{A, B};
-                solve_worker<C, U, P>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+                solve_worker<C, U, P, X>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             } else {
                 ClusterSlotsM<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B), per};
-                solve_worker<C, U, P>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+                solve_worker<C, U, P, X>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             }
         } else {
             float2 *B = reinterpret_cast<float2 *>(sm + per);
             if (C == 1) {
                 LocalSlots st{A, B};
-                solve_worker<C, U, P>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+                solve_worker<C, U, P, X>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             } else {
                 ClusterSlots<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B), per};
-                solve_worker<C, U, P>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
+                solve_worker<C, U, P, X>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             }
         }
     } else if (rank == 0) {
         // one CTA takes the whole worker: every owner bucket of every colour
         LocalSlots st{a.scratch + (size_t)b0, reinterpret_cast<float2 *>(a.scratch + (size_t)a.n_entries) + b0};
-        solve_worker<1, U, false>(a, st, p, 0, nb, Buckets{goff, 2 * OWNER_RANKS, OWNER_RANKS}, row0, row1);
+        solve_worker<1, U, false, X>(a, st, p, 0, nb, Buckets{goff, 2 * OWNER_RANKS, OWNER_RANKS}, row0, row1);
     }
 }
 
@@ -823,10 +816,10 @@ int solve_smem_bytes(int slots, bool masses) {
     return slots * (int)(masses ? 2 * sizeof(float4) : sizeof(float4) + sizeof(float2));
 }
 
-template <int C, int U, bool M, bool P>
+template <int C, int U, bool M, bool P, bool X>
 static void launch_solve_c(const SolveArgs &a, int threads, cudaStream_t s) {
     int smem = solve_smem_bytes(a.smem_slots, M);
-    CK(cudaFuncSetAttribute(k_solve<C, U, M, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaFuncSetAttribute(k_solve<C, U, M, P, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.n_parts * C);
     cfg.blockDim = dim3(threads);
@@ -839,30 +832,40 @@ static void launch_solve_c(const SolveArgs &a, int threads, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, k_solve<C, U, M, P>, a));
+    CK(cudaLaunchKernelEx(&cfg, k_solve<C, U, M, P, X>, a));
     note_launch();
 }
 
-template <int U, bool M, bool P>
+template <int U, bool M, bool P, bool X = false>
 static void launch_solve_u(const SolveArgs &a, int threads, int cluster, cudaStream_t s) {
     switch (cluster) {
-        case 8: launch_solve_c<8, U, M, P>(a, threads, s); break;
-        case 6: launch_solve_c<6, U, M, P>(a, threads, s); break;
-        case 4: launch_solve_c<4, U, M, P>(a, threads, s); break;
-        case 3: launch_solve_c<3, U, M, P>(a, threads, s); break;
-        case 2: launch_solve_c<2, U, M, P>(a, threads, s); break;
-        default: launch_solve_c<1, U, M, P>(a, threads, s); break;
+        case 8: launch_solve_c<8, U, M, P, X>(a, threads, s); break;
+        case 6: launch_solve_c<6, U, M, P, X>(a, threads, s); break;
+        case 4: launch_solve_c<4, U, M, P, X>(a, threads, s); break;
+        case 3: launch_solve_c<3, U, M, P, X>(a, threads, s); break;
+        case 2: launch_solve_c<2, U, M, P, X>(a, threads, s); break;
+        default: launch_solve_c<1, U, M, P, X>(a, threads, s); break;
     }
 }
 
 void launch_solve(const SolveArgs &a, int threads, int cluster, int unroll, bool masses, cudaStream_t s) {
     if (!a.n_parts) return;
     if (threads > SOLVE_THREADS) threads = SOLVE_THREADS;
-    if (unroll == 2) {
-        // a full-size CTA (one per SM) with the masses in shared memory loads rows ahead
-        if (masses && threads == SOLVE_THREADS) launch_solve_u<2, true, true>(a, threads, cluster, s);
-        else if (masses) launch_solve_u<2, true, false>(a, threads, cluster, s);
-        else launch_solve_u<2, false, false>(a, threads, cluster, s);
+    if (a.row_full) {
+        // a context with boxes: the kernels that hold the full rows (two rows
+        // per thread, no rows loaded ahead; one CTA per SM at 512 threads)
+        if (masses) launch_solve_u<2, true, false, true>(a, threads, cluster, s);
+        else launch_solve_u<2, false, false, true>(a, threads, cluster, s);
+    } else if (unroll == 2) {
+        // a full-size CTA (one per SM) loads rows ahead
+        if (threads == SOLVE_THREADS) {
+            if (masses) launch_solve_u<2, true, true>(a, threads, cluster, s);
+            else launch_solve_u<2, false, true>(a, threads, cluster, s);
+        } else if (masses) {
+            launch_solve_u<2, true, false>(a, threads, cluster, s);
+        } else {
+            launch_solve_u<2, false, false>(a, threads, cluster, s);
+        }
     } else {
         if (masses) launch_solve_u<1, true, false>(a, threads, cluster, s);
         else launch_solve_u<1, false, false>(a, threads, cluster, s);

@@ -165,7 +165,7 @@ struct RowArgs {
     const float *scene_mu;
     float dt_override;
     float erp, slop;
-    float4 *r0, *r1, *r2, *r3, *r4;   // r2: joints only; r4: contacts only
+    float4 *r0, *r1, *r2, *r3;   // r2: joints only
     int *rpair;                // [np] pair index of every row (canonical order)
     float4 *rlam;
     int *status;
@@ -206,7 +206,7 @@ struct SolveArgs {
     float3 gravity;
     const float4 *st;
     const float *scene_mu;
-    const float4 *r0, *r1, *r2, *r3, *r4;
+    const float4 *r0, *r1, *r2, *r3;
     const int *rpair;
     float4 *rlam;
     int n_entries;
