@@ -31,7 +31,7 @@
 #define DEV_ERR_MEMBERSHIP 3
 #define DEV_ERR_COLOURS 4
 #define DEV_ERR_TIMEOUT 5
-#define DEV_ERR_SLOTS 6        // a worker slot out of range (reserved)
+#define DEV_ERR_SLOTS 6        // a worker of 2^24 or more bodies (beyond the slot codes)
 
 namespace ovl {
 

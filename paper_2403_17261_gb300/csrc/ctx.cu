@@ -44,7 +44,7 @@ ovl_status check_device_status(ovl_ctx *c) {
             return fail(c, OVL_ERR_CAPACITY,
                         "a body touches more spheres of larger index than its neighbour capacity "
                         "(set from the radii: deep interpenetration)");
-        case DEV_ERR_SLOTS: return fail(c, OVL_ERR_CAPACITY, "worker slot out of range");
+        case DEV_ERR_SLOTS: return fail(c, OVL_ERR_CAPACITY, "a worker holds 2^24 or more bodies");
         case DEV_ERR_NONFINITE: return fail(c, OVL_ERR_NONFINITE, "non-finite value in the blended state");
         case DEV_ERR_MEMBERSHIP:
             return fail(c, OVL_ERR_MEMBERSHIP, "dynamic body with no worker, or a worker index out of range");
@@ -296,9 +296,10 @@ int solve_smem_budget(ovl_ctx *c, int ctas_per_sm) {
 }
 
 // Shared-memory body slots per CTA (24 B each, the layout without masses: the
-// CTA counts are planned with it, so adding the masses never adds CTAs)
+// CTA counts are planned with it, so adding the masses never adds CTAs), less
+// the CTA's zero slot
 int solve_slot_capacity(ovl_ctx *c, int ctas_per_sm) {
-    int n = std::max(0, solve_smem_budget(c, ctas_per_sm) / solve_smem_bytes(1, false));
+    int n = std::max(0, solve_smem_budget(c, ctas_per_sm) / solve_slot_bytes(false) - 1);
     return c->P.smem_slot_limit > 0 ? std::min(n, c->P.smem_slot_limit) : n;
 }
 
@@ -441,7 +442,7 @@ bool plan_solve_classes(ovl_ctx *c, const SolveShape &shape, std::vector<SolveCl
     const int cap_plain = solve_slot_capacity(c, shape.per_sm);
     int cap = cap_plain;
     if (c->P.smem_slot_limit <= 0) {
-        const int cap_m = solve_smem_budget(c, shape.per_sm) / solve_smem_bytes(1, true);
+        const int cap_m = solve_smem_budget(c, shape.per_sm) / solve_slot_bytes(true) - 1;
         const long long with_m = fewest_ctas(c, cap_m), plain = fewest_ctas(c, cap_plain);
         if (with_m > 0 && (with_m <= slots || plain < 0 || plain > 2 * slots)) cap = cap_m;
     }
@@ -532,6 +533,7 @@ void phase_rows(ovl_ctx *c, float dt_override) {
     a.scene_dt = c->scene_dt.p; a.scene_mu = c->scene_mu.p; a.dt_override = dt_override;
     a.erp = c->P.erp; a.slop = c->P.slop;
     a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
+    a.part_bstart = c->part_bstart.p; a.solve_C = c->solve_C.p;
     a.rpair = c->rpair.p; a.status = c->status.p;
     if (c->has_boxes) {
         c->row_full.ensure(npr + 1);

@@ -552,12 +552,30 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
 //   r0 = (n, slot_b)  r1 = (r_a, r_b, target_n, slot_a)  r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b)
 // Ball joints (rows along the world axes):
 //   r0 = (r_A, target_x)  r1 = (r_B, target_y)  r2 = (target_z, 0, slot_a, slot_b)  r3 as for contacts
-// (a slot word holds the int bits of the worker slot, -1 for a static end).
+// A slot word holds the bits of the solver's slot code of a worker slot s:
+// rank << 24 | i, with rank = s / per the CTA of the worker's group that
+// holds s (per = ceil(nb / C), C the worker's CTAs in the solve plan) and i
+// = s - rank per; a static end (or a body not active in this worker) gets
+// the zero slot i = per of the CTA that owns the row (the one holding its
+// first dynamic body).
 // with r_A, r_B the pivot offsets from each body's centre in the world frame.
 // ---------------------------------------------------------------------------
 
-// a worker slot stored in a record word (its int bits; -1: static end)
-__device__ __forceinline__ float slot_word(int s) { return __int_as_float(s < 0 ? -1 : s); }
+// the two slot words of a row (see above); a worker of 2^24 bodies or more
+// is a capacity error
+struct SlotWords { float a, b; };
+__device__ __forceinline__ SlotWords slot_words(const RowArgs &a, int p, int2 sl) {
+    const int nb = a.part_bstart[p + 1] - a.part_bstart[p];
+    const int C = max(1, a.solve_C[p]);
+    const int per = max(1, (nb + C - 1) / C);
+    if (per >= (1 << 24) - 1) atomicCAS(a.status, DEV_OK, DEV_ERR_SLOTS);
+    const int own = sl.x >= 0 ? sl.x / per : max(sl.y, 0) / per;
+    auto code = [&](int s) {
+        const uint32_t c = s >= 0 ? ((uint32_t)(s / per) << 24 | (uint32_t)(s % per)) : ((uint32_t)own << 24 | (uint32_t)per);
+        return __uint_as_float(c);
+    };
+    return SlotWords{code(sl.x), code(sl.y)};
+}
 
 __device__ __forceinline__ bool body_is_box(const float4 *half, int b) {
     if (!half || b < 0) return false;
@@ -607,6 +625,7 @@ __global__ void k_rows(RowArgs a) {
         const int2 sl = a.p_slot[k];
         const int scene = a.part_scene[a.ps_part[k]];
         const float h = a.dt_override > 0.f ? a.dt_override : a.scene_dt[scene];
+        const SlotWords sw = slot_words(a, a.ps_part[k], sl);
         if (a.row_full) {
             // a constraint with a box end: the full row, plus the slots in the
             // plain records (the solver reads its bodies through them)
@@ -633,8 +652,8 @@ __global__ void k_rows(RowArgs a) {
                     const float phi = nphi.w;
                     tg[0] = phi > 0.f ? -phi / h : a.erp * fmaxf(-phi - a.slop, 0.f) / h;
                     tg[1] = tg[2] = 0.f;
-                    a.r0[r] = make_float4(0.f, 0.f, 0.f, slot_word(sl.y));
-                    a.r1[r] = make_float4(0.f, 0.f, 0.f, slot_word(sl.x));
+                    a.r0[r] = make_float4(0.f, 0.f, 0.f, sw.b);
+                    a.r1[r] = make_float4(0.f, 0.f, 0.f, sw.a);
                     a.r3[r] = z;
                 } else {
                     const int j = i - a.nc;
@@ -663,7 +682,7 @@ __global__ void k_rows(RowArgs a) {
                     dir[2] = make_float3(0.f, 0.f, 1.f);
                     a.r0[r] = z;
                     a.r1[r] = z;
-                    a.r2[r] = make_float4(0.f, 0.f, slot_word(sl.x), slot_word(sl.y));
+                    a.r2[r] = make_float4(0.f, 0.f, sw.a, sw.b);
                     a.r3[r] = z;
                 }
                 write_full_row(a, r, ea, eb, rA, rB, dir, tg);
@@ -684,8 +703,8 @@ __global__ void k_rows(RowArgs a) {
             }
             float phi = nphi.w;
             float target = phi > 0.f ? -phi / h : a.erp * fmaxf(-phi - a.slop, 0.f) / h;
-            a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, slot_word(sl.y));
-            a.r1[r] = make_float4(ra, rb, target, slot_word(sl.x));
+            a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, sw.b);
+            a.r1[r] = make_float4(ra, rb, target, sw.a);
             a.r3[r] = make_float4(ima, imb, iia, iib);
         } else {
             const int j = i - a.nc;
@@ -718,7 +737,7 @@ __global__ void k_rows(RowArgs a) {
             float g = -a.erp / h;
             a.r0[r] = make_float4(rA.x, rA.y, rA.z, g * err.x);
             a.r1[r] = make_float4(rB.x, rB.y, rB.z, g * err.y);
-            a.r2[r] = make_float4(g * err.z, 0.f, slot_word(sl.x), slot_word(sl.y));
+            a.r2[r] = make_float4(g * err.z, 0.f, sw.a, sw.b);
             a.r3[r] = make_float4(ima, imb, iia, iib);
         }
         a.rpair[r] = k;

@@ -33,8 +33,8 @@
 // Row records (float4 each): contact r0 = (n, slot_b), r1 = (r_a, r_b,
 // target, slot_a); joint r0 = (r_A, target_x), r1 = (r_B, target_y), r2 =
 // (target_z, 0, slot_a, slot_b); both r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b),
-// read only when the masses are not in shared memory.  A slot is a 32-bit
-// worker slot (-1: static end).  A contact forms t1 = normalise(e_k - (n .
+// read only when the masses are not in shared memory.  Slots are slot codes
+// (below).  A contact forms t1 = normalise(e_k - (n .
 // e_k) n) (k the axis of the smallest |n_k|), k_n = 1 / (1/m_a + 1/m_b) and
 // the tangents' k_t = 1 / (1/m_a + 1/m_b + r_a^2 / I_a + r_b^2 / I_b) from
 // the bodies' masses, so both layouts compute the same bits.
@@ -77,38 +77,54 @@ struct Body {
 
 
 // ---- body storage --------------------------------------------------------
-// Plain pointers: one CTA, shared or global memory.  kMasses: the slots hold
-// the inverse mass and inertia too (else they come with the row).
+// A row names its bodies by slot codes: rank << 24 | i, body i of the slot
+// range CTA `rank` of the group holds (rank 0 and the worker slot itself
+// with one CTA).  A static end (or a body not active in this worker) names
+// the zero slot i = per of the row's own CTA: zero velocity, mass and
+// inertia, and every impulse leaves it zero, so no row branches on its ends.
+// Shared-memory slots per CTA: per + 1.
+
+__device__ __forceinline__ uint32_t code_rank(uint32_t c) { return c >> 24; }
+__device__ __forceinline__ uint32_t code_index(uint32_t c) { return c & 0xffffffu; }
+
+// One CTA, shared memory.  kMasses: the slots hold the inverse mass and
+// inertia too (else they come with the row).
 struct LocalSlots {
     static constexpr bool kMasses = false;
     float4 *A;   // (vx, vy, vz, wx)
     float2 *B;   // (wy, wz)
-    __device__ __forceinline__ void load(int s, Body &b) const {
-        float4 x = A[s];
-        float2 y = B[s];
+    __device__ __forceinline__ uint32_t code_of(int s) const { return (uint32_t)s; }
+    __device__ __forceinline__ void load(uint32_t c, Body &b) const {
+        const uint32_t i = code_index(c);
+        const float4 x = A[i];
+        const float2 y = B[i];
         b.v = make_float3(x.x, x.y, x.z);
         b.w = make_float3(x.w, y.x, y.y);
     }
-    __device__ __forceinline__ void store(int s, const Body &b) const {
-        A[s] = make_float4(b.v.x, b.v.y, b.v.z, b.w.x);
-        B[s] = make_float2(b.w.y, b.w.z);
+    __device__ __forceinline__ void store(uint32_t c, const Body &b) const {
+        const uint32_t i = code_index(c);
+        A[i] = make_float4(b.v.x, b.v.y, b.v.z, b.w.x);
+        B[i] = make_float2(b.w.y, b.w.z);
     }
 };
 
+// (v, 1/m) and (w, 1/I) of slot i at S[2i], S[2i + 1]
 struct LocalSlotsM {
     static constexpr bool kMasses = true;
-    float4 *A;   // (vx, vy, vz, 1/m)
-    float4 *B;   // (wx, wy, wz, 1/I)
-    __device__ __forceinline__ void load(int s, Body &b) const {
-        const float4 x = A[s], y = B[s];
+    float4 *S;
+    __device__ __forceinline__ uint32_t code_of(int s) const { return (uint32_t)s; }
+    __device__ __forceinline__ void load(uint32_t c, Body &b) const {
+        const uint32_t i = code_index(c);
+        const float4 x = S[2 * i], y = S[2 * i + 1];
         b.v = make_float3(x.x, x.y, x.z);
         b.w = make_float3(y.x, y.y, y.z);
         b.im = x.w;
         b.ii = y.w;
     }
-    __device__ __forceinline__ void store(int s, const Body &b) const {
-        A[s] = make_float4(b.v.x, b.v.y, b.v.z, b.im);
-        B[s] = make_float4(b.w.x, b.w.y, b.w.z, b.ii);
+    __device__ __forceinline__ void store(uint32_t c, const Body &b) const {
+        const uint32_t i = code_index(c);
+        S[2 * i] = make_float4(b.v.x, b.v.y, b.v.z, b.im);
+        S[2 * i + 1] = make_float4(b.w.x, b.w.y, b.w.z, b.ii);
     }
 };
 
@@ -118,73 +134,89 @@ __device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
     return r;
 }
 
-// Distributed over the C CTAs of a cluster: slot s in CTA k = s / per at
-// index s - k per.  The accesses are volatile asm, so they keep their order
-// among themselves and with the cluster barriers; ordinary loads of row
-// records may move around them.
+// Distributed over the C CTAs of a cluster: the slot range of CTA `rank` is
+// in that CTA's shared memory, reached through distributed shared memory
+// (mapa + ld/st.shared::cluster).  The accesses are volatile asm, so they
+// keep their order among themselves and with the cluster barriers; ordinary
+// loads of row records may move around them.
 template <int C>
 struct ClusterSlots {
     static constexpr bool kMasses = false;
     uint32_t A, B;   // shared-window offsets of this CTA's arrays (same in every CTA)
-    int per;         // slots per CTA
-    __device__ __forceinline__ uint32_t owner(int s) const {
-        uint32_t r = 0;
-#pragma unroll
-        for (int k = 1; k < C; ++k) r += s >= k * per ? 1u : 0u;
-        return r;
-    }
-    __device__ __forceinline__ void load(int s, Body &b) const {
-        const uint32_t r = owner(s), i = (uint32_t)s - r * (uint32_t)per;
-        const uint32_t a = mapa(A + 16u * i, r), c = mapa(B + 8u * i, r);
+    uint32_t per;    // slots per CTA
+    __device__ __forceinline__ uint32_t code_of(int s) const { return ((uint32_t)s / per) << 24 | (uint32_t)s % per; }
+    __device__ __forceinline__ void load(uint32_t c, Body &b) const {
+        const uint32_t r = code_rank(c), i = code_index(c);
+        const uint32_t a = mapa(A + 16u * i, r), d = mapa(B + 8u * i, r);
         float4 x;
         float2 y;
         asm volatile("ld.shared::cluster.v4.f32 {%0,%1,%2,%3}, [%4];"
                      : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w) : "r"(a));
-        asm volatile("ld.shared::cluster.v2.f32 {%0,%1}, [%2];" : "=f"(y.x), "=f"(y.y) : "r"(c));
+        asm volatile("ld.shared::cluster.v2.f32 {%0,%1}, [%2];" : "=f"(y.x), "=f"(y.y) : "r"(d));
         b.v = make_float3(x.x, x.y, x.z);
         b.w = make_float3(x.w, y.x, y.y);
     }
-    __device__ __forceinline__ void store(int s, const Body &b) const {
-        const uint32_t r = owner(s), i = (uint32_t)s - r * (uint32_t)per;
-        const uint32_t a = mapa(A + 16u * i, r), c = mapa(B + 8u * i, r);
+    __device__ __forceinline__ void store(uint32_t c, const Body &b) const {
+        const uint32_t r = code_rank(c), i = code_index(c);
+        const uint32_t a = mapa(A + 16u * i, r), d = mapa(B + 8u * i, r);
         asm volatile("st.shared::cluster.v4.f32 [%0], {%1,%2,%3,%4};"
                      :: "r"(a), "f"(b.v.x), "f"(b.v.y), "f"(b.v.z), "f"(b.w.x));
-        asm volatile("st.shared::cluster.v2.f32 [%0], {%1,%2};" :: "r"(c), "f"(b.w.y), "f"(b.w.z));
+        asm volatile("st.shared::cluster.v2.f32 [%0], {%1,%2};" :: "r"(d), "f"(b.w.y), "f"(b.w.z));
     }
 };
 
-// the same with the masses: 2 x 16 B per slot
+// the same with the masses: one 32 B slot, one mapa per access
 template <int C>
 struct ClusterSlotsM {
     static constexpr bool kMasses = true;
-    uint32_t A, B;
-    int per;
-    __device__ __forceinline__ uint32_t owner(int s) const {
-        uint32_t r = 0;
-#pragma unroll
-        for (int k = 1; k < C; ++k) r += s >= k * per ? 1u : 0u;
-        return r;
-    }
-    __device__ __forceinline__ void load(int s, Body &b) const {
-        const uint32_t r = owner(s), i = (uint32_t)s - r * (uint32_t)per;
-        const uint32_t a = mapa(A + 16u * i, r), c = mapa(B + 16u * i, r);
+    uint32_t S;      // shared-window offset of this CTA's slots (same in every CTA)
+    uint32_t per;    // slots per CTA
+    __device__ __forceinline__ uint32_t code_of(int s) const { return ((uint32_t)s / per) << 24 | (uint32_t)s % per; }
+    __device__ __forceinline__ void load(uint32_t c, Body &b) const {
+        const uint32_t a = mapa(S + 32u * code_index(c), code_rank(c));
         float4 x, y;
         asm volatile("ld.shared::cluster.v4.f32 {%0,%1,%2,%3}, [%4];"
                      : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w) : "r"(a));
         asm volatile("ld.shared::cluster.v4.f32 {%0,%1,%2,%3}, [%4];"
-                     : "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w) : "r"(c));
+                     : "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w) : "r"(a + 16u));
         b.v = make_float3(x.x, x.y, x.z);
         b.w = make_float3(y.x, y.y, y.z);
         b.im = x.w;
         b.ii = y.w;
     }
-    __device__ __forceinline__ void store(int s, const Body &b) const {
-        const uint32_t r = owner(s), i = (uint32_t)s - r * (uint32_t)per;
-        const uint32_t a = mapa(A + 16u * i, r), c = mapa(B + 16u * i, r);
+    __device__ __forceinline__ void store(uint32_t c, const Body &b) const {
+        const uint32_t a = mapa(S + 32u * code_index(c), code_rank(c));
         asm volatile("st.shared::cluster.v4.f32 [%0], {%1,%2,%3,%4};"
                      :: "r"(a), "f"(b.v.x), "f"(b.v.y), "f"(b.v.z), "f"(b.im));
         asm volatile("st.shared::cluster.v4.f32 [%0], {%1,%2,%3,%4};"
-                     :: "r"(c), "f"(b.w.x), "f"(b.w.y), "f"(b.w.z), "f"(b.ii));
+                     :: "r"(a + 16u), "f"(b.w.x), "f"(b.w.y), "f"(b.w.z), "f"(b.ii));
+    }
+};
+
+// A worker too large for shared memory, solved by one CTA in a global
+// scratch area of worker slots: a code's slot is rank per + i, and i = per
+// is a static end (no zero slot here).
+struct GlobalSlots {
+    static constexpr bool kMasses = false;
+    float4 *A;
+    float2 *B;
+    uint32_t per;    // slots per CTA of the worker's launch (the codes' ranges)
+    __device__ __forceinline__ uint32_t code_of(int s) const { return ((uint32_t)s / per) << 24 | (uint32_t)s % per; }
+    __device__ __forceinline__ void load(uint32_t c, Body &b) const {
+        const uint32_t i = code_index(c);
+        if (i >= per) { b.v = make_float3(0.f, 0.f, 0.f); b.w = b.v; return; }
+        const uint32_t s = code_rank(c) * per + i;
+        const float4 x = A[s];
+        const float2 y = B[s];
+        b.v = make_float3(x.x, x.y, x.z);
+        b.w = make_float3(x.w, y.x, y.y);
+    }
+    __device__ __forceinline__ void store(uint32_t c, const Body &b) const {
+        const uint32_t i = code_index(c);
+        if (i >= per) return;
+        const uint32_t s = code_rank(c) * per + i;
+        A[s] = make_float4(b.v.x, b.v.y, b.v.z, b.w.x);
+        B[s] = make_float2(b.w.y, b.w.z);
     }
 };
 
@@ -210,20 +242,19 @@ __device__ __forceinline__ void fetch_row_rest(const SolveArgs &a, int r, bool j
     if (joint) w.z = a.r2[r];
 }
 
-// the row's two worker slots (a, b); -1 for a static end
-__device__ __forceinline__ int2 row_slots(const Row &w) {
-    return w.joint ? make_int2(__float_as_int(w.z.z), __float_as_int(w.z.w))
-                   : make_int2(__float_as_int(w.y.w), __float_as_int(w.x.w));
+// the slot codes (a, b) of a row
+__device__ __forceinline__ uint2 row_slots(const Row &w) {
+    return w.joint ? make_uint2(__float_as_uint(w.z.z), __float_as_uint(w.z.w))
+                   : make_uint2(__float_as_uint(w.y.w), __float_as_uint(w.x.w));
 }
 
-// a static end (or a body not active in this worker) has zero velocity,
-// inverse mass and inverse inertia
+// a static end reads its zero slot (or, without the masses in the slots,
+// zero masses from r3)
 template <class S>
 __device__ __forceinline__ void load_pair(const S &st, const Row &w, Body &A, Body &B) {
-    const int2 slots = row_slots(w);
-    const int sa = slots.x, sb = slots.y;
-    if (sa >= 0) st.load(sa, A); else { A.v = make_float3(0.f, 0.f, 0.f); A.w = A.v; A.im = 0.f; A.ii = 0.f; }
-    if (sb >= 0) st.load(sb, B); else { B.v = make_float3(0.f, 0.f, 0.f); B.w = B.v; B.im = 0.f; B.ii = 0.f; }
+    const uint2 slots = row_slots(w);
+    st.load(slots.x, A);
+    st.load(slots.y, B);
     if (!S::kMasses) { A.im = w.m.x; B.im = w.m.y; A.ii = w.m.z; B.ii = w.m.w; }
 }
 
@@ -242,10 +273,9 @@ __device__ __forceinline__ void contact_frame(const Row &w, const Body &A, const
 }
 
 template <class S>
-__device__ __forceinline__ void store_pair(const S &st, int2 slots, const Body &A, const Body &B) {
-    const int sa = slots.x, sb = slots.y;
-    if (sa >= 0) st.store(sa, A);
-    if (sb >= 0) st.store(sb, B);
+__device__ __forceinline__ void store_pair(const S &st, uint2 slots, const Body &A, const Body &B) {
+    st.store(slots.x, A);
+    st.store(slots.y, B);
 }
 
 // ---- rows ----------------------------------------------------------------
@@ -588,7 +618,16 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
         x.w = make_float3(w.x, w.y, w.z);
         x.im = v.w;
         x.ii = w.w;
-        st.store(s, x);
+        st.store(st.code_of(s), x);
+    }
+    // this CTA's zero slot (static ends of its rows)
+    if (tid == 0) {
+        Body z;
+        z.v = make_float3(0.f, 0.f, 0.f);
+        z.w = z.v;
+        z.im = 0.f;
+        z.ii = 0.f;
+        st.store((uint32_t)rank << 24 | (uint32_t)per, z);
     }
     group_sync<C>();
     const int ncol = a.part_ncol[p];
@@ -740,7 +779,7 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
         int b = a.entry_body[e];
         float4 x = a.st[4 * b], q = a.st[4 * b + 1], v0 = a.st[4 * b + 2], w0 = a.st[4 * b + 3];
         Body y;
-        st.load(s, y);
+        st.load(st.code_of(s), y);
         float3 v = y.v, w = y.w;
         float4 xn = make_float4(x.x + h * v.x, x.y + h * v.y, x.z + h * v.z, x.w);
         // (0, w) (x) q = (-w.qv, qw w + w x qv)
@@ -783,38 +822,41 @@ __global__ void __launch_bounds__(SOLVE_THREADS, U == 1 ? 2 : 1) k_solve(SolveAr
     __syncthreads();
     const int row0 = goff[0], row1 = goff[OWNER_NB - 1];
     if (per <= a.smem_slots) {
+        // per + 1 slots: the CTA's range and its zero slot
         float4 *A = sm;
         if (M) {
-            float4 *B = sm + per;
             if (C == 1) {
-                LocalSlotsM st{A, B};
+                LocalSlotsM st{A};
                 solve_worker<C, U, P, X>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             } else {
-                ClusterSlotsM<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B), per};
+                ClusterSlotsM<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)per};
                 solve_worker<C, U, P, X>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             }
         } else {
-            float2 *B = reinterpret_cast<float2 *>(sm + per);
+            float2 *B = reinterpret_cast<float2 *>(sm + per + 1);
             if (C == 1) {
                 LocalSlots st{A, B};
                 solve_worker<C, U, P, X>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             } else {
-                ClusterSlots<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B), per};
+                ClusterSlots<C> st{(uint32_t)__cvta_generic_to_shared(A), (uint32_t)__cvta_generic_to_shared(B),
+                                   (uint32_t)per};
                 solve_worker<C, U, P, X>(a, st, p, rank, per, Buckets{boff, 3, 1}, row0, row1);
             }
         }
     } else if (rank == 0) {
         // one CTA takes the whole worker: every owner bucket of every colour
-        LocalSlots st{a.scratch + (size_t)b0, reinterpret_cast<float2 *>(a.scratch + (size_t)a.n_entries) + b0};
+        GlobalSlots st{a.scratch + (size_t)b0, reinterpret_cast<float2 *>(a.scratch + (size_t)a.n_entries) + b0,
+                       (uint32_t)per};
         solve_worker<1, U, false, X>(a, st, p, 0, nb, Buckets{goff, 2 * OWNER_RANKS, OWNER_RANKS}, row0, row1);
     }
 }
 
 }  // namespace
 
-int solve_smem_bytes(int slots, bool masses) {
-    return slots * (int)(masses ? 2 * sizeof(float4) : sizeof(float4) + sizeof(float2));
-}
+int solve_slot_bytes(bool masses) { return (int)(masses ? 2 * sizeof(float4) : sizeof(float4) + sizeof(float2)); }
+
+// a CTA's slots and its zero slot
+int solve_smem_bytes(int slots, bool masses) { return (slots + 1) * solve_slot_bytes(masses); }
 
 template <int C, int U, bool M, bool P, bool X>
 static void launch_solve_c(const SolveArgs &a, int threads, cudaStream_t s) {

@@ -166,6 +166,8 @@ struct RowArgs {
     float dt_override;
     float erp, slop;
     float4 *r0, *r1, *r2, *r3;   // r2: joints only
+    const int *part_bstart;      // [P+1] worker slot ranges
+    const int *solve_C;          // [P] CTAs per worker in the solve plan (slot codes)
     int *rpair;                // [np] pair index of every row (canonical order)
     float4 *rlam;
     int *status;
@@ -228,7 +230,8 @@ struct SolveArgs {
 // per slot; contact rows read as two records); else 24 B per slot
 void launch_solve(const SolveArgs &a, int threads, int cluster, int unroll, bool masses, cudaStream_t s);
 int solve_ctas_per_sm(int unroll);
-int solve_smem_bytes(int slots, bool masses);
+int solve_slot_bytes(bool masses);              // bytes of one shared-memory body slot
+int solve_smem_bytes(int slots, bool masses);   // a CTA's slots plus its zero slot
 
 // ---- geodesics, weights, blend (k_blend.cu) --------------------------------
 struct GeoArgs {
