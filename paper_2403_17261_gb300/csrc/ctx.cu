@@ -269,12 +269,12 @@ void phase_membership(ovl_ctx *c, float dt_override) {
 
 int colour_smem_capacity(ovl_ctx *c) {
     int avail = c->smem_optin - colour_static_smem() - 1024;
-    int n = std::max(0, avail / 24);
+    int n = std::max(0, avail / 16);
     return c->P.smem_slot_limit > 0 ? std::min(n, c->P.smem_slot_limit) : n;
 }
 
 // CTAs per worker for the colouring: the smallest cluster whose share of the
-// largest worker's slots fits one CTA's shared memory (24 B per slot)
+// largest worker's slots fits one CTA's shared memory (16 B per slot)
 void colour_config(ovl_ctx *c, int *cluster, int *slots) {
     const int cap = colour_smem_capacity(c);
     const int fixed = (c->P.pgs_cluster == 1 || c->P.pgs_cluster == 2 || c->P.pgs_cluster == 4 ||
@@ -498,7 +498,8 @@ void phase_colour(ovl_ctx *c) {
     a.p_key = c->p_key.p; a.p_slot = c->p_slot.p; a.p_colour = c->p_colour.p;
     a.part_ncol = c->part_ncol.p; a.col_off = c->col_off.p; a.pair_of_row = c->pair_of_row.p;
     a.part_rounds = c->part_rounds.p;
-    a.scratch = c->colour_scratch.p; a.status = c->status.p;
+    a.scratch = c->colour_scratch.p; a.hi_mask = c->colour_scratch.p + 2 * (size_t)c->ne;
+    a.status = c->status.p;
     a.worklist = c->worklist.p; a.worklist2 = c->worklist2.p;
     a.wprio = c->wprio.p; a.wprio2 = c->wprio2.p;
     const bool fixed = c->P.pgs_cluster > 0 || c->P.smem_slot_limit > 0;

@@ -248,7 +248,8 @@ __device__ __forceinline__ uint32_t mapa_u32(uint32_t a, uint32_t rank) {
 
 // Per-slot colouring state of one worker: the maximum priority of the
 // uncoloured constraints posted this round (array 0) and the mask of colours
-// taken, colours 0-63 (array 1) and 64-127 (array 2).
+// 0-63 taken (array 1).  Colours 64-127, which only bodies in about 64 or
+// more constraints need, are tracked in global memory (hi_mask).
 // C > 1: spread over the cluster's shared memory, CTA k holding the
 // contiguous slots [k per, (k + 1) per).  The
 // maximum is taken in two 32-bit stages (high words, then low words among the
@@ -258,10 +259,10 @@ __device__ __forceinline__ uint32_t mapa_u32(uint32_t a, uint32_t rank) {
 template <int C>
 struct ColourSlots {
     static constexpr bool two_stage = true;
-    uint32_t b0, b1, b2;   // shared-window offsets of this CTA's arrays (hi/lo words, used mask lo, hi)
-    int per;               // slots per CTA
+    uint32_t b0, b1;   // shared-window offsets of this CTA's arrays (hi/lo words, used mask)
+    int per;           // slots per CTA
     __device__ __forceinline__ uint32_t at(int arr, int s) const {
-        uint32_t base = arr == 0 ? b0 : (arr == 1 ? b1 : b2);
+        uint32_t base = arr == 0 ? b0 : b1;
         uint32_t r = 0;
 #pragma unroll
         for (int k = 1; k < C; ++k) r += s >= k * per ? 1u : 0u;
@@ -294,9 +295,9 @@ struct ColourSlots {
 // one 64-bit atomic max per slot.
 struct ColourPtrs {
     static constexpr bool two_stage = false;
-    unsigned long long *p0, *p1, *p2;
+    unsigned long long *p0, *p1;
     __device__ __forceinline__ unsigned long long *ptr(int arr, int s) const {
-        return (arr == 0 ? p0 : (arr == 1 ? p1 : p2)) + s;
+        return (arr == 0 ? p0 : p1) + s;
     }
     __device__ __forceinline__ void amax_hi(int s, unsigned long long v) const { atomicMax(ptr(0, s), v); }
     __device__ __forceinline__ void amax_lo(int, unsigned long long) const {}
@@ -377,7 +378,10 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, ColourShared &sh
     const int wbase = c0 + (j0 - ncw);
     int4 *wl_cur = a.worklist + q0 + wbase, *wl_next = a.worklist2 + q0 + wbase;
     unsigned long long *pr_cur = a.wprio + q0 + wbase, *pr_next = a.wprio2 + q0 + wbase;
-    for (int s = s_lo + tid; s < s_hi; s += T) { S.st(1, s, 0ull); S.st(2, s, 0ull); }
+    // colours 64-127 of the worker's slots (global memory, read past L1: other
+    // CTAs of the group write them)
+    unsigned long long *hi = a.hi_mask + b0;
+    for (int s = s_lo + tid; s < s_hi; s += T) { S.st(1, s, 0ull); __stcg(hi + s, 0ull); }
     for (int v = tid; v < m0; v += T) {
         const int k = item(v);
         int2 sl = a.p_slot[q0 + k];
@@ -421,18 +425,30 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, ColourShared &sh
                 continue;
             }
             // only this constraint touches its slots in this round
-            unsigned long long u0 = 0ull, u1 = 0ull;   // colours 0-63, 64-127 taken at its slots
-            if (w.y >= 0) { u0 |= S.ld(1, w.y); u1 |= S.ld(2, w.y); }
-            if (w.z >= 0) { u0 |= S.ld(1, w.z); u1 |= S.ld(2, w.z); }
+            unsigned long long u = 0ull;   // colours 0-63 taken at its slots
+            if (w.y >= 0) u |= S.ld(1, w.y);
+            if (w.z >= 0) u |= S.ld(1, w.z);
             int c;
-            if (~u0) c = __ffsll((long long)~u0) - 1;
-            else if (~u1) c = 64 + __ffsll((long long)~u1) - 1;
-            else { c = OVL_MAX_COLOURS - 1; atomicCAS(a.status, DEV_OK, DEV_ERR_COLOURS); }
+            if (~u) {
+                c = __ffsll((long long)~u) - 1;
+                const unsigned long long bit = 1ull << c;
+                if (w.y >= 0) S.st(1, w.y, S.ld(1, w.y) | bit);
+                if (w.z >= 0) S.st(1, w.z, S.ld(1, w.z) | bit);
+            } else {
+                unsigned long long v = 0ull;   // colours 64-127
+                if (w.y >= 0) v |= __ldcg(hi + w.y);
+                if (w.z >= 0) v |= __ldcg(hi + w.z);
+                if (~v) {
+                    c = 64 + __ffsll((long long)~v) - 1;
+                } else {
+                    c = OVL_MAX_COLOURS - 1;
+                    atomicCAS(a.status, DEV_OK, DEV_ERR_COLOURS);
+                }
+                const unsigned long long bit = 1ull << (c - 64);
+                if (w.y >= 0) __stcg(hi + w.y, __ldcg(hi + w.y) | bit);
+                if (w.z >= 0) __stcg(hi + w.z, __ldcg(hi + w.z) | bit);
+            }
             a.p_colour[q0 + w.x] = c;
-            const int arr = c < 64 ? 1 : 2;
-            const unsigned long long bit = 1ull << (c & 63);
-            if (w.y >= 0) S.st(arr, w.y, S.ld(arr, w.y) | bit);
-            if (w.z >= 0) S.st(arr, w.z, S.ld(arr, w.z) | bit);
             atomicMax(&ncol_sh, c + 1);
         }
         __syncthreads();
@@ -530,18 +546,17 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
     const int nb = a.part_bstart[p + 1] - a.part_bstart[p];
     const int per = (nb + C - 1) / C;
     if (per <= a.smem_slots) {
-        unsigned long long *mx = dyn_smem, *u = dyn_smem + per, *u2 = dyn_smem + 2 * per;
+        unsigned long long *mx = dyn_smem, *u = dyn_smem + per;
         if (C == 1) {
-            ColourPtrs S{mx, u, u2};
+            ColourPtrs S{mx, u};
             colour_worker<1>(a, S, sh, p, 0, per);
         } else {
-            ColourSlots<C> S{(uint32_t)__cvta_generic_to_shared(mx), (uint32_t)__cvta_generic_to_shared(u),
-                             (uint32_t)__cvta_generic_to_shared(u2), per};
+            ColourSlots<C> S{(uint32_t)__cvta_generic_to_shared(mx), (uint32_t)__cvta_generic_to_shared(u), per};
             colour_worker<C>(a, S, sh, p, rank, per);
         }
     } else if (rank == 0) {
-        unsigned long long *mx = a.scratch + 3 * (size_t)a.part_bstart[p];
-        ColourPtrs S{mx, mx + nb, mx + 2 * (size_t)nb};
+        unsigned long long *mx = a.scratch + 2 * (size_t)a.part_bstart[p];
+        ColourPtrs S{mx, mx + nb};
         colour_worker<1>(a, S, sh, p, 0, nb);
     }
 }
@@ -808,7 +823,7 @@ void launch_worker_cost_keys(const int *part_pstart, int P, uint32_t *keys, uint
 }
 template <int C>
 static void launch_colour_c(const ColourArgs &a, cudaStream_t s) {
-    size_t smem = (size_t)a.smem_slots * 3 * sizeof(unsigned long long);
+    size_t smem = (size_t)a.smem_slots * 2 * sizeof(unsigned long long);
     CK(cudaFuncSetAttribute(k_colour<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.n_parts * C);

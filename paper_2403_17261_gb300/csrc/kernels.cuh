@@ -137,6 +137,7 @@ struct ColourArgs {
     int *col_off;              // [P][2*OVL_MAX_COLOURS+1] absolute row offsets per (colour, kind)
     int *pair_of_row;          // [np]
     unsigned long long *scratch;  // 2 per entry, for workers too large for shared memory
+    unsigned long long *hi_mask;  // [ne] colours 64-127 taken at every worker slot
     int4 *worklist, *worklist2;                 // [np] each: uncoloured constraints per round
     unsigned long long *wprio, *wprio2;         // [np] each: their priorities
     int smem_slots;            // slots that fit in shared memory
