@@ -120,6 +120,9 @@ __device__ __forceinline__ void write_box_contact(int o, int a, int b, int k, do
 }
 
 // neighbours b > a of body a (sorted ascending) + its plane contacts
+// X: the context has boxes.  The box narrow phase (FP64 locals, a large
+// stack) is only in the X kernels, so sphere scenes keep a lean kernel.
+template <bool X>
 __global__ void k_find_pairs(const float4 *__restrict__ st, const float *__restrict__ im, int n,
                              const int *__restrict__ sob, const int *__restrict__ scene_flags,
                              const int4 *__restrict__ cell, const int *__restrict__ bstart,
@@ -179,7 +182,7 @@ __global__ void k_find_pairs(const float4 *__restrict__ st, const float *__restr
         nb_count[a] = cnt;
         // contacts: one per sphere pair, 0-4 per pair with a box end
         int nct = cnt;
-        if (half) {
+        if constexpr (X) {
             const int *lst = spilled ? gl : local;
             nct = 0;
             for (int j = 0; j < cnt; ++j) {
@@ -192,20 +195,23 @@ __global__ void k_find_pairs(const float4 *__restrict__ st, const float *__restr
         }
         int np_ = 0;
         if (dyn_a) {
-            const bool box_a = is_box(half, a);
+            const bool box_a = X && is_box(half, a);
             for (int k = plane_ptr[s]; k < plane_ptr[s + 1]; ++k) {
                 const float4 pl = planes[plane_list[k]];
                 if (plane_gap(pa, pl) > margin) continue;   // the (bounding) sphere test
                 if (!box_a) { ++np_; continue; }
-                double3 pts[4], nrm;
-                double gaps[4];
-                np_ += box_plane_pair(st, half, a, pl, margin, pts, gaps, nrm);
+                if constexpr (X) {
+                    double3 pts[4], nrm;
+                    double gaps[4];
+                    np_ += box_plane_pair(st, half, a, pl, margin, pts, gaps, nrm);
+                }
             }
         }
         contact_count[a] = nct + np_;
     }
 }
 
+template <bool X>
 __global__ void k_write_contacts(const float4 *__restrict__ st, const float *__restrict__ im, int n,
                                  const int *__restrict__ sob, const float4 *__restrict__ planes,
                                  const int *__restrict__ plane_ptr, const int *__restrict__ plane_list,
@@ -222,12 +228,15 @@ __global__ void k_write_contacts(const float4 *__restrict__ st, const float *__r
         for (int j = 0; j < cnt; ++j) {
             const int b = nb_list[nb_off[a] + j];
             const float4 pb = st[4 * b];
-            if (is_box(half, a) || is_box(half, b)) {
-                double3 pts[4], nrm;
-                double gaps[4];
-                const int m = box_pair(st, half, nullptr, a, b, margin, pts, gaps, nrm);
-                for (int k = 0; k < m; ++k) write_box_contact(o++, a, b, k, pts[k], gaps[k], nrm, c_ab, c_n, c_t1, c_p);
-                continue;
+            if constexpr (X) {
+                if (is_box(half, a) || is_box(half, b)) {
+                    double3 pts[4], nrm;
+                    double gaps[4];
+                    const int m = box_pair(st, half, nullptr, a, b, margin, pts, gaps, nrm);
+                    for (int k = 0; k < m; ++k)
+                        write_box_contact(o++, a, b, k, pts[k], gaps[k], nrm, c_ab, c_n, c_t1, c_p);
+                    continue;
+                }
             }
             float dx = __fsub_rn(pb.x, pa.x), dy = __fsub_rn(pb.y, pa.y), dz = __fsub_rn(pb.z, pa.z);
             float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
@@ -258,18 +267,20 @@ __global__ void k_write_contacts(const float4 *__restrict__ st, const float *__r
         }
         if (im[a] > 0.0f) {
             const int s = sob[a];
-            const bool box_a = is_box(half, a);
+            const bool box_a = X && is_box(half, a);
             for (int k2 = plane_ptr[s]; k2 < plane_ptr[s + 1]; ++k2) {
                 const int pidx = plane_list[k2];
                 const float4 pl = planes[pidx];
                 if (plane_gap(pa, pl) > margin) continue;   // the FP32 (bounding-sphere) decision
-                if (box_a) {
-                    double3 pts[4], nrm;
-                    double gaps[4];
-                    const int m = box_plane_pair(st, half, a, pl, margin, pts, gaps, nrm);
-                    for (int k = 0; k < m; ++k)
-                        write_box_contact(o++, a, n + pidx, k, pts[k], gaps[k], nrm, c_ab, c_n, c_t1, c_p);
-                    continue;
+                if constexpr (X) {
+                    if (box_a) {
+                        double3 pts[4], nrm;
+                        double gaps[4];
+                        const int m = box_plane_pair(st, half, a, pl, margin, pts, gaps, nrm);
+                        for (int k = 0; k < m; ++k)
+                            write_box_contact(o++, a, n + pidx, k, pts[k], gaps[k], nrm, c_ab, c_n, c_t1, c_p);
+                        continue;
+                    }
                 }
                 // the gap itself from large coordinates: FP64, then rounded once
                 const float gap = (float)((double)pl.x * pa.x + (double)pl.y * pa.y +
@@ -391,7 +402,8 @@ void launch_bucket_fill(const ContactArgs &a, cudaStream_t s) {
 }
 
 void launch_find_pairs(const ContactArgs &a, cudaStream_t s) {
-    k_find_pairs<<<grid1d(a.n, 128), 128, 0, s>>>(
+    auto k = a.half ? k_find_pairs<true> : k_find_pairs<false>;
+    k<<<grid1d(a.n, 128), 128, 0, s>>>(
         a.st, a.im, a.n, a.sob, a.scene_flags, a.cell, a.bucket_start, a.items, a.tmask, a.planes,
         a.plane_ptr, a.plane_list, a.margin, a.nb_list, a.nb_off, a.nb_count, a.contact_count, a.status, a.half);
     note_launch();
@@ -399,7 +411,8 @@ void launch_find_pairs(const ContactArgs &a, cudaStream_t s) {
 }
 
 void launch_write_contacts(const ContactArgs &a, cudaStream_t s) {
-    k_write_contacts<<<grid1d(a.n, 128), 128, 0, s>>>(a.st, a.im, a.n, a.sob, a.planes, a.plane_ptr,
+    auto k = a.half ? k_write_contacts<true> : k_write_contacts<false>;
+    k<<<grid1d(a.n, 128), 128, 0, s>>>(a.st, a.im, a.n, a.sob, a.planes, a.plane_ptr,
                                                       a.plane_list, a.margin, a.nb_list, a.nb_off,
                                                       a.nb_count, a.contact_start, a.c_ab, a.c_n,
                                                       a.c_t1, a.half, a.c_p);
