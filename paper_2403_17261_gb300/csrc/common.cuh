@@ -128,9 +128,13 @@ struct BallWorkspace {
 void host_assign_overlap(const HostScene &sc, std::vector<uint64_t> &mask);
 // contacts ab: pairs of dynamic bodies in canonical order; graph CSR of G^t;
 // mask [n] updated in place; loads [n_parts]: |P_w| of every worker for
-// these masks; scenes spread over up to `threads` threads (ws.size())
+// these masks; scenes spread over up to `threads` threads (ws.size()).
+// ball_start [n+1] / ball_vtx (both NULL, or both set): the gamma-ball of
+// body v found beforehand at ball_vtx[ball_start[v] .. ball_start[v+1]);
+// an empty range means the pass searches that ball itself.
 void host_load_balance(const HostScene &sc, uint64_t *mask, const int *loads, const int *deg, int64_t nc,
                        const int2 *ab, const int *row_ptr, const int *col, bool do_activate,
-                       bool do_deactivate, std::vector<BallWorkspace> &ws);
+                       bool do_deactivate, std::vector<BallWorkspace> &ws, const int *ball_start = nullptr,
+                       const int *ball_vtx = nullptr);
 
 }  // namespace ovl

@@ -166,10 +166,37 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
     launch_worker_loads(c->mask.p, c->sob.p, c->part_base.p, by_contacts ? c->lb_deg.p : nullptr, n,
                         c->n_parts, c->lb_loads.p, s);
     CK(cudaMemcpyAsync(c->h_loads.p, c->lb_loads.p, sizeof(int) * c->n_parts, cudaMemcpyDeviceToHost, s));
+    // the gamma-balls of the ends of the disjoint candidates, found on the
+    // device (the pass activates those of its roots).  Not on removal steps:
+    // there the activations come mostly from contacts that become disjoint
+    // during the pass, and the host searches those (measured: no gain).
+    const int *hb_start = nullptr, *hb_vtx = nullptr;
+    if (act && !deact) {
+        c->ball_root.ensure((size_t)n + 1);
+        c->ball_size.ensure((size_t)n + 1);
+        c->ball_start.ensure((size_t)n + 1);
+        CK(cudaMemsetAsync(c->ball_root.p, 0, sizeof(int) * n, s));
+        launch_ball_roots(c->lb_pairs.p, m, c->mask.p, c->ball_root.p, s);
+        launch_balls(false, n, c->ball_root.p, c->row_ptr.p, c->col.p, c->sob.p, c->scene_gamma.p,
+                     c->ball_size.p, nullptr, nullptr, s);
+        scan_i32(c->ball_size.p, c->ball_start.p, n, c->scan_tmp, s);
+        const int total = read_i32(c, c->ball_start.p + n);
+        c->ball_vtx.ensure((size_t)total + 1);
+        launch_balls(true, n, c->ball_root.p, c->row_ptr.p, c->col.p, c->sob.p, c->scene_gamma.p,
+                     c->ball_size.p, c->ball_start.p, c->ball_vtx.p, s);
+        c->h_ball_start.ensure((size_t)n + 1);
+        c->h_ball_vtx.ensure((size_t)total + 1);
+        CK(cudaMemcpyAsync(c->h_ball_start.p, c->ball_start.p, sizeof(int) * ((size_t)n + 1),
+                           cudaMemcpyDeviceToHost, s));
+        if (total) CK(cudaMemcpyAsync(c->h_ball_vtx.p, c->ball_vtx.p, sizeof(int) * (size_t)total,
+                                      cudaMemcpyDeviceToHost, s));
+        hb_start = c->h_ball_start.p;
+        hb_vtx = c->h_ball_vtx.p;
+    }
     CK(cudaStreamSynchronize(s));
     if ((int)c->lb_ws.size() != c->lb_threads) c->lb_ws.resize(c->lb_threads);
     host_load_balance(c->hs, c->h_mask.p, c->h_loads.p, by_contacts ? c->h_deg.p : nullptr, m, c->h_ab.p,
-                      c->h_rp.p, c->h_col.p, act, deact, c->lb_ws);
+                      c->h_rp.p, c->h_col.p, act, deact, c->lb_ws, hb_start, hb_vtx);
     CK(cudaMemcpyAsync(c->mask.p, c->h_mask.p, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     c->lb_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -989,7 +1016,7 @@ namespace {
 void release_all(ovl_ctx *c) {
     c->st.release(); c->st_alt.release(); c->radius.release(); c->im.release();
     c->scene_mu.release(); c->scene_dt.release(); c->sob.release(); c->scene_flags.release();
-    c->n_sets.release(); c->part_base.release(); c->body_base.release(); c->scene_beta.release();
+    c->n_sets.release(); c->part_base.release(); c->body_base.release(); c->scene_beta.release(); c->scene_gamma.release();
     c->joint_scene.release(); c->part_scene.release(); c->planes.release(); c->plane_ptr.release();
     c->plane_list.release(); c->jab.release(); c->janc.release(); c->vb_base.release();
     c->mask.release(); c->cell.release(); c->bucket_count.release(); c->bucket_start.release();
@@ -1010,6 +1037,7 @@ void release_all(ovl_ctx *c) {
     c->qctl.release(); c->D.release(); c->weight.release(); c->stage13.release(); c->scan_tmp.release();
     c->sort_hist.release(); c->sort_tmp.release();
     c->lb_flag.release(); c->lb_pos.release(); c->lb_pairs.release();
+    c->ball_root.release(); c->ball_size.release(); c->ball_start.release(); c->ball_vtx.release();
     c->worker_order.release(); c->wk.release(); c->wk2.release(); c->wv2.release();
     c->class_order.release(); c->colour_order.release(); c->solve_C.release(); c->col_off2.release();
     c->row_owner.release();
@@ -1049,6 +1077,7 @@ ovl_status ovl_destroy(ovl_ctx *c) {
     release_all(c);
     release_mlp(c);
     c->h_loads.release();
+    c->h_ball_start.release(); c->h_ball_vtx.release();
     c->h_i32.release(); c->h_ab.release(); c->h_rp.release(); c->h_col.release(); c->h_mask.release();
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -1199,6 +1228,7 @@ ovl_status ovl_scene_upload(ovl_ctx *c, const ovl_scene_desc *d) {
         upload(c->scene_dt, d->scene_dt, ns, s);
         upload(c->scene_flags, d->scene_flags, ns, s);
         upload(c->scene_beta, d->scene_beta, ns, s);
+        upload(c->scene_gamma, d->scene_gamma, ns, s);
         upload(c->n_sets, d->n_sets, ns, s);
         upload(c->part_base, part_base.data(), ns + 1, s);
         upload(c->body_base, c->h_body_base.data(), ns + 1, s);

@@ -44,7 +44,7 @@ struct ovl_ctx {
     // scene (device)
     DBuf<float4> st, st_alt;
     DBuf<float> radius, im, scene_mu, scene_dt;
-    DBuf<int> sob, scene_flags, n_sets, part_base, body_base, scene_beta, joint_scene, part_scene;
+    DBuf<int> sob, scene_flags, n_sets, part_base, body_base, scene_beta, scene_gamma, joint_scene, part_scene;
     DBuf<float4> planes;
     DBuf<int> plane_ptr, plane_list;
     DBuf<int2> jab;
@@ -94,6 +94,8 @@ struct ovl_ctx {
     HBuf<int> h_rp, h_col;
     HBuf<uint64_t> h_mask;
     DBuf<int> lb_flag, lb_pos;
+    DBuf<int> ball_root, ball_size, ball_start, ball_vtx;   // Algorithm 6's gamma-balls, found ahead
+    HBuf<int> h_ball_start, h_ball_vtx;
     DBuf<int2> lb_pairs;
     DBuf<uint32_t> worker_order, wk, wk2, wv2;   // workers longest first (launch order)
     DBuf<uint32_t> class_order, colour_order;    // solve / colouring: workers grouped by CTAs per worker

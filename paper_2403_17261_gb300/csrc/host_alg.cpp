@@ -181,7 +181,7 @@ namespace {
 // Algorithm 6 over candidates [i0, i1), all of scenes [s0, s1)
 void load_balance_range(const HostScene &sc, Membership &mem, const int2 *ab, int64_t i0, int64_t i1,
                         int s0, int s1, const int *row_ptr, const int *col, bool do_activate,
-                        bool do_deactivate, BallWorkspace &bw) {
+                        bool do_deactivate, BallWorkspace &bw, const int *ball_start, const int *ball_vtx) {
     if (i0 == i1) return;
     int widest = 0;
     for (int s = s0; s < s1; ++s) widest = std::max(widest, sc.body_base[s + 1] - sc.body_base[s]);
@@ -220,6 +220,14 @@ void load_balance_range(const HostScene &sc, Membership &mem, const int2 *ab, in
                 mem.activate(WB, A);
                 root = A;
             }
+            if (ball_start && ball_start[root + 1] > ball_start[root]) {
+                // the gamma-ball found beforehand (the same vertex set)
+                for (int k = ball_start[root]; k < ball_start[root + 1]; ++k) {
+                    const int v = ball_vtx[k];
+                    mem.activate((WA | WB) & ~mem.W(v), v);
+                }
+                continue;
+            }
             if (scene != ball_scene) { ball.rebase(sc.body_base[scene]); ball_scene = scene; }
             const std::vector<int> &N =
                 ball.collect(row_ptr, col, root, sc.scene_gamma[scene]);   // gamma-ball
@@ -248,7 +256,8 @@ void load_balance_range(const HostScene &sc, Membership &mem, const int2 *ab, in
 // `threads` host threads; the result is the sequential one.
 void host_load_balance(const HostScene &sc, uint64_t *mask, const int *loads, const int *deg, int64_t nc,
                        const int2 *ab, const int *row_ptr, const int *col, bool do_activate,
-                       bool do_deactivate, std::vector<BallWorkspace> &ws) {
+                       bool do_deactivate, std::vector<BallWorkspace> &ws, const int *ball_start,
+                       const int *ball_vtx) {
     if (nc == 0 || (!do_activate && !do_deactivate) || ws.empty()) return;
     const int threads = (int)ws.size();
     Membership mem(sc, mask, loads, deg);
@@ -269,7 +278,7 @@ void host_load_balance(const HostScene &sc, uint64_t *mask, const int *loads, co
     auto run = [&](size_t k) {
         const int s0 = cut[k], s1 = cut[k + 1];
         load_balance_range(sc, mem, ab, first[s0], first[s1], s0, s1, row_ptr, col, do_activate,
-                           do_deactivate, ws[k]);
+                           do_deactivate, ws[k], ball_start, ball_vtx);
     };
     if (cut.size() == 2) {
         run(0);

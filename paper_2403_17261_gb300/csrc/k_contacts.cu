@@ -20,6 +20,8 @@
 // built without contraction) then gives 0-4 contacts: the manifold, in
 // (a, b, k) order, each with its point.  Counting and writing run the same
 // functions on the same inputs, so they agree.
+#include <algorithm>
+
 #include "box_geom.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
@@ -379,6 +381,103 @@ __global__ void k_lb_compact(const int2 *__restrict__ c_ab, int nc, const int *_
         if (flag[i]) out[pos[i]] = c_ab[i];
 }
 
+// ---- gamma-balls for the load balance --------------------------------------
+// The vertex set within gamma hops of a root in G^t (Algorithm 6, line 12)
+// depends on the graph only, which Algorithm 6 does not change, so it is
+// found for every possible root before the sequential pass: one warp per
+// body that is an end of a candidate contact, breadth first, level by
+// level, with the vertices seen in a shared-memory hash set.  The set is the
+// same whatever the discovery order; the pass applies it in any order (each
+// vertex's activation and load update are independent).  A ball larger than
+// BALL_CAP vertices is left empty (size 0), and the pass searches it itself.
+constexpr int BALL_WARPS = 4, BALL_CAP = 512, BALL_HASH = 1024;
+
+// 1 if u was not in the set (and is now), 0 if it was, -1 if the set is full
+__device__ __forceinline__ int ball_insert(int *hs, int u) {
+    uint32_t h = ((uint32_t)u * 2654435761u) & (BALL_HASH - 1);
+    for (int probe = 0; probe < BALL_HASH; ++probe) {
+        const int old = atomicCAS(hs + h, -1, u);
+        if (old == -1) return 1;
+        if (old == u) return 0;
+        h = (h + 1) & (BALL_HASH - 1);
+    }
+    return -1;
+}
+
+// the ends of the candidates whose masks are disjoint now (the activation
+// branch); those that become disjoint during the pass are rare enough for
+// the host to search
+__global__ void k_ball_roots(const int2 *__restrict__ ab, int m, const uint64_t *__restrict__ mask,
+                             int *__restrict__ root) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int2 e = ab[i];
+        if (mask[e.x] & mask[e.y]) continue;
+        root[e.x] = 1;
+        root[e.y] = 1;
+    }
+}
+
+// FILL = false: size[v] = |ball(v)| (0: not a root, or larger than BALL_CAP);
+// FILL = true: the ball of every root v with size[v] > 0 at vtx[start[v]...]
+template <bool FILL>
+__global__ void __launch_bounds__(BALL_WARPS * 32)
+k_balls(int n, const int *__restrict__ root, const int *__restrict__ row_ptr, const int *__restrict__ col,
+        const int *__restrict__ sob, const int *__restrict__ scene_gamma, int *__restrict__ size,
+        const int *__restrict__ start, int *__restrict__ vtx) {
+    __shared__ int hs[BALL_WARPS][BALL_HASH];
+    __shared__ int lst[BALL_WARPS][BALL_CAP];
+    __shared__ int len[BALL_WARPS];
+    __shared__ int full[BALL_WARPS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *const H = hs[w], *const L = lst[w];
+    for (int v = blockIdx.x * BALL_WARPS + w; v < n; v += gridDim.x * BALL_WARPS) {
+        if (!root[v] || (FILL && size[v] == 0)) {
+            if (!FILL && lane == 0) size[v] = 0;
+            continue;
+        }
+        for (int k = lane; k < BALL_HASH; k += 32) H[k] = -1;
+        __syncwarp();
+        if (lane == 0) {
+            ball_insert(H, v);
+            L[0] = v;
+            len[w] = 1;
+            full[w] = 0;
+        }
+        __syncwarp();
+        const int gamma = scene_gamma[sob[v]];
+        int lo = 0, hi = 1;
+        for (int d = 0; d < gamma && lo < hi; ++d) {
+            for (int i = lo; i < hi; ++i) {
+                const int x = L[i];
+                for (int k = row_ptr[x] + lane; k < row_ptr[x + 1]; k += 32) {
+                    const int u = col[k];
+                    const int r = ball_insert(H, u);
+                    if (r > 0) {
+                        const int pos = atomicAdd(&len[w], 1);
+                        if (pos < BALL_CAP) L[pos] = u;
+                        else full[w] = 1;
+                    } else if (r < 0) {
+                        full[w] = 1;
+                    }
+                }
+            }
+            __syncwarp();
+            lo = hi;
+            hi = min(len[w], BALL_CAP);
+            __syncwarp();
+            if (full[w]) break;
+        }
+        const int total = full[w] ? 0 : len[w];
+        if (!FILL) {
+            if (lane == 0) size[v] = total;
+        } else {
+            const int s0 = start[v];
+            for (int k = lane; k < total; k += 32) vtx[s0 + k] = L[k];
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace
 
 int grid1d(size_t n, int threads) {
@@ -521,6 +620,23 @@ void launch_lb_compact(const int2 *c_ab, int nc, const int *flag, const int *pos
                        cudaStream_t s) {
     if (!nc) return;
     k_lb_compact<<<grid1d(nc, 256), 256, 0, s>>>(c_ab, nc, flag, pos, out);
+    note_launch();
+    CK(cudaGetLastError());
+}
+void launch_ball_roots(const int2 *ab, int m, const uint64_t *mask, int *root, cudaStream_t s) {
+    if (!m) return;
+    k_ball_roots<<<grid1d(m, 256), 256, 0, s>>>(ab, m, mask, root);
+    note_launch();
+    CK(cudaGetLastError());
+}
+void launch_balls(bool fill, int n, const int *root, const int *row_ptr, const int *col, const int *sob,
+                  const int *scene_gamma, int *size, const int *start, int *vtx, cudaStream_t s) {
+    if (!n) return;
+    const int blocks = (int)std::min<size_t>(((size_t)n + BALL_WARPS - 1) / BALL_WARPS, 152 * 16);
+    if (fill)
+        k_balls<true><<<blocks, BALL_WARPS * 32, 0, s>>>(n, root, row_ptr, col, sob, scene_gamma, size, start, vtx);
+    else
+        k_balls<false><<<blocks, BALL_WARPS * 32, 0, s>>>(n, root, row_ptr, col, sob, scene_gamma, size, start, vtx);
     note_launch();
     CK(cudaGetLastError());
 }
