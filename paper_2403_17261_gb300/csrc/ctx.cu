@@ -479,13 +479,33 @@ bool plan_solve_classes(ovl_ctx *c, const SolveShape &shape, std::vector<SolveCl
     return true;
 }
 
-// launches on the context's stream and its side streams, then joins them
+// The order in which a plan's classes are launched.  When all CTAs fit the
+// SMs at once, classes of even cluster sizes go first, then odd ones, single
+// CTAs last: clusters are placed in pairs of SMs more easily before odd
+// clusters and single CTAs split the pairs (measured on the large pile: a
+// plan of 32 three-CTA, 16 two-CTA and 16 one-CTA workers took 4.2 ms
+// launched largest first and 2.5 ms this way).  A plan with more CTAs than
+// SMs keeps the largest clusters first (the way measured faster there).
+std::vector<size_t> class_launch_order(ovl_ctx *c, const std::vector<SolveClass> &classes) {
+    std::vector<size_t> ord(classes.size());
+    std::iota(ord.begin(), ord.end(), 0);
+    long long ctas = 0;
+    for (const SolveClass &k : classes) ctas += (long long)k.C * k.count;
+    if (ctas > c->num_sms) return ord;
+    auto key = [&](size_t k) { const int C = classes[k].C; return C == 1 ? 0 : (C % 2 == 0 ? 2 * 16 + C : 16 + C); };
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return key(x) > key(y); });
+    return ord;
+}
+
+// launches class ord[j] (all classes when ord is empty) on the context's
+// stream (j = 0) or a side stream, then joins them
 template <class F>
-void run_on_streams(ovl_ctx *c, size_t n, F &&launch) {
+void run_on_streams(ovl_ctx *c, size_t n, F &&launch, const std::vector<size_t> &ord = {}) {
     CK(cudaEventRecord(c->fork, c->stream));
-    for (size_t k = 0; k < n; ++k) {
-        cudaStream_t sk = k == 0 ? c->stream : c->aux[k - 1];
-        if (k) CK(cudaStreamWaitEvent(sk, c->fork, 0));
+    for (size_t j = 0; j < n; ++j) {
+        const size_t k = ord.empty() ? j : ord[j];
+        cudaStream_t sk = j == 0 ? c->stream : c->aux[j - 1];
+        if (j) CK(cudaStreamWaitEvent(sk, c->fork, 0));
         launch(k, sk);
     }
     for (size_t k = 1; k < n; ++k) {
@@ -503,7 +523,7 @@ void launch_solve_classes(ovl_ctx *c, const SolveArgs &a, const SolveShape &shap
         b.smem_slots = classes[k].slots;
         launch_solve(b, shape.threads, classes[k].C, shape.unroll,
                      solve_masses_fit(c, classes[k].slots, shape.per_sm), sk);
-    });
+    }, class_launch_order(c, classes));
 }
 
 void phase_colour(ovl_ctx *c) {
