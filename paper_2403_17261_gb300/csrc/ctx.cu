@@ -172,17 +172,21 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
     // during the pass, and the host searches those (measured: no gain).
     const int *hb_start = nullptr, *hb_vtx = nullptr;
     if (act && !deact) {
+        const int max_roots = (int)std::min<long long>(2LL * m, n);
         c->ball_root.ensure((size_t)n + 1);
         c->ball_size.ensure((size_t)n + 1);
         c->ball_start.ensure((size_t)n + 1);
-        CK(cudaMemsetAsync(c->ball_root.p, 0, sizeof(int) * n, s));
-        launch_ball_roots(c->lb_pairs.p, m, c->mask.p, c->ball_root.p, s);
-        launch_balls(false, n, c->ball_root.p, c->row_ptr.p, c->col.p, c->sob.p, c->scene_gamma.p,
+        c->ball_list.ensure((size_t)max_roots + 1);
+        CK(cudaMemsetAsync(c->ball_root.p, 0, sizeof(int) * ((size_t)n + 1), s));   // [n]: the root count
+        CK(cudaMemsetAsync(c->ball_size.p, 0, sizeof(int) * n, s));
+        int *const nroot = c->ball_root.p + n;
+        launch_ball_roots(c->lb_pairs.p, m, c->mask.p, c->ball_root.p, c->ball_list.p, nroot, s);
+        launch_balls(false, max_roots, c->ball_list.p, nroot, c->row_ptr.p, c->col.p, c->sob.p, c->scene_gamma.p,
                      c->ball_size.p, nullptr, nullptr, s);
         scan_i32(c->ball_size.p, c->ball_start.p, n, c->scan_tmp, s);
         const int total = read_i32(c, c->ball_start.p + n);
         c->ball_vtx.ensure((size_t)total + 1);
-        launch_balls(true, n, c->ball_root.p, c->row_ptr.p, c->col.p, c->sob.p, c->scene_gamma.p,
+        launch_balls(true, max_roots, c->ball_list.p, nroot, c->row_ptr.p, c->col.p, c->sob.p, c->scene_gamma.p,
                      c->ball_size.p, c->ball_start.p, c->ball_vtx.p, s);
         c->h_ball_start.ensure((size_t)n + 1);
         c->h_ball_vtx.ensure((size_t)total + 1);
@@ -1058,6 +1062,7 @@ void release_all(ovl_ctx *c) {
     c->sort_hist.release(); c->sort_tmp.release();
     c->lb_flag.release(); c->lb_pos.release(); c->lb_pairs.release();
     c->ball_root.release(); c->ball_size.release(); c->ball_start.release(); c->ball_vtx.release();
+    c->ball_list.release();
     c->worker_order.release(); c->wk.release(); c->wk2.release(); c->wv2.release();
     c->class_order.release(); c->colour_order.release(); c->solve_C.release(); c->col_off2.release();
     c->row_owner.release();

@@ -94,7 +94,7 @@ struct ovl_ctx {
     HBuf<int> h_rp, h_col;
     HBuf<uint64_t> h_mask;
     DBuf<int> lb_flag, lb_pos;
-    DBuf<int> ball_root, ball_size, ball_start, ball_vtx;   // Algorithm 6's gamma-balls, found ahead
+    DBuf<int> ball_root, ball_size, ball_start, ball_vtx, ball_list;   // Algorithm 6's gamma-balls, found ahead
     HBuf<int> h_ball_start, h_ball_vtx;
     DBuf<int2> lb_pairs;
     DBuf<uint32_t> worker_order, wk, wk2, wv2;   // workers longest first (launch order)

@@ -198,7 +198,14 @@ void load_balance_range(const HostScene &sc, Membership &mem, const int2 *ab, in
         return false;
     };
     constexpr int64_t kAhead = 16;   // candidates between a prefetch and its use
+    constexpr int64_t kBallAhead = 4;   // the same for the masks of balls found beforehand
     for (int64_t i = i0; i < i1; ++i) {
+        if (ball_start && i + kBallAhead < i1) {
+            // either end may become the root: fetch the masks of both balls
+            const int2 e = ab[i + kBallAhead];
+            for (int k = ball_start[e.x]; k < ball_start[e.x + 1]; ++k) __builtin_prefetch(mem.mask_ptr() + ball_vtx[k]);
+            for (int k = ball_start[e.y]; k < ball_start[e.y + 1]; ++k) __builtin_prefetch(mem.mask_ptr() + ball_vtx[k]);
+        }
         if (i + kAhead < i1) {
             // the second body of a contact is a random index: fetch its mask
             // and adjacency range while earlier candidates are processed

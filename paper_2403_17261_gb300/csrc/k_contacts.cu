@@ -407,34 +407,35 @@ __device__ __forceinline__ int ball_insert(int *hs, int u) {
 // the ends of the candidates whose masks are disjoint now (the activation
 // branch); those that become disjoint during the pass are rare enough for
 // the host to search
+// root[v] = 1 marks v once; list[0..*count) the roots (in any order)
 __global__ void k_ball_roots(const int2 *__restrict__ ab, int m, const uint64_t *__restrict__ mask,
-                             int *__restrict__ root) {
+                             int *__restrict__ root, int *__restrict__ list, int *__restrict__ count) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         const int2 e = ab[i];
         if (mask[e.x] & mask[e.y]) continue;
-        root[e.x] = 1;
-        root[e.y] = 1;
+        if (atomicExch(root + e.x, 1) == 0) list[atomicAdd(count, 1)] = e.x;
+        if (atomicExch(root + e.y, 1) == 0) list[atomicAdd(count, 1)] = e.y;
     }
 }
 
-// FILL = false: size[v] = |ball(v)| (0: not a root, or larger than BALL_CAP);
-// FILL = true: the ball of every root v with size[v] > 0 at vtx[start[v]...]
+// Over the roots list[0..*count): FILL = false: size[v] = |ball(v)| (0 when
+// larger than BALL_CAP; size is zero elsewhere); FILL = true: the ball of
+// every root v with size[v] > 0 at vtx[start[v]...]
 template <bool FILL>
 __global__ void __launch_bounds__(BALL_WARPS * 32)
-k_balls(int n, const int *__restrict__ root, const int *__restrict__ row_ptr, const int *__restrict__ col,
-        const int *__restrict__ sob, const int *__restrict__ scene_gamma, int *__restrict__ size,
-        const int *__restrict__ start, int *__restrict__ vtx) {
+k_balls(const int *__restrict__ list, const int *__restrict__ count, const int *__restrict__ row_ptr,
+        const int *__restrict__ col, const int *__restrict__ sob, const int *__restrict__ scene_gamma,
+        int *__restrict__ size, const int *__restrict__ start, int *__restrict__ vtx) {
     __shared__ int hs[BALL_WARPS][BALL_HASH];
     __shared__ int lst[BALL_WARPS][BALL_CAP];
     __shared__ int len[BALL_WARPS];
     __shared__ int full[BALL_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *const H = hs[w], *const L = lst[w];
-    for (int v = blockIdx.x * BALL_WARPS + w; v < n; v += gridDim.x * BALL_WARPS) {
-        if (!root[v] || (FILL && size[v] == 0)) {
-            if (!FILL && lane == 0) size[v] = 0;
-            continue;
-        }
+    const int nr = *count;
+    for (int j = blockIdx.x * BALL_WARPS + w; j < nr; j += gridDim.x * BALL_WARPS) {
+        const int v = list[j];
+        if (FILL && size[v] == 0) continue;
         for (int k = lane; k < BALL_HASH; k += 32) H[k] = -1;
         __syncwarp();
         if (lane == 0) {
@@ -623,20 +624,21 @@ void launch_lb_compact(const int2 *c_ab, int nc, const int *flag, const int *pos
     note_launch();
     CK(cudaGetLastError());
 }
-void launch_ball_roots(const int2 *ab, int m, const uint64_t *mask, int *root, cudaStream_t s) {
+void launch_ball_roots(const int2 *ab, int m, const uint64_t *mask, int *root, int *list, int *count,
+                       cudaStream_t s) {
     if (!m) return;
-    k_ball_roots<<<grid1d(m, 256), 256, 0, s>>>(ab, m, mask, root);
+    k_ball_roots<<<grid1d(m, 256), 256, 0, s>>>(ab, m, mask, root, list, count);
     note_launch();
     CK(cudaGetLastError());
 }
-void launch_balls(bool fill, int n, const int *root, const int *row_ptr, const int *col, const int *sob,
-                  const int *scene_gamma, int *size, const int *start, int *vtx, cudaStream_t s) {
-    if (!n) return;
-    const int blocks = (int)std::min<size_t>(((size_t)n + BALL_WARPS - 1) / BALL_WARPS, 152 * 16);
+void launch_balls(bool fill, int max_roots, const int *list, const int *count, const int *row_ptr, const int *col,
+                  const int *sob, const int *scene_gamma, int *size, const int *start, int *vtx, cudaStream_t s) {
+    if (max_roots <= 0) return;
+    const int blocks = (int)std::min<size_t>(((size_t)max_roots + BALL_WARPS - 1) / BALL_WARPS, 152 * 16);
     if (fill)
-        k_balls<true><<<blocks, BALL_WARPS * 32, 0, s>>>(n, root, row_ptr, col, sob, scene_gamma, size, start, vtx);
+        k_balls<true><<<blocks, BALL_WARPS * 32, 0, s>>>(list, count, row_ptr, col, sob, scene_gamma, size, start, vtx);
     else
-        k_balls<false><<<blocks, BALL_WARPS * 32, 0, s>>>(n, root, row_ptr, col, sob, scene_gamma, size, start, vtx);
+        k_balls<false><<<blocks, BALL_WARPS * 32, 0, s>>>(list, count, row_ptr, col, sob, scene_gamma, size, start, vtx);
     note_launch();
     CK(cudaGetLastError());
 }

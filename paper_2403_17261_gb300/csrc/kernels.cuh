@@ -56,14 +56,15 @@ void launch_lb_flags(const int2 *c_ab, int nc, const float *im, int n, const uin
                      int disjoint_only, int *flag, const float4 *c_p, cudaStream_t s);
 void launch_lb_compact(const int2 *c_ab, int nc, const int *flag, const int *pos, int2 *out,
                        cudaStream_t s);
-// Algorithm 6's gamma-balls, found ahead of the host pass: root[v] = 1 for the
-// ends of the m candidate contacts whose masks are disjoint (root zeroed by
-// the caller); size[v] the
-// ball's vertex count (0: not a root or too large); vtx at start[v] (the
-// exclusive scan of size) the vertices
-void launch_ball_roots(const int2 *ab, int m, const uint64_t *mask, int *root, cudaStream_t s);
-void launch_balls(bool fill, int n, const int *root, const int *row_ptr, const int *col, const int *sob,
-                  const int *scene_gamma, int *size, const int *start, int *vtx, cudaStream_t s);
+// Algorithm 6's gamma-balls, found ahead of the host pass: root[v] = 1 and v
+// in list[0..*count) for the ends of the m candidate contacts whose masks
+// are disjoint (root, count zeroed by the caller; list holds up to 2m);
+// size[v] the ball's vertex count (0: not a root or too large; zeroed by the
+// caller); vtx at start[v] (the exclusive scan of size) the vertices
+void launch_ball_roots(const int2 *ab, int m, const uint64_t *mask, int *root, int *list, int *count,
+                       cudaStream_t s);
+void launch_balls(bool fill, int max_roots, const int *list, const int *count, const int *row_ptr, const int *col,
+                  const int *sob, const int *scene_gamma, int *size, const int *start, int *vtx, cudaStream_t s);
 void launch_adj_compact(const int *tptr, const int *tcol, int n, const int *row_ptr, int *col,
                         cudaStream_t s);
 
