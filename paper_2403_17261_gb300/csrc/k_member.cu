@@ -104,18 +104,24 @@ __device__ __forceinline__ int body_slot(const MemberArgs &a, int x, int w) {
 }
 
 // One block per (worker, colour); warp w takes the w-th contiguous chunk of
-// the colour's rows.  The warps count their rows per (kind, owner rank), the
-// buckets are laid out rank by rank (contacts, then joints) with the warps'
-// shares in warp order, and every warp scatters its chunk -- rows keep their
-// order inside a bucket.
+// the colour's rows.  A row's owner is the CTA that holds its first dynamic
+// body.  The warps count their rows per (owner rank, kind); the buckets are
+// then sized evenly: every CTA of the group gets total / C rows of each kind
+// (the first total % C one more), since a colour step lasts as long as its
+// fullest CTA.  A CTA keeps its own rows up to its share, in order; the rows
+// beyond it go, in order, to the CTAs below their share (after those CTAs'
+// own rows), which reach their bodies in the owner's shared memory.  Buckets
+// are laid out rank by rank (contacts, then joints).  Rows of one colour are
+// independent, so any assignment gives the same result.
 constexpr int OWNER_THREADS = 256, OWNER_WARPS = OWNER_THREADS / 32;
 
 __global__ void __launch_bounds__(OWNER_THREADS)
 k_row_owner(int P, const int *part_bstart, const int *part_ncol, const int *solve_C,
             const int *off_in, const int *pair_of_row, const int2 *p_slot, uint8_t *owner_of_row,
             int *pair_of_row_out, int *off_out) {
-    __shared__ int cnt[OWNER_WARPS][2 * OWNER_RANKS];
-    __shared__ int base[OWNER_WARPS][2 * OWNER_RANKS];
+    constexpr int NK = 2 * OWNER_RANKS;
+    __shared__ int cnt[OWNER_WARPS][NK];    // a warp's rows per (owner, kind), then its first index in the group
+    __shared__ int total[NK], share[NK], start[NK], exc0[NK], def0[NK];
     const int p = blockIdx.x, c = blockIdx.y;
     if (p >= P) return;
     const int ncol = part_ncol[p];
@@ -124,7 +130,7 @@ k_row_owner(int P, const int *part_bstart, const int *part_ncol, const int *solv
     const int end = off[2 * ncol];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (c >= ncol) {
-        if (tid < 2 * OWNER_RANKS) o2[c * OWNER_RANKS * 2 + tid] = end;
+        if (tid < NK) o2[c * NK + tid] = end;
         if (c == OVL_MAX_COLOURS - 1 && tid == 0) o2[OWNER_NB - 1] = end;
         return;
     }
@@ -134,7 +140,7 @@ k_row_owner(int P, const int *part_bstart, const int *part_ncol, const int *solv
     const int s0 = off[2 * c], s1 = off[2 * c + 1], s2 = off[2 * c + 2];
     const int chunk = (s2 - s0 + OWNER_WARPS - 1) / OWNER_WARPS;
     const int w0 = min(s2, s0 + warp * chunk), w1 = min(s2, w0 + chunk);
-    if (lane < 2 * OWNER_RANKS) cnt[warp][lane] = 0;
+    if (lane < NK) cnt[warp][lane] = 0;
     __syncwarp();
     const unsigned full = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
@@ -154,13 +160,33 @@ k_row_owner(int P, const int *part_bstart, const int *part_ncol, const int *solv
     }
     __syncthreads();
     if (tid == 0) {
-        int pos = s0;
-        for (int k = 0; k < 2 * OWNER_RANKS; ++k) {
-            o2[c * OWNER_RANKS * 2 + k] = pos;
-            for (int w = 0; w < OWNER_WARPS; ++w) {
-                base[w][k] = pos;
-                pos += cnt[w][k];
+        for (int k = 0; k < NK; ++k) {
+            int t = 0;
+            for (int w = 0; w < OWNER_WARPS; ++w) {   // counts -> each warp's first index in its group
+                const int x = cnt[w][k];
+                cnt[w][k] = t;
+                t += x;
             }
+            total[k] = t;
+        }
+        for (int kind = 0; kind < 2; ++kind) {
+            int all = 0;
+            for (int r = 0; r < OWNER_RANKS; ++r) all += total[2 * r + kind];
+            int e = 0, d = 0;
+            for (int r = 0; r < OWNER_RANKS; ++r) {
+                const int k = 2 * r + kind;
+                share[k] = r < C ? all / C + (r < all % C ? 1 : 0) : 0;
+                exc0[k] = e;
+                def0[k] = d;
+                e += max(0, total[k] - share[k]);
+                d += max(0, share[k] - total[k]);
+            }
+        }
+        int pos = s0;
+        for (int k = 0; k < NK; ++k) {
+            start[k] = pos;
+            o2[c * NK + k] = pos;
+            pos += share[k];
         }
         if (c == OVL_MAX_COLOURS - 1) o2[OWNER_NB - 1] = end;
     }
@@ -169,9 +195,24 @@ k_row_owner(int P, const int *part_bstart, const int *part_ncol, const int *solv
         const int r = b + lane;
         const int key = r < w1 ? (int)owner_of_row[r] : -1;
         const unsigned peers = __match_any_sync(full, key);
-        if (key >= 0) pair_of_row_out[base[warp][key] + __popc(peers & lt)] = pair_of_row[r];
+        if (key >= 0) {
+            const int idx = cnt[warp][key] + __popc(peers & lt);   // index in its (owner, kind) group
+            int dst;
+            if (idx < share[key]) {
+                dst = start[key] + idx;
+            } else {
+                // the e-th row beyond its owner's share (over owners in rank
+                // order) fills the e-th free place of the same kind
+                const int kind = key & 1;
+                const int e = exc0[key] + (idx - share[key]);
+                int k = kind;
+                while (k + 2 < NK && def0[k + 2] <= e) k += 2;
+                dst = start[k] + total[k] + (e - def0[k]);
+            }
+            pair_of_row_out[dst] = pair_of_row[r];
+        }
         __syncwarp();
-        if (key >= 0 && (peers & lt) == 0) base[warp][key] += __popc(peers);
+        if (key >= 0 && (peers & lt) == 0) cnt[warp][key] += __popc(peers);
         __syncwarp();
     }
 }
