@@ -606,6 +606,7 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
 // Row records in colour order (the solver forms t1, t2, k_n, k_t and the
 // joint k's itself).  Contacts (sphere-sphere or sphere-plane):
 //   r0 = (n, slot_b)  r1 = (r_a, r_b, target_n, slot_a)  r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b)
+//   and the impulse record (lambda_n, lambda_t1, lambda_t2, k_n)
 // Ball joints (rows along the world axes):
 //   r0 = (r_A, target_x)  r1 = (r_B, target_y)  r2 = (target_z, 0, slot_a, slot_b)  r3 as for contacts
 // A slot word holds the bits of the solver's slot code of a worker slot s:
@@ -682,6 +683,7 @@ __global__ void k_rows(RowArgs a) {
         const int scene = a.part_scene[a.ps_part[k]];
         const float h = a.dt_override > 0.f ? a.dt_override : a.scene_dt[scene];
         const SlotWords sw = slot_words(a, a.ps_part[k], sl);
+        float lam_w = 0.f;   // a plain contact row: k_n (see below)
         if (a.row_full) {
             // a constraint with a box end: the full row, plus the slots in the
             // plain records (the solver reads its bodies through them)
@@ -762,6 +764,7 @@ __global__ void k_rows(RowArgs a) {
             a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, sw.b);
             a.r1[r] = make_float4(ra, rb, target, sw.a);
             a.r3[r] = make_float4(ima, imb, iia, iib);
+            lam_w = __frcp_rn(ima + imb);   // k_n, in the impulse record's spare lane
         } else {
             const int j = i - a.nc;
             const int2 ab = a.jab[j];
@@ -797,7 +800,8 @@ __global__ void k_rows(RowArgs a) {
             a.r3[r] = make_float4(ima, imb, iia, iib);
         }
         a.rpair[r] = k;
-        a.rlam[r] = a.p_lam0[k];
+        const float4 l0 = a.p_lam0[k];
+        a.rlam[r] = make_float4(l0.x, l0.y, l0.z, lam_w);
     }
 }
 

@@ -34,10 +34,11 @@
 // target, slot_a); joint r0 = (r_A, target_x), r1 = (r_B, target_y), r2 =
 // (target_z, 0, slot_a, slot_b); both r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b),
 // read only when the masses are not in shared memory.  Slots are slot codes
-// (below).  A contact forms t1 = normalise(e_k - (n .
-// e_k) n) (k the axis of the smallest |n_k|), k_n = 1 / (1/m_a + 1/m_b) and
-// the tangents' k_t = 1 / (1/m_a + 1/m_b + r_a^2 / I_a + r_b^2 / I_b) from
-// the bodies' masses, so both layouts compute the same bits.
+// (below).  A contact's impulse record is (lambda_n, lambda_t1, lambda_t2,
+// k_n), k_n = 1 / (1/m_a + 1/m_b) written by the row build.  The contact
+// forms t1 = normalise(e_k - (n . e_k) n) (k the axis of the smallest
+// |n_k|) and the tangents' k_t = 1 / (1/m_a + 1/m_b + r_a^2 / I_a + r_b^2 /
+// I_b) from the bodies' masses, so both layouts compute the same bits.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -263,13 +264,10 @@ __device__ __forceinline__ float contact_kt(const Body &A, const Body &B, float 
     return __frcp_rn(fmaf(B.ii, rb * rb, fmaf(A.ii, ra * ra, A.im + B.im)));
 }
 
-// t1 and k_n of a contact, formed from its normal and the bodies' masses
-template <class S>
-__device__ __forceinline__ void contact_frame(const Row &w, const Body &A, const Body &B, float3 &t1,
-                                              float &kn) {
+// t1 of a contact, formed from its normal
+__device__ __forceinline__ float3 contact_t1(const Row &w) {
     const float3 n = make_float3(w.x.x, w.x.y, w.x.z);
-    t1 = tangent_from(n, tangent_axis(n.x, n.y, n.z));
-    kn = __frcp_rn(A.im + B.im);
+    return tangent_from(n, tangent_axis(n.x, n.y, n.z));
 }
 
 template <class S>
@@ -372,10 +370,7 @@ __device__ __forceinline__ void solve_row(Body &A, Body &B, const Row &w, float 
     if (w.joint) {
         joint_rows(A, B, w.x, w.y, w.z, lam);
     } else {
-        float3 t1;
-        float kn;
-        contact_frame<S>(w, A, B, t1, kn);
-        contact_row(A, B, w.x, w.y, t1, kn, mu, lam);
+        contact_row(A, B, w.x, w.y, contact_t1(w), lam.w, mu, lam);
     }
 }
 
@@ -581,10 +576,7 @@ __device__ float rows_residual_sq(const SolveArgs &a, const S &st, const Buckets
                 } else if (w.joint) {
                     sq += joint_residual_sq(A, B, w.x, w.y, w.z);
                 } else {
-                    float3 t1;
-                    float kn;
-                    contact_frame<S>(w, A, B, t1, kn);
-                    sq += contact_residual_sq(A, B, w.x, w.y, t1, kn, mu, lam);
+                    sq += contact_residual_sq(A, B, w.x, w.y, contact_t1(w), lam.w, mu, lam);
                 }
             }
         }
@@ -646,9 +638,7 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
             if (is_full<X>(a, r)) {
                 full_warm(a, r, A, B, lam);
             } else if (!w.joint) {
-                float3 t1;
-                float kn;
-                contact_frame<S>(w, A, B, t1, kn);
+                const float3 t1 = contact_t1(w);
                 const float3 n = f3(w.x);
                 contact_impulse(A, B, n, t1, cross3(n, t1), w.y.x, w.y.y, lam.x, lam.y, lam.z);
             } else {
