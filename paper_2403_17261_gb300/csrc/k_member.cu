@@ -105,12 +105,14 @@ __device__ __forceinline__ int body_slot(const MemberArgs &a, int x, int w) {
 
 // One block per (worker, colour); warp w takes the w-th contiguous chunk of
 // the colour's rows.  A row's owner is the CTA that holds its first dynamic
-// body.  The warps count their rows per (owner rank, kind); the buckets are
-// then sized evenly: every CTA of the group gets total / C rows of each kind
-// (the first total % C one more), since a colour step lasts as long as its
-// fullest CTA.  A CTA keeps its own rows up to its share, in order; the rows
-// beyond it go, in order, to the CTAs below their share (after those CTAs'
-// own rows), which reach their bodies in the owner's shared memory.  Buckets
+// body.  The warps count their rows per (owner rank, kind); a colour step
+// lasts as long as its fullest CTA, so a CTA with more rows of a kind than
+// the even share (total / C) passes half of the excess on: it keeps its own
+// rows up to its new share, in order, and the rows beyond it go, in order, to
+// the CTAs below the even share (after those CTAs' own rows), which reach
+// their bodies in the owner's shared memory.  (Measured on the large pile:
+// moving the whole excess saved less, the remote accesses cost more than the
+// balance gained.)  Buckets
 // are laid out rank by rank (contacts, then joints).  Rows of one colour are
 // independent, so any assignment gives the same result.
 constexpr int OWNER_THREADS = 256, OWNER_WARPS = OWNER_THREADS / 32;
@@ -172,10 +174,23 @@ k_row_owner(int P, const int *part_bstart, const int *part_ncol, const int *solv
         for (int kind = 0; kind < 2; ++kind) {
             int all = 0;
             for (int r = 0; r < OWNER_RANKS; ++r) all += total[2 * r + kind];
+            // a CTA above the even share passes on half of its excess; the
+            // CTAs below it take those rows in rank order
+            int moved = 0;
+            for (int r = 0; r < OWNER_RANKS; ++r) {
+                const int k = 2 * r + kind;
+                const int even = r < C ? all / C + (r < all % C ? 1 : 0) : 0;
+                share[k] = total[k] > even ? total[k] - (total[k] - even) / 2 : even;
+                moved += total[k] - min(total[k], share[k]);
+            }
             int e = 0, d = 0;
             for (int r = 0; r < OWNER_RANKS; ++r) {
                 const int k = 2 * r + kind;
-                share[k] = r < C ? all / C + (r < all % C ? 1 : 0) : 0;
+                if (share[k] > total[k]) {
+                    const int take = min(share[k] - total[k], moved);
+                    share[k] = total[k] + take;
+                    moved -= take;
+                }
                 exc0[k] = e;
                 def0[k] = d;
                 e += max(0, total[k] - share[k]);
