@@ -585,7 +585,7 @@ void phase_rows(ovl_ctx *c, float dt_override) {
     a.scene_dt = c->scene_dt.p; a.scene_mu = c->scene_mu.p; a.dt_override = dt_override;
     a.erp = c->P.erp; a.slop = c->P.slop;
     a.r0 = c->r0.p; a.r1 = c->r1.p; a.r2 = c->r2.p; a.r3 = c->r3.p; a.rlam = c->rlam.p;
-    a.part_bstart = c->part_bstart.p; a.solve_C = c->solve_C.p;
+    a.part_bstart = c->part_bstart.p; a.solve_C = c->solve_C.p; a.solve_M = c->solve_M.p;
     a.rpair = c->rpair.p; a.status = c->status.p;
     if (c->has_boxes) {
         c->row_full.ensure(npr + 1);
@@ -694,6 +694,18 @@ void apply_solve_order(ovl_ctx *c, const SolvePlan &pl) {
     std::vector<int> C(P, pl.cluster);
     if (pl.shape >= 0) C = c->h_class_C;
     upload(c->solve_C, C.data(), (size_t)P, c->stream);
+    // which workers' launches keep the masses in shared memory (their rows
+    // take the packed form); the classes of a per-worker plan differ in C
+    std::vector<int> M(P, 0);
+    if (pl.shape >= 0) {
+        const int per_sm = kSolveShapes[pl.shape].per_sm;
+        for (int p = 0; p < P; ++p)
+            for (const SolveClass &k : pl.classes)
+                if (k.C == C[p]) M[p] = solve_masses_fit(c, k.slots, per_sm) ? 1 : 0;
+    } else {
+        std::fill(M.begin(), M.end(), solve_masses_fit(c, pl.slots, solve_ctas_per_sm(pl.unroll)) ? 1 : 0);
+    }
+    upload(c->solve_M, M.data(), (size_t)P, c->stream);
     c->col_off2.ensure((size_t)P * OWNER_NB + 1);
     c->pair_of_row2.ensure((size_t)c->npairs + 1);
     c->row_owner.ensure((size_t)c->npairs + 1);
@@ -1064,7 +1076,7 @@ void release_all(ovl_ctx *c) {
     c->ball_root.release(); c->ball_size.release(); c->ball_start.release(); c->ball_vtx.release();
     c->ball_list.release();
     c->worker_order.release(); c->wk.release(); c->wk2.release(); c->wv2.release();
-    c->class_order.release(); c->colour_order.release(); c->solve_C.release(); c->col_off2.release();
+    c->class_order.release(); c->colour_order.release(); c->solve_C.release(); c->solve_M.release(); c->col_off2.release();
     c->row_owner.release();
     c->pair_of_row2.release(); c->lb_loads.release();
     c->half.release(); c->iib.release(); c->c_p.release(); c->row_full.release(); c->rfull.release();

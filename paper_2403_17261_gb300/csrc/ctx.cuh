@@ -101,7 +101,7 @@ struct ovl_ctx {
     DBuf<uint32_t> class_order, colour_order;    // solve / colouring: workers grouped by CTAs per worker
     std::vector<int> h_pb, h_pp;                 // part_bstart, part_pstart of this step on the host
     std::vector<int> h_class_C;                  // CTAs per worker of the last per-worker plan
-    DBuf<int> solve_C, col_off2, pair_of_row2;   // solve: CTAs per worker, rows grouped by owner CTA
+    DBuf<int> solve_C, solve_M, col_off2, pair_of_row2;   // solve: CTAs per worker, masses in shared memory, rows by owner CTA
     DBuf<uint8_t> row_owner;                     // owner CTA of every row (scratch of the grouping)
     DBuf<uint8_t> row_full;                      // rows with a box end (contexts with boxes)
     DBuf<float4> rfull;                          // their records, FULL_ROW_WORDS float4 per row

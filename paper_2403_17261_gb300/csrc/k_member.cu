@@ -621,7 +621,9 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
 // Row records in colour order (the solver forms t1, t2, k_n, k_t and the
 // joint k's itself).  Contacts (sphere-sphere or sphere-plane):
 //   r0 = (n, slot_b)  r1 = (r_a, r_b, target_n, slot_a)  r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b)
-//   and the impulse record (lambda_n, lambda_t1, lambda_t2, k_n)
+//   and the impulse record (lambda_n, lambda_t1, lambda_t2, k_n); for a launch
+//   with the masses in shared memory r0 = (n, k_t) and r1 = (r_a, r_b,
+//   target_n, slot_a | slot_b << 16) with 16-bit slot codes
 // Ball joints (rows along the world axes):
 //   r0 = (r_A, target_x)  r1 = (r_B, target_y)  r2 = (target_z, 0, slot_a, slot_b)  r3 as for contacts
 // A slot word holds the bits of the solver's slot code of a worker slot s:
@@ -633,20 +635,22 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_colour(ColourArgs a) {
 // with r_A, r_B the pivot offsets from each body's centre in the world frame.
 // ---------------------------------------------------------------------------
 
-// the two slot words of a row (see above); a worker of 2^24 bodies or more
-// is a capacity error
-struct SlotWords { float a, b; };
-__device__ __forceinline__ SlotWords slot_words(const RowArgs &a, int p, int2 sl) {
+// the two slot words of a row (see above), and both as 16-bit codes (rank <<
+// 13 | i) packed in one word for a launch with the masses in shared memory;
+// a worker of 2^24 bodies or more, or a packed CTA of 8192 slots or more, is
+// a capacity error
+struct SlotWords { float a, b, packed; };
+__device__ __forceinline__ SlotWords slot_words(const RowArgs &a, int p, int2 sl, bool pack) {
     const int nb = a.part_bstart[p + 1] - a.part_bstart[p];
     const int C = max(1, a.solve_C[p]);
     const int per = max(1, (nb + C - 1) / C);
-    if (per >= (1 << 24) - 1) atomicCAS(a.status, DEV_OK, DEV_ERR_SLOTS);
+    if (per >= (1 << 24) - 1 || (pack && per >= (1 << 13))) atomicCAS(a.status, DEV_OK, DEV_ERR_SLOTS);
     const int own = sl.x >= 0 ? sl.x / per : max(sl.y, 0) / per;
-    auto code = [&](int s) {
-        const uint32_t c = s >= 0 ? ((uint32_t)(s / per) << 24 | (uint32_t)(s % per)) : ((uint32_t)own << 24 | (uint32_t)per);
-        return __uint_as_float(c);
+    auto code = [&](int s, int shift) {
+        return s >= 0 ? ((uint32_t)(s / per) << shift | (uint32_t)(s % per)) : ((uint32_t)own << shift | (uint32_t)per);
     };
-    return SlotWords{code(sl.x), code(sl.y)};
+    const uint32_t p16 = (code(sl.x, 13) & 0xffffu) | (code(sl.y, 13) & 0xffffu) << 16;
+    return SlotWords{__uint_as_float(code(sl.x, 24)), __uint_as_float(code(sl.y, 24)), __uint_as_float(p16)};
 }
 
 __device__ __forceinline__ bool body_is_box(const float4 *half, int b) {
@@ -697,7 +701,8 @@ __global__ void k_rows(RowArgs a) {
         const int2 sl = a.p_slot[k];
         const int scene = a.part_scene[a.ps_part[k]];
         const float h = a.dt_override > 0.f ? a.dt_override : a.scene_dt[scene];
-        const SlotWords sw = slot_words(a, a.ps_part[k], sl);
+        const bool pack = a.solve_M && a.solve_M[a.ps_part[k]];   // a launch with the masses in shared memory
+        const SlotWords sw = slot_words(a, a.ps_part[k], sl, pack);
         float lam_w = 0.f;   // a plain contact row: k_n (see below)
         if (a.row_full) {
             // a constraint with a box end: the full row, plus the slots in the
@@ -725,8 +730,8 @@ __global__ void k_rows(RowArgs a) {
                     const float phi = nphi.w;
                     tg[0] = phi > 0.f ? -phi / h : a.erp * fmaxf(-phi - a.slop, 0.f) / h;
                     tg[1] = tg[2] = 0.f;
-                    a.r0[r] = make_float4(0.f, 0.f, 0.f, sw.b);
-                    a.r1[r] = make_float4(0.f, 0.f, 0.f, sw.a);
+                    a.r0[r] = make_float4(0.f, 0.f, 0.f, pack ? 0.f : sw.b);
+                    a.r1[r] = make_float4(0.f, 0.f, 0.f, pack ? sw.packed : sw.a);
                     a.r3[r] = z;
                 } else {
                     const int j = i - a.nc;
@@ -776,8 +781,15 @@ __global__ void k_rows(RowArgs a) {
             }
             float phi = nphi.w;
             float target = phi > 0.f ? -phi / h : a.erp * fmaxf(-phi - a.slop, 0.f) / h;
-            a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, sw.b);
-            a.r1[r] = make_float4(ra, rb, target, sw.a);
+            if (pack) {
+                // k_t with the solver's operations (contact_kt)
+                const float kt = __frcp_rn(fmaf(iib, __fmul_rn(rb, rb), fmaf(iia, __fmul_rn(ra, ra), __fadd_rn(ima, imb))));
+                a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, kt);
+                a.r1[r] = make_float4(ra, rb, target, sw.packed);
+            } else {
+                a.r0[r] = make_float4(nphi.x, nphi.y, nphi.z, sw.b);
+                a.r1[r] = make_float4(ra, rb, target, sw.a);
+            }
             a.r3[r] = make_float4(ima, imb, iia, iib);
             lam_w = __frcp_rn(ima + imb);   // k_n, in the impulse record's spare lane
         } else {

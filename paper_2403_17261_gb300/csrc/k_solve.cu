@@ -34,11 +34,14 @@
 // target, slot_a); joint r0 = (r_A, target_x), r1 = (r_B, target_y), r2 =
 // (target_z, 0, slot_a, slot_b); both r3 = (1/m_a, 1/m_b, 1/I_a, 1/I_b),
 // read only when the masses are not in shared memory.  Slots are slot codes
-// (below).  A contact's impulse record is (lambda_n, lambda_t1, lambda_t2,
-// k_n), k_n = 1 / (1/m_a + 1/m_b) written by the row build.  The contact
-// forms t1 = normalise(e_k - (n . e_k) n) (k the axis of the smallest
-// |n_k|) and the tangents' k_t = 1 / (1/m_a + 1/m_b + r_a^2 / I_a + r_b^2 /
-// I_b) from the bodies' masses, so both layouts compute the same bits.
+// (below).  In a launch with the masses in shared memory a contact has r0 =
+// (n, k_t) and r1 = (r_a, r_b, target, slot_a | slot_b << 16) with 16-bit
+// codes (such a CTA holds under 8192 slots).  A contact's impulse record is
+// (lambda_n, lambda_t1, lambda_t2, k_n).  k_n = 1 / (1/m_a + 1/m_b) and k_t =
+// 1 / (1/m_a + 1/m_b + r_a^2 / I_a + r_b^2 / I_b) come from the row build, or
+// k_t is formed here from the row's masses with the same operations, so both
+// layouts compute the same bits; t1 = normalise(e_k - (n . e_k) n) (k the
+// axis of the smallest |n_k|) is formed here.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -243,17 +246,26 @@ __device__ __forceinline__ void fetch_row_rest(const SolveArgs &a, int r, bool j
     if (joint) w.z = a.r2[r];
 }
 
-// the slot codes (a, b) of a row
+// a 16-bit slot code (rank << 13 | i) as a slot code
+__device__ __forceinline__ uint32_t code_from16(uint32_t c) { return (c >> 13) << 24 | (c & 0x1fffu); }
+
+// the slot codes (a, b) of a row: a contact of a launch with the masses in
+// shared memory packs both as 16-bit codes in r1.w (its r0.w holds k_t)
+template <class S>
 __device__ __forceinline__ uint2 row_slots(const Row &w) {
-    return w.joint ? make_uint2(__float_as_uint(w.z.z), __float_as_uint(w.z.w))
-                   : make_uint2(__float_as_uint(w.y.w), __float_as_uint(w.x.w));
+    if (w.joint) return make_uint2(__float_as_uint(w.z.z), __float_as_uint(w.z.w));
+    if (S::kMasses) {
+        const uint32_t c = __float_as_uint(w.y.w);
+        return make_uint2(code_from16(c & 0xffffu), code_from16(c >> 16));
+    }
+    return make_uint2(__float_as_uint(w.y.w), __float_as_uint(w.x.w));
 }
 
 // a static end reads its zero slot (or, without the masses in the slots,
 // zero masses from r3)
 template <class S>
 __device__ __forceinline__ void load_pair(const S &st, const Row &w, Body &A, Body &B) {
-    const uint2 slots = row_slots(w);
+    const uint2 slots = row_slots<S>(w);
     st.load(slots.x, A);
     st.load(slots.y, B);
     if (!S::kMasses) { A.im = w.m.x; B.im = w.m.y; A.ii = w.m.z; B.ii = w.m.w; }
@@ -262,6 +274,13 @@ __device__ __forceinline__ void load_pair(const S &st, const Row &w, Body &A, Bo
 // k_t of a contact's tangent rows from the bodies' masses and lever radii
 __device__ __forceinline__ float contact_kt(const Body &A, const Body &B, float ra, float rb) {
     return __frcp_rn(fmaf(B.ii, rb * rb, fmaf(A.ii, ra * ra, A.im + B.im)));
+}
+
+// k_t as the launch has it: in r0.w (masses in shared memory, written by the
+// row build with the same operations), or formed from the row's masses
+template <class S>
+__device__ __forceinline__ float row_kt(const Row &w, const Body &A, const Body &B) {
+    return S::kMasses ? w.x.w : contact_kt(A, B, w.y.x, w.y.y);
 }
 
 // t1 of a contact, formed from its normal
@@ -291,10 +310,9 @@ __device__ __forceinline__ void contact_impulse(Body &A, Body &B, float3 n, floa
 }
 
 __device__ __forceinline__ void contact_row(Body &A, Body &B, float4 r0, float4 r1, float3 t1, float kn,
-                                            float mu, float4 &lam) {
+                                            float kt, float mu, float4 &lam) {
     const float3 n = f3(r0);
     const float ra = r1.x, rb = r1.y, target = r1.z;
-    const float kt = contact_kt(A, B, ra, rb);
     const float3 t2 = cross3(n, t1);
     // normal row
     float3 dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
@@ -370,7 +388,7 @@ __device__ __forceinline__ void solve_row(Body &A, Body &B, const Row &w, float 
     if (w.joint) {
         joint_rows(A, B, w.x, w.y, w.z, lam);
     } else {
-        contact_row(A, B, w.x, w.y, contact_t1(w), lam.w, mu, lam);
+        contact_row(A, B, w.x, w.y, contact_t1(w), lam.w, row_kt<S>(w, A, B), mu, lam);
     }
 }
 
@@ -448,10 +466,9 @@ __device__ float full_residual_sq(const SolveArgs &a, int r, bool joint, const B
 // residual (lambda - clamp(lambda + k (target - w), lo, hi)) / k of a row
 // group, squared and summed
 __device__ __forceinline__ float contact_residual_sq(const Body &A, const Body &B, float4 r0, float4 r1,
-                                                     float3 t1, float kn, float mu, float4 lam) {
+                                                     float3 t1, float kn, float kt, float mu, float4 lam) {
     const float3 n = f3(r0);
     const float ra = r1.x, rb = r1.y, target = r1.z;
-    const float kt = contact_kt(A, B, ra, rb);
     const float3 t2 = cross3(n, t1);
     float3 dv = make_float3(B.v.x - A.v.x, B.v.y - A.v.y, B.v.z - A.v.z);
     float3 u = lever_sum(ra, A.w, rb, B.w);
@@ -576,7 +593,7 @@ __device__ float rows_residual_sq(const SolveArgs &a, const S &st, const Buckets
                 } else if (w.joint) {
                     sq += joint_residual_sq(A, B, w.x, w.y, w.z);
                 } else {
-                    sq += contact_residual_sq(A, B, w.x, w.y, contact_t1(w), lam.w, mu, lam);
+                    sq += contact_residual_sq(A, B, w.x, w.y, contact_t1(w), lam.w, row_kt<S>(w, A, B), mu, lam);
                 }
             }
         }
@@ -646,7 +663,7 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                 joint_impulse(A, B, f3(w.x), f3(w.y), 1, lam.y);
                 joint_impulse(A, B, f3(w.x), f3(w.y), 2, lam.z);
             }
-            store_pair(st, row_slots(w), A, B);
+            store_pair(st, row_slots<S>(w), A, B);
         }
       }
       group_sync<C>();
@@ -686,8 +703,8 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                     load_pair(st, w, D, E);
                     solve_any<S, X>(a, r, A, B, u, mu, xl);
                     solve_any<S, X>(a, q, D, E, w, mu, yl);
-                    store_pair(st, row_slots(u), A, B);
-                    store_pair(st, row_slots(w), D, E);
+                    store_pair(st, row_slots<S>(u), A, B);
+                    store_pair(st, row_slots<S>(w), D, E);
                     a.rlam[r] = xl;
                     a.rlam[q] = yl;
                     pre_rows<S>(a, r + 2 * T, ce, T, cur);
@@ -700,7 +717,7 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                     Body A, B;
                     load_pair(st, w, A, B);
                     solve_any<S, X>(a, r, A, B, w, mu, lam);
-                    store_pair(st, row_slots(w), A, B);
+                    store_pair(st, row_slots<S>(w), A, B);
                     a.rlam[r] = lam;
                 }
             } else {
@@ -717,8 +734,8 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                         load_pair(st, w, D, E);
                         solve_any<S, X>(a, r, A, B, u, mu, xl);
                         solve_any<S, X>(a, q, D, E, w, mu, yl);
-                        store_pair(st, row_slots(u), A, B);
-                        store_pair(st, row_slots(w), D, E);
+                        store_pair(st, row_slots<S>(u), A, B);
+                        store_pair(st, row_slots<S>(w), D, E);
                         a.rlam[r] = xl;
                         a.rlam[q] = yl;
                     }
@@ -730,7 +747,7 @@ __device__ void solve_worker(const SolveArgs &a, const S &st, int p, int rank, i
                     Body A, B;
                     load_pair(st, w, A, B);
                     solve_any<S, X>(a, r, A, B, w, mu, lam);
-                    store_pair(st, row_slots(w), A, B);
+                    store_pair(st, row_slots<S>(w), A, B);
                     a.rlam[r] = lam;
                 }
             }

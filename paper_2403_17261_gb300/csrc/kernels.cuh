@@ -178,6 +178,7 @@ struct RowArgs {
     float4 *r0, *r1, *r2, *r3;   // r2: joints only
     const int *part_bstart;      // [P+1] worker slot ranges
     const int *solve_C;          // [P] CTAs per worker in the solve plan (slot codes)
+    const int *solve_M;          // [P] 1: the worker's launch keeps the masses in shared memory (or NULL)
     int *rpair;                // [np] pair index of every row (canonical order)
     float4 *rlam;
     int *status;
