@@ -21,20 +21,7 @@
 
 using namespace ovl;
 
-
-namespace {
-
-uint32_t next_pow2(uint64_t x) {
-    uint32_t p = 1;
-    while (p < x && p < (1u << 31)) p <<= 1;
-    return p;
-}
-
-int bits_for(int n) {
-    int b = 1;
-    while ((1 << b) < n && b < 31) ++b;
-    return b;
-}
+namespace ovl {
 
 ovl_status check_device_status(ovl_ctx *c) {
     int s = read_i32(c, c->status.p);
@@ -50,9 +37,26 @@ ovl_status check_device_status(ovl_ctx *c) {
             return fail(c, OVL_ERR_MEMBERSHIP, "dynamic body with no worker, or a worker index out of range");
         case DEV_ERR_COLOURS:
             return fail(c, OVL_ERR_CAPACITY, "a worker needs more than 128 colours (bodies in about 128 or more constraints)");
-        case DEV_ERR_TIMEOUT: return fail(c, OVL_ERR_TIMEOUT, "colouring did not finish within its round limit");
+        case DEV_ERR_TIMEOUT:
+            return fail(c, OVL_ERR_TIMEOUT, "a bounded device-side wait gave up (colouring rounds, or a tensor-core MMA)");
         default: return fail(c, OVL_ERR_CUDA, "unknown device status");
     }
+}
+
+}  // namespace ovl
+
+namespace {
+
+uint32_t next_pow2(uint64_t x) {
+    uint32_t p = 1;
+    while (p < x && p < (1u << 31)) p <<= 1;
+    return p;
+}
+
+int bits_for(int n) {
+    int b = 1;
+    while ((1 << b) < n && b < 31) ++b;
+    return b;
 }
 
 void mark(ovl_ctx *c, int i) {

@@ -189,6 +189,9 @@ void download(T *dst, const T *src, size_t n, cudaStream_t s) {
     if (n) CK(cudaMemcpyAsync(dst, src, sizeof(T) * n, cudaMemcpyDeviceToHost, s));
 }
 
+// the step's device status word as an ovl_status (and the message)
+ovl_status check_device_status(ovl_ctx *c);
+
 // learned warm start (mlp.cu): features and the network's proposal before
 // the rows are built; the log after the solve; buffers freed with the context
 void phase_warmstart(ovl_ctx *c, float dt_override);

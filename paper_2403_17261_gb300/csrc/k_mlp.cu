@@ -17,13 +17,16 @@
 // (features 4-6, added in FP32).  A warm start takes s y, keeps the normal
 // impulse non-negative and clamps each friction impulse to mu times it.
 //
-// Inference runs on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32
-// accumulators): a warp takes 16 pairs, and the accumulator fragments of one
-// layer become the operand fragments of the next without leaving registers.
-// Training uses the same arithmetic on CUDA cores (operands rounded to BF16,
-// products exact in FP32, FP32 sums): one thread per sample for the forward
-// and backward passes, block-partial weight gradients summed in block order
-// (deterministic), and Adam on FP32 master parameters.
+// Inference runs on the 5th-generation tensor cores: tcgen05.mma with BF16
+// operands in shared memory and FP32 accumulators in tensor memory, 128 pairs
+// per CTA at a time (one MMA for layer 1, four K-steps each for layers 2 and
+// 3); the epilogue of each layer reads its accumulator rows from tensor
+// memory (tcgen05.ld), adds the bias, applies the ReLU and writes the next
+// layer's BF16 operand to shared memory.  Training uses the same arithmetic
+// on CUDA cores (operands rounded to BF16, products exact in FP32, FP32
+// sums): one thread per sample for the forward and backward passes,
+// block-partial weight gradients summed in block order (deterministic), and
+// Adam on FP32 master parameters.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -38,11 +41,12 @@ namespace {
 // parameter vector (C ABI layout)
 constexpr int OFF_W1 = 0, OFF_B1 = 768, OFF_W2 = 832, OFF_B2 = 4928, OFF_W3 = 4992, OFF_B3 = 5184;
 static_assert(OFF_B3 + 3 == MLP_N_PARAMS, "parameter layout");
-// packed inference weights (32-bit words): B fragments of W1 [8 n-tiles][32
-// lanes][2], W2 [4 k-tiles][8 n-tiles][32][2], W3 [4 k-tiles][32][2], then
-// FP32 biases b1 [64], b2 [64], b3 [8] (zero-padded)
-constexpr int PK_W1 = 0, PK_W2 = 512, PK_W3 = 2560, PK_B1 = 2816, PK_B2 = 2880, PK_B3 = 2944;
-static_assert(PK_B3 + 8 == MLP_PK_WORDS, "packed layout");
+// packed inference weights (32-bit words): the MMAs' B operands in the
+// K-major, unswizzled tensor-core layout (below) -- W1^T [64 x 16] (inputs
+// 12-15 zero), W2^T [64 x 64], W3^T [16 x 64] (outputs 3-15 zero) -- then
+// FP32 biases b1 [64], b2 [64], b3 [16] (zero-padded)
+constexpr int PK_W1 = 0, PK_W2 = 512, PK_W3 = 2560, PK_B1 = 3072, PK_B2 = 3136, PK_B3 = 3200;
+static_assert(PK_B3 + 16 == MLP_PK_WORDS, "packed layout");
 // activation rows of the training pass
 constexpr int A_X = 0, A_H1 = 16, A_H2 = 80, A_DZ1 = 144, A_DZ2 = 208, A_DY = 272;
 static_assert(A_DY + 4 == MLP_ACT_STRIDE, "activation layout");
@@ -54,12 +58,67 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
-__device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint2 b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+// ---- tensor-core operands and instructions (tcgen05) --------------------------
+// A K-major operand with K columns, unswizzled: 8 x 8 core matrices (8 rows of
+// 16 B, 128 B each), the core matrices of one 8-row group adjacent along K
+// (leading byte offset 128 B), the 8-row groups K * 16 B apart (stride byte
+// offset).  Byte offset of element (row r, column k):
+__host__ __device__ __forceinline__ uint32_t kmajor_off(int r, int k, int K) {
+    return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start >> 4 (bits 0-13), leading byte
+// offset >> 4 (16-29), stride byte offset >> 4 (32-45), the fixed 0b001 at
+// 46-48, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | (uint64_t)((lbo >> 4) & 0x3FFFu) << 16 |
+           (uint64_t)((sbo >> 4) & 0x3FFFu) << 32 | (uint64_t)1 << 46;
+}
+
+// instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
+constexpr uint32_t umma_idesc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// D[tmem] (+)= A B^T for M = 128 rows, one K = 16 step; issued by one thread
+__device__ __forceinline__ void umma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, bool acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 :: "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc ? 1u : 0u) : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
+}
+
+// waits for phase `parity` of the mbarrier; false after the iteration limit
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// this thread's accumulator row (TMEM lane = row), 16 columns from column col
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {   // SplitMix64 finaliser
@@ -166,31 +225,28 @@ __global__ void k_features(FeatArgs a) {
 // ---- inference ---------------------------------------------------------------
 
 __global__ void k_mlp_pack(const float *th, uint32_t *pk) {
-    for (int e = threadIdx.x; e < 8 * 32; e += blockDim.x) {
-        const int j = e >> 5, lane = e & 31, g = lane >> 2, t = lane & 3, col = 8 * j + g;
-        auto w = [&](int k) { return k < 12 ? th[OFF_W1 + k * 64 + col] : 0.f; };
-        pk[PK_W1 + 2 * e] = pack_bf16(w(2 * t), w(2 * t + 1));
-        pk[PK_W1 + 2 * e + 1] = pack_bf16(w(2 * t + 8), w(2 * t + 9));
+    uint8_t *w = reinterpret_cast<uint8_t *>(pk);
+    auto put = [&](int word0, int r, int k, int K, float v) {
+        *reinterpret_cast<__nv_bfloat16 *>(w + 4 * word0 + kmajor_off(r, k, K)) = __float2bfloat16_rn(v);
+    };
+    for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) {    // W1^T: row = output, column = input
+        const int n = e / 16, k = e % 16;
+        put(PK_W1, n, k, 16, k < 12 ? th[OFF_W1 + k * 64 + n] : 0.f);
     }
-    for (int e = threadIdx.x; e < 4 * 8 * 32; e += blockDim.x) {
-        const int kk = e >> 8, j = (e >> 5) & 7, lane = e & 31, g = lane >> 2, t = lane & 3;
-        const int col = 8 * j + g, k0 = 16 * kk + 2 * t;
-        auto w = [&](int k) { return th[OFF_W2 + k * 64 + col]; };
-        pk[PK_W2 + 2 * e] = pack_bf16(w(k0), w(k0 + 1));
-        pk[PK_W2 + 2 * e + 1] = pack_bf16(w(k0 + 8), w(k0 + 9));
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int n = e / 64, k = e % 64;
+        put(PK_W2, n, k, 64, th[OFF_W2 + k * 64 + n]);
     }
-    for (int e = threadIdx.x; e < 4 * 32; e += blockDim.x) {
-        const int kk = e >> 5, lane = e & 31, g = lane >> 2, t = lane & 3, k0 = 16 * kk + 2 * t;
-        auto w = [&](int k) { return g < 3 ? th[OFF_W3 + k * 3 + g] : 0.f; };
-        pk[PK_W3 + 2 * e] = pack_bf16(w(k0), w(k0 + 1));
-        pk[PK_W3 + 2 * e + 1] = pack_bf16(w(k0 + 8), w(k0 + 9));
+    for (int e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
+        const int n = e / 64, k = e % 64;
+        put(PK_W3, n, k, 64, n < 3 ? th[OFF_W3 + k * 3 + n] : 0.f);
     }
     float *bias = reinterpret_cast<float *>(pk);
     for (int e = threadIdx.x; e < 64; e += blockDim.x) {
         bias[PK_B1 + e] = th[OFF_B1 + e];
         bias[PK_B2 + e] = th[OFF_B2 + e];
     }
-    for (int e = threadIdx.x; e < 8; e += blockDim.x) bias[PK_B3 + e] = e < 3 ? th[OFF_B3 + e] : 0.f;
+    for (int e = threadIdx.x; e < 16; e += blockDim.x) bias[PK_B3 + e] = e < 3 ? th[OFF_B3 + e] : 0.f;
 }
 
 template <int MODE>
@@ -212,76 +268,129 @@ __device__ __forceinline__ void infer_store(int r, int n, float y0, float y1, fl
                           fminf(fmaxf(meta.y * y2, -lim), lim), 0.f);
 }
 
+// One CTA of 128 threads holds the weights in shared memory and takes tiles
+// of 128 pairs in turn; thread t owns row t of a tile (TMEM lane t).  Per
+// tile: X (12 features + 4 zero columns, BF16) -> D1 = X W1 (one MMA) ->
+// H = relu(D1 + b1) -> D2 = H W2 (four K-steps) -> H = relu(D2 + b2) -> D3
+// = H W3 (N = 16, four K-steps) -> y = D3 + b3.  Accumulators: D1 and D3 in
+// TMEM columns 0-63 (D3 in 0-15), D2 in 64-127.  Every wait on an MMA is
+// bounded; a wait that gives up sets the device status, and the CTA stops
+// taking tiles, waits once more and frees its tensor memory.
+constexpr int INFER_THREADS = 128, INFER_COLS = 128;
+
 template <int MODE>
-__global__ void __launch_bounds__(256) k_mlp_infer(const uint32_t *pk, const float4 *feat, int n,
-                                                   float4 *lam0, float *y3) {
-    __shared__ __align__(16) uint32_t sp[MLP_PK_WORDS];
-    for (int i = threadIdx.x; i < MLP_PK_WORDS; i += blockDim.x) sp[i] = pk[i];
-    __syncthreads();
-    const uint2 *w1 = reinterpret_cast<const uint2 *>(sp + PK_W1);
-    const uint2 *w2 = reinterpret_cast<const uint2 *>(sp + PK_W2);
-    const uint2 *w3 = reinterpret_cast<const uint2 *>(sp + PK_W3);
-    const float *b1 = reinterpret_cast<const float *>(sp + PK_B1);
-    const float *b2 = reinterpret_cast<const float *>(sp + PK_B2);
-    const float *b3 = reinterpret_cast<const float *>(sp + PK_B3);
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    const float *F = reinterpret_cast<const float *>(feat);
-    const int tiles = (n + 15) >> 4;
-    for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < tiles; tile += warps) {
-        const int r0 = 16 * tile + g, r1 = r0 + 8;
-        // layer-1 operands: features 0..11 of rows r0 and r1, columns 12..15 zero
-        float2 x00 = make_float2(0.f, 0.f), x01 = x00, x10 = x00, x11 = x00;
-        if (r0 < n) {
-            x00 = *reinterpret_cast<const float2 *>(F + 16 * (size_t)r0 + 2 * t);
-            if (t < 2) x01 = *reinterpret_cast<const float2 *>(F + 16 * (size_t)r0 + 2 * t + 8);
-        }
-        if (r1 < n) {
-            x10 = *reinterpret_cast<const float2 *>(F + 16 * (size_t)r1 + 2 * t);
-            if (t < 2) x11 = *reinterpret_cast<const float2 *>(F + 16 * (size_t)r1 + 2 * t + 8);
-        }
-        uint32_t a[4] = {pack_bf16(x00.x, x00.y), pack_bf16(x10.x, x10.y), pack_bf16(x01.x, x01.y),
-                         pack_bf16(x11.x, x11.y)};
-        float acc[8][4];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float c0 = b1[8 * j + 2 * t], c1 = b1[8 * j + 2 * t + 1];
-            acc[j][0] = c0; acc[j][1] = c1; acc[j][2] = c0; acc[j][3] = c1;
-            mma_bf16(acc[j], a, w1[j * 32 + lane]);
-        }
-        uint32_t hf[4][4];
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            hf[kk][0] = pack_bf16(fmaxf(acc[2 * kk][0], 0.f), fmaxf(acc[2 * kk][1], 0.f));
-            hf[kk][1] = pack_bf16(fmaxf(acc[2 * kk][2], 0.f), fmaxf(acc[2 * kk][3], 0.f));
-            hf[kk][2] = pack_bf16(fmaxf(acc[2 * kk + 1][0], 0.f), fmaxf(acc[2 * kk + 1][1], 0.f));
-            hf[kk][3] = pack_bf16(fmaxf(acc[2 * kk + 1][2], 0.f), fmaxf(acc[2 * kk + 1][3], 0.f));
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float c0 = b2[8 * j + 2 * t], c1 = b2[8 * j + 2 * t + 1];
-            acc[j][0] = c0; acc[j][1] = c1; acc[j][2] = c0; acc[j][3] = c1;
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) mma_bf16(acc[j], hf[kk], w2[(kk * 8 + j) * 32 + lane]);
-        }
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            hf[kk][0] = pack_bf16(fmaxf(acc[2 * kk][0], 0.f), fmaxf(acc[2 * kk][1], 0.f));
-            hf[kk][1] = pack_bf16(fmaxf(acc[2 * kk][2], 0.f), fmaxf(acc[2 * kk][3], 0.f));
-            hf[kk][2] = pack_bf16(fmaxf(acc[2 * kk + 1][0], 0.f), fmaxf(acc[2 * kk + 1][1], 0.f));
-            hf[kk][3] = pack_bf16(fmaxf(acc[2 * kk + 1][2], 0.f), fmaxf(acc[2 * kk + 1][3], 0.f));
-        }
-        float o[4] = {b3[2 * t], b3[2 * t + 1], b3[2 * t], b3[2 * t + 1]};
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) mma_bf16(o, hf[kk], w3[kk * 32 + lane]);
-        // outputs 0, 1 sit in lane 4g (t = 0), output 2 in lane 4g + 1
-        const float y2a = __shfl_down_sync(0xffffffffu, o[0], 1);
-        const float y2b = __shfl_down_sync(0xffffffffu, o[2], 1);
-        if (t == 0) {
-            infer_store<MODE>(r0, n, o[0], o[1], y2a, feat, lam0, y3);
-            infer_store<MODE>(r1, n, o[2], o[3], y2b, feat, lam0, y3);
-        }
+__global__ void __launch_bounds__(INFER_THREADS) k_mlp_infer(const uint32_t *pk, const float4 *feat, int n,
+                                                            float4 *lam0, float *y3, int *status) {
+    __shared__ __align__(1024) uint8_t sw1[64 * 16 * 2];
+    __shared__ __align__(1024) uint8_t sw2[64 * 64 * 2];
+    __shared__ __align__(1024) uint8_t sw3[16 * 64 * 2];
+    __shared__ __align__(1024) uint8_t sx[128 * 16 * 2];
+    __shared__ __align__(1024) uint8_t sh[128 * 64 * 2];
+    __shared__ float sb[64 + 64 + 16];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    {
+        const uint32_t *src = pk;
+        for (int i = tid; i < 512; i += INFER_THREADS) reinterpret_cast<uint32_t *>(sw1)[i] = src[PK_W1 + i];
+        for (int i = tid; i < 2048; i += INFER_THREADS) reinterpret_cast<uint32_t *>(sw2)[i] = src[PK_W2 + i];
+        for (int i = tid; i < 512; i += INFER_THREADS) reinterpret_cast<uint32_t *>(sw3)[i] = src[PK_W3 + i];
+        const float *b = reinterpret_cast<const float *>(pk);
+        for (int i = tid; i < 144; i += INFER_THREADS) sb[i] = b[PK_B1 + i];
     }
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(dst), "n"(INFER_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 rows
+    const uint32_t ax = (uint32_t)__cvta_generic_to_shared(sx), ah = (uint32_t)__cvta_generic_to_shared(sh);
+    const uint32_t b1a = (uint32_t)__cvta_generic_to_shared(sw1), b2a = (uint32_t)__cvta_generic_to_shared(sw2),
+                   b3a = (uint32_t)__cvta_generic_to_shared(sw3);
+    uint32_t phase = 0;
+    bool ok = true;
+    const float *F = reinterpret_cast<const float *>(feat);
+    const int tiles = (n + 127) >> 7;
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const int r = 128 * tile + tid;
+        // layer-1 operand: this thread's row, features 0-11 and four zeros
+        {
+            float x[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) x[k] = 0.f;
+            if (r < n) {
+#pragma unroll
+                for (int k = 0; k < 12; ++k) x[k] = F[16 * (size_t)r + k];
+            }
+            uint32_t q[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) q[k] = pack_bf16(x[2 * k], x[2 * k + 1]);
+            *reinterpret_cast<uint4 *>(sx + kmajor_off(tid, 0, 16)) = make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4 *>(sx + kmajor_off(tid, 8, 16)) = make_uint4(q[4], q[5], q[6], q[7]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_sync();
+        if (tid == 0) {
+            umma_f16(tmem, umma_desc(ax, 128, 16 * 16), umma_desc(b1a, 128, 16 * 16), umma_idesc(128, 64), false);
+            umma_commit(mb);
+        }
+        ok = __syncthreads_and(mbar_wait(mb, phase));   // the same decision in every thread
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) break;
+        // H = relu(D + b) as this row of the next operand, twice (layers 1, 2)
+#pragma unroll 1
+        for (int layer = 0; layer < 2; ++layer) {
+            const uint32_t dcol = layer == 0 ? 0u : 64u;
+            const float *bias = sb + 64 * layer;
+#pragma unroll
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                float v[16];
+                tmem_ld16(lane_base + dcol + c0, v);
+                uint32_t q[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    q[k] = pack_bf16(fmaxf(v[2 * k] + bias[c0 + 2 * k], 0.f), fmaxf(v[2 * k + 1] + bias[c0 + 2 * k + 1], 0.f));
+                *reinterpret_cast<uint4 *>(sh + kmajor_off(tid, c0, 64)) = make_uint4(q[0], q[1], q[2], q[3]);
+                *reinterpret_cast<uint4 *>(sh + kmajor_off(tid, c0 + 8, 64)) = make_uint4(q[4], q[5], q[6], q[7]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_sync();
+            if (tid == 0) {
+                // layer 2 into D2 (columns 64-127); layer 3 (N = 16) into columns 0-15
+                const uint32_t d = layer == 0 ? tmem + 64u : tmem;
+                const uint32_t bop = layer == 0 ? b2a : b3a;
+                const uint32_t idesc = layer == 0 ? umma_idesc(128, 64) : umma_idesc(128, 16);
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                    umma_f16(d, umma_desc(ah + 256u * ks, 128, 64 * 16), umma_desc(bop + 256u * ks, 128, 64 * 16), idesc, ks > 0);
+                umma_commit(mb);
+            }
+            ok = __syncthreads_and(mbar_wait(mb, phase));
+            phase ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok) break;
+        }
+        if (!ok) break;
+        float o[16];
+        tmem_ld16(lane_base, o);
+        const float *b3 = sb + 128;
+        infer_store<MODE>(r, n, o[0] + b3[0], o[1] + b3[1], o[2] + b3[2], feat, lam0, y3);
+        tc_sync();   // every row read out before the next tile's MMAs reuse the operands and columns
+    }
+    if (!ok) {
+        if (tid == 0) atomicCAS(status, DEV_OK, DEV_ERR_TIMEOUT);
+        mbar_wait(mb, phase);   // an MMA still in flight, once more (bounded)
+    }
+    tc_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(INFER_COLS) : "memory");
 }
 
 // ---- log -----------------------------------------------------------------------
@@ -555,13 +664,14 @@ void launch_mlp_pack(const float *theta, uint32_t *packed, cudaStream_t s) {
 }
 
 void launch_mlp_infer(const uint32_t *packed, const float4 *feat, int n, int mode, float4 *lam0,
-                      float *y3, int grid_limit, cudaStream_t s) {
+                      float *y3, int grid_limit, int *status, cudaStream_t s) {
     if (n <= 0) return;
-    const int tiles = (n + 15) / 16;
-    int grid = std::min((tiles + 7) / 8, grid_limit > 0 ? grid_limit : 152 * 4);
-    if (mode == 0) k_mlp_infer<0><<<grid, 256, 0, s>>>(packed, feat, n, lam0, y3);
-    else if (mode == 1) k_mlp_infer<1><<<grid, 256, 0, s>>>(packed, feat, n, lam0, y3);
-    else k_mlp_infer<2><<<grid, 256, 0, s>>>(packed, feat, n, lam0, y3);
+    // up to 4 CTAs per SM: 4 x 128 tensor-memory columns fill an SM's 512
+    const int tiles = (n + 127) / 128;
+    const int grid = std::min(tiles, grid_limit > 0 ? grid_limit : 152 * 4);
+    if (mode == 0) k_mlp_infer<0><<<grid, INFER_THREADS, 0, s>>>(packed, feat, n, lam0, y3, status);
+    else if (mode == 1) k_mlp_infer<1><<<grid, INFER_THREADS, 0, s>>>(packed, feat, n, lam0, y3, status);
+    else k_mlp_infer<2><<<grid, INFER_THREADS, 0, s>>>(packed, feat, n, lam0, y3, status);
     note_launch();
     CK(cudaGetLastError());
 }

@@ -293,7 +293,7 @@ void launch_unpack_state(const float4 *st, int n, float *out13, cudaStream_t s);
 // friction coefficient, contact flag (1 for contacts, 0 for joints).
 #define MLP_DEPTH_CAP 8
 #define MLP_N_PARAMS 5187
-#define MLP_PK_WORDS 2952      // packed BF16 fragments + FP32 biases
+#define MLP_PK_WORDS 3216      // BF16 tensor-core operands + FP32 biases
 #define MLP_ACT_STRIDE 276     // x 16, h1 64, h2 64, dz1 64, dz2 64, dy 4
 struct FeatArgs {
     int np, nc, n;
@@ -316,9 +316,11 @@ void launch_depth(const uint64_t *mask, const int *row_ptr, const int *col, int 
 void launch_features(const FeatArgs &a, cudaStream_t s);
 void launch_mlp_pack(const float *theta, uint32_t *packed, cudaStream_t s);
 // mode 0: raw outputs to y3 [n][3]; 1: warm start of every contact into lam0;
-// 2: warm start of the contacts without previous impulses into lam0
+// 2: warm start of the contacts without previous impulses into lam0.  On the
+// tensor cores (tcgen05); a wait on them that gives up sets *status to
+// DEV_ERR_TIMEOUT.
 void launch_mlp_infer(const uint32_t *packed, const float4 *feat, int n, int mode, float4 *lam0,
-                      float *y3, int grid_limit, cudaStream_t s);
+                      float *y3, int grid_limit, int *status, cudaStream_t s);
 void launch_log_append(const float4 *feat, const float4 *lam, const int *pos, int np,
                        float *log_feat, float *log_targ, long long base, long long cap,
                        cudaStream_t s);

@@ -73,7 +73,7 @@ void phase_warmstart(ovl_ctx *c, float dt_override) {
     a.feat = c->feat.p; a.is_contact = c->is_contact.p;
     launch_features(a, s);
     if (c->ws_mode != OVL_WS_PREVIOUS)
-        launch_mlp_infer(c->mlp_packed.p, c->feat.p, np, c->ws_mode, c->p_lam0.p, nullptr, 0, s);
+        launch_mlp_infer(c->mlp_packed.p, c->feat.p, np, c->ws_mode, c->p_lam0.p, nullptr, 0, c->status.p, s);
     if (c->P.flags & OVL_FLAG_TIMING) CK(cudaEventRecord(c->ev[13], s));
     c->feat_valid = true;
 }
@@ -173,10 +173,10 @@ ovl_status ovl_mlp_forward(ovl_ctx *c, int64_t n, const float *feat12, float *y3
         c->infer_feat.ensure(4 * (size_t)n);
         CK(cudaMemcpyAsync(c->infer_feat.p, rows.data(), rows.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         c->infer_y.ensure(3 * (size_t)n);
-        launch_mlp_infer(c->mlp_packed.p, c->infer_feat.p, (int)n, 0, nullptr, c->infer_y.p, 0, c->stream);
+        launch_mlp_infer(c->mlp_packed.p, c->infer_feat.p, (int)n, 0, nullptr, c->infer_y.p, 0, c->status.p, c->stream);
         download(y3, c->infer_y.p, 3 * (size_t)n, c->stream);
         CK(cudaStreamSynchronize(c->stream));
-        return OVL_OK;
+        return check_device_status(c);
     });
 }
 
