@@ -316,19 +316,30 @@ __global__ void __launch_bounds__(INFER_THREADS) k_mlp_infer(const uint32_t *pk,
                    b3a = (uint32_t)__cvta_generic_to_shared(sw3);
     uint32_t phase = 0;
     bool ok = true;
-    const float *F = reinterpret_cast<const float *>(feat);
     const int tiles = (n + 127) >> 7;
+    // this thread's features of its row of a tile (zeros past the end); the
+    // next tile's are loaded while the current tile's MMAs run
+    auto load_row = [&](int t, float *x) {
+        const int rr = 128 * t + tid;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) x[k] = 0.f;
+        if (t < tiles && rr < n) {
+            const float4 *f = feat + 4 * (size_t)rr;
+            const float4 a = f[0], b = f[1], c = f[2];
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y;
+            x[6] = b.z; x[7] = b.w; x[8] = c.x; x[9] = c.y; x[10] = c.z; x[11] = c.w;
+        }
+    };
+    float xn[12];
+    load_row(blockIdx.x, xn);
     for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
         const int r = 128 * tile + tid;
         // layer-1 operand: this thread's row, features 0-11 and four zeros
         {
             float x[16];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) x[k] = 0.f;
-            if (r < n) {
-#pragma unroll
-                for (int k = 0; k < 12; ++k) x[k] = F[16 * (size_t)r + k];
-            }
+            for (int k = 0; k < 12; ++k) x[k] = xn[k];
+            x[12] = x[13] = x[14] = x[15] = 0.f;
             uint32_t q[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) q[k] = pack_bf16(x[2 * k], x[2 * k + 1]);
@@ -341,6 +352,7 @@ __global__ void __launch_bounds__(INFER_THREADS) k_mlp_infer(const uint32_t *pk,
             umma_f16(tmem, umma_desc(ax, 128, 16 * 16), umma_desc(b1a, 128, 16 * 16), umma_idesc(128, 64), false);
             umma_commit(mb);
         }
+        load_row(tile + gridDim.x, xn);
         ok = __syncthreads_and(mbar_wait(mb, phase));   // the same decision in every thread
         phase ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
