@@ -69,9 +69,10 @@ def parse():
     ap.add_argument("--impl", default="ovl", choices=["ovl", "reference"])
     ap.add_argument("--workload", default="pile_large",
                     choices=["pile_large", "pile_mixed", "chain", "pile_small", "batched", "building", "bridge",
-                             "warmstart", "gamma"],
+                             "warmstart", "gamma", "mlp_forward"],
                     help="warmstart: the learned warm start on the large pile (log, train, "
-                         "sweeps to RMS residual 1e-4 against the previous-step warm start)")
+                         "sweeps to RMS residual 1e-4 against the previous-step warm start); "
+                         "mlp_forward: the warm start's network alone on 2^21 rows through ovl_mlp_forward")
     ap.add_argument("--ws-log-steps", type=int, default=6)
     ap.add_argument("--ws-eval-steps", type=int, default=50)
     ap.add_argument("--ws-train-steps", type=int, default=20000)
@@ -87,7 +88,7 @@ def parse():
 
 def default_settle(workload):
     return {"pile_large": 150, "pile_mixed": 150, "chain": 0, "pile_small": 0, "batched": 0,
-            "building": 0, "bridge": 0, "warmstart": 150, "gamma": 0}[workload]
+            "building": 0, "bridge": 0, "warmstart": 150, "gamma": 0, "mlp_forward": 0}[workload]
 
 
 def step_params(ovl, lb_load: str = "bodies") -> dict:
@@ -530,6 +531,43 @@ def warmstart_arm(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def mlp_forward_arm(args, rank, world, local_rank):
+    """The learned warm start's network alone (the tensor-core inference
+    kernel): 2^21 rows of 12 seeded features with seeded parameters through
+    ovl_mlp_forward, host arrays in and out; rows per second over --steps
+    calls after --warmup."""
+    import time
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    from paper_2403_17261_gb300 import ovl
+    from paper_2403_17261_gb300 import scenes as S
+
+    torch.cuda.set_device(local_rank)
+    g.build()
+    sim = ovl.Simulation(S.pile_small(), {})
+    rng = np.random.default_rng(7)
+    sim.mlp_set_params((rng.standard_normal(ovl.OVL_MLP_N_PARAMS) * 0.1).astype(np.float32))
+    n = 1 << 21
+    feat = rng.standard_normal((n, 12)).astype(np.float32)
+    for _ in range(args.warmup):
+        sim.mlp_forward(feat)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        y = sim.mlp_forward(feat)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    sim.close()
+    if rank == 0:
+        print(json.dumps({"metric": "network rows/s", "value": n / dt, "unit": "rows/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                          "data": "synthetic", "config": {"workload": "mlp_forward", "rows": n,
+                                                          "network": "12-64-64-3 ReLU"},
+                          "e2e": {"value": n / dt, "unit": "rows/s", "h2d_bytes_per_step": n * 64,
+                                  "d2h_bytes_per_step": n * 12},
+                          "y0": [float(v) for v in y[0]]}), flush=True)
+
+
 def gamma_arm(args, rank, world, local_rank):
     """Growth depth sweep and computed-versus-uniform weights on a hanging
     chain of 512 links in 8 workers, 1000 sweeps (the paper's error-study
@@ -573,6 +611,9 @@ def main():
         return
     if args.workload == "gamma":
         gamma_arm(args, rank, world, local_rank)
+        return
+    if args.workload == "mlp_forward":
+        mlp_forward_arm(args, rank, world, local_rank)
         return
     if world > 1:
         import torch
