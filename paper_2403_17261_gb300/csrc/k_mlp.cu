@@ -678,12 +678,15 @@ void launch_mlp_pack(const float *theta, uint32_t *packed, cudaStream_t s) {
 void launch_mlp_infer(const uint32_t *packed, const float4 *feat, int n, int mode, float4 *lam0,
                       float *y3, int grid_limit, int *status, cudaStream_t s) {
     if (n <= 0) return;
-    // up to 4 CTAs per SM: 4 x 128 tensor-memory columns fill an SM's 512
+    // At most 4 CTAs per SM: 4 x 128 tensor-memory columns fill an SM's 512.
+    // Unused dynamic shared memory keeps a fifth CTA off the SM, where it
+    // would wait in tcgen05.alloc for a resident one to finish.
+    constexpr int kPad = 24 * 1024;
     const int tiles = (n + 127) / 128;
     const int grid = std::min(tiles, grid_limit > 0 ? grid_limit : 152 * 4);
-    if (mode == 0) k_mlp_infer<0><<<grid, INFER_THREADS, 0, s>>>(packed, feat, n, lam0, y3, status);
-    else if (mode == 1) k_mlp_infer<1><<<grid, INFER_THREADS, 0, s>>>(packed, feat, n, lam0, y3, status);
-    else k_mlp_infer<2><<<grid, INFER_THREADS, 0, s>>>(packed, feat, n, lam0, y3, status);
+    if (mode == 0) k_mlp_infer<0><<<grid, INFER_THREADS, kPad, s>>>(packed, feat, n, lam0, y3, status);
+    else if (mode == 1) k_mlp_infer<1><<<grid, INFER_THREADS, kPad, s>>>(packed, feat, n, lam0, y3, status);
+    else k_mlp_infer<2><<<grid, INFER_THREADS, kPad, s>>>(packed, feat, n, lam0, y3, status);
     note_launch();
     CK(cudaGetLastError());
 }
