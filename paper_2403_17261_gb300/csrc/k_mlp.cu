@@ -428,8 +428,7 @@ __global__ void k_log_append(const float4 *feat, const float4 *lam, const int *p
 // ---- training --------------------------------------------------------------------
 
 constexpr int TRAIN_THREADS = 256;
-constexpr int WGRAD_THREADS = 256, WGRAD_CHUNK = 128, WGRAD_TILE = 32;
-constexpr int WGRAD_PER_THREAD = (MLP_N_PARAMS + 1 + WGRAD_THREADS - 1) / WGRAD_THREADS;
+constexpr int WGRAD_CHUNK = 128;   // samples of one gradient block (one tensor-core K = 128 product)
 
 __device__ __forceinline__ long long sample_row(const TrainArgs &a, long long step, int j) {
     if (a.sampling == 0) return a.first + (long long)(((unsigned long long)step * a.batch + j) % (unsigned long long)a.count);
@@ -529,65 +528,117 @@ __global__ void __launch_bounds__(TRAIN_THREADS) k_train_fwd(TrainArgs a) {
     }
 }
 
-// Block-partial gradients over WGRAD_CHUNK samples: every parameter is a sum
-// over samples of (operand A) x (operand B) taken from the activation rows;
-// biases have A = 1.  Slot MLP_N_PARAMS holds the block's loss sum.
-__device__ __forceinline__ void param_operands(int p, int &oa, int &ob) {
-    if (p < OFF_B1) { oa = A_X + p / 64; ob = A_DZ1 + p % 64; }
-    else if (p < OFF_W2) { oa = -1; ob = A_DZ1 + (p - OFF_B1); }
-    else if (p < OFF_B2) { const int q = p - OFF_W2; oa = A_H1 + q / 64; ob = A_DZ2 + q % 64; }
-    else if (p < OFF_W3) { oa = -1; ob = A_DZ2 + (p - OFF_B2); }
-    else if (p < OFF_B3) { const int q = p - OFF_W3; oa = A_H2 + q / 3; ob = A_DY + q % 3; }
-    else { oa = -1; ob = A_DY + (p - OFF_B3); }
-}
+// Block-partial gradients over the WGRAD_CHUNK = 128 samples of one CTA, on
+// the tensor cores: every weight gradient is a sum over samples of (operand
+// A) x (operand B) of the activation rows (all BF16 values, so the products
+// are exact), i.e. a GEMM with the samples as K:
+//   dW1 = X^T dZ1 (12 x 64), dW2 = H1^T dZ2 (64 x 64), dW3 = H2^T dY (64 x 3),
+// and a bias gradient is the same sum with A = 1.  Each GEMM is one M = 128
+// tcgen05 product over K = 128 samples (eight K-steps): A holds the
+// transposed activations in its first rows and a row of ones after them (its
+// accumulator row is the bias gradient), B the transposed deltas; thread s
+// writes sample s's column of every operand.  Accumulators: dW1 in TMEM
+// columns 0-63, dW2 in 64-127, dW3 in 128-143.  Slot MLP_N_PARAMS of a
+// block's partials holds its loss sum.
+constexpr int WG_A_BYTES = 128 * WGRAD_CHUNK * 2, WG_B_BYTES = 64 * WGRAD_CHUNK * 2, WG_B3_BYTES = 16 * WGRAD_CHUNK * 2;
+constexpr int WG_SMEM = 3 * WG_A_BYTES + 2 * WG_B_BYTES + WG_B3_BYTES;
 
-__global__ void __launch_bounds__(WGRAD_THREADS) k_train_wgrad(TrainArgs a) {
-    __shared__ float tile[WGRAD_TILE * MLP_ACT_STRIDE];
-    __shared__ float lsum[WGRAD_THREADS];
-    const int s0 = blockIdx.x * WGRAD_CHUNK, s1 = min(s0 + WGRAD_CHUNK, a.batch);
-    int oa[WGRAD_PER_THREAD], ob[WGRAD_PER_THREAD];
-    float acc[WGRAD_PER_THREAD];
-#pragma unroll
-    for (int m = 0; m < WGRAD_PER_THREAD; ++m) {
-        const int p = threadIdx.x + m * WGRAD_THREADS;
-        acc[m] = 0.f;
-        if (p < MLP_N_PARAMS) param_operands(p, oa[m], ob[m]);
-        else { oa[m] = -2; ob[m] = 0; }
-    }
-    for (int base = s0; base < s1; base += WGRAD_TILE) {
-        const int cnt = min(WGRAD_TILE, s1 - base);
-        __syncthreads();
-        for (int i = threadIdx.x; i < cnt * MLP_ACT_STRIDE; i += blockDim.x)
-            tile[i] = a.act[(size_t)base * MLP_ACT_STRIDE + i];
-        __syncthreads();
-#pragma unroll
-        for (int m = 0; m < WGRAD_PER_THREAD; ++m) {
-            if (oa[m] == -2) continue;
-            float s = acc[m];
-            if (oa[m] < 0) {
-                for (int q = 0; q < cnt; ++q) s += tile[q * MLP_ACT_STRIDE + ob[m]];
-            } else {
-                for (int q = 0; q < cnt; ++q) s += tile[q * MLP_ACT_STRIDE + oa[m]] * tile[q * MLP_ACT_STRIDE + ob[m]];
-            }
-            acc[m] = s;
+__global__ void __launch_bounds__(WGRAD_CHUNK) k_train_wgrad(TrainArgs a) {
+    extern __shared__ __align__(1024) uint8_t wsm[];
+    uint8_t *A1 = wsm, *A2 = A1 + WG_A_BYTES, *A3 = A2 + WG_A_BYTES;
+    uint8_t *B1 = A3 + WG_A_BYTES, *B2 = B1 + WG_B_BYTES, *B3 = B2 + WG_B_BYTES;
+    __shared__ float lsum[WGRAD_CHUNK];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int s0 = blockIdx.x * WGRAD_CHUNK, cnt = min(WGRAD_CHUNK, a.batch - s0);
+    for (int i = tid; i < WG_SMEM / 16; i += WGRAD_CHUNK) reinterpret_cast<uint4 *>(wsm)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    // this sample's column of every operand (zeros past the batch)
+    {
+        const bool valid = tid < cnt;
+        const float *r = a.act + (size_t)(s0 + (valid ? tid : 0)) * MLP_ACT_STRIDE;
+        auto put = [&](uint8_t *op, int row, float v) {
+            *reinterpret_cast<__nv_bfloat16 *>(op + kmajor_off(row, tid, WGRAD_CHUNK)) = __float2bfloat16_rn(valid ? v : 0.f);
+        };
+        for (int k = 0; k < 12; ++k) put(A1, k, r[A_X + k]);
+        put(A1, 12, 1.f);
+        for (int k = 0; k < 64; ++k) {
+            put(A2, k, r[A_H1 + k]);
+            put(A3, k, r[A_H2 + k]);
+            put(B1, k, r[A_DZ1 + k]);
+            put(B2, k, r[A_DZ2 + k]);
         }
+        put(A2, 64, 1.f);
+        put(A3, 64, 1.f);
+        for (int j = 0; j < 3; ++j) put(B3, j, r[A_DY + j]);
     }
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" :: "r"(dst) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+        const uint32_t sbo = WGRAD_CHUNK * 16;
+        const uint32_t a1 = (uint32_t)__cvta_generic_to_shared(A1), a2 = (uint32_t)__cvta_generic_to_shared(A2),
+                       a3 = (uint32_t)__cvta_generic_to_shared(A3), b1 = (uint32_t)__cvta_generic_to_shared(B1),
+                       b2 = (uint32_t)__cvta_generic_to_shared(B2), b3 = (uint32_t)__cvta_generic_to_shared(B3);
+#pragma unroll 1
+        for (int ks = 0; ks < WGRAD_CHUNK / 16; ++ks) {
+            const uint32_t o = 256u * ks;
+            umma_f16(tmem, umma_desc(a1 + o, 128, sbo), umma_desc(b1 + o, 128, sbo), umma_idesc(128, 64), ks > 0);
+            umma_f16(tmem + 64u, umma_desc(a2 + o, 128, sbo), umma_desc(b2 + o, 128, sbo), umma_idesc(128, 64), ks > 0);
+            umma_f16(tmem + 128u, umma_desc(a3 + o, 128, sbo), umma_desc(b3 + o, 128, sbo), umma_idesc(128, 16), ks > 0);
+        }
+        umma_commit(mb);
+    }
+    const bool ok = __syncthreads_and(mbar_wait(mb, 0));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float *out = a.partials + (size_t)blockIdx.x * (MLP_N_PARAMS + 1);
-#pragma unroll
-    for (int m = 0; m < WGRAD_PER_THREAD; ++m) {
-        const int p = threadIdx.x + m * WGRAD_THREADS;
-        if (p < MLP_N_PARAMS) out[p] = acc[m];
+    if (ok) {
+        // accumulator row tid (TMEM lane tid): weight rows, and the bias rows
+        const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+        float v[16];
+#pragma unroll 1
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            tmem_ld16(lane + c0, v);
+            for (int i = 0; i < 16; ++i) {
+                if (tid < 12) out[OFF_W1 + tid * 64 + c0 + i] = v[i];
+                else if (tid == 12) out[OFF_B1 + c0 + i] = v[i];
+            }
+            tmem_ld16(lane + 64u + c0, v);
+            for (int i = 0; i < 16; ++i) {
+                if (tid < 64) out[OFF_W2 + tid * 64 + c0 + i] = v[i];
+                else if (tid == 64) out[OFF_B2 + c0 + i] = v[i];
+            }
+        }
+        tmem_ld16(lane + 128u, v);
+        for (int j = 0; j < 3; ++j) {
+            if (tid < 64) out[OFF_W3 + tid * 3 + j] = v[j];
+            else if (tid == 64) out[OFF_B3 + j] = v[j];
+        }
+    } else {
+        if (tid == 0) atomicCAS(a.status, DEV_OK, DEV_ERR_TIMEOUT);
+        mbar_wait(mb, 0);   // the MMAs still in flight, once more (bounded)
     }
     // loss of this block's samples, summed in a fixed tree order
-    float l = 0.f;
-    for (int q = s0 + threadIdx.x; q < s1; q += blockDim.x) l += a.sample_loss[q];
-    lsum[threadIdx.x] = l;
+    lsum[tid] = tid < cnt ? a.sample_loss[s0 + tid] : 0.f;
     __syncthreads();
-    for (int w = WGRAD_THREADS / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) lsum[threadIdx.x] += lsum[threadIdx.x + w];
+    for (int w = WGRAD_CHUNK / 2; w > 0; w >>= 1) {
+        if (tid < w) lsum[tid] += lsum[tid + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[MLP_N_PARAMS] = lsum[0];
+    if (tid == 0) out[MLP_N_PARAMS] = lsum[0];
+    tc_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
 }
 
 __global__ void k_train_reduce(const float *partials, int blocks, int batch, float *grad_out,
@@ -675,15 +726,40 @@ void launch_mlp_pack(const float *theta, uint32_t *packed, cudaStream_t s) {
     CK(cudaGetLastError());
 }
 
+// Padding (dynamic shared bytes) of the inference kernel and its CTAs per SM.
+int g_infer_pad = 0, g_infer_per_sm = 4;
+
+void mlp_kernels_setup(int device) {
+    // At most 4 inference CTAs per SM: 4 x 128 tensor-memory columns fill an
+    // SM's 512, and a fifth CTA would wait in tcgen05.alloc for a resident
+    // one to finish.  Unused dynamic shared memory that makes a CTA take more
+    // than a fifth of the SM's shared memory keeps the fifth off.
+    int smem_sm = 0, reserved = 0;
+    CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+    CK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
+    cudaFuncAttributes fa{};
+    CK(cudaFuncGetAttributes(&fa, k_mlp_infer<0>));
+    const int need = smem_sm / 5 + 1 - (int)fa.sharedSizeBytes - reserved;
+    g_infer_pad = need > 0 ? (need + 15) & ~15 : 0;
+    auto infer_attr = [&](const void *k) {
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, g_infer_pad));
+    };
+    infer_attr((const void *)k_mlp_infer<0>);
+    infer_attr((const void *)k_mlp_infer<1>);
+    infer_attr((const void *)k_mlp_infer<2>);
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mlp_infer<0>, INFER_THREADS, g_infer_pad));
+    g_infer_per_sm = std::max(1, std::min(occ, 4));
+    CK(cudaFuncSetAttribute(k_train_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM));
+}
+
 void launch_mlp_infer(const uint32_t *packed, const float4 *feat, int n, int mode, float4 *lam0,
                       float *y3, int grid_limit, int *status, cudaStream_t s) {
     if (n <= 0) return;
-    // At most 4 CTAs per SM: 4 x 128 tensor-memory columns fill an SM's 512.
-    // Unused dynamic shared memory keeps a fifth CTA off the SM, where it
-    // would wait in tcgen05.alloc for a resident one to finish.
-    constexpr int kPad = 24 * 1024;
+    const int kPad = g_infer_pad;   // set by mlp_kernels_setup
     const int tiles = (n + 127) / 128;
-    const int grid = std::min(tiles, grid_limit > 0 ? grid_limit : 152 * 4);
+    const int grid = std::min(tiles, grid_limit > 0 ? grid_limit : 152 * g_infer_per_sm);
     if (mode == 0) k_mlp_infer<0><<<grid, INFER_THREADS, kPad, s>>>(packed, feat, n, lam0, y3, status);
     else if (mode == 1) k_mlp_infer<1><<<grid, INFER_THREADS, kPad, s>>>(packed, feat, n, lam0, y3, status);
     else k_mlp_infer<2><<<grid, INFER_THREADS, kPad, s>>>(packed, feat, n, lam0, y3, status);
@@ -712,7 +788,7 @@ void launch_train_fwd(const TrainArgs &a, cudaStream_t s) {
 int train_wgrad_blocks(int batch) { return (batch + WGRAD_CHUNK - 1) / WGRAD_CHUNK; }
 
 void launch_train_wgrad(const TrainArgs &a, cudaStream_t s) {
-    k_train_wgrad<<<train_wgrad_blocks(a.batch), WGRAD_THREADS, 0, s>>>(a);
+    k_train_wgrad<<<train_wgrad_blocks(a.batch), WGRAD_CHUNK, WG_SMEM, s>>>(a);
     note_launch();
     CK(cudaGetLastError());
 }

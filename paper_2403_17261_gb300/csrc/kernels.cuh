@@ -338,9 +338,13 @@ struct TrainArgs {
     float *act;                         // [batch][MLP_ACT_STRIDE]
     float *sample_loss;                 // [batch]
     float *partials;                    // [blocks][MLP_N_PARAMS + 1]
+    int *status;                        // set to DEV_ERR_TIMEOUT if a tensor-core wait gives up
 };
 void launch_train_fwd(const TrainArgs &a, cudaStream_t s);
 int train_wgrad_blocks(int batch);
+// Function attributes of the network's kernels on `device`: once per context,
+// before any of their launches (outside graph capture).
+void mlp_kernels_setup(int device);
 void launch_train_wgrad(const TrainArgs &a, cudaStream_t s);
 // sums the partials in block order; grad_out (optional) gets the gradient and
 // loss_out[0] the mean loss; with adam != 0 also updates theta, m, v

@@ -35,6 +35,7 @@ TrainArgs train_args(ovl_ctx *c, long long first, long long count, int batch, in
     a.theta = c->mlp_theta.p;
     a.act = c->train_act.p; a.sample_loss = c->train_sample_loss.p;
     a.partials = c->train_partials.p;
+    a.status = c->status.p;
     return a;
 }
 
@@ -301,7 +302,7 @@ ovl_status ovl_mlp_train(ovl_ctx *c, const ovl_train_desc *d, float *loss_per_st
         launch_mlp_pack(c->mlp_theta.p, c->mlp_packed.p, c->stream);
         if (loss_per_step && d->steps > 0) download(loss_per_step, c->train_loss_hist.p, (size_t)d->steps, c->stream);
         CK(cudaStreamSynchronize(c->stream));
-        return OVL_OK;
+        return check_device_status(c);
     });
 }
 
@@ -323,7 +324,7 @@ ovl_status ovl_mlp_grad(ovl_ctx *c, int64_t first, int64_t count, float *grad, d
         download(&l, c->mlp_loss.p, 1, c->stream);
         CK(cudaStreamSynchronize(c->stream));
         if (loss) *loss = l;
-        return OVL_OK;
+        return check_device_status(c);
     });
 }
 
