@@ -382,7 +382,7 @@ __global__ void k_lb_compact(const int2 *__restrict__ c_ab, int nc, const int *_
 }
 
 // ---- gamma-balls for the load balance --------------------------------------
-// The vertex set within gamma hops of a root in G^t (Algorithm 6, line 12)
+// The vertex set within gamma hops of a root in G^t (the ball an activation of Algorithm 6 adds)
 // depends on the graph only, which Algorithm 6 does not change, so it is
 // found for every possible root before the sequential pass: one warp per
 // body that is an end of a candidate contact, breadth first, level by
