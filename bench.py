@@ -69,10 +69,12 @@ def parse():
     ap.add_argument("--impl", default="ovl", choices=["ovl", "reference"])
     ap.add_argument("--workload", default="pile_large",
                     choices=["pile_large", "pile_mixed", "chain", "pile_small", "batched", "building", "bridge",
-                             "warmstart", "gamma", "mlp_forward"],
+                             "warmstart", "gamma", "mlp_forward", "mlp_train"],
                     help="warmstart: the learned warm start on the large pile (log, train, "
                          "sweeps to RMS residual 1e-4 against the previous-step warm start); "
-                         "mlp_forward: the warm start's network alone on 2^21 rows through ovl_mlp_forward")
+                         "mlp_forward: the warm start's network alone on 2^21 rows through ovl_mlp_forward; "
+                         "mlp_train: its training alone (Adam, batches of 4096 drawn from 2^20 logged rows) "
+                         "through ovl_mlp_train")
     ap.add_argument("--ws-log-steps", type=int, default=6)
     ap.add_argument("--ws-eval-steps", type=int, default=50)
     ap.add_argument("--ws-train-steps", type=int, default=20000)
@@ -88,7 +90,8 @@ def parse():
 
 def default_settle(workload):
     return {"pile_large": 150, "pile_mixed": 150, "chain": 0, "pile_small": 0, "batched": 0,
-            "building": 0, "bridge": 0, "warmstart": 150, "gamma": 0, "mlp_forward": 0}[workload]
+            "building": 0, "bridge": 0, "warmstart": 150, "gamma": 0, "mlp_forward": 0,
+            "mlp_train": 0}[workload]
 
 
 def step_params(ovl, lb_load: str = "bodies") -> dict:
@@ -568,6 +571,47 @@ def mlp_forward_arm(args, rank, world, local_rank):
                           "y0": [float(v) for v in y[0]]}), flush=True)
 
 
+def mlp_train_arm(args, rank, world, local_rank):
+    """The learned warm start's training alone (forward and backward passes,
+    tensor-core weight gradients, Adam): 2^20 seeded rows in the context's
+    log, then per step one ovl_mlp_train call of 500 Adam steps on batches of
+    4096 rows drawn with replacement; training rows per second over --steps
+    calls after --warmup (each call returns its per-step losses to the host)."""
+    import time
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    from paper_2403_17261_gb300 import ovl
+    from paper_2403_17261_gb300 import scenes as S
+
+    torch.cuda.set_device(local_rank)
+    g.build()
+    sim = ovl.Simulation(S.pile_small(), {})
+    n, batch, adam_steps = 1 << 20, 4096, 500
+    X, T = S.synthetic_rows(n, seed=8)
+    sim.log_reserve(n)
+    sim.log_append(X, T)
+    sim.mlp_set_params(S.mlp_init_params(9))
+    for k in range(args.warmup):
+        sim.mlp_train(0, n, batch, adam_steps, seed=k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        loss = sim.mlp_train(0, n, batch, adam_steps, seed=100 + k)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    sim.close()
+    if rank == 0:
+        rows = batch * adam_steps
+        print(json.dumps({"metric": "training rows/s", "value": rows / dt, "unit": "rows/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                          "data": "synthetic", "config": {"workload": "mlp_train", "logged_rows": n,
+                                                          "batch": batch, "adam_steps_per_call": adam_steps,
+                                                          "network": "12-64-64-3 ReLU"},
+                          "e2e": {"value": rows / dt, "unit": "rows/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 4 * adam_steps},
+                          "final_loss": float(np.asarray(loss).reshape(-1)[-1])}), flush=True)
+
+
 def gamma_arm(args, rank, world, local_rank):
     """Growth depth sweep and computed-versus-uniform weights on a hanging
     chain of 512 links in 8 workers, 1000 sweeps (the paper's error-study
@@ -614,6 +658,9 @@ def main():
         return
     if args.workload == "mlp_forward":
         mlp_forward_arm(args, rank, world, local_rank)
+        return
+    if args.workload == "mlp_train":
+        mlp_train_arm(args, rank, world, local_rank)
         return
     if world > 1:
         import torch
