@@ -168,8 +168,9 @@ ovl_status ovl_default_params(ovl_params *p);
 
 /* Creates a context on the current CUDA device.  cuda_stream: a cudaStream_t
  * to run on, or NULL for a stream the context owns.  *out receives the
- * context; destroy it with ovl_destroy.  The context also creates six side
- * streams for concurrent per-class launches.  It sets the environment
+ * context; destroy it with ovl_destroy.  The context also creates seven side
+ * streams: six for concurrent per-class launches (priorities falling in
+ * launch order) and one for the geodesic weights.  It sets the environment
  * variable CUDA_DEVICE_MAX_CONNECTIONS to 32 when it is unset, so that those
  * streams get hardware queues of their own.  That takes effect only if the
  * process has not yet created its CUDA context; otherwise, set the variable

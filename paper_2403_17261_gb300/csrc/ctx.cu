@@ -205,8 +205,9 @@ void phase_load_balance(ovl_ctx *c, bool act, bool deact) {
     if ((int)c->lb_ws.size() != c->lb_threads) c->lb_ws.resize(c->lb_threads);
     host_load_balance(c->hs, c->h_mask.p, c->h_loads.p, by_contacts ? c->h_deg.p : nullptr, m, c->h_ab.p,
                       c->h_rp.p, c->h_col.p, act, deact, c->lb_ws, hb_start, hb_vtx);
+    // no wait for the copy: the next kernels are ordered after it on s, and
+    // the host touches h_mask again only after the next download into it
     CK(cudaMemcpyAsync(c->mask.p, c->h_mask.p, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));
     c->lb_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
@@ -505,20 +506,22 @@ std::vector<size_t> class_launch_order(ovl_ctx *c, const std::vector<SolveClass>
     return ord;
 }
 
-// launches class ord[j] (all classes when ord is empty) on the context's
-// stream (j = 0) or a side stream, then joins them
+// launches class ord[j] (all classes when ord is empty) on side stream j
+// (priorities falling with j), forked from and joined into the context's
+// stream
 template <class F>
 void run_on_streams(ovl_ctx *c, size_t n, F &&launch, const std::vector<size_t> &ord = {}) {
+    if (n > sizeof(c->aux) / sizeof(c->aux[0])) throw std::logic_error("more launch classes than side streams");
+    if (n == 0) return;
     CK(cudaEventRecord(c->fork, c->stream));
     for (size_t j = 0; j < n; ++j) {
         const size_t k = ord.empty() ? j : ord[j];
-        cudaStream_t sk = j == 0 ? c->stream : c->aux[j - 1];
-        if (j) CK(cudaStreamWaitEvent(sk, c->fork, 0));
-        launch(k, sk);
+        CK(cudaStreamWaitEvent(c->aux[j], c->fork, 0));
+        launch(k, c->aux[j]);
     }
-    for (size_t k = 1; k < n; ++k) {
-        CK(cudaEventRecord(c->join[k - 1], c->aux[k - 1]));
-        CK(cudaStreamWaitEvent(c->stream, c->join[k - 1], 0));
+    for (size_t j = 0; j < n; ++j) {
+        CK(cudaEventRecord(c->join[j], c->aux[j]));
+        CK(cudaStreamWaitEvent(c->stream, c->join[j], 0));
     }
 }
 
@@ -1022,7 +1025,13 @@ ovl_status ovl_create(ovl_ctx **out, const ovl_params *p, void *cuda_stream) {
             c->own_stream = true;
         }
         for (auto &e : c->ev) CK(cudaEventCreate(&e));
-        for (auto &x : c->aux) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        // the class launched first gets the highest priority, so that when a
+        // plan has more CTAs than SMs its CTAs are placed before the later
+        // classes' (numerically lower is higher)
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        for (int j = 0; j < (int)(sizeof(c->aux) / sizeof(c->aux[0])); ++j)
+            CK(cudaStreamCreateWithPriority(&c->aux[j], cudaStreamNonBlocking, std::min(least, greatest + j)));
         CK(cudaStreamCreateWithFlags(&c->geo_stream, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&c->geo_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->geo_join, cudaEventDisableTiming));

@@ -105,10 +105,10 @@ struct ovl_ctx {
     DBuf<uint8_t> row_owner;                     // owner CTA of every row (scratch of the grouping)
     DBuf<uint8_t> row_full;                      // rows with a box end (contexts with boxes)
     DBuf<float4> rfull;                          // their records, FULL_ROW_WORDS float4 per row
-    cudaStream_t aux[5] = {};                    // side streams of the per-class solve launches
+    cudaStream_t aux[6] = {};                    // per-class launches, priorities falling with the index
     cudaStream_t geo_stream = nullptr;           // the geodesic weights, beside colouring and solve
     cudaEvent_t geo_fork = nullptr, geo_join = nullptr;
-    cudaEvent_t fork = nullptr, join[5] = {};
+    cudaEvent_t fork = nullptr, join[6] = {};
     cudaGraphExec_t geo_exec = nullptr;          // the geodesic phase, captured
     std::vector<const void *> geo_key;           // its arguments when captured
     long long geo_kernels = 0;
