@@ -392,7 +392,7 @@ __device__ __forceinline__ int cluster_int_sum(int *v) {
 // instantiations of colour_worker (cluster slots and the global-memory
 // fallback) share it instead of each holding its own copy.
 struct ColourShared {
-    int n_next, ncol_sh, pub_left, pub_ncol;
+    int n_next, ncol_sh, pub_left[2], pub_ncol;   // pub_left: by round parity
     int counts[NBUCKET + 1];
     int base_b[NBUCKET + 1];
     int running[NBUCKET];
@@ -401,7 +401,8 @@ struct ColourShared {
 
 template <int C, class SL>
 __device__ void colour_worker(const ColourArgs &a, const SL &S, ColourShared &sh, int p, int rank, int per) {
-    int &n_next = sh.n_next, &ncol_sh = sh.ncol_sh, &pub_left = sh.pub_left, &pub_ncol = sh.pub_ncol;
+    int &n_next = sh.n_next, &ncol_sh = sh.ncol_sh, &pub_ncol = sh.pub_ncol;
+    int *pub_left = sh.pub_left;
     int (&counts)[NBUCKET + 1] = sh.counts;
     int (&base_b)[NBUCKET + 1] = sh.base_b;
     int (&running)[NBUCKET] = sh.running;
@@ -508,9 +509,12 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, ColourShared &sh
             atomicMax(&ncol_sh, c + 1);
         }
         __syncthreads();
-        if (tid == 0) pub_left = n_next;
+        // the count of this round goes to pub_left[rounds & 1]: it is written
+        // again two rounds later, after the barriers of the next round, which
+        // every CTA passes only once it has summed this one
+        if (tid == 0) pub_left[rounds & 1] = n_next;
         csync<C>();
-        const int left = cluster_int_sum<C>(&pub_left);
+        const int left = cluster_int_sum<C>(&pub_left[rounds & 1]);
         m = n_next;
         ++rounds;
         __syncthreads();
@@ -518,7 +522,6 @@ __device__ void colour_worker(const ColourArgs &a, const SL &S, ColourShared &sh
         { int4 *t = wl_cur; wl_cur = wl_next; wl_next = t; }
         { unsigned long long *t = pr_cur; pr_cur = pr_next; pr_next = t; }
         if (left == 0) break;
-        csync<C>();   // the counts published above stay readable until every CTA has summed them
     }
     if (rank == 0 && tid == 0 && rounds > nq + 1) atomicCAS(a.status, DEV_OK, DEV_ERR_TIMEOUT);
     // stable counting sort of the worker's constraints by (colour, kind):
