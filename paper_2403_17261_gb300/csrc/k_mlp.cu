@@ -30,6 +30,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <stdexcept>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -726,10 +727,15 @@ void launch_mlp_pack(const float *theta, uint32_t *packed, cudaStream_t s) {
     CK(cudaGetLastError());
 }
 
-// Padding (dynamic shared bytes) of the inference kernel and its CTAs per SM.
-int g_infer_pad = 0, g_infer_per_sm = 4;
+// Launch shape of the inference kernel on each device: the padding (dynamic
+// shared bytes) that caps its CTAs per SM, the CTAs per SM and the SM count.
+struct InferShape { int pad = 0, per_sm = 4, sms = 0; };
+constexpr int kMaxDevices = 64;
+InferShape g_infer[kMaxDevices];
 
 void mlp_kernels_setup(int device) {
+    if (device < 0 || device >= kMaxDevices) throw std::invalid_argument("device ordinal out of range");
+    InferShape &g = g_infer[device];
     // At most 4 inference CTAs per SM: 4 x 128 tensor-memory columns fill an
     // SM's 512, and a fifth CTA would wait in tcgen05.alloc for a resident
     // one to finish.  Unused dynamic shared memory that makes a CTA take more
@@ -740,26 +746,34 @@ void mlp_kernels_setup(int device) {
     cudaFuncAttributes fa{};
     CK(cudaFuncGetAttributes(&fa, k_mlp_infer<0>));
     const int need = smem_sm / 5 + 1 - (int)fa.sharedSizeBytes - reserved;
-    g_infer_pad = need > 0 ? (need + 15) & ~15 : 0;
+    const int pad = need > 0 ? (need + 15) & ~15 : 0;
     auto infer_attr = [&](const void *k) {
         CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
-        CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, g_infer_pad));
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, pad));
     };
     infer_attr((const void *)k_mlp_infer<0>);
     infer_attr((const void *)k_mlp_infer<1>);
     infer_attr((const void *)k_mlp_infer<2>);
-    int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mlp_infer<0>, INFER_THREADS, g_infer_pad));
-    g_infer_per_sm = std::max(1, std::min(occ, 4));
+    int occ = 0, sms = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mlp_infer<0>, INFER_THREADS, pad));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    g.pad = pad;
+    g.per_sm = std::max(1, std::min(occ, 4));
+    g.sms = sms;
     CK(cudaFuncSetAttribute(k_train_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM));
 }
 
 void launch_mlp_infer(const uint32_t *packed, const float4 *feat, int n, int mode, float4 *lam0,
                       float *y3, int grid_limit, int *status, cudaStream_t s) {
     if (n <= 0) return;
-    const int kPad = g_infer_pad;   // set by mlp_kernels_setup
+    int device = -1;
+    CK(cudaGetDevice(&device));
+    if (device < 0 || device >= kMaxDevices || g_infer[device].sms == 0)
+        throw std::logic_error("the network's kernels are not set up on this device");
+    const InferShape &g = g_infer[device];   // set by mlp_kernels_setup
+    const int kPad = g.pad;
     const int tiles = (n + 127) / 128;
-    const int grid = std::min(tiles, grid_limit > 0 ? grid_limit : 152 * g_infer_per_sm);
+    const int grid = std::min(tiles, grid_limit > 0 ? grid_limit : g.sms * g.per_sm);
     if (mode == 0) k_mlp_infer<0><<<grid, INFER_THREADS, kPad, s>>>(packed, feat, n, lam0, y3, status);
     else if (mode == 1) k_mlp_infer<1><<<grid, INFER_THREADS, kPad, s>>>(packed, feat, n, lam0, y3, status);
     else k_mlp_infer<2><<<grid, INFER_THREADS, kPad, s>>>(packed, feat, n, lam0, y3, status);
