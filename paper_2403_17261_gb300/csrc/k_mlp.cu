@@ -22,11 +22,12 @@
 // per CTA at a time (one MMA for layer 1, four K-steps each for layers 2 and
 // 3); the epilogue of each layer reads its accumulator rows from tensor
 // memory (tcgen05.ld), adds the bias, applies the ReLU and writes the next
-// layer's BF16 operand to shared memory.  Training uses the same arithmetic
-// on CUDA cores (operands rounded to BF16, products exact in FP32, FP32
-// sums): one thread per sample for the forward and backward passes,
-// block-partial weight gradients summed in block order (deterministic), and
-// Adam on FP32 master parameters.
+// layer's BF16 operand to shared memory.  Training runs on the tensor cores
+// too, with the same arithmetic (operands rounded to BF16, products exact,
+// FP32 sums): the forward and backward passes of 128 samples per CTA as five
+// products, the weight gradients of 128 samples per CTA as three products
+// with the samples as K, summed over blocks in block order (deterministic),
+// and Adam on FP32 master parameters.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -400,7 +401,7 @@ __global__ void __launch_bounds__(INFER_THREADS) k_mlp_infer(const uint32_t *pk,
     }
     if (!ok) {
         if (tid == 0) atomicCAS(status, DEV_OK, DEV_ERR_TIMEOUT);
-        mbar_wait(mb, phase);   // an MMA still in flight, once more (bounded)
+        mbar_wait(mb, phase ^ 1u);   // the product that was not seen to finish, once more (bounded)
     }
     tc_sync();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(INFER_COLS) : "memory");
@@ -428,7 +429,6 @@ __global__ void k_log_append(const float4 *feat, const float4 *lam, const int *p
 
 // ---- training --------------------------------------------------------------------
 
-constexpr int TRAIN_THREADS = 256;
 constexpr int WGRAD_CHUNK = 128;   // samples of one gradient block (one tensor-core K = 128 product)
 
 __device__ __forceinline__ long long sample_row(const TrainArgs &a, long long step, int j) {
@@ -437,96 +437,217 @@ __device__ __forceinline__ long long sample_row(const TrainArgs &a, long long st
     return a.first + (long long)(z % (uint64_t)a.count);
 }
 
-// Forward, loss and the backward pass down to the pre-activation gradients,
-// one warp per sample at a time: lane l owns hidden units l and l + 32, and
-// the activations of the layer below are broadcast by shuffles.  The
-// operands every product uses (x, h1, h2, dy, dz2 and the weights) are
-// rounded to BF16; sums are FP32 in a fixed order.
-__device__ __forceinline__ float warp_sum(float v) {
+// Forward, loss and the backward pass down to the pre-activation gradients
+// of one tile of 128 samples per CTA, on the tensor cores; thread t owns
+// sample t of the tile (TMEM lane t).  Five products, each M = 128 with BF16
+// operands in shared memory and FP32 accumulators in tensor memory:
+//   D1 = X W1 (K 16), D2 = H1 W2 (K 64), D3 = H2 W3 (N 16, K 64),
+//   T2 = dY W3^T (K 16, dY in columns 0-2), T1 = dZ2 W2^T (K 64),
+// with h1 = bf16(relu(D1 + b1)), h2 = bf16(relu(D2 + b2)), y = (D3 + b3) +
+// x[4..6] (the skip connection in FP32), dy = bf16(2 (y - t) / (3 B)),
+// dz2 = bf16(T2) where h2 > 0, dz1 = bf16(T1) where h1 > 0.  Every operand
+// of a product is BF16 (the products exact) and the sums FP32.  The B
+// operands are built from the FP32 parameters by every CTA.  Accumulators:
+// D1 and then T1 in TMEM columns 0-63, D2 in 64-127, D3 in 128-143, T2 in
+// 192-255.  Waits on the MMAs are bounded; one that gives up sets the device
+// status, and the CTA waits once more and frees its tensor memory.
+constexpr int TRAIN_TILE = 128, TRAIN_COLS = 256;
+constexpr int TF_X = 0, TF_H1 = TF_X + 128 * 16 * 2, TF_H2 = TF_H1 + 128 * 64 * 2, TF_DY = TF_H2 + 128 * 64 * 2,
+              TF_DZ2 = TF_DY + 128 * 16 * 2, TF_B1 = TF_DZ2 + 128 * 64 * 2, TF_B2 = TF_B1 + 64 * 16 * 2,
+              TF_B3 = TF_B2 + 64 * 64 * 2, TF_B4 = TF_B3 + 16 * 64 * 2, TF_B5 = TF_B4 + 64 * 16 * 2,
+              TF_SMEM = TF_B5 + 64 * 64 * 2;
+// two CTAs per SM at most: each holds half of the SM's 512 tensor-memory
+// columns, and a third would wait in tcgen05.alloc
+static_assert(3 * (TF_SMEM + 2048) > 228 * 1024 && 2 * (TF_SMEM + 2048) <= 227 * 1024, "two CTAs per SM");
+
+// one row (K columns) of a K-major BF16 operand from FP32 values
+template <int K>
+__device__ __forceinline__ void put_row(uint8_t *op, int r, const float *v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int c = 0; c < K; c += 8) {
+        uint4 q;
+        q.x = pack_bf16(v[c], v[c + 1]); q.y = pack_bf16(v[c + 2], v[c + 3]);
+        q.z = pack_bf16(v[c + 4], v[c + 5]); q.w = pack_bf16(v[c + 6], v[c + 7]);
+        *reinterpret_cast<uint4 *>(op + kmajor_off(r, c, K)) = q;
+    }
 }
 
-__global__ void __launch_bounds__(TRAIN_THREADS) k_train_fwd(TrainArgs a) {
-    __shared__ float W[MLP_N_PARAMS];
-    __shared__ float W2T[64 * 64];   // W2 transposed: [out][in]
-    for (int i = threadIdx.x; i < MLP_N_PARAMS; i += blockDim.x) {
-        const bool bias = (i >= OFF_B1 && i < OFF_W2) || (i >= OFF_B2 && i < OFF_W3) || i >= OFF_B3;
-        W[i] = bias ? a.theta[i] : bf16r(a.theta[i]);
+__global__ void __launch_bounds__(TRAIN_TILE) k_train_fwd(TrainArgs a) {
+    extern __shared__ __align__(1024) uint8_t tsm[];
+    __shared__ float sb[64 + 64 + 4];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // B operands from the parameters: row n, column k
+    {
+        const float *th = a.theta;
+        auto put = [&](int off, int r, int k, int K, float v) {
+            *reinterpret_cast<__nv_bfloat16 *>(tsm + off + kmajor_off(r, k, K)) = __float2bfloat16_rn(v);
+        };
+        for (int e = tid; e < 64 * 16; e += TRAIN_TILE) {
+            const int n = e / 16, k = e % 16;
+            put(TF_B1, n, k, 16, k < 12 ? th[OFF_W1 + k * 64 + n] : 0.f);        // W1^T
+            put(TF_B4, n, k, 16, k < 3 ? th[OFF_W3 + n * 3 + k] : 0.f);          // (W3^T)^T = W3
+        }
+        for (int e = tid; e < 64 * 64; e += TRAIN_TILE) {
+            const int n = e / 64, k = e % 64;
+            put(TF_B2, n, k, 64, th[OFF_W2 + k * 64 + n]);                       // W2^T
+            put(TF_B5, n, k, 64, th[OFF_W2 + n * 64 + k]);                       // (W2^T)^T = W2
+        }
+        for (int e = tid; e < 16 * 64; e += TRAIN_TILE) {
+            const int n = e / 64, k = e % 64;
+            put(TF_B3, n, k, 64, n < 3 ? th[OFF_W3 + k * 3 + n] : 0.f);          // W3^T
+        }
+        for (int e = tid; e < 64; e += TRAIN_TILE) { sb[e] = th[OFF_B1 + e]; sb[64 + e] = th[OFF_B2 + e]; }
+        if (tid < 4) sb[128 + tid] = tid < 3 ? th[OFF_B3 + tid] : 0.f;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) W2T[(i % 64) * 64 + i / 64] = W[OFF_W2 + i];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    const unsigned full = 0xffffffffu;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(dst), "n"(TRAIN_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // this thread's sample: features (rounded to BF16 for the product, FP32
+    // for the skip connection) and targets
     const long long step = a.step_dev ? *a.step_dev : a.step;
-    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < a.batch; j += warps) {
-        const long long r = sample_row(a, step, j);
-        const float xraw = lane < 12 ? a.log_feat[12 * r + lane] : 0.f;
-        const float xv = bf16r(xraw);
-        float z1a = W[OFF_B1 + lane], z1b = W[OFF_B1 + lane + 32];
+    const int j = blockIdx.x * TRAIN_TILE + tid;
+    const bool valid = j < a.batch;
+    float xraw[12], targ[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {
-            const float x = __shfl_sync(full, xv, i);
-            z1a += x * W[OFF_W1 + i * 64 + lane];
-            z1b += x * W[OFF_W1 + i * 64 + lane + 32];
-        }
-        const float h1a = bf16r(fmaxf(z1a, 0.f)), h1b = bf16r(fmaxf(z1b, 0.f));
-        float z2a = W[OFF_B2 + lane], z2b = W[OFF_B2 + lane + 32];
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-            const float h = __shfl_sync(full, h1a, k);
-            z2a += h * W[OFF_W2 + k * 64 + lane];
-            z2b += h * W[OFF_W2 + k * 64 + lane + 32];
-        }
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-            const float h = __shfl_sync(full, h1b, k);
-            z2a += h * W[OFF_W2 + (k + 32) * 64 + lane];
-            z2b += h * W[OFF_W2 + (k + 32) * 64 + lane + 32];
-        }
-        const float h2a = bf16r(fmaxf(z2a, 0.f)), h2b = bf16r(fmaxf(z2b, 0.f));
-        float y[3], dy[3], loss = 0.f;
-#pragma unroll
-        for (int o = 0; o < 3; ++o) {
-            y[o] = W[OFF_B3 + o] + warp_sum(h2a * W[OFF_W3 + lane * 3 + o] + h2b * W[OFF_W3 + (lane + 32) * 3 + o]) +
-                   __shfl_sync(full, xraw, 4 + o);   // skip connection, FP32
-            const float d = y[o] - a.log_targ[3 * r + o];
-            loss += d * d;
-            dy[o] = bf16r(2.f * d / (3.f * (float)a.batch));
-        }
-        if (lane == 0) a.sample_loss[j] = loss;
-        if (!a.backward) continue;
-        float *act = a.act + (size_t)j * MLP_ACT_STRIDE;
-        if (lane < 16) act[A_X + lane] = xv;
-        act[A_H1 + lane] = h1a; act[A_H1 + lane + 32] = h1b;
-        act[A_H2 + lane] = h2a; act[A_H2 + lane + 32] = h2b;
-        if (lane < 4) act[A_DY + lane] = lane == 0 ? dy[0] : (lane == 1 ? dy[1] : (lane == 2 ? dy[2] : 0.f));
-        // dz2 = (W3 dy) where h2 > 0
-        const float sa = W[OFF_W3 + lane * 3] * dy[0] + W[OFF_W3 + lane * 3 + 1] * dy[1] + W[OFF_W3 + lane * 3 + 2] * dy[2];
-        const float sb = W[OFF_W3 + (lane + 32) * 3] * dy[0] + W[OFF_W3 + (lane + 32) * 3 + 1] * dy[1] +
-                         W[OFF_W3 + (lane + 32) * 3 + 2] * dy[2];
-        const float dz2a = h2a > 0.f ? bf16r(sa) : 0.f, dz2b = h2b > 0.f ? bf16r(sb) : 0.f;
-        act[A_DZ2 + lane] = dz2a; act[A_DZ2 + lane + 32] = dz2b;
-        // dz1 = (W2 dz2) where h1 > 0
-        float ta = 0.f, tb = 0.f;
-#pragma unroll 8
-        for (int u = 0; u < 32; ++u) {
-            const float d = __shfl_sync(full, dz2a, u);
-            ta += W2T[u * 64 + lane] * d;
-            tb += W2T[u * 64 + lane + 32] * d;
-        }
-#pragma unroll 8
-        for (int u = 0; u < 32; ++u) {
-            const float d = __shfl_sync(full, dz2b, u);
-            ta += W2T[(u + 32) * 64 + lane] * d;
-            tb += W2T[(u + 32) * 64 + lane + 32] * d;
-        }
-        act[A_DZ1 + lane] = h1a > 0.f ? bf16r(ta) : 0.f;
-        act[A_DZ1 + lane + 32] = h1b > 0.f ? bf16r(tb) : 0.f;
+    for (int k = 0; k < 12; ++k) xraw[k] = 0.f;
+    long long r = 0;
+    if (valid) {
+        r = sample_row(a, step, j);
+        const float4 *f = reinterpret_cast<const float4 *>(a.log_feat + 12 * r);
+        const float4 f0 = f[0], f1 = f[1], f2 = f[2];
+        xraw[0] = f0.x; xraw[1] = f0.y; xraw[2] = f0.z; xraw[3] = f0.w; xraw[4] = f1.x; xraw[5] = f1.y;
+        xraw[6] = f1.z; xraw[7] = f1.w; xraw[8] = f2.x; xraw[9] = f2.y; xraw[10] = f2.z; xraw[11] = f2.w;
+        targ[0] = a.log_targ[3 * r]; targ[1] = a.log_targ[3 * r + 1]; targ[2] = a.log_targ[3 * r + 2];
     }
+    float *act = a.act + (size_t)(valid ? j : 0) * MLP_ACT_STRIDE;
+    const bool wr = valid && a.backward;
+    {
+        float x[16];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) x[k] = bf16r(xraw[k]);
+        x[12] = x[13] = x[14] = x[15] = 0.f;
+        put_row<16>(tsm + TF_X, tid, x);
+        if (wr)
+#pragma unroll
+            for (int c = 0; c < 16; c += 4) *reinterpret_cast<float4 *>(act + A_X + c) = make_float4(x[c], x[c + 1], x[c + 2], x[c + 3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(tsm);
+    uint32_t phase = 0;
+    bool ok = true;
+    // one product (ks K-steps of 16) into columns dcol, then the wait
+    auto mma = [&](uint32_t dcol, int aoff, int boff, int K, int N) {
+        if (tid == 0) {
+            const uint32_t sbo = (uint32_t)K * 16u;
+            for (int ks = 0; ks < K / 16; ++ks)
+                umma_f16(tmem + dcol, umma_desc(base + aoff + 256u * ks, 128, sbo),
+                         umma_desc(base + boff + 256u * ks, 128, sbo), umma_idesc(128, N), ks > 0);
+            umma_commit(mb);
+        }
+        ok = __syncthreads_and(mbar_wait(mb, phase));
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    };
+    uint64_t m1 = 0, m2 = 0;   // h1 > 0, h2 > 0 per hidden unit
+    // h = bf16(relu(D + b)) into the next operand (and the activation row)
+    auto hidden = [&](uint32_t dcol, const float *bias, int opoff, int aoff_act, uint64_t &mask) {
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tmem_ld16(lane_base + dcol + c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                v[i] = bf16r(fmaxf(v[i] + bias[c0 + i], 0.f));
+                if (v[i] > 0.f) mask |= 1ull << (c0 + i);
+            }
+            uint8_t *op = tsm + opoff;
+#pragma unroll
+            for (int c = 0; c < 16; c += 8) {
+                uint4 q;
+                q.x = pack_bf16(v[c], v[c + 1]); q.y = pack_bf16(v[c + 2], v[c + 3]);
+                q.z = pack_bf16(v[c + 4], v[c + 5]); q.w = pack_bf16(v[c + 6], v[c + 7]);
+                *reinterpret_cast<uint4 *>(op + kmajor_off(tid, c0 + c, 64)) = q;
+            }
+            if (wr)
+#pragma unroll
+                for (int c = 0; c < 16; c += 4)
+                    *reinterpret_cast<float4 *>(act + aoff_act + c0 + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_sync();
+    };
+    // delta = bf16(T) where the unit is active, into the activation row (and
+    // an operand when opoff >= 0)
+    auto delta = [&](uint32_t dcol, uint64_t mask, int opoff, int aoff_act) {
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tmem_ld16(lane_base + dcol + c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = (mask >> (c0 + i) & 1ull) ? bf16r(v[i]) : 0.f;
+            if (opoff >= 0) {
+                uint8_t *op = tsm + opoff;
+#pragma unroll
+                for (int c = 0; c < 16; c += 8) {
+                    uint4 q;
+                    q.x = pack_bf16(v[c], v[c + 1]); q.y = pack_bf16(v[c + 2], v[c + 3]);
+                    q.z = pack_bf16(v[c + 4], v[c + 5]); q.w = pack_bf16(v[c + 6], v[c + 7]);
+                    *reinterpret_cast<uint4 *>(op + kmajor_off(tid, c0 + c, 64)) = q;
+                }
+            }
+            if (wr)
+#pragma unroll
+                for (int c = 0; c < 16; c += 4)
+                    *reinterpret_cast<float4 *>(act + aoff_act + c0 + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_sync();
+    };
+    mma(0u, TF_X, TF_B1, 16, 64);
+    if (ok) { hidden(0u, sb, TF_H1, A_H1, m1); mma(64u, TF_H1, TF_B2, 64, 64); }
+    if (ok) { hidden(64u, sb + 64, TF_H2, A_H2, m2); mma(128u, TF_H2, TF_B3, 64, 16); }
+    if (ok) {
+        float o[16];
+        tmem_ld16(lane_base + 128u, o);
+        float dy[16], loss = 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) dy[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float y = (o[k] + sb[128 + k]) + xraw[4 + k];
+            const float d = y - targ[k];
+            loss += d * d;
+            dy[k] = bf16r(2.f * d / (3.f * (float)a.batch));
+        }
+        if (valid) a.sample_loss[j] = loss;
+        if (wr) *reinterpret_cast<float4 *>(act + A_DY) = make_float4(dy[0], dy[1], dy[2], 0.f);
+        if (a.backward) {
+            put_row<16>(tsm + TF_DY, tid, dy);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_sync();
+            mma(192u, TF_DY, TF_B4, 16, 64);
+            if (ok) { delta(192u, m2, TF_DZ2, A_DZ2); mma(0u, TF_DZ2, TF_B5, 64, 64); }
+            if (ok) delta(0u, m1, -1, A_DZ1);
+        }
+    }
+    if (!ok) {
+        if (tid == 0) atomicCAS(a.status, DEV_OK, DEV_ERR_TIMEOUT);
+        mbar_wait(mb, phase ^ 1u);   // the product that was not seen to finish, once more (bounded)
+    }
+    tc_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(TRAIN_COLS) : "memory");
 }
 
 // Block-partial gradients over the WGRAD_CHUNK = 128 samples of one CTA, on
@@ -761,6 +882,7 @@ void mlp_kernels_setup(int device) {
     g.per_sm = std::max(1, std::min(occ, 4));
     g.sms = sms;
     CK(cudaFuncSetAttribute(k_train_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM));
+    CK(cudaFuncSetAttribute(k_train_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM));
 }
 
 void launch_mlp_infer(const uint32_t *packed, const float4 *feat, int n, int mode, float4 *lam0,
@@ -792,9 +914,7 @@ void launch_log_append(const float4 *feat, const float4 *lam, const int *pos, in
 }
 
 void launch_train_fwd(const TrainArgs &a, cudaStream_t s) {
-    const int warps_per_block = TRAIN_THREADS / 32;
-    const int grid = std::min((a.batch + warps_per_block - 1) / warps_per_block, 152 * 2);
-    k_train_fwd<<<grid, TRAIN_THREADS, 0, s>>>(a);
+    k_train_fwd<<<(a.batch + TRAIN_TILE - 1) / TRAIN_TILE, TRAIN_TILE, TF_SMEM, s>>>(a);
     note_launch();
     CK(cudaGetLastError());
 }
